@@ -1,0 +1,478 @@
+"""CPU FP64 oracle of the cache-accelerated INR volume renderer.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``; never by the
+product path.  The arithmetic lives in ``cinr_oracle.c`` (plain C, FP64 for
+values, binary32 without FMA contraction for every discrete decision); this
+module only builds that library with gcc and marshals numpy arrays.
+
+Pins (tests/test_oracle_pins.py) tie each function to something other than
+itself: closed forms (constant-density slab, linear-field interpolation),
+brute force on tiny grids (dense bijection, hash range), the paper's worked
+brick-origin example (Sec. 4.3.2), a hand-computed MLP, finite differences
+for the training gradient, and scripted cache scenarios checked by hand.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cinr_oracle.c")
+_HDR = os.path.join(_HERE, "cinr_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+          "-shared", "-Wall"]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (no GPU, no CUDA)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = (not os.path.exists(_LIB) or
+             os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class InrParams(C.Structure):
+    _fields_ = [("levels", C.c_int), ("feats", C.c_int), ("log2_table", C.c_int),
+                ("base_res", C.c_int), ("growth", C.c_double), ("in_dim", C.c_int),
+                ("hidden", C.c_int), ("n_hidden_layers", C.c_int),
+                ("vmin", C.c_double), ("vmax", C.c_double)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3),
+                ("fov_y_deg", C.c_float), ("width", C.c_int), ("height", C.c_int),
+                ("step_voxels", C.c_float)]
+
+
+class MarchOpts(C.Structure):
+    _fields_ = [("K", C.c_int), ("eps_T", C.c_float), ("lod_mode", C.c_int),
+                ("lod_scale", C.c_float), ("seed", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in (
+        "samples", "inr_queries_direct", "inr_queries_decode", "true_misses",
+        "fallback_hits", "hits", "bricks_requested", "bricks_decoded", "evictions")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class CacheOpts(C.Structure):
+    _fields_ = [("brick", C.c_int), ("levels", C.c_int), ("n_slots", C.c_long),
+                ("n_req", C.c_int), ("ranking", C.c_int), ("preload", C.c_int)]
+
+
+_P = C.POINTER
+_dp = _P(C.c_double)
+_fp = _P(C.c_float)
+_up = _P(C.c_uint32)
+_ip = _P(C.c_int)
+
+_SIGS = {
+    "orc_splitmix64": (C.c_uint64, [C.c_uint64]),
+    "orc_xorshift32": (C.c_uint32, [C.c_uint32]),
+    "orc_uniform_coords": (None, [C.c_uint64, C.c_uint64, C.c_long, _fp]),
+    "orc_mlp_param_count": (C.c_long, [_P(InrParams)]),
+    "orc_level_res": (None, [_P(InrParams), _ip]),
+    "orc_level_is_dense": (C.c_int, [_P(InrParams), C.c_int]),
+    "orc_vertex_index": (C.c_uint32, [_P(InrParams), C.c_int, C.c_uint32, C.c_uint32, C.c_uint32]),
+    "orc_encode_indices": (None, [_P(InrParams), _fp, C.c_long, _up]),
+    "orc_encode": (None, [_P(InrParams), _dp, _fp, C.c_long, _dp]),
+    "orc_mlp": (None, [_P(InrParams), _dp, _dp, C.c_long, _dp]),
+    "orc_inr_eval": (None, [_P(InrParams), _dp, _dp, _fp, C.c_long, _dp]),
+    "orc_inr_raw_range": (None, [_P(InrParams), _dp, _dp, _ip, C.c_int, _dp, _dp]),
+    "orc_ray": (C.c_int, [_P(Camera), _ip, C.c_int, C.c_int, _fp, _fp, _fp, _fp]),
+    "orc_sample": (C.c_int, [_P(Camera), _ip, _fp, _fp, C.c_float, C.c_float, C.c_int,
+                             _fp, _fp, _fp]),
+    "orc_sample_lod": (C.c_int, [_P(Camera), _ip, _P(MarchOpts), C.c_int, C.c_int,
+                                 C.c_uint32, C.c_float]),
+    "orc_frame_seed": (C.c_uint32, [C.c_uint64, C.c_uint64]),
+    "orc_ray_seed": (C.c_uint32, [C.c_uint32, C.c_uint32]),
+    "orc_tf_lookup": (None, [_dp, C.c_double, _dp]),
+    "orc_render_direct": (None, [_P(InrParams), _dp, _dp, _P(Camera), _ip, _P(MarchOpts),
+                                 _dp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _P(Stats)]),
+    "orc_cache_create": (C.c_void_p, [_P(InrParams), _dp, _dp, _ip, _P(CacheOpts),
+                                      _P(MarchOpts)]),
+    "orc_cache_destroy": (None, [C.c_void_p]),
+    "orc_cache_num_bricks": (C.c_long, [C.c_void_p]),
+    "orc_cache_level_offset": (C.c_long, [C.c_void_p, C.c_int]),
+    "orc_cache_level_dims": (None, [C.c_void_p, C.c_int, _ip, _ip]),
+    "orc_render_cached": (None, [C.c_void_p, _P(Camera), _dp, C.c_int, C.c_int, C.c_int,
+                                 C.c_int, _dp, _P(Stats)]),
+    "orc_cache_dump": (C.c_long, [C.c_void_p, C.c_int, _up, C.c_long]),
+    "orc_cache_slot_values": (None, [C.c_void_p, C.c_long, _dp]),
+    "orc_brick_values": (None, [_P(InrParams), _dp, _dp, _ip, C.c_int, C.c_int, C.c_int,
+                                C.c_int, C.c_int, _dp]),
+    "orc_brick_origin": (None, [_ip, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp]),
+    "orc_resident_sample": (C.c_double, [_P(InrParams), _dp, _dp, _ip, C.c_int, _fp]),
+    "orc_brick_sample": (C.c_double, [_P(InrParams), _dp, _dp, _ip, C.c_int, C.c_int, _fp]),
+    "orc_psnr": (C.c_double, [_dp, _dp, C.c_long]),
+    "orc_field_trilinear": (C.c_double, [_fp, _ip, _fp]),
+    "orc_loss_grad": (C.c_double, [_P(InrParams), _dp, _dp, _fp, _dp, C.c_long, _dp, _dp]),
+    "orc_adam": (None, [_dp, _dp, _dp, _dp, C.c_long, C.c_double, C.c_double, C.c_double,
+                        C.c_double, C.c_long]),
+    "orc_train_step": (C.c_double, [_P(InrParams), _dp, _dp, _dp, _dp, _dp, _dp, _fp, _ip,
+                                    C.c_double, C.c_double, C.c_long, C.c_uint64, C.c_long,
+                                    C.c_double, C.c_double, C.c_double, C.c_double]),
+}
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+# ----------------------------------------------------------------- helpers
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _f(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(_fp)
+
+
+def _i3(v):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.int32).reshape(3))
+    return a, a.ctypes.data_as(_ip)
+
+
+def inr_params(levels, feats, log2_table, base_res, growth, hidden,
+               n_hidden_layers=2, vmin=0.0, vmax=1.0) -> InrParams:
+    return InrParams(levels, feats, log2_table, base_res, float(growth), levels * feats,
+                     hidden, n_hidden_layers, float(vmin), float(vmax))
+
+
+def camera(eye, target, up, fov_y_deg, width, height, step_voxels) -> Camera:
+    c = Camera()
+    c.eye[:] = [float(v) for v in eye]
+    c.target[:] = [float(v) for v in target]
+    c.up[:] = [float(v) for v in up]
+    c.fov_y_deg, c.width, c.height, c.step_voxels = float(fov_y_deg), int(width), int(height), float(step_voxels)
+    return c
+
+
+def march_opts(K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0) -> MarchOpts:
+    return MarchOpts(int(K), float(eps_T), int(lod_mode), float(lod_scale), int(seed))
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().orc_splitmix64(C.c_uint64(x & (2**64 - 1))))
+
+
+def xorshift32(s: int) -> int:
+    return int(lib().orc_xorshift32(C.c_uint32(s & 0xFFFFFFFF)))
+
+
+def uniform_coords(seed: int, first: int, n: int) -> np.ndarray:
+    out = np.zeros((n, 3), np.float32)
+    lib().orc_uniform_coords(seed, first, n, out.ctypes.data_as(_fp))
+    return out
+
+
+def level_res(p: InrParams) -> np.ndarray:
+    out = np.zeros(p.levels, np.int32)
+    lib().orc_level_res(C.byref(p), out.ctypes.data_as(_ip))
+    return out
+
+
+def level_is_dense(p: InrParams, level: int) -> bool:
+    return bool(lib().orc_level_is_dense(C.byref(p), level))
+
+
+def vertex_index(p: InrParams, level: int, ix: int, iy: int, iz: int) -> int:
+    return int(lib().orc_vertex_index(C.byref(p), level, ix, iy, iz))
+
+
+def encode_indices(p: InrParams, xyz) -> np.ndarray:
+    x, xp = _f(xyz)
+    n = x.shape[0]
+    out = np.zeros((n, p.levels, 8), np.uint32)
+    lib().orc_encode_indices(C.byref(p), xp, n, out.ctypes.data_as(_up))
+    return out
+
+
+def encode(p: InrParams, table, xyz) -> np.ndarray:
+    t, tp = _d(table)
+    x, xp = _f(xyz)
+    n = x.shape[0]
+    out = np.zeros((n, p.in_dim), np.float64)
+    lib().orc_encode(C.byref(p), tp, xp, n, out.ctypes.data_as(_dp))
+    return out
+
+
+def mlp(p: InrParams, w, feats) -> np.ndarray:
+    wa, wp = _d(w)
+    fa, fp = _d(feats)
+    n = fa.shape[0]
+    out = np.zeros(n, np.float64)
+    lib().orc_mlp(C.byref(p), wp, fp, n, out.ctypes.data_as(_dp))
+    return out
+
+
+def inr_eval(p: InrParams, table, w, xyz) -> np.ndarray:
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    x, xp = _f(xyz)
+    n = x.shape[0]
+    out = np.zeros(n, np.float64)
+    lib().orc_inr_eval(C.byref(p), tp, wp, xp, n, out.ctypes.data_as(_dp))
+    return out
+
+
+def inr_raw_range(p: InrParams, table, w, vol, stride):
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    v, vp = _i3(vol)
+    lo, hi = C.c_double(), C.c_double()
+    lib().orc_inr_raw_range(C.byref(p), tp, wp, vp, int(stride), C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
+
+def ray(cam: Camera, vol, px, py):
+    v, vp = _i3(vol)
+    o = np.zeros(3, np.float32)
+    d = np.zeros(3, np.float32)
+    tn, tf = C.c_float(), C.c_float()
+    hit = lib().orc_ray(C.byref(cam), vp, px, py, o.ctypes.data_as(_fp), d.ctypes.data_as(_fp),
+                        C.byref(tn), C.byref(tf))
+    return bool(hit), o, d, tn.value, tf.value
+
+
+def sample(cam: Camera, vol, o, d, tn, tf, k):
+    v, vp = _i3(vol)
+    oa, op = _f(o)
+    da, dp = _f(d)
+    x = np.zeros(3, np.float32)
+    tm, ln = C.c_float(), C.c_float()
+    ok = lib().orc_sample(C.byref(cam), vp, op, dp, tn, tf, k, x.ctypes.data_as(_fp),
+                          C.byref(tm), C.byref(ln))
+    return bool(ok), x, tm.value, ln.value
+
+
+def sample_lod(cam: Camera, vol, mo: MarchOpts, levels, lod_min, state, t_mid):
+    v, vp = _i3(vol)
+    return int(lib().orc_sample_lod(C.byref(cam), vp, C.byref(mo), levels, lod_min,
+                                    state & 0xFFFFFFFF, t_mid))
+
+
+def frame_seed(seed: int, frame: int) -> int:
+    return int(lib().orc_frame_seed(seed, frame))
+
+
+def ray_seed(fseed: int, pixel: int) -> int:
+    return int(lib().orc_ray_seed(fseed & 0xFFFFFFFF, pixel & 0xFFFFFFFF))
+
+
+def ray_states(fseed: int, pixel: int, n: int):
+    """xorshift32 states of samples 0..n-1 of a ray."""
+    s = ray_seed(fseed, pixel)
+    out = []
+    for _ in range(n):
+        s = xorshift32(s)
+        out.append(s)
+    return out
+
+
+def tf_lookup(tf, v):
+    t, tp = _d(tf)
+    out = np.zeros(4, np.float64)
+    lib().orc_tf_lookup(tp, float(v), out.ctypes.data_as(_dp))
+    return out
+
+
+def render_direct(p: InrParams, table, w, cam: Camera, vol, mo: MarchOpts, tf,
+                  window=None):
+    """Cache-off render; returns (rgba[ph, pw, 4] float64, stats dict)."""
+    px0, py0, pw, ph = window if window is not None else (0, 0, cam.width, cam.height)
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    v, vp = _i3(vol)
+    tfa, tfp = _d(tf)
+    out = np.zeros((ph, pw, 4), np.float64)
+    st = Stats()
+    lib().orc_render_direct(C.byref(p), tp, wp, C.byref(cam), vp, C.byref(mo), tfp,
+                            px0, py0, pw, ph, out.ctypes.data_as(_dp), C.byref(st))
+    return out, st.as_dict()
+
+
+DUMP_PT, DUMP_STAMP, DUMP_OWNER, DUMP_RANK, DUMP_REQ, DUMP_VICT, DUMP_MISS, DUMP_PINNED = range(8)
+
+
+class Cache:
+    """Oracle brick cache (owns its own host memory)."""
+
+    def __init__(self, p: InrParams, table, w, vol, brick, levels, n_slots, mo: MarchOpts,
+                 n_req=40, ranking=1, preload=1):
+        self._t, tp = _d(table)
+        self._w, wp = _d(w)
+        self._v, vp = _i3(vol)
+        self.p = p
+        self.mo = mo
+        self.co = CacheOpts(int(brick), int(levels), int(n_slots), int(n_req), int(ranking),
+                            int(preload))
+        h = lib().orc_cache_create(C.byref(p), tp, wp, vp, C.byref(self.co), C.byref(mo))
+        if not h:
+            raise ValueError("orc_cache_create failed (levels or pool too small for preload)")
+        self.h = C.c_void_p(h)
+
+    def close(self):
+        if self.h:
+            lib().orc_cache_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_bricks(self):
+        return int(lib().orc_cache_num_bricks(self.h))
+
+    def level_offset(self, level):
+        return int(lib().orc_cache_level_offset(self.h, level))
+
+    def level_dims(self, level):
+        d = np.zeros(3, np.int32)
+        nb = np.zeros(3, np.int32)
+        lib().orc_cache_level_dims(self.h, level, d.ctypes.data_as(_ip), nb.ctypes.data_as(_ip))
+        return d, nb
+
+    def render(self, cam: Camera, tf, window=None):
+        px0, py0, pw, ph = window if window is not None else (0, 0, cam.width, cam.height)
+        tfa, tfp = _d(tf)
+        out = np.zeros((ph, pw, 4), np.float64)
+        st = Stats()
+        lib().orc_render_cached(self.h, C.byref(cam), tfp, px0, py0, pw, ph,
+                                out.ctypes.data_as(_dp), C.byref(st))
+        return out, st.as_dict()
+
+    def dump(self, what):
+        n = int(lib().orc_cache_dump(self.h, what, None, 0))
+        out = np.zeros(max(n, 0), np.uint32)
+        if n > 0:
+            lib().orc_cache_dump(self.h, what, out.ctypes.data_as(_up), n)
+        return out
+
+    def slot_values(self, slot):
+        S = self.co.brick + 2
+        out = np.zeros(S ** 3, np.float64)
+        lib().orc_cache_slot_values(self.h, slot, out.ctypes.data_as(_dp))
+        return out
+
+
+def brick_values(p: InrParams, table, w, vol, brick, level, b):
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    v, vp = _i3(vol)
+    S = brick + 2
+    out = np.zeros(S ** 3, np.float64)
+    lib().orc_brick_values(C.byref(p), tp, wp, vp, brick, level, int(b[0]), int(b[1]), int(b[2]),
+                           out.ctypes.data_as(_dp))
+    return out.reshape(S, S, S)
+
+
+def brick_origin(vol, brick, level, b):
+    v, vp = _i3(vol)
+    out = np.zeros(3, np.float64)
+    lib().orc_brick_origin(vp, brick, level, int(b[0]), int(b[1]), int(b[2]),
+                           out.ctypes.data_as(_dp))
+    return out
+
+
+def resident_sample(p: InrParams, table, w, vol, level, x):
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    v, vp = _i3(vol)
+    xa, xp = _f(x)
+    return float(lib().orc_resident_sample(C.byref(p), tp, wp, vp, level, xp))
+
+
+def brick_sample(p: InrParams, table, w, vol, brick, level, x):
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    v, vp = _i3(vol)
+    xa, xp = _f(x)
+    return float(lib().orc_brick_sample(C.byref(p), tp, wp, vp, brick, level, xp))
+
+
+def psnr(a, b):
+    aa, ap = _d(a)
+    ba, bp = _d(b)
+    n = aa.size // 4
+    return float(lib().orc_psnr(ap, bp, n))
+
+
+def field_trilinear(field, x):
+    fa, fp = _f(field)
+    dims, dp = _i3(fa.shape[::-1])
+    xa, xp = _f(x)
+    return float(lib().orc_field_trilinear(fp, dp, xp))
+
+
+def loss_grad(p: InrParams, table, w, xyz, target):
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    x, xp = _f(xyz)
+    tg, tgp = _d(target)
+    gt = np.zeros_like(t)
+    gw = np.zeros_like(wa)
+    loss = lib().orc_loss_grad(C.byref(p), tp, wp, xp, tgp, x.shape[0],
+                               gt.ctypes.data_as(_dp), gw.ctypes.data_as(_dp))
+    return float(loss), gt, gw
+
+
+class Trainer:
+    """FP64 Adam training state (Sec. 4.1); arrays are updated in place."""
+
+    def __init__(self, p: InrParams, table, w, field, fmin, fmax, batch, seed,
+                 lr=1e-2, b1=0.9, b2=0.99, eps=1e-15):
+        self.p = p
+        self.table = np.array(table, dtype=np.float64)
+        self.w = np.array(w, dtype=np.float64)
+        self.m_t = np.zeros_like(self.table)
+        self.v_t = np.zeros_like(self.table)
+        self.m_w = np.zeros_like(self.w)
+        self.v_w = np.zeros_like(self.w)
+        self.field = np.ascontiguousarray(field, dtype=np.float32)
+        self.dims = np.ascontiguousarray(np.array(self.field.shape[::-1], np.int32))
+        self.fmin, self.fmax = float(fmin), float(fmax)
+        self.batch, self.seed = int(batch), int(seed)
+        self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
+        self.step_no = 0
+
+    def step(self) -> float:
+        self.step_no += 1
+        return float(lib().orc_train_step(
+            C.byref(self.p), self.table.ctypes.data_as(_dp), self.w.ctypes.data_as(_dp),
+            self.m_t.ctypes.data_as(_dp), self.v_t.ctypes.data_as(_dp),
+            self.m_w.ctypes.data_as(_dp), self.v_w.ctypes.data_as(_dp),
+            self.field.ctypes.data_as(_fp), self.dims.ctypes.data_as(_ip), self.fmin, self.fmax,
+            self.batch, self.seed, self.step_no, self.lr, self.b1, self.b2, self.eps))

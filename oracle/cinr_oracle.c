@@ -1,0 +1,1148 @@
+/*
+ * CPU FP64 oracle of the cache-accelerated INR volume renderer.
+ * TEST INFRASTRUCTURE ONLY -- see cinr_oracle.h for the rules it follows.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared
+ * (oracle/__init__.py does this).  -ffp-contract=off is part of the numeric
+ * contract: every float expression below rounds after each operation.
+ *
+ * Readings of the paper where it is silent or ambiguous are marked READING.
+ */
+#include "cinr_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ===================================================================== */
+/* Random generators                                                       */
+/* ===================================================================== */
+
+/* SplitMix64 (Steele, Lea & Flood 2014): one output for state x. */
+uint64_t orc_splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/* Xorshift32 with the (13, 17, 5) triple (Marsaglia 2003): the "simple
+ * xorshift operation" of Sec. 5.3. */
+uint32_t orc_xorshift32(uint32_t s) {
+  s ^= s << 13;
+  s ^= s >> 17;
+  s ^= s << 5;
+  return s;
+}
+
+/* Counter-based uniform coordinates in [0,1)^3 for training batches
+ * (Sec. 4.1 "a batch of random coordinates").  Coordinate c of element j is
+ * the top 24 bits of splitmix64(seed + 3*(first+j) + c), times 2^-24. */
+void orc_uniform_coords(uint64_t seed, uint64_t first, long n, float* xyz) {
+  for (long j = 0; j < n; ++j)
+    for (int c = 0; c < 3; ++c) {
+      uint64_t ctr = 3ull * (first + (uint64_t)j) + (uint64_t)c;
+      uint64_t z = orc_splitmix64(seed + ctr);
+      xyz[3 * j + c] = (float)(z >> 40) * (1.0f / 16777216.0f);
+    }
+}
+
+/* ===================================================================== */
+/* INR: multiresolution hash-grid encoding + small MLP (Sec. 3, Fig. 2)    */
+/* ===================================================================== */
+
+long orc_mlp_param_count(const orc_inr_params* p) {
+  long h = p->hidden;
+  return h * p->in_dim + (long)(p->n_hidden_layers - 1) * h * h + h;
+}
+
+/* Level resolutions.  READING: N_l = floor(N_min * b^l), with b^l formed by
+ * repeated FP64 multiplication (the paper leaves the rule to Instant-NGP). */
+void orc_level_res(const orc_inr_params* p, int* res) {
+  double s = (double)p->base_res;
+  for (int l = 0; l < p->levels; ++l) {
+    res[l] = (int)floor(s);
+    s = s * p->growth;
+  }
+}
+
+static int level_res(const orc_inr_params* p, int level) {
+  double s = (double)p->base_res;
+  for (int l = 0; l < level; ++l) s = s * p->growth;
+  return (int)floor(s);
+}
+
+/* A level whose (N+1)^3 grid vertices fit in the table is stored densely. */
+int orc_level_is_dense(const orc_inr_params* p, int level) {
+  uint64_t n1 = (uint64_t)level_res(p, level) + 1u;
+  uint64_t T = 1ull << p->log2_table;
+  return n1 * n1 * n1 <= T;
+}
+
+/* Table index of grid vertex (ix,iy,iz) at a level: the dense row-major index
+ * when the level fits, else the spatial hash of Instant-NGP (XOR of the
+ * coordinates times the per-axis primes 1, 2654435761, 805459861, in u32
+ * arithmetic) modulo T. */
+uint32_t orc_vertex_index(const orc_inr_params* p, int level, uint32_t ix,
+                          uint32_t iy, uint32_t iz) {
+  uint64_t n1 = (uint64_t)level_res(p, level) + 1u;
+  uint32_t T = 1u << p->log2_table;
+  if (n1 * n1 * n1 <= (uint64_t)T)
+    return (uint32_t)((uint64_t)ix + n1 * ((uint64_t)iy + n1 * (uint64_t)iz));
+  uint32_t h = (ix * 1u) ^ (iy * 2654435761u) ^ (iz * 805459861u);
+  return h & (T - 1u);
+}
+
+/* Cell of coordinate x (already in [0,1]) on an N-cell grid: binary32
+ * x_l = x*N, i = clamp(floor(x_l), 0, N-1), w = x_l - i. */
+static void grid_cell(float x, int N, int* i, float* w) {
+  float xl = x * (float)N;
+  int ii = (int)floorf(xl);
+  if (ii < 0) ii = 0;
+  if (ii > N - 1) ii = N - 1;
+  *i = ii;
+  *w = xl - (float)ii;
+}
+
+static float clamp01(float x) {
+  if (x < 0.0f) return 0.0f;
+  if (x > 1.0f) return 1.0f;
+  return x;
+}
+
+void orc_encode_indices(const orc_inr_params* p, const float* xyz, long n,
+                        uint32_t* idx) {
+  int L = p->levels;
+  for (long j = 0; j < n; ++j) {
+    float x[3] = {clamp01(xyz[3 * j]), clamp01(xyz[3 * j + 1]),
+                  clamp01(xyz[3 * j + 2])};
+    for (int l = 0; l < L; ++l) {
+      int N = level_res(p, l);
+      int i[3];
+      float w[3];
+      for (int a = 0; a < 3; ++a) grid_cell(x[a], N, &i[a], &w[a]);
+      for (int c = 0; c < 8; ++c)
+        idx[(j * L + l) * 8 + c] = orc_vertex_index(
+            p, l, (uint32_t)(i[0] + (c & 1)), (uint32_t)(i[1] + ((c >> 1) & 1)),
+            (uint32_t)(i[2] + ((c >> 2) & 1)));
+    }
+  }
+}
+
+/* Feature vector of one point: per level, trilinear interpolation of the n
+ * features stored at the 8 surrounding vertices; levels concatenated
+ * level-major (Sec. 3, Fig. 2). */
+static void encode_one(const orc_inr_params* p, const double* table,
+                       const float* xin, double* out) {
+  int L = p->levels, F = p->feats;
+  long T = 1L << p->log2_table;
+  float x[3] = {clamp01(xin[0]), clamp01(xin[1]), clamp01(xin[2])};
+  for (int l = 0; l < L; ++l) {
+    int N = level_res(p, l);
+    int i[3];
+    float w[3];
+    for (int a = 0; a < 3; ++a) grid_cell(x[a], N, &i[a], &w[a]);
+    for (int f = 0; f < F; ++f) out[l * F + f] = 0.0;
+    for (int c = 0; c < 8; ++c) {
+      double wc = 1.0;
+      for (int a = 0; a < 3; ++a) {
+        int bit = (c >> a) & 1;
+        wc *= bit ? (double)w[a] : 1.0 - (double)w[a];
+      }
+      uint32_t id = orc_vertex_index(p, l, (uint32_t)(i[0] + (c & 1)),
+                                     (uint32_t)(i[1] + ((c >> 1) & 1)),
+                                     (uint32_t)(i[2] + ((c >> 2) & 1)));
+      const double* e = table + ((long)l * T + (long)id) * F;
+      for (int f = 0; f < F; ++f) out[l * F + f] += wc * e[f];
+    }
+  }
+}
+
+void orc_encode(const orc_inr_params* p, const double* table, const float* xyz,
+                long n, double* feats) {
+  for (long j = 0; j < n; ++j)
+    encode_one(p, table, xyz + 3 * j, feats + j * (long)p->in_dim);
+}
+
+/* MLP: in -> hidden (ReLU) [-> hidden (ReLU)]* -> 1, linear output.
+ * READING: no biases (the fully fused MLP convention of the INR line of work
+ * the paper builds on).  Weights: layer-major, each row-major [out][in]. */
+static double mlp_one(const orc_inr_params* p, const double* w,
+                      const double* in, double* act /* scratch 2*hidden */) {
+  int H = p->hidden, I = p->in_dim;
+  double* a = act;
+  double* b = act + H;
+  for (int o = 0; o < H; ++o) {
+    double s = 0.0;
+    for (int i = 0; i < I; ++i) s += w[(long)o * I + i] * in[i];
+    a[o] = s > 0.0 ? s : 0.0;
+  }
+  const double* wl = w + (long)H * I;
+  for (int layer = 1; layer < p->n_hidden_layers; ++layer) {
+    for (int o = 0; o < H; ++o) {
+      double s = 0.0;
+      for (int i = 0; i < H; ++i) s += wl[(long)o * H + i] * a[i];
+      b[o] = s > 0.0 ? s : 0.0;
+    }
+    double* t = a;
+    a = b;
+    b = t;
+    wl += (long)H * H;
+  }
+  double y = 0.0;
+  for (int i = 0; i < H; ++i) y += wl[i] * a[i];
+  return y;
+}
+
+void orc_mlp(const orc_inr_params* p, const double* w, const double* feats,
+             long n, double* y) {
+  double* act = (double*)malloc(sizeof(double) * 2 * p->hidden);
+  for (long j = 0; j < n; ++j) y[j] = mlp_one(p, w, feats + j * p->in_dim, act);
+  free(act);
+}
+
+static double inr_one(const orc_inr_params* p, const double* table,
+                      const double* w, const float* x, double* feat,
+                      double* act) {
+  encode_one(p, table, x, feat);
+  double y = mlp_one(p, w, feat, act);
+  return p->vmin + (p->vmax - p->vmin) * y; /* Sec. 4.1 de-normalisation */
+}
+
+void orc_inr_eval(const orc_inr_params* p, const double* table,
+                  const double* w, const float* xyz, long n, double* v) {
+  double* feat = (double*)malloc(sizeof(double) * p->in_dim);
+  double* act = (double*)malloc(sizeof(double) * 2 * p->hidden);
+  for (long j = 0; j < n; ++j) v[j] = inr_one(p, table, w, xyz + 3 * j, feat, act);
+  free(feat);
+  free(act);
+}
+
+/* Raw network output range over LoD-0 voxel centres (every stride-th voxel
+ * per axis).  Used to normalise a seed-initialised (untrained) network so
+ * that its field spans [0,1] (Sec. 4.1 keeps the exact value range). */
+void orc_inr_raw_range(const orc_inr_params* p, const double* table,
+                       const double* w, const int vol[3], int stride,
+                       double* ymin, double* ymax) {
+  double* feat = (double*)malloc(sizeof(double) * p->in_dim);
+  double* act = (double*)malloc(sizeof(double) * 2 * p->hidden);
+  double lo = INFINITY, hi = -INFINITY;
+  for (int z = 0; z < vol[2]; z += stride)
+    for (int y = 0; y < vol[1]; y += stride)
+      for (int x = 0; x < vol[0]; x += stride) {
+        float xn[3] = {((float)x + 0.5f) / (float)vol[0],
+                       ((float)y + 0.5f) / (float)vol[1],
+                       ((float)z + 0.5f) / (float)vol[2]};
+        encode_one(p, table, xn, feat);
+        double v = mlp_one(p, w, feat, act);
+        if (v < lo) lo = v;
+        if (v > hi) hi = v;
+      }
+  *ymin = lo;
+  *ymax = hi;
+  free(feat);
+  free(act);
+}
+
+/* ===================================================================== */
+/* Rays, sample schedule and LoD (Sec. 5.1, Sec. 5.3, Alg. 2)              */
+/* ===================================================================== */
+
+static int max3i(const int v[3]) {
+  int m = v[0];
+  if (v[1] > m) m = v[1];
+  if (v[2] > m) m = v[2];
+  return m;
+}
+
+static void normalize3(const float a[3], float out[3]) {
+  float l2 = a[0] * a[0] + a[1] * a[1];
+  l2 = l2 + a[2] * a[2];
+  float l = sqrtf(l2);
+  out[0] = a[0] / l;
+  out[1] = a[1] / l;
+  out[2] = a[2] / l;
+}
+
+static void cross3(const float a[3], const float b[3], float out[3]) {
+  out[0] = a[1] * b[2] - a[2] * b[1];
+  out[1] = a[2] * b[0] - a[0] * b[2];
+  out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static float tan_half_fov(const orc_camera* cam) {
+  return (float)tan((double)cam->fov_y_deg * (3.14159265358979323846 / 360.0));
+}
+
+/* Box extents: the volume occupies [-e/2, e/2] with e = V / max(V). */
+static void box_extent(const int vol[3], float e[3], float h[3]) {
+  float m = (float)max3i(vol);
+  for (int a = 0; a < 3; ++a) {
+    e[a] = (float)vol[a] / m;
+    h[a] = e[a] * 0.5f;
+  }
+}
+
+/* One primary ray per pixel centre through a pinhole camera, clipped to the
+ * volume box by the slab test (ray-generation kernel, Sec. 5.1).
+ * READING: the paper gives no camera model; this one is perspective with
+ * vertical field of view fov_y.  Returns 1 when the ray hits the box. */
+int orc_ray(const orc_camera* cam, const int vol[3], int px, int py, float o[3],
+            float d[3], float* tn, float* tf) {
+  float fwd[3], right[3], upv[3], tmp[3];
+  for (int a = 0; a < 3; ++a) tmp[a] = cam->target[a] - cam->eye[a];
+  normalize3(tmp, fwd);
+  cross3(fwd, cam->up, tmp);
+  normalize3(tmp, right);
+  cross3(right, fwd, upv);
+  float th = tan_half_fov(cam);
+  float aspect = (float)cam->width / (float)cam->height;
+  float ax = th * aspect, ay = th;
+  float sx = ((float)px + 0.5f) / (float)cam->width;
+  float sy = ((float)py + 0.5f) / (float)cam->height;
+  float u = (sx * 2.0f - 1.0f) * ax;
+  float v = (1.0f - sy * 2.0f) * ay;
+  float dr[3];
+  for (int a = 0; a < 3; ++a) {
+    float t = fwd[a] + u * right[a];
+    dr[a] = t + v * upv[a];
+  }
+  normalize3(dr, d);
+  for (int a = 0; a < 3; ++a) o[a] = cam->eye[a];
+  float e[3], h[3];
+  box_extent(vol, e, h);
+  float tmin[3], tmax[3];
+  for (int a = 0; a < 3; ++a) {
+    float inv = 1.0f / d[a];
+    float lo = -h[a];
+    float t0 = (lo - o[a]) * inv;
+    float t1 = (h[a] - o[a]) * inv;
+    tmin[a] = fminf(t0, t1);
+    tmax[a] = fmaxf(t0, t1);
+  }
+  float n = fmaxf(fmaxf(tmin[0], tmin[1]), fmaxf(tmin[2], 0.0f));
+  float f = fminf(fminf(tmax[0], tmax[1]), tmax[2]);
+  *tn = n;
+  *tf = f;
+  return n < f;
+}
+
+/* Sample k of a ray.  READING: the paper gives no step rule.  Segment k is
+ * [tn + k*dt, min(tn + (k+1)*dt, tf)], dt = step / max(V) world units; the
+ * sample sits at its midpoint and carries its length, so the lengths sum to
+ * tf - tn.  Returns 0 when the ray has no sample k.  x is the normalised
+ * coordinate in [0,1]^3. */
+int orc_sample(const orc_camera* cam, const int vol[3], const float o[3],
+               const float d[3], float tn, float tf, int k, float x[3],
+               float* t_mid, float* seg_len) {
+  float dt = cam->step_voxels / (float)max3i(vol);
+  float a = tn + (float)k * dt;
+  if (!(a < tf)) return 0;
+  float b = fminf(tn + (float)(k + 1) * dt, tf);
+  float tm = (a + b) * 0.5f;
+  *t_mid = tm;
+  *seg_len = b - a;
+  float e[3], h[3];
+  box_extent(vol, e, h);
+  for (int c = 0; c < 3; ++c) {
+    float pc = o[c] + tm * d[c];
+    x[c] = clamp01((pc + h[c]) / e[c]);
+  }
+  return 1;
+}
+
+/* Higher-quality per-frame seed of the xorshift dither (Sec. 5.3). */
+uint32_t orc_frame_seed(uint64_t seed, uint64_t frame) {
+  return (uint32_t)orc_splitmix64(seed ^ frame);
+}
+
+/* Start state of a ray's xorshift stream: the MurmurHash3 32-bit finaliser
+ * (Appleby) of frame seed ^ pixel*0x9E3779B9; zero is replaced by a fixed
+ * non-zero constant (xorshift has no zero state). */
+uint32_t orc_ray_seed(uint32_t frame_seed, uint32_t pixel) {
+  uint32_t h = frame_seed ^ (pixel * 0x9E3779B9u);
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h ? h : 0x6D2B79F5u;
+}
+
+/* Stochastic LoD (Alg. 2, Sec. 5.3) of one sample, given the ray's xorshift
+ * state already advanced once for this sample (one xorshift32 step per
+ * sample along the ray).
+ * Distance mode (Alg. 2): D = dist * lod_scale, dist = the ray parameter.
+ * Footprint mode: D = log2*(dist * pixel_angle * max(V) * lod_scale), i.e.
+ * the log2 of the pixel footprint in LoD-0 voxels, with log2* the exact
+ * piecewise-linear log2 read off the binary32 exponent and mantissa.
+ * LoD = floor(D), plus 1 when u < frac(D) for u = (state >> 8) * 2^-24.
+ * READING: Alg. 2 prints "xorshift > fraction", which would jump two levels
+ * at integer D and contradict the smoothing purpose of Sec. 5.3; the
+ * increment is taken with probability frac(D) (stochastic rounding).
+ * READING: per sample (Alg. 2), on a per-ray stream (Sec. 5.3). */
+int orc_sample_lod(const orc_camera* cam, const int vol[3],
+                   const orc_march_opts* mo, int levels, int lod_min,
+                   uint32_t state, float t_mid) {
+  uint32_t u24 = state >> 8;
+  int base, inc;
+  if (mo->lod_mode == 0) {
+    float th = tan_half_fov(cam);
+    float c1 = (2.0f * th) / (float)cam->height;
+    float c2 = c1 * (float)max3i(vol);
+    float c = c2 * mo->lod_scale;
+    float xf = t_mid * c;
+    if (!(xf >= 1.0f)) {
+      base = 0;
+      inc = 0;
+    } else {
+      uint32_t bits;
+      memcpy(&bits, &xf, 4);
+      base = (int)((bits >> 23) & 0xFFu) - 127;
+      uint32_t mant = bits & 0x7FFFFFu; /* fraction = mant * 2^-23 */
+      inc = u24 < 2u * mant;
+    }
+  } else {
+    float D = t_mid * mo->lod_scale;
+    float fl = floorf(D);
+    float fr = D - fl;
+    base = fl > 1e6f ? 1000000 : (int)fl;
+    inc = ((float)u24 * (1.0f / 16777216.0f)) < fr;
+  }
+  int lod = base + inc;
+  if (lod < lod_min) lod = lod_min;
+  if (lod > levels - 1) lod = levels - 1;
+  return lod;
+}
+
+/* ===================================================================== */
+/* Transfer function and front-to-back compositing (Sec. 3, Sec. 5.1)      */
+/* ===================================================================== */
+
+/* 256-entry piecewise-linear TF; entry = (r, g, b, sigma), sigma the
+ * extinction per world unit.  x = clamp(v,0,1)*255, linear between
+ * floor(x) and floor(x)+1. */
+void orc_tf_lookup(const double* tf, double v, double out[4]) {
+  if (v < 0.0) v = 0.0;
+  if (v > 1.0) v = 1.0;
+  double x = v * 255.0;
+  int i = (int)floor(x);
+  if (i > 255) i = 255;
+  int i1 = i + 1 > 255 ? 255 : i + 1;
+  double fr = x - (double)i;
+  for (int c = 0; c < 4; ++c)
+    out[c] = tf[i * 4 + c] * (1.0 - fr) + tf[i1 * 4 + c] * fr;
+}
+
+/* Emission-absorption compositing of one sample, front to back:
+ * alpha = 1 - exp(-sigma*len); C += T*alpha*rgb; T *= 1 - alpha. */
+static void composite(const double* tf, double v, double len, double C[3],
+                      double* T) {
+  double e[4];
+  orc_tf_lookup(tf, v, e);
+  double alpha = 1.0 - exp(-e[3] * len);
+  for (int c = 0; c < 3; ++c) C[c] += (*T) * alpha * e[c];
+  *T = (*T) * (1.0 - alpha);
+}
+
+/* Cache-off rendering: every sample is inferred directly by the INR
+ * (Alg. 1 with every sample a miss).  Termination is tested only after each
+ * segment of K samples (wavefront loop of Sec. 5.1).  Renders the pixel
+ * window [px0, px0+pw) x [py0, py0+ph). */
+void orc_render_direct(const orc_inr_params* p, const double* table,
+                       const double* w, const orc_camera* cam,
+                       const int vol[3], const orc_march_opts* mo,
+                       const double* tf, int px0, int py0, int pw, int ph,
+                       double* rgba, orc_stats* st) {
+  memset(st, 0, sizeof(*st));
+  double* feat = (double*)malloc(sizeof(double) * p->in_dim);
+  double* act = (double*)malloc(sizeof(double) * 2 * p->hidden);
+  for (int yy = 0; yy < ph; ++yy)
+    for (int xx = 0; xx < pw; ++xx) {
+      double* out = rgba + ((long)yy * pw + xx) * 4;
+      out[0] = out[1] = out[2] = out[3] = 0.0;
+      float o[3], d[3], tn, tf_;
+      if (!orc_ray(cam, vol, px0 + xx, py0 + yy, o, d, &tn, &tf_)) continue;
+      double C[3] = {0, 0, 0}, T = 1.0;
+      for (int k = 0;; ++k) {
+        float x[3], tm, len;
+        if (!orc_sample(cam, vol, o, d, tn, tf_, k, x, &tm, &len)) break;
+        double v = inr_one(p, table, w, x, feat, act);
+        st->samples++;
+        st->inr_queries_direct++;
+        st->true_misses++;
+        composite(tf, v, (double)len, C, &T);
+        if ((k + 1) % mo->K == 0 && T < (double)mo->eps_T) break;
+      }
+      out[0] = C[0];
+      out[1] = C[1];
+      out[2] = C[2];
+      out[3] = 1.0 - T;
+    }
+  free(feat);
+  free(act);
+}
+
+/* ===================================================================== */
+/* Multi-resolution brick cache (Sec. 4.3)                                 */
+/* ===================================================================== */
+
+#define PT_MAPPED 0x80000000u
+#define NO_OWNER 0xFFFFFFFFu
+
+struct orc_cache {
+  orc_inr_params p;
+  const double* table;
+  const double* w;
+  int vol[3];
+  orc_cache_opts co;
+  orc_march_opts mo;
+  int dims[16][3], nb[16][3];
+  long off[17];
+  long n_bricks;
+  int S; /* stored edge B + 2 */
+  uint32_t* pt;
+  uint32_t* rank;
+  uint32_t* stamp;
+  uint32_t* owner;
+  uint32_t* pinned;
+  double* pool;
+  uint64_t frame;
+  uint32_t* last_req;
+  long n_last_req;
+  uint32_t* last_vict;
+  long n_last_vict;
+  uint32_t* miss;
+  long n_miss, cap_miss;
+};
+
+long orc_cache_num_bricks(const orc_cache* c) { return c->n_bricks; }
+long orc_cache_level_offset(const orc_cache* c, int level) {
+  return c->off[level];
+}
+void orc_cache_level_dims(const orc_cache* c, int level, int dims[3],
+                          int nb[3]) {
+  for (int a = 0; a < 3; ++a) {
+    dims[a] = c->dims[level][a];
+    nb[a] = c->nb[level][a];
+  }
+}
+
+/* LoD-l voxel grid: dims_l = ceil(V / 2^l); bricks of B voxels per edge. */
+static void level_geometry(const int vol[3], int B, int l, int dims[3],
+                           int nb[3]) {
+  for (int a = 0; a < 3; ++a) {
+    dims[a] = (vol[a] + (1 << l) - 1) >> l;
+    nb[a] = (dims[a] + B - 1) / B;
+  }
+}
+
+/* Normalised coordinate of the centre of LoD-l voxel j (clamped to the grid):
+ * LoD-0 voxel-edge coordinate (j + 0.5) * 2^l, divided by V (Sec. 4.3.2:
+ * coordinates strided by 2^LoD, no interpolation needed). */
+static float voxel_centre(int j, int l, int dim_l, int V) {
+  if (j < 0) j = 0;
+  if (j > dim_l - 1) j = dim_l - 1;
+  float t = ((float)j + 0.5f) * (float)(1 << l);
+  return clamp01(t / (float)V);
+}
+
+/* Brick (bx,by,bz) at LoD l stores voxels [b*B - 1, b*B + B] per axis, i.e.
+ * the interior plus a one-voxel apron ("covering", Sec. 4.3.2), x fastest.
+ * READING: the apron is kept on both sides so that trilinear sampling of any
+ * point whose brick is b = floor(s/B) stays inside the brick. */
+void orc_brick_values(const orc_inr_params* p, const double* table,
+                      const double* w, const int vol[3], int brick, int level,
+                      int bx, int by, int bz, double* out) {
+  int dims[3], nb[3];
+  level_geometry(vol, brick, level, dims, nb);
+  int S = brick + 2;
+  int b[3] = {bx, by, bz};
+  double* feat = (double*)malloc(sizeof(double) * p->in_dim);
+  double* act = (double*)malloc(sizeof(double) * 2 * p->hidden);
+  for (int lz = 0; lz < S; ++lz)
+    for (int ly = 0; ly < S; ++ly)
+      for (int lx = 0; lx < S; ++lx) {
+        int l3[3] = {lx, ly, lz};
+        float x[3];
+        for (int a = 0; a < 3; ++a)
+          x[a] = voxel_centre(b[a] * brick - 1 + l3[a], level, dims[a], vol[a]);
+        out[((long)lz * S + ly) * S + lx] = inr_one(p, table, w, x, feat, act);
+      }
+  free(feat);
+  free(act);
+}
+
+/* Origin of a brick: the centre of its first stored voxel in LoD-0
+ * voxel-edge coordinates (voxel i spans [i, i+1)), i.e. b*B*2^l - 2^(l-1)
+ * per axis, clamped at the grid start.  The y and z components reproduce the
+ * worked example of Sec. 4.3.2 (origin 79 and 159 for brick 1 and 2 at LoD 1,
+ * B = 40); along x the apron voxel -1 is clamped to voxel 0, centre 2^(l-1). */
+void orc_brick_origin(const int vol[3], int brick, int level, int bx, int by,
+                      int bz, double origin[3]) {
+  int dims[3], nb[3];
+  level_geometry(vol, brick, level, dims, nb);
+  int b[3] = {bx, by, bz};
+  for (int a = 0; a < 3; ++a) {
+    int j = b[a] * brick - 1;
+    if (j < 0) j = 0;
+    if (j > dims[a] - 1) j = dims[a] - 1;
+    origin[a] = ((double)j + 0.5) * (double)(1 << level);
+  }
+}
+
+/* Position of a sample at LoD l in LoD-l edge units, s = x*V / 2^l. */
+static void level_coord(const float x[3], const int vol[3], int l, float s[3]) {
+  float sc = 1.0f / (float)(1 << l);
+  for (int a = 0; a < 3; ++a) {
+    float pv = x[a] * (float)vol[a];
+    s[a] = pv * sc;
+  }
+}
+
+static void brick_of(const float s[3], int B, const int nb[3], int b[3]) {
+  for (int a = 0; a < 3; ++a) {
+    int bi = (int)floorf(s[a] / (float)B);
+    if (bi < 0) bi = 0;
+    if (bi > nb[a] - 1) bi = nb[a] - 1;
+    b[a] = bi;
+  }
+}
+
+/* Trilinear reconstruction inside a stored brick (Sec. 4.3: samples read from
+ * brick memory).  q = clamp(s - 0.5, 0, dims-1) in binary32. */
+static double brick_trilinear(const double* data, int S, int B,
+                              const int b[3], const int dims[3],
+                              const float s[3]) {
+  int li[3];
+  float f[3];
+  for (int a = 0; a < 3; ++a) {
+    float q = fminf(fmaxf(s[a] - 0.5f, 0.0f), (float)(dims[a] - 1));
+    int i0 = (int)floorf(q);
+    f[a] = q - (float)i0;
+    li[a] = i0 - (b[a] * B - 1);
+  }
+  double v = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    double wc = 1.0;
+    int o[3];
+    for (int a = 0; a < 3; ++a) {
+      int bit = (c >> a) & 1;
+      wc *= bit ? (double)f[a] : 1.0 - (double)f[a];
+      o[a] = li[a] + bit;
+    }
+    v += wc * data[((long)o[2] * S + o[1]) * S + o[0]];
+  }
+  return v;
+}
+
+double orc_resident_sample(const orc_inr_params* p, const double* table,
+                           const double* w, const int vol[3], int level,
+                           const float x[3]) {
+  /* Brute force: trilinear over the whole LoD-l voxel grid of INR values at
+   * the voxel centres, clamp-to-edge; no bricks involved. */
+  int dims[3];
+  for (int a = 0; a < 3; ++a) dims[a] = (vol[a] + (1 << level) - 1) >> level;
+  float s[3];
+  level_coord(x, vol, level, s);
+  int i0[3];
+  float f[3];
+  for (int a = 0; a < 3; ++a) {
+    float q = fminf(fmaxf(s[a] - 0.5f, 0.0f), (float)(dims[a] - 1));
+    i0[a] = (int)floorf(q);
+    f[a] = q - (float)i0[a];
+  }
+  double* feat = (double*)malloc(sizeof(double) * p->in_dim);
+  double* act = (double*)malloc(sizeof(double) * 2 * p->hidden);
+  double v = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    double wc = 1.0;
+    float xc[3];
+    for (int a = 0; a < 3; ++a) {
+      int bit = (c >> a) & 1;
+      wc *= bit ? (double)f[a] : 1.0 - (double)f[a];
+      xc[a] = voxel_centre(i0[a] + bit, level, dims[a], vol[a]);
+    }
+    v += wc * inr_one(p, table, w, xc, feat, act);
+  }
+  free(feat);
+  free(act);
+  return v;
+}
+
+/* One sample at LoD l served from the brick that contains it (brick address,
+ * apron brick contents, in-brick trilinear), without any cache state. */
+double orc_brick_sample(const orc_inr_params* p, const double* table,
+                        const double* w, const int vol[3], int brick, int level,
+                        const float x[3]) {
+  int dims[3], nb[3], b[3];
+  level_geometry(vol, brick, level, dims, nb);
+  float s[3];
+  level_coord(x, vol, level, s);
+  brick_of(s, brick, nb, b);
+  int S = brick + 2;
+  double* data = (double*)malloc(sizeof(double) * (size_t)S * S * S);
+  orc_brick_values(p, table, w, vol, brick, level, b[0], b[1], b[2], data);
+  double v = brick_trilinear(data, S, brick, b, dims, s);
+  free(data);
+  return v;
+}
+
+static void decode_into(orc_cache* c, uint32_t key, long slot) {
+  int l = 0;
+  while (l + 1 <= c->co.levels - 1 && (long)key >= c->off[l + 1]) ++l;
+  long local = (long)key - c->off[l];
+  int bx = (int)(local % c->nb[l][0]);
+  int by = (int)((local / c->nb[l][0]) % c->nb[l][1]);
+  int bz = (int)(local / ((long)c->nb[l][0] * c->nb[l][1]));
+  long S3 = (long)c->S * c->S * c->S;
+  orc_brick_values(&c->p, c->table, c->w, c->vol, c->co.brick, l, bx, by, bz,
+                   c->pool + slot * S3);
+}
+
+orc_cache* orc_cache_create(const orc_inr_params* p, const double* table,
+                            const double* w, const int vol[3],
+                            const orc_cache_opts* co,
+                            const orc_march_opts* mo) {
+  if (co->levels < 1 || co->levels > 16) return NULL;
+  orc_cache* c = (orc_cache*)calloc(1, sizeof(orc_cache));
+  c->p = *p;
+  c->table = table;
+  c->w = w;
+  for (int a = 0; a < 3; ++a) c->vol[a] = vol[a];
+  c->co = *co;
+  c->mo = *mo;
+  c->S = co->brick + 2;
+  c->off[0] = 0;
+  for (int l = 0; l < co->levels; ++l) {
+    level_geometry(vol, co->brick, l, c->dims[l], c->nb[l]);
+    c->off[l + 1] =
+        c->off[l] + (long)c->nb[l][0] * c->nb[l][1] * c->nb[l][2];
+  }
+  c->n_bricks = c->off[co->levels];
+  c->pt = (uint32_t*)calloc((size_t)c->n_bricks, 4);
+  c->rank = (uint32_t*)calloc((size_t)c->n_bricks, 4);
+  c->stamp = (uint32_t*)calloc((size_t)co->n_slots, 4);
+  c->owner = (uint32_t*)malloc((size_t)co->n_slots * 4);
+  c->pinned = (uint32_t*)calloc((size_t)co->n_slots, 4);
+  for (long s = 0; s < co->n_slots; ++s) c->owner[s] = NO_OWNER;
+  long S3 = (long)c->S * c->S * c->S;
+  c->pool = (double*)calloc((size_t)(co->n_slots * S3), sizeof(double));
+  c->last_req = (uint32_t*)malloc(sizeof(uint32_t) * (co->n_req + 1));
+  c->last_vict = (uint32_t*)malloc(sizeof(uint32_t) * (co->n_req + 1));
+  c->cap_miss = 1024;
+  c->miss = (uint32_t*)malloc(sizeof(uint32_t) * 2 * c->cap_miss);
+  /* Preload (Sec. 4.3.4).  READING: the coarsest LoD is decoded and pinned
+   * at creation, in key order into slots 0.., so that the fallback always
+   * finds a brick. */
+  if (co->preload) {
+    int L = co->levels - 1;
+    long nc = c->off[L + 1] - c->off[L];
+    if (nc > co->n_slots) {
+      orc_cache_destroy(c);
+      return NULL;
+    }
+    for (long i = 0; i < nc; ++i) {
+      uint32_t key = (uint32_t)(c->off[L] + i);
+      decode_into(c, key, i);
+      c->pt[key] = PT_MAPPED | (uint32_t)i;
+      c->owner[i] = key;
+      c->pinned[i] = 1;
+    }
+  }
+  return c;
+}
+
+void orc_cache_destroy(orc_cache* c) {
+  if (!c) return;
+  free(c->pt);
+  free(c->rank);
+  free(c->stamp);
+  free(c->owner);
+  free(c->pinned);
+  free(c->pool);
+  free(c->last_req);
+  free(c->last_vict);
+  free(c->miss);
+  free(c);
+}
+
+static void push_miss(orc_cache* c, uint32_t pixel, uint32_t k) {
+  if (c->n_miss == c->cap_miss) {
+    c->cap_miss *= 2;
+    c->miss = (uint32_t*)realloc(c->miss, sizeof(uint32_t) * 2 * c->cap_miss);
+  }
+  c->miss[2 * c->n_miss] = pixel;
+  c->miss[2 * c->n_miss + 1] = k;
+  c->n_miss++;
+}
+
+typedef struct {
+  uint64_t a;
+  uint32_t b;
+} sort_pair;
+
+static int cmp_u64_key(const void* x, const void* y) {
+  const sort_pair* p = (const sort_pair*)x;
+  const sort_pair* q = (const sort_pair*)y;
+  if (p->a < q->a) return -1;
+  if (p->a > q->a) return 1;
+  return 0;
+}
+
+/* Cached rendering of frame f (Fig. 1; Alg. 1 and 2; Sec. 4.3).
+ * Per sample: stochastic LoD l; page-table lookup at l; if the brick is
+ * Unmapped a request is raised for it (priority rank, Sec. 4.3.3) and the
+ * lookup falls back to l+1, l+2, ... (Sec. 4.3); the first Mapped brick is
+ * sampled trilinearly and its slot stamped with f (LRU); no Mapped brick at
+ * any level = true miss, recorded and inferred directly by the INR (Alg. 1).
+ * End of frame: top-n requests, victims, decode + write-back, map (lag-1:
+ * the new bricks serve frame f+1). */
+void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
+                       int px0, int py0, int pw, int ph, double* rgba,
+                       orc_stats* st) {
+  memset(st, 0, sizeof(*st));
+  c->frame += 1;
+  uint64_t f = c->frame;
+  /* READING of the ranking rule (Sec. 4.3.3): the frame timestamp advances
+   * by 1001 per frame; a request sets r = max(r, T_f) + 1, clamped at
+   * T_f + 1000, so the score of a brick this frame is min(#requests, 1000)
+   * and stale ranks never outrank fresh requests. */
+  uint32_t Tf = (uint32_t)(1001u * (uint32_t)f);
+  uint32_t fseed = orc_frame_seed(c->mo.seed, f);
+  int L = c->co.levels, B = c->co.brick, S = c->S;
+  long S3 = (long)S * S * S;
+  c->n_miss = 0;
+  double* feat = (double*)malloc(sizeof(double) * c->p.in_dim);
+  double* act = (double*)malloc(sizeof(double) * 2 * c->p.hidden);
+  for (int yy = 0; yy < ph; ++yy)
+    for (int xx = 0; xx < pw; ++xx) {
+      double* out = rgba + ((long)yy * pw + xx) * 4;
+      out[0] = out[1] = out[2] = out[3] = 0.0;
+      int px = px0 + xx, py = py0 + yy;
+      uint32_t pixel = (uint32_t)(py * cam->width + px);
+      float o[3], d[3], tn, tf_;
+      if (!orc_ray(cam, c->vol, px, py, o, d, &tn, &tf_)) continue;
+      double C[3] = {0, 0, 0}, T = 1.0;
+      uint32_t rs = orc_ray_seed(fseed, pixel);
+      for (int k = 0;; ++k) {
+        float x[3], tm, len;
+        if (!orc_sample(cam, c->vol, o, d, tn, tf_, k, x, &tm, &len)) break;
+        st->samples++;
+        rs = orc_xorshift32(rs);
+        int l = orc_sample_lod(cam, c->vol, &c->mo, L, 0, rs, tm);
+        double v = 0.0;
+        int found = 0;
+        for (int lev = l; lev < L; ++lev) {
+          float s[3];
+          int b[3];
+          level_coord(x, c->vol, lev, s);
+          brick_of(s, B, c->nb[lev], b);
+          long key = c->off[lev] +
+                     b[0] + (long)c->nb[lev][0] * (b[1] + (long)c->nb[lev][1] * b[2]);
+          uint32_t e = c->pt[key];
+          if (!(e & PT_MAPPED)) {
+            if (lev == l) {
+              uint32_t r = c->rank[key];
+              if (r < Tf) {
+                r = Tf;
+                st->bricks_requested++;
+              }
+              r = r + 1u;
+              if (r > Tf + 1000u) r = Tf + 1000u;
+              c->rank[key] = r;
+            }
+            continue;
+          }
+          long slot = (long)(e & ~PT_MAPPED);
+          v = brick_trilinear(c->pool + slot * S3, S, B, b, c->dims[lev], s);
+          c->stamp[slot] = (uint32_t)f;
+          if (lev == l)
+            st->hits++;
+          else
+            st->fallback_hits++;
+          found = 1;
+          break;
+        }
+        if (!found) {
+          st->true_misses++;
+          st->inr_queries_direct++;
+          push_miss(c, pixel, (uint32_t)k);
+          v = inr_one(&c->p, c->table, c->w, x, feat, act);
+        }
+        composite(tf, v, (double)len, C, &T);
+        if ((k + 1) % c->mo.K == 0 && T < (double)c->mo.eps_T) break;
+      }
+      out[0] = C[0];
+      out[1] = C[1];
+      out[2] = C[2];
+      out[3] = 1.0 - T;
+    }
+  free(feat);
+  free(act);
+
+  /* ---- Cache Manager: request list (Sec. 4.3.3; Sarton first-n when the
+   * ranking is off) ---- */
+  long nb = c->n_bricks;
+  sort_pair* cand = (sort_pair*)malloc(sizeof(sort_pair) * (size_t)(nb + 1));
+  long nc = 0;
+  for (long key = 0; key < nb; ++key) {
+    uint32_t r = c->rank[key];
+    if (r > Tf) {
+      uint64_t score = (uint64_t)(r - Tf);
+      uint64_t sk = c->co.ranking ? ((1000u - score) << 32) | (uint64_t)key
+                                  : (uint64_t)key;
+      cand[nc].a = sk;
+      cand[nc].b = (uint32_t)key;
+      nc++;
+    }
+  }
+  qsort(cand, (size_t)nc, sizeof(sort_pair), cmp_u64_key);
+  long nreq = nc < c->co.n_req ? nc : c->co.n_req;
+  for (long i = 0; i < nreq; ++i) c->last_req[i] = cand[i].b;
+  c->n_last_req = nreq;
+  free(cand);
+
+  /* ---- victims: LRU by (stamp, slot); never-used slots carry stamp 0;
+   * slots used this frame and pinned slots are not eligible ---- */
+  long ns = c->co.n_slots;
+  sort_pair* vc = (sort_pair*)malloc(sizeof(sort_pair) * (size_t)(ns + 1));
+  long nv = 0;
+  for (long s = 0; s < ns; ++s) {
+    if (c->pinned[s] || c->stamp[s] >= (uint32_t)f) continue;
+    vc[nv].a = ((uint64_t)c->stamp[s] << 32) | (uint64_t)s;
+    vc[nv].b = (uint32_t)s;
+    nv++;
+  }
+  qsort(vc, (size_t)nv, sizeof(sort_pair), cmp_u64_key);
+  long m = nreq < nv ? nreq : nv;
+  for (long i = 0; i < m; ++i) c->last_vict[i] = vc[i].b;
+  c->n_last_vict = m;
+  free(vc);
+
+  /* ---- Request Handler: decode each requested brick by INR inference
+   * into its victim slot, then update page table and LRU (Sec. 4.3.2,
+   * Fig. 1) ---- */
+  for (long i = 0; i < m; ++i) {
+    uint32_t slot = c->last_vict[i];
+    uint32_t key = c->last_req[i];
+    if (c->owner[slot] != NO_OWNER) {
+      c->pt[c->owner[slot]] = 0u;
+      st->evictions++;
+    }
+    decode_into(c, key, (long)slot);
+    c->pt[key] = PT_MAPPED | slot;
+    c->owner[slot] = key;
+    c->stamp[slot] = (uint32_t)f;
+  }
+  st->bricks_decoded = (uint64_t)m;
+  st->inr_queries_decode = (uint64_t)m * (uint64_t)S3;
+}
+
+long orc_cache_dump(const orc_cache* c, int what, uint32_t* out, long cap) {
+  const uint32_t* src = NULL;
+  long n = 0;
+  switch (what) {
+    case 0: src = c->pt; n = c->n_bricks; break;
+    case 1: src = c->stamp; n = c->co.n_slots; break;
+    case 2: src = c->owner; n = c->co.n_slots; break;
+    case 3: src = c->rank; n = c->n_bricks; break;
+    case 4: src = c->last_req; n = c->n_last_req; break;
+    case 5: src = c->last_vict; n = c->n_last_vict; break;
+    case 6: src = c->miss; n = 2 * c->n_miss; break;
+    case 7: src = c->pinned; n = c->co.n_slots; break;
+    default: return -1;
+  }
+  long m = n < cap ? n : cap;
+  if (out && m > 0) memcpy(out, src, sizeof(uint32_t) * (size_t)m);
+  return n;
+}
+
+void orc_cache_slot_values(const orc_cache* c, long slot, double* out) {
+  long S3 = (long)c->S * c->S * c->S;
+  memcpy(out, c->pool + slot * S3, sizeof(double) * (size_t)S3);
+}
+
+/* PSNR over RGB of premultiplied images on black, peak 1.0. */
+double orc_psnr(const double* a, const double* b, long n_pixels) {
+  double se = 0.0;
+  for (long i = 0; i < n_pixels; ++i)
+    for (int c = 0; c < 3; ++c) {
+      double d = a[i * 4 + c] - b[i * 4 + c];
+      se += d * d;
+    }
+  double mse = se / (double)(n_pixels * 3);
+  if (mse <= 0.0) return INFINITY;
+  return 10.0 * log10(1.0 / mse);
+}
+
+/* ===================================================================== */
+/* Training (Sec. 4.1)                                                     */
+/* ===================================================================== */
+
+/* Ground truth at a random coordinate: trilinear interpolation of the
+ * explicit field stored at voxel centres (i + 0.5)/V, clamp-to-edge. */
+double orc_field_trilinear(const float* field, const int dims[3],
+                           const float x[3]) {
+  int i0[3], i1[3];
+  float f[3];
+  for (int a = 0; a < 3; ++a) {
+    float q = clamp01(x[a]) * (float)dims[a] - 0.5f;
+    q = fminf(fmaxf(q, 0.0f), (float)(dims[a] - 1));
+    i0[a] = (int)floorf(q);
+    f[a] = q - (float)i0[a];
+    i1[a] = i0[a] + 1 > dims[a] - 1 ? dims[a] - 1 : i0[a] + 1;
+  }
+  double v = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    double wc = 1.0;
+    int ix[3];
+    for (int a = 0; a < 3; ++a) {
+      int bit = (c >> a) & 1;
+      wc *= bit ? (double)f[a] : 1.0 - (double)f[a];
+      ix[a] = bit ? i1[a] : i0[a];
+    }
+    v += wc * (double)field[((long)ix[2] * dims[1] + ix[1]) * dims[0] + ix[0]];
+  }
+  return v;
+}
+
+/* Mean squared error of the raw network output y against normalised targets
+ * over a batch, and its exact gradient with respect to every table entry and
+ * weight (back-propagation through the MLP, then through the trilinear
+ * hash-grid interpolation, accumulated per table entry). */
+double orc_loss_grad(const orc_inr_params* p, const double* table,
+                     const double* w, const float* xyz, const double* target,
+                     long n, double* g_table, double* g_w) {
+  int L = p->levels, F = p->feats, H = p->hidden, I = p->in_dim;
+  int NH = p->n_hidden_layers;
+  long T = 1L << p->log2_table;
+  long nw = orc_mlp_param_count(p);
+  memset(g_table, 0, sizeof(double) * (size_t)(L * T * F));
+  memset(g_w, 0, sizeof(double) * (size_t)nw);
+  double* feat = (double*)malloc(sizeof(double) * I);
+  double* acts = (double*)malloc(sizeof(double) * (size_t)(NH * H));
+  double* delta = (double*)malloc(sizeof(double) * H);
+  double* dprev = (double*)malloc(sizeof(double) * (H > I ? H : I));
+  double loss = 0.0;
+  for (long j = 0; j < n; ++j) {
+    const float* x = xyz + 3 * j;
+    encode_one(p, table, x, feat);
+    /* forward, keeping post-ReLU activations of each hidden layer */
+    for (int o = 0; o < H; ++o) {
+      double s = 0.0;
+      for (int i = 0; i < I; ++i) s += w[(long)o * I + i] * feat[i];
+      acts[o] = s > 0.0 ? s : 0.0;
+    }
+    const double* wl = w + (long)H * I;
+    for (int layer = 1; layer < NH; ++layer) {
+      for (int o = 0; o < H; ++o) {
+        double s = 0.0;
+        for (int i = 0; i < H; ++i) s += wl[(long)o * H + i] * acts[(layer - 1) * H + i];
+        acts[layer * H + o] = s > 0.0 ? s : 0.0;
+      }
+      wl += (long)H * H;
+    }
+    const double* wout = wl;
+    double y = 0.0;
+    for (int i = 0; i < H; ++i) y += wout[i] * acts[(NH - 1) * H + i];
+    double r = y - target[j];
+    loss += r * r;
+    double dy = 2.0 * r / (double)n;
+    /* backward: output layer */
+    double* gout = g_w + (wout - w);
+    for (int i = 0; i < H; ++i) {
+      gout[i] += dy * acts[(NH - 1) * H + i];
+      delta[i] = acts[(NH - 1) * H + i] > 0.0 ? dy * wout[i] : 0.0;
+    }
+    /* hidden layers NH-1 .. 1 */
+    for (int layer = NH - 1; layer >= 1; --layer) {
+      const double* wh = w + (long)H * I + (long)(layer - 1) * H * H;
+      double* gh = g_w + (wh - w);
+      for (int o = 0; o < H; ++o)
+        for (int i = 0; i < H; ++i) gh[(long)o * H + i] += delta[o] * acts[(layer - 1) * H + i];
+      for (int i = 0; i < H; ++i) {
+        double s = 0.0;
+        for (int o = 0; o < H; ++o) s += wh[(long)o * H + i] * delta[o];
+        dprev[i] = acts[(layer - 1) * H + i] > 0.0 ? s : 0.0;
+      }
+      memcpy(delta, dprev, sizeof(double) * H);
+    }
+    /* first layer */
+    for (int o = 0; o < H; ++o)
+      for (int i = 0; i < I; ++i) g_w[(long)o * I + i] += delta[o] * feat[i];
+    for (int i = 0; i < I; ++i) {
+      double s = 0.0;
+      for (int o = 0; o < H; ++o) s += w[(long)o * I + i] * delta[o];
+      dprev[i] = s; /* d loss / d feature i */
+    }
+    /* hash grid: each feature is a trilinear blend of 8 table entries */
+    float xc[3] = {clamp01(x[0]), clamp01(x[1]), clamp01(x[2])};
+    for (int l = 0; l < L; ++l) {
+      int N = level_res(p, l);
+      int i3[3];
+      float w3[3];
+      for (int a = 0; a < 3; ++a) grid_cell(xc[a], N, &i3[a], &w3[a]);
+      for (int c = 0; c < 8; ++c) {
+        double wc = 1.0;
+        for (int a = 0; a < 3; ++a) {
+          int bit = (c >> a) & 1;
+          wc *= bit ? (double)w3[a] : 1.0 - (double)w3[a];
+        }
+        uint32_t id = orc_vertex_index(p, l, (uint32_t)(i3[0] + (c & 1)),
+                                       (uint32_t)(i3[1] + ((c >> 1) & 1)),
+                                       (uint32_t)(i3[2] + ((c >> 2) & 1)));
+        double* g = g_table + ((long)l * T + (long)id) * F;
+        for (int f = 0; f < F; ++f) g[f] += wc * dprev[l * F + f];
+      }
+    }
+  }
+  free(feat);
+  free(acts);
+  free(delta);
+  free(dprev);
+  return loss / (double)n;
+}
+
+/* Adam (Kingma & Ba 2015), bias-corrected, step counted from 1. */
+void orc_adam(double* param, const double* grad, double* m, double* v, long n,
+              double lr, double b1, double b2, double eps, long step) {
+  double c1 = 1.0 - pow(b1, (double)step);
+  double c2 = 1.0 - pow(b2, (double)step);
+  for (long i = 0; i < n; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * grad[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * grad[i] * grad[i];
+    double mh = m[i] / c1;
+    double vh = v[i] / c2;
+    param[i] -= lr * mh / (sqrt(vh) + eps);
+  }
+}
+
+/* One training step (Sec. 4.1): a batch of counter-based random coordinates
+ * (elements step*batch .. step*batch+batch-1), ground truth by trilinear
+ * lookup normalised to [0,1] with the field range, MSE gradient, Adam on the
+ * table and on the weights.  `step` counts from 1. */
+double orc_train_step(const orc_inr_params* p, double* table, double* w,
+                      double* m_t, double* v_t, double* m_w, double* v_w,
+                      const float* field, const int dims[3], double fmin,
+                      double fmax, long batch, uint64_t seed, long step,
+                      double lr, double b1, double b2, double eps) {
+  long T = 1L << p->log2_table;
+  long nt = (long)p->levels * T * p->feats;
+  long nw = orc_mlp_param_count(p);
+  float* xyz = (float*)malloc(sizeof(float) * 3 * (size_t)batch);
+  double* tg = (double*)malloc(sizeof(double) * (size_t)batch);
+  double* gt = (double*)malloc(sizeof(double) * (size_t)nt);
+  double* gw = (double*)malloc(sizeof(double) * (size_t)nw);
+  orc_uniform_coords(seed, (uint64_t)(step - 1) * (uint64_t)batch, batch, xyz);
+  for (long j = 0; j < batch; ++j)
+    tg[j] = (orc_field_trilinear(field, dims, xyz + 3 * j) - fmin) / (fmax - fmin);
+  double loss = orc_loss_grad(p, table, w, xyz, tg, batch, gt, gw);
+  orc_adam(table, gt, m_t, v_t, nt, lr, b1, b2, eps, step);
+  orc_adam(w, gw, m_w, v_w, nw, lr, b1, b2, eps, step);
+  free(xyz);
+  free(tg);
+  free(gt);
+  free(gw);
+  return loss;
+}

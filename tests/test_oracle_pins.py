@@ -1,0 +1,510 @@
+"""Pins of the CPU FP64 oracle against facts that do not come from the oracle
+itself: published generator outputs, hand computations, closed forms,
+invariants, brute force on tiny inputs and the paper's worked example.
+Each test names the mistake it would catch."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_18001_gb300 import synthetic as S
+
+
+# ------------------------------------------------------------ generators
+def test_splitmix64_published_first_output():
+    # First output of SplitMix64 started from state 0 (Steele et al. 2014;
+    # the widely quoted value 0xE220A8397B1DCDAF).  Catches a wrong constant
+    # or shift in the mixer.
+    assert O.splitmix64(0) == 0xE220A8397B1DCDAF
+
+
+def test_xorshift32_hand_computed():
+    # s=1: s ^= s<<13 -> 8193; s ^= s>>17 -> 8193; s ^= s<<5 -> 8193^262176.
+    assert O.xorshift32(1) == 8193 ^ 262176 == 270369
+    # s=0x80000000: <<13 drops the bit; >>17 -> 0x80004000; <<5 -> 0x80084000 ^ ... by hand:
+    s = 0x80000000
+    s ^= (s << 13) & 0xFFFFFFFF  # 0x80000000
+    s ^= s >> 17                 # 0x80004000
+    s ^= (s << 5) & 0xFFFFFFFF   # 0x80004000 ^ 0x00080000 = 0x80084000
+    assert s == 0x80084000
+    assert O.xorshift32(0x80000000) == 0x80084000
+
+
+def test_uniform_coords_grid_and_range():
+    x = O.uniform_coords(seed=7, first=0, n=20000)
+    assert x.min() >= 0.0 and x.max() < 1.0
+    # values are multiples of 2^-24 (24-bit uniform)
+    assert np.all((x.astype(np.float64) * 2**24) % 1 == 0)
+    assert abs(x.mean() - 0.5) < 0.01
+    # counter-based: element j of batch starting at `first` is element first+j
+    y = O.uniform_coords(seed=7, first=100, n=10)
+    assert np.array_equal(y, x[100:110])
+
+
+# ------------------------------------------------------------ hash grid
+def test_level_resolutions_hand_computed():
+    # 4 * 1.5^l: 4, 6, 9, 13.5, 20.25, 30.375, 45.5625, 68.34375 -> floors
+    p = O.inr_params(8, 2, 14, 4, 1.5, 32)
+    assert O.level_res(p).tolist() == [4, 6, 9, 13, 20, 30, 45, 68]
+    # dense iff (N+1)^3 <= 2^14: 125, 343, 1000, 2744, 9261 yes; 29791 no
+    assert [O.level_is_dense(p, l) for l in range(8)] == [True] * 5 + [False] * 3
+
+
+def test_dense_level_is_row_major_bijection():
+    p = O.inr_params(1, 2, 10, 6, 2.0, 8)  # N=6: 343 vertices <= 1024
+    n1 = 7
+    seen = set()
+    for iz in range(n1):
+        for iy in range(n1):
+            for ix in range(n1):
+                idx = O.vertex_index(p, 0, ix, iy, iz)
+                seen.add(idx)
+    assert seen == set(range(n1 ** 3))
+    assert O.vertex_index(p, 0, 1, 0, 0) == 1
+    assert O.vertex_index(p, 0, 0, 1, 0) == n1
+    assert O.vertex_index(p, 0, 0, 0, 1) == n1 * n1
+
+
+def test_hash_level_brute_force_tiny_grid():
+    # N=8 (729 vertices) in T=2^6: hashed.  Brute force with the published
+    # Instant-NGP primes written out independently in Python big ints.
+    p = O.inr_params(1, 2, 6, 8, 2.0, 8)
+    assert not O.level_is_dense(p, 0)
+    primes = (1, 2654435761, 805459861)
+    counts = np.zeros(64, np.int64)
+    for iz in range(9):
+        for iy in range(9):
+            for ix in range(9):
+                h = ((ix * primes[0]) ^ (iy * primes[1]) ^ (iz * primes[2])) % (1 << 32)
+                ref = h % 64
+                got = O.vertex_index(p, 0, ix, iy, iz)
+                assert got == ref
+                counts[got] += 1
+    assert counts.sum() == 729 and (counts > 0).all()
+    # x prime is 1: along x the hash is the identity mod T
+    assert [O.vertex_index(p, 0, ix, 0, 0) for ix in range(9)] == list(range(9))
+
+
+def test_encode_at_vertices_returns_table_entries():
+    # N = 4, 8, 16 (growth 2) all dense in 2^13; x = k/4 lies on a vertex at
+    # every level, so each level's feature equals that vertex's entry.
+    p = O.inr_params(3, 2, 13, 4, 2.0, 8)
+    T = 1 << 13
+    rng = np.random.default_rng(0)
+    table = rng.normal(size=3 * T * 2)
+    pts = np.array([[0.25, 0.5, 0.75], [0.0, 1.0, 0.5], [1.0, 1.0, 1.0]], np.float32)
+    feats = O.encode(p, table, pts)
+    for j, x in enumerate(pts):
+        for l, N in enumerate([4, 8, 16]):
+            v = np.minimum((x * N).astype(np.int64), N)
+            idx = int(v[0] + (N + 1) * (v[1] + (N + 1) * v[2]))
+            assert np.allclose(feats[j, 2 * l:2 * l + 2], table[(l * T + idx) * 2:(l * T + idx) * 2 + 2],
+                               atol=1e-15)
+
+
+def test_encode_reproduces_affine_fields():
+    # Trilinear interpolation reproduces affine functions of the vertex
+    # coordinates exactly: catches swapped axes, flipped weights, a wrong
+    # corner offset or a wrong level scale.
+    p = O.inr_params(2, 2, 12, 5, 1.5, 8)  # N = 5, 7 (dense)
+    T = 1 << 12
+    table = np.zeros(2 * T * 2)
+    coef = [(0.3, 1.0, -2.0, 0.5), (-0.1, 0.25, 0.75, -1.5)]
+    for l, N in enumerate([5, 7]):
+        for iz in range(N + 1):
+            for iy in range(N + 1):
+                for ix in range(N + 1):
+                    idx = ix + (N + 1) * (iy + (N + 1) * iz)
+                    for f in range(2):
+                        a, b, c, d = coef[f]
+                        table[(l * T + idx) * 2 + f] = a + b * ix + c * iy + d * iz + l
+    pts = S.random_points(200, seed=3)
+    feats = O.encode(p, table, pts)
+    for l, N in enumerate([5, 7]):
+        g = pts.astype(np.float64) * N
+        for f in range(2):
+            a, b, c, d = coef[f]
+            ref = a + b * g[:, 0] + c * g[:, 1] + d * g[:, 2] + l
+            assert np.allclose(feats[:, 2 * l + f], ref, atol=1e-5)
+
+
+# -------------------------------------------------------------------- MLP
+def test_mlp_hand_computed_one_hidden_layer():
+    p = O.inr_params(1, 2, 4, 2, 2.0, 2, n_hidden_layers=1)
+    w = np.array([1.0, -2.0, 0.5, 0.25,  # W0 [2][2]
+                  3.0, -1.0])            # Wout [1][2]
+    # a = relu([0.2 - 0.6, 0.1 + 0.075]) = [0, 0.175]; y = 3*0 - 0.175
+    y = O.mlp(p, w, np.array([[0.2, 0.3]]))
+    assert y[0] == pytest.approx(-0.175, abs=1e-15)
+
+
+def test_mlp_relu_inactive_is_matrix_product():
+    p = O.inr_params(2, 2, 4, 2, 2.0, 3, n_hidden_layers=2)
+    rng = np.random.default_rng(1)
+    W1 = rng.uniform(0.1, 1.0, (3, 4))
+    W2 = rng.uniform(0.1, 1.0, (3, 3))
+    W3 = rng.uniform(-1.0, 1.0, (1, 3))
+    x = rng.uniform(0.1, 1.0, (5, 4))
+    w = np.concatenate([W1.ravel(), W2.ravel(), W3.ravel()])
+    ref = (W3 @ W2 @ W1 @ x.T).ravel()
+    assert np.allclose(O.mlp(p, w, x), ref, rtol=1e-13)
+    # negative pre-activations are cut: flip W1 sign -> all zero
+    w2 = np.concatenate([(-W1).ravel(), W2.ravel(), W3.ravel()])
+    assert np.allclose(O.mlp(p, w2, x), 0.0)
+
+
+def test_inr_denormalisation():
+    p = O.inr_params(1, 2, 4, 2, 2.0, 2, n_hidden_layers=1, vmin=-3.0, vmax=5.0)
+    table = np.zeros(16 * 2)
+    w = np.zeros(2 * 2 + 2)
+    v = O.inr_eval(p, table, w, np.array([[0.5, 0.5, 0.5]], np.float32))
+    assert v[0] == -3.0  # y = 0 -> vmin
+
+
+# ------------------------------------------------------- rays + compositing
+def _zero_inr():
+    cfg = S.INR_64
+    p = O.inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden,
+                     vmin=0.5, vmax=1.5)
+    return p, np.zeros(cfg.table_entries), np.zeros(cfg.mlp_params)
+
+
+def test_single_pixel_axis_ray_slab_closed_form():
+    cam = O.camera((0, 0, 2), (0, 0, 0), (0, 1, 0), 45.0, 1, 1, 0.5)
+    hit, o, d, tn, tf = O.ray(cam, (64, 64, 64), 0, 0)
+    assert hit and d.tolist() == [0.0, 0.0, -1.0]
+    assert tn == 1.5 and tf == 2.5
+
+
+@pytest.mark.parametrize("sigma", [0.5, 3.0, 40.0])
+def test_constant_density_slab_composites_to_exp(sigma):
+    # Constant field (zero MLP -> v = vmin = 0.5), constant TF: opacity of a
+    # ray through the box is 1 - exp(-sigma * (tf - tn)) and its colour is
+    # rgb times that opacity.  Catches a wrong segment length, a dropped
+    # transmittance factor or a wrong alpha.
+    p, table, w = _zero_inr()
+    cam = O.camera((0.3, 0.2, 2.0), (0, 0, 0), (0, 1, 0), 45.0, 16, 16, 0.5)
+    tf = S.tf_constant((0.2, 0.6, 1.0), sigma).astype(np.float64)
+    mo = O.march_opts(K=8, eps_T=0.0)
+    img, st = O.render_direct(p, table, w, cam, (64, 64, 64), mo, tf)
+    n_hit = 0
+    for py in range(16):
+        for px in range(16):
+            hit, o, d, tn, tf_ = O.ray(cam, (64, 64, 64), px, py)
+            if not hit:
+                assert np.all(img[py, px] == 0.0)
+                continue
+            n_hit += 1
+            a = 1.0 - math.exp(-sigma * (float(tf_) - float(tn)))
+            assert img[py, px, 3] == pytest.approx(a, rel=1e-12, abs=1e-14)
+            assert np.allclose(img[py, px, :3], np.array([0.2, 0.6, 1.0], np.float32).astype(np.float64) * a,
+                               rtol=1e-12, atol=1e-14)
+    assert n_hit > 100
+    assert st["samples"] == st["inr_queries_direct"] == st["true_misses"]
+
+
+def test_sample_count_and_termination_at_segment_boundaries():
+    p, table, w = _zero_inr()
+    cam = O.camera((0.3, 0.2, 2.0), (0, 0, 0), (0, 1, 0), 45.0, 8, 8, 0.5)
+    vol = (64, 64, 64)
+    tf = S.tf_constant((1, 1, 1), 5.0).astype(np.float64)
+    n_total = 0
+    n_first_seg = 0
+    K = 8
+    for py in range(8):
+        for px in range(8):
+            hit, o, d, tn, tf_ = O.ray(cam, vol, px, py)
+            if not hit:
+                continue
+            k = 0
+            while O.sample(cam, vol, o, d, tn, tf_, k)[0]:
+                k += 1
+            dt = np.float32(0.5) / np.float32(64)
+            assert abs(k - (tf_ - tn) / dt) <= 1.0 + 1e-3
+            n_total += k
+            n_first_seg += min(k, K)
+    _, st = O.render_direct(p, table, w, cam, vol, O.march_opts(K=K, eps_T=0.0), tf)
+    assert st["samples"] == n_total
+    # eps_T = 1: every ray stops at its first segment boundary
+    _, st1 = O.render_direct(p, table, w, cam, vol, O.march_opts(K=K, eps_T=1.0), tf)
+    assert st1["samples"] == n_first_seg
+
+
+def test_tf_lookup_endpoints_and_linearity():
+    tf = np.zeros((256, 4))
+    tf[:, 0] = np.arange(256) / 255.0
+    tf[:, 3] = 2.0 * np.arange(256)
+    assert O.tf_lookup(tf, -1.0)[0] == 0.0
+    assert O.tf_lookup(tf, 2.0)[0] == 1.0
+    v = 0.123456
+    out = O.tf_lookup(tf, v)
+    assert out[0] == pytest.approx(v, abs=1e-15)
+    assert out[3] == pytest.approx(2.0 * 255.0 * v, abs=1e-12)
+
+
+# ------------------------------------------------------------------- LoD
+def test_stochastic_lod_mean_equals_continuous_lod_distance_mode():
+    cam = O.camera((0, 0, 2), (0, 0, 0), (0, 1, 0), 45.0, 64, 64, 0.5)
+    mo = O.march_opts(lod_mode=1, lod_scale=1.0)
+    fs = O.frame_seed(0, 1)
+    for D in (0.0, 0.3, 1.7, 2.5):
+        lods = [O.sample_lod(cam, (64, 64, 64), mo, 8, 0, s, D)
+                for px in range(200) for s in O.ray_states(fs, px, 50)]
+        lods = np.array(lods)
+        assert set(np.unique(lods)) <= {math.floor(D), math.floor(D) + 1}
+        assert abs(lods.mean() - D) < 0.02
+
+
+def test_stochastic_lod_footprint_mode_piecewise_linear_log2():
+    # footprint x = t * (2 tan(fov/2) / H) * maxV * lod_scale; D = e + m for
+    # x = 2^e (1 + m).  Choose t so that x = 2.5 -> e = 1, m = 0.25.
+    cam = O.camera((0, 0, 2), (0, 0, 0), (0, 1, 0), 45.0, 64, 64, 0.5)
+    mo = O.march_opts(lod_mode=0, lod_scale=1.0)
+    th = np.float32(math.tan(math.radians(22.5)))
+    c = np.float32(np.float32(np.float32(2.0) * th) / np.float32(64)) * np.float32(64)
+    c = np.float32(c * np.float32(1.0))
+    t = np.float32(2.5) / c
+    x = np.float32(t * c)
+    e = math.floor(math.log2(float(x)))
+    m = float(x) / 2 ** e - 1.0
+    fs = O.frame_seed(5, 3)
+    lods = np.array([O.sample_lod(cam, (64, 64, 64), mo, 8, 0, s, float(t))
+                     for px in range(300) for s in O.ray_states(fs, px, 40)])
+    assert abs(lods.mean() - (e + m)) < 0.02
+    # below one voxel of footprint: LoD 0
+    assert O.sample_lod(cam, (64, 64, 64), mo, 8, 0, 0xFFFFFFFF, float(t) / 4) == 0
+    # clamped to the coarsest level
+    assert O.sample_lod(cam, (64, 64, 64), mo, 2, 0, 0, float(t) * 64) == 1
+
+
+# ------------------------------------------------------------------ cache
+def test_brick_origin_worked_example():
+    # Sec. 4.3.2: request id (0,1,2) at LoD 1 with brick side 40 starts at
+    # (0, 79, 159) in LoD-0 voxel coordinates.  y and z must match exactly.
+    # x: the apron voxel before brick 0 is clamped to voxel 0, whose LoD-1
+    # centre sits at 2^(l-1) = 1 (the paper's 0 has no apron at the volume
+    # start; documented reading).
+    o = O.brick_origin((400, 400, 400), 40, 1, (0, 1, 2))
+    assert o[1] == 79.0 and o[2] == 159.0
+    assert o[0] == 1.0
+    # A brick of 40 stored voxels at LoD 1 / 2 covers 80 / 160 LoD-0 voxels:
+    # consecutive bricks' origins are B * 2^l apart.
+    for lev, span in ((1, 80.0), (2, 160.0)):
+        a0 = O.brick_origin((4000, 4000, 4000), 40, lev, (1, 1, 1))
+        a1 = O.brick_origin((4000, 4000, 4000), 40, lev, (2, 3, 4))
+        assert np.allclose(a1 - a0, [span, 2 * span, 3 * span])
+
+
+def _small_inr(seed=0, scale=0.5):
+    cfg = S.INR_64
+    table, w = S.inr_init(cfg, seed, table_scale=scale)
+    p = O.inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden)
+    return p, table.astype(np.float64), w.astype(np.float64)
+
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+@pytest.mark.parametrize("vol", [(64, 64, 64), (40, 24, 72)])
+def test_brick_sample_equals_whole_grid_trilinear(level, vol):
+    # Fully resident cache == trilinear reconstruction of INR values at the
+    # LoD-l voxel centres with clamp-to-edge (brute force over the grid, no
+    # bricks).  Catches a wrong apron, brick index or local offset.
+    p, table, w = _small_inr()
+    pts = S.random_points(60, seed=11 + level)
+    for x in pts:
+        a = O.brick_sample(p, table, w, vol, 8, level, x)
+        b = O.resident_sample(p, table, w, vol, level, x)
+        assert a == pytest.approx(b, rel=1e-12, abs=1e-13)
+
+
+def _cache_scene(preload=1, n_slots=200, n_req=6, ranking=1, lod_scale=1.0, lod_mode=0):
+    p, table, w = _small_inr(seed=2)
+    vol = (32, 32, 32)
+    mo = O.march_opts(K=8, eps_T=0.0, lod_mode=lod_mode, lod_scale=lod_scale, seed=9)
+    c = O.Cache(p, table, w, vol, brick=8, levels=3, n_slots=n_slots, mo=mo, n_req=n_req,
+                ranking=ranking, preload=preload)
+    cam = O.camera((0.6, 0.5, 1.6), (0, 0, 0), (0, 1, 0), 45.0, 24, 24, 0.5)
+    tf = S.tf_ramps(2).astype(np.float64)
+    return c, cam, tf, p, table, w, vol
+
+
+def test_cache_geometry_and_preload():
+    c, cam, tf, *_ = _cache_scene()
+    # 32^3, B=8: LoD0 4^3=64 bricks, LoD1 16^3 -> 2^3 = 8, LoD2 8^3 -> 1
+    assert c.n_bricks == 64 + 8 + 1
+    assert [c.level_offset(l) for l in range(3)] == [0, 64, 72]
+    pt = c.dump(O.DUMP_PT)
+    assert pt[72] == 0x80000000 and np.all(pt[:72] == 0)
+    assert c.dump(O.DUMP_PINNED)[0] == 1 and c.dump(O.DUMP_PINNED)[1:].sum() == 0
+
+
+def test_cache_first_frame_all_fallback_then_ranked_requests():
+    c, cam, tf, *_ = _cache_scene(n_req=6)
+    img, st = c.render(cam, tf)
+    # Only the coarsest brick is mapped: every sample falls back or hits it.
+    assert st["true_misses"] == 0
+    assert st["hits"] + st["fallback_hits"] == st["samples"]
+    rank = c.dump(O.DUMP_RANK).astype(np.int64)
+    Tf = 1001
+    cand = np.nonzero(rank > Tf)[0]
+    assert len(cand) == st["bricks_requested"] > 6
+    score = np.minimum(rank[cand] - Tf, 1000)
+    order = sorted(zip(-score, cand))[:6]
+    assert c.dump(O.DUMP_REQ).tolist() == [int(k) for _, k in order]
+    # victims: never-used slots in ascending order (slot 0 is pinned)
+    assert c.dump(O.DUMP_VICT).tolist() == [1, 2, 3, 4, 5, 6]
+    pt = c.dump(O.DUMP_PT)
+    for s, k in zip(c.dump(O.DUMP_VICT), c.dump(O.DUMP_REQ)):
+        assert pt[k] == (0x80000000 | int(s))
+    assert st["bricks_decoded"] == 6 and st["inr_queries_decode"] == 6 * 1000
+    assert st["evictions"] == 0
+
+
+def test_cache_ranking_off_takes_first_keys():
+    c, cam, tf, *_ = _cache_scene(n_req=5, ranking=0)
+    img, st = c.render(cam, tf)
+    rank = c.dump(O.DUMP_RANK)
+    cand = np.nonzero(rank > 1001)[0]
+    assert c.dump(O.DUMP_REQ).tolist() == cand[:5].tolist()
+
+
+def test_cache_no_preload_first_frame_is_all_true_misses():
+    c, cam, tf, p, table, w, vol = _cache_scene(preload=0)
+    img, st = c.render(cam, tf)
+    assert st["true_misses"] == st["samples"] == st["inr_queries_direct"]
+    miss = c.dump(O.DUMP_MISS).reshape(-1, 2)
+    assert len(miss) == st["samples"]
+    # with no brick resident the cached render is the direct render
+    ref, st2 = O.render_direct(p, table, w, cam, vol, c.mo, tf)
+    assert np.allclose(img, ref, atol=1e-15)
+    assert st2["samples"] == st["samples"]
+
+
+def test_cache_lru_victims_brute_force_over_frames():
+    # Small pool: replacement kicks in.  Victims of each frame must be the
+    # eligible slots (not pinned, not used this frame) in ascending
+    # (stamp before the frame, slot) order.
+    c, cam0, tf, *_ = _cache_scene(n_slots=12, n_req=5)
+    pinned = c.dump(O.DUMP_PINNED).astype(bool)
+    for f in range(1, 9):
+        cam = O.camera((0.6 * math.cos(0.3 * f), 0.5, 1.6 + 0.05 * f), (0, 0, 0), (0, 1, 0),
+                       45.0, 24, 24, 0.5)
+        before = c.dump(O.DUMP_STAMP).astype(np.int64)
+        img, st = c.render(cam, tf)
+        after = c.dump(O.DUMP_STAMP).astype(np.int64)
+        vict = c.dump(O.DUMP_VICT).tolist()
+        used = set(np.nonzero(after == f)[0].tolist()) - set(vict)
+        elig = [s for s in range(12) if not pinned[s] and s not in used]
+        ref = sorted(elig, key=lambda s: (before[s], s))[:len(vict)]
+        assert vict == ref
+        assert len(vict) == min(st["bricks_requested"], 5, len(elig))
+        # page table and owners stay consistent
+        pt = c.dump(O.DUMP_PT)
+        own = c.dump(O.DUMP_OWNER)
+        for s in range(12):
+            if own[s] != 0xFFFFFFFF:
+                assert pt[own[s]] == (0x80000000 | s)
+        assert np.count_nonzero(pt & 0x80000000) == np.count_nonzero(own != 0xFFFFFFFF)
+
+
+def test_cache_fully_resident_frame_equals_resident_trilinear():
+    # Pool large enough and n_req = all bricks: after frame 1 every requested
+    # brick is resident; a second frame from the same view has no requests and
+    # its image must equal a render from the resident brute-force sampler.
+    c, cam, tf, p, table, w, vol = _cache_scene(n_slots=200, n_req=200, lod_mode=1, lod_scale=0.0)
+    c.render(cam, tf)
+    img, st = c.render(cam, tf)
+    assert st["bricks_requested"] == 0 and st["fallback_hits"] == 0 and st["true_misses"] == 0
+    assert st["hits"] == st["samples"]
+    # recomposite a few pixels from resident_sample at LoD 0
+    for (px, py) in [(12, 12), (5, 17), (20, 3)]:
+        hit, o, d, tn, tf_ = O.ray(cam, vol, px, py)
+        if not hit:
+            continue
+        Cc = np.zeros(3)
+        T = 1.0
+        k = 0
+        while True:
+            ok, x, tm, ln = O.sample(cam, vol, o, d, tn, tf_, k)
+            if not ok:
+                break
+            v = O.resident_sample(p, table, w, vol, 0, x)
+            e = O.tf_lookup(tf, v)
+            a = 1.0 - math.exp(-e[3] * ln)
+            Cc += T * a * e[:3]
+            T *= 1.0 - a
+            k += 1
+        assert np.allclose(img[py, px, :3], Cc, atol=1e-12)
+        assert img[py, px, 3] == pytest.approx(1.0 - T, abs=1e-12)
+
+
+# --------------------------------------------------------------- training
+def test_field_trilinear_voxel_centres_and_affine():
+    dims = (5, 4, 3)
+    rng = np.random.default_rng(0)
+    f = rng.normal(size=(3, 4, 5)).astype(np.float32)
+    for (i, j, k) in [(0, 0, 0), (4, 3, 2), (2, 1, 1)]:
+        x = np.array([(i + 0.5) / 5, (j + 0.5) / 4, (k + 0.5) / 3], np.float32)
+        assert O.field_trilinear(f, x) == pytest.approx(float(f[k, j, i]), abs=1e-6)
+    zz, yy, xx = np.meshgrid(np.arange(3), np.arange(4), np.arange(5), indexing="ij")
+    g = (0.5 + 0.25 * xx - 0.5 * yy + 2.0 * zz).astype(np.float32)
+    x = np.array([0.37, 0.61, 0.55], np.float32)
+    q = x.astype(np.float64) * np.array(dims) - 0.5
+    assert O.field_trilinear(g, x) == pytest.approx(0.5 + 0.25 * q[0] - 0.5 * q[1] + 2.0 * q[2],
+                                                    abs=1e-5)
+
+
+def test_loss_gradient_matches_central_differences():
+    p = O.inr_params(2, 2, 5, 3, 1.7, 4, n_hidden_layers=2)
+    T = 1 << 5
+    rng = np.random.default_rng(4)
+    table = rng.uniform(-0.5, 0.5, 2 * T * 2)
+    w = rng.normal(0, 0.8, 4 * 4 + 4 * 4 + 4)
+    xyz = rng.uniform(0, 1, (7, 3)).astype(np.float32)
+    tgt = rng.uniform(0, 1, 7)
+    loss, gt, gw = O.loss_grad(p, table, w, xyz, tgt)
+    h = 1e-6
+    for arr, g in ((table, gt), (w, gw)):
+        idx = np.nonzero(g)[0]
+        idx = np.concatenate([idx[:: max(1, len(idx) // 25)], [0]])
+        for i in idx:
+            a = arr.copy()
+            a[i] += h
+            lp = O.loss_grad(p, *(a, w) if arr is table else (table, a), xyz, tgt)[0]
+            a[i] -= 2 * h
+            lm = O.loss_grad(p, *(a, w) if arr is table else (table, a), xyz, tgt)[0]
+            fd = (lp - lm) / (2 * h)
+            assert g[i] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_adam_first_step_closed_form():
+    # from zero moments, bias-corrected m/sqrt(v) = g/|g|: step = -lr*sign(g)
+    g = np.array([0.5, -2.0, 1e-3])
+    prm = np.zeros(3)
+    m = np.zeros(3)
+    v = np.zeros(3)
+    O.lib().orc_adam(prm.ctypes.data_as(O._dp), g.ctypes.data_as(O._dp),
+                     m.ctypes.data_as(O._dp), v.ctypes.data_as(O._dp), 3, 0.01, 0.9, 0.99,
+                     1e-15, 1)
+    assert np.allclose(prm, -0.01 * np.sign(g), rtol=1e-9)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.01 * g * g)
+
+
+def test_training_reduces_loss():
+    cfg = S.InrConfig(levels=4, feats=2, log2_table=10, base_res=4, growth=1.6, hidden=16)
+    table, w = S.inr_init(cfg, 1)
+    fld = S.explicit_field((16, 16, 16), S.field_params(0, n_gaussians=8))
+    p = O.inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden)
+    tr = O.Trainer(p, table, w, fld, 0.0, 1.0, batch=512, seed=5)
+    first = tr.step()
+    for _ in range(60):
+        last = tr.step()
+    assert last < 0.3 * first
+
+
+def test_psnr_known_mse():
+    a = np.zeros((10, 10, 4))
+    b = a.copy()
+    b[..., :3] = 0.1  # mse 0.01 -> 20 dB
+    assert O.psnr(a, b) == pytest.approx(20.0, abs=1e-12)
+    assert O.psnr(a, a) == float("inf")
