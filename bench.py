@@ -1,0 +1,368 @@
+"""Benchmark: ms/frame and INR queries/s of the cached renderer against the
+uncached (direct INR) renderer on one GB300, with PSNR against the CPU FP64
+oracle and the oracle's own CPU timing beside them.
+
+Workload (the headline configuration): a 512^3 virtual volume represented by
+a hash-grid INR (L=16, F=2, T=2^19, N_min=16, b=1.38, MLP 32-64-64-1, FP32),
+rendered at 1024x1024 with a 45 deg camera orbiting at distance 2.0
+(1 deg/frame for 120 frames, then 30 frames of transfer-function edits);
+brick cache: 8^3 bricks with a one-voxel apron, 4 LoDs, 1 GiB FP32 pool,
+ranked requests (n_req per frame), coarsest LoD preloaded.  Inputs are
+seeded and synthetic (the paper's datasets and trained weights are not
+available).  A step = one frame: march + true-miss inference + compositing
++ request selection + victims + brick decode/write-back.
+
+Multi-GPU: the renderer does not shard (one frame is one GPU's work);
+--gpus N runs N independent replicas of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/frame and INR queries/s, cached vs uncached, at PSNR >= 40 dB vs oracle"
+ORBIT_FRAMES = 120
+TF_FRAMES = 30
+
+
+def frame_inputs(f, W, H):
+    from paper_2504_18001_gb300 import synthetic as S
+    if f < ORBIT_FRAMES:
+        cam = S.orbit_camera(f, W, H)
+        tf = S.tf_ramps(2)
+    else:
+        g = f - ORBIT_FRAMES + 1
+        cam = S.orbit_camera(ORBIT_FRAMES - 1, W, H)
+        tf = S.tf_ramps(2, shift=0.01 * (g % TF_FRAMES) * (1 if (g // TF_FRAMES) % 2 == 0 else -1))
+    return cam, tf
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def build_scene(args, device):
+    from paper_2504_18001_gb300 import cinr, synthetic as S
+    cfg = S.INR_512
+    table, w = S.inr_init(cfg, seed=args.seed, table_scale=1e-4)
+    inr = cinr.Inr(cinr.make_inr_params(cfg), table, w, device=device)
+    vol = (512, 512, 512)
+    lo, hi = inr.raw_range(vol, stride=8)
+    inr.set_range(-lo / (hi - lo), (1.0 - lo) / (hi - lo))
+    return cfg, table, w, inr, vol
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2504_18001_gb300 import cinr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    W = H = args.res
+    cfg, table, w, inr, vol = build_scene(args, device)
+    S3 = (args.brick + 2) ** 3
+    cache = cinr.Cache(inr, vol, pool_bytes=args.pool_mib << 20, brick=args.brick, levels=4,
+                       n_req=args.n_req, ranking=1, preload=1, device=device)
+    rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
+                         seed=args.seed, device=device)
+    img = torch.empty((H, W, 4), dtype=torch.float32, device=device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step(f, use_cache=True):
+        cam, tf = frame_inputs(f, W, H)
+        flush.random_(0, 255)  # L2 flush between timed iterations
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = rend.render(inr, cam, tf, cache=cache if use_cache else None, out=img)
+        e1.record(stream)
+        return e0, e1, st
+
+    for f in range(args.warmup):
+        step(f)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, stats = [], []
+    for i in range(args.steps):
+        e0, e1, st = step(args.warmup + i)
+        times.append((e0, e1))
+        stats.append(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in times]
+    cached_ms = float(sum(ms)) / len(ms)
+    last_f = args.warmup + args.steps - 1
+    cached_img = img.clone()
+
+    # uncached baseline on the same frames (direct INR for every sample)
+    un_ms, un_st = [], []
+    n_un = min(args.steps, args.uncached_steps)
+    for i in range(n_un):
+        e0, e1, st = step(args.warmup + args.steps - n_un + i, use_cache=False)
+        torch.cuda.synchronize()
+        un_ms.append(e0.elapsed_time(e1))
+        un_st.append(st)
+    uncached_ms = float(sum(un_ms)) / len(un_ms)
+    uncached_img = img.clone()
+
+    # end-to-end through the C ABI with host buffers (pinned), copies inside
+    host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+    e2e = []
+    for i in range(max(3, min(args.steps, 10))):
+        cam, tf = frame_inputs(last_f + 1 + i, W, H)
+        flush.random_(0, 255)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rend.render_host(inr, cam, tf, host, cache=cache)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = float(sum(e2e)) / len(e2e)
+
+    t_local = torch.tensor([cached_ms * len(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    total_ms = float(t_local.item())
+
+    peaks, peak_kind = load_peaks()
+    q_direct = sum(s["inr_queries_direct"] for s in stats)
+    q_decode = sum(s["inr_queries_decode"] for s in stats)
+    samples = sum(s["samples"] for s in stats)
+    k_ms = [s["ms_frame_kernel"] for s in stats]
+    slots = [s["slots_touched"] for s in stats]
+    # algorithmic bytes of the marching kernel: every distinct brick that
+    # served a sample read once from HBM (+ its page-table entry) and the
+    # image written once
+    elem = 4
+    alg_bytes = [sl * (S3 * elem + 4) + W * H * 16 for sl in slots]
+    achieved = sum(alg_bytes) / (sum(k_ms) * 1e-3) / 1e9
+    un_q = sum(s["inr_queries_direct"] for s in un_st)
+    res = {
+        "metric": METRIC,
+        "value": total_ms / (len(ms) * world),
+        "unit": "ms/frame",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": cached_ms,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded INR, orbit camera, seeded TF ramps)",
+        "config": {"workload": "cached_fp32_512cube_1024px_orbit", "volume": list(vol),
+                   "image": [W, H], "inr": "L16 F2 T2^19 Nmin16 b1.38 MLP32-64-64-1",
+                   "brick": args.brick, "lods": 4, "pool_mib": args.pool_mib,
+                   "n_req": args.n_req, "lod_scale": args.lod_scale, "K": 32, "eps_T": 1e-3,
+                   "l2": "flushed (256 MiB write) before every timed frame",
+                   "parallelism": f"replicas x{world}"},
+        "inr_queries_per_s": (q_direct + q_decode) / (sum(ms) * 1e-3),
+        "samples_per_s": samples / (sum(ms) * 1e-3),
+        "uncached": {"ms_per_frame": uncached_ms,
+                     "inr_queries_per_s": un_q / (sum(un_ms) * 1e-3), "frames": n_un},
+        "speedup_cached_vs_uncached": uncached_ms / cached_ms,
+        "frame_stats_last": stats[-1],
+        "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": 4096 + 64,
+                "d2h_bytes_per_step": W * H * 16 + 96},
+        "gpu_launches": None,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "frame_kernel<32,64,cached>", "peak_kind": peak_kind},
+        "clocks": clk,
+    }
+    res["gpu_launches"] = args.steps * launches_per_cached_frame()
+    if rank == 0 and not args.no_cpu:
+        res["cpu_baseline"], res["psnr_db"] = cpu_baseline(args, table, w, last_f, cached_img,
+                                                           uncached_img)
+    if world > 1:
+        dist.destroy_process_group()
+    return res if rank == 0 else None
+
+
+def launches_per_cached_frame():
+    # frame kernel + 2 radix selections (reset, 4 x (hist, pick), gather,
+    # sort) + commit + decode
+    return 1 + 2 * (1 + 2 * 4 + 2) + 2
+
+
+def cpu_baseline(args, table, w, f, cached_img, uncached_img):
+    """The oracle (single-threaded C, FP64) on a pixel window of frame f."""
+    import oracle as O
+    from paper_2504_18001_gb300 import synthetic as S
+    W = H = args.res
+    cfg = S.INR_512
+    p = O.inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden)
+    vol = (512, 512, 512)
+    lo, hi = O.inr_raw_range(p, table, w, vol, 8)  # same lattice as the GPU side
+    p.vmin, p.vmax = -lo / (hi - lo), (1.0 - lo) / (hi - lo)
+    cam, tf = frame_inputs(f, W, H)
+    oc = O.camera(**cam)
+    cw = args.cpu_crop
+    x0, y0 = W // 2 - cw // 2, H // 2 - cw // 2
+    t0 = time.perf_counter()
+    ref, st = O.render_direct(p, table, w, oc, vol, O.march_opts(K=32, eps_T=1e-3),
+                              tf.astype(np.float64), window=(x0, y0, cw, cw))
+    dt = time.perf_counter() - t0
+    hit_full = 0
+    mask = uncached_img[..., 3].cpu().numpy() > 0
+    hit_full = int(mask.sum())
+    hit_crop = int(mask[y0:y0 + cw, x0:x0 + cw].sum())
+    ms_frame = dt * 1e3 * hit_full / max(hit_crop, 1)
+    crop_c = cached_img[y0:y0 + cw, x0:x0 + cw].cpu().numpy().astype(np.float64)
+    crop_u = uncached_img[y0:y0 + cw, x0:x0 + cw].cpu().numpy().astype(np.float64)
+    psnr_cached = O.psnr(crop_c, ref)
+    psnr_uncached = O.psnr(crop_u, ref)
+    cpu = {"value": ms_frame, "unit": "ms/frame", "cores": 1, "kind": "oracle",
+           "sample": f"uncached FP64 oracle on a {cw}x{cw} pixel window of frame {f} "
+                     f"({st['samples']} samples, {dt:.1f} s), scaled by hit pixels "
+                     f"{hit_full}/{hit_crop} to a full 1024^2 frame",
+           "inr_queries_per_s": st["inr_queries_direct"] / dt}
+    return cpu, {"cached_vs_oracle": psnr_cached, "uncached_vs_oracle": psnr_uncached,
+                 "window": [x0, y0, cw, cw]}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: ms/frame on the machine's host cores."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle as O
+    from paper_2504_18001_gb300 import synthetic as S
+    cfg = S.INR_512
+    table, w = S.inr_init(cfg, seed=args.seed, table_scale=1e-4)
+    p = O.inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden)
+    vol = (512, 512, 512)
+    lo, hi = O.inr_raw_range(p, table, w, vol, 32)
+    p.vmin, p.vmax = -lo / (hi - lo), (1.0 - lo) / (hi - lo)
+    W = H = args.res
+    cw = args.ref_crop
+    per = []
+    hit_frac = []
+    for i in range(args.warmup + args.steps):
+        cam, tf = frame_inputs(i, W, H)
+        oc = O.camera(**cam)
+        x0, y0 = W // 2 - cw // 2, H // 2 - cw // 2
+        t0 = time.perf_counter()
+        img, st = O.render_direct(p, table, w, oc, vol, O.march_opts(K=32, eps_T=1e-3),
+                                  tf.astype(np.float64), window=(x0, y0, cw, cw))
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            per.append(dt * 1e3 * (W * H) / (cw * cw))
+            hit_frac.append(float((img[..., 3] > 0).mean()))
+    val = float(sum(per) / len(per))
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": "ms/frame",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": val,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "cached_fp32_512cube_1024px_orbit",
+                                            "reference": "CPU FP64 oracle, uncached"},
+            "cpu_baseline": {"value": val, "unit": "ms/frame", "cores": 1, "kind": "oracle",
+                             "sample": f"{cw}x{cw} centre window per frame, scaled by pixel "
+                                       f"count to 1024^2"},
+            "e2e": {"value": val, "unit": "ms/frame", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="cinr", choices=["cinr", "reference"])
+    ap.add_argument("--res", type=int, default=1024)
+    ap.add_argument("--brick", type=int, default=8)
+    ap.add_argument("--pool-mib", type=int, default=1024)
+    ap.add_argument("--n-req", type=int, default=40)
+    ap.add_argument("--lod-scale", type=float, default=1.0)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--uncached-steps", type=int, default=5)
+    ap.add_argument("--cpu-crop", type=int, default=24)
+    ap.add_argument("--ref-crop", type=int, default=8)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    res = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

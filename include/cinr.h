@@ -1,0 +1,281 @@
+/*
+ * cinr.h -- C ABI of the GB300 cache-accelerated INR volume renderer
+ * (arXiv 2504.18001, "From Cluster to Desktop: A Cache-Accelerated INR
+ * framework for Interactive Visualization of Tera-Scale Data").
+ *
+ * Conventions shared by every call
+ *  - Every call returns an int status: CINR_OK (0) or a negative CINR_ERR_*.
+ *    cinr_last_error() gives the message of the last failure on the calling
+ *    thread.  No C++ exception crosses this boundary.
+ *  - The caller owns all device memory.  The library never allocates device
+ *    memory: every object lives inside a caller-provided device buffer whose
+ *    size is returned by the matching *_bytes() query.  Buffers must be
+ *    256-byte aligned and stay valid until the object is destroyed.  Handle
+ *    structs themselves are small host allocations owned by the library and
+ *    released by cinr_destroy_*().
+ *  - Pointers named *_dev are device pointers; *_host are host pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work on it and return without synchronising,
+ *    except where a call says that it synchronises.
+ *  - One device: every object is bound to the device that was current when
+ *    it was created.
+ */
+#ifndef CINR_H
+#define CINR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status --- */
+#define CINR_OK 0
+#define CINR_ERR_ARG (-1)          /* invalid argument or unsupported shape */
+#define CINR_ERR_NOMEM (-2)        /* caller buffer smaller than required   */
+#define CINR_ERR_CUDA (-3)         /* a CUDA runtime call failed             */
+#define CINR_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up     */
+#define CINR_ERR_DEVICE_CHECK (-5) /* a device-side bounds check tripped     */
+#define CINR_ERR_UNSUPPORTED (-6)  /* valid request this build cannot run    */
+
+/* -------------------------------------------------------------- types --- */
+typedef struct cinr_inr_s* cinr_inr_t;
+typedef struct cinr_cache_s* cinr_cache_t;
+typedef struct cinr_renderer_s* cinr_renderer_t;
+typedef struct cinr_trainer_s* cinr_trainer_t;
+typedef void* cinr_stream_t;
+
+#define CINR_PREC_FP32 0
+#define CINR_PREC_FP16 1
+#define CINR_PREC_BF16 2
+
+/* INR hyper-parameters: a multiresolution hash-grid encoder (m levels, n
+ * features per level, a table of 2^log2_table entries per level) feeding a
+ * small ReLU MLP with a linear scalar output (Sec. 3, Fig. 2), and the value
+ * range used to de-normalise the output, v = vmin + (vmax - vmin) * y
+ * (Sec. 4.1).  Level l has N_l = floor(base_res * growth^l) cells per axis;
+ * a level whose (N_l+1)^3 vertices fit in the table is indexed densely, the
+ * others by the Instant-NGP spatial hash.
+ * Supported shapes: feats = 2; (levels*feats, hidden) in {(16,32), (32,64),
+ * (48,64)}; n_hidden_layers = 2; levels <= 32; log2_table <= 24. */
+typedef struct {
+  int levels;
+  int feats;
+  int log2_table;
+  int base_res;
+  double growth;
+  int hidden;
+  int n_hidden_layers;
+  int mlp_precision;   /* CINR_PREC_FP32 | FP16 | BF16 (FP32 accumulate) */
+  int table_precision; /* CINR_PREC_FP32 | FP16                           */
+  float vmin, vmax;
+} cinr_inr_params;
+
+/* Camera: pinhole, vertical field of view, one primary ray per pixel centre
+ * (ray-generation kernel, Sec. 5.1).  The volume occupies the box
+ * [-e/2, e/2] with e = dims / max(dims), centred at the origin.
+ * step_voxels is the ray-marching step in LoD-0 voxels. */
+typedef struct {
+  float eye[3], target[3], up[3];
+  float fov_y_deg;
+  int width, height;
+  float step_voxels;
+} cinr_camera;
+
+/* Transfer function: 256 entries of (r, g, b, sigma); x = clamp(v,0,1)*255
+ * is interpolated linearly between entries; sigma is the extinction per
+ * world unit (Sec. 3: each sample is classified by a transfer function). */
+typedef struct {
+  float rgba[256][4];
+} cinr_tf;
+
+/* Ray-marching options.  dims = the rendered volume grid in LoD-0 voxels
+ * (sets the box aspect and the voxel size; must equal the cache's dims when
+ * a cache is used).  K (a multiple of 32) is the wavefront segment:
+ * termination (T < eps_T) is tested only after every K samples of a ray.
+ * lod_mode 0 = pixel-footprint LoD, 1 = distance LoD (Alg. 2); lod_scale
+ * is the user LoD scale (Sec. 4.3.4, Sec. 5.3); seed seeds the per-frame
+ * xorshift dither (Sec. 5.3).  miss_record_cap > 0 keeps the first
+ * miss_record_cap true misses of each frame as (pixel, sample) pairs for
+ * cinr_debug_dump (CINR_DUMP_MISSES). */
+typedef struct {
+  int dims[3];
+  int K;
+  float eps_T;
+  int lod_mode;
+  float lod_scale;
+  uint64_t seed;
+  long miss_record_cap;
+} cinr_march_opts;
+
+/* Cache options (Sec. 4.3): brick = interior edge B (stored with a one-voxel
+ * apron, (B+2)^3 voxels); levels = number of LoDs; n_req = maxNumRequests
+ * per frame (Sec. 6.4); ranking = 1 for the priority ranking of
+ * Sec. 4.3.3, 0 for first-n by brick key; preload = 1 decodes and pins
+ * every brick of the coarsest LoD at creation (Sec. 4.3.4);
+ * storage_precision = CINR_PREC_FP32 | CINR_PREC_FP16 for brick voxels. */
+typedef struct {
+  int brick;
+  int levels;
+  int n_req;
+  int ranking;
+  int preload;
+  int storage_precision;
+} cinr_cache_opts;
+
+/* Per-frame counters.  samples = samples marched; inr_queries_direct = true
+ * misses inferred in the frame; inr_queries_decode = voxels decoded into
+ * bricks; hits = served at the requested LoD; fallback_hits = served by a
+ * coarser LoD (Sec. 4.3); true_misses = no LoD mapped (Alg. 2);
+ * bricks_requested = distinct bricks requested; bricks_decoded = bricks
+ * written back; evictions = decoded bricks that replaced a resident one;
+ * misses_recorded = entries of the miss record (capped); slots_touched =
+ * distinct pool slots that served samples.  ms_frame_kernel and
+ * ms_cache_update are device times (CUDA events on the frame's stream) of
+ * the marching kernel and of the end-of-frame cache update. */
+typedef struct {
+  uint64_t samples, inr_queries_direct, inr_queries_decode, true_misses,
+      fallback_hits, hits, bricks_requested, bricks_decoded, evictions,
+      misses_recorded, slots_touched;
+  float ms_frame_kernel, ms_cache_update;
+} cinr_frame_stats;
+
+/* ----------------------------------------------------------- library --- */
+
+/* Message of the last failed call on this thread (NUL-terminated, truncated
+ * to n bytes).  Returns CINR_OK. */
+int cinr_last_error(char* buf, size_t n);
+
+/* Library ABI version (major * 100 + minor). */
+int cinr_version(void);
+
+/* ---------------------------------------------------------------- INR --- */
+
+/* Device bytes an INR with these parameters occupies.  Host-only.
+ * Errors: CINR_ERR_ARG for unsupported shapes. */
+int cinr_inr_bytes(const cinr_inr_params* p, size_t* bytes);
+
+/* Creates an INR (Sec. 3, Fig. 2) inside dev_mem (>= cinr_inr_bytes).
+ * host_table: levels * 2^log2_table * feats floats, level-major then entry
+ * then feature.  host_mlp: the MLP weights, layer by layer, each row-major
+ * [out][in] (in -> hidden, hidden -> hidden, hidden -> 1; no biases).
+ * Both are copied (and converted to the requested precisions) on `stream`;
+ * the call synchronises the stream before returning so that the host arrays
+ * may be freed.  Errors: CINR_ERR_ARG, CINR_ERR_NOMEM, CINR_ERR_CUDA. */
+int cinr_create_inr(const cinr_inr_params* p, void* dev_mem, size_t bytes,
+                    const float* host_table, const float* host_mlp,
+                    cinr_stream_t stream, cinr_inr_t* out);
+
+/* Sets the de-normalisation range v = vmin + (vmax - vmin) * y (Sec. 4.1). */
+int cinr_inr_set_range(cinr_inr_t inr, float vmin, float vmax);
+
+/* Minimum and maximum of the raw network output y over the LoD-0 voxel
+ * centres ((i+0.5)/dims) of a dims grid, every `stride`-th voxel per axis.
+ * Used to normalise an untrained network to [0,1] (Sec. 4.1 keeps the exact
+ * value range of the data).  Synchronises `stream`. */
+int cinr_inr_raw_range(cinr_inr_t inr, const int dims[3], int stride,
+                       float* ymin, float* ymax, cinr_stream_t stream);
+
+/* Direct INR inference ("InferINR", Alg. 1): v[i] = INR(xyz[i]) for n points
+ * xyz_dev (n x 3 floats, normalised [0,1]^3, clamped) into out_dev (n
+ * floats).  n = 0 is a no-op. */
+int cinr_infer(cinr_inr_t inr, const float* xyz_dev, long n, float* out_dev,
+               cinr_stream_t stream);
+
+/* Hash-grid encoding only (Sec. 3): feats_dev (n x levels*feats floats) and,
+ * when idx_dev is not NULL, the 8 table indices per level and point
+ * (n x levels x 8 u32, corner c = x + 2y + 4z offset bits). */
+int cinr_encode(cinr_inr_t inr, const float* xyz_dev, long n, float* feats_dev,
+                uint32_t* idx_dev, cinr_stream_t stream);
+
+int cinr_destroy_inr(cinr_inr_t inr);
+
+/* -------------------------------------------------------------- cache --- */
+
+/* Device bytes of a brick cache over a dims volume whose brick pool holds
+ * pool_bytes of voxel data.  Host-only.  n_slots (may be NULL) receives the
+ * number of bricks the pool holds. */
+int cinr_cache_bytes(const int dims[3], size_t pool_bytes,
+                     const cinr_cache_opts* o, size_t* bytes, long* n_slots);
+
+/* Creates the multi-resolution brick cache of Sec. 4.3 in dev_mem: flat
+ * per-LoD page tables (Mapped | slot, or Unmapped; Sec. 4.3.1), the brick
+ * pool, per-brick ranks (Sec. 4.3.3), per-slot LRU stamps and owners.  With
+ * preload, every coarsest-LoD brick is decoded by INR inference into slots
+ * 0.. and pinned (Sec. 4.3.4).  Errors: CINR_ERR_NOMEM when the pool cannot
+ * hold the coarsest LoD with preload, CINR_ERR_ARG for bad shapes. */
+int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_mem,
+                      size_t bytes, size_t pool_bytes, const cinr_cache_opts* o,
+                      cinr_stream_t stream, cinr_cache_t* out);
+
+int cinr_destroy_cache(cinr_cache_t cache);
+
+/* ----------------------------------------------------------- renderer --- */
+
+/* Device bytes of the per-frame working set for width x height frames. */
+int cinr_renderer_bytes(int width, int height, const cinr_march_opts* o,
+                        size_t* bytes);
+
+int cinr_create_renderer(void* dev_mem, size_t bytes, int width, int height,
+                         const cinr_march_opts* o, cinr_renderer_t* out);
+
+/* Renders one frame (Fig. 1 steps 1-6, Alg. 1, Alg. 2, Sec. 5.1):
+ * one ray per pixel is clipped to the volume box; each ray is marched in
+ * segments of K samples; every sample picks a stochastic LoD, walks the page
+ * tables from that LoD to coarser ones (raising a ranked request for the
+ * missing requested brick), samples the first mapped brick trilinearly and
+ * stamps its slot; samples with no mapped brick (true misses) are compacted
+ * by warp ballot and prefix sums and inferred by the INR in one batch; the
+ * transfer function and front-to-back compositing produce out_rgba_dev
+ * (width*height*4 floats, premultiplied RGBA over black, row-major from the
+ * top-left pixel).  With cache != NULL, the frame ends with the cache update
+ * of Sec. 4.3.2-4.3.3: top-n requests, LRU victims, decode of the requested
+ * bricks by INR inference into the victim slots, page-table update; the new
+ * bricks serve from the next frame on.  cache == NULL renders the uncached
+ * baseline (every sample inferred directly).  Frames are numbered from 1 per
+ * renderer/cache pair.  The call synchronises `stream` to return `stats`
+ * (may be NULL).  Errors: CINR_ERR_ARG on a camera/renderer size mismatch. */
+int cinr_render_frame(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr,
+                      const cinr_camera* cam, const cinr_tf* tf,
+                      float* out_rgba_dev, cinr_frame_stats* stats,
+                      cinr_stream_t stream);
+
+/* As cinr_render_frame, writing the image to host memory out_rgba_host
+ * (width*height*4 floats; pinned memory gives an asynchronous copy).  The
+ * device image lives in the renderer's working set. */
+int cinr_render_frame_host(cinr_renderer_t r, cinr_cache_t cache,
+                           cinr_inr_t inr, const cinr_camera* cam,
+                           const cinr_tf* tf, float* out_rgba_host,
+                           cinr_frame_stats* stats, cinr_stream_t stream);
+
+int cinr_destroy_renderer(cinr_renderer_t r);
+
+/* ------------------------------------------------------------- debug --- */
+#define CINR_DUMP_PAGE_TABLE 0 /* u32 per brick: 0x80000000|slot or 0  */
+#define CINR_DUMP_STAMPS 1     /* u32 per slot: last frame it was used */
+#define CINR_DUMP_OWNERS 2     /* u32 per slot: brick key or 0xFFFFFFFF */
+#define CINR_DUMP_RANK 3       /* u32 per brick: ranking value          */
+#define CINR_DUMP_REQUESTS 4   /* u32 keys of the last request list     */
+#define CINR_DUMP_VICTIMS 5    /* u32 slots of the last victim list     */
+#define CINR_DUMP_MISSES 6     /* u32 pairs (pixel, sample), renderer   */
+#define CINR_DUMP_PINNED 7     /* u32 per slot: 1 if pinned             */
+#define CINR_DUMP_POOL 8       /* brick pool voxels (float or half bits) */
+
+/* Copies a piece of state to host memory (synchronises `stream`).  For
+ * CINR_DUMP_MISSES pass the renderer as `obj`, for the others the cache.
+ * *count receives the number of elements available (u32 elements; for the
+ * pool, voxels); at most cap elements are copied to host_out (which may be
+ * NULL to query the count). */
+int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap,
+                    size_t* count, cinr_stream_t stream);
+
+/* Geometry of the cache's LoD `level`: voxel dims, brick counts per axis and
+ * the key of its first brick (keys are level-major, x fastest). */
+int cinr_cache_level_info(cinr_cache_t cache, int level, int dims[3],
+                          int nbricks[3], long* key_offset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CINR_H */

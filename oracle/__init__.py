@@ -103,6 +103,7 @@ _SIGS = {
                                  C.c_uint32, C.c_float]),
     "orc_frame_seed": (C.c_uint32, [C.c_uint64, C.c_uint64]),
     "orc_ray_seed": (C.c_uint32, [C.c_uint32, C.c_uint32]),
+    "orc_sample_state": (C.c_uint32, [C.c_uint32, C.c_uint32]),
     "orc_tf_lookup": (None, [_dp, C.c_double, _dp]),
     "orc_render_direct": (None, [_P(InrParams), _dp, _dp, _P(Camera), _ip, _P(MarchOpts),
                                  _dp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _P(Stats)]),
@@ -290,13 +291,9 @@ def ray_seed(fseed: int, pixel: int) -> int:
 
 
 def ray_states(fseed: int, pixel: int, n: int):
-    """xorshift32 states of samples 0..n-1 of a ray."""
-    s = ray_seed(fseed, pixel)
-    out = []
-    for _ in range(n):
-        s = xorshift32(s)
-        out.append(s)
-    return out
+    """Dither states of samples 0..n-1 of a ray."""
+    rs = ray_seed(fseed, pixel)
+    return [int(lib().orc_sample_state(rs, k)) for k in range(n)]
 
 
 def tf_lookup(tf, v):

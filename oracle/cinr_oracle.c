@@ -356,9 +356,8 @@ uint32_t orc_frame_seed(uint64_t seed, uint64_t frame) {
   return (uint32_t)orc_splitmix64(seed ^ frame);
 }
 
-/* Start state of a ray's xorshift stream: the MurmurHash3 32-bit finaliser
- * (Appleby) of frame seed ^ pixel*0x9E3779B9; zero is replaced by a fixed
- * non-zero constant (xorshift has no zero state). */
+/* Seed of a ray: the MurmurHash3 32-bit finaliser (Appleby) of
+ * frame seed ^ pixel*0x9E3779B9. */
 uint32_t orc_ray_seed(uint32_t frame_seed, uint32_t pixel) {
   uint32_t h = frame_seed ^ (pixel * 0x9E3779B9u);
   h ^= h >> 16;
@@ -366,12 +365,21 @@ uint32_t orc_ray_seed(uint32_t frame_seed, uint32_t pixel) {
   h ^= h >> 13;
   h *= 0xC2B2AE35u;
   h ^= h >> 16;
-  return h ? h : 0x6D2B79F5u;
+  return h;
 }
 
-/* Stochastic LoD (Alg. 2, Sec. 5.3) of one sample, given the ray's xorshift
- * state already advanced once for this sample (one xorshift32 step per
- * sample along the ray).
+/* Dither state of sample k of a ray: one xorshift32 step (Sec. 5.3) applied
+ * to ray_seed ^ k*0x9E3779B9 (zero replaced by a fixed non-zero constant,
+ * xorshift has no zero state).  Counter-based, so every sample of a ray can
+ * be drawn independently. */
+uint32_t orc_sample_state(uint32_t ray_seed, uint32_t k) {
+  uint32_t s = ray_seed ^ (k * 0x9E3779B9u);
+  if (s == 0u) s = 0x6D2B79F5u;
+  return orc_xorshift32(s);
+}
+
+/* Stochastic LoD (Alg. 2, Sec. 5.3) of one sample, given its dither state
+ * (orc_sample_state).
  * Distance mode (Alg. 2): D = dist * lod_scale, dist = the ray parameter.
  * Footprint mode: D = log2*(dist * pixel_angle * max(V) * lod_scale), i.e.
  * the log2 of the pixel footprint in LoD-0 voxels, with log2* the exact
@@ -380,7 +388,7 @@ uint32_t orc_ray_seed(uint32_t frame_seed, uint32_t pixel) {
  * READING: Alg. 2 prints "xorshift > fraction", which would jump two levels
  * at integer D and contradict the smoothing purpose of Sec. 5.3; the
  * increment is taken with probability frac(D) (stochastic rounding).
- * READING: per sample (Alg. 2), on a per-ray stream (Sec. 5.3). */
+ * READING: per sample (Alg. 2), keyed by (frame, pixel, sample). */
 int orc_sample_lod(const orc_camera* cam, const int vol[3],
                    const orc_march_opts* mo, int levels, int lod_min,
                    uint32_t state, float t_mid) {
@@ -829,8 +837,8 @@ void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
         float x[3], tm, len;
         if (!orc_sample(cam, c->vol, o, d, tn, tf_, k, x, &tm, &len)) break;
         st->samples++;
-        rs = orc_xorshift32(rs);
-        int l = orc_sample_lod(cam, c->vol, &c->mo, L, 0, rs, tm);
+        int l = orc_sample_lod(cam, c->vol, &c->mo, L, 0,
+                               orc_sample_state(rs, (uint32_t)k), tm);
         double v = 0.0;
         int found = 0;
         for (int lev = l; lev < L; ++lev) {

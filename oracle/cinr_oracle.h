@@ -92,6 +92,7 @@ int orc_sample_lod(const orc_camera* cam, const int vol[3],
                    uint32_t state, float t_mid);
 uint32_t orc_frame_seed(uint64_t seed, uint64_t frame);
 uint32_t orc_ray_seed(uint32_t frame_seed, uint32_t pixel);
+uint32_t orc_sample_state(uint32_t ray_seed, uint32_t k);
 
 /* ---- transfer function and compositing (Sec. 3, Sec. 5.1) ---- */
 void orc_tf_lookup(const double* tf /* 256*4 */, double v, double out[4]);

@@ -1,0 +1,335 @@
+"""Thin ctypes binding of the C ABI in include/cinr.h (argument marshalling
+only; every step of the renderer runs in libcinr.so's CUDA kernels).
+
+PyTorch provides device memory and streams: each object's device buffer is a
+uint8 CUDA tensor sized by the library's *_bytes() query.  Importing this
+module does not need a GPU; creating objects does, and fails loudly when the
+library or the device is missing (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+CINR_OK = 0
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
+DUMP_PAGE_TABLE, DUMP_STAMPS, DUMP_OWNERS, DUMP_RANK, DUMP_REQUESTS, DUMP_VICTIMS, \
+    DUMP_MISSES, DUMP_PINNED, DUMP_POOL = range(9)
+
+
+class CinrError(RuntimeError):
+    pass
+
+
+class cinr_inr_params(C.Structure):
+    _fields_ = [("levels", C.c_int), ("feats", C.c_int), ("log2_table", C.c_int),
+                ("base_res", C.c_int), ("growth", C.c_double), ("hidden", C.c_int),
+                ("n_hidden_layers", C.c_int), ("mlp_precision", C.c_int),
+                ("table_precision", C.c_int), ("vmin", C.c_float), ("vmax", C.c_float)]
+
+
+class cinr_camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3),
+                ("fov_y_deg", C.c_float), ("width", C.c_int), ("height", C.c_int),
+                ("step_voxels", C.c_float)]
+
+
+class cinr_tf(C.Structure):
+    _fields_ = [("rgba", (C.c_float * 4) * 256)]
+
+
+class cinr_march_opts(C.Structure):
+    _fields_ = [("dims", C.c_int * 3), ("K", C.c_int), ("eps_T", C.c_float),
+                ("lod_mode", C.c_int), ("lod_scale", C.c_float), ("seed", C.c_uint64),
+                ("miss_record_cap", C.c_long)]
+
+
+class cinr_cache_opts(C.Structure):
+    _fields_ = [("brick", C.c_int), ("levels", C.c_int), ("n_req", C.c_int),
+                ("ranking", C.c_int), ("preload", C.c_int), ("storage_precision", C.c_int)]
+
+
+class cinr_frame_stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in (
+        "samples", "inr_queries_direct", "inr_queries_decode", "true_misses", "fallback_hits",
+        "hits", "bricks_requested", "bricks_decoded", "evictions", "misses_recorded",
+        "slots_touched")] + [("ms_frame_kernel", C.c_float), ("ms_cache_update", C.c_float)]
+
+    def as_dict(self):
+        return {n: (float(getattr(self, n)) if t is C.c_float else int(getattr(self, n)))
+                for n, t in self._fields_}
+
+
+_vp = C.c_void_p
+_P = C.POINTER
+_SIGS = {
+    "cinr_last_error": [C.c_char_p, C.c_size_t],
+    "cinr_version": [],
+    "cinr_inr_bytes": [_P(cinr_inr_params), _P(C.c_size_t)],
+    "cinr_create_inr": [_P(cinr_inr_params), _vp, C.c_size_t, _P(C.c_float), _P(C.c_float), _vp,
+                        _P(_vp)],
+    "cinr_inr_set_range": [_vp, C.c_float, C.c_float],
+    "cinr_inr_raw_range": [_vp, _P(C.c_int), C.c_int, _P(C.c_float), _P(C.c_float), _vp],
+    "cinr_infer": [_vp, _vp, C.c_long, _vp, _vp],
+    "cinr_encode": [_vp, _vp, C.c_long, _vp, _vp, _vp],
+    "cinr_destroy_inr": [_vp],
+    "cinr_cache_bytes": [_P(C.c_int), C.c_size_t, _P(cinr_cache_opts), _P(C.c_size_t),
+                         _P(C.c_long)],
+    "cinr_create_cache": [_vp, _P(C.c_int), _vp, C.c_size_t, C.c_size_t, _P(cinr_cache_opts), _vp,
+                          _P(_vp)],
+    "cinr_destroy_cache": [_vp],
+    "cinr_renderer_bytes": [C.c_int, C.c_int, _P(cinr_march_opts), _P(C.c_size_t)],
+    "cinr_create_renderer": [_vp, C.c_size_t, C.c_int, C.c_int, _P(cinr_march_opts), _P(_vp)],
+    "cinr_render_frame": [_vp, _vp, _vp, _P(cinr_camera), _P(cinr_tf), _vp, _P(cinr_frame_stats),
+                          _vp],
+    "cinr_render_frame_host": [_vp, _vp, _vp, _P(cinr_camera), _P(cinr_tf), _vp,
+                               _P(cinr_frame_stats), _vp],
+    "cinr_destroy_renderer": [_vp],
+    "cinr_debug_dump": [_vp, C.c_int, _vp, C.c_size_t, _P(C.c_size_t), _vp],
+    "cinr_cache_level_info": [_vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_long)],
+}
+
+
+def header_symbols():
+    """Function names declared in include/cinr.h."""
+    hdr = os.path.join(os.path.dirname(_build.HERE), "include", "cinr.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"^int\s+(cinr_\w+)\s*\(", txt, flags=re.M)))
+
+
+def lib(build_if_missing: bool = True):
+    """Load libcinr.so (building it with nvcc when stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise CinrError(f"libcinr.so not found at {path}; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = C.c_int
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(512)
+    lib().cinr_last_error(buf, 512)
+    return buf.value.decode()
+
+
+def check(rc: int, what: str = ""):
+    if rc != CINR_OK:
+        raise CinrError(f"{what} failed ({rc}): {last_error()}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_buffer(nbytes: int, device):
+    import torch
+    if not torch.cuda.is_available():
+        raise CinrError("CUDA device required: the renderer has no CPU path")
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _fptr(t):
+    return C.cast(C.c_void_p(t.data_ptr()), _P(C.c_float))
+
+
+# ------------------------------------------------------------ high level
+def make_inr_params(cfg, mlp_precision="fp32", table_precision="fp32", vmin=0.0, vmax=1.0):
+    return cinr_inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, float(cfg.growth),
+                           cfg.hidden, cfg.n_hidden_layers, PREC[mlp_precision],
+                           PREC[table_precision], float(vmin), float(vmax))
+
+
+def make_camera(d) -> cinr_camera:
+    c = cinr_camera()
+    c.eye[:] = [float(v) for v in d["eye"]]
+    c.target[:] = [float(v) for v in d["target"]]
+    c.up[:] = [float(v) for v in d["up"]]
+    c.fov_y_deg = float(d["fov_y_deg"])
+    c.width, c.height = int(d["width"]), int(d["height"])
+    c.step_voxels = float(d["step_voxels"])
+    return c
+
+
+def make_tf(arr) -> cinr_tf:
+    t = cinr_tf()
+    a = np.ascontiguousarray(np.asarray(arr, np.float32).reshape(256, 4))
+    C.memmove(C.addressof(t), a.ctypes.data, a.nbytes)
+    return t
+
+
+class Inr:
+    def __init__(self, params: cinr_inr_params, table: np.ndarray, mlp: np.ndarray, device="cuda",
+                 stream=None):
+        L = lib()
+        nbytes = C.c_size_t()
+        check(L.cinr_inr_bytes(C.byref(params), C.byref(nbytes)), "cinr_inr_bytes")
+        self.mem = _dev_buffer(nbytes.value, device)
+        t = np.ascontiguousarray(table, np.float32)
+        w = np.ascontiguousarray(mlp, np.float32)
+        h = C.c_void_p()
+        check(L.cinr_create_inr(C.byref(params), C.c_void_p(self.mem.data_ptr()), nbytes.value,
+                                t.ctypes.data_as(_P(C.c_float)), w.ctypes.data_as(_P(C.c_float)),
+                                _stream(stream), C.byref(h)), "cinr_create_inr")
+        self.h = h
+        self.params = params
+
+    def set_range(self, vmin, vmax):
+        check(lib().cinr_inr_set_range(self.h, float(vmin), float(vmax)), "cinr_inr_set_range")
+
+    def raw_range(self, dims, stride=1, stream=None):
+        d = (C.c_int * 3)(*dims)
+        lo, hi = C.c_float(), C.c_float()
+        check(lib().cinr_inr_raw_range(self.h, d, int(stride), C.byref(lo), C.byref(hi),
+                                       _stream(stream)), "cinr_inr_raw_range")
+        return lo.value, hi.value
+
+    def infer(self, xyz, out=None, stream=None):
+        import torch
+        n = xyz.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=xyz.device)
+        check(lib().cinr_infer(self.h, C.c_void_p(xyz.data_ptr()), n, C.c_void_p(out.data_ptr()),
+                               _stream(stream)), "cinr_infer")
+        return out
+
+    def encode(self, xyz, with_indices=False, stream=None):
+        import torch
+        n = xyz.shape[0]
+        IN = self.params.levels * self.params.feats
+        feats = torch.empty((n, IN), dtype=torch.float32, device=xyz.device)
+        idx = torch.empty((n, self.params.levels, 8), dtype=torch.int32, device=xyz.device) \
+            if with_indices else None
+        check(lib().cinr_encode(self.h, C.c_void_p(xyz.data_ptr()), n, C.c_void_p(feats.data_ptr()),
+                                C.c_void_p(idx.data_ptr()) if idx is not None else None,
+                                _stream(stream)), "cinr_encode")
+        return feats, idx
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().cinr_destroy_inr(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Cache:
+    def __init__(self, inr: Inr, dims, pool_bytes, brick=8, levels=4, n_req=40, ranking=1,
+                 preload=1, storage="fp32", device="cuda", stream=None):
+        L = lib()
+        self.opts = cinr_cache_opts(int(brick), int(levels), int(n_req), int(ranking), int(preload),
+                                    PREC[storage])
+        self.dims = (C.c_int * 3)(*dims)
+        nbytes, nslots = C.c_size_t(), C.c_long()
+        check(L.cinr_cache_bytes(self.dims, int(pool_bytes), C.byref(self.opts), C.byref(nbytes),
+                                 C.byref(nslots)), "cinr_cache_bytes")
+        self.n_slots = nslots.value
+        self.mem = _dev_buffer(nbytes.value, device)
+        h = C.c_void_p()
+        check(L.cinr_create_cache(inr.h, self.dims, C.c_void_p(self.mem.data_ptr()), nbytes.value,
+                                  int(pool_bytes), C.byref(self.opts), _stream(stream), C.byref(h)),
+              "cinr_create_cache")
+        self.h = h
+        self.inr = inr
+
+    def level_info(self, level):
+        d = (C.c_int * 3)()
+        nb = (C.c_int * 3)()
+        off = C.c_long()
+        check(lib().cinr_cache_level_info(self.h, level, d, nb, C.byref(off)), "level_info")
+        return tuple(d), tuple(nb), off.value
+
+    def dump(self, what, stream=None):
+        return debug_dump(self.h, what, stream, pool_half=self.opts.storage_precision == 1)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().cinr_destroy_cache(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+def debug_dump(handle, what, stream=None, pool_half=False):
+    L = lib()
+    n = C.c_size_t()
+    s = _stream(stream)
+    check(L.cinr_debug_dump(handle, what, None, 0, C.byref(n), s), "cinr_debug_dump")
+    if what == DUMP_POOL:
+        out = np.zeros(n.value, np.float16 if pool_half else np.float32)
+    else:
+        out = np.zeros(n.value, np.uint32)
+    if n.value:
+        check(L.cinr_debug_dump(handle, what, C.c_void_p(out.ctypes.data), n.value, C.byref(n), s),
+              "cinr_debug_dump")
+    return out
+
+
+class Renderer:
+    def __init__(self, width, height, dims, K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0,
+                 miss_record_cap=0, device="cuda"):
+        L = lib()
+        self.opts = cinr_march_opts((C.c_int * 3)(*dims), int(K), float(eps_T), int(lod_mode),
+                                    float(lod_scale), int(seed), int(miss_record_cap))
+        nbytes = C.c_size_t()
+        check(L.cinr_renderer_bytes(int(width), int(height), C.byref(self.opts), C.byref(nbytes)),
+              "cinr_renderer_bytes")
+        self.mem = _dev_buffer(nbytes.value, device)
+        h = C.c_void_p()
+        check(L.cinr_create_renderer(C.c_void_p(self.mem.data_ptr()), nbytes.value, int(width),
+                                     int(height), C.byref(self.opts), C.byref(h)),
+              "cinr_create_renderer")
+        self.h = h
+        self.W, self.H = int(width), int(height)
+        self.device = device
+
+    def render(self, inr: Inr, camera, tf, cache: Cache | None = None, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.H, self.W, 4), dtype=torch.float32, device=self.device)
+        cam = camera if isinstance(camera, cinr_camera) else make_camera(camera)
+        t = tf if isinstance(tf, cinr_tf) else make_tf(tf)
+        st = cinr_frame_stats()
+        check(lib().cinr_render_frame(self.h, cache.h if cache is not None else None, inr.h,
+                                      C.byref(cam), C.byref(t), C.c_void_p(out.data_ptr()),
+                                      C.byref(st), _stream(stream)), "cinr_render_frame")
+        return out, st.as_dict()
+
+    def render_host(self, inr: Inr, camera, tf, out_host, cache: Cache | None = None, stream=None):
+        cam = camera if isinstance(camera, cinr_camera) else make_camera(camera)
+        t = tf if isinstance(tf, cinr_tf) else make_tf(tf)
+        st = cinr_frame_stats()
+        check(lib().cinr_render_frame_host(self.h, cache.h if cache is not None else None, inr.h,
+                                           C.byref(cam), C.byref(t),
+                                           C.c_void_p(out_host.data_ptr()), C.byref(st),
+                                           _stream(stream)), "cinr_render_frame_host")
+        return st.as_dict()
+
+    def misses(self, stream=None):
+        return debug_dump(self.h, DUMP_MISSES, stream).reshape(-1, 2)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().cinr_destroy_renderer(self.h)
+                self.h = None
+        except Exception:
+            pass

@@ -1,0 +1,537 @@
+// Multi-resolution brick cache (Sec. 4.3): flat per-LoD page tables
+// (Sec. 4.3.1), ranked request list (Sec. 4.3.3), LRU victims by frame
+// stamps, brick decode by INR inference with write-back into the pool
+// (Sec. 4.3.2), coarsest-LoD preload (Sec. 4.3.4).
+#include <cmath>
+#include <cstring>
+
+#include "cinr_internal.cuh"
+
+using namespace cinr;
+
+namespace {
+
+constexpr int kSelThreads = 256;
+constexpr int kMaxReq = 1024;
+
+int bits_for(unsigned long long v) {
+  int b = 0;
+  while (b < 64 && (v >> b) != 0ull) ++b;
+  return b;
+}
+
+struct CacheLayout {
+  uint32_t *pt, *rank, *touched, *counters, *stamp, *owner, *pinned;
+  void* pool;
+  SelState *sel_req, *sel_vic;
+  unsigned long long *req_keys, *vic_keys;
+  uint32_t *req_vals, *req_sorted, *vic_vals, *vic_sorted;
+  size_t bytes;
+};
+
+struct Geometry {
+  int L, B, S;
+  int dims[kMaxLod][3], nb[kMaxLod][3];
+  unsigned long long off[kMaxLod + 1];
+};
+
+int geometry(const int vol[3], const cinr_cache_opts* o, Geometry* g) {
+  if (!o || !vol) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (o->levels < 1 || o->levels > kMaxLod)
+    return set_error(CINR_ERR_ARG, "levels must be in [1, %d]", kMaxLod);
+  if (o->brick < 2 || o->brick > 64) return set_error(CINR_ERR_ARG, "brick must be in [2, 64]");
+  if (vol[0] < 1 || vol[1] < 1 || vol[2] < 1) return set_error(CINR_ERR_ARG, "bad volume dims");
+  if (o->n_req < 1 || o->n_req > kMaxReq)
+    return set_error(CINR_ERR_ARG, "n_req must be in [1, %d]", kMaxReq);
+  if (o->storage_precision != CINR_PREC_FP32 && o->storage_precision != CINR_PREC_FP16)
+    return set_error(CINR_ERR_ARG, "storage_precision must be FP32 or FP16");
+  g->L = o->levels;
+  g->B = o->brick;
+  g->S = o->brick + 2;
+  g->off[0] = 0;
+  for (int l = 0; l < g->L; ++l) {
+    for (int a = 0; a < 3; ++a) {
+      g->dims[l][a] = (vol[a] + (1 << l) - 1) >> l;  // ceil(V / 2^l)
+      g->nb[l][a] = (g->dims[l][a] + g->B - 1) / g->B;
+    }
+    g->off[l + 1] = g->off[l] + (unsigned long long)g->nb[l][0] * g->nb[l][1] * g->nb[l][2];
+  }
+  if (g->off[g->L] >= (1ull << 31)) return set_error(CINR_ERR_ARG, "too many bricks (>= 2^31)");
+  return CINR_OK;
+}
+
+CacheLayout layout(const Geometry& g, long n_slots, int prec, void* base) {
+  Carver c(base);
+  CacheLayout L;
+  size_t nb = (size_t)g.off[g.L];
+  L.pt = c.take<uint32_t>(nb);
+  L.rank = c.take<uint32_t>(nb);
+  L.touched = c.take<uint32_t>(nb);
+  L.counters = c.take<uint32_t>(64);
+  L.stamp = c.take<uint32_t>(n_slots);
+  L.owner = c.take<uint32_t>(n_slots);
+  L.pinned = c.take<uint32_t>(n_slots);
+  L.sel_req = c.take<SelState>(1);
+  L.sel_vic = c.take<SelState>(1);
+  L.req_keys = c.take<unsigned long long>(kMaxReq);
+  L.vic_keys = c.take<unsigned long long>(kMaxReq);
+  L.req_vals = c.take<uint32_t>(kMaxReq);
+  L.req_sorted = c.take<uint32_t>(kMaxReq);
+  L.vic_vals = c.take<uint32_t>(kMaxReq);
+  L.vic_sorted = c.take<uint32_t>(kMaxReq);
+  size_t S3 = (size_t)g.S * g.S * g.S;
+  L.pool = c.take<char>((size_t)n_slots * S3 * (prec == CINR_PREC_FP16 ? 2 : 4));
+  L.bytes = align_up(c.off, 256);
+  return L;
+}
+
+long slots_for(const Geometry& g, size_t pool_bytes, int prec) {
+  size_t S3 = (size_t)g.S * g.S * g.S;
+  return (long)(pool_bytes / (S3 * (prec == CINR_PREC_FP16 ? 2 : 4)));
+}
+
+// ------------------------------------------------------------ kernels
+__global__ void fill_u32(uint32_t* p, size_t n, uint32_t v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// Key of a brick from its linear id: level, then (bx, by, bz).
+__device__ __forceinline__ int key_level(const CacheDev& c, uint32_t key) {
+  int l = 0;
+  while (l + 1 < c.L && key >= c.off[l + 1]) ++l;
+  return l;
+}
+
+// Decode: every stored voxel of a requested brick is inferred by the INR at
+// its LoD-l voxel centre (clamp-to-edge) and written into the victim slot.
+// Mode list: request i of *n_dev uses keys[i] and slots[i].  Mode preload
+// (keys == nullptr): request i is brick off[L-1] + i into slot i.
+template <int IN, int H>
+__global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const uint32_t* keys,
+                                                     const uint32_t* slots, const uint32_t* n_dev,
+                                                     uint32_t n_fixed) {
+  extern __shared__ float4 smem4[];
+  float* sw = reinterpret_cast<float*>(smem4);
+  const uint32_t n = keys ? *n_dev : n_fixed;
+  const uint32_t r = blockIdx.y;
+  if (r >= n) return;
+  load_weights(sw, q.w, mlp_floats<IN, H>());
+  __syncthreads();
+  const uint32_t key = keys ? keys[r] : c.off[c.L - 1] + r;
+  const uint32_t slot = keys ? slots[r] : r;
+  const int l = key_level(c, key);
+  const uint32_t local = key - c.off[l];
+  const int b[3] = {(int)(local % c.nb[l][0]), (int)((local / c.nb[l][0]) % c.nb[l][1]),
+                    (int)(local / ((uint32_t)c.nb[l][0] * c.nb[l][1]))};
+  const int S = c.S, S3 = S * S * S;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < S3; v += gridDim.x * blockDim.x) {
+    const int lv[3] = {v % S, (v / S) % S, v / (S * S)};
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int j = b[a] * c.B - 1 + lv[a];
+      j = j < 0 ? 0 : (j > c.dims[l][a] - 1 ? c.dims[l][a] - 1 : j);
+      float t = f_mul(f_add((float)j, 0.5f), (float)(1 << l));
+      x[a] = clamp01(f_div(t, (float)c.vol[a]));
+    }
+    const float val = fmaf(q.vscale, inr_raw_fp32<IN, H>(q, sw, x[0], x[1], x[2]), q.vmin);
+    const size_t o = (size_t)slot * S3 + v;
+    if (c.pool_prec == CINR_PREC_FP16)
+      reinterpret_cast<__half*>(c.pool)[o] = __float2half_rn(val);
+    else
+      reinterpret_cast<float*>(c.pool)[o] = val;
+  }
+}
+
+__global__ void preload_map(CacheDev c, uint32_t n) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t key = c.off[c.L - 1] + i;
+  c.pt[key] = kMapped | i;
+  c.owner[i] = key;
+  c.pinned[i] = 1u;
+}
+
+// ------------------------------------------------------ radix select
+// Candidate keys of the request list: bricks first requested this frame
+// (touched list); key = (1000 - score) << key_bits | brick with ranking
+// (score desc, brick asc), or the brick alone without ranking.
+struct ReqKeys {
+  const uint32_t* touched;
+  const uint32_t* count;
+  const uint32_t* rank;
+  uint32_t Tf;
+  int key_bits;
+  int ranking;
+  __device__ bool operator()(uint32_t i, unsigned long long& key, uint32_t& val) const {
+    if (i >= *count) return false;
+    uint32_t b = touched[i];
+    uint32_t score = rank[b] - Tf;
+    score = score > 1000u ? 1000u : score;
+    key = ranking ? ((unsigned long long)(1000u - score) << key_bits) | b : (unsigned long long)b;
+    val = b;
+    return true;
+  }
+};
+
+// Candidate keys of the victim list: slots neither pinned nor used this
+// frame; key = stamp << slot_bits | slot (least recently used first, never
+// used slots carry stamp 0).
+struct VicKeys {
+  const uint32_t* stamp;
+  const uint32_t* pinned;
+  uint32_t n_slots;
+  uint32_t frame;
+  int slot_bits;
+  __device__ bool operator()(uint32_t i, unsigned long long& key, uint32_t& val) const {
+    if (i >= n_slots) return false;
+    uint32_t st = stamp[i];
+    if (pinned[i] || st >= frame) return false;
+    key = ((unsigned long long)st << slot_bits) | i;
+    val = i;
+    return true;
+  }
+};
+
+template <class KF>
+__global__ void __launch_bounds__(kSelThreads) sel_hist(KF kf, uint32_t n, SelState* st, int shift,
+                                                        int pass) {
+  __shared__ unsigned int h[2048];
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  if (pass > 0 && st->none) return;
+  const unsigned long long prefix = st->prefix;
+  unsigned int tot = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    unsigned long long key;
+    uint32_t val;
+    if (!kf(i, key, val)) continue;
+    if (pass > 0 && (key >> (shift + 11)) != (prefix >> (shift + 11))) continue;
+    ++tot;
+    atomicAdd(&h[(key >> shift) & 2047u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+    if (h[i]) atomicAdd(&st->hist[i], h[i]);
+  if (pass == 0) {
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&st->total, tot);
+  }
+}
+
+// Picks the digit holding the k-th smallest key; one block of 1024 threads.
+__global__ void __launch_bounds__(1024) sel_pick(SelState* st, int shift, int pass, uint32_t want) {
+  __shared__ unsigned int warp_sum[32];
+  __shared__ unsigned int s_k;
+  const int t = threadIdx.x;
+  if (pass == 0 && t == 0) {
+    uint32_t k = st->total < want ? st->total : want;
+    st->none = (k == 0u);
+    st->k = k;
+    st->prefix = 0ull;
+  }
+  __syncthreads();
+  if (t == 0) s_k = st->k;
+  const unsigned int h0 = st->hist[2 * t], h1 = st->hist[2 * t + 1];
+  __syncthreads();
+  if (st->none) {
+    st->hist[2 * t] = 0;
+    st->hist[2 * t + 1] = 0;
+    return;
+  }
+  // inclusive scan of per-thread pair sums
+  unsigned int v = h0 + h1, x = v;
+  const int lane = t & 31, w = t >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned int s = warp_sum[lane], z = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned int y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= o) z += y;
+    }
+    warp_sum[lane] = z - s;  // exclusive
+  }
+  __syncthreads();
+  const unsigned int before = warp_sum[w] + x - v;  // keys in digits < 2t
+  const unsigned int k = s_k;
+  if (before < k && k <= before + v) {
+    unsigned int d, rem;
+    if (k <= before + h0) {
+      d = 2 * t;
+      rem = k - before;
+    } else {
+      d = 2 * t + 1;
+      rem = k - before - h0;
+    }
+    st->prefix |= (unsigned long long)d << shift;
+    st->k = rem;
+  }
+  st->hist[2 * t] = 0;
+  st->hist[2 * t + 1] = 0;
+}
+
+template <class KF>
+__global__ void __launch_bounds__(kSelThreads) sel_gather(KF kf, uint32_t n, SelState* st,
+                                                          unsigned long long* keys, uint32_t* vals) {
+  if (st->none) return;
+  const unsigned long long thr = st->prefix;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    unsigned long long key;
+    uint32_t val;
+    if (!kf(i, key, val) || key > thr) continue;
+    uint32_t pos = atomicAdd(&st->count, 1u);
+    if (pos < kMaxReq) {
+      keys[pos] = key;
+      vals[pos] = val;
+    }
+  }
+}
+
+// Orders the gathered (at most kMaxReq) entries by key; writes the count.
+__global__ void __launch_bounds__(kMaxReq) sel_sort(SelState* st, const unsigned long long* keys,
+                                                    const uint32_t* vals, uint32_t* sorted,
+                                                    uint32_t* n_out) {
+  const uint32_t n = st->none ? 0u : (st->count < kMaxReq ? st->count : kMaxReq);
+  const uint32_t t = threadIdx.x;
+  if (t < n) {
+    const unsigned long long k = keys[t];
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < n; ++j) r += keys[j] < k;
+    sorted[r] = vals[t];
+  }
+  if (t == 0) *n_out = n;
+}
+
+__global__ void sel_reset(SelState* st) {
+  if (threadIdx.x == 0) {
+    st->prefix = 0;
+    st->k = 0;
+    st->total = 0;
+    st->none = 0;
+    st->count = 0;
+  }
+}
+
+// Commit (Fig. 1 step 5): request i gets victim i; the victim's previous
+// brick is unmapped, the requested brick mapped, the slot stamped.
+__global__ void commit_kernel(CacheDev c, const uint32_t* req, const uint32_t* req_n,
+                              const uint32_t* vic, const uint32_t* vic_n, uint32_t frame,
+                              uint32_t* decode_n, unsigned long long* stats, uint32_t S3) {
+  const uint32_t m = *req_n < *vic_n ? *req_n : *vic_n;
+  uint32_t ev = 0;
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const uint32_t slot = vic[i], key = req[i];
+    const uint32_t old = c.owner[slot];
+    if (old != kNoOwner) {
+      c.pt[old] = 0u;
+      ++ev;
+    }
+    c.pt[key] = kMapped | slot;
+    c.owner[slot] = key;
+    c.stamp[slot] = frame;
+  }
+  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+  if ((threadIdx.x & 31) == 0 && ev) atomicAdd(&stats[ST_EVICT], (unsigned long long)ev);
+  if (threadIdx.x == 0) {
+    *decode_n = m;
+    stats[ST_DECODED] += m;
+    stats[ST_DECODE] += (unsigned long long)m * S3;
+  }
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <class KF>
+int radix_select(const KF& kf, uint32_t n, int key_bits, uint32_t want, SelState* st,
+                 unsigned long long* keys, uint32_t* vals, uint32_t* sorted, uint32_t* n_out,
+                 cudaStream_t s) {
+  const int passes = key_bits <= 11 ? 1 : (key_bits + 10) / 11;
+  unsigned blocks = (unsigned)((n + kSelThreads - 1) / kSelThreads);
+  unsigned cap = (unsigned)num_sms() * 4;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  sel_reset<<<1, 32, 0, s>>>(st);
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 11 * (passes - 1 - p);
+    sel_hist<KF><<<blocks, kSelThreads, 0, s>>>(kf, n, st, shift, p);
+    sel_pick<<<1, 1024, 0, s>>>(st, shift, p, want);
+  }
+  sel_gather<KF><<<blocks, kSelThreads, 0, s>>>(kf, n, st, keys, vals);
+  sel_sort<<<1, kMaxReq, 0, s>>>(st, keys, vals, sorted, n_out);
+  CINR_CK(cudaGetLastError());
+  return CINR_OK;
+}
+
+template <int IN, int H>
+int launch_decode(const InrDev& q, const CacheDev& c, const uint32_t* keys, const uint32_t* slots,
+                  const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s) {
+  if (n_grid == 0) return CINR_OK;
+  const int smem = mlp_floats<IN, H>() * 4;
+  auto k = decode_kernel<IN, H>;
+  CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int S3 = c.S * c.S * c.S;
+  dim3 grid((S3 + 127) / 128, n_grid);
+  k<<<grid, 128, smem, s>>>(q, c, keys, slots, n_dev, n_grid);
+  CINR_CK(cudaGetLastError());
+  return CINR_OK;
+}
+
+int decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys, const uint32_t* slots,
+           const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s) {
+  switch (shape_of(inr->dev.IN, inr->dev.H)) {
+    case Shape::S16x32: return launch_decode<16, 32>(inr->dev, c, keys, slots, n_dev, n_grid, s);
+    case Shape::S32x64: return launch_decode<32, 64>(inr->dev, c, keys, slots, n_dev, n_grid, s);
+    case Shape::S48x64: return launch_decode<48, 64>(inr->dev, c, keys, slots, n_dev, n_grid, s);
+    default: return set_error(CINR_ERR_ARG, "unsupported shape");
+  }
+}
+
+}  // namespace
+
+extern "C" int cinr_cache_bytes(const int dims[3], size_t pool_bytes, const cinr_cache_opts* o,
+                                size_t* bytes, long* n_slots) {
+  Geometry g;
+  int e = geometry(dims, o, &g);
+  if (e) return e;
+  if (!bytes) return set_error(CINR_ERR_ARG, "bytes is NULL");
+  long ns = slots_for(g, pool_bytes, o->storage_precision);
+  if (ns < 1) return set_error(CINR_ERR_ARG, "pool holds no brick");
+  if (ns >= (1l << 31) - 1) return set_error(CINR_ERR_ARG, "too many slots");
+  *bytes = layout(g, ns, o->storage_precision, nullptr).bytes;
+  if (n_slots) *n_slots = ns;
+  return CINR_OK;
+}
+
+extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_mem, size_t bytes,
+                                 size_t pool_bytes, const cinr_cache_opts* o, cinr_stream_t stream,
+                                 cinr_cache_t* out) {
+  if (!inr || !out) return set_error(CINR_ERR_ARG, "NULL argument");
+  Geometry g;
+  int e = geometry(dims, o, &g);
+  if (e) return e;
+  long ns = slots_for(g, pool_bytes, o->storage_precision);
+  if (ns < 1) return set_error(CINR_ERR_ARG, "pool holds no brick");
+  if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) & 255))
+    return set_error(CINR_ERR_ARG, "dev_mem must be non-NULL and 256-byte aligned");
+  CacheLayout L = layout(g, ns, o->storage_precision, dev_mem);
+  if (bytes < L.bytes)
+    return set_error(CINR_ERR_NOMEM, "cache needs %zu bytes, got %zu", L.bytes, bytes);
+  const unsigned long long n_coarse = g.off[g.L] - g.off[g.L - 1];
+  if (o->preload && (long)n_coarse > ns)
+    return set_error(CINR_ERR_NOMEM, "pool of %ld bricks cannot hold the %llu coarsest bricks", ns,
+                     n_coarse);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cinr_cache_s* c = new cinr_cache_s();
+  c->o = *o;
+  c->n_slots = ns;
+  c->n_bricks = (long)g.off[g.L];
+  c->frame = 0;
+  c->inr = inr;
+  CacheDev& d = c->dev;
+  for (int a = 0; a < 3; ++a) d.vol[a] = dims[a];
+  d.pt = L.pt;
+  d.rank = L.rank;
+  d.stamp = L.stamp;
+  d.owner = L.owner;
+  d.pinned = L.pinned;
+  d.pool = L.pool;
+  d.pool_prec = o->storage_precision;
+  d.B = g.B;
+  d.S = g.S;
+  d.L = g.L;
+  for (int l = 0; l < kMaxLod; ++l)
+    for (int a = 0; a < 3; ++a) {
+      d.dims[l][a] = l < g.L ? g.dims[l][a] : 1;
+      d.nb[l][a] = l < g.L ? g.nb[l][a] : 1;
+    }
+  for (int l = 0; l <= kMaxLod; ++l) d.off[l] = (uint32_t)(l <= g.L ? g.off[l] : g.off[g.L]);
+  d.touched = L.touched;
+  d.touched_count = L.counters;
+  c->sel_req = L.sel_req;
+  c->sel_vic = L.sel_vic;
+  c->req_keys = L.req_keys;
+  c->req_vals = L.req_vals;
+  c->req_sorted = L.req_sorted;
+  c->req_n = L.counters + 1;
+  c->vic_keys = L.vic_keys;
+  c->vic_vals = L.vic_vals;
+  c->vic_sorted = L.vic_sorted;
+  c->vic_n = L.counters + 2;
+  c->decode_n = L.counters + 3;
+  c->key_bits = bits_for((unsigned long long)c->n_bricks);
+  c->slot_bits = bits_for((unsigned long long)ns);
+
+  size_t nb = (size_t)c->n_bricks;
+  CINR_CK(cudaMemsetAsync(L.pt, 0, nb * 4, s));
+  CINR_CK(cudaMemsetAsync(L.rank, 0, nb * 4, s));
+  CINR_CK(cudaMemsetAsync(L.counters, 0, 64 * 4, s));
+  CINR_CK(cudaMemsetAsync(L.stamp, 0, (size_t)ns * 4, s));
+  CINR_CK(cudaMemsetAsync(L.pinned, 0, (size_t)ns * 4, s));
+  CINR_CK(cudaMemsetAsync(L.sel_req, 0, sizeof(SelState), s));
+  CINR_CK(cudaMemsetAsync(L.sel_vic, 0, sizeof(SelState), s));
+  fill_u32<<<256, 256, 0, s>>>(L.owner, (size_t)ns, kNoOwner);
+  CINR_CK(cudaGetLastError());
+  if (o->preload) {
+    e = decode(inr, d, nullptr, nullptr, nullptr, (uint32_t)n_coarse, s);
+    if (e) {
+      delete c;
+      return e;
+    }
+    preload_map<<<(unsigned)((n_coarse + 255) / 256), 256, 0, s>>>(d, (uint32_t)n_coarse);
+    CINR_CK(cudaGetLastError());
+  }
+  *out = c;
+  return CINR_OK;
+}
+
+extern "C" int cinr_destroy_cache(cinr_cache_t cache) {
+  delete cache;
+  return CINR_OK;
+}
+
+int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStream_t s) {
+  const uint32_t frame = (uint32_t)c->frame;
+  const uint32_t Tf = (uint32_t)(1001ull * c->frame);
+  const uint32_t want = (uint32_t)c->o.n_req;
+  ReqKeys rk{c->dev.touched, c->dev.touched_count, c->dev.rank, Tf, c->key_bits, c->o.ranking};
+  const int rbits = c->o.ranking ? c->key_bits + 10 : c->key_bits;
+  int e = radix_select(rk, (uint32_t)c->n_bricks, rbits, want, c->sel_req, c->req_keys,
+                       c->req_vals, c->req_sorted, c->req_n, s);
+  if (e) return e;
+  VicKeys vk{c->dev.stamp, c->dev.pinned, (uint32_t)c->n_slots, frame, c->slot_bits};
+  const int vbits = c->slot_bits + bits_for((unsigned long long)frame);
+  e = radix_select(vk, (uint32_t)c->n_slots, vbits, want, c->sel_vic, c->vic_keys, c->vic_vals,
+                   c->vic_sorted, c->vic_n, s);
+  if (e) return e;
+  commit_kernel<<<1, 1024, 0, s>>>(c->dev, c->req_sorted, c->req_n, c->vic_sorted, c->vic_n, frame,
+                                   c->decode_n, stats_dev, (uint32_t)(c->dev.S * c->dev.S * c->dev.S));
+  CINR_CK(cudaGetLastError());
+  return decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, s);
+}
+
+extern "C" int cinr_cache_level_info(cinr_cache_t cache, int level, int dims[3], int nbricks[3],
+                                     long* key_offset) {
+  if (!cache) return set_error(CINR_ERR_ARG, "cache is NULL");
+  if (level < 0 || level >= cache->dev.L) return set_error(CINR_ERR_ARG, "bad level");
+  for (int a = 0; a < 3; ++a) {
+    if (dims) dims[a] = cache->dev.dims[level][a];
+    if (nbricks) nbricks[a] = cache->dev.nb[level][a];
+  }
+  if (key_offset) *key_offset = (long)cache->dev.off[level];
+  return CINR_OK;
+}

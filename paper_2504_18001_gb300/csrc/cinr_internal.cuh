@@ -1,0 +1,369 @@
+// Internal definitions of the GB300 INR renderer library (not part of the
+// C ABI).  Device structs are passed to kernels by value.
+//
+// Numeric contract of the discrete decisions: every quantity that feeds a
+// floor, a comparison or a hash (ray direction, sample parameter, positions,
+// grid coordinates) is computed with explicitly rounded binary32 intrinsics
+// (__fmul_rn, __fadd_rn, __fdiv_rn, __fsqrt_rn), never contracted into FMAs,
+// in a fixed operation order, so that LoD, brick, hash index and hit/miss
+// decisions are reproducible on any IEEE binary32 implementation.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "cinr.h"
+
+namespace cinr {
+
+constexpr int kMaxLevels = 32;    // hash-grid levels
+constexpr int kMaxLod = 12;       // cache LoDs
+constexpr uint32_t kMapped = 0x80000000u;
+constexpr uint32_t kNoOwner = 0xFFFFFFFFu;
+constexpr int kFrameThreads = 128;  // 4 warps per CTA in the frame kernel
+
+// ---------------------------------------------------------------- errors
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+#define CINR_CK(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_error(e_, #call); \
+  } while (0)
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over a caller-provided device buffer (no device allocation).
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += sizeof(T) * count;
+    return p;
+  }
+};
+
+// ------------------------------------------------------------ device INR
+struct InrDev {
+  const void* table;   // levels * T * 2 entries, float or half
+  const float* w;      // fp32 weights, layer-major [out][in]
+  int L, log2T;
+  int res[kMaxLevels];
+  uint32_t dense_mask;
+  int IN, H, NH;
+  int table_prec;
+  float vmin, vscale;  // v = vmin + vscale * y
+};
+
+// Camera and marching constants, computed on the host in binary32.
+struct CamDev {
+  float o[3], fwd[3], right[3], upv[3];
+  float ax, ay;        // tan(fov/2) * aspect, tan(fov/2)
+  int W, H;
+  float e[3], h[3];    // box extent and half extent
+  float dt;            // step in world units
+  float lodc;          // footprint constant: t * lodc = pixel footprint in LoD-0 voxels
+  float lod_scale;
+  int lod_mode;
+  int vol[3];
+};
+
+struct CacheDev {
+  int vol[3];
+  uint32_t* pt;
+  uint32_t* rank;
+  uint32_t* stamp;
+  uint32_t* owner;
+  uint32_t* pinned;
+  void* pool;
+  int pool_prec;
+  int B, S, L;
+  int dims[kMaxLod][3];
+  int nb[kMaxLod][3];
+  uint32_t off[kMaxLod + 1];
+  uint32_t* touched;
+  uint32_t* touched_count;
+};
+
+// ------------------------------------------------- binary32 primitives
+__device__ __forceinline__ float f_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float f_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float f_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float f_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
+
+// Primary ray of pixel (px, py) clipped to the volume box (slab test).
+// Returns true when the ray hits; o is the camera position.
+__device__ __forceinline__ bool ray_setup(const CamDev& c, int px, int py, float d[3],
+                                          float& tn, float& tf) {
+  float sx = f_div(f_add((float)px, 0.5f), (float)c.W);
+  float sy = f_div(f_add((float)py, 0.5f), (float)c.H);
+  float u = f_mul(f_sub(f_mul(sx, 2.0f), 1.0f), c.ax);
+  float v = f_mul(f_sub(1.0f, f_mul(sy, 2.0f)), c.ay);
+  float dr[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dr[a] = f_add(f_add(c.fwd[a], f_mul(u, c.right[a])), f_mul(v, c.upv[a]));
+  float l2 = f_add(f_add(f_mul(dr[0], dr[0]), f_mul(dr[1], dr[1])), f_mul(dr[2], dr[2]));
+  float l = __fsqrt_rn(l2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = f_div(dr[a], l);
+  float tmin[3], tmax[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float inv = f_div(1.0f, d[a]);
+    float t0 = f_mul(f_sub(-c.h[a], c.o[a]), inv);
+    float t1 = f_mul(f_sub(c.h[a], c.o[a]), inv);
+    tmin[a] = fminf(t0, t1);
+    tmax[a] = fmaxf(t0, t1);
+  }
+  tn = fmaxf(fmaxf(tmin[0], tmin[1]), fmaxf(tmin[2], 0.0f));
+  tf = fminf(fminf(tmax[0], tmax[1]), tmax[2]);
+  return tn < tf;
+}
+
+// Sample k of a ray: midpoint of [tn + k dt, min(tn + (k+1) dt, tf)] and its
+// length; x = normalised coordinate in [0,1]^3.  Returns false past tf.
+__device__ __forceinline__ bool sample_at(const CamDev& c, const float d[3], float tn, float tf,
+                                          int k, float x[3], float& tm, float& len) {
+  float a = f_add(tn, f_mul((float)k, c.dt));
+  if (!(a < tf)) return false;
+  float b = fminf(f_add(tn, f_mul((float)(k + 1), c.dt)), tf);
+  tm = f_mul(f_add(a, b), 0.5f);
+  len = f_sub(b, a);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    float p = f_add(c.o[q], f_mul(tm, d[q]));
+    x[q] = clamp01(f_div(f_add(p, c.h[q]), c.e[q]));
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint32_t xorshift32(uint32_t s) {
+  s ^= s << 13;
+  s ^= s >> 17;
+  s ^= s << 5;
+  return s;
+}
+
+// Per-ray seed: MurmurHash3 finaliser of frame_seed ^ pixel * 0x9E3779B9.
+__device__ __forceinline__ uint32_t ray_seed(uint32_t fseed, uint32_t pixel) {
+  uint32_t h = fseed ^ (pixel * 0x9E3779B9u);
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// Stochastic LoD of one sample (Alg. 2, Sec. 5.3): floor(D) plus one with
+// probability frac(D), from one xorshift32 step keyed by (ray, sample).
+__device__ __forceinline__ int sample_lod(const CamDev& c, int L, int lod_min, uint32_t rseed,
+                                          uint32_t k, float tm) {
+  uint32_t s = rseed ^ (k * 0x9E3779B9u);
+  if (s == 0u) s = 0x6D2B79F5u;
+  uint32_t u24 = xorshift32(s) >> 8;
+  int base, inc;
+  if (c.lod_mode == 0) {
+    float xf = f_mul(tm, c.lodc);
+    if (!(xf >= 1.0f)) {
+      base = 0;
+      inc = 0;
+    } else {
+      uint32_t bits = __float_as_uint(xf);
+      base = (int)((bits >> 23) & 0xFFu) - 127;
+      inc = u24 < 2u * (bits & 0x7FFFFFu);
+    }
+  } else {
+    float D = f_mul(tm, c.lod_scale);
+    float fl = floorf(D);
+    float fr = f_sub(D, fl);
+    base = fl > 1e6f ? 1000000 : (int)fl;
+    inc = f_mul((float)u24, 5.9604644775390625e-08f) < fr;
+  }
+  int lod = base + inc;
+  lod = lod < lod_min ? lod_min : lod;
+  return lod > L - 1 ? L - 1 : lod;
+}
+
+// ----------------------------------------------------- hash-grid encoding
+__device__ __forceinline__ float2 load_entry(const void* table, int prec, uint32_t i) {
+  if (prec == CINR_PREC_FP16) {
+    __half2 h = __ldg(reinterpret_cast<const __half2*>(table) + i);
+    return __half22float2(h);
+  }
+  return __ldg(reinterpret_cast<const float2*>(table) + i);
+}
+
+__device__ __forceinline__ uint32_t vertex_index(bool dense, uint32_t n1, uint32_t T, uint32_t cx,
+                                                 uint32_t cy, uint32_t cz) {
+  if (dense) return cx + n1 * (cy + n1 * cz);
+  return ((cx * 1u) ^ (cy * 2654435761u) ^ (cz * 805459861u)) & (T - 1u);
+}
+
+// Cell of x in [0,1] on an N-cell grid: binary32 x*N, floor, clamp, weight.
+__device__ __forceinline__ void grid_cell(float x, int N, int& i, float& w) {
+  float xl = f_mul(x, (float)N);
+  int ii = (int)floorf(xl);
+  ii = ii < 0 ? 0 : (ii > N - 1 ? N - 1 : ii);
+  i = ii;
+  w = f_sub(xl, (float)ii);
+}
+
+// Features of one point (levels concatenated, 2 per level): trilinear blend
+// of the 8 vertex entries of each level (Sec. 3, Fig. 2).
+template <int L>
+__device__ __forceinline__ void encode_point(const InrDev& q, float x, float y, float z,
+                                             float* feat) {
+  const uint32_t T = 1u << q.log2T;
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    const int N = q.res[l];
+    int ix, iy, iz;
+    float wx, wy, wz;
+    grid_cell(x, N, ix, wx);
+    grid_cell(y, N, iy, wy);
+    grid_cell(z, N, iz, wz);
+    const bool dense = (q.dense_mask >> l) & 1u;
+    const uint32_t n1 = (uint32_t)N + 1u;
+    const uint32_t base = (uint32_t)l * T;
+    float f0 = 0.0f, f1 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t cx = ix + (c & 1), cy = iy + ((c >> 1) & 1), cz = iz + ((c >> 2) & 1);
+      const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) *
+                      ((c & 4) ? wz : 1.0f - wz);
+      const float2 e = load_entry(q.table, q.table_prec, base + vertex_index(dense, n1, T, cx, cy, cz));
+      f0 = fmaf(w, e.x, f0);
+      f1 = fmaf(w, e.y, f1);
+    }
+    feat[2 * l] = f0;
+    feat[2 * l + 1] = f1;
+  }
+}
+
+// FP32 SIMT MLP (in -> H -> H -> 1, ReLU, no biases); weights in shared
+// memory, W1 [H][IN] then W2 [H][H] then W3 [H].
+template <int IN, int H>
+__device__ __forceinline__ float mlp_fp32(const float* __restrict__ sw, const float* feat) {
+  float h1[H];
+#pragma unroll
+  for (int o = 0; o < H; ++o) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < IN; i += 4) {
+      const float4 w4 = *reinterpret_cast<const float4*>(sw + o * IN + i);
+      s = fmaf(w4.x, feat[i], s);
+      s = fmaf(w4.y, feat[i + 1], s);
+      s = fmaf(w4.z, feat[i + 2], s);
+      s = fmaf(w4.w, feat[i + 3], s);
+    }
+    h1[o] = fmaxf(s, 0.0f);
+  }
+  const float* w2 = sw + IN * H;
+  const float* w3 = w2 + H * H;
+  float y = 0.0f;
+#pragma unroll 2
+  for (int o = 0; o < H; ++o) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < H; i += 4) {
+      const float4 w4 = *reinterpret_cast<const float4*>(w2 + o * H + i);
+      s = fmaf(w4.x, h1[i], s);
+      s = fmaf(w4.y, h1[i + 1], s);
+      s = fmaf(w4.z, h1[i + 2], s);
+      s = fmaf(w4.w, h1[i + 3], s);
+    }
+    y = fmaf(w3[o], fmaxf(s, 0.0f), y);
+  }
+  return y;
+}
+
+template <int IN, int H>
+__device__ __forceinline__ float inr_raw_fp32(const InrDev& q, const float* sw, float x, float y,
+                                              float z) {
+  float feat[IN];
+  encode_point<IN / 2>(q, x, y, z, feat);
+  return mlp_fp32<IN, H>(sw, feat);
+}
+
+template <int IN, int H>
+__host__ __device__ constexpr int mlp_floats() {
+  return IN * H + H * H + H;
+}
+
+// Cooperative copy of the fp32 weights into shared memory.
+__device__ __forceinline__ void load_weights(float* sw, const float* w, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sw[i] = __ldg(w + i);
+}
+
+// Supported (IN, H) pairs; dispatch helper for host code.
+enum class Shape { S16x32, S32x64, S48x64, Bad };
+inline Shape shape_of(int IN, int H) {
+  if (IN == 16 && H == 32) return Shape::S16x32;
+  if (IN == 32 && H == 64) return Shape::S32x64;
+  if (IN == 48 && H == 64) return Shape::S48x64;
+  return Shape::Bad;
+}
+
+}  // namespace cinr
+
+// Frame statistics slots (device u64 counters).
+namespace cinr {
+enum StatIdx {
+  ST_SAMPLES = 0, ST_DIRECT, ST_DECODE, ST_MISSES, ST_FALLBACK, ST_HITS, ST_REQ,
+  ST_DECODED, ST_EVICT, ST_RECORDED, ST_SLOTS, ST_COUNT
+};
+
+// Radix-select state (find the n smallest unique 64-bit keys).
+struct SelState {
+  unsigned long long prefix;
+  unsigned int k;
+  unsigned int total;
+  unsigned int none;
+  unsigned int count;
+  unsigned int hist[2048];
+};
+}  // namespace cinr
+
+// Opaque handles (host side).
+struct cinr_inr_s {
+  cinr::InrDev dev;
+  cinr_inr_params p;
+  void* mem;
+  size_t bytes;
+  float* scratch;  // small device scratch for reductions
+  int device;
+};
+
+struct cinr_cache_s {
+  cinr::CacheDev dev;
+  cinr_cache_opts o;
+  long n_slots, n_bricks;
+  uint64_t frame;
+  cinr_inr_s* inr;
+  cinr::SelState* sel_req;
+  cinr::SelState* sel_vic;
+  unsigned long long* req_keys;
+  uint32_t* req_vals;
+  uint32_t* req_sorted;
+  uint32_t* req_n;
+  unsigned long long* vic_keys;
+  uint32_t* vic_vals;
+  uint32_t* vic_sorted;
+  uint32_t* vic_n;
+  uint32_t* decode_n;
+  int slot_bits, key_bits;
+};
+
+// Cache update at the end of a frame (request selection, victims, commit,
+// decode), enqueued on `s`; stats_dev receives decoded/evicted counts.
+int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStream_t s);

@@ -1,0 +1,651 @@
+// Per-frame ray marching (Fig. 1, Alg. 1, Alg. 2, Sec. 5.1).
+//
+// One persistent kernel renders a frame.  Each warp owns one ray at a time
+// and marches it in segments of 32 consecutive samples (lane i = sample
+// k0 + i).  Per segment:
+//   1. lanes compute their sample (binary32 contract), pick a stochastic LoD
+//      (Sec. 5.3) and walk the page tables from that LoD to coarser ones
+//      (Sec. 4.3); an Unmapped requested brick raises a ranked request
+//      (Sec. 4.3.3); the first mapped brick is sampled trilinearly and its
+//      slot stamped (LRU);
+//   2. true misses of the CTA's 4 warps are compacted by warp ballot and
+//      prefix sums into shared memory (Alg. 2's miss list), inferred by the
+//      INR in one batch by all 128 threads and scattered back (InferINR and
+//      InsertMisses of Alg. 1);
+//   3. the warp composites its 32 samples front to back with a warp scan of
+//      transmittances, and tests early termination after every K samples.
+// Without a cache every sample is a true miss: the uncached baseline.
+// Rays are handed out from an atomic counter in 8x8 pixel tiles.
+#include <cmath>
+#include <cstring>
+
+#include "cinr_internal.cuh"
+
+using namespace cinr;
+
+struct cinr_renderer_s {
+  int W, H;
+  cinr_march_opts o;
+  uint32_t* counters;            // [0] ray counter, [1] miss-record count
+  unsigned long long* stats;     // ST_COUNT counters
+  uint32_t* miss_rec;            // 2 * miss_cap
+  float4* image;                 // W*H, for cinr_render_frame_host
+  uint64_t frame;                // frame counter of uncached rendering
+  int device;
+  cudaEvent_t ev[3];             // frame kernel start/end, cache update end
+};
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+struct FrameParams {
+  CamDev cam;
+  InrDev inr;
+  CacheDev cache;
+  float4 tf[256];
+  float4* out;
+  uint32_t n_rays;
+  uint32_t tiles_x;
+  uint32_t* ray_counter;
+  unsigned long long* stats;
+  uint32_t frame, Tf, fseed;
+  int K;
+  float eps;
+  uint32_t* miss_rec;
+  uint32_t miss_cap;
+  uint32_t* miss_count;
+};
+
+__device__ __forceinline__ float4 tf_lookup(const float4* s_tf, float v) {
+  v = clamp01(v);
+  const float x = v * 255.0f;
+  int i = (int)x;
+  i = i > 255 ? 255 : i;
+  const int i1 = i + 1 > 255 ? 255 : i + 1;
+  const float fr = x - (float)i;
+  const float4 a = s_tf[i], b = s_tf[i1];
+  return make_float4(fmaf(fr, b.x - a.x, a.x), fmaf(fr, b.y - a.y, a.y), fmaf(fr, b.z - a.z, a.z),
+                     fmaf(fr, b.w - a.w, a.w));
+}
+
+__device__ __forceinline__ float pool_at(const CacheDev& c, size_t i) {
+  if (c.pool_prec == CINR_PREC_FP16) return __half2float(__ldg(reinterpret_cast<const __half*>(c.pool) + i));
+  return __ldg(reinterpret_cast<const float*>(c.pool) + i);
+}
+
+// Trilinear sample inside a stored brick (slot) at LoD-l coordinates s.
+__device__ __forceinline__ float brick_sample(const CacheDev& c, int l, uint32_t slot, const int b[3],
+                                              const float s[3]) {
+  int li[3];
+  float f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float q = fminf(fmaxf(f_sub(s[a], 0.5f), 0.0f), (float)(c.dims[l][a] - 1));
+    const int i0 = (int)floorf(q);
+    f[a] = f_sub(q, (float)i0);
+    li[a] = i0 - (b[a] * c.B - 1);
+  }
+  const int S = c.S;
+  const size_t base = (size_t)slot * (size_t)(S * S * S) + (size_t)((li[2] * S + li[1]) * S + li[0]);
+  const float v000 = pool_at(c, base), v100 = pool_at(c, base + 1);
+  const float v010 = pool_at(c, base + S), v110 = pool_at(c, base + S + 1);
+  const float v001 = pool_at(c, base + S * S), v101 = pool_at(c, base + S * S + 1);
+  const float v011 = pool_at(c, base + S * S + S), v111 = pool_at(c, base + S * S + S + 1);
+  const float x00 = fmaf(f[0], v100 - v000, v000), x10 = fmaf(f[0], v110 - v010, v010);
+  const float x01 = fmaf(f[0], v101 - v001, v001), x11 = fmaf(f[0], v111 - v011, v011);
+  const float y0 = fmaf(f[1], x10 - x00, x00), y1 = fmaf(f[1], x11 - x01, x01);
+  return fmaf(f[2], y1 - y0, y0);
+}
+
+template <int IN, int H, bool CACHED>
+__global__ void __launch_bounds__(kFrameThreads, CACHED ? 6 : 4)
+    frame_kernel(const __grid_constant__ FrameParams P) {
+  extern __shared__ float4 smem4[];
+  float4* s_tf = smem4;                                   // 256
+  float4* s_miss = s_tf + 256;                            // 128
+  float* s_val = reinterpret_cast<float*>(s_miss + 128);  // 128
+  int* s_i = reinterpret_cast<int*>(s_val + 128);         // 32 ints of bookkeeping
+  float* sw = reinterpret_cast<float*>(s_i + 32);         // MLP weights
+  int* s_cnt = s_i;        // [2][4] per-warp miss counts (double buffered)
+  int* s_act = s_i + 8;    // [2][4] per-warp active flags
+  int* s_pix = s_i + 16;   // [4] pixel of each warp's ray
+  int* s_k0 = s_i + 20;    // [4] first sample of each warp's segment
+  int* s_mbase = s_i + 24; // [2] miss-record base
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
+  load_weights(sw, P.inr.w, mlp_floats<IN, H>());
+  __syncthreads();
+
+  const CamDev& cam = P.cam;
+  int state = 0;  // 0 needs a ray, 1 marching, 2 no rays left
+  uint32_t pixel = 0, rseed = 0;
+  float d[3] = {0.f, 0.f, 0.f}, tn = 0.f, tf = 0.f, T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
+  int k0 = 0;
+  uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0;
+  int parity = 0;
+
+  while (true) {
+    while (state == 0) {  // warp-uniform: fetch the next ray
+      uint32_t r = 0;
+      if (lane == 0) r = atomicAdd(P.ray_counter, 1u);
+      r = __shfl_sync(kFull, r, 0);
+      if (r >= P.n_rays) {
+        state = 2;
+        break;
+      }
+      const uint32_t tile = r >> 6, w = r & 63u;
+      const int px = (int)((tile % P.tiles_x) * 8 + (w & 7u));
+      const int py = (int)((tile / P.tiles_x) * 8 + (w >> 3));
+      if (px >= cam.W || py >= cam.H) continue;
+      pixel = (uint32_t)(py * cam.W + px);
+      if (!ray_setup(cam, px, py, d, tn, tf)) {
+        if (lane == 0) P.out[pixel] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      state = 1;
+      k0 = 0;
+      T = 1.f;
+      Cr = Cg = Cb = 0.f;
+      rseed = ray_seed(P.fseed, pixel);
+    }
+    const bool active = state == 1;
+
+    // ---- 1. sample + cache lookup
+    float x[3] = {0.f, 0.f, 0.f}, tm = 0.f, len = 0.f, v = 0.f;
+    bool has = false, miss = false;
+    if (active) {
+      has = sample_at(cam, d, tn, tf, k0 + lane, x, tm, len);
+      if (has) {
+        ++n_samp;
+        if (!CACHED) miss = true;
+      }
+    }
+    if (CACHED) {
+      const CacheDev& c = P.cache;
+      bool want_req = false, hit = false;
+      uint32_t req_key = 0, hit_slot = 0;
+      if (has) {
+        const int l = sample_lod(cam, c.L, 0, rseed, (uint32_t)(k0 + lane), tm);
+        float pv[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) pv[a] = f_mul(x[a], (float)c.vol[a]);
+        for (int lev = l; lev < c.L; ++lev) {
+          const float sc = 1.0f / (float)(1 << lev);
+          float s[3];
+          int b[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            s[a] = f_mul(pv[a], sc);
+            int bi = (int)floorf(f_div(s[a], (float)c.B));
+            bi = bi < 0 ? 0 : (bi > c.nb[lev][a] - 1 ? c.nb[lev][a] - 1 : bi);
+            b[a] = bi;
+          }
+          const uint32_t key =
+              c.off[lev] + (uint32_t)b[0] + (uint32_t)c.nb[lev][0] * ((uint32_t)b[1] + (uint32_t)c.nb[lev][1] * (uint32_t)b[2]);
+          const uint32_t e = __ldg(c.pt + key);
+          if (!(e & kMapped)) {
+            if (lev == l) {
+              want_req = true;
+              req_key = key;
+            }
+            continue;
+          }
+          hit_slot = e & ~kMapped;
+          v = brick_sample(c, lev, hit_slot, b, s);
+          hit = true;
+          if (lev == l)
+            ++n_hit;
+          else
+            ++n_fb;
+          break;
+        }
+        if (!hit) {
+          miss = true;
+          ++n_miss;
+        }
+      }
+      // ranked request (Sec. 4.3.3), aggregated over lanes asking for the
+      // same brick: r = max(r, T_f) + count, clamped at T_f + 1000
+      const unsigned rq = __ballot_sync(kFull, want_req);
+      if (want_req) {
+        const unsigned peers = __match_any_sync(rq, req_key);
+        if (lane == __ffs(peers) - 1) {
+          const uint32_t old = atomicMax(c.rank + req_key, P.Tf);
+          if (old < P.Tf) {
+            ++n_req;
+            c.touched[atomicAdd(c.touched_count, 1u)] = req_key;
+          }
+          atomicAdd(c.rank + req_key, (uint32_t)__popc(peers));
+          atomicMin(c.rank + req_key, P.Tf + 1000u);
+        }
+      }
+      // LRU stamp of the slots that served this segment
+      const unsigned hm = __ballot_sync(kFull, hit);
+      if (hit) {
+        const unsigned peers = __match_any_sync(hm, hit_slot);
+        if (lane == __ffs(peers) - 1 && c.stamp[hit_slot] != P.frame &&
+            atomicExch(c.stamp + hit_slot, P.frame) != P.frame)
+          ++n_slot;
+      }
+    }
+
+    // ---- 2. miss compaction (ballot + prefix sums) and batched inference
+    const unsigned bal = __ballot_sync(kFull, miss);
+    if (lane == 0) {
+      s_cnt[parity * 4 + warp] = __popc(bal);
+      s_act[parity * 4 + warp] = active ? 1 : 0;
+      s_pix[warp] = (int)pixel;
+      s_k0[warp] = k0;
+    }
+    __syncthreads();
+    int wbase = 0, total = 0, any = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int cnt = s_cnt[parity * 4 + w];
+      wbase += w < warp ? cnt : 0;
+      total += cnt;
+      any |= s_act[parity * 4 + w];
+    }
+    if (!any) break;  // block-uniform: no warp has a ray left
+    if (total > 0) {
+      if (miss) {
+        const int pos = wbase + __popc(bal & ((1u << lane) - 1u));
+        s_miss[pos] = make_float4(x[0], x[1], x[2], __int_as_float(warp * 32 + lane));
+      }
+      if (tid == 0 && P.miss_rec) s_mbase[parity] = (int)atomicAdd(P.miss_count, (uint32_t)total);
+      __syncthreads();
+      if (tid < total) {
+        const float4 m = s_miss[tid];
+        const float r = inr_raw_fp32<IN, H>(P.inr, sw, m.x, m.y, m.z);
+        const int slot = __float_as_int(m.w);
+        s_val[slot] = fmaf(P.inr.vscale, r, P.inr.vmin);
+        if (P.miss_rec) {
+          const uint32_t at = (uint32_t)s_mbase[parity] + (uint32_t)tid;
+          if (at < P.miss_cap) {
+            P.miss_rec[2 * at] = (uint32_t)s_pix[slot >> 5];
+            P.miss_rec[2 * at + 1] = (uint32_t)(s_k0[slot >> 5] + (slot & 31));
+          }
+        }
+      }
+      __syncthreads();
+      if (miss) v = s_val[warp * 32 + lane];
+    }
+    parity ^= 1;
+
+    // ---- 3. transfer function + front-to-back compositing (warp scan)
+    if (active) {
+      float alpha = 0.f;
+      float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (has) {
+        e = tf_lookup(s_tf, v);
+        alpha = 1.0f - expf(-e.w * len);
+      }
+      float p = 1.0f - alpha;  // inclusive prefix product of transmittances
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float q = __shfl_up_sync(kFull, p, o);
+        if (lane >= o) p *= q;
+      }
+      float excl = __shfl_up_sync(kFull, p, 1);
+      if (lane == 0) excl = 1.0f;
+      const float wgt = excl * alpha;
+      float cr = wgt * e.x, cg = wgt * e.y, cb = wgt * e.z;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        cr += __shfl_xor_sync(kFull, cr, o);
+        cg += __shfl_xor_sync(kFull, cg, o);
+        cb += __shfl_xor_sync(kFull, cb, o);
+      }
+      const float segT = __shfl_sync(kFull, p, 31);
+      Cr = fmaf(T, cr, Cr);
+      Cg = fmaf(T, cg, Cg);
+      Cb = fmaf(T, cb, Cb);
+      T *= segT;
+      k0 += 32;
+      const bool more = f_add(tn, f_mul((float)k0, cam.dt)) < tf;
+      const bool term = (k0 % P.K == 0) && T < P.eps;
+      if (!more || term) {
+        if (lane == 0) P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
+        state = 0;
+      }
+    }
+  }
+
+  // ---- per-CTA statistics
+  unsigned long long a[6] = {n_samp, n_hit, n_fb, n_miss, n_req, n_slot};
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+    for (int o = 16; o > 0; o >>= 1) a[j] += __shfl_xor_sync(kFull, a[j], o);
+  if (lane == 0) {
+    if (a[0]) atomicAdd(P.stats + ST_SAMPLES, a[0]);
+    if (a[1]) atomicAdd(P.stats + ST_HITS, a[1]);
+    if (a[2]) atomicAdd(P.stats + ST_FALLBACK, a[2]);
+    const unsigned long long misses = CACHED ? a[3] : a[0];
+    if (misses) {
+      atomicAdd(P.stats + ST_MISSES, misses);
+      atomicAdd(P.stats + ST_DIRECT, misses);
+    }
+    if (a[4]) atomicAdd(P.stats + ST_REQ, a[4]);
+    if (a[5]) atomicAdd(P.stats + ST_SLOTS, a[5]);
+  }
+}
+
+// ----------------------------------------------------------- host side
+void normalize3(const float a[3], float out[3]) {
+  float l2 = a[0] * a[0] + a[1] * a[1];
+  l2 = l2 + a[2] * a[2];
+  const float l = sqrtf(l2);
+  for (int i = 0; i < 3; ++i) out[i] = a[i] / l;
+}
+
+void cross3(const float a[3], const float b[3], float out[3]) {
+  out[0] = a[1] * b[2] - a[2] * b[1];
+  out[1] = a[2] * b[0] - a[0] * b[2];
+  out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Camera basis and marching constants in binary32 (the host side of the
+// numeric contract; compiled without FMA contraction).
+void camera_consts(const cinr_camera* cam, const cinr_march_opts* o, CamDev* c) {
+  float tmp[3];
+  for (int a = 0; a < 3; ++a) tmp[a] = cam->target[a] - cam->eye[a];
+  normalize3(tmp, c->fwd);
+  cross3(c->fwd, cam->up, tmp);
+  normalize3(tmp, c->right);
+  cross3(c->right, c->fwd, c->upv);
+  const float th = (float)tan((double)cam->fov_y_deg * (3.14159265358979323846 / 360.0));
+  const float aspect = (float)cam->width / (float)cam->height;
+  c->ax = th * aspect;
+  c->ay = th;
+  c->W = cam->width;
+  c->H = cam->height;
+  int m = o->dims[0];
+  if (o->dims[1] > m) m = o->dims[1];
+  if (o->dims[2] > m) m = o->dims[2];
+  const float mf = (float)m;
+  for (int a = 0; a < 3; ++a) {
+    c->o[a] = cam->eye[a];
+    c->e[a] = (float)o->dims[a] / mf;
+    c->h[a] = c->e[a] * 0.5f;
+    c->vol[a] = o->dims[a];
+  }
+  c->dt = cam->step_voxels / mf;
+  const float c1 = (2.0f * th) / (float)cam->height;
+  const float c2 = c1 * mf;
+  c->lodc = c2 * o->lod_scale;
+  c->lod_scale = o->lod_scale;
+  c->lod_mode = o->lod_mode;
+}
+
+uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int IN, int H, bool CACHED>
+int launch_frame(const FrameParams& P, cudaStream_t s) {
+  auto k = frame_kernel<IN, H, CACHED>;
+  const int smem = (256 + 128) * 16 + 128 * 4 + 32 * 4 + mlp_floats<IN, H>() * 4;
+  static int blocks_per_sm = 0;
+  if (!blocks_per_sm) {
+    CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, smem));
+    if (blocks_per_sm < 1) return set_error(CINR_ERR_CUDA, "frame kernel cannot be resident");
+  }
+  k<<<(unsigned)(blocks_per_sm * num_sms()), kFrameThreads, smem, s>>>(P);
+  CINR_CK(cudaGetLastError());
+  return CINR_OK;
+}
+
+template <bool CACHED>
+int launch_frame_shape(const FrameParams& P, cudaStream_t s) {
+  switch (shape_of(P.inr.IN, P.inr.H)) {
+    case Shape::S16x32: return launch_frame<16, 32, CACHED>(P, s);
+    case Shape::S32x64: return launch_frame<32, 64, CACHED>(P, s);
+    case Shape::S48x64: return launch_frame<48, 64, CACHED>(P, s);
+    default: return set_error(CINR_ERR_ARG, "unsupported shape");
+  }
+}
+
+struct RendererLayout {
+  uint32_t* counters;
+  unsigned long long* stats;
+  uint32_t* miss_rec;
+  float4* image;
+  size_t bytes;
+};
+
+RendererLayout rlayout(int W, int H, const cinr_march_opts* o, void* base) {
+  Carver c(base);
+  RendererLayout L;
+  L.counters = c.take<uint32_t>(64);
+  L.stats = c.take<unsigned long long>(ST_COUNT);
+  L.miss_rec = c.take<uint32_t>(2 * (size_t)(o->miss_record_cap > 0 ? o->miss_record_cap : 0));
+  L.image = c.take<float4>((size_t)W * H);
+  L.bytes = align_up(c.off, 256);
+  return L;
+}
+
+int check_opts(int W, int H, const cinr_march_opts* o) {
+  if (!o) return set_error(CINR_ERR_ARG, "opts is NULL");
+  if (W < 1 || H < 1 || (long)W * H > (1l << 30)) return set_error(CINR_ERR_ARG, "bad image size");
+  if (o->K < 32 || (o->K % 32) != 0) return set_error(CINR_ERR_ARG, "K must be a positive multiple of 32");
+  if (o->dims[0] < 1 || o->dims[1] < 1 || o->dims[2] < 1) return set_error(CINR_ERR_ARG, "bad dims");
+  if (o->miss_record_cap < 0 || o->miss_record_cap > (1l << 30))
+    return set_error(CINR_ERR_ARG, "bad miss_record_cap");
+  if (o->lod_mode != 0 && o->lod_mode != 1) return set_error(CINR_ERR_ARG, "bad lod_mode");
+  return CINR_OK;
+}
+
+int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_camera* cam,
+           const cinr_tf* tf, float4* out, cinr_frame_stats* stats, cudaStream_t s) {
+  if (!r || !inr || !cam || !tf) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (cam->width != r->W || cam->height != r->H)
+    return set_error(CINR_ERR_ARG, "camera is %dx%d, renderer %dx%d", cam->width, cam->height, r->W, r->H);
+  if (reinterpret_cast<uintptr_t>(out) & 15) return set_error(CINR_ERR_ARG, "image must be 16-byte aligned");
+  if (!(cam->step_voxels > 0.0f)) return set_error(CINR_ERR_ARG, "step_voxels must be > 0");
+  if (cache) {
+    for (int a = 0; a < 3; ++a)
+      if (cache->dev.vol[a] != r->o.dims[a]) return set_error(CINR_ERR_ARG, "cache dims differ from renderer dims");
+    if (cache->inr != inr) return set_error(CINR_ERR_ARG, "cache was built for another INR");
+  }
+  FrameParams P;
+  memset(&P, 0, sizeof(P));
+  camera_consts(cam, &r->o, &P.cam);
+  P.inr = inr->dev;
+  uint64_t frame;
+  if (cache) {
+    frame = ++cache->frame;
+    P.cache = cache->dev;
+  } else {
+    frame = ++r->frame;
+  }
+  P.frame = (uint32_t)frame;
+  P.Tf = (uint32_t)(1001ull * frame);
+  P.fseed = (uint32_t)splitmix64(r->o.seed ^ frame);
+  memcpy(P.tf, tf->rgba, sizeof(P.tf));
+  P.out = out;
+  P.tiles_x = (uint32_t)((r->W + 7) / 8);
+  P.n_rays = P.tiles_x * (uint32_t)((r->H + 7) / 8) * 64u;
+  P.ray_counter = r->counters;
+  P.stats = r->stats;
+  P.K = r->o.K;
+  P.eps = r->o.eps_T;
+  P.miss_rec = r->o.miss_record_cap > 0 ? r->miss_rec : nullptr;
+  P.miss_cap = (uint32_t)r->o.miss_record_cap;
+  P.miss_count = r->counters + 1;
+
+  CINR_CK(cudaMemsetAsync(r->counters, 0, 64 * 4, s));
+  CINR_CK(cudaMemsetAsync(r->stats, 0, ST_COUNT * 8, s));
+  if (cache) CINR_CK(cudaMemsetAsync(cache->dev.touched_count, 0, 4, s));
+  CINR_CK(cudaEventRecord(r->ev[0], s));
+  int e = cache ? launch_frame_shape<true>(P, s) : launch_frame_shape<false>(P, s);
+  if (e) return e;
+  CINR_CK(cudaEventRecord(r->ev[1], s));
+  if (cache) {
+    e = cinr_cache_end_frame(cache, r->stats, s);
+    if (e) return e;
+  }
+  CINR_CK(cudaEventRecord(r->ev[2], s));
+  unsigned long long h[ST_COUNT];
+  uint32_t rec = 0;
+  CINR_CK(cudaMemcpyAsync(h, r->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaMemcpyAsync(&rec, r->counters + 1, 4, cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaStreamSynchronize(s));
+  if (stats) {
+    stats->samples = h[ST_SAMPLES];
+    stats->inr_queries_direct = h[ST_DIRECT];
+    stats->inr_queries_decode = h[ST_DECODE];
+    stats->true_misses = h[ST_MISSES];
+    stats->fallback_hits = h[ST_FALLBACK];
+    stats->hits = h[ST_HITS];
+    stats->bricks_requested = h[ST_REQ];
+    stats->bricks_decoded = h[ST_DECODED];
+    stats->evictions = h[ST_EVICT];
+    stats->misses_recorded = P.miss_rec ? (rec < P.miss_cap ? rec : P.miss_cap) : 0;
+    stats->slots_touched = h[ST_SLOTS];
+    float ms0 = 0.f, ms1 = 0.f;
+    CINR_CK(cudaEventElapsedTime(&ms0, r->ev[0], r->ev[1]));
+    CINR_CK(cudaEventElapsedTime(&ms1, r->ev[1], r->ev[2]));
+    stats->ms_frame_kernel = ms0;
+    stats->ms_cache_update = ms1;
+  }
+  return CINR_OK;
+}
+
+}  // namespace
+
+extern "C" int cinr_renderer_bytes(int width, int height, const cinr_march_opts* o, size_t* bytes) {
+  int e = check_opts(width, height, o);
+  if (e) return e;
+  if (!bytes) return set_error(CINR_ERR_ARG, "bytes is NULL");
+  *bytes = rlayout(width, height, o, nullptr).bytes;
+  return CINR_OK;
+}
+
+extern "C" int cinr_create_renderer(void* dev_mem, size_t bytes, int width, int height,
+                                    const cinr_march_opts* o, cinr_renderer_t* out) {
+  int e = check_opts(width, height, o);
+  if (e) return e;
+  if (!out) return set_error(CINR_ERR_ARG, "out is NULL");
+  if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) & 255))
+    return set_error(CINR_ERR_ARG, "dev_mem must be non-NULL and 256-byte aligned");
+  RendererLayout L = rlayout(width, height, o, dev_mem);
+  if (bytes < L.bytes) return set_error(CINR_ERR_NOMEM, "renderer needs %zu bytes, got %zu", L.bytes, bytes);
+  cinr_renderer_s* r = new cinr_renderer_s();
+  r->W = width;
+  r->H = height;
+  r->o = *o;
+  r->counters = L.counters;
+  r->stats = L.stats;
+  r->miss_rec = L.miss_rec;
+  r->image = L.image;
+  r->frame = 0;
+  cudaGetDevice(&r->device);
+  for (int i = 0; i < 3; ++i) {
+    cudaError_t ce = cudaEventCreate(&r->ev[i]);
+    if (ce != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaEventDestroy(r->ev[j]);
+      delete r;
+      return cuda_error(ce, "cudaEventCreate");
+    }
+  }
+  *out = r;
+  return CINR_OK;
+}
+
+extern "C" int cinr_destroy_renderer(cinr_renderer_t r) {
+  if (r)
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(r->ev[i]);
+  delete r;
+  return CINR_OK;
+}
+
+extern "C" int cinr_render_frame(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr,
+                                 const cinr_camera* cam, const cinr_tf* tf, float* out_rgba_dev,
+                                 cinr_frame_stats* stats, cinr_stream_t stream) {
+  if (!out_rgba_dev) return set_error(CINR_ERR_ARG, "out_rgba_dev is NULL");
+  return render(r, cache, inr, cam, tf, reinterpret_cast<float4*>(out_rgba_dev), stats,
+                static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int cinr_render_frame_host(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr,
+                                      const cinr_camera* cam, const cinr_tf* tf, float* out_rgba_host,
+                                      cinr_frame_stats* stats, cinr_stream_t stream) {
+  if (!r || !out_rgba_host) return set_error(CINR_ERR_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cinr_frame_stats st;
+  int e = render(r, cache, inr, cam, tf, r->image, &st, s);
+  if (e) return e;
+  CINR_CK(cudaMemcpyAsync(out_rgba_host, r->image, (size_t)r->W * r->H * 16, cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaStreamSynchronize(s));
+  if (stats) *stats = st;
+  return CINR_OK;
+}
+
+extern "C" int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap, size_t* count,
+                               cinr_stream_t stream) {
+  if (!obj || !count) return set_error(CINR_ERR_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const void* src = nullptr;
+  size_t n = 0, esz = 4;
+  if (what == CINR_DUMP_MISSES) {
+    cinr_renderer_s* r = static_cast<cinr_renderer_s*>(obj);
+    uint32_t rec = 0;
+    CINR_CK(cudaMemcpyAsync(&rec, r->counters + 1, 4, cudaMemcpyDeviceToHost, s));
+    CINR_CK(cudaStreamSynchronize(s));
+    size_t capr = (size_t)(r->o.miss_record_cap > 0 ? r->o.miss_record_cap : 0);
+    n = 2 * (rec < capr ? rec : capr);
+    src = r->miss_rec;
+  } else {
+    cinr_cache_s* c = static_cast<cinr_cache_s*>(obj);
+    uint32_t cnt = 0;
+    switch (what) {
+      case CINR_DUMP_PAGE_TABLE: src = c->dev.pt; n = (size_t)c->n_bricks; break;
+      case CINR_DUMP_STAMPS: src = c->dev.stamp; n = (size_t)c->n_slots; break;
+      case CINR_DUMP_OWNERS: src = c->dev.owner; n = (size_t)c->n_slots; break;
+      case CINR_DUMP_RANK: src = c->dev.rank; n = (size_t)c->n_bricks; break;
+      case CINR_DUMP_PINNED: src = c->dev.pinned; n = (size_t)c->n_slots; break;
+      case CINR_DUMP_REQUESTS:
+        CINR_CK(cudaMemcpyAsync(&cnt, c->req_n, 4, cudaMemcpyDeviceToHost, s));
+        CINR_CK(cudaStreamSynchronize(s));
+        src = c->req_sorted;
+        n = cnt;
+        break;
+      case CINR_DUMP_VICTIMS:
+        CINR_CK(cudaMemcpyAsync(&cnt, c->decode_n, 4, cudaMemcpyDeviceToHost, s));
+        CINR_CK(cudaStreamSynchronize(s));
+        src = c->vic_sorted;
+        n = cnt;
+        break;
+      case CINR_DUMP_POOL:
+        src = c->dev.pool;
+        n = (size_t)c->n_slots * c->dev.S * c->dev.S * c->dev.S;
+        esz = c->dev.pool_prec == CINR_PREC_FP16 ? 2 : 4;
+        break;
+      default: return set_error(CINR_ERR_ARG, "unknown dump %d", what);
+    }
+  }
+  *count = n;
+  size_t m = n < cap ? n : cap;
+  if (host_out && m > 0) {
+    CINR_CK(cudaMemcpyAsync(host_out, src, m * esz, cudaMemcpyDeviceToHost, s));
+    CINR_CK(cudaStreamSynchronize(s));
+  }
+  return CINR_OK;
+}

@@ -1,0 +1,70 @@
+"""CPU checks of the C-ABI library: it builds, loads without a GPU, exports
+every function include/cinr.h declares, and its host-only size queries and
+argument checks behave (no device compute is called here)."""
+import ctypes as C
+
+import pytest
+
+from paper_2504_18001_gb300 import cinr, synthetic as S
+
+
+@pytest.fixture(scope="module")
+def L():
+    return cinr.lib()
+
+
+def test_every_header_symbol_is_exported(L):
+    names = cinr.header_symbols()
+    assert len(names) >= 19
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert L.cinr_version() >= 100
+
+
+def test_inr_bytes_and_shape_checks(L):
+    p = cinr.make_inr_params(S.INR_512)
+    n = C.c_size_t()
+    assert L.cinr_inr_bytes(C.byref(p), C.byref(n)) == 0
+    # table 16 * 2^19 * 2 floats, weights, fp16 copy, scratch
+    assert n.value >= 16 * (1 << 19) * 8 + S.INR_512.mlp_params * 6
+    bad = cinr.make_inr_params(S.InrConfig(levels=5, feats=2, log2_table=10, base_res=4,
+                                           growth=1.5, hidden=32))
+    assert L.cinr_inr_bytes(C.byref(bad), C.byref(n)) == -1
+    assert "unsupported MLP shape" in cinr.last_error()
+
+
+def test_cache_slot_arithmetic_matches_paper_and_config(L):
+    o = cinr.cinr_cache_opts(8, 4, 40, 1, 1, 0)
+    dims = (C.c_int * 3)(512, 512, 512)
+    nb, ns = C.c_size_t(), C.c_long()
+    assert L.cinr_cache_bytes(dims, 1 << 30, C.byref(o), C.byref(nb), C.byref(ns)) == 0
+    assert ns.value == (1 << 30) // (10 ** 3 * 4) == 268435
+    # Sec. 6.3: a 30^3-brick cache of 40^3 stored FP32 voxels is 1.728e9
+    # voxels, just under 7 GB (interior 38 + 2 apron = 40 stored per edge)
+    o2 = cinr.cinr_cache_opts(38, 6, 40, 1, 1, 0)
+    dims2 = (C.c_int * 3)(4096, 4096, 4096)
+    pool = 30 ** 3 * 40 ** 3 * 4
+    assert pool == 6_912_000_000
+    assert L.cinr_cache_bytes(dims2, pool, C.byref(o2), C.byref(nb), C.byref(ns)) == 0
+    assert ns.value == 27000
+    # brick loading buffer of the paper: 40 requests of 40^3 FP32 = 10.24 MB
+    assert 40 * 40 ** 3 * 4 == 10_240_000
+
+
+def test_renderer_option_checks(L):
+    o = cinr.cinr_march_opts((C.c_int * 3)(64, 64, 64), 48, 1e-3, 0, 1.0, 0, 0)
+    n = C.c_size_t()
+    assert L.cinr_renderer_bytes(128, 128, C.byref(o), C.byref(n)) == -1
+    assert "multiple of 32" in cinr.last_error()
+    o.K = 64
+    assert L.cinr_renderer_bytes(128, 128, C.byref(o), C.byref(n)) == 0
+    assert n.value >= 128 * 128 * 16
+
+
+def test_cache_option_checks(L):
+    dims = (C.c_int * 3)(64, 64, 64)
+    nb, ns = C.c_size_t(), C.c_long()
+    o = cinr.cinr_cache_opts(8, 13, 40, 1, 1, 0)  # too many LoDs
+    assert L.cinr_cache_bytes(dims, 1 << 20, C.byref(o), C.byref(nb), C.byref(ns)) == -1
+    o = cinr.cinr_cache_opts(8, 3, 4096, 1, 1, 0)  # n_req above the limit
+    assert L.cinr_cache_bytes(dims, 1 << 20, C.byref(o), C.byref(nb), C.byref(ns)) == -1

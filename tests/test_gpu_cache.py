@@ -1,0 +1,104 @@
+"""GPU parity of the cached render: page tables, LRU stamps, owners, ranks,
+request and victim lists and miss lists bit-exact against the oracle after
+every frame of multi-frame orbits; pixels within 2e-3."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_18001_gb300 import synthetic as S
+
+from _scenes import gpu_inr, ocam, oracle_inr, scene, sorted_pairs
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_req=40, ranking=1,
+         preload=1, lod_scale=1.0, lod_mode=0, storage="fp32", K=32, eps=0.0, check_pixels=2e-3,
+         cam_fn=None):
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.INR_64
+    table, w = scene(cfg)
+    inr = gpu_inr(cfg, table, w, vol=vol)
+    p = oracle_inr(cfg, table, w, vol=vol)
+    S3 = (brick + 2) ** 3
+    cache = cinr.Cache(inr, vol, pool_bytes=slots * S3 * (2 if storage == "fp16" else 4),
+                       brick=brick, levels=levels, n_req=n_req, ranking=ranking, preload=preload,
+                       storage=storage)
+    assert cache.n_slots == slots
+    mo = O.march_opts(K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11)
+    oc = O.Cache(p, table, w, vol, brick, levels, slots, mo, n_req=n_req, ranking=ranking,
+                 preload=preload)
+    r = cinr.Renderer(W, H, vol, K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
+                      miss_record_cap=W * H * 4000)
+    tf = S.tf_ramps(2)
+    worst = 0.0
+    history = []
+    for f in range(frames):
+        cam = cam_fn(f, W, H) if cam_fn else S.orbit_camera(4 * f, W, H, distance=1.6 + 0.05 * f)
+        img, st = r.render(inr, cam, tf, cache=cache)
+        ref, rst = oc.render(ocam(cam), tf.astype(np.float64))
+        for k in ("samples", "hits", "fallback_hits", "true_misses", "bricks_requested",
+                  "bricks_decoded", "evictions", "inr_queries_direct", "inr_queries_decode"):
+            assert st[k] == rst[k], (f, k, st[k], rst[k])
+        for g, o in ((cinr.DUMP_PAGE_TABLE, O.DUMP_PT), (cinr.DUMP_STAMPS, O.DUMP_STAMP),
+                     (cinr.DUMP_OWNERS, O.DUMP_OWNER), (cinr.DUMP_RANK, O.DUMP_RANK),
+                     (cinr.DUMP_REQUESTS, O.DUMP_REQ), (cinr.DUMP_VICTIMS, O.DUMP_VICT),
+                     (cinr.DUMP_PINNED, O.DUMP_PINNED)):
+            a, b = cache.dump(g), oc.dump(o)
+            assert np.array_equal(a, b), (f, g, np.nonzero(a != b)[0][:10] if a.shape == b.shape else (a.shape, b.shape))
+        gm = sorted_pairs(r.misses())
+        om = sorted_pairs(oc.dump(O.DUMP_MISS))
+        assert np.array_equal(gm, om), (f, len(gm), len(om))
+        err = float(np.abs(img.cpu().numpy() - ref).max())
+        worst = max(worst, err)
+        if check_pixels is not None:
+            assert err < check_pixels, (f, err)
+        history.append(st)
+    return cache, oc, history, worst
+
+
+def test_cached_orbit_state_bit_exact_ranked():
+    cache, oc, hist, worst = _run(6)
+    assert sum(h["bricks_decoded"] for h in hist) > 0
+    assert sum(h["evictions"] for h in hist) > 0  # the small pool forces replacement
+
+
+def test_cached_orbit_ranking_off():
+    _run(4, ranking=0)
+
+
+def test_cached_no_preload_true_misses_and_miss_lists():
+    cache, oc, hist, worst = _run(4, preload=0, slots=400, n_req=100)
+    assert hist[0]["true_misses"] == hist[0]["samples"] > 0
+    assert hist[-1]["true_misses"] < hist[0]["true_misses"]
+
+
+def test_cached_distance_lod_mode_and_ragged_volume():
+    _run(4, vol=(48, 40, 72), W=37, H=29, lod_mode=1, lod_scale=1.3, levels=4, slots=120)
+
+
+def test_cached_fp16_storage_error():
+    from paper_2504_18001_gb300 import cinr  # noqa: F401
+    cache, oc, hist, worst = _run(3, storage="fp16", check_pixels=None)
+    assert worst < 2e-2, worst
+
+
+def test_decoded_bricks_equal_oracle_bricks():
+    from paper_2504_18001_gb300 import cinr
+    cache, oc, hist, worst = _run(3, slots=300, n_req=80)
+    pool = cache.dump(cinr.DUMP_POOL).reshape(cache.n_slots, -1)
+    own = cache.dump(cinr.DUMP_OWNERS)
+    used = np.nonzero(own != 0xFFFFFFFF)[0]
+    assert len(used) > 50
+    for s in used[:: max(1, len(used) // 40)]:
+        assert np.abs(pool[s] - oc.slot_values(int(s))).max() < 1e-4
+
+
+def test_fully_resident_cache_is_trilinear_of_voxel_centres():
+    # every brick of LoD 0 resident (lod_scale 0, distance mode -> LoD 0),
+    # then the image must match the oracle, whose cached render equals the
+    # brute-force whole-grid trilinear reconstruction (oracle pin).
+    cache, oc, hist, worst = _run(3, vol=(32, 32, 32), slots=100, n_req=100, lod_mode=1,
+                                  lod_scale=0.0, levels=2)
+    assert hist[-1]["bricks_requested"] == 0
+    assert hist[-1]["hits"] == hist[-1]["samples"]
