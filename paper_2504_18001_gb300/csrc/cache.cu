@@ -12,7 +12,7 @@ using namespace cinr;
 namespace {
 
 constexpr int kSelThreads = 256;
-constexpr int kMaxReq = 1024;
+constexpr int kMaxReq = 8192;  // max requests (and victims) per frame
 
 int bits_for(unsigned long long v) {
   int b = 0;
@@ -293,12 +293,13 @@ __global__ void __launch_bounds__(kSelThreads) sel_gather(KF kf, uint32_t n, Sel
   }
 }
 
-// Orders the gathered (at most kMaxReq) entries by key; writes the count.
-__global__ void __launch_bounds__(kMaxReq) sel_sort(SelState* st, const unsigned long long* keys,
-                                                    const uint32_t* vals, uint32_t* sorted,
-                                                    uint32_t* n_out) {
-  const uint32_t n = st->none ? 0u : (st->count < kMaxReq ? st->count : kMaxReq);
-  const uint32_t t = threadIdx.x;
+// Orders the gathered (at most kMaxReq, unique) keys: each entry's rank is
+// the number of smaller keys; writes the count.
+__global__ void __launch_bounds__(256) sel_sort(SelState* st, const unsigned long long* keys,
+                                                const uint32_t* vals, uint32_t* sorted,
+                                                uint32_t* n_out) {
+  const uint32_t n = st->none ? 0u : (st->count < (uint32_t)kMaxReq ? st->count : (uint32_t)kMaxReq);
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) {
     const unsigned long long k = keys[t];
     uint32_t r = 0;
@@ -372,7 +373,7 @@ int radix_select(const KF& kf, uint32_t n, int key_bits, uint32_t want, SelState
     sel_pick<<<1, 1024, 0, s>>>(st, shift, p, want);
   }
   sel_gather<KF><<<blocks, kSelThreads, 0, s>>>(kf, n, st, keys, vals);
-  sel_sort<<<1, kMaxReq, 0, s>>>(st, keys, vals, sorted, n_out);
+  sel_sort<<<(want + 255) / 256, 256, 0, s>>>(st, keys, vals, sorted, n_out);
   CINR_CK(cudaGetLastError());
   return CINR_OK;
 }
