@@ -66,5 +66,5 @@ def test_cache_option_checks(L):
     nb, ns = C.c_size_t(), C.c_long()
     o = cinr.cinr_cache_opts(8, 13, 40, 1, 1, 0)  # too many LoDs
     assert L.cinr_cache_bytes(dims, 1 << 20, C.byref(o), C.byref(nb), C.byref(ns)) == -1
-    o = cinr.cinr_cache_opts(8, 3, 4096, 1, 1, 0)  # n_req above the limit
+    o = cinr.cinr_cache_opts(8, 3, 10000, 1, 1, 0)  # n_req above the limit (8192)
     assert L.cinr_cache_bytes(dims, 1 << 20, C.byref(o), C.byref(nb), C.byref(ns)) == -1
