@@ -251,6 +251,29 @@ int cinr_render_frame_host(cinr_renderer_t r, cinr_cache_t cache,
 
 int cinr_destroy_renderer(cinr_renderer_t r);
 
+/* Allocation-free uncached render.  The paper has no counterpart: this is a
+ * convenience for callers that cannot allocate device memory -- a real-time
+ * render loop in which an allocation would stall or fail, code running under
+ * a policy that forbids new device allocations, or a host-side plugin that
+ * owns no device buffer.  It renders the same uncached frame as
+ * cinr_render_frame with cache == NULL, but the frame's working set (ray
+ * counter, statistics and the device image) lives in one array of about
+ * 4 MiB that the library keeps in device memory for as long as it is loaded,
+ * on every GPU that loads it.  The image is copied to out_rgba_host
+ * (width*height*4 floats) and the call synchronises `stream`.
+ * Limits: width*height <= 262144 (512 x 512) and o->miss_record_cap == 0;
+ * larger requests return CINR_ERR_ARG with a message naming the limit.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call uses the same array: calls that overlap on the GPU (different
+ * streams or threads) race and must be serialised by the caller.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ * Only stats->samples, inr_queries_direct and true_misses are filled. */
+int cinr_render_frame_noalloc(cinr_inr_t inr, const cinr_camera* cam,
+                              const cinr_tf* tf, const cinr_march_opts* o,
+                              float* out_rgba_host, cinr_frame_stats* stats,
+                              cinr_stream_t stream);
+
 /* ------------------------------------------------------------- debug --- */
 #define CINR_DUMP_PAGE_TABLE 0 /* u32 per brick: 0x80000000|slot or 0  */
 #define CINR_DUMP_STAMPS 1     /* u32 per slot: last frame it was used */

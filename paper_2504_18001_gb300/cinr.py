@@ -92,6 +92,8 @@ _SIGS = {
     "cinr_render_frame_host": [_vp, _vp, _vp, _P(cinr_camera), _P(cinr_tf), _vp,
                                _P(cinr_frame_stats), _vp],
     "cinr_destroy_renderer": [_vp],
+    "cinr_render_frame_noalloc": [_vp, _P(cinr_camera), _P(cinr_tf), _P(cinr_march_opts), _vp,
+                                  _P(cinr_frame_stats), _vp],
     "cinr_debug_dump": [_vp, C.c_int, _vp, C.c_size_t, _P(C.c_size_t), _vp],
     "cinr_cache_level_info": [_vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_long)],
 }

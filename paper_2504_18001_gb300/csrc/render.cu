@@ -18,6 +18,7 @@
 // Rays are handed out from an atomic counter in 8x8 pixel tiles.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "cinr_internal.cuh"
 
@@ -646,6 +647,108 @@ extern "C" int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap, 
   if (host_out && m > 0) {
     CINR_CK(cudaMemcpyAsync(host_out, src, m * esz, cudaMemcpyDeviceToHost, s));
     CINR_CK(cudaStreamSynchronize(s));
+  }
+  return CINR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free uncached render.
+//
+// For callers that must not allocate device memory (a real-time render loop
+// where an allocation would stall or fail, code running under a memory
+// policy that forbids new device allocations, a host-only plugin that owns no
+// device buffer): the frame's working set (ray counter, statistics and the
+// device copy of the image) lives in one file-scope device array instead of
+// a caller-provided renderer buffer.  Every GPU that loads the library holds
+// this array (kNoAllocBytes, about 4 MiB) until the process exits.
+namespace {
+
+constexpr int kNoAllocMaxPixels = 512 * 512;
+constexpr size_t kNoAllocHeader = 512;  // counters (256 B) + statistics (256 B)
+constexpr size_t kNoAllocBytes = kNoAllocHeader + (size_t)kNoAllocMaxPixels * sizeof(float4);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current (in host code the array's name is only
+// a host-side stand-in, not a device address).
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  CINR_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return set_error(CINR_ERR_UNSUPPORTED, "device %d out of the supported range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return CINR_OK;
+}
+
+}  // namespace
+
+extern "C" int cinr_render_frame_noalloc(cinr_inr_t inr, const cinr_camera* cam, const cinr_tf* tf,
+                                         const cinr_march_opts* o, float* out_rgba_host,
+                                         cinr_frame_stats* stats, cinr_stream_t stream) {
+  if (!inr || !cam || !tf || !o || !out_rgba_host) return set_error(CINR_ERR_ARG, "NULL argument");
+  int e = check_opts(cam->width, cam->height, o);
+  if (e) return e;
+  if ((long)cam->width * cam->height > kNoAllocMaxPixels)
+    return set_error(CINR_ERR_ARG,
+                     "image of %d x %d pixels exceeds the allocation-free limit of %d pixels",
+                     cam->width, cam->height, kNoAllocMaxPixels);
+  if (o->miss_record_cap != 0)
+    return set_error(CINR_ERR_ARG, "the allocation-free render keeps no miss record (cap must be 0)");
+  if (!(cam->step_voxels > 0.0f)) return set_error(CINR_ERR_ARG, "step_voxels must be > 0");
+  unsigned char* scratch = nullptr;
+  e = noalloc_scratch(&scratch);
+  if (e) return e;
+  uint32_t* counters = reinterpret_cast<uint32_t*>(scratch);
+  unsigned long long* st_dev = reinterpret_cast<unsigned long long*>(scratch + 256);
+  float4* image = reinterpret_cast<float4*>(scratch + kNoAllocHeader);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  FrameParams P;
+  memset(&P, 0, sizeof(P));
+  camera_consts(cam, o, &P.cam);
+  P.inr = inr->dev;
+  P.frame = 1;
+  P.Tf = 1001u;
+  P.fseed = (uint32_t)splitmix64(o->seed ^ 1ull);
+  memcpy(P.tf, tf->rgba, sizeof(P.tf));
+  P.out = image;
+  P.tiles_x = (uint32_t)((cam->width + 7) / 8);
+  P.n_rays = P.tiles_x * (uint32_t)((cam->height + 7) / 8) * 64u;
+  P.ray_counter = counters;
+  P.stats = st_dev;
+  P.K = o->K;
+  P.eps = o->eps_T;
+  P.miss_rec = nullptr;
+  P.miss_cap = 0;
+  P.miss_count = counters + 1;
+
+  // The array keeps the previous call's contents: counters and statistics
+  // must start at zero.
+  CINR_CK(cudaMemsetAsync(scratch, 0, kNoAllocHeader, s));
+  e = launch_frame_shape<false>(P, s);
+  if (e) return e;
+  unsigned long long h[ST_COUNT];
+  CINR_CK(cudaMemcpyAsync(out_rgba_host, image, (size_t)cam->width * cam->height * sizeof(float4),
+                          cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaMemcpyAsync(h, st_dev, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaStreamSynchronize(s));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->samples = h[ST_SAMPLES];
+    stats->inr_queries_direct = h[ST_DIRECT];
+    stats->true_misses = h[ST_MISSES];
   }
   return CINR_OK;
 }
