@@ -274,6 +274,53 @@ int cinr_render_frame_noalloc(cinr_inr_t inr, const cinr_camera* cam,
                               float* out_rgba_host, cinr_frame_stats* stats,
                               cinr_stream_t stream);
 
+/* ---------------------------------------------------------- training --- */
+
+/* Training options (Sec. 4.1): each step draws `batch` random coordinates
+ * in [0,1)^3 from a counter-based generator (coordinate c of element j of
+ * step s is the top 24 bits of SplitMix64(seed + 3*((s-1)*batch + j) + c),
+ * times 2^-24), looks their ground truth up by trilinear interpolation of an
+ * explicit field normalised to [0,1], and takes one Adam step (Kingma & Ba,
+ * bias-corrected) on the MSE of the raw network output. */
+typedef struct {
+  long batch;
+  float lr, beta1, beta2, eps;
+  uint64_t seed;
+} cinr_train_opts;
+
+/* Device bytes of a trainer (Adam moments, gradients and per-batch
+ * activations) for this INR.  The INR's table must be FP32. */
+int cinr_trainer_bytes(cinr_inr_t inr, const cinr_train_opts* o,
+                       size_t* bytes);
+
+/* Creates a trainer in dev_mem; it updates the INR's FP32 table and weights
+ * in place (and refreshes the INR's half-precision weight copy). */
+int cinr_create_trainer(cinr_inr_t inr, const cinr_train_opts* o,
+                        void* dev_mem, size_t bytes, cinr_stream_t stream,
+                        cinr_trainer_t* out);
+
+/* One training step (Sec. 4.1) on field_dev (dims[0]*dims[1]*dims[2]
+ * floats, x fastest, values in [0,1], sampled at voxel centres).  When
+ * loss_dev is not NULL it receives the step's mean squared error. */
+int cinr_train_step(cinr_trainer_t t, const float* field_dev,
+                    const int dims[3], float* loss_dev, cinr_stream_t stream);
+
+/* Gradient of the mean squared error (1/n) sum (y_i - target_i)^2 of the
+ * raw network output at n given points (no parameter update): g_table_dev
+ * (levels * 2^log2_table * 2 floats) and g_mlp_dev (weight count floats)
+ * are overwritten; loss_dev (nullable) receives the loss.  n <= batch. */
+int cinr_inr_loss_grad(cinr_trainer_t t, const float* xyz_dev,
+                       const float* target_dev, long n, float* g_table_dev,
+                       float* g_mlp_dev, float* loss_dev, cinr_stream_t stream);
+
+int cinr_destroy_trainer(cinr_trainer_t t);
+
+/* Copies the INR's FP32 parameters to host memory (the same layouts as
+ * cinr_create_inr takes): a trained INR saved this way can be re-created,
+ * e.g. with half-precision tables.  Synchronises `stream`. */
+int cinr_inr_export(cinr_inr_t inr, float* host_table, float* host_mlp,
+                    cinr_stream_t stream);
+
 /* ------------------------------------------------------------- debug --- */
 #define CINR_DUMP_PAGE_TABLE 0 /* u32 per brick: 0x80000000|slot or 0  */
 #define CINR_DUMP_STAMPS 1     /* u32 per slot: last frame it was used */

@@ -94,6 +94,12 @@ _SIGS = {
     "cinr_destroy_renderer": [_vp],
     "cinr_render_frame_noalloc": [_vp, _P(cinr_camera), _P(cinr_tf), _P(cinr_march_opts), _vp,
                                   _P(cinr_frame_stats), _vp],
+    "cinr_trainer_bytes": [_vp, _vp, _P(C.c_size_t)],
+    "cinr_create_trainer": [_vp, _vp, _vp, C.c_size_t, _vp, _P(_vp)],
+    "cinr_train_step": [_vp, _vp, _P(C.c_int), _vp, _vp],
+    "cinr_inr_loss_grad": [_vp, _vp, _vp, C.c_long, _vp, _vp, _vp, _vp],
+    "cinr_destroy_trainer": [_vp],
+    "cinr_inr_export": [_vp, _vp, _vp, _vp],
     "cinr_debug_dump": [_vp, C.c_int, _vp, C.c_size_t, _P(C.c_size_t), _vp],
     "cinr_cache_level_info": [_vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_long)],
 }
@@ -283,6 +289,73 @@ def debug_dump(handle, what, stream=None, pool_half=False):
         check(L.cinr_debug_dump(handle, what, C.c_void_p(out.ctypes.data), n.value, C.byref(n), s),
               "cinr_debug_dump")
     return out
+
+
+class cinr_train_opts(C.Structure):
+    _fields_ = [("batch", C.c_long), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64)]
+
+
+def inr_export(inr: Inr, stream=None):
+    """(table, mlp) FP32 host copies of a trained (FP32-table) INR."""
+    cfg = inr.params
+    table = np.zeros(cfg.levels * (1 << cfg.log2_table) * cfg.feats, np.float32)
+    IN, H = cfg.levels * cfg.feats, cfg.hidden
+    mlp = np.zeros(H * IN + H * H + H, np.float32)
+    check(lib().cinr_inr_export(inr.h, C.c_void_p(table.ctypes.data), C.c_void_p(mlp.ctypes.data),
+                                _stream(stream)), "cinr_inr_export")
+    return table, mlp
+
+
+class Trainer:
+    """INR training on an explicit field (Sec. 4.1): Adam steps on batches of
+    counter-based random coordinates; updates the INR in place."""
+
+    def __init__(self, inr: Inr, batch=1 << 18, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15, seed=0,
+                 device="cuda", stream=None):
+        import torch
+        L = lib()
+        self.opts = cinr_train_opts(int(batch), float(lr), float(beta1), float(beta2), float(eps),
+                                    int(seed))
+        nbytes = C.c_size_t()
+        check(L.cinr_trainer_bytes(inr.h, C.byref(self.opts), C.byref(nbytes)), "cinr_trainer_bytes")
+        self.mem = _dev_buffer(nbytes.value, device)
+        h = C.c_void_p()
+        check(L.cinr_create_trainer(inr.h, C.byref(self.opts), C.c_void_p(self.mem.data_ptr()),
+                                    nbytes.value, _stream(stream), C.byref(h)), "cinr_create_trainer")
+        self.h = h
+        self.inr = inr
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+
+    def step(self, field, stream=None):
+        """One step on field (torch float32 [z, y, x] on the device)."""
+        dims = (C.c_int * 3)(field.shape[2], field.shape[1], field.shape[0])
+        check(lib().cinr_train_step(self.h, C.c_void_p(field.data_ptr()), dims,
+                                    C.c_void_p(self.loss.data_ptr()), _stream(stream)),
+              "cinr_train_step")
+        return self.loss
+
+    def loss_grad(self, xyz, target, stream=None):
+        import torch
+        p = self.inr.params
+        gt = torch.empty(p.levels * (1 << p.log2_table) * p.feats, dtype=torch.float32,
+                         device=xyz.device)
+        IN, H = p.levels * p.feats, p.hidden
+        gw = torch.empty(H * IN + H * H + H, dtype=torch.float32, device=xyz.device)
+        check(lib().cinr_inr_loss_grad(self.h, C.c_void_p(xyz.data_ptr()),
+                                       C.c_void_p(target.data_ptr()), xyz.shape[0],
+                                       C.c_void_p(gt.data_ptr()), C.c_void_p(gw.data_ptr()),
+                                       C.c_void_p(self.loss.data_ptr()), _stream(stream)),
+              "cinr_inr_loss_grad")
+        return self.loss, gt, gw
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().cinr_destroy_trainer(self.h)
+                self.h = None
+        except Exception:
+            pass
 
 
 class Renderer:

@@ -341,6 +341,7 @@ struct cinr_inr_s {
   void* mem;
   size_t bytes;
   float* scratch;  // small device scratch for reductions
+  uint16_t* w16;   // half-precision (FP16 or BF16) copy of the MLP weights
   int device;
 };
 

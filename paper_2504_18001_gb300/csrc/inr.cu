@@ -107,6 +107,7 @@ extern "C" int cinr_create_inr(const cinr_inr_params* p, void* dev_mem, size_t b
   h->mem = dev_mem;
   h->bytes = bytes;
   h->scratch = L.scratch;
+  h->w16 = L.w16;
   CINR_CK(cudaGetDevice(&h->device));
   InrDev& d = h->dev;
   d.table = L.table;

@@ -1,0 +1,487 @@
+// INR training (Sec. 4.1): random-coordinate batches with ground truth from
+// an explicit field, MSE on the normalised value, back-propagation through
+// the MLP and the hash-grid interpolation (scatter-add of table gradients),
+// and Adam on the FP32 master parameters.
+//
+// Per step:
+//   fwd_bwd_kernel   one thread per sample: coordinates (counter-based
+//                    SplitMix64), trilinear ground truth, encode, MLP
+//                    forward, loss, MLP backward to the feature gradient,
+//                    atomic scatter-add into the table gradient; the
+//                    activations the weight gradients need are stored
+//                    structure-of-arrays (feature-major) for the next kernel;
+//   outer_kernel     weight gradients dW = sum_s a_s b_s^T over the batch,
+//                    split over blocks (partials), then reduce_kernel;
+//   adam_kernel      bias-corrected Adam over table and weights, and the
+//                    half-precision weight copy refreshed.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cinr_internal.cuh"
+
+using namespace cinr;
+
+struct cinr_trainer_s {
+  cinr_inr_s* inr;
+  cinr_train_opts o;
+  long n_table, n_w;  // parameter counts
+  float *m_t, *v_t, *g_t, *m_w, *v_w, *g_w;
+  float* act;         // (IN + 4H + 1) x batch, feature-major
+  float* partial;     // per-block weight-gradient partials
+  float* loss;        // device scalar
+  long step;
+  int n_part;         // blocks of the outer-product reduction
+};
+
+namespace {
+
+constexpr int kChunk = 2048;     // samples per block in the weight-gradient reduction
+constexpr int kFwdThreads = 128;
+
+__device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Trilinear ground truth of a field stored at voxel centres (clamp-to-edge).
+__device__ __forceinline__ float field_trilinear(const float* __restrict__ f, int3 d, float x, float y,
+                                                 float z) {
+  const float p[3] = {x, y, z};
+  const int dd[3] = {d.x, d.y, d.z};
+  int i0[3], i1[3];
+  float w[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float q = f_sub(f_mul(clamp01(p[a]), (float)dd[a]), 0.5f);
+    q = fminf(fmaxf(q, 0.0f), (float)(dd[a] - 1));
+    i0[a] = (int)floorf(q);
+    w[a] = f_sub(q, (float)i0[a]);
+    i1[a] = i0[a] + 1 > dd[a] - 1 ? dd[a] - 1 : i0[a] + 1;
+  }
+  float v = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int ix = (c & 1) ? i1[0] : i0[0], iy = (c & 2) ? i1[1] : i0[1], iz = (c & 4) ? i1[2] : i0[2];
+    const float wc = ((c & 1) ? w[0] : 1.0f - w[0]) * ((c & 2) ? w[1] : 1.0f - w[1]) *
+                     ((c & 4) ? w[2] : 1.0f - w[2]);
+    v = fmaf(wc, __ldg(f + ((size_t)iz * d.y + iy) * d.x + ix), v);
+  }
+  return v;
+}
+
+template <int IN, int H>
+__global__ void __launch_bounds__(kFwdThreads) fwd_bwd_kernel(
+    InrDev q, long n, const float* __restrict__ xyz_in, const float* __restrict__ tgt_in,
+    const float* __restrict__ field, int3 dims, uint64_t seed, uint64_t first, float* __restrict__ act,
+    float* __restrict__ g_table, float* __restrict__ loss) {
+  extern __shared__ float4 smem4[];
+  float* sw = reinterpret_cast<float*>(smem4);
+  load_weights(sw, q.w, mlp_floats<IN, H>());
+  __syncthreads();
+  const float* W1 = sw;
+  const float* W2 = sw + IN * H;
+  const float* W3 = W2 + H * H;
+  const long s = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  float r2 = 0.0f;
+  if (s < n) {
+    float x, y, z;
+    if (xyz_in) {
+      x = xyz_in[3 * s];
+      y = xyz_in[3 * s + 1];
+      z = xyz_in[3 * s + 2];
+    } else {
+      const uint64_t c0 = 3ull * (first + (uint64_t)s);
+      x = (float)(splitmix64_dev(seed + c0) >> 40) * (1.0f / 16777216.0f);
+      y = (float)(splitmix64_dev(seed + c0 + 1) >> 40) * (1.0f / 16777216.0f);
+      z = (float)(splitmix64_dev(seed + c0 + 2) >> 40) * (1.0f / 16777216.0f);
+    }
+    x = clamp01(x);
+    y = clamp01(y);
+    z = clamp01(z);
+    const float t = tgt_in ? tgt_in[s] : field_trilinear(field, dims, x, y, z);
+    float* a_feat = act;
+    float* a_h1 = act + (size_t)IN * n;
+    float* a_h2 = a_h1 + (size_t)H * n;
+    float* a_dh1 = a_h2 + (size_t)H * n;
+    float* a_dh2 = a_dh1 + (size_t)H * n;
+    float* a_dy = a_dh2 + (size_t)H * n;
+
+    // forward
+    float h1[H];
+    uint64_t m1 = 0ull, m2 = 0ull;
+    {
+      float feat[IN];
+      encode_point<IN / 2>(q, x, y, z, feat);
+#pragma unroll
+      for (int k = 0; k < IN; ++k) a_feat[(size_t)k * n + s] = feat[k];
+#pragma unroll
+      for (int o = 0; o < H; ++o) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < IN; ++k) acc = fmaf(W1[o * IN + k], feat[k], acc);
+        h1[o] = fmaxf(acc, 0.0f);
+        if (acc > 0.0f) m1 |= 1ull << o;
+        a_h1[(size_t)o * n + s] = h1[o];
+      }
+    }
+    float yv = 0.0f;
+#pragma unroll 4
+    for (int o = 0; o < H; ++o) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < H; ++k) acc = fmaf(W2[o * H + k], h1[k], acc);
+      const float h2 = fmaxf(acc, 0.0f);
+      if (acc > 0.0f) m2 |= 1ull << o;
+      a_h2[(size_t)o * n + s] = h2;
+      yv = fmaf(W3[o], h2, yv);
+    }
+    const float r = yv - t;
+    r2 = r * r;
+    const float dy = 2.0f * r / (float)n;
+    a_dy[s] = dy;
+    // backward through the MLP
+    float dh1[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) dh1[k] = 0.0f;
+#pragma unroll 4
+    for (int o = 0; o < H; ++o) {
+      const float dh2 = ((m2 >> o) & 1ull) ? dy * W3[o] : 0.0f;
+      a_dh2[(size_t)o * n + s] = dh2;
+#pragma unroll
+      for (int k = 0; k < H; ++k) dh1[k] = fmaf(W2[o * H + k], dh2, dh1[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      dh1[k] = ((m1 >> k) & 1ull) ? dh1[k] : 0.0f;
+      a_dh1[(size_t)k * n + s] = dh1[k];
+    }
+    float dfeat[IN];
+#pragma unroll
+    for (int k = 0; k < IN; ++k) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int o = 0; o < H; ++o) acc = fmaf(W1[o * IN + k], dh1[o], acc);
+      dfeat[k] = acc;
+    }
+    // backward through the hash grid: scatter-add into the table gradient
+    const uint32_t T = 1u << q.log2T;
+#pragma unroll
+    for (int l = 0; l < IN / 2; ++l) {
+      const int N = q.res[l];
+      int ix, iy, iz;
+      float wx, wy, wz;
+      grid_cell(x, N, ix, wx);
+      grid_cell(y, N, iy, wy);
+      grid_cell(z, N, iz, wz);
+      const bool dense = (q.dense_mask >> l) & 1u;
+      const uint32_t n1 = (uint32_t)N + 1u;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) *
+                        ((c & 4) ? wz : 1.0f - wz);
+        const uint32_t idx = (uint32_t)l * T + vertex_index(dense, n1, T, ix + (c & 1),
+                                                            iy + ((c >> 1) & 1), iz + ((c >> 2) & 1));
+        atomicAdd(g_table + 2 * (size_t)idx, w * dfeat[2 * l]);
+        atomicAdd(g_table + 2 * (size_t)idx + 1, w * dfeat[2 * l + 1]);
+      }
+    }
+  }
+  if (loss) {
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    if ((threadIdx.x & 31) == 0 && r2 != 0.0f) atomicAdd(loss, r2 / (float)n);
+  }
+}
+
+// partial[blk][i][j] = sum over the block's samples of A[i][s] * B[j][s]
+// (A: M x n, B: N x n, feature-major).  Thread tile 4 x 4.
+template <int M, int N>
+__global__ void __launch_bounds__((M / 4) * (N / 4)) outer_kernel(const float* __restrict__ A,
+                                                                  const float* __restrict__ B, long n,
+                                                                  float* __restrict__ partial) {
+  constexpr int TPB = (M / 4) * (N / 4);
+  constexpr int SUB = 32;
+  __shared__ float sa[M][SUB + 1];
+  __shared__ float sb[N][SUB + 1];
+  const int tid = threadIdx.x;
+  const int ti = (tid / (N / 4)) * 4, tj = (tid % (N / 4)) * 4;
+  float acc[4][4] = {};
+  const long s0 = (long)blockIdx.x * kChunk;
+  const long s1 = s0 + kChunk < n ? s0 + kChunk : n;
+  for (long base = s0; base < s1; base += SUB) {
+    for (int e = tid; e < M * SUB; e += TPB) {
+      const int i = e / SUB, k = e % SUB;
+      sa[i][k] = base + k < s1 ? A[(size_t)i * n + base + k] : 0.0f;
+    }
+    for (int e = tid; e < N * SUB; e += TPB) {
+      const int j = e / SUB, k = e % SUB;
+      sb[j][k] = base + k < s1 ? B[(size_t)j * n + base + k] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < SUB; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = sa[ti + u][k];
+        b[u] = sb[tj + u][k];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  float* out = partial + (size_t)blockIdx.x * M * N;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[(ti + u) * N + tj + v] = acc[u][v];
+}
+
+// partial[blk][j] = sum over the block's samples of a[s] * B[j][s].
+template <int N>
+__global__ void __launch_bounds__(256) vec_kernel(const float* __restrict__ a, const float* __restrict__ B,
+                                                  long n, float* __restrict__ partial) {
+  __shared__ float red[256 / 32][N];
+  const long s0 = (long)blockIdx.x * kChunk;
+  const long s1 = s0 + kChunk < n ? s0 + kChunk : n;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = 0; j < N; ++j) {
+    float acc = 0.0f;
+    for (long s = s0 + threadIdx.x; s < s1; s += 256) acc = fmaf(a[s], B[(size_t)j * n + s], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[w][j] = acc;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += 256) {
+    float t = 0.0f;
+    for (int q = 0; q < 256 / 32; ++q) t += red[q][j];
+    partial[(size_t)blockIdx.x * N + j] = t;
+  }
+}
+
+__global__ void reduce_kernel(const float* __restrict__ partial, int blocks, int count,
+                              float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float t = 0.0f;
+  for (int b = 0; b < blocks; ++b) t += partial[(size_t)b * count + i];
+  out[i] = t;
+}
+
+// Bias-corrected Adam (Kingma & Ba): c1 = 1 - b1^t, c2 = 1 - b2^t.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+__global__ void half_copy_kernel(const float* __restrict__ w, uint16_t* __restrict__ w16, int n, int bf16) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (bf16) {
+    __nv_bfloat16 b = __float2bfloat16_rn(w[i]);
+    w16[i] = *reinterpret_cast<uint16_t*>(&b);
+  } else {
+    __half h = __float2half_rn(w[i]);
+    w16[i] = *reinterpret_cast<uint16_t*>(&h);
+  }
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+struct TrainLayout {
+  float *m_t, *v_t, *g_t, *m_w, *v_w, *g_w, *act, *partial, *loss;
+  size_t bytes;
+};
+
+TrainLayout tlayout(const cinr_inr_s* inr, long batch, void* base) {
+  const long nt = (long)inr->p.levels * (1l << inr->p.log2_table) * 2;
+  const int IN = inr->dev.IN, H = inr->dev.H;
+  const long nw = (long)H * IN + (long)H * H + H;
+  const long blocks = (batch + kChunk - 1) / kChunk;
+  Carver c(base);
+  TrainLayout L;
+  L.m_t = c.take<float>(nt);
+  L.v_t = c.take<float>(nt);
+  L.g_t = c.take<float>(nt);
+  L.m_w = c.take<float>(nw);
+  L.v_w = c.take<float>(nw);
+  L.g_w = c.take<float>(nw);
+  L.act = c.take<float>((size_t)(IN + 4 * H + 1) * batch);
+  L.partial = c.take<float>((size_t)blocks * nw);
+  L.loss = c.take<float>(64);
+  L.bytes = align_up(c.off, 256);
+  return L;
+}
+
+int check(const cinr_inr_s* inr, const cinr_train_opts* o) {
+  if (!inr || !o) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (inr->p.table_precision != CINR_PREC_FP32) return set_error(CINR_ERR_ARG, "training needs an FP32 table");
+  if (o->batch < 1 || o->batch > (1l << 26)) return set_error(CINR_ERR_ARG, "batch must be in [1, 2^26]");
+  if (!(o->lr > 0.0f) || !(o->beta1 >= 0.0f && o->beta1 < 1.0f) || !(o->beta2 >= 0.0f && o->beta2 < 1.0f))
+    return set_error(CINR_ERR_ARG, "bad Adam hyper-parameters");
+  return CINR_OK;
+}
+
+template <int IN, int H>
+int grads(cinr_trainer_s* t, const float* xyz, const float* tgt, long n, const float* field, int3 dims,
+          uint64_t first, float* g_table, float* g_w, cudaStream_t s) {
+  const InrDev& q = t->inr->dev;
+  CINR_CK(cudaMemsetAsync(g_table, 0, sizeof(float) * t->n_table, s));
+  const int smem = mlp_floats<IN, H>() * 4;
+  auto k = fwd_bwd_kernel<IN, H>;
+  CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  k<<<(unsigned)((n + kFwdThreads - 1) / kFwdThreads), kFwdThreads, smem, s>>>(
+      q, n, xyz, tgt, field, dims, t->o.seed, first, t->act, g_table, t->loss);
+  CINR_CK(cudaGetLastError());
+  const int blocks = (int)((n + kChunk - 1) / kChunk);
+  const float* a_feat = t->act;
+  const float* a_h1 = a_feat + (size_t)IN * n;
+  const float* a_h2 = a_h1 + (size_t)H * n;
+  const float* a_dh1 = a_h2 + (size_t)H * n;
+  const float* a_dh2 = a_dh1 + (size_t)H * n;
+  const float* a_dy = a_dh2 + (size_t)H * n;
+  float* p1 = t->partial;
+  float* p2 = p1 + (size_t)blocks * H * IN;
+  float* p3 = p2 + (size_t)blocks * H * H;
+  outer_kernel<H, IN><<<blocks, (H / 4) * (IN / 4), 0, s>>>(a_dh1, a_feat, n, p1);
+  outer_kernel<H, H><<<blocks, (H / 4) * (H / 4), 0, s>>>(a_dh2, a_h1, n, p2);
+  vec_kernel<H><<<blocks, 256, 0, s>>>(a_dy, a_h2, n, p3);
+  reduce_kernel<<<(H * IN + 255) / 256, 256, 0, s>>>(p1, blocks, H * IN, g_w);
+  reduce_kernel<<<(H * H + 255) / 256, 256, 0, s>>>(p2, blocks, H * H, g_w + H * IN);
+  reduce_kernel<<<(H + 255) / 256, 256, 0, s>>>(p3, blocks, H, g_w + H * IN + H * H);
+  CINR_CK(cudaGetLastError());
+  return CINR_OK;
+}
+
+int grads_dispatch(cinr_trainer_s* t, const float* xyz, const float* tgt, long n, const float* field,
+                   int3 dims, uint64_t first, float* g_table, float* g_w, cudaStream_t s) {
+  switch (shape_of(t->inr->dev.IN, t->inr->dev.H)) {
+    case Shape::S16x32: return grads<16, 32>(t, xyz, tgt, n, field, dims, first, g_table, g_w, s);
+    case Shape::S32x64: return grads<32, 64>(t, xyz, tgt, n, field, dims, first, g_table, g_w, s);
+    case Shape::S48x64: return grads<48, 64>(t, xyz, tgt, n, field, dims, first, g_table, g_w, s);
+    default: return set_error(CINR_ERR_ARG, "unsupported shape");
+  }
+}
+
+}  // namespace
+
+extern "C" int cinr_trainer_bytes(cinr_inr_t inr, const cinr_train_opts* o, size_t* bytes) {
+  int e = check(inr, o);
+  if (e) return e;
+  if (!bytes) return set_error(CINR_ERR_ARG, "bytes is NULL");
+  *bytes = tlayout(inr, o->batch, nullptr).bytes;
+  return CINR_OK;
+}
+
+extern "C" int cinr_create_trainer(cinr_inr_t inr, const cinr_train_opts* o, void* dev_mem, size_t bytes,
+                                   cinr_stream_t stream, cinr_trainer_t* out) {
+  int e = check(inr, o);
+  if (e) return e;
+  if (!out) return set_error(CINR_ERR_ARG, "out is NULL");
+  if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) & 255))
+    return set_error(CINR_ERR_ARG, "dev_mem must be non-NULL and 256-byte aligned");
+  TrainLayout L = tlayout(inr, o->batch, dev_mem);
+  if (bytes < L.bytes) return set_error(CINR_ERR_NOMEM, "trainer needs %zu bytes, got %zu", L.bytes, bytes);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cinr_trainer_s* t = new cinr_trainer_s();
+  t->inr = inr;
+  t->o = *o;
+  t->n_table = (long)inr->p.levels * (1l << inr->p.log2_table) * 2;
+  t->n_w = (long)inr->dev.H * inr->dev.IN + (long)inr->dev.H * inr->dev.H + inr->dev.H;
+  t->m_t = L.m_t;
+  t->v_t = L.v_t;
+  t->g_t = L.g_t;
+  t->m_w = L.m_w;
+  t->v_w = L.v_w;
+  t->g_w = L.g_w;
+  t->act = L.act;
+  t->partial = L.partial;
+  t->loss = L.loss;
+  t->step = 0;
+  t->n_part = (int)((o->batch + kChunk - 1) / kChunk);
+  CINR_CK(cudaMemsetAsync(L.m_t, 0, sizeof(float) * t->n_table, s));
+  CINR_CK(cudaMemsetAsync(L.v_t, 0, sizeof(float) * t->n_table, s));
+  CINR_CK(cudaMemsetAsync(L.m_w, 0, sizeof(float) * t->n_w, s));
+  CINR_CK(cudaMemsetAsync(L.v_w, 0, sizeof(float) * t->n_w, s));
+  *out = t;
+  return CINR_OK;
+}
+
+extern "C" int cinr_destroy_trainer(cinr_trainer_t t) {
+  delete t;
+  return CINR_OK;
+}
+
+extern "C" int cinr_train_step(cinr_trainer_t t, const float* field_dev, const int dims[3], float* loss_dev,
+                               cinr_stream_t stream) {
+  if (!t || !field_dev || !dims) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return set_error(CINR_ERR_ARG, "bad field dims");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long n = t->o.batch;
+  t->step += 1;
+  CINR_CK(cudaMemsetAsync(t->loss, 0, 4, s));
+  int e = grads_dispatch(t, nullptr, nullptr, n, field_dev, make_int3(dims[0], dims[1], dims[2]),
+                         (uint64_t)(t->step - 1) * (uint64_t)n, t->g_t, t->g_w, s);
+  if (e) return e;
+  const double c1 = 1.0 - pow((double)t->o.beta1, (double)t->step);
+  const double c2 = 1.0 - pow((double)t->o.beta2, (double)t->step);
+  float* table = const_cast<float*>(static_cast<const float*>(t->inr->dev.table));
+  float* w = const_cast<float*>(t->inr->dev.w);
+  const unsigned gb = (unsigned)num_sms() * 8;
+  adam_kernel<<<gb, 256, 0, s>>>(table, t->g_t, t->m_t, t->v_t, t->n_table, t->o.lr, t->o.beta1, t->o.beta2,
+                                 t->o.eps, (float)c1, (float)c2);
+  adam_kernel<<<(unsigned)((t->n_w + 255) / 256), 256, 0, s>>>(w, t->g_w, t->m_w, t->v_w, t->n_w, t->o.lr,
+                                                              t->o.beta1, t->o.beta2, t->o.eps, (float)c1,
+                                                              (float)c2);
+  half_copy_kernel<<<(unsigned)((t->n_w + 255) / 256), 256, 0, s>>>(
+      w, t->inr->w16, (int)t->n_w, t->inr->p.mlp_precision == CINR_PREC_BF16);
+  CINR_CK(cudaGetLastError());
+  if (loss_dev) CINR_CK(cudaMemcpyAsync(loss_dev, t->loss, 4, cudaMemcpyDeviceToDevice, s));
+  return CINR_OK;
+}
+
+extern "C" int cinr_inr_loss_grad(cinr_trainer_t t, const float* xyz_dev, const float* target_dev, long n,
+                                  float* g_table_dev, float* g_mlp_dev, float* loss_dev, cinr_stream_t stream) {
+  if (!t || !xyz_dev || !target_dev || !g_table_dev || !g_mlp_dev) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (n < 1 || n > t->o.batch) return set_error(CINR_ERR_ARG, "n must be in [1, batch]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CINR_CK(cudaMemsetAsync(t->loss, 0, 4, s));
+  int e = grads_dispatch(t, xyz_dev, target_dev, n, nullptr, make_int3(1, 1, 1), 0, g_table_dev, g_mlp_dev, s);
+  if (e) return e;
+  if (loss_dev) CINR_CK(cudaMemcpyAsync(loss_dev, t->loss, 4, cudaMemcpyDeviceToDevice, s));
+  return CINR_OK;
+}
+
+extern "C" int cinr_inr_export(cinr_inr_t inr, float* host_table, float* host_mlp, cinr_stream_t stream) {
+  if (!inr || !host_table || !host_mlp) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (inr->p.table_precision != CINR_PREC_FP32) return set_error(CINR_ERR_ARG, "export needs an FP32 table");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nt = (size_t)inr->p.levels * ((size_t)1 << inr->p.log2_table) * 2;
+  const size_t nw = (size_t)inr->dev.H * inr->dev.IN + (size_t)inr->dev.H * inr->dev.H + inr->dev.H;
+  CINR_CK(cudaMemcpyAsync(host_table, inr->dev.table, nt * 4, cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaMemcpyAsync(host_mlp, inr->dev.w, nw * 4, cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaStreamSynchronize(s));
+  return CINR_OK;
+}

@@ -63,10 +63,10 @@ def test_cached_orbit_state_bit_exact_ranked():
 
 
 def test_cached_replacement_under_pressure():
-    # views 75 deg apart at LoD 0 with a 60-slot pool: bricks of earlier views
-    # are not used by the current one and get evicted (LRU by frame stamp)
+    # narrow views 75 deg apart at LoD 0 with a 60-slot pool: bricks of earlier
+    # views are not used by the current one and get evicted (LRU by stamp)
     def cam_fn(f, W, H):
-        return S.orbit_camera(0, W, H, start_deg=75.0 * f, distance=1.3)
+        return S.orbit_camera(0, W, H, start_deg=75.0 * f, distance=1.3, fov_y_deg=12.0)
     cache, oc, hist, worst = _run(6, slots=60, n_req=30, lod_mode=1, lod_scale=0.0, levels=3,
                                   cam_fn=cam_fn)
     assert sum(h["evictions"] for h in hist) > 0
