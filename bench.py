@@ -112,7 +112,7 @@ def load_peaks():
 def build_scene(args, device):
     from paper_2504_18001_gb300 import cinr, synthetic as S
     cfg = S.INR_512
-    table, w = S.inr_init(cfg, seed=args.seed, table_scale=1e-4)
+    table, w = S.inr_init(cfg, seed=args.seed, table_scale=1e-4, level_decay=args.level_decay)
     inr = cinr.Inr(cinr.make_inr_params(cfg), table, w, device=device)
     vol = (512, 512, 512)
     lo, hi = inr.raw_range(vol, stride=8)
@@ -248,9 +248,11 @@ def run_gpu(args):
         "clocks": clk,
     }
     res["gpu_launches"] = args.steps * launches_per_cached_frame()
+    mse = torch.mean((cached_img[..., :3].double() - uncached_img[..., :3].double()) ** 2).item()
+    res["psnr_db"] = {"cached_vs_uncached_full_frame": 10 * np.log10(1.0 / max(mse, 1e-30))}
     if rank == 0 and not args.no_cpu:
-        res["cpu_baseline"], res["psnr_db"] = cpu_baseline(args, table, w, last_f, cached_img,
-                                                           uncached_img)
+        res["cpu_baseline"], p = cpu_baseline(args, table, w, last_f, cached_img, uncached_img)
+        res["psnr_db"].update(p)
     if world > 1:
         dist.destroy_process_group()
     return res if rank == 0 else None
@@ -307,7 +309,7 @@ def run_reference(args):
     import oracle as O
     from paper_2504_18001_gb300 import synthetic as S
     cfg = S.INR_512
-    table, w = S.inr_init(cfg, seed=args.seed, table_scale=1e-4)
+    table, w = S.inr_init(cfg, seed=args.seed, table_scale=1e-4, level_decay=args.level_decay)
     p = O.inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden)
     vol = (512, 512, 512)
     lo, hi = O.inr_raw_range(p, table, w, vol, 32)
@@ -344,12 +346,13 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=40)
     ap.add_argument("--impl", default="cinr", choices=["cinr", "reference"])
     ap.add_argument("--res", type=int, default=1024)
     ap.add_argument("--brick", type=int, default=8)
     ap.add_argument("--pool-mib", type=int, default=1024)
-    ap.add_argument("--n-req", type=int, default=40)
+    ap.add_argument("--n-req", type=int, default=4096)
+    ap.add_argument("--level-decay", type=float, default=0.5)
     ap.add_argument("--lod-scale", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--uncached-steps", type=int, default=5)

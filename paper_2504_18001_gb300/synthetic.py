@@ -90,11 +90,18 @@ TERA = SceneConfig(name="terascale_10240x7680x1536_1080p", vol=(10240, 7680, 153
 
 
 # ------------------------------------------------------------- INR weights
-def inr_init(cfg: InrConfig, seed: int, table_scale: float = 1e-4):
-    """Initial parameters: table U(-s, s) (L*T*F, level-major, feature-minor);
-    MLP weights He-normal N(0, 2/fan_in), layer-major, each [out][in]."""
+def inr_init(cfg: InrConfig, seed: int, table_scale: float = 1e-4, level_decay: float = 1.0):
+    """Initial parameters: table U(-s d^l, s d^l) for level l (L*T*F,
+    level-major, feature-minor); MLP weights He-normal N(0, 2/fan_in),
+    layer-major, each [out][in].  level_decay d < 1 gives a band-limited
+    field whose energy sits in the coarse levels, the spectrum a network
+    trained on a smooth scientific field ends up with."""
     rng = np.random.default_rng(np.random.PCG64(seed))
     table = rng.uniform(-table_scale, table_scale, cfg.table_entries).astype(np.float32)
+    if level_decay != 1.0:
+        per = (1 << cfg.log2_table) * cfg.feats
+        scale = np.repeat(np.float32(level_decay) ** np.arange(cfg.levels, dtype=np.float32), per)
+        table = (table * scale).astype(np.float32)
     ws = []
     fan = cfg.in_dim
     for _ in range(cfg.n_hidden_layers):
