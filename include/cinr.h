@@ -340,6 +340,19 @@ int cinr_inr_export(cinr_inr_t inr, float* host_table, float* host_mlp,
 int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap,
                     size_t* count, cinr_stream_t stream);
 
+/* Tensor-core self-test of one 128 x 64 tile: d_dev[128][64] = A B^T with
+ * a_dev [128][K] and b_dev [64][K] (row-major FP32, rounded to BF16 when
+ * bf16 != 0, else FP16), accumulated in FP32 by tcgen05.mma in tensor
+ * memory; K in {16, 32, 64}.  Checks the shared-memory operand layout the
+ * MLP kernels use. */
+int cinr_debug_mma_tile(const float* a_dev, const float* b_dev, int K,
+                        int bf16, float* d_dev, cinr_stream_t stream);
+
+/* Synchronises `stream` and reports whether a bounded device-side wait of a
+ * tensor-core MLP kernel gave up since the last call on this INR
+ * (CINR_ERR_TIMEOUT), clearing the flag. */
+int cinr_inr_status(cinr_inr_t inr, cinr_stream_t stream);
+
 /* Geometry of the cache's LoD `level`: voxel dims, brick counts per axis and
  * the key of its first brick (keys are level-major, x fastest). */
 int cinr_cache_level_info(cinr_cache_t cache, int level, int dims[3],

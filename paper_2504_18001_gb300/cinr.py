@@ -101,6 +101,8 @@ _SIGS = {
     "cinr_destroy_trainer": [_vp],
     "cinr_inr_export": [_vp, _vp, _vp, _vp],
     "cinr_debug_dump": [_vp, C.c_int, _vp, C.c_size_t, _P(C.c_size_t), _vp],
+    "cinr_debug_mma_tile": [_vp, _vp, C.c_int, C.c_int, _vp, _vp],
+    "cinr_inr_status": [_vp, _vp],
     "cinr_cache_level_info": [_vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_long)],
 }
 

@@ -453,6 +453,7 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
   d.pool = L.pool;
   d.pool_prec = o->storage_precision;
   d.B = g.B;
+  d.invB = (g.B & (g.B - 1)) == 0 ? 1.0f / (float)g.B : 0.0f;
   d.S = g.S;
   d.L = g.L;
   for (int l = 0; l < kMaxLod; ++l)

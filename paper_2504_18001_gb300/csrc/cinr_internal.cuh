@@ -86,6 +86,7 @@ struct CacheDev {
   void* pool;
   int pool_prec;
   int B, S, L;
+  float invB;  // 1/B when B is a power of two (exact), else 0
   int dims[kMaxLod][3];
   int nb[kMaxLod][3];
   uint32_t off[kMaxLod + 1];
@@ -141,7 +142,9 @@ __device__ __forceinline__ bool sample_at(const CamDev& c, const float d[3], flo
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     float p = f_add(c.o[q], f_mul(tm, d[q]));
-    x[q] = clamp01(f_div(f_add(p, c.h[q]), c.e[q]));
+    const float num = f_add(p, c.h[q]);
+    // division by an extent of exactly 1 (the longest axis) is the identity
+    x[q] = clamp01(c.e[q] == 1.0f ? num : f_div(num, c.e[q]));
   }
   return true;
 }
@@ -368,3 +371,6 @@ struct cinr_cache_s {
 // Cache update at the end of a frame (request selection, victims, commit,
 // decode), enqueued on `s`; stats_dev receives decoded/evicted counts.
 int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStream_t s);
+
+// Tensor-core direct inference (FP16/BF16 MLP), used by cinr_infer.
+int cinr_infer_tc(const cinr_inr_s* inr, const float* xyz, long n, float* out, cudaStream_t s);

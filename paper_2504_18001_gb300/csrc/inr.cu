@@ -100,6 +100,7 @@ extern "C" int cinr_create_inr(const cinr_inr_params* p, void* dev_mem, size_t b
     }
   }
   CINR_CK(cudaMemcpyAsync(L.w16, w16.data(), nw * 2, cudaMemcpyHostToDevice, s));
+  CINR_CK(cudaMemsetAsync(L.scratch, 0, 1024 * sizeof(float), s));
   CINR_CK(cudaStreamSynchronize(s));
 
   cinr_inr_s* h = new cinr_inr_s();
@@ -287,6 +288,7 @@ extern "C" int cinr_infer(cinr_inr_t inr, const float* xyz_dev, long n, float* o
   if (n == 0) return CINR_OK;
   if (!xyz_dev || !out_dev) return set_error(CINR_ERR_ARG, "NULL buffer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (inr->p.mlp_precision != CINR_PREC_FP32) return cinr_infer_tc(inr, xyz_dev, n, out_dev, s);
   switch (shape_of(inr->dev.IN, inr->dev.H)) {
     case Shape::S16x32: return launch_infer<16, 32>(inr->dev, xyz_dev, n, out_dev, s);
     case Shape::S32x64: return launch_infer<32, 64>(inr->dev, xyz_dev, n, out_dev, s);

@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(kFrameThreads, CACHED ? 6 : 4)
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             s[a] = f_mul(pv[a], sc);
-            int bi = (int)floorf(f_div(s[a], (float)c.B));
+            // s / B: a power-of-two B divides exactly by multiplying with 1/B
+            const float q = c.invB > 0.0f ? f_mul(s[a], c.invB) : f_div(s[a], (float)c.B);
+            int bi = (int)floorf(q);
             bi = bi < 0 ? 0 : (bi > c.nb[lev][a] - 1 ? c.nb[lev][a] - 1 : bi);
             b[a] = bi;
           }
@@ -223,12 +225,13 @@ __global__ void __launch_bounds__(kFrameThreads, CACHED ? 6 : 4)
         }
       }
       // LRU stamp of the slots that served this segment
-      const unsigned hm = __ballot_sync(kFull, hit);
-      if (hit) {
+      // (only lanes that see a stale stamp take part; a stale cached read
+      // costs one extra atomic, never a wrong count)
+      const bool stale = hit && c.stamp[hit_slot] != P.frame;
+      const unsigned hm = __ballot_sync(kFull, stale);
+      if (stale) {
         const unsigned peers = __match_any_sync(hm, hit_slot);
-        if (lane == __ffs(peers) - 1 && c.stamp[hit_slot] != P.frame &&
-            atomicExch(c.stamp + hit_slot, P.frame) != P.frame)
-          ++n_slot;
+        if (lane == __ffs(peers) - 1 && atomicExch(c.stamp + hit_slot, P.frame) != P.frame) ++n_slot;
       }
     }
 

@@ -1,0 +1,281 @@
+// Tensor-core MLP for tiles of 128 queries on sm_103a: tcgen05.mma with
+// operands in shared memory and the FP32 accumulator in tensor memory
+// (TMEM), read back with tcgen05.ld.  The MLP is in -> H (ReLU) -> H (ReLU)
+// -> 1 with FP16 or BF16 operands and FP32 accumulation; the last layer
+// (H -> 1) is a per-thread FP32 dot product.
+//
+// Shared-memory operand layout (no swizzle, K-major): 8-row x 16-byte core
+// matrices, stored 128 contiguous bytes each; core (r, k) of a rows x K
+// matrix sits at ((r/8) * (K/8) + k/8) * 128 bytes, so the core matrices
+// adjacent along K are 128 B apart (leading-dimension byte offset) and the
+// 8-row groups are (K/8) * 128 B apart (stride-dimension byte offset).
+//
+// Every wait on an mbarrier is bounded; on a timeout the routine records an
+// error word and carries on, so that the kernel always frees its TMEM and
+// returns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace cinr {
+namespace tc {
+
+constexpr int kM = 128;               // queries per tile (one per thread)
+constexpr int kTmemCols = 64;         // accumulator columns per CTA
+constexpr uint32_t kWaitLimit = 1u << 22;
+// Dynamic shared memory per CTA (bytes) that keeps at most 8 CTAs (8 x 64
+// TMEM columns = 512) resident on an SM of 228 KB shared memory.
+constexpr int kMinSmemPerCta = 29 * 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Warp-wide (all 32 lanes of one warp).
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Makes this thread's generic-proxy shared-memory writes visible to the
+// tensor core (async proxy).
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (M/N) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D F32, A and B both FP16 (fmt 0) or
+// both BF16 (fmt 1), K-major, N and M.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int fmt) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Byte offset of element (r, k) of a K-major operand with K columns.
+__device__ __forceinline__ uint32_t core_off(int r, int k, int K) {
+  return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint16_t to16(float x) {
+  if (BF16) {
+    __nv_bfloat16 b = __float2bfloat16_rn(x);
+    return *reinterpret_cast<uint16_t*>(&b);
+  }
+  __half h = __float2half_rn(x);
+  return *reinterpret_cast<uint16_t*>(&h);
+}
+
+// Row r (8 values at k0..k0+7) of a K-major operand, one 16-byte store.
+template <bool BF16>
+__device__ __forceinline__ void store8(unsigned char* base, int r, int k0, int K, const float* v) {
+  uint4 q;
+  q.x = (uint32_t)to16<BF16>(v[0]) | ((uint32_t)to16<BF16>(v[1]) << 16);
+  q.y = (uint32_t)to16<BF16>(v[2]) | ((uint32_t)to16<BF16>(v[3]) << 16);
+  q.z = (uint32_t)to16<BF16>(v[4]) | ((uint32_t)to16<BF16>(v[5]) << 16);
+  q.w = (uint32_t)to16<BF16>(v[6]) | ((uint32_t)to16<BF16>(v[7]) << 16);
+  *reinterpret_cast<uint4*>(base + core_off(r, k0, K)) = q;
+}
+
+// Shared memory of one CTA's tensor-core MLP.
+template <int IN, int H>
+struct TcSmem {
+  alignas(128) unsigned char a[kM * IN * 2];   // features, K = IN
+  alignas(128) unsigned char a2[kM * H * 2];   // hidden layer 1, K = H
+  alignas(128) unsigned char w1[H * IN * 2];   // W1 [H][IN]
+  alignas(128) unsigned char w2[H * H * 2];    // W2 [H][H]
+  float w3[H];
+  uint64_t bar;
+  uint32_t tmem;
+};
+
+// Stage the half-precision weights (row-major [out][in] in global memory)
+// into the core-matrix layout and W3 (FP32) into shared memory.  All
+// threads of the CTA.
+template <int IN, int H>
+__device__ __forceinline__ void load_tc_weights(TcSmem<IN, H>& s, const uint16_t* w16, const float* w32) {
+  for (int e = threadIdx.x; e < H * IN; e += blockDim.x) {
+    const int r = e / IN, k = e % IN;
+    *reinterpret_cast<uint16_t*>(s.w1 + core_off(r, k, IN)) = __ldg(w16 + e);
+  }
+  for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
+    const int r = e / H, k = e % H;
+    *reinterpret_cast<uint16_t*>(s.w2 + core_off(r, k, H)) = __ldg(w16 + H * IN + e);
+  }
+  for (int e = threadIdx.x; e < H; e += blockDim.x) s.w3[e] = __ldg(w32 + H * IN + H * H + e);
+}
+
+// CTA set-up: mbarrier and TMEM allocation (warp 0).  Call after
+// load_tc_weights, before the first tile, by all threads.
+template <int IN, int H>
+__device__ __forceinline__ void tc_setup(TcSmem<IN, H>& s) {
+  if (threadIdx.x == 0) mbar_init(&s.bar, 1);
+  if (threadIdx.x < 32) tmem_alloc(&s.tmem, kTmemCols);
+  fence_proxy_async();
+  fence_before();
+  __syncthreads();
+  fence_after();
+}
+
+template <int IN, int H>
+__device__ __forceinline__ void tc_teardown(TcSmem<IN, H>& s) {
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (threadIdx.x < 32) tmem_dealloc(s.tmem, kTmemCols);
+}
+
+// One 128-query tile.  Thread t supplies row t's features (IN floats; zeros
+// when !valid) and gets the raw network output of row t.  All 128 threads
+// of the CTA (4 warps) must call it together.  `phase` is the mbarrier
+// parity this CTA waits for next (starts at 0); *err is set on a timeout.
+template <int IN, int H, bool BF16>
+__device__ __forceinline__ float mlp_tile(TcSmem<IN, H>& s, const float* feat, bool valid, uint32_t& phase,
+                                          int* err) {
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  {
+    float z[8];
+#pragma unroll
+    for (int k0 = 0; k0 < IN; k0 += 8) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) z[i] = valid ? feat[k0 + i] : 0.0f;
+      store8<BF16>(s.a, t, k0, IN, z);
+    }
+  }
+  fence_proxy_async();
+  __syncthreads();
+  constexpr uint32_t idesc = idesc_f16(kM, H, BF16 ? 1 : 0);
+  const uint32_t dt = s.tmem;
+  if (t == 0) {
+    fence_after();
+    const uint32_t a0 = smem_u32(s.a), b0 = smem_u32(s.w1);
+#pragma unroll
+    for (int kk = 0; kk < IN / 16; ++kk)
+      mma_f16(dt, sdesc(a0 + kk * 256, 128, (IN / 8) * 128), sdesc(b0 + kk * 256, 128, (IN / 8) * 128), idesc,
+              kk > 0 ? 1u : 0u);
+    commit(&s.bar);
+  }
+  bool ok = mbar_wait(&s.bar, phase);
+  phase ^= 1u;
+  fence_after();
+  const uint32_t lane_addr = dt + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+  for (int c0 = 0; c0 < H; c0 += 16) {
+    float v[16];
+    ld16(lane_addr + c0, v);
+    wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+    store8<BF16>(s.a2, t, c0, H, v);
+    store8<BF16>(s.a2, t, c0 + 8, H, v + 8);
+  }
+  fence_before();
+  fence_proxy_async();
+  __syncthreads();
+  if (t == 0) {
+    fence_after();
+    const uint32_t a0 = smem_u32(s.a2), b0 = smem_u32(s.w2);
+#pragma unroll
+    for (int kk = 0; kk < H / 16; ++kk)
+      mma_f16(dt, sdesc(a0 + kk * 256, 128, (H / 8) * 128), sdesc(b0 + kk * 256, 128, (H / 8) * 128), idesc,
+              kk > 0 ? 1u : 0u);
+    commit(&s.bar);
+  }
+  ok = mbar_wait(&s.bar, phase) && ok;
+  phase ^= 1u;
+  fence_after();
+  float y = 0.0f;
+#pragma unroll
+  for (int c0 = 0; c0 < H; c0 += 16) {
+    float v[16];
+    ld16(lane_addr + c0, v);
+    wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) y = fmaf(s.w3[c0 + i], fmaxf(v[i], 0.0f), y);
+  }
+  fence_before();
+  if (!ok && err) atomicExch(err, 1);
+  return y;
+}
+
+}  // namespace tc
+}  // namespace cinr

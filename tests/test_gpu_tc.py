@@ -1,0 +1,66 @@
+"""Tensor-core (tcgen05) MLP: the shared-memory operand layout through a
+single-tile GEMM self-test, and FP16/BF16 INR inference against the FP64
+oracle (error stated per precision)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_18001_gb300 import synthetic as S
+
+from _scenes import gpu_inr, oracle_inr, scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _round(x, bf16):
+    import torch
+    t = torch.from_numpy(x)
+    return (t.to(torch.bfloat16) if bf16 else t.to(torch.float16)).float().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("K", [16, 32, 64])
+@pytest.mark.parametrize("bf16", [0, 1], ids=["fp16", "bf16"])
+def test_mma_tile_matches_reference_gemm(K, bf16):
+    import torch
+    from paper_2504_18001_gb300 import cinr
+    rng = np.random.default_rng(K + 10 * bf16)
+    A = rng.normal(size=(128, K)).astype(np.float32)
+    B = rng.normal(size=(64, K)).astype(np.float32)
+    # distinct row/column signatures catch permuted or transposed operands
+    A[:, 0] += np.arange(128, dtype=np.float32) / 16
+    B[:, 1] += np.arange(64, dtype=np.float32) / 8
+    a, b = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    d = torch.full((128, 64), float("nan"), device="cuda")
+    cinr.check(cinr.lib().cinr_debug_mma_tile(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), K,
+                                              bf16, C.c_void_p(d.data_ptr()), cinr._stream(None)),
+               "cinr_debug_mma_tile")
+    ref = _round(A, bf16) @ _round(B, bf16).T
+    got = d.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max() + 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("cfg", [S.INR_64, S.INR_512, S.INR_TERA], ids=["L8", "L16", "L24"])
+def test_tensor_core_inference_error(prec, cfg):
+    import torch
+    from paper_2504_18001_gb300 import cinr
+    vol = (64, 64, 64)
+    table, w = scene(cfg, seed=4, table_scale=0.5)
+    inr32 = gpu_inr(cfg, table, w, vol=vol)
+    inr = gpu_inr(cfg, table, w, vol=vol, mlp=prec)
+    p = oracle_inr(cfg, table, w, vol=vol)
+    pts = S.random_points(10007, 21)  # ragged: not a multiple of the 128-query tile
+    x = torch.from_numpy(pts).cuda()
+    v = inr.infer(x).cpu().numpy()
+    v32 = inr32.infer(x).cpu().numpy()
+    cinr.check(cinr.lib().cinr_inr_status(inr.h, cinr._stream(None)), "cinr_inr_status")
+    ref = O.inr_eval(p, table, w, pts)
+    err = np.abs(v - ref).max()
+    # stated error on the [0,1]-normalised field: FP32 path 1e-4; FP16 MLP
+    # 1e-2; BF16 MLP (8-bit mantissa) 5e-2
+    assert np.abs(v32 - ref).max() < 1e-4
+    assert err < (1e-2 if prec == "fp16" else 5e-2), err
+    assert np.mean(np.abs(v - ref)) < (2e-3 if prec == "fp16" else 1e-2)
