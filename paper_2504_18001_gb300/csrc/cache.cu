@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "cinr_internal.cuh"
+#include "tc_mlp.cuh"
 
 using namespace cinr;
 
@@ -103,30 +104,46 @@ __device__ __forceinline__ int key_level(const CacheDev& c, uint32_t key) {
   return l;
 }
 
-// Decode: every stored voxel of a requested brick is inferred by the INR at
-// its LoD-l voxel centre (clamp-to-edge) and written into the victim slot.
+// Decode (persistent): every stored voxel of a requested brick is inferred
+// by the INR at its LoD-l voxel centre (clamp-to-edge) and written into the
+// victim slot.  Work items are (request, 128-voxel tile) pairs, taken by the
+// resident CTAs in a grid-stride loop, so one launch absorbs the uneven
+// per-frame request count read from the device.
 // Mode list: request i of *n_dev uses keys[i] and slots[i].  Mode preload
 // (keys == nullptr): request i is brick off[L-1] + i into slot i.
-template <int IN, int H>
-__global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const uint32_t* keys,
-                                                     const uint32_t* slots, const uint32_t* n_dev,
-                                                     uint32_t n_fixed) {
-  extern __shared__ float4 smem4[];
+// MLPP: 0 = FP32 SIMT MLP, 1 / 2 = FP16 / BF16 tensor cores.
+template <int IN, int H, int MLPP>
+__global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const uint16_t* w16,
+                                                     const uint32_t* keys, const uint32_t* slots,
+                                                     const uint32_t* n_dev, uint32_t n_fixed, int* err) {
+  extern __shared__ __align__(1024) float4 smem4[];
   float* sw = reinterpret_cast<float*>(smem4);
+  tc::TcSmem<IN, H>& tcs = *reinterpret_cast<tc::TcSmem<IN, H>*>(smem4);
   const uint32_t n = keys ? *n_dev : n_fixed;
-  const uint32_t r = blockIdx.y;
-  if (r >= n) return;
-  load_weights(sw, q.w, mlp_floats<IN, H>());
-  __syncthreads();
-  const uint32_t key = keys ? keys[r] : c.off[c.L - 1] + r;
-  const uint32_t slot = keys ? slots[r] : r;
-  const int l = key_level(c, key);
-  const uint32_t local = key - c.off[l];
-  const int b[3] = {(int)(local % c.nb[l][0]), (int)((local / c.nb[l][0]) % c.nb[l][1]),
-                    (int)(local / ((uint32_t)c.nb[l][0] * c.nb[l][1]))};
   const int S = c.S, S3 = S * S * S;
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < S3; v += gridDim.x * blockDim.x) {
-    const int lv[3] = {v % S, (v / S) % S, v / (S * S)};
+  const uint32_t tiles_per = (uint32_t)((S3 + 127) / 128);
+  const uint32_t work = n * tiles_per;
+  if (blockIdx.x >= work) return;  // block-uniform, before any barrier
+  uint32_t phase = 0;
+  if (MLPP) {
+    tc::load_tc_weights(tcs, w16, q.w);
+    tc::tc_setup(tcs);
+  } else {
+    load_weights(sw, q.w, mlp_floats<IN, H>());
+    __syncthreads();
+  }
+  for (uint32_t wi = blockIdx.x; wi < work; wi += gridDim.x) {
+    const uint32_t r = wi / tiles_per;
+    const int v = (int)(wi % tiles_per) * 128 + (int)threadIdx.x;
+    const bool valid = v < S3;
+    const uint32_t key = keys ? keys[r] : c.off[c.L - 1] + r;
+    const uint32_t slot = keys ? slots[r] : r;
+    const int l = key_level(c, key);
+    const uint32_t local = key - c.off[l];
+    const int b[3] = {(int)(local % c.nb[l][0]), (int)((local / c.nb[l][0]) % c.nb[l][1]),
+                      (int)(local / ((uint32_t)c.nb[l][0] * c.nb[l][1]))};
+    const int vv = valid ? v : 0;
+    const int lv[3] = {vv % S, (vv / S) % S, vv / (S * S)};
     float x[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -135,13 +152,24 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
       float t = f_mul(f_add((float)j, 0.5f), (float)(1 << l));
       x[a] = clamp01(f_div(t, (float)c.vol[a]));
     }
-    const float val = fmaf(q.vscale, inr_raw_fp32<IN, H>(q, sw, x[0], x[1], x[2]), q.vmin);
-    const size_t o = (size_t)slot * S3 + v;
-    if (c.pool_prec == CINR_PREC_FP16)
-      reinterpret_cast<__half*>(c.pool)[o] = __float2half_rn(val);
-    else
-      reinterpret_cast<float*>(c.pool)[o] = val;
+    float y;
+    if (MLPP == 0) {
+      y = valid ? inr_raw_fp32<IN, H>(q, sw, x[0], x[1], x[2]) : 0.0f;
+    } else {
+      float feat[IN];
+      encode_point<IN / 2>(q, x[0], x[1], x[2], feat);
+      y = tc::mlp_tile<IN, H, MLPP == 2>(tcs, feat, valid, phase, err);
+    }
+    if (valid) {
+      const float val = fmaf(q.vscale, y, q.vmin);
+      const size_t o = (size_t)slot * S3 + v;
+      if (c.pool_prec == CINR_PREC_FP16)
+        reinterpret_cast<__half*>(c.pool)[o] = __float2half_rn(val);
+      else
+        reinterpret_cast<float*>(c.pool)[o] = val;
+    }
   }
+  if (MLPP) tc::tc_teardown(tcs);
 }
 
 __global__ void preload_map(CacheDev c, uint32_t n) {
@@ -378,28 +406,48 @@ int radix_select(const KF& kf, uint32_t n, int key_bits, uint32_t want, SelState
   return CINR_OK;
 }
 
-template <int IN, int H>
-int launch_decode(const InrDev& q, const CacheDev& c, const uint32_t* keys, const uint32_t* slots,
+// n_grid = the largest request count the launch may see (the device count
+// n_dev decides at run time); the grid is the resident CTAs, at most one
+// per work item.
+template <int IN, int H, int MLPP>
+int launch_decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys, const uint32_t* slots,
                   const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s) {
   if (n_grid == 0) return CINR_OK;
-  const int smem = mlp_floats<IN, H>() * 4;
-  auto k = decode_kernel<IN, H>;
-  CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  auto k = decode_kernel<IN, H, MLPP>;
+  int smem = MLPP ? (int)sizeof(tc::TcSmem<IN, H>) : mlp_floats<IN, H>() * 4;
+  if (MLPP && smem < tc::kMinSmemPerCta) smem = tc::kMinSmemPerCta;  // <= 8 TMEM users per SM
+  static int per_sm = 0;
+  if (!per_sm) {
+    CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem));
+    if (per_sm < 1) return set_error(CINR_ERR_CUDA, "decode kernel cannot be resident");
+  }
   const int S3 = c.S * c.S * c.S;
-  dim3 grid((S3 + 127) / 128, n_grid);
-  k<<<grid, 128, smem, s>>>(q, c, keys, slots, n_dev, n_grid);
+  const long work = (long)n_grid * ((S3 + 127) / 128);
+  long grid = (long)per_sm * num_sms();
+  if (grid > work) grid = work;
+  k<<<(unsigned)grid, 128, smem, s>>>(inr->dev, c, inr->w16, keys, slots, n_dev, n_grid,
+                                      reinterpret_cast<int*>(inr->scratch + 16));
   CINR_CK(cudaGetLastError());
   return CINR_OK;
 }
 
-int decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys, const uint32_t* slots,
-           const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s) {
+template <int MLPP>
+int decode_prec(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys, const uint32_t* slots,
+                const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s) {
   switch (shape_of(inr->dev.IN, inr->dev.H)) {
-    case Shape::S16x32: return launch_decode<16, 32>(inr->dev, c, keys, slots, n_dev, n_grid, s);
-    case Shape::S32x64: return launch_decode<32, 64>(inr->dev, c, keys, slots, n_dev, n_grid, s);
-    case Shape::S48x64: return launch_decode<48, 64>(inr->dev, c, keys, slots, n_dev, n_grid, s);
+    case Shape::S16x32: return launch_decode<16, 32, MLPP>(inr, c, keys, slots, n_dev, n_grid, s);
+    case Shape::S32x64: return launch_decode<32, 64, MLPP>(inr, c, keys, slots, n_dev, n_grid, s);
+    case Shape::S48x64: return launch_decode<48, 64, MLPP>(inr, c, keys, slots, n_dev, n_grid, s);
     default: return set_error(CINR_ERR_ARG, "unsupported shape");
   }
+}
+
+int decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys, const uint32_t* slots,
+           const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s) {
+  if (inr->p.mlp_precision == CINR_PREC_FP16) return decode_prec<1>(inr, c, keys, slots, n_dev, n_grid, s);
+  if (inr->p.mlp_precision == CINR_PREC_BF16) return decode_prec<2>(inr, c, keys, slots, n_dev, n_grid, s);
+  return decode_prec<0>(inr, c, keys, slots, n_dev, n_grid, s);
 }
 
 }  // namespace

@@ -21,6 +21,7 @@
 #include <mutex>
 
 #include "cinr_internal.cuh"
+#include "tc_mlp.cuh"
 
 using namespace cinr;
 
@@ -56,7 +57,13 @@ struct FrameParams {
   uint32_t* miss_rec;
   uint32_t miss_cap;
   uint32_t* miss_count;
+  const uint16_t* w16;  // half-precision MLP weights (tensor-core path)
+  int* err;             // set when a bounded device-side wait gives up
 };
+
+// Bytes of the frame kernel's shared memory before the MLP region (TF,
+// miss batch, values, bookkeeping); a multiple of 128.
+constexpr int kFrameSmemHead = (256 + 128) * 16 + 128 * 4 + 32 * 4;
 
 __device__ __forceinline__ float4 tf_lookup(const float4* s_tf, float v) {
   v = clamp01(v);
@@ -99,15 +106,17 @@ __device__ __forceinline__ float brick_sample(const CacheDev& c, int l, uint32_t
   return fmaf(f[2], y1 - y0, y0);
 }
 
-template <int IN, int H, bool CACHED>
-__global__ void __launch_bounds__(kFrameThreads, CACHED ? 6 : 4)
+// MLPP: 0 = FP32 SIMT MLP, 1 = FP16 tensor cores, 2 = BF16 tensor cores.
+template <int IN, int H, bool CACHED, int MLPP>
+__global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
     frame_kernel(const __grid_constant__ FrameParams P) {
-  extern __shared__ float4 smem4[];
+  extern __shared__ __align__(1024) float4 smem4[];
   float4* s_tf = smem4;                                   // 256
   float4* s_miss = s_tf + 256;                            // 128
   float* s_val = reinterpret_cast<float*>(s_miss + 128);  // 128
   int* s_i = reinterpret_cast<int*>(s_val + 128);         // 32 ints of bookkeeping
-  float* sw = reinterpret_cast<float*>(s_i + 32);         // MLP weights
+  float* sw = reinterpret_cast<float*>(s_i + 32);         // MLP weights (FP32 path)
+  tc::TcSmem<IN, H>& tcs = *reinterpret_cast<tc::TcSmem<IN, H>*>(s_i + 32);  // tensor-core path
   int* s_cnt = s_i;        // [2][4] per-warp miss counts (double buffered)
   int* s_act = s_i + 8;    // [2][4] per-warp active flags
   int* s_pix = s_i + 16;   // [4] pixel of each warp's ray
@@ -116,8 +125,14 @@ __global__ void __launch_bounds__(kFrameThreads, CACHED ? 6 : 4)
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
-  load_weights(sw, P.inr.w, mlp_floats<IN, H>());
-  __syncthreads();
+  uint32_t phase = 0;
+  if (MLPP) {
+    tc::load_tc_weights(tcs, P.w16, P.inr.w);
+    tc::tc_setup(tcs);
+  } else {
+    load_weights(sw, P.inr.w, mlp_floats<IN, H>());
+    __syncthreads();
+  }
 
   const CamDev& cam = P.cam;
   int state = 0;  // 0 needs a ray, 1 marching, 2 no rays left
@@ -260,9 +275,17 @@ __global__ void __launch_bounds__(kFrameThreads, CACHED ? 6 : 4)
       }
       if (tid == 0 && P.miss_rec) s_mbase[parity] = (int)atomicAdd(P.miss_count, (uint32_t)total);
       __syncthreads();
-      if (tid < total) {
-        const float4 m = s_miss[tid];
-        const float r = inr_raw_fp32<IN, H>(P.inr, sw, m.x, m.y, m.z);
+      const bool mine = tid < total;
+      float r = 0.f;
+      const float4 m = mine ? s_miss[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (MLPP == 0) {
+        if (mine) r = inr_raw_fp32<IN, H>(P.inr, sw, m.x, m.y, m.z);
+      } else {
+        float feat[IN];
+        if (mine) encode_point<IN / 2>(P.inr, m.x, m.y, m.z, feat);
+        r = tc::mlp_tile<IN, H, MLPP == 2>(tcs, feat, mine, phase, P.err);
+      }
+      if (mine) {
         const int slot = __float_as_int(m.w);
         s_val[slot] = fmaf(P.inr.vscale, r, P.inr.vmin);
         if (P.miss_rec) {
@@ -316,6 +339,8 @@ __global__ void __launch_bounds__(kFrameThreads, CACHED ? 6 : 4)
       }
     }
   }
+
+  if (MLPP) tc::tc_teardown(tcs);
 
   // ---- per-CTA statistics
   unsigned long long a[6] = {n_samp, n_hit, n_fb, n_miss, n_req, n_slot};
@@ -401,10 +426,12 @@ int num_sms() {
   return n;
 }
 
-template <int IN, int H, bool CACHED>
+template <int IN, int H, bool CACHED, int MLPP>
 int launch_frame(const FrameParams& P, cudaStream_t s) {
-  auto k = frame_kernel<IN, H, CACHED>;
-  const int smem = (256 + 128) * 16 + 128 * 4 + 32 * 4 + mlp_floats<IN, H>() * 4;
+  auto k = frame_kernel<IN, H, CACHED, MLPP>;
+  int smem = kFrameSmemHead + (MLPP ? (int)sizeof(tc::TcSmem<IN, H>) : mlp_floats<IN, H>() * 4);
+  // tensor-core path: at most 8 CTAs (8 x 64 TMEM columns) per SM
+  if (MLPP && smem < tc::kMinSmemPerCta) smem = tc::kMinSmemPerCta;
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -416,14 +443,22 @@ int launch_frame(const FrameParams& P, cudaStream_t s) {
   return CINR_OK;
 }
 
-template <bool CACHED>
-int launch_frame_shape(const FrameParams& P, cudaStream_t s) {
+template <bool CACHED, int MLPP>
+int launch_frame_prec(const FrameParams& P, cudaStream_t s) {
   switch (shape_of(P.inr.IN, P.inr.H)) {
-    case Shape::S16x32: return launch_frame<16, 32, CACHED>(P, s);
-    case Shape::S32x64: return launch_frame<32, 64, CACHED>(P, s);
-    case Shape::S48x64: return launch_frame<48, 64, CACHED>(P, s);
+    case Shape::S16x32: return launch_frame<16, 32, CACHED, MLPP>(P, s);
+    case Shape::S32x64: return launch_frame<32, 64, CACHED, MLPP>(P, s);
+    case Shape::S48x64: return launch_frame<48, 64, CACHED, MLPP>(P, s);
     default: return set_error(CINR_ERR_ARG, "unsupported shape");
   }
+}
+
+// mlp_precision: CINR_PREC_FP32 -> SIMT, FP16 / BF16 -> tensor cores.
+template <bool CACHED>
+int launch_frame_shape(const FrameParams& P, int mlp_precision, cudaStream_t s) {
+  if (mlp_precision == CINR_PREC_FP16) return launch_frame_prec<CACHED, 1>(P, s);
+  if (mlp_precision == CINR_PREC_BF16) return launch_frame_prec<CACHED, 2>(P, s);
+  return launch_frame_prec<CACHED, 0>(P, s);
 }
 
 struct RendererLayout {
@@ -498,7 +533,10 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
   CINR_CK(cudaMemsetAsync(r->stats, 0, ST_COUNT * 8, s));
   if (cache) CINR_CK(cudaMemsetAsync(cache->dev.touched_count, 0, 4, s));
   CINR_CK(cudaEventRecord(r->ev[0], s));
-  int e = cache ? launch_frame_shape<true>(P, s) : launch_frame_shape<false>(P, s);
+  P.w16 = inr->w16;
+  P.err = reinterpret_cast<int*>(r->counters + 2);
+  int e = cache ? launch_frame_shape<true>(P, inr->p.mlp_precision, s)
+                : launch_frame_shape<false>(P, inr->p.mlp_precision, s);
   if (e) return e;
   CINR_CK(cudaEventRecord(r->ev[1], s));
   if (cache) {
@@ -507,10 +545,12 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
   }
   CINR_CK(cudaEventRecord(r->ev[2], s));
   unsigned long long h[ST_COUNT];
-  uint32_t rec = 0;
+  uint32_t cnt[3] = {0, 0, 0};  // ray counter, miss-record count, device error word
   CINR_CK(cudaMemcpyAsync(h, r->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
-  CINR_CK(cudaMemcpyAsync(&rec, r->counters + 1, 4, cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaMemcpyAsync(cnt, r->counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
   CINR_CK(cudaStreamSynchronize(s));
+  const uint32_t rec = cnt[1];
+  if (cnt[2]) return set_error(CINR_ERR_TIMEOUT, "a bounded device-side wait gave up in the frame kernel");
   if (stats) {
     stats->samples = h[ST_SAMPLES];
     stats->inr_queries_direct = h[ST_DIRECT];
@@ -740,7 +780,9 @@ extern "C" int cinr_render_frame_noalloc(cinr_inr_t inr, const cinr_camera* cam,
   // The array keeps the previous call's contents: counters and statistics
   // must start at zero.
   CINR_CK(cudaMemsetAsync(scratch, 0, kNoAllocHeader, s));
-  e = launch_frame_shape<false>(P, s);
+  P.w16 = inr->w16;
+  P.err = reinterpret_cast<int*>(counters + 2);
+  e = launch_frame_shape<false>(P, inr->p.mlp_precision, s);
   if (e) return e;
   unsigned long long h[ST_COUNT];
   CINR_CK(cudaMemcpyAsync(out_rgba_host, image, (size_t)cam->width * cam->height * sizeof(float4),

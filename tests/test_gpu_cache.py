@@ -14,11 +14,11 @@ pytestmark = pytest.mark.gpu
 
 def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_req=40, ranking=1,
          preload=1, lod_scale=1.0, lod_mode=0, storage="fp32", K=32, eps=0.0, check_pixels=2e-3,
-         cam_fn=None):
+         cam_fn=None, mlp="fp32", tab="fp32"):
     from paper_2504_18001_gb300 import cinr
     cfg = S.INR_64
     table, w = scene(cfg)
-    inr = gpu_inr(cfg, table, w, vol=vol)
+    inr = gpu_inr(cfg, table, w, vol=vol, mlp=mlp, tab=tab)
     p = oracle_inr(cfg, table, w, vol=vol)
     S3 = (brick + 2) ** 3
     cache = cinr.Cache(inr, vol, pool_bytes=slots * S3 * (2 if storage == "fp16" else 4),
@@ -50,6 +50,7 @@ def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_r
         om = sorted_pairs(oc.dump(O.DUMP_MISS))
         assert np.array_equal(gm, om), (f, len(gm), len(om))
         err = float(np.abs(img.cpu().numpy() - ref).max())
+        st["psnr"] = O.psnr(img.cpu().numpy().astype(np.float64), ref)
         worst = max(worst, err)
         if check_pixels is not None:
             assert err < check_pixels, (f, err)

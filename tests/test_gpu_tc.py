@@ -64,3 +64,34 @@ def test_tensor_core_inference_error(prec, cfg):
     assert np.abs(v32 - ref).max() < 1e-4
     assert err < (1e-2 if prec == "fp16" else 5e-2), err
     assert np.mean(np.abs(v - ref)) < (2e-3 if prec == "fp16" else 1e-2)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_uncached_render_tensor_core_mlp(prec):
+    from paper_2504_18001_gb300 import cinr
+    from _scenes import ocam
+    vol = (64, 64, 64)
+    cfg = S.INR_64
+    table, w = scene(cfg)
+    inr = gpu_inr(cfg, table, w, vol=vol, mlp=prec)
+    p = oracle_inr(cfg, table, w, vol=vol)
+    cam = S.orbit_camera(5, 64, 48)
+    tf = S.tf_ramps(2)
+    r = cinr.Renderer(64, 48, vol, K=32, eps_T=0.0)
+    img, st = r.render(inr, cam, tf)
+    ref, rst = O.render_direct(p, table, w, ocam(cam), vol, O.march_opts(K=32, eps_T=0.0),
+                               tf.astype(np.float64))
+    assert st["samples"] == rst["samples"]
+    err = np.abs(img.cpu().numpy() - ref).max()
+    assert err < (2e-2 if prec == "fp16" else 6e-2), err
+    assert O.psnr(img.cpu().numpy().astype(np.float64), ref) > 40.0
+
+
+def test_cached_mixed_precision_state_exact_and_psnr():
+    # FP16 hash table, BF16 tensor-core MLP, FP16 bricks: discrete cache state
+    # stays bit-exact (it depends on geometry only); pixels within the stated
+    # error, PSNR >= 40 dB against the FP64 oracle image
+    from test_gpu_cache import _run
+    cache, oc, hist, worst = _run(4, storage="fp16", mlp="bf16", tab="fp16", check_pixels=None)
+    assert worst < 6e-2, worst
+    assert min(h["psnr"] for h in hist) > 40.0, [h["psnr"] for h in hist]
