@@ -109,15 +109,30 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def build_scene(args, device):
-    from paper_2504_18001_gb300 import cinr, synthetic as S
+def scene_weights(args):
+    from paper_2504_18001_gb300 import synthetic as S
     cfg = S.INR_512
-    table, w = S.inr_init(cfg, seed=args.seed, table_scale=1e-4, level_decay=args.level_decay)
-    inr = cinr.Inr(cinr.make_inr_params(cfg), table, w, device=device)
+    table, w = S.inr_init(cfg, seed=args.seed, table_scale=1.0, level_decay=args.level_decay)
+    return cfg, table, w
+
+
+def build_scene(args, device):
+    """The uncached baseline INR (FP32 table, FP32 SIMT MLP) and the INR of
+    the cached path (mixed: FP16 table + BF16 tensor-core MLP; or FP32)."""
+    from paper_2504_18001_gb300 import cinr
+    cfg, table, w = scene_weights(args)
     vol = (512, 512, 512)
-    lo, hi = inr.raw_range(vol, stride=8)
-    inr.set_range(-lo / (hi - lo), (1.0 - lo) / (hi - lo))
-    return cfg, table, w, inr, vol
+
+    def make(mlp, tab):
+        inr = cinr.Inr(cinr.make_inr_params(cfg, mlp_precision=mlp, table_precision=tab), table, w,
+                       device=device)
+        lo, hi = inr.raw_range(vol, stride=8)
+        inr.set_range(-lo / (hi - lo), (1.0 - lo) / (hi - lo))
+        return inr
+
+    inr32 = make("fp32", "fp32")
+    inr_c = make("bf16", "fp16") if args.precision == "mixed" else inr32
+    return cfg, table, w, inr32, inr_c, vol
 
 
 def run_gpu(args):
@@ -133,9 +148,10 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
     W = H = args.res
-    cfg, table, w, inr, vol = build_scene(args, device)
+    cfg, table, w, inr32, inr_c, vol = build_scene(args, device)
+    storage = "fp16" if args.precision == "mixed" else "fp32"
     S3 = (args.brick + 2) ** 3
-    cache = cinr.Cache(inr, vol, pool_bytes=args.pool_mib << 20, brick=args.brick, levels=4,
+    cache = cinr.Cache(inr_c, vol, pool_bytes=args.pool_mib << 20, brick=args.brick, levels=4, storage=storage,
                        n_req=args.n_req, ranking=1, preload=1, device=device)
     rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
                          seed=args.seed, device=device)
@@ -148,7 +164,10 @@ def run_gpu(args):
         flush.random_(0, 255)  # L2 flush between timed iterations
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, st = rend.render(inr, cam, tf, cache=cache if use_cache else None, out=img)
+        if use_cache:
+            _, st = rend.render(inr_c, cam, tf, cache=cache, out=img)
+        else:
+            _, st = rend.render(inr32, cam, tf, cache=None, out=img)
         e1.record(stream)
         return e0, e1, st
 
@@ -192,7 +211,7 @@ def run_gpu(args):
         flush.random_(0, 255)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rend.render_host(inr, cam, tf, host, cache=cache)
+        rend.render_host(inr_c, cam, tf, host, cache=cache)
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = float(sum(e2e)) / len(e2e)
 
@@ -210,7 +229,7 @@ def run_gpu(args):
     # algorithmic bytes of the marching kernel: every distinct brick that
     # served a sample read once from HBM (+ its page-table entry) and the
     # image written once
-    elem = 4
+    elem = 2 if args.precision == "mixed" else 4
     alg_bytes = [sl * (S3 * elem + 4) + W * H * 16 for sl in slots]
     achieved = sum(alg_bytes) / (sum(k_ms) * 1e-3) / 1e9
     un_q = sum(s["inr_queries_direct"] for s in un_st)
@@ -225,9 +244,12 @@ def run_gpu(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "bf16" if args.precision == "mixed" else "f32",
         "data": "synthetic (seeded INR, orbit camera, seeded TF ramps)",
-        "config": {"workload": "cached_fp32_512cube_1024px_orbit", "volume": list(vol),
+        "config": {"workload": f"cached_{args.precision}_512cube_1024px_orbit", "volume": list(vol),
+                   "cached_path": ("FP16 table + FP16 bricks + BF16 tensor-core MLP (FP32 accumulate)"
+                                   if args.precision == "mixed" else "FP32"),
+                   "uncached_path": "FP32 table + FP32 SIMT MLP",
                    "image": [W, H], "inr": "L16 F2 T2^19 Nmin16 b1.38 MLP32-64-64-1",
                    "brick": args.brick, "lods": 4, "pool_mib": args.pool_mib,
                    "n_req": args.n_req, "lod_scale": args.lod_scale, "K": 32, "eps_T": 1e-3,
@@ -308,8 +330,7 @@ def run_reference(args):
         return None
     import oracle as O
     from paper_2504_18001_gb300 import synthetic as S
-    cfg = S.INR_512
-    table, w = S.inr_init(cfg, seed=args.seed, table_scale=1e-4, level_decay=args.level_decay)
+    cfg, table, w = scene_weights(args)
     p = O.inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden)
     vol = (512, 512, 512)
     lo, hi = O.inr_raw_range(p, table, w, vol, 32)
@@ -353,6 +374,7 @@ def main():
     ap.add_argument("--pool-mib", type=int, default=1024)
     ap.add_argument("--n-req", type=int, default=4096)
     ap.add_argument("--level-decay", type=float, default=0.5)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
     ap.add_argument("--lod-scale", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--uncached-steps", type=int, default=5)

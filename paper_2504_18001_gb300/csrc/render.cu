@@ -126,11 +126,15 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
   uint32_t phase = 0;
+  // With a cache, true misses are rare (none once the coarsest LoD is
+  // preloaded): their MLP reads the FP32 weights through L1 and the shared
+  // memory stays small, leaving the SM's L1 to the brick voxels.
+  const float* wmlp = CACHED ? P.inr.w : sw;
   if (MLPP) {
     tc::load_tc_weights(tcs, P.w16, P.inr.w);
     tc::tc_setup(tcs);
   } else {
-    load_weights(sw, P.inr.w, mlp_floats<IN, H>());
+    if (!CACHED) load_weights(sw, P.inr.w, mlp_floats<IN, H>());
     __syncthreads();
   }
 
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
       float r = 0.f;
       const float4 m = mine ? s_miss[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
       if (MLPP == 0) {
-        if (mine) r = inr_raw_fp32<IN, H>(P.inr, sw, m.x, m.y, m.z);
+        if (mine) r = inr_raw_fp32<IN, H>(P.inr, wmlp, m.x, m.y, m.z);
       } else {
         float feat[IN];
         if (mine) encode_point<IN / 2>(P.inr, m.x, m.y, m.z, feat);
@@ -429,7 +433,7 @@ int num_sms() {
 template <int IN, int H, bool CACHED, int MLPP>
 int launch_frame(const FrameParams& P, cudaStream_t s) {
   auto k = frame_kernel<IN, H, CACHED, MLPP>;
-  int smem = kFrameSmemHead + (MLPP ? (int)sizeof(tc::TcSmem<IN, H>) : mlp_floats<IN, H>() * 4);
+  int smem = kFrameSmemHead + (MLPP ? (int)sizeof(tc::TcSmem<IN, H>) : (CACHED ? 0 : mlp_floats<IN, H>() * 4));
   // tensor-core path: at most 8 CTAs (8 x 64 TMEM columns) per SM
   if (MLPP && smem < tc::kMinSmemPerCta) smem = tc::kMinSmemPerCta;
   static int blocks_per_sm = 0;
@@ -453,9 +457,12 @@ int launch_frame_prec(const FrameParams& P, cudaStream_t s) {
   }
 }
 
-// mlp_precision: CINR_PREC_FP32 -> SIMT, FP16 / BF16 -> tensor cores.
+// mlp_precision: CINR_PREC_FP32 -> SIMT, FP16 / BF16 -> tensor cores
+// (uncached frames; cached frames infer their rare true misses with the
+// FP32 weights, see frame_kernel).
 template <bool CACHED>
 int launch_frame_shape(const FrameParams& P, int mlp_precision, cudaStream_t s) {
+  if constexpr (CACHED) return launch_frame_prec<CACHED, 0>(P, s);
   if (mlp_precision == CINR_PREC_FP16) return launch_frame_prec<CACHED, 1>(P, s);
   if (mlp_precision == CINR_PREC_BF16) return launch_frame_prec<CACHED, 2>(P, s);
   return launch_frame_prec<CACHED, 0>(P, s);
