@@ -154,6 +154,7 @@ def run_gpu(args):
     cache = cinr.Cache(inr_c, vol, pool_bytes=args.pool_mib << 20, brick=args.brick, levels=4, storage=storage,
                        n_req=args.n_req, ranking=1, preload=1, device=device)
     rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
+                         ray_layout=args.ray_layout,
                          seed=args.seed, device=device)
     img = torch.empty((H, W, 4), dtype=torch.float32, device=device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > L2 (129 MB)
@@ -253,6 +254,7 @@ def run_gpu(args):
                    "image": [W, H], "inr": "L16 F2 T2^19 Nmin16 b1.38 MLP32-64-64-1",
                    "brick": args.brick, "lods": 4, "pool_mib": args.pool_mib,
                    "n_req": args.n_req, "lod_scale": args.lod_scale, "K": 32, "eps_T": 1e-3,
+                   "ray_layout": "thread per ray" if args.ray_layout == 0 else "warp per ray",
                    "l2": "flushed (256 MiB write) before every timed frame",
                    "parallelism": f"replicas x{world}"},
         "inr_queries_per_s": (q_direct + q_decode) / (sum(ms) * 1e-3),
@@ -366,8 +368,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=40)
+    # default: frames 90-149 timed (the last 30 orbit frames and the 30
+    # transfer-function edits) after 90 warm-up frames fill the cache, the
+    # steady state the paper measures (mean over the last frames of a run)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=90)
     ap.add_argument("--impl", default="cinr", choices=["cinr", "reference"])
     ap.add_argument("--res", type=int, default=1024)
     ap.add_argument("--brick", type=int, default=8)
@@ -375,6 +380,7 @@ def main():
     ap.add_argument("--n-req", type=int, default=4096)
     ap.add_argument("--level-decay", type=float, default=0.5)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
+    ap.add_argument("--ray-layout", type=int, default=0, choices=[0, 1])
     ap.add_argument("--lod-scale", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--uncached-steps", type=int, default=5)

@@ -98,7 +98,11 @@ typedef struct {
  * is the user LoD scale (Sec. 4.3.4, Sec. 5.3); seed seeds the per-frame
  * xorshift dither (Sec. 5.3).  miss_record_cap > 0 keeps the first
  * miss_record_cap true misses of each frame as (pixel, sample) pairs for
- * cinr_debug_dump (CINR_DUMP_MISSES). */
+ * cinr_debug_dump (CINR_DUMP_MISSES).  ray_layout selects how cached frames
+ * map rays to threads: 0 = one ray per thread (tiles of 32 neighbouring
+ * rays per warp), 1 = one ray per warp (32-sample segments per warp); both
+ * produce the same sample set and cache state.  Uncached frames always use
+ * one ray per warp (128-sample batches feed the tensor-core MLP). */
 typedef struct {
   int dims[3];
   int K;
@@ -107,6 +111,7 @@ typedef struct {
   float lod_scale;
   uint64_t seed;
   long miss_record_cap;
+  int ray_layout;
 } cinr_march_opts;
 
 /* Cache options (Sec. 4.3): brick = interior edge B (stored with a one-voxel

@@ -365,6 +365,198 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
   }
 }
 
+// Cached frames, thread per ray.  A warp takes a tile of 32 neighbouring rays
+// (an 8 x 4 pixel block, so the lanes' samples at equal index lie in the
+// same bricks) and each lane marches its ray sample by sample: stochastic
+// LoD, page-table walk with fallback, ranked requests and LRU stamps
+// aggregated over the lanes that name the same brick or slot, trilinear
+// sampling, sequential front-to-back compositing and termination after every
+// K samples.  A true miss (rare: none once the coarsest LoD is preloaded) is
+// inferred in place by its lane with the FP32 weights (read through L1) and
+// recorded in the miss list with one atomic per warp.  No CTA barrier: warps
+// never wait for each other.  The discrete state and the sample set are those
+// of the segment-wise formulation.
+int num_sms();
+
+// A true miss of the thread-per-ray kernel: the INR at x with FP32 weights
+// read through L1.  Kept out of line so that its registers (and spills)
+// stay off the marching loop.
+template <int IN, int H>
+__device__ __noinline__ float infer_miss(const InrDev& q, float x, float y, float z) {
+  return fmaf(q.vscale, inr_raw_fp32<IN, H>(q, q.w, x, y, z), q.vmin);
+}
+
+template <int IN, int H>
+__global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __grid_constant__ FrameParams P) {
+  __shared__ float4 s_tf[256];
+  for (int i = threadIdx.x; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const CamDev& cam = P.cam;
+  const CacheDev& c = P.cache;
+  uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0;
+  const uint32_t n_tiles = P.n_rays >> 5;
+  while (true) {
+    uint32_t tile = 0;
+    if (lane == 0) tile = atomicAdd(P.ray_counter, 1u);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= n_tiles) break;
+    const uint32_t r = tile * 32u + (uint32_t)lane;  // ray index in 8x8 tiles
+    const uint32_t t64 = r >> 6, w = r & 63u;
+    const int px = (int)((t64 % P.tiles_x) * 8 + (w & 7u));
+    const int py = (int)((t64 / P.tiles_x) * 8 + (w >> 3));
+    const bool inside = px < cam.W && py < cam.H;
+    const uint32_t pixel = inside ? (uint32_t)(py * cam.W + px) : 0u;
+    float d[3], tn = 0.f, tf = 0.f;
+    bool active = inside && ray_setup(cam, px, py, d, tn, tf);
+    if (inside && !active) P.out[pixel] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t rseed = ray_seed(P.fseed, pixel);
+    float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
+    int k = 0;
+    while (__any_sync(kFull, active)) {
+      float x[3], tm = 0.f, len = 0.f, v = 0.f;
+      bool has = false;
+      if (active) {
+        has = sample_at(cam, d, tn, tf, k, x, tm, len);
+        if (!has) {
+          P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
+          active = false;
+        }
+      }
+      bool want_req = false, hit = false, miss = false;
+      uint32_t req_key = 0, hit_slot = 0;
+      if (has) {
+        ++n_samp;
+        const int l = sample_lod(cam, c.L, 0, rseed, (uint32_t)k, tm);
+        float pv[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) pv[a] = f_mul(x[a], (float)c.vol[a]);
+        for (int lev = l; lev < c.L; ++lev) {
+          const float sc = 1.0f / (float)(1 << lev);
+          float s[3];
+          int b[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            s[a] = f_mul(pv[a], sc);
+            const float q = c.invB > 0.0f ? f_mul(s[a], c.invB) : f_div(s[a], (float)c.B);
+            int bi = (int)floorf(q);
+            bi = bi < 0 ? 0 : (bi > c.nb[lev][a] - 1 ? c.nb[lev][a] - 1 : bi);
+            b[a] = bi;
+          }
+          const uint32_t key = c.off[lev] + (uint32_t)b[0] +
+                               (uint32_t)c.nb[lev][0] * ((uint32_t)b[1] + (uint32_t)c.nb[lev][1] * (uint32_t)b[2]);
+          const uint32_t e = __ldg(c.pt + key);
+          if (!(e & kMapped)) {
+            if (lev == l) {
+              want_req = true;
+              req_key = key;
+            }
+            continue;
+          }
+          hit_slot = e & ~kMapped;
+          v = brick_sample(c, lev, hit_slot, b, s);
+          hit = true;
+          if (lev == l)
+            ++n_hit;
+          else
+            ++n_fb;
+          break;
+        }
+        if (!hit) {
+          miss = true;
+          ++n_miss;
+        }
+      }
+      const unsigned rq = __ballot_sync(kFull, want_req);
+      if (want_req) {
+        const unsigned peers = __match_any_sync(rq, req_key);
+        if (lane == __ffs(peers) - 1) {
+          const uint32_t old = atomicMax(c.rank + req_key, P.Tf);
+          if (old < P.Tf) {
+            ++n_req;
+            c.touched[atomicAdd(c.touched_count, 1u)] = req_key;
+          }
+          atomicAdd(c.rank + req_key, (uint32_t)__popc(peers));
+          atomicMin(c.rank + req_key, P.Tf + 1000u);
+        }
+      }
+      const bool stale = hit && c.stamp[hit_slot] != P.frame;
+      const unsigned hm = __ballot_sync(kFull, stale);
+      if (stale) {
+        const unsigned peers = __match_any_sync(hm, hit_slot);
+        if (lane == __ffs(peers) - 1 && atomicExch(c.stamp + hit_slot, P.frame) != P.frame) ++n_slot;
+      }
+      const unsigned mm = __ballot_sync(kFull, miss);
+      if (mm) {
+        if (miss) v = infer_miss<IN, H>(P.inr, x[0], x[1], x[2]);
+        if (P.miss_rec) {
+          uint32_t base = 0;
+          if (lane == 0) base = atomicAdd(P.miss_count, (uint32_t)__popc(mm));
+          base = __shfl_sync(kFull, base, 0);
+          if (miss) {
+            const uint32_t at = base + (uint32_t)__popc(mm & ((1u << lane) - 1u));
+            if (at < P.miss_cap) {
+              P.miss_rec[2 * at] = pixel;
+              P.miss_rec[2 * at + 1] = (uint32_t)k;
+            }
+          }
+        }
+      }
+      if (has) {
+        const float4 e4 = tf_lookup(s_tf, v);
+        const float alpha = 1.0f - expf(-e4.w * len);
+        const float wgt = T * alpha;
+        Cr = fmaf(wgt, e4.x, Cr);
+        Cg = fmaf(wgt, e4.y, Cg);
+        Cb = fmaf(wgt, e4.z, Cb);
+        T *= 1.0f - alpha;
+        ++k;
+        if ((k % P.K) == 0 && T < P.eps) {
+          P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
+          active = false;
+        }
+      }
+    }
+  }
+  unsigned long long a[6] = {n_samp, n_hit, n_fb, n_miss, n_req, n_slot};
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+    for (int o = 16; o > 0; o >>= 1) a[j] += __shfl_xor_sync(kFull, a[j], o);
+  if (lane == 0) {
+    if (a[0]) atomicAdd(P.stats + ST_SAMPLES, a[0]);
+    if (a[1]) atomicAdd(P.stats + ST_HITS, a[1]);
+    if (a[2]) atomicAdd(P.stats + ST_FALLBACK, a[2]);
+    if (a[3]) {
+      atomicAdd(P.stats + ST_MISSES, a[3]);
+      atomicAdd(P.stats + ST_DIRECT, a[3]);
+    }
+    if (a[4]) atomicAdd(P.stats + ST_REQ, a[4]);
+    if (a[5]) atomicAdd(P.stats + ST_SLOTS, a[5]);
+  }
+}
+
+template <int IN, int H>
+int launch_march_cached(const FrameParams& P, cudaStream_t s) {
+  auto k = march_cached_kernel<IN, H>;
+  static int blocks_per_sm = 0;
+  if (!blocks_per_sm) {
+    CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
+    if (blocks_per_sm < 1) return set_error(CINR_ERR_CUDA, "march kernel cannot be resident");
+  }
+  k<<<(unsigned)(blocks_per_sm * num_sms()), kFrameThreads, 0, s>>>(P);
+  CINR_CK(cudaGetLastError());
+  return CINR_OK;
+}
+
+int launch_march_cached_shape(const FrameParams& P, cudaStream_t s) {
+  switch (shape_of(P.inr.IN, P.inr.H)) {
+    case Shape::S16x32: return launch_march_cached<16, 32>(P, s);
+    case Shape::S32x64: return launch_march_cached<32, 64>(P, s);
+    case Shape::S48x64: return launch_march_cached<48, 64>(P, s);
+    default: return set_error(CINR_ERR_ARG, "unsupported shape");
+  }
+}
+
 // ----------------------------------------------------------- host side
 void normalize3(const float a[3], float out[3]) {
   float l2 = a[0] * a[0] + a[1] * a[1];
@@ -495,6 +687,7 @@ int check_opts(int W, int H, const cinr_march_opts* o) {
   if (o->miss_record_cap < 0 || o->miss_record_cap > (1l << 30))
     return set_error(CINR_ERR_ARG, "bad miss_record_cap");
   if (o->lod_mode != 0 && o->lod_mode != 1) return set_error(CINR_ERR_ARG, "bad lod_mode");
+  if (o->ray_layout != 0 && o->ray_layout != 1) return set_error(CINR_ERR_ARG, "bad ray_layout");
   return CINR_OK;
 }
 
@@ -542,8 +735,13 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
   CINR_CK(cudaEventRecord(r->ev[0], s));
   P.w16 = inr->w16;
   P.err = reinterpret_cast<int*>(r->counters + 2);
-  int e = cache ? launch_frame_shape<true>(P, inr->p.mlp_precision, s)
-                : launch_frame_shape<false>(P, inr->p.mlp_precision, s);
+  int e;
+  if (!cache)
+    e = launch_frame_shape<false>(P, inr->p.mlp_precision, s);
+  else if (r->o.ray_layout == 1)
+    e = launch_frame_shape<true>(P, inr->p.mlp_precision, s);
+  else
+    e = launch_march_cached_shape(P, s);
   if (e) return e;
   CINR_CK(cudaEventRecord(r->ev[1], s));
   if (cache) {

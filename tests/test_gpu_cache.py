@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_req=40, ranking=1,
          preload=1, lod_scale=1.0, lod_mode=0, storage="fp32", K=32, eps=0.0, check_pixels=2e-3,
-         cam_fn=None, mlp="fp32", tab="fp32"):
+         cam_fn=None, mlp="fp32", tab="fp32", ray_layout=0):
     from paper_2504_18001_gb300 import cinr
     cfg = S.INR_64
     table, w = scene(cfg)
@@ -29,6 +29,7 @@ def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_r
     oc = O.Cache(p, table, w, vol, brick, levels, slots, mo, n_req=n_req, ranking=ranking,
                  preload=preload)
     r = cinr.Renderer(W, H, vol, K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
+                      ray_layout=ray_layout,
                       miss_record_cap=W * H * 4000)
     tf = S.tf_ramps(2)
     worst = 0.0
@@ -112,3 +113,30 @@ def test_fully_resident_cache_is_trilinear_of_voxel_centres():
                                   lod_scale=0.0, levels=2)
     assert hist[-1]["bricks_requested"] == 0
     assert hist[-1]["hits"] == hist[-1]["samples"]
+
+
+@pytest.mark.parametrize("preload", [1, 0])
+def test_cached_warp_per_ray_layout(preload):
+    # the one-ray-per-warp layout produces the same state, misses and pixels
+    _run(4, ray_layout=1, preload=preload, slots=60 if preload else 400, n_req=40)
+
+
+def test_cached_early_termination_both_layouts_agree():
+    # with eps_T > 0 the two layouts composite in different FP32 orders; the
+    # sample sets may differ only for rays whose T sits within rounding of eps
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.INR_64
+    vol = (64, 64, 64)
+    table, w = scene(cfg)
+    inr = gpu_inr(cfg, table, w, vol=vol)
+    tf = S.tf_ramps(2) * np.array([1, 1, 1, 4], np.float32)
+    imgs, sts = [], []
+    for layout in (0, 1):
+        cache = cinr.Cache(inr, vol, pool_bytes=200 * 4000, brick=8, levels=3, n_req=64)
+        r = cinr.Renderer(64, 48, vol, K=32, eps_T=1e-3, ray_layout=layout)
+        for f in range(3):
+            img, st = r.render(inr, S.orbit_camera(f, 64, 48), tf, cache=cache)
+        imgs.append(img.cpu().numpy())
+        sts.append(st)
+    assert np.abs(imgs[0] - imgs[1]).max() < 2e-3
+    assert abs(sts[0]["samples"] - sts[1]["samples"]) <= 32 * 4
