@@ -386,14 +386,49 @@ __device__ __noinline__ float infer_miss(const InrDev& q, float x, float y, floa
   return fmaf(q.vscale, inr_raw_fp32<IN, H>(q, q.w, x, y, z), q.vmin);
 }
 
-template <int IN, int H>
+// Per-LoD constants of the cache, staged in shared memory (lanes of a warp
+// sit at different LoDs, so indexing them in the parameter space would
+// serialise the accesses).
+struct LevelGeo {
+  int nb0, nb1, nb2;
+  uint32_t off;
+  float dmax0, dmax1, dmax2;  // dims - 1
+  float scale;                // 2^-level, exact
+};
+
+template <bool F16POOL>
+__device__ __forceinline__ float pool_ld(const void* pool, size_t i) {
+  if (F16POOL) return __half2float(__ldg(reinterpret_cast<const __half*>(pool) + i));
+  return __ldg(reinterpret_cast<const float*>(pool) + i);
+}
+
+template <int IN, int H, bool F16POOL>
 __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __grid_constant__ FrameParams P) {
   __shared__ float4 s_tf[256];
+  __shared__ LevelGeo s_geo[kMaxLod];
+  const CacheDev& c = P.cache;
   for (int i = threadIdx.x; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
+  if (threadIdx.x < c.L) {
+    const int l = threadIdx.x;
+    LevelGeo g;
+    g.nb0 = c.nb[l][0];
+    g.nb1 = c.nb[l][1];
+    g.nb2 = c.nb[l][2];
+    g.off = c.off[l];
+    g.dmax0 = (float)(c.dims[l][0] - 1);
+    g.dmax1 = (float)(c.dims[l][1] - 1);
+    g.dmax2 = (float)(c.dims[l][2] - 1);
+    g.scale = __int_as_float((127 - l) << 23);
+    s_geo[l] = g;
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const CamDev& cam = P.cam;
-  const CacheDev& c = P.cache;
+  const float volf[3] = {(float)c.vol[0], (float)c.vol[1], (float)c.vol[2]};
+  const int L = c.L, B = c.B, S = c.S;
+  const float invB = c.invB, fB = (float)c.B;
+  const size_t S3 = (size_t)S * S * S;
+  const void* pool = c.pool;
   uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0;
   const uint32_t n_tiles = P.n_rays >> 5;
   while (true) {
@@ -412,7 +447,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
     if (inside && !active) P.out[pixel] = make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t rseed = ray_seed(P.fseed, pixel);
     float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
-    int k = 0;
+    int k = 0, seg = P.K;  // seg: samples left in the current K-segment
     while (__any_sync(kFull, active)) {
       float x[3], tm = 0.f, len = 0.f, v = 0.f;
       bool has = false;
@@ -427,24 +462,18 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
       uint32_t req_key = 0, hit_slot = 0;
       if (has) {
         ++n_samp;
-        const int l = sample_lod(cam, c.L, 0, rseed, (uint32_t)k, tm);
-        float pv[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) pv[a] = f_mul(x[a], (float)c.vol[a]);
-        for (int lev = l; lev < c.L; ++lev) {
-          const float sc = 1.0f / (float)(1 << lev);
-          float s[3];
-          int b[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            s[a] = f_mul(pv[a], sc);
-            const float q = c.invB > 0.0f ? f_mul(s[a], c.invB) : f_div(s[a], (float)c.B);
-            int bi = (int)floorf(q);
-            bi = bi < 0 ? 0 : (bi > c.nb[lev][a] - 1 ? c.nb[lev][a] - 1 : bi);
-            b[a] = bi;
-          }
-          const uint32_t key = c.off[lev] + (uint32_t)b[0] +
-                               (uint32_t)c.nb[lev][0] * ((uint32_t)b[1] + (uint32_t)c.nb[lev][1] * (uint32_t)b[2]);
+        const int l = sample_lod(cam, L, 0, rseed, (uint32_t)k, tm);
+        const float pv0 = f_mul(x[0], volf[0]), pv1 = f_mul(x[1], volf[1]), pv2 = f_mul(x[2], volf[2]);
+        for (int lev = l; lev < L; ++lev) {
+          const LevelGeo g = s_geo[lev];
+          const float s0 = f_mul(pv0, g.scale), s1 = f_mul(pv1, g.scale), s2 = f_mul(pv2, g.scale);
+          int b0 = (int)floorf(invB > 0.0f ? f_mul(s0, invB) : f_div(s0, fB));
+          int b1 = (int)floorf(invB > 0.0f ? f_mul(s1, invB) : f_div(s1, fB));
+          int b2 = (int)floorf(invB > 0.0f ? f_mul(s2, invB) : f_div(s2, fB));
+          b0 = min(max(b0, 0), g.nb0 - 1);
+          b1 = min(max(b1, 0), g.nb1 - 1);
+          b2 = min(max(b2, 0), g.nb2 - 1);
+          const uint32_t key = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
           const uint32_t e = __ldg(c.pt + key);
           if (!(e & kMapped)) {
             if (lev == l) {
@@ -454,7 +483,23 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
             continue;
           }
           hit_slot = e & ~kMapped;
-          v = brick_sample(c, lev, hit_slot, b, s);
+          // trilinear inside the stored brick (apron included)
+          const float q0 = fminf(fmaxf(f_sub(s0, 0.5f), 0.0f), g.dmax0);
+          const float q1 = fminf(fmaxf(f_sub(s1, 0.5f), 0.0f), g.dmax1);
+          const float q2 = fminf(fmaxf(f_sub(s2, 0.5f), 0.0f), g.dmax2);
+          const int i0 = (int)floorf(q0), i1 = (int)floorf(q1), i2 = (int)floorf(q2);
+          const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
+          const int l0 = i0 - (b0 * B - 1), l1 = i1 - (b1 * B - 1), l2 = i2 - (b2 * B - 1);
+          const size_t base = (size_t)hit_slot * S3 + (size_t)((l2 * S + l1) * S + l0);
+          const float v000 = pool_ld<F16POOL>(pool, base), v100 = pool_ld<F16POOL>(pool, base + 1);
+          const float v010 = pool_ld<F16POOL>(pool, base + S), v110 = pool_ld<F16POOL>(pool, base + S + 1);
+          const float v001 = pool_ld<F16POOL>(pool, base + S * S), v101 = pool_ld<F16POOL>(pool, base + S * S + 1);
+          const float v011 = pool_ld<F16POOL>(pool, base + S * S + S),
+                      v111 = pool_ld<F16POOL>(pool, base + S * S + S + 1);
+          const float x00 = fmaf(f0, v100 - v000, v000), x10 = fmaf(f0, v110 - v010, v010);
+          const float x01 = fmaf(f0, v101 - v001, v001), x11 = fmaf(f0, v111 - v011, v011);
+          const float y0 = fmaf(f1, x10 - x00, x00), y1 = fmaf(f1, x11 - x01, x01);
+          v = fmaf(f2, y1 - y0, y0);
           hit = true;
           if (lev == l)
             ++n_hit;
@@ -504,16 +549,19 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
       }
       if (has) {
         const float4 e4 = tf_lookup(s_tf, v);
-        const float alpha = 1.0f - expf(-e4.w * len);
+        const float alpha = 1.0f - __expf(-e4.w * len);
         const float wgt = T * alpha;
         Cr = fmaf(wgt, e4.x, Cr);
         Cg = fmaf(wgt, e4.y, Cg);
         Cb = fmaf(wgt, e4.z, Cb);
         T *= 1.0f - alpha;
         ++k;
-        if ((k % P.K) == 0 && T < P.eps) {
-          P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
-          active = false;
+        if (--seg == 0) {
+          seg = P.K;
+          if (T < P.eps) {
+            P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
+            active = false;
+          }
         }
       }
     }
@@ -535,9 +583,9 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
   }
 }
 
-template <int IN, int H>
+template <int IN, int H, bool F16POOL>
 int launch_march_cached(const FrameParams& P, cudaStream_t s) {
-  auto k = march_cached_kernel<IN, H>;
+  auto k = march_cached_kernel<IN, H, F16POOL>;
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
@@ -548,13 +596,19 @@ int launch_march_cached(const FrameParams& P, cudaStream_t s) {
   return CINR_OK;
 }
 
-int launch_march_cached_shape(const FrameParams& P, cudaStream_t s) {
+template <bool F16POOL>
+int launch_march_cached_pool(const FrameParams& P, cudaStream_t s) {
   switch (shape_of(P.inr.IN, P.inr.H)) {
-    case Shape::S16x32: return launch_march_cached<16, 32>(P, s);
-    case Shape::S32x64: return launch_march_cached<32, 64>(P, s);
-    case Shape::S48x64: return launch_march_cached<48, 64>(P, s);
+    case Shape::S16x32: return launch_march_cached<16, 32, F16POOL>(P, s);
+    case Shape::S32x64: return launch_march_cached<32, 64, F16POOL>(P, s);
+    case Shape::S48x64: return launch_march_cached<48, 64, F16POOL>(P, s);
     default: return set_error(CINR_ERR_ARG, "unsupported shape");
   }
+}
+
+int launch_march_cached_shape(const FrameParams& P, cudaStream_t s) {
+  return P.cache.pool_prec == CINR_PREC_FP16 ? launch_march_cached_pool<true>(P, s)
+                                             : launch_march_cached_pool<false>(P, s);
 }
 
 // ----------------------------------------------------------- host side
