@@ -254,6 +254,17 @@ int cinr_render_frame_host(cinr_renderer_t r, cinr_cache_t cache,
                            const cinr_tf* tf, float* out_rgba_host,
                            cinr_frame_stats* stats, cinr_stream_t stream);
 
+/* Explicit-voxel render: the same rays, samples, transfer function and
+ * compositing as cinr_render_frame, every sample valued by trilinear
+ * interpolation of field_dev (fdims[0]*fdims[1]*fdims[2] floats, x fastest,
+ * stored at voxel centres (i+0.5)/fdims, clamp-to-edge).  The quality
+ * reference of a trained INR (the uncompressed data of Sec. 4.1).
+ * Synchronises `stream` to fill stats->samples. */
+int cinr_render_field(cinr_renderer_t r, const float* field_dev,
+                      const int fdims[3], const cinr_camera* cam,
+                      const cinr_tf* tf, float* out_rgba_dev,
+                      cinr_frame_stats* stats, cinr_stream_t stream);
+
 int cinr_destroy_renderer(cinr_renderer_t r);
 
 /* Allocation-free uncached render.  The paper has no counterpart: this is a

@@ -107,6 +107,8 @@ _SIGS = {
     "orc_tf_lookup": (None, [_dp, C.c_double, _dp]),
     "orc_render_direct": (None, [_P(InrParams), _dp, _dp, _P(Camera), _ip, _P(MarchOpts),
                                  _dp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _P(Stats)]),
+    "orc_render_field": (None, [_fp, _ip, _P(Camera), _ip, _P(MarchOpts), _dp, C.c_int, C.c_int,
+                                C.c_int, C.c_int, _dp, _P(Stats)]),
     "orc_cache_create": (C.c_void_p, [_P(InrParams), _dp, _dp, _ip, _P(CacheOpts),
                                       _P(MarchOpts)]),
     "orc_cache_destroy": (None, [C.c_void_p]),
@@ -315,6 +317,20 @@ def render_direct(p: InrParams, table, w, cam: Camera, vol, mo: MarchOpts, tf,
     st = Stats()
     lib().orc_render_direct(C.byref(p), tp, wp, C.byref(cam), vp, C.byref(mo), tfp,
                             px0, py0, pw, ph, out.ctypes.data_as(_dp), C.byref(st))
+    return out, st.as_dict()
+
+
+def render_field(field, cam: Camera, vol, mo: MarchOpts, tf, window=None):
+    """Explicit-voxel render of field [z, y, x]; returns (rgba, stats)."""
+    px0, py0, pw, ph = window if window is not None else (0, 0, cam.width, cam.height)
+    fa, fp = _f(field)
+    fd, fdp = _i3(fa.shape[::-1])
+    v, vp = _i3(vol)
+    tfa, tfp = _d(tf)
+    out = np.zeros((ph, pw, 4), np.float64)
+    st = Stats()
+    lib().orc_render_field(fp, fdp, C.byref(cam), vp, C.byref(mo), tfp, px0, py0, pw, ph,
+                           out.ctypes.data_as(_dp), C.byref(st))
     return out, st.as_dict()
 
 

@@ -491,6 +491,39 @@ void orc_render_direct(const orc_inr_params* p, const double* table,
   free(act);
 }
 
+/* Explicit-voxel render: the same marching and compositing, every sample
+ * valued by trilinear interpolation of an explicit field stored at voxel
+ * centres (the uncompressed data an INR is trained on, Sec. 4.1). */
+double orc_field_trilinear(const float* field, const int dims[3],
+                           const float x[3]);
+
+void orc_render_field(const float* field, const int fdims[3],
+                      const orc_camera* cam, const int vol[3],
+                      const orc_march_opts* mo, const double* tf, int px0,
+                      int py0, int pw, int ph, double* rgba, orc_stats* st) {
+  memset(st, 0, sizeof(*st));
+  for (int yy = 0; yy < ph; ++yy)
+    for (int xx = 0; xx < pw; ++xx) {
+      double* out = rgba + ((long)yy * pw + xx) * 4;
+      out[0] = out[1] = out[2] = out[3] = 0.0;
+      float o[3], d[3], tn, tf_;
+      if (!orc_ray(cam, vol, px0 + xx, py0 + yy, o, d, &tn, &tf_)) continue;
+      double C[3] = {0, 0, 0}, T = 1.0;
+      for (int k = 0;; ++k) {
+        float x[3], tm, len;
+        if (!orc_sample(cam, vol, o, d, tn, tf_, k, x, &tm, &len)) break;
+        double v = orc_field_trilinear(field, fdims, x);
+        st->samples++;
+        composite(tf, v, (double)len, C, &T);
+        if ((k + 1) % mo->K == 0 && T < (double)mo->eps_T) break;
+      }
+      out[0] = C[0];
+      out[1] = C[1];
+      out[2] = C[2];
+      out[3] = 1.0 - T;
+    }
+}
+
 /* ===================================================================== */
 /* Multi-resolution brick cache (Sec. 4.3)                                 */
 /* ===================================================================== */

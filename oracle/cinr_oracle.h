@@ -105,6 +105,12 @@ void orc_render_direct(const orc_inr_params* p, const double* table,
                        const double* tf, int px0, int py0, int pw, int ph,
                        double* rgba /* pw*ph*4 */, orc_stats* st);
 
+/* Explicit-voxel render (values by trilinear interpolation of the field). */
+void orc_render_field(const float* field, const int fdims[3],
+                      const orc_camera* cam, const int vol[3],
+                      const orc_march_opts* mo, const double* tf, int px0,
+                      int py0, int pw, int ph, double* rgba, orc_stats* st);
+
 /* ---- multi-resolution brick cache (Sec. 4.3) ---- */
 typedef struct orc_cache orc_cache;
 typedef struct {

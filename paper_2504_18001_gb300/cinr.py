@@ -92,6 +92,8 @@ _SIGS = {
     "cinr_render_frame_host": [_vp, _vp, _vp, _P(cinr_camera), _P(cinr_tf), _vp,
                                _P(cinr_frame_stats), _vp],
     "cinr_destroy_renderer": [_vp],
+    "cinr_render_field": [_vp, _vp, _P(C.c_int), _P(cinr_camera), _P(cinr_tf), _vp,
+                          _P(cinr_frame_stats), _vp],
     "cinr_render_frame_noalloc": [_vp, _P(cinr_camera), _P(cinr_tf), _P(cinr_march_opts), _vp,
                                   _P(cinr_frame_stats), _vp],
     "cinr_trainer_bytes": [_vp, _vp, _P(C.c_size_t)],
@@ -400,6 +402,20 @@ class Renderer:
                                            C.c_void_p(out_host.data_ptr()), C.byref(st),
                                            _stream(stream)), "cinr_render_frame_host")
         return st.as_dict()
+
+    def render_field(self, field, camera, tf, out=None, stream=None):
+        """Explicit-voxel render of field (torch float32 [z, y, x] on the device)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.H, self.W, 4), dtype=torch.float32, device=self.device)
+        cam = camera if isinstance(camera, cinr_camera) else make_camera(camera)
+        t = tf if isinstance(tf, cinr_tf) else make_tf(tf)
+        dims = (C.c_int * 3)(field.shape[2], field.shape[1], field.shape[0])
+        st = cinr_frame_stats()
+        check(lib().cinr_render_field(self.h, C.c_void_p(field.data_ptr()), dims, C.byref(cam),
+                                      C.byref(t), C.c_void_p(out.data_ptr()), C.byref(st),
+                                      _stream(stream)), "cinr_render_field")
+        return out, st.as_dict()
 
     def misses(self, stream=None):
         return debug_dump(self.h, DUMP_MISSES, stream).reshape(-1, 2)

@@ -197,6 +197,34 @@ __device__ __forceinline__ int sample_lod(const CamDev& c, int L, int lod_min, u
   return lod > L - 1 ? L - 1 : lod;
 }
 
+// Explicit field stored at voxel centres (i+0.5)/dims, x fastest: trilinear
+// interpolation with clamp-to-edge (training ground truth, Sec. 4.1, and the
+// explicit-voxel render).
+__device__ __forceinline__ float field_trilinear(const float* __restrict__ f, int3 d, float x, float y,
+                                                 float z) {
+  const float p[3] = {x, y, z};
+  const int dd[3] = {d.x, d.y, d.z};
+  int i0[3], i1[3];
+  float w[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float q = f_sub(f_mul(clamp01(p[a]), (float)dd[a]), 0.5f);
+    q = fminf(fmaxf(q, 0.0f), (float)(dd[a] - 1));
+    i0[a] = (int)floorf(q);
+    w[a] = f_sub(q, (float)i0[a]);
+    i1[a] = i0[a] + 1 > dd[a] - 1 ? dd[a] - 1 : i0[a] + 1;
+  }
+  float v = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int ix = (c & 1) ? i1[0] : i0[0], iy = (c & 2) ? i1[1] : i0[1], iz = (c & 4) ? i1[2] : i0[2];
+    const float wc = ((c & 1) ? w[0] : 1.0f - w[0]) * ((c & 2) ? w[1] : 1.0f - w[1]) *
+                     ((c & 4) ? w[2] : 1.0f - w[2]);
+    v = fmaf(wc, __ldg(f + ((size_t)iz * d.y + iy) * d.x + ix), v);
+  }
+  return v;
+}
+
 // ----------------------------------------------------- hash-grid encoding
 __device__ __forceinline__ float2 load_entry(const void* table, int prec, uint32_t i) {
   if (prec == CINR_PREC_FP16) {

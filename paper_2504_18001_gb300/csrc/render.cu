@@ -1056,3 +1056,116 @@ extern "C" int cinr_render_frame_noalloc(cinr_inr_t inr, const cinr_camera* cam,
   }
   return CINR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Explicit-voxel render: the same rays, samples, transfer function and
+// compositing, each sample valued by trilinear interpolation of an explicit
+// field (the data an INR compresses, Sec. 4.1).  It is the quality judge of
+// a trained INR and the uncompressed fallback.  Thread per ray, 8 x 4 ray
+// tiles per warp.
+namespace {
+
+struct FieldParams {
+  CamDev cam;
+  float4 tf[256];
+  const float* field;
+  int3 fdims;
+  float4* out;
+  uint32_t n_rays, tiles_x;
+  uint32_t* ray_counter;
+  unsigned long long* stats;
+  int K;
+  float eps;
+};
+
+__global__ void __launch_bounds__(kFrameThreads, 8) march_field_kernel(const __grid_constant__ FieldParams P) {
+  __shared__ float4 s_tf[256];
+  for (int i = threadIdx.x; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const CamDev& cam = P.cam;
+  uint32_t n_samp = 0;
+  const uint32_t n_tiles = P.n_rays >> 5;
+  while (true) {
+    uint32_t tile = 0;
+    if (lane == 0) tile = atomicAdd(P.ray_counter, 1u);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= n_tiles) break;
+    const uint32_t r = tile * 32u + (uint32_t)lane;
+    const uint32_t t64 = r >> 6, w = r & 63u;
+    const int px = (int)((t64 % P.tiles_x) * 8 + (w & 7u));
+    const int py = (int)((t64 / P.tiles_x) * 8 + (w >> 3));
+    if (px >= cam.W || py >= cam.H) continue;
+    const uint32_t pixel = (uint32_t)(py * cam.W + px);
+    float d[3], tn = 0.f, tf = 0.f;
+    float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
+    if (ray_setup(cam, px, py, d, tn, tf)) {
+      int seg = P.K;
+      for (int k = 0;; ++k) {
+        float x[3], tm, len;
+        if (!sample_at(cam, d, tn, tf, k, x, tm, len)) break;
+        ++n_samp;
+        const float v = field_trilinear(P.field, P.fdims, x[0], x[1], x[2]);
+        const float4 e4 = tf_lookup(s_tf, v);
+        const float alpha = 1.0f - __expf(-e4.w * len);
+        const float wgt = T * alpha;
+        Cr = fmaf(wgt, e4.x, Cr);
+        Cg = fmaf(wgt, e4.y, Cg);
+        Cb = fmaf(wgt, e4.z, Cb);
+        T *= 1.0f - alpha;
+        if (--seg == 0) {
+          seg = P.K;
+          if (T < P.eps) break;
+        }
+      }
+    }
+    P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
+  }
+  unsigned long long a = n_samp;
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+  if (lane == 0 && a) atomicAdd(P.stats + ST_SAMPLES, a);
+}
+
+}  // namespace
+
+extern "C" int cinr_render_field(cinr_renderer_t r, const float* field_dev, const int fdims[3],
+                                 const cinr_camera* cam, const cinr_tf* tf, float* out_rgba_dev,
+                                 cinr_frame_stats* stats, cinr_stream_t stream) {
+  if (!r || !field_dev || !fdims || !cam || !tf || !out_rgba_dev) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (fdims[0] < 1 || fdims[1] < 1 || fdims[2] < 1) return set_error(CINR_ERR_ARG, "bad field dims");
+  if (cam->width != r->W || cam->height != r->H)
+    return set_error(CINR_ERR_ARG, "camera is %dx%d, renderer %dx%d", cam->width, cam->height, r->W, r->H);
+  if (reinterpret_cast<uintptr_t>(out_rgba_dev) & 15) return set_error(CINR_ERR_ARG, "image must be 16-byte aligned");
+  if (!(cam->step_voxels > 0.0f)) return set_error(CINR_ERR_ARG, "step_voxels must be > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FieldParams P;
+  memset(&P, 0, sizeof(P));
+  camera_consts(cam, &r->o, &P.cam);
+  memcpy(P.tf, tf->rgba, sizeof(P.tf));
+  P.field = field_dev;
+  P.fdims = make_int3(fdims[0], fdims[1], fdims[2]);
+  P.out = reinterpret_cast<float4*>(out_rgba_dev);
+  P.tiles_x = (uint32_t)((r->W + 7) / 8);
+  P.n_rays = P.tiles_x * (uint32_t)((r->H + 7) / 8) * 64u;
+  P.ray_counter = r->counters;
+  P.stats = r->stats;
+  P.K = r->o.K;
+  P.eps = r->o.eps_T;
+  CINR_CK(cudaMemsetAsync(r->counters, 0, 64 * 4, s));
+  CINR_CK(cudaMemsetAsync(r->stats, 0, ST_COUNT * 8, s));
+  static int per_sm = 0;
+  if (!per_sm) {
+    CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_field_kernel, kFrameThreads, 0));
+    if (per_sm < 1) return set_error(CINR_ERR_CUDA, "field kernel cannot be resident");
+  }
+  march_field_kernel<<<(unsigned)(per_sm * num_sms()), kFrameThreads, 0, s>>>(P);
+  CINR_CK(cudaGetLastError());
+  unsigned long long h[ST_COUNT];
+  CINR_CK(cudaMemcpyAsync(h, r->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaStreamSynchronize(s));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->samples = h[ST_SAMPLES];
+  }
+  return CINR_OK;
+}

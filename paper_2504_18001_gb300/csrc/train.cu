@@ -46,32 +46,6 @@ __device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
   return z ^ (z >> 31);
 }
 
-// Trilinear ground truth of a field stored at voxel centres (clamp-to-edge).
-__device__ __forceinline__ float field_trilinear(const float* __restrict__ f, int3 d, float x, float y,
-                                                 float z) {
-  const float p[3] = {x, y, z};
-  const int dd[3] = {d.x, d.y, d.z};
-  int i0[3], i1[3];
-  float w[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float q = f_sub(f_mul(clamp01(p[a]), (float)dd[a]), 0.5f);
-    q = fminf(fmaxf(q, 0.0f), (float)(dd[a] - 1));
-    i0[a] = (int)floorf(q);
-    w[a] = f_sub(q, (float)i0[a]);
-    i1[a] = i0[a] + 1 > dd[a] - 1 ? dd[a] - 1 : i0[a] + 1;
-  }
-  float v = 0.0f;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int ix = (c & 1) ? i1[0] : i0[0], iy = (c & 2) ? i1[1] : i0[1], iz = (c & 4) ? i1[2] : i0[2];
-    const float wc = ((c & 1) ? w[0] : 1.0f - w[0]) * ((c & 2) ? w[1] : 1.0f - w[1]) *
-                     ((c & 4) ? w[2] : 1.0f - w[2]);
-    v = fmaf(wc, __ldg(f + ((size_t)iz * d.y + iy) * d.x + ix), v);
-  }
-  return v;
-}
-
 template <int IN, int H>
 __global__ void __launch_bounds__(kFwdThreads) fwd_bwd_kernel(
     InrDev q, long n, const float* __restrict__ xyz_in, const float* __restrict__ tgt_in,

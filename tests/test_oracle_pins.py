@@ -508,3 +508,18 @@ def test_psnr_known_mse():
     b[..., :3] = 0.1  # mse 0.01 -> 20 dB
     assert O.psnr(a, b) == pytest.approx(20.0, abs=1e-12)
     assert O.psnr(a, a) == float("inf")
+
+
+def test_field_render_constant_field_closed_form():
+    # explicit-voxel render of a constant field: opacity 1 - exp(-sigma L)
+    f = np.full((8, 6, 10), 0.25, np.float32)
+    cam = O.camera((0.3, 0.2, 2.0), (0, 0, 0), (0, 1, 0), 45.0, 12, 10, 0.5)
+    tf = S.tf_constant((1.0, 0.5, 0.25), 6.0).astype(np.float64)
+    vol = (40, 40, 40)
+    img, st = O.render_field(f, cam, vol, O.march_opts(K=32, eps_T=0.0), tf)
+    for py in range(10):
+        for px in range(12):
+            hit, o, d, tn, tf_ = O.ray(cam, vol, px, py)
+            a = 1.0 - math.exp(-6.0 * (tf_ - tn)) if hit else 0.0
+            assert img[py, px, 3] == pytest.approx(a, abs=1e-12)
+    assert st["samples"] > 0
