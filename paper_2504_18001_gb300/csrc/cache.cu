@@ -81,7 +81,9 @@ CacheLayout layout(const Geometry& g, long n_slots, int prec, void* base) {
   L.vic_vals = c.take<uint32_t>(kMaxReq);
   L.vic_sorted = c.take<uint32_t>(kMaxReq);
   size_t S3 = (size_t)g.S * g.S * g.S;
-  L.pool = c.take<char>((size_t)n_slots * S3 * (prec == CINR_PREC_FP16 ? 2 : 4));
+  // + 256 B: the paired voxel loads of the marching kernel may read one
+  // element past the last slot
+  L.pool = c.take<char>((size_t)n_slots * S3 * (prec == CINR_PREC_FP16 ? 2 : 4) + 256);
   L.bytes = align_up(c.off, 256);
   return L;
 }

@@ -396,10 +396,25 @@ struct LevelGeo {
   float scale;                // 2^-level, exact
 };
 
+// Voxels i and i+1 of the pool (x neighbours) with aligned vector loads: one
+// load when i is even, two when it is odd.  Slots start at even voxel
+// indices and the pool is padded by 256 bytes, so the second load of the
+// last voxel pair stays inside the cache buffer.
 template <bool F16POOL>
-__device__ __forceinline__ float pool_ld(const void* pool, size_t i) {
-  if (F16POOL) return __half2float(__ldg(reinterpret_cast<const __half*>(pool) + i));
-  return __ldg(reinterpret_cast<const float*>(pool) + i);
+__device__ __forceinline__ float2 pool_ld2(const void* pool, size_t i) {
+  const size_t a = i & ~(size_t)1;
+  if (F16POOL) {
+    const __half2* p = reinterpret_cast<const __half2*>(pool) + (a >> 1);
+    const __half2 h0 = __ldg(p);
+    if (!(i & 1)) return __half22float2(h0);
+    const __half2 h1 = __ldg(p + 1);
+    return make_float2(__high2float(h0), __low2float(h1));
+  }
+  const float2* p = reinterpret_cast<const float2*>(pool) + (a >> 1);
+  const float2 f0 = __ldg(p);
+  if (!(i & 1)) return f0;
+  const float2 f1 = __ldg(p + 1);
+  return make_float2(f0.y, f1.x);
 }
 
 template <int IN, int H, bool F16POOL>
@@ -430,6 +445,8 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
   const size_t S3 = (size_t)S * S * S;
   const void* pool = c.pool;
   uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0;
+  uint32_t memo_key = 0xFFFFFFFFu, memo_e = 0u;  // last page-table lookup of this lane
+  uint32_t stamped = 0xFFFFFFFFu;                // last slot this lane saw stamped
   const uint32_t n_tiles = P.n_rays >> 5;
   while (true) {
     uint32_t tile = 0;
@@ -474,7 +491,13 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           b1 = min(max(b1, 0), g.nb1 - 1);
           b2 = min(max(b2, 0), g.nb2 - 1);
           const uint32_t key = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
-          const uint32_t e = __ldg(c.pt + key);
+          // page tables change only between frames: the lane's last lookup
+          // is reused while consecutive samples stay in one brick
+          if (key != memo_key) {
+            memo_key = key;
+            memo_e = __ldg(c.pt + key);
+          }
+          const uint32_t e = memo_e;
           if (!(e & kMapped)) {
             if (lev == l) {
               want_req = true;
@@ -491,13 +514,11 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
           const int l0 = i0 - (b0 * B - 1), l1 = i1 - (b1 * B - 1), l2 = i2 - (b2 * B - 1);
           const size_t base = (size_t)hit_slot * S3 + (size_t)((l2 * S + l1) * S + l0);
-          const float v000 = pool_ld<F16POOL>(pool, base), v100 = pool_ld<F16POOL>(pool, base + 1);
-          const float v010 = pool_ld<F16POOL>(pool, base + S), v110 = pool_ld<F16POOL>(pool, base + S + 1);
-          const float v001 = pool_ld<F16POOL>(pool, base + S * S), v101 = pool_ld<F16POOL>(pool, base + S * S + 1);
-          const float v011 = pool_ld<F16POOL>(pool, base + S * S + S),
-                      v111 = pool_ld<F16POOL>(pool, base + S * S + S + 1);
-          const float x00 = fmaf(f0, v100 - v000, v000), x10 = fmaf(f0, v110 - v010, v010);
-          const float x01 = fmaf(f0, v101 - v001, v001), x11 = fmaf(f0, v111 - v011, v011);
+          const float2 p00 = pool_ld2<F16POOL>(pool, base), p10 = pool_ld2<F16POOL>(pool, base + S);
+          const float2 p01 = pool_ld2<F16POOL>(pool, base + S * S);
+          const float2 p11 = pool_ld2<F16POOL>(pool, base + S * S + S);
+          const float x00 = fmaf(f0, p00.y - p00.x, p00.x), x10 = fmaf(f0, p10.y - p10.x, p10.x);
+          const float x01 = fmaf(f0, p01.y - p01.x, p01.x), x11 = fmaf(f0, p11.y - p11.x, p11.x);
           const float y0 = fmaf(f1, x10 - x00, x00), y1 = fmaf(f1, x11 - x01, x01);
           v = fmaf(f2, y1 - y0, y0);
           hit = true;
@@ -525,7 +546,11 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           atomicMin(c.rank + req_key, P.Tf + 1000u);
         }
       }
-      const bool stale = hit && c.stamp[hit_slot] != P.frame;
+      // LRU stamp: a lane checks a slot again only when it changes (a slot
+      // stamped this frame stays stamped until the frame ends)
+      const bool fresh = hit && hit_slot != stamped;
+      if (fresh) stamped = hit_slot;
+      const bool stale = fresh && c.stamp[hit_slot] != P.frame;
       const unsigned hm = __ballot_sync(kFull, stale);
       if (stale) {
         const unsigned peers = __match_any_sync(hm, hit_slot);
