@@ -102,7 +102,11 @@ typedef struct {
  * map rays to threads: 0 = one ray per thread (tiles of 32 neighbouring
  * rays per warp), 1 = one ray per warp (32-sample segments per warp); both
  * produce the same sample set and cache state.  Uncached frames always use
- * one ray per warp (128-sample batches feed the tensor-core MLP). */
+ * one ray per warp (128-sample batches feed the tensor-core MLP).
+ * step_mode 0 steps every sample by step_voxels; step_mode 1 scales the
+ * step with distance for tera-scale volumes: segments of 32 samples, segment
+ * s starting at t_s (t_0 = t_near, t_{s+1} = t_s + 32 dt_s) with step
+ * dt_s = dt 2^l, l the undithered LoD at t_s clamped to [0, step_lod_max]. */
 typedef struct {
   int dims[3];
   int K;
@@ -112,6 +116,8 @@ typedef struct {
   uint64_t seed;
   long miss_record_cap;
   int ray_layout;
+  int step_mode;
+  int step_lod_max;
 } cinr_march_opts;
 
 /* Cache options (Sec. 4.3): brick = interior edge B (stored with a one-voxel

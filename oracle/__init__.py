@@ -60,7 +60,8 @@ class Camera(C.Structure):
 
 class MarchOpts(C.Structure):
     _fields_ = [("K", C.c_int), ("eps_T", C.c_float), ("lod_mode", C.c_int),
-                ("lod_scale", C.c_float), ("seed", C.c_uint64)]
+                ("lod_scale", C.c_float), ("seed", C.c_uint64), ("step_mode", C.c_int),
+                ("step_lod_max", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -180,8 +181,10 @@ def camera(eye, target, up, fov_y_deg, width, height, step_voxels) -> Camera:
     return c
 
 
-def march_opts(K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0) -> MarchOpts:
-    return MarchOpts(int(K), float(eps_T), int(lod_mode), float(lod_scale), int(seed))
+def march_opts(K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0, step_mode=0,
+               step_lod_max=0) -> MarchOpts:
+    return MarchOpts(int(K), float(eps_T), int(lod_mode), float(lod_scale), int(seed),
+                     int(step_mode), int(step_lod_max))
 
 
 def splitmix64(x: int) -> int:

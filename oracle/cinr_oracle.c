@@ -351,6 +351,73 @@ int orc_sample(const orc_camera* cam, const int vol[3], const float o[3],
   return 1;
 }
 
+/* Pixel-footprint constant: t * c = footprint of a pixel at distance t in
+ * LoD-0 voxels, times lod_scale (binary32). */
+static float footprint_const(const orc_camera* cam, const int vol[3],
+                             const orc_march_opts* mo) {
+  float th = tan_half_fov(cam);
+  float c1 = (2.0f * th) / (float)cam->height;
+  float c2 = c1 * (float)max3i(vol);
+  return c2 * mo->lod_scale;
+}
+
+/* Undithered LoD at distance t: floor of D (Sec. 5.3), at least 0. */
+static int base_level(const orc_camera* cam, const int vol[3],
+                      const orc_march_opts* mo, float t) {
+  if (mo->lod_mode == 0) {
+    float xf = t * footprint_const(cam, vol, mo);
+    if (!(xf >= 1.0f)) return 0;
+    uint32_t bits;
+    memcpy(&bits, &xf, 4);
+    return (int)((bits >> 23) & 0xFFu) - 127;
+  }
+  float fl = floorf(t * mo->lod_scale);
+  return fl > 1e6f ? 1000000 : (int)fl;
+}
+
+/* Sample k of a ray under the schedule of mo->step_mode (k = 0, 1, 2, ... in
+ * order; `s` carries the ray's segment state).
+ * step_mode 0: the fixed-step schedule of orc_sample.
+ * step_mode 1 (READING; the paper steps at one rate, which at tera-scale
+ * oversamples the coarse LoDs that Sec. 5.3 already picks far from the
+ * camera): segments of 32 samples; segment s starts at t_s (t_0 = tn,
+ * t_{s+1} = t_s + 32 dt_s) and steps dt_s = dt * 2^l, l the undithered LoD
+ * of t_s clamped to [0, step_lod_max]; within a segment sample j spans
+ * [t_s + j dt_s, min(t_s + (j+1) dt_s, tf)]. */
+int orc_sample_sched(const orc_camera* cam, const int vol[3],
+                     const orc_march_opts* mo, const float o[3],
+                     const float d[3], float tn, float tf, int k,
+                     orc_sched* s, float x[3], float* t_mid,
+                     float* seg_len) {
+  if (mo->step_mode == 0)
+    return orc_sample(cam, vol, o, d, tn, tf, k, x, t_mid, seg_len);
+  float dt = cam->step_voxels / (float)max3i(vol);
+  int j = k & 31;
+  if (j == 0) {
+    if (k == 0)
+      s->ts = tn;
+    else
+      s->ts = s->ts + 32.0f * s->dts;
+    int lvl = base_level(cam, vol, mo, s->ts);
+    if (lvl > mo->step_lod_max) lvl = mo->step_lod_max;
+    if (lvl < 0) lvl = 0;
+    s->dts = dt * (float)(1 << lvl);
+  }
+  float a = s->ts + (float)j * s->dts;
+  if (!(a < tf)) return 0;
+  float b = fminf(s->ts + (float)(j + 1) * s->dts, tf);
+  float tm = (a + b) * 0.5f;
+  *t_mid = tm;
+  *seg_len = b - a;
+  float e[3], h[3];
+  box_extent(vol, e, h);
+  for (int c = 0; c < 3; ++c) {
+    float pc = o[c] + tm * d[c];
+    x[c] = clamp01((pc + h[c]) / e[c]);
+  }
+  return 1;
+}
+
 /* Higher-quality per-frame seed of the xorshift dither (Sec. 5.3). */
 uint32_t orc_frame_seed(uint64_t seed, uint64_t frame) {
   return (uint32_t)orc_splitmix64(seed ^ frame);
@@ -472,9 +539,11 @@ void orc_render_direct(const orc_inr_params* p, const double* table,
       float o[3], d[3], tn, tf_;
       if (!orc_ray(cam, vol, px0 + xx, py0 + yy, o, d, &tn, &tf_)) continue;
       double C[3] = {0, 0, 0}, T = 1.0;
+      orc_sched sc = {0.0f, 0.0f};
       for (int k = 0;; ++k) {
         float x[3], tm, len;
-        if (!orc_sample(cam, vol, o, d, tn, tf_, k, x, &tm, &len)) break;
+        if (!orc_sample_sched(cam, vol, mo, o, d, tn, tf_, k, &sc, x, &tm, &len))
+          break;
         double v = inr_one(p, table, w, x, feat, act);
         st->samples++;
         st->inr_queries_direct++;
@@ -509,9 +578,11 @@ void orc_render_field(const float* field, const int fdims[3],
       float o[3], d[3], tn, tf_;
       if (!orc_ray(cam, vol, px0 + xx, py0 + yy, o, d, &tn, &tf_)) continue;
       double C[3] = {0, 0, 0}, T = 1.0;
+      orc_sched sc = {0.0f, 0.0f};
       for (int k = 0;; ++k) {
         float x[3], tm, len;
-        if (!orc_sample(cam, vol, o, d, tn, tf_, k, x, &tm, &len)) break;
+        if (!orc_sample_sched(cam, vol, mo, o, d, tn, tf_, k, &sc, x, &tm, &len))
+          break;
         double v = orc_field_trilinear(field, fdims, x);
         st->samples++;
         composite(tf, v, (double)len, C, &T);
@@ -866,9 +937,12 @@ void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
       if (!orc_ray(cam, c->vol, px, py, o, d, &tn, &tf_)) continue;
       double C[3] = {0, 0, 0}, T = 1.0;
       uint32_t rs = orc_ray_seed(fseed, pixel);
+      orc_sched sc = {0.0f, 0.0f};
       for (int k = 0;; ++k) {
         float x[3], tm, len;
-        if (!orc_sample(cam, c->vol, o, d, tn, tf_, k, x, &tm, &len)) break;
+        if (!orc_sample_sched(cam, c->vol, &c->mo, o, d, tn, tf_, k, &sc, x, &tm,
+                              &len))
+          break;
         st->samples++;
         int l = orc_sample_lod(cam, c->vol, &c->mo, L, 0,
                                orc_sample_state(rs, (uint32_t)k), tm);

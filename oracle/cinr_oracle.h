@@ -51,7 +51,13 @@ typedef struct {
   int lod_mode;        /* 0 = screen footprint, 1 = distance (Alg. 2) */
   float lod_scale;
   uint64_t seed;       /* per-run seed of the per-frame dither seed */
+  int step_mode;       /* 0 fixed step, 1 LoD-scaled 32-sample segments */
+  int step_lod_max;    /* highest LoD that scales the step (mode 1) */
 } orc_march_opts;
+
+typedef struct {
+  float ts, dts;       /* segment start and step (schedule state of a ray) */
+} orc_sched;
 
 typedef struct {
   uint64_t samples, inr_queries_direct, inr_queries_decode, true_misses,
@@ -87,6 +93,11 @@ int orc_ray(const orc_camera* cam, const int vol[3], int px, int py, float o[3],
 int orc_sample(const orc_camera* cam, const int vol[3], const float o[3],
                const float d[3], float tn, float tf, int k, float x[3],
                float* t_mid, float* seg_len);
+int orc_sample_sched(const orc_camera* cam, const int vol[3],
+                     const orc_march_opts* mo, const float o[3],
+                     const float d[3], float tn, float tf, int k,
+                     orc_sched* s, float x[3], float* t_mid,
+                     float* seg_len);
 int orc_sample_lod(const orc_camera* cam, const int vol[3],
                    const orc_march_opts* mo, int levels, int lod_min,
                    uint32_t state, float t_mid);

@@ -74,6 +74,13 @@ struct CamDev {
   float lod_scale;
   int lod_mode;
   int vol[3];
+  int step_mode;       // 0 fixed step, 1 LoD-scaled 32-sample segments
+  int step_lod_max;
+};
+
+// Sample schedule state of a ray under step_mode 1.
+struct Sched {
+  float ts, dts;  // segment start, step
 };
 
 struct CacheDev {
@@ -147,6 +154,55 @@ __device__ __forceinline__ bool sample_at(const CamDev& c, const float d[3], flo
     x[q] = clamp01(c.e[q] == 1.0f ? num : f_div(num, c.e[q]));
   }
   return true;
+}
+
+// Undithered LoD at distance t (floor of D, Sec. 5.3), clamped to
+// [0, step_lod_max]: the step scale of step_mode 1.
+__device__ __forceinline__ int step_level(const CamDev& c, float t) {
+  int l;
+  if (c.lod_mode == 0) {
+    const float xf = f_mul(t, c.lodc);
+    l = xf >= 1.0f ? (int)((__float_as_uint(xf) >> 23) & 0xFFu) - 127 : 0;
+  } else {
+    const float fl = floorf(f_mul(t, c.lod_scale));
+    l = fl > 1e6f ? 1000000 : (int)fl;
+  }
+  l = l < 0 ? 0 : l;
+  return l > c.step_lod_max ? c.step_lod_max : l;
+}
+
+// Enters the segment that starts at sample k (a multiple of 32).
+__device__ __forceinline__ void sched_segment(const CamDev& c, float tn, int k, Sched& s) {
+  if (c.step_mode == 0) return;
+  s.ts = k == 0 ? tn : f_add(s.ts, f_mul(32.0f, s.dts));
+  s.dts = f_mul(c.dt, (float)(1 << step_level(c, s.ts)));
+}
+
+// Sample k under the ray's schedule (the segment of k entered before).
+__device__ __forceinline__ bool sample_in(const CamDev& c, const float d[3], float tn, float tf, int k,
+                                          const Sched& s, float x[3], float& tm, float& len) {
+  if (c.step_mode == 0) return sample_at(c, d, tn, tf, k, x, tm, len);
+  const int j = k & 31;
+  const float a = f_add(s.ts, f_mul((float)j, s.dts));
+  if (!(a < tf)) return false;
+  const float b = fminf(f_add(s.ts, f_mul((float)(j + 1), s.dts)), tf);
+  tm = f_mul(f_add(a, b), 0.5f);
+  len = f_sub(b, a);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float p = f_add(c.o[q], f_mul(tm, d[q]));
+    const float num = f_add(p, c.h[q]);
+    x[q] = clamp01(c.e[q] == 1.0f ? num : f_div(num, c.e[q]));
+  }
+  return true;
+}
+
+// Whether a segment follows the one that starts at sample k0 (k0 + 32 is
+// the next segment's first sample).
+__device__ __forceinline__ bool next_segment_exists(const CamDev& c, float tn, float tf, int k0,
+                                                    const Sched& s) {
+  if (c.step_mode == 0) return f_add(tn, f_mul((float)(k0 + 32), c.dt)) < tf;
+  return f_add(s.ts, f_mul(32.0f, s.dts)) < tf;
 }
 
 __device__ __forceinline__ uint32_t xorshift32(uint32_t s) {

@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
   uint32_t pixel = 0, rseed = 0;
   float d[3] = {0.f, 0.f, 0.f}, tn = 0.f, tf = 0.f, T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
   int k0 = 0;
+  Sched sch = {0.f, 0.f};
   uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0;
   int parity = 0;
 
@@ -176,7 +177,8 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
     float x[3] = {0.f, 0.f, 0.f}, tm = 0.f, len = 0.f, v = 0.f;
     bool has = false, miss = false;
     if (active) {
-      has = sample_at(cam, d, tn, tf, k0 + lane, x, tm, len);
+      sched_segment(cam, tn, k0, sch);
+      has = sample_in(cam, d, tn, tf, k0 + lane, sch, x, tm, len);
       if (has) {
         ++n_samp;
         if (!CACHED) miss = true;
@@ -334,8 +336,8 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
       Cg = fmaf(T, cg, Cg);
       Cb = fmaf(T, cb, Cb);
       T *= segT;
+      const bool more = next_segment_exists(cam, tn, tf, k0, sch);
       k0 += 32;
-      const bool more = f_add(tn, f_mul((float)k0, cam.dt)) < tf;
       const bool term = (k0 % P.K == 0) && T < P.eps;
       if (!more || term) {
         if (lane == 0) P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
@@ -396,25 +398,10 @@ struct LevelGeo {
   float scale;                // 2^-level, exact
 };
 
-// Voxels i and i+1 of the pool (x neighbours) with aligned vector loads: one
-// load when i is even, two when it is odd.  Slots start at even voxel
-// indices and the pool is padded by 256 bytes, so the second load of the
-// last voxel pair stays inside the cache buffer.
 template <bool F16POOL>
-__device__ __forceinline__ float2 pool_ld2(const void* pool, size_t i) {
-  const size_t a = i & ~(size_t)1;
-  if (F16POOL) {
-    const __half2* p = reinterpret_cast<const __half2*>(pool) + (a >> 1);
-    const __half2 h0 = __ldg(p);
-    if (!(i & 1)) return __half22float2(h0);
-    const __half2 h1 = __ldg(p + 1);
-    return make_float2(__high2float(h0), __low2float(h1));
-  }
-  const float2* p = reinterpret_cast<const float2*>(pool) + (a >> 1);
-  const float2 f0 = __ldg(p);
-  if (!(i & 1)) return f0;
-  const float2 f1 = __ldg(p + 1);
-  return make_float2(f0.y, f1.x);
+__device__ __forceinline__ float pool_ld(const void* pool, size_t i) {
+  if (F16POOL) return __half2float(__ldg(reinterpret_cast<const __half*>(pool) + i));
+  return __ldg(reinterpret_cast<const float*>(pool) + i);
 }
 
 template <int IN, int H, bool F16POOL>
@@ -465,11 +452,13 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
     const uint32_t rseed = ray_seed(P.fseed, pixel);
     float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
     int k = 0, seg = P.K;  // seg: samples left in the current K-segment
+    Sched sch = {0.f, 0.f};
     while (__any_sync(kFull, active)) {
       float x[3], tm = 0.f, len = 0.f, v = 0.f;
       bool has = false;
       if (active) {
-        has = sample_at(cam, d, tn, tf, k, x, tm, len);
+        if ((k & 31) == 0) sched_segment(cam, tn, k, sch);
+        has = sample_in(cam, d, tn, tf, k, sch, x, tm, len);
         if (!has) {
           P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
           active = false;
@@ -514,11 +503,13 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
           const int l0 = i0 - (b0 * B - 1), l1 = i1 - (b1 * B - 1), l2 = i2 - (b2 * B - 1);
           const size_t base = (size_t)hit_slot * S3 + (size_t)((l2 * S + l1) * S + l0);
-          const float2 p00 = pool_ld2<F16POOL>(pool, base), p10 = pool_ld2<F16POOL>(pool, base + S);
-          const float2 p01 = pool_ld2<F16POOL>(pool, base + S * S);
-          const float2 p11 = pool_ld2<F16POOL>(pool, base + S * S + S);
-          const float x00 = fmaf(f0, p00.y - p00.x, p00.x), x10 = fmaf(f0, p10.y - p10.x, p10.x);
-          const float x01 = fmaf(f0, p01.y - p01.x, p01.x), x11 = fmaf(f0, p11.y - p11.x, p11.x);
+          const float v000 = pool_ld<F16POOL>(pool, base), v100 = pool_ld<F16POOL>(pool, base + 1);
+          const float v010 = pool_ld<F16POOL>(pool, base + S), v110 = pool_ld<F16POOL>(pool, base + S + 1);
+          const float v001 = pool_ld<F16POOL>(pool, base + S * S), v101 = pool_ld<F16POOL>(pool, base + S * S + 1);
+          const float v011 = pool_ld<F16POOL>(pool, base + S * S + S),
+                      v111 = pool_ld<F16POOL>(pool, base + S * S + S + 1);
+          const float x00 = fmaf(f0, v100 - v000, v000), x10 = fmaf(f0, v110 - v010, v010);
+          const float x01 = fmaf(f0, v101 - v001, v001), x11 = fmaf(f0, v111 - v011, v011);
           const float y0 = fmaf(f1, x10 - x00, x00), y1 = fmaf(f1, x11 - x01, x01);
           v = fmaf(f2, y1 - y0, y0);
           hit = true;
@@ -681,6 +672,8 @@ void camera_consts(const cinr_camera* cam, const cinr_march_opts* o, CamDev* c) 
   c->lodc = c2 * o->lod_scale;
   c->lod_scale = o->lod_scale;
   c->lod_mode = o->lod_mode;
+  c->step_mode = o->step_mode;
+  c->step_lod_max = o->step_lod_max;
 }
 
 uint64_t splitmix64(uint64_t x) {
@@ -767,6 +760,8 @@ int check_opts(int W, int H, const cinr_march_opts* o) {
     return set_error(CINR_ERR_ARG, "bad miss_record_cap");
   if (o->lod_mode != 0 && o->lod_mode != 1) return set_error(CINR_ERR_ARG, "bad lod_mode");
   if (o->ray_layout != 0 && o->ray_layout != 1) return set_error(CINR_ERR_ARG, "bad ray_layout");
+  if (o->step_mode != 0 && o->step_mode != 1) return set_error(CINR_ERR_ARG, "bad step_mode");
+  if (o->step_lod_max < 0 || o->step_lod_max > 15) return set_error(CINR_ERR_ARG, "step_lod_max must be in [0, 15]");
   return CINR_OK;
 }
 
@@ -1126,9 +1121,11 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_field_kernel(const __g
     float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
     if (ray_setup(cam, px, py, d, tn, tf)) {
       int seg = P.K;
+      Sched sch = {0.f, 0.f};
       for (int k = 0;; ++k) {
         float x[3], tm, len;
-        if (!sample_at(cam, d, tn, tf, k, x, tm, len)) break;
+        if ((k & 31) == 0) sched_segment(cam, tn, k, sch);
+        if (!sample_in(cam, d, tn, tf, k, sch, x, tm, len)) break;
         ++n_samp;
         const float v = field_trilinear(P.field, P.fdims, x[0], x[1], x[2]);
         const float4 e4 = tf_lookup(s_tf, v);

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_req=40, ranking=1,
          preload=1, lod_scale=1.0, lod_mode=0, storage="fp32", K=32, eps=0.0, check_pixels=2e-3,
-         cam_fn=None, mlp="fp32", tab="fp32", ray_layout=0):
+         cam_fn=None, mlp="fp32", tab="fp32", ray_layout=0, step_mode=0, step_lod_max=0):
     from paper_2504_18001_gb300 import cinr
     cfg = S.INR_64
     table, w = scene(cfg)
@@ -25,11 +25,12 @@ def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_r
                        brick=brick, levels=levels, n_req=n_req, ranking=ranking, preload=preload,
                        storage=storage)
     assert cache.n_slots == slots
-    mo = O.march_opts(K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11)
+    mo = O.march_opts(K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
+                      step_mode=step_mode, step_lod_max=step_lod_max)
     oc = O.Cache(p, table, w, vol, brick, levels, slots, mo, n_req=n_req, ranking=ranking,
                  preload=preload)
     r = cinr.Renderer(W, H, vol, K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
-                      ray_layout=ray_layout,
+                      ray_layout=ray_layout, step_mode=step_mode, step_lod_max=step_lod_max,
                       miss_record_cap=W * H * 4000)
     tf = S.tf_ramps(2)
     worst = 0.0
@@ -140,3 +141,38 @@ def test_cached_early_termination_both_layouts_agree():
         sts.append(st)
     assert np.abs(imgs[0] - imgs[1]).max() < 2e-3
     assert abs(sts[0]["samples"] - sts[1]["samples"]) <= 32 * 4
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("lod_mode,lod_scale", [(0, 4.0), (1, 2.5)])
+def test_lod_scaled_steps_state_bit_exact(layout, lod_mode, lod_scale):
+    # step_mode 1 (segments of 32 samples stepping dt 2^l): same sample set,
+    # cache state and miss lists as the oracle, both ray layouts
+    _run(4, ray_layout=layout, lod_mode=lod_mode, lod_scale=lod_scale, step_mode=1, step_lod_max=2,
+         levels=3, slots=200)
+    _run(2, ray_layout=layout, lod_mode=lod_mode, lod_scale=lod_scale, step_mode=1, step_lod_max=2,
+         levels=3, slots=400, preload=0, n_req=200)
+
+
+def test_lod_scaled_steps_uncached_and_field():
+    import torch
+    from paper_2504_18001_gb300 import cinr
+    from _scenes import oracle_inr
+    cfg = S.INR_64
+    vol = (64, 64, 64)
+    table, w = scene(cfg)
+    inr = gpu_inr(cfg, table, w, vol=vol)
+    p = oracle_inr(cfg, table, w, vol=vol)
+    cam = S.orbit_camera(3, 40, 32)
+    tf = S.tf_ramps(2)
+    r = cinr.Renderer(40, 32, vol, K=32, eps_T=0.0, lod_scale=4.0, step_mode=1, step_lod_max=3)
+    mo = O.march_opts(K=32, eps_T=0.0, lod_scale=4.0, step_mode=1, step_lod_max=3)
+    img, st = r.render(inr, cam, tf)
+    ref, rst = O.render_direct(p, table, w, ocam(cam), vol, mo, tf.astype(np.float64))
+    assert st["samples"] == rst["samples"]
+    assert np.abs(img.cpu().numpy() - ref).max() < 2e-3
+    field = S.explicit_field((20, 24, 28), S.field_params(5, n_gaussians=6))
+    img, st = r.render_field(torch.from_numpy(field).cuda(), cam, tf)
+    ref, rst = O.render_field(field, ocam(cam), vol, mo, tf.astype(np.float64))
+    assert st["samples"] == rst["samples"]
+    assert np.abs(img.cpu().numpy() - ref).max() < 2e-3

@@ -510,6 +510,31 @@ def test_psnr_known_mse():
     assert O.psnr(a, a) == float("inf")
 
 
+@pytest.mark.parametrize("lod_mode,lod_scale", [(0, 3.0), (1, 10.0)])
+def test_lod_scaled_steps_cover_the_chord_and_scale_by_powers_of_two(lod_mode, lod_scale):
+    # step mode 1: the segments still tile [tn, tf] exactly (constant slab
+    # closed form), and with the level clamped at 2 every step is 4 dt
+    p, table, w = _zero_inr()
+    cam = O.camera((0.3, 0.2, 2.0), (0, 0, 0), (0, 1, 0), 45.0, 16, 12, 0.5)
+    vol = (64, 64, 64)
+    tf = S.tf_constant((1.0, 1.0, 1.0), 4.0).astype(np.float64)
+    mo = O.march_opts(K=32, eps_T=0.0, lod_mode=lod_mode, lod_scale=lod_scale, step_mode=1,
+                      step_lod_max=2)
+    img, st = O.render_direct(p, table, w, cam, vol, mo, tf)
+    n_ref = 0
+    dt = np.float32(0.5) / np.float32(64)
+    for py in range(12):
+        for px in range(16):
+            hit, o, d, tn, tf_ = O.ray(cam, vol, px, py)
+            if not hit:
+                continue
+            a = 1.0 - math.exp(-4.0 * (tf_ - tn))
+            assert img[py, px, 3] == pytest.approx(a, abs=1e-12)
+            n_ref += math.ceil((tf_ - tn) / (4 * dt))
+    if lod_mode == 1:  # D >= 15 everywhere: clamped to level 2, steps of 4 dt
+        assert abs(st["samples"] - n_ref) <= 2 * 16 * 12
+
+
 def test_field_render_constant_field_closed_form():
     # explicit-voxel render of a constant field: opacity 1 - exp(-sigma L)
     f = np.full((8, 6, 10), 0.25, np.float32)
