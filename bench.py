@@ -2,17 +2,25 @@
 uncached (direct INR) renderer on one GB300, with PSNR against the CPU FP64
 oracle and the oracle's own CPU timing beside them.
 
-Workload (the headline configuration): a 512^3 virtual volume represented by
-a hash-grid INR (L=16, F=2, T=2^19, N_min=16, b=1.38, MLP 32-64-64-1, FP32),
-rendered at 1024x1024 with a 45 deg camera orbiting at distance 2.0
-(1 deg/frame for 120 frames, then 30 frames of transfer-function edits);
-brick cache: 8^3 bricks with a one-voxel apron, 4 LoDs, 1 GiB FP32 pool,
-ranked requests (n_req per frame), coarsest LoD preloaded.  Inputs are
-seeded and synthetic (the paper's datasets and trained weights are not
-available).  A step = one frame: march + true-miss inference + compositing
-+ request selection + victims + brick decode/write-back.
+Workloads (seeded synthetic inputs; the paper's datasets and trained
+weights are not available):
+  orbit (default, the headline): a 512^3 volume represented by a hash-grid
+    INR (L=16, F=2, T=2^19, N_min=16, b=1.38, MLP 32-64-64-1), 1024x1024,
+    45 deg camera orbiting at distance 2.0 (1 deg/frame for 120 frames, then
+    30 frames of transfer-function edits); brick cache 8^3 + apron, 4 LoDs,
+    1 GiB pool, ranked requests, coarsest LoD preloaded.
+  terascale: a 10240x7680x1536 virtual volume, INR L=24, T=2^22, MLP
+    48-64-64-1, 1920x1080 fly-through with zoom-ins, bricks 16^3 + apron,
+    6 LoDs, 40 GB FP16 pool, LoD-scaled steps.
+  learned: the INR trained from scratch on an explicit 1024^3 field by the
+    library's kernels, then the cached FP16 render judged by PSNR against the
+    explicit-voxel render.
+A step = one frame: march + true-miss inference + compositing + request
+selection + victims + brick decode/write-back.  The cached path is mixed
+precision (FP16 table, FP16 bricks, BF16 tensor-core MLP with FP32
+accumulation); the uncached baseline is FP32 (FP32 table, FP32 SIMT MLP).
 
-Multi-GPU: the renderer does not shard (one frame is one GPU's work);
+Multi-GPU: the renderer does not shard (a frame is one GPU's work);
 --gpus N runs N independent replicas of the workload (weak scaling).
 """
 from __future__ import annotations
@@ -34,13 +42,28 @@ sys.path.insert(0, ROOT)
 METRIC = "ms/frame and INR queries/s, cached vs uncached, at PSNR >= 40 dB vs oracle"
 ORBIT_FRAMES = 120
 TF_FRAMES = 30
+FLY_FRAMES = 300
+
+WORKLOADS = {
+    "orbit": dict(name="cached_{prec}_512cube_1024px_orbit", vol=(512, 512, 512), inr="INR_512",
+                  brick=8, levels=4, pool_mib=1024, W=1024, H=1024, n_req=4096, step_mode=0,
+                  step_lod_max=0, warmup=90, steps=60, camera="orbit", range_stride=8,
+                  uncached_steps=5),
+    "terascale": dict(name="terascale_{prec}_10240x7680x1536_1080p_flythrough",
+                      vol=(10240, 7680, 1536), inr="INR_TERA", brick=16, levels=6,
+                      pool_mib=40 * 1024, W=1920, H=1080, n_req=8192, step_mode=1,
+                      step_lod_max=5, warmup=100, steps=50, camera="fly", range_stride=64,
+                      uncached_steps=2),
+}
 
 
-def frame_inputs(f, W, H):
+def frame_inputs(f, W, H, camera="orbit"):
     from paper_2504_18001_gb300 import synthetic as S
+    tf = S.tf_ramps(2)
+    if camera == "fly":
+        return S.flythrough_camera(f % FLY_FRAMES, FLY_FRAMES, W, H), tf
     if f < ORBIT_FRAMES:
         cam = S.orbit_camera(f, W, H)
-        tf = S.tf_ramps(2)
     else:
         g = f - ORBIT_FRAMES + 1
         cam = S.orbit_camera(ORBIT_FRAMES - 1, W, H)
@@ -109,24 +132,24 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def scene_weights(args):
+def scene_weights(args, wl):
     from paper_2504_18001_gb300 import synthetic as S
-    cfg = S.INR_512
+    cfg = getattr(S, wl["inr"])
     table, w = S.inr_init(cfg, seed=args.seed, table_scale=1.0, level_decay=args.level_decay)
     return cfg, table, w
 
 
-def build_scene(args, device):
+def build_scene(args, wl, device):
     """The uncached baseline INR (FP32 table, FP32 SIMT MLP) and the INR of
     the cached path (mixed: FP16 table + BF16 tensor-core MLP; or FP32)."""
     from paper_2504_18001_gb300 import cinr
-    cfg, table, w = scene_weights(args)
-    vol = (512, 512, 512)
+    cfg, table, w = scene_weights(args, wl)
+    vol = wl["vol"]
 
     def make(mlp, tab):
         inr = cinr.Inr(cinr.make_inr_params(cfg, mlp_precision=mlp, table_precision=tab), table, w,
                        device=device)
-        lo, hi = inr.raw_range(vol, stride=8)
+        lo, hi = inr.raw_range(vol, stride=wl["range_stride"])
         inr.set_range(-lo / (hi - lo), (1.0 - lo) / (hi - lo))
         return inr
 
@@ -135,7 +158,7 @@ def build_scene(args, device):
     return cfg, table, w, inr32, inr_c, vol
 
 
-def run_gpu(args):
+def run_gpu(args, wl):
     import torch
     import torch.distributed as dist
     from paper_2504_18001_gb300 import cinr
@@ -147,21 +170,22 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
-    W = H = args.res
-    cfg, table, w, inr32, inr_c, vol = build_scene(args, device)
+    W, H = wl["W"], wl["H"]
+    cfg, table, w, inr32, inr_c, vol = build_scene(args, wl, device)
     storage = "fp16" if args.precision == "mixed" else "fp32"
-    S3 = (args.brick + 2) ** 3
-    cache = cinr.Cache(inr_c, vol, pool_bytes=args.pool_mib << 20, brick=args.brick, levels=4, storage=storage,
-                       n_req=args.n_req, ranking=1, preload=1, device=device)
+    S3 = (wl["brick"] + 2) ** 3
+    cache = cinr.Cache(inr_c, vol, pool_bytes=wl["pool_mib"] << 20, brick=wl["brick"],
+                       levels=wl["levels"], storage=storage, n_req=wl["n_req"], ranking=1,
+                       preload=1, device=device)
     rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
-                         ray_layout=args.ray_layout,
-                         seed=args.seed, device=device)
+                         ray_layout=args.ray_layout, seed=args.seed, step_mode=wl["step_mode"],
+                         step_lod_max=wl["step_lod_max"], device=device)
     img = torch.empty((H, W, 4), dtype=torch.float32, device=device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
     def step(f, use_cache=True):
-        cam, tf = frame_inputs(f, W, H)
+        cam, tf = frame_inputs(f, W, H, wl["camera"])
         flush.random_(0, 255)  # L2 flush between timed iterations
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -193,11 +217,11 @@ def run_gpu(args):
     last_f = args.warmup + args.steps - 1
     cached_img = img.clone()
 
-    # uncached baseline on the same frames (direct INR for every sample)
+    # uncached baseline on the last timed frames (direct INR for every sample)
     un_ms, un_st = [], []
-    n_un = min(args.steps, args.uncached_steps)
+    n_un = min(args.steps, args.uncached_steps or wl["uncached_steps"])
     for i in range(n_un):
-        e0, e1, st = step(args.warmup + args.steps - n_un + i, use_cache=False)
+        e0, e1, st = step(last_f - n_un + 1 + i, use_cache=False)
         torch.cuda.synchronize()
         un_ms.append(e0.elapsed_time(e1))
         un_st.append(st)
@@ -208,7 +232,7 @@ def run_gpu(args):
     host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
     e2e = []
     for i in range(max(3, min(args.steps, 10))):
-        cam, tf = frame_inputs(last_f + 1 + i, W, H)
+        cam, tf = frame_inputs(last_f + 1 + i, W, H, wl["camera"])
         flush.random_(0, 255)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -234,6 +258,7 @@ def run_gpu(args):
     alg_bytes = [sl * (S3 * elem + 4) + W * H * 16 for sl in slots]
     achieved = sum(alg_bytes) / (sum(k_ms) * 1e-3) / 1e9
     un_q = sum(s["inr_queries_direct"] for s in un_st)
+    prec = args.precision
     res = {
         "metric": METRIC,
         "value": total_ms / (len(ms) * world),
@@ -245,122 +270,140 @@ def run_gpu(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16" if args.precision == "mixed" else "f32",
-        "data": "synthetic (seeded INR, orbit camera, seeded TF ramps)",
-        "config": {"workload": f"cached_{args.precision}_512cube_1024px_orbit", "volume": list(vol),
+        "dtype": "bf16" if prec == "mixed" else "f32",
+        "data": "synthetic (seeded INR, seeded camera path, seeded TF ramps)",
+        "config": {"workload": wl["name"].format(prec=prec), "volume": list(vol),
                    "cached_path": ("FP16 table + FP16 bricks + BF16 tensor-core MLP (FP32 accumulate)"
-                                   if args.precision == "mixed" else "FP32"),
+                                   if prec == "mixed" else "FP32"),
                    "uncached_path": "FP32 table + FP32 SIMT MLP",
-                   "image": [W, H], "inr": "L16 F2 T2^19 Nmin16 b1.38 MLP32-64-64-1",
-                   "brick": args.brick, "lods": 4, "pool_mib": args.pool_mib,
-                   "n_req": args.n_req, "lod_scale": args.lod_scale, "K": 32, "eps_T": 1e-3,
+                   "image": [W, H], "inr": f"L{cfg.levels} F{cfg.feats} T2^{cfg.log2_table} "
+                                           f"Nmin{cfg.base_res} b{cfg.growth} "
+                                           f"MLP{cfg.in_dim}-{cfg.hidden}-{cfg.hidden}-1",
+                   "brick": wl["brick"], "lods": wl["levels"], "pool_mib": wl["pool_mib"],
+                   "n_req": wl["n_req"], "lod_scale": args.lod_scale, "K": 32, "eps_T": 1e-3,
+                   "step_mode": wl["step_mode"], "step_lod_max": wl["step_lod_max"],
                    "ray_layout": "thread per ray" if args.ray_layout == 0 else "warp per ray",
+                   "timed_frames": [args.warmup, last_f],
                    "l2": "flushed (256 MiB write) before every timed frame",
                    "parallelism": f"replicas x{world}"},
         "inr_queries_per_s": (q_direct + q_decode) / (sum(ms) * 1e-3),
         "samples_per_s": samples / (sum(ms) * 1e-3),
+        "ms_per_frame_p50": float(np.percentile(ms, 50)),
+        "ms_per_frame_p90": float(np.percentile(ms, 90)),
         "uncached": {"ms_per_frame": uncached_ms,
                      "inr_queries_per_s": un_q / (sum(un_ms) * 1e-3), "frames": n_un},
         "speedup_cached_vs_uncached": uncached_ms / cached_ms,
         "frame_stats_last": stats[-1],
         "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": 4096 + 64,
-                "d2h_bytes_per_step": W * H * 16 + 96},
-        "gpu_launches": None,
+                "d2h_bytes_per_step": W * H * 16 + 104},
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "kernel": "frame_kernel<32,64,cached>", "peak_kind": peak_kind},
+                     "kernel": ("march_cached_kernel<%d,%d,%s pool>"
+                                % (cfg.in_dim, cfg.hidden, "fp16" if prec == "mixed" else "fp32")),
+                     "peak_kind": peak_kind},
         "clocks": clk,
     }
-    res["gpu_launches"] = args.steps * launches_per_cached_frame()
     mse = torch.mean((cached_img[..., :3].double() - uncached_img[..., :3].double()) ** 2).item()
     res["psnr_db"] = {"cached_vs_uncached_full_frame": 10 * np.log10(1.0 / max(mse, 1e-30))}
     if rank == 0 and not args.no_cpu:
-        res["cpu_baseline"], p = cpu_baseline(args, table, w, last_f, cached_img, uncached_img)
+        res["cpu_baseline"], p = cpu_baseline(args, wl, table, w, last_f, cached_img, uncached_img,
+                                              un_st[-1])
         res["psnr_db"].update(p)
     if world > 1:
         dist.destroy_process_group()
     return res if rank == 0 else None
 
 
-def launches_per_cached_frame():
-    # frame kernel + 2 radix selections (reset, 4 x (hist, pick), gather,
-    # sort) + commit + decode
-    return 1 + 2 * (1 + 2 * 4 + 2) + 2
-
-
-def cpu_baseline(args, table, w, f, cached_img, uncached_img):
-    """The oracle (single-threaded C, FP64) on a pixel window of frame f."""
+def oracle_scene(args, wl):
     import oracle as O
-    from paper_2504_18001_gb300 import synthetic as S
-    W = H = args.res
-    cfg = S.INR_512
+    cfg, table, w = scene_weights(args, wl)
     p = O.inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden)
-    vol = (512, 512, 512)
-    lo, hi = O.inr_raw_range(p, table, w, vol, 8)  # same lattice as the GPU side
+    return cfg, table, w, p
+
+
+def cpu_baseline(args, wl, table, w, f, cached_img, uncached_img, un_stats):
+    """The oracle (single-threaded C, FP64) on a pixel window of frame f; for
+    the tera-scale volume (too large for a normalisation pass and a window in
+    a bounded CPU budget) its per-query rate times the frame's queries."""
+    import oracle as O
+    W, H = wl["W"], wl["H"]
+    cfg, table, w, p = oracle_scene(args, wl)
+    vol = wl["vol"]
+    cam, tf = frame_inputs(f, W, H, wl["camera"])
+    if wl["camera"] == "fly":
+        pts = np.random.default_rng(0).uniform(0, 1, (4000, 3)).astype(np.float32)
+        t0 = time.perf_counter()
+        O.inr_eval(p, table, w, pts)
+        dt = time.perf_counter() - t0
+        qps = len(pts) / dt
+        cpu = {"value": un_stats["inr_queries_direct"] / qps * 1e3, "unit": "ms/frame", "cores": 1,
+               "kind": "oracle", "inr_queries_per_s": qps,
+               "sample": f"{len(pts)} FP64 oracle INR queries ({dt:.1f} s), scaled to the "
+                         f"{un_stats['inr_queries_direct']} queries of an uncached frame"}
+        return cpu, {}
+    lo, hi = O.inr_raw_range(p, table, w, vol, wl["range_stride"])  # the GPU side's lattice
     p.vmin, p.vmax = -lo / (hi - lo), (1.0 - lo) / (hi - lo)
-    cam, tf = frame_inputs(f, W, H)
     oc = O.camera(**cam)
     cw = args.cpu_crop
     x0, y0 = W // 2 - cw // 2, H // 2 - cw // 2
+    mo = O.march_opts(K=32, eps_T=1e-3, lod_scale=args.lod_scale, step_mode=wl["step_mode"],
+                      step_lod_max=wl["step_lod_max"])
     t0 = time.perf_counter()
-    ref, st = O.render_direct(p, table, w, oc, vol, O.march_opts(K=32, eps_T=1e-3),
-                              tf.astype(np.float64), window=(x0, y0, cw, cw))
+    ref, st = O.render_direct(p, table, w, oc, vol, mo, tf.astype(np.float64),
+                              window=(x0, y0, cw, cw))
     dt = time.perf_counter() - t0
-    hit_full = 0
     mask = uncached_img[..., 3].cpu().numpy() > 0
     hit_full = int(mask.sum())
     hit_crop = int(mask[y0:y0 + cw, x0:x0 + cw].sum())
     ms_frame = dt * 1e3 * hit_full / max(hit_crop, 1)
     crop_c = cached_img[y0:y0 + cw, x0:x0 + cw].cpu().numpy().astype(np.float64)
     crop_u = uncached_img[y0:y0 + cw, x0:x0 + cw].cpu().numpy().astype(np.float64)
-    psnr_cached = O.psnr(crop_c, ref)
-    psnr_uncached = O.psnr(crop_u, ref)
     cpu = {"value": ms_frame, "unit": "ms/frame", "cores": 1, "kind": "oracle",
            "sample": f"uncached FP64 oracle on a {cw}x{cw} pixel window of frame {f} "
                      f"({st['samples']} samples, {dt:.1f} s), scaled by hit pixels "
-                     f"{hit_full}/{hit_crop} to a full 1024^2 frame",
+                     f"{hit_full}/{hit_crop} to a full {W}x{H} frame",
            "inr_queries_per_s": st["inr_queries_direct"] / dt}
-    return cpu, {"cached_vs_oracle": psnr_cached, "uncached_vs_oracle": psnr_uncached,
+    return cpu, {"cached_vs_oracle": O.psnr(crop_c, ref), "uncached_vs_oracle": O.psnr(crop_u, ref),
                  "window": [x0, y0, cw, cw]}
 
 
-def run_reference(args):
-    """The oracle as the reference arm: ms/frame on the machine's host cores."""
+def run_reference(args, wl):
+    """The oracle as the reference arm: ms/frame on the machine's host cores
+    (uncached FP64; a centre window of each frame scaled by pixel count)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     import oracle as O
-    from paper_2504_18001_gb300 import synthetic as S
-    cfg, table, w = scene_weights(args)
-    p = O.inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden)
-    vol = (512, 512, 512)
-    lo, hi = O.inr_raw_range(p, table, w, vol, 32)
-    p.vmin, p.vmax = -lo / (hi - lo), (1.0 - lo) / (hi - lo)
-    W = H = args.res
+    cfg, table, w, p = oracle_scene(args, wl)
+    vol = wl["vol"]
+    p.vmin, p.vmax = 0.0, 1.0  # timing only: the cost does not depend on the range
+    W, H = wl["W"], wl["H"]
     cw = args.ref_crop
+    mo = O.march_opts(K=32, eps_T=1e-3, lod_scale=args.lod_scale, step_mode=wl["step_mode"],
+                      step_lod_max=wl["step_lod_max"])
     per = []
-    hit_frac = []
-    for i in range(args.warmup + args.steps):
-        cam, tf = frame_inputs(i, W, H)
+    # the oracle keeps no state between frames: only the last 3 warm-up
+    # frames are run (untimed)
+    for i in range(max(args.warmup - 3, 0), args.warmup + args.steps):
+        cam, tf = frame_inputs(i, W, H, wl["camera"])
         oc = O.camera(**cam)
         x0, y0 = W // 2 - cw // 2, H // 2 - cw // 2
         t0 = time.perf_counter()
-        img, st = O.render_direct(p, table, w, oc, vol, O.march_opts(K=32, eps_T=1e-3),
-                                  tf.astype(np.float64), window=(x0, y0, cw, cw))
+        O.render_direct(p, table, w, oc, vol, mo, tf.astype(np.float64), window=(x0, y0, cw, cw))
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             per.append(dt * 1e3 * (W * H) / (cw * cw))
-            hit_frac.append(float((img[..., 3] > 0).mean()))
     val = float(sum(per) / len(per))
     return {"impl": "reference", "metric": METRIC, "value": val, "unit": "ms/frame",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": val,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "cached_fp32_512cube_1024px_orbit",
+            "data": "synthetic", "config": {"workload": wl["name"].format(prec=args.precision),
                                             "reference": "CPU FP64 oracle, uncached"},
             "cpu_baseline": {"value": val, "unit": "ms/frame", "cores": 1, "kind": "oracle",
                              "sample": f"{cw}x{cw} centre window per frame, scaled by pixel "
-                                       f"count to 1024^2"},
+                                       f"count to {W}x{H}"},
             "e2e": {"value": val, "unit": "ms/frame", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -408,9 +451,9 @@ def run_learned(args):
     def cached_psnr(tab, wts, ref_fn):
         m = cinr.Inr(cinr.make_inr_params(cfg, mlp_precision="bf16", table_precision="fp16"), tab,
                      wts)
-        cache = cinr.Cache(m, vol, pool_bytes=args.pool_mib << 20, brick=8, levels=4,
-                           n_req=args.n_req, storage="fp16")
-        out, ms = [], []
+        cache = cinr.Cache(m, vol, pool_bytes=4096 << 20, brick=8, levels=4, n_req=8192,
+                           storage="fp16")
+        psnr, ms = None, []
         for f in range(args.learned_frames):
             cam = S.orbit_camera(f, W, H)
             img, st = r.render(m, cam, tf, cache=cache)
@@ -418,8 +461,8 @@ def run_learned(args):
             if f == args.learned_frames - 1:
                 ref = ref_fn(cam)
                 mse = torch.mean((img[..., :3].double() - ref[..., :3].double()) ** 2).item()
-                out.append(10 * np.log10(1.0 / max(mse, 1e-30)))
-        return out[-1], float(np.mean(ms[-5:]))
+                psnr = 10 * np.log10(1.0 / max(mse, 1e-30))
+        return psnr, float(np.mean(ms[-5:]))
 
     def explicit(cam):
         return r.render_field(field, cam, tf)[0]
@@ -427,7 +470,7 @@ def run_learned(args):
     psnr_trained, ms_trained = cached_psnr(t_tab, t_w, explicit)
     psnr_untrained, _ = cached_psnr(table, w, explicit)
     steps = args.train_steps - 3
-    res = {
+    return {
         "metric": "PSNR (dB) of the trained INR's cached FP16 render vs the explicit-voxel render",
         "value": psnr_trained, "unit": "dB", "higher_is_better": True, "n_gpus": 1,
         "dtype": "f32 training; fp16/bf16 render",
@@ -436,49 +479,48 @@ def run_learned(args):
                    "inr": "L16 F2 T2^20 Nmin16 b1.38 MLP32-64-64-1", "batch": 1 << 18,
                    "lr": 1e-2, "steps": args.train_steps, "frames": args.learned_frames},
         "psnr_untrained_db": psnr_untrained,
-        "train": {"ms_per_step": train_ms / steps, "samples_per_s": steps * (1 << 18) / (train_ms * 1e-3),
+        "train": {"ms_per_step": train_ms / steps,
+                  "samples_per_s": steps * (1 << 18) / (train_ms * 1e-3),
                   "loss_first": losses[0] if losses else None, "loss_final": final_loss,
                   "field_gen_s": t_field},
         "cached_ms_per_frame_last5": ms_trained,
         "compression": {"field_bytes": 4 * dims[0] * dims[1] * dims[2],
                         "inr_bytes": 4 * (cfg.table_entries + cfg.mlp_params)},
     }
-    return res
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    # default: frames 90-149 timed (the last 30 orbit frames and the 30
-    # transfer-function edits) after 90 warm-up frames fill the cache, the
-    # steady state the paper measures (mean over the last frames of a run)
-    ap.add_argument("--steps", type=int, default=60)
-    ap.add_argument("--warmup", type=int, default=90)
+    ap.add_argument("--steps", type=int, default=None, help="timed frames (workload default)")
+    ap.add_argument("--warmup", type=int, default=None, help="warm-up frames (workload default)")
     ap.add_argument("--impl", default="cinr", choices=["cinr", "reference"])
-    ap.add_argument("--res", type=int, default=1024)
-    ap.add_argument("--brick", type=int, default=8)
-    ap.add_argument("--pool-mib", type=int, default=1024)
-    ap.add_argument("--n-req", type=int, default=4096)
-    ap.add_argument("--level-decay", type=float, default=0.5)
+    ap.add_argument("--workload", default="orbit", choices=["orbit", "terascale", "learned"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
     ap.add_argument("--ray-layout", type=int, default=0, choices=[0, 1])
-    ap.add_argument("--workload", default="orbit", choices=["orbit", "learned"])
-    ap.add_argument("--field", type=int, default=1024, help="learned: explicit field edge")
-    ap.add_argument("--train-steps", type=int, default=5000, help="learned: Adam steps")
-    ap.add_argument("--learned-frames", type=int, default=60, help="learned: cached frames")
     ap.add_argument("--lod-scale", type=float, default=1.0)
+    ap.add_argument("--level-decay", type=float, default=0.5)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--uncached-steps", type=int, default=5)
+    ap.add_argument("--uncached-steps", type=int, default=None)
     ap.add_argument("--cpu-crop", type=int, default=24)
     ap.add_argument("--ref-crop", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--res", type=int, default=1024, help="learned: image edge")
+    ap.add_argument("--field", type=int, default=1024, help="learned: explicit field edge")
+    ap.add_argument("--train-steps", type=int, default=5000, help="learned: Adam steps")
+    ap.add_argument("--learned-frames", type=int, default=60, help="learned: cached frames")
     args = ap.parse_args()
-    if args.warmup < 3:
-        ap.error("--warmup must be >= 3")
     if args.workload == "learned":
         res = run_learned(args)
     else:
-        res = run_reference(args) if args.impl == "reference" else run_gpu(args)
+        wl = WORKLOADS[args.workload]
+        if args.steps is None:
+            args.steps = wl["steps"]
+        if args.warmup is None:
+            args.warmup = wl["warmup"]
+        if args.warmup < 3:
+            ap.error("--warmup must be >= 3")
+        res = run_reference(args, wl) if args.impl == "reference" else run_gpu(args, wl)
     if res is not None:
         print(json.dumps(res))
 

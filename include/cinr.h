@@ -142,13 +142,14 @@ typedef struct {
  * bricks_requested = distinct bricks requested; bricks_decoded = bricks
  * written back; evictions = decoded bricks that replaced a resident one;
  * misses_recorded = entries of the miss record (capped); slots_touched =
- * distinct pool slots that served samples.  ms_frame_kernel and
- * ms_cache_update are device times (CUDA events on the frame's stream) of
- * the marching kernel and of the end-of-frame cache update. */
+ * distinct pool slots that served samples; kernel_launches = kernels the
+ * library launched for the frame.  ms_frame_kernel and ms_cache_update are
+ * device times (CUDA events on the frame's stream) of the marching kernel
+ * and of the end-of-frame cache update. */
 typedef struct {
   uint64_t samples, inr_queries_direct, inr_queries_decode, true_misses,
       fallback_hits, hits, bricks_requested, bricks_decoded, evictions,
-      misses_recorded, slots_touched;
+      misses_recorded, slots_touched, kernel_launches;
   float ms_frame_kernel, ms_cache_update;
 } cinr_frame_stats;
 

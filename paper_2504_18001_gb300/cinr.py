@@ -61,7 +61,8 @@ class cinr_frame_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "samples", "inr_queries_direct", "inr_queries_decode", "true_misses", "fallback_hits",
         "hits", "bricks_requested", "bricks_decoded", "evictions", "misses_recorded",
-        "slots_touched")] + [("ms_frame_kernel", C.c_float), ("ms_cache_update", C.c_float)]
+        "slots_touched", "kernel_launches")] + [("ms_frame_kernel", C.c_float),
+                                                ("ms_cache_update", C.c_float)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if t is C.c_float else int(getattr(self, n)))

@@ -573,6 +573,10 @@ int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStr
   commit_kernel<<<1, 1024, 0, s>>>(c->dev, c->req_sorted, c->req_n, c->vic_sorted, c->vic_n, frame,
                                    c->decode_n, stats_dev, (uint32_t)(c->dev.S * c->dev.S * c->dev.S));
   CINR_CK(cudaGetLastError());
+  // kernels of this update: per radix select reset + (hist, pick) per pass +
+  // gather + sort; commit; decode
+  auto sel = [](int bits) { return 3 + 2 * (bits <= 11 ? 1 : (bits + 10) / 11); };
+  c->last_launches = (uint32_t)(sel(rbits) + sel(vbits) + 2);
   return decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, s);
 }
 

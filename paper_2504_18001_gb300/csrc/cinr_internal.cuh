@@ -450,6 +450,7 @@ struct cinr_cache_s {
   uint32_t* vic_n;
   uint32_t* decode_n;
   int slot_bits, key_bits;
+  uint32_t last_launches;  // kernels of the last end-of-frame update
 };
 
 // Cache update at the end of a frame (request selection, victims, commit,

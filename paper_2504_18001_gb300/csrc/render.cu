@@ -842,6 +842,7 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
     stats->evictions = h[ST_EVICT];
     stats->misses_recorded = P.miss_rec ? (rec < P.miss_cap ? rec : P.miss_cap) : 0;
     stats->slots_touched = h[ST_SLOTS];
+    stats->kernel_launches = 1u + (cache ? cache->last_launches : 0u);
     float ms0 = 0.f, ms1 = 0.f;
     CINR_CK(cudaEventElapsedTime(&ms0, r->ev[0], r->ev[1]));
     CINR_CK(cudaEventElapsedTime(&ms1, r->ev[1], r->ev[2]));
