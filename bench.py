@@ -173,13 +173,24 @@ def run_gpu(args, wl):
     W, H = wl["W"], wl["H"]
     cfg, table, w, inr32, inr_c, vol = build_scene(args, wl, device)
     storage = "fp16" if args.precision == "mixed" else "fp32"
+    tuned = None
+    if args.autotune:
+        from paper_2504_18001_gb300 import autotune
+        best, trials = autotune.tune(
+            inr_c, inr32, vol, lambda f: frame_inputs(f, W, H, wl["camera"]), W, H,
+            bricks=(wl["brick"],), levels=wl["levels"], pool_mib=wl["pool_mib"], storage=storage,
+            lod_scale=args.lod_scale, step_mode=wl["step_mode"],
+            step_lod_max=wl["step_lod_max"], device=device)
+        wl = dict(wl, n_req=best["n_req"], brick=best["brick"])
+        args.ray_layout, args.graph = best["ray_layout"], best["use_graph"]
+        tuned = {"chosen": best, "trials": trials}
     S3 = (wl["brick"] + 2) ** 3
     cache = cinr.Cache(inr_c, vol, pool_bytes=wl["pool_mib"] << 20, brick=wl["brick"],
                        levels=wl["levels"], storage=storage, n_req=wl["n_req"], ranking=1,
                        preload=1, device=device)
     rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
                          ray_layout=args.ray_layout, seed=args.seed, step_mode=wl["step_mode"],
-                         step_lod_max=wl["step_lod_max"], device=device)
+                         step_lod_max=wl["step_lod_max"], use_graph=args.graph, device=device)
     img = torch.empty((H, W, 4), dtype=torch.float32, device=device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
@@ -283,6 +294,7 @@ def run_gpu(args, wl):
                    "n_req": wl["n_req"], "lod_scale": args.lod_scale, "K": 32, "eps_T": 1e-3,
                    "step_mode": wl["step_mode"], "step_lod_max": wl["step_lod_max"],
                    "ray_layout": "thread per ray" if args.ray_layout == 0 else "warp per ray",
+                   "cuda_graph": bool(args.graph),
                    "timed_frames": [args.warmup, last_f],
                    "l2": "flushed (256 MiB write) before every timed frame",
                    "parallelism": f"replicas x{world}"},
@@ -304,6 +316,8 @@ def run_gpu(args, wl):
                      "peak_kind": peak_kind},
         "clocks": clk,
     }
+    if tuned is not None:
+        res["autotune"] = tuned
     mse = torch.mean((cached_img[..., :3].double() - uncached_img[..., :3].double()) ** 2).item()
     res["psnr_db"] = {"cached_vs_uncached_full_frame": 10 * np.log10(1.0 / max(mse, 1e-30))}
     if rank == 0 and not args.no_cpu:
@@ -498,6 +512,10 @@ def main():
     ap.add_argument("--workload", default="orbit", choices=["orbit", "terascale", "learned"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
     ap.add_argument("--ray-layout", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--graph", type=int, default=0, choices=[0, 1],
+                    help="run each frame's launch sequence as a CUDA graph")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the free knobs (n_req, ray layout, CUDA graph) first")
     ap.add_argument("--lod-scale", type=float, default=1.0)
     ap.add_argument("--level-decay", type=float, default=0.5)
     ap.add_argument("--seed", type=int, default=0)

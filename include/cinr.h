@@ -118,6 +118,7 @@ typedef struct {
   int ray_layout;
   int step_mode;
   int step_lod_max;
+  int use_graph; /* 1: each frame's launch sequence runs as a CUDA graph */
 } cinr_march_opts;
 
 /* Cache options (Sec. 4.3): brick = interior edge B (stored with a one-voxel

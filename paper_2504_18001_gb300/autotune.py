@@ -1,0 +1,68 @@
+"""Autotuner of the renderer's free knobs on the GPU.
+
+The paper names brick size and the per-frame request budget (maxNumRequests)
+as performance knobs that leave image quality unchanged (Sec. 6.4).  This
+tuner times short runs of a workload for every candidate setting of the
+knobs the workload leaves free -- requests per frame (which also sets the
+decode batch that the persistent decode kernel takes), the ray layout of the
+marching kernel (one ray per thread or per warp), whether each frame runs as
+a CUDA graph, and the brick edge -- and returns the fastest setting whose
+cached frame stays within `min_psnr` dB of the uncached FP32 frame.
+All timing is on the device (CUDA events around the frame's launch
+sequence); every candidate builds its own cache and renderer.
+"""
+from __future__ import annotations
+
+import itertools
+import time
+
+import numpy as np
+
+
+def _psnr(a, b):
+    import torch
+    mse = torch.mean((a[..., :3].double() - b[..., :3].double()) ** 2).item()
+    return 10.0 * np.log10(1.0 / max(mse, 1e-30))
+
+
+def tune(inr_cached, inr_fp32, vol, frame_inputs, W, H, *, bricks=(8,), n_reqs=(1024, 4096, 8192),
+         layouts=(0, 1), graphs=(0, 1), levels=4, pool_mib=1024, storage="fp16", warmup=40, timed=10,
+         lod_scale=1.0, step_mode=0, step_lod_max=0, min_psnr=40.0, device="cuda"):
+    """Returns (best, results): best is the chosen knob dict; results lists
+    every candidate with its mean ms/frame and PSNR."""
+    import torch
+    from . import cinr
+
+    img = torch.empty((H, W, 4), dtype=torch.float32, device=device)
+    ref = torch.empty_like(img)
+    results = []
+    for brick, n_req, layout, graph in itertools.product(bricks, n_reqs, layouts, graphs):
+        t0 = time.perf_counter()
+        cache = cinr.Cache(inr_cached, vol, pool_bytes=pool_mib << 20, brick=brick, levels=levels,
+                           n_req=n_req, storage=storage, device=device)
+        rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_scale=lod_scale, ray_layout=layout,
+                             step_mode=step_mode, step_lod_max=step_lod_max, use_graph=graph,
+                             device=device)
+        for f in range(warmup):
+            cam, tf = frame_inputs(f)
+            rend.render(inr_cached, cam, tf, cache=cache, out=img)
+        ms = []
+        for f in range(warmup, warmup + timed):
+            cam, tf = frame_inputs(f)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rend.render(inr_cached, cam, tf, cache=cache, out=img)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        cam, tf = frame_inputs(warmup + timed - 1)
+        rend.render(inr_fp32, cam, tf, cache=None, out=ref)
+        psnr = _psnr(img, ref)
+        results.append(dict(brick=brick, n_req=n_req, ray_layout=layout, use_graph=graph,
+                            ms_per_frame=float(np.mean(ms)), psnr_db=psnr,
+                            tune_s=time.perf_counter() - t0))
+        del cache, rend
+        torch.cuda.synchronize()
+    ok = [r for r in results if r["psnr_db"] >= min_psnr] or results
+    best = min(ok, key=lambda r: r["ms_per_frame"])
+    return {k: best[k] for k in ("brick", "n_req", "ray_layout", "use_graph")}, results

@@ -49,7 +49,7 @@ class cinr_march_opts(C.Structure):
     _fields_ = [("dims", C.c_int * 3), ("K", C.c_int), ("eps_T", C.c_float),
                 ("lod_mode", C.c_int), ("lod_scale", C.c_float), ("seed", C.c_uint64),
                 ("miss_record_cap", C.c_long), ("ray_layout", C.c_int), ("step_mode", C.c_int),
-                ("step_lod_max", C.c_int)]
+                ("step_lod_max", C.c_int), ("use_graph", C.c_int)]
 
 
 class cinr_cache_opts(C.Structure):
@@ -366,11 +366,13 @@ class Trainer:
 
 class Renderer:
     def __init__(self, width, height, dims, K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0,
-                 miss_record_cap=0, ray_layout=0, step_mode=0, step_lod_max=0, device="cuda"):
+                 miss_record_cap=0, ray_layout=0, step_mode=0, step_lod_max=0, use_graph=0,
+                 device="cuda"):
         L = lib()
         self.opts = cinr_march_opts((C.c_int * 3)(*dims), int(K), float(eps_T), int(lod_mode),
                                     float(lod_scale), int(seed), int(miss_record_cap),
-                                    int(ray_layout), int(step_mode), int(step_lod_max))
+                                    int(ray_layout), int(step_mode), int(step_lod_max),
+                                    int(use_graph))
         nbytes = C.c_size_t()
         check(L.cinr_renderer_bytes(int(width), int(height), C.byref(self.opts), C.byref(nbytes)),
               "cinr_renderer_bytes")

@@ -35,6 +35,8 @@ struct cinr_renderer_s {
   uint64_t frame;                // frame counter of uncached rendering
   int device;
   cudaEvent_t ev[3];             // frame kernel start/end, cache update end
+  cudaStream_t cap = nullptr;    // capture stream of the per-frame CUDA graph
+  cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -765,6 +767,43 @@ int check_opts(int W, int H, const cinr_march_opts* o) {
   return CINR_OK;
 }
 
+// Captures one frame's launch sequence into a CUDA graph on the renderer's
+// capture stream, updates the executable graph of the previous frame in
+// place (same topology, new parameters) or instantiates a new one, and
+// launches it on the caller's stream.
+template <class F>
+int launch_as_graph(cinr_renderer_s* r, F&& enqueue, cudaStream_t s) {
+  if (!r->cap) CINR_CK(cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking));
+  CINR_CK(cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal));
+  const int e = enqueue(r->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(r->cap, &g);
+  if (e) {
+    if (g) cudaGraphDestroy(g);
+    return e;
+  }
+  if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
+  if (r->exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(r->exec, g, &info) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cudaGraphExecDestroy(r->exec);
+      r->exec = nullptr;
+    }
+  }
+  if (!r->exec) {
+    const cudaError_t ie = cudaGraphInstantiate(&r->exec, g, 0);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(g);
+      r->exec = nullptr;
+      return cuda_error(ie, "cudaGraphInstantiate");
+    }
+  }
+  cudaGraphDestroy(g);
+  CINR_CK(cudaGraphLaunch(r->exec, s));
+  return CINR_OK;
+}
+
 int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_camera* cam,
            const cinr_tf* tf, float4* out, cinr_frame_stats* stats, cudaStream_t s) {
   if (!r || !inr || !cam || !tf) return set_error(CINR_ERR_ARG, "NULL argument");
@@ -803,26 +842,33 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
   P.miss_cap = (uint32_t)r->o.miss_record_cap;
   P.miss_count = r->counters + 1;
 
-  CINR_CK(cudaMemsetAsync(r->counters, 0, 64 * 4, s));
-  CINR_CK(cudaMemsetAsync(r->stats, 0, ST_COUNT * 8, s));
-  if (cache) CINR_CK(cudaMemsetAsync(cache->dev.touched_count, 0, 4, s));
-  CINR_CK(cudaEventRecord(r->ev[0], s));
   P.w16 = inr->w16;
   P.err = reinterpret_cast<int*>(r->counters + 2);
-  int e;
-  if (!cache)
-    e = launch_frame_shape<false>(P, inr->p.mlp_precision, s);
-  else if (r->o.ray_layout == 1)
-    e = launch_frame_shape<true>(P, inr->p.mlp_precision, s);
-  else
-    e = launch_march_cached_shape(P, s);
+  // The frame's device work, enqueued on q: the caller's stream, or the
+  // renderer's capture stream when the frame runs as a CUDA graph.
+  auto enqueue = [&](cudaStream_t q) -> int {
+    CINR_CK(cudaMemsetAsync(r->counters, 0, 64 * 4, q));
+    CINR_CK(cudaMemsetAsync(r->stats, 0, ST_COUNT * 8, q));
+    if (cache) CINR_CK(cudaMemsetAsync(cache->dev.touched_count, 0, 4, q));
+    CINR_CK(cudaEventRecord(r->ev[0], q));
+    int ee;
+    if (!cache)
+      ee = launch_frame_shape<false>(P, inr->p.mlp_precision, q);
+    else if (r->o.ray_layout == 1)
+      ee = launch_frame_shape<true>(P, inr->p.mlp_precision, q);
+    else
+      ee = launch_march_cached_shape(P, q);
+    if (ee) return ee;
+    CINR_CK(cudaEventRecord(r->ev[1], q));
+    if (cache) {
+      ee = cinr_cache_end_frame(cache, r->stats, q);
+      if (ee) return ee;
+    }
+    CINR_CK(cudaEventRecord(r->ev[2], q));
+    return CINR_OK;
+  };
+  int e = r->o.use_graph ? launch_as_graph(r, enqueue, s) : enqueue(s);
   if (e) return e;
-  CINR_CK(cudaEventRecord(r->ev[1], s));
-  if (cache) {
-    e = cinr_cache_end_frame(cache, r->stats, s);
-    if (e) return e;
-  }
-  CINR_CK(cudaEventRecord(r->ev[2], s));
   unsigned long long h[ST_COUNT];
   uint32_t cnt[3] = {0, 0, 0};  // ray counter, miss-record count, device error word
   CINR_CK(cudaMemcpyAsync(h, r->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -894,8 +940,11 @@ extern "C" int cinr_create_renderer(void* dev_mem, size_t bytes, int width, int 
 }
 
 extern "C" int cinr_destroy_renderer(cinr_renderer_t r) {
-  if (r)
+  if (r) {
     for (int i = 0; i < 3; ++i) cudaEventDestroy(r->ev[i]);
+    if (r->exec) cudaGraphExecDestroy(r->exec);
+    if (r->cap) cudaStreamDestroy(r->cap);
+  }
   delete r;
   return CINR_OK;
 }

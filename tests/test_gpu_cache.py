@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 
 def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_req=40, ranking=1,
          preload=1, lod_scale=1.0, lod_mode=0, storage="fp32", K=32, eps=0.0, check_pixels=2e-3,
-         cam_fn=None, mlp="fp32", tab="fp32", ray_layout=0, step_mode=0, step_lod_max=0):
+         cam_fn=None, mlp="fp32", tab="fp32", ray_layout=0, step_mode=0, step_lod_max=0,
+         use_graph=0):
     from paper_2504_18001_gb300 import cinr
     cfg = S.INR_64
     table, w = scene(cfg)
@@ -31,7 +32,7 @@ def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_r
                  preload=preload)
     r = cinr.Renderer(W, H, vol, K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
                       ray_layout=ray_layout, step_mode=step_mode, step_lod_max=step_lod_max,
-                      miss_record_cap=W * H * 4000)
+                      use_graph=use_graph, miss_record_cap=W * H * 4000)
     tf = S.tf_ramps(2)
     worst = 0.0
     history = []
@@ -141,6 +142,14 @@ def test_cached_early_termination_both_layouts_agree():
         sts.append(st)
     assert np.abs(imgs[0] - imgs[1]).max() < 2e-3
     assert abs(sts[0]["samples"] - sts[1]["samples"]) <= 32 * 4
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_frames_as_cuda_graphs_match_oracle(layout):
+    # each frame captured, the executable graph updated with the new frame's
+    # parameters and replayed: same state, misses and pixels as the oracle
+    _run(5, slots=60, ray_layout=layout, use_graph=1)
+    _run(3, preload=0, slots=400, n_req=100, ray_layout=layout, use_graph=1)
 
 
 @pytest.mark.parametrize("layout", [0, 1])
