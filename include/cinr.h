@@ -49,6 +49,7 @@ typedef void* cinr_stream_t;
 #define CINR_PREC_FP32 0
 #define CINR_PREC_FP16 1
 #define CINR_PREC_BF16 2
+#define CINR_PREC_FP8 3 /* MLP only: E4M3 operands, FP32 accumulation (trial) */
 
 /* INR hyper-parameters: a multiresolution hash-grid encoder (m levels, n
  * features per level, a table of 2^log2_table entries per level) feeding a

@@ -19,7 +19,7 @@ from . import build as _build
 _lib = None
 
 CINR_OK = 0
-PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3}
 DUMP_PAGE_TABLE, DUMP_STAMPS, DUMP_OWNERS, DUMP_RANK, DUMP_REQUESTS, DUMP_VICTIMS, \
     DUMP_MISSES, DUMP_PINNED, DUMP_POOL = range(9)
 

@@ -113,7 +113,7 @@ __device__ __forceinline__ int key_level(const CacheDev& c, uint32_t key) {
 // per-frame request count read from the device.
 // Mode list: request i of *n_dev uses keys[i] and slots[i].  Mode preload
 // (keys == nullptr): request i is brick off[L-1] + i into slot i.
-// MLPP: 0 = FP32 SIMT MLP, 1 / 2 = FP16 / BF16 tensor cores.
+// MLPP: 0 = FP32 SIMT MLP, 1 / 2 / 3 = FP16 / BF16 / FP8 tensor cores.
 template <int IN, int H, int MLPP>
 __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const uint16_t* w16,
                                                      const uint32_t* keys, const uint32_t* slots,
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
   if (blockIdx.x >= work) return;  // block-uniform, before any barrier
   uint32_t phase = 0;
   if (MLPP) {
-    tc::load_tc_weights(tcs, w16, q.w);
+    tc::load_tc_weights<IN, H, (MLPP > 0 ? MLPP - 1 : 0)>(tcs, w16, q.w);
     tc::tc_setup(tcs);
   } else {
     load_weights(sw, q.w, mlp_floats<IN, H>());
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
     } else {
       float feat[IN];
       encode_point<IN / 2>(q, x[0], x[1], x[2], feat);
-      y = tc::mlp_tile<IN, H, MLPP == 2>(tcs, feat, valid, phase, err);
+      y = tc::mlp_tile<IN, H, (MLPP > 0 ? MLPP - 1 : 0)>(tcs, feat, valid, phase, err);
     }
     if (valid) {
       const float val = fmaf(q.vscale, y, q.vmin);
@@ -449,6 +449,7 @@ int decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys, const
            const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s) {
   if (inr->p.mlp_precision == CINR_PREC_FP16) return decode_prec<1>(inr, c, keys, slots, n_dev, n_grid, s);
   if (inr->p.mlp_precision == CINR_PREC_BF16) return decode_prec<2>(inr, c, keys, slots, n_dev, n_grid, s);
+  if (inr->p.mlp_precision == CINR_PREC_FP8) return decode_prec<3>(inr, c, keys, slots, n_dev, n_grid, s);
   return decode_prec<0>(inr, c, keys, slots, n_dev, n_grid, s);
 }
 

@@ -23,8 +23,8 @@ int validate(const cinr_inr_params* p) {
   if (p->base_res < 1 || !(p->growth >= 1.0)) return set_error(CINR_ERR_ARG, "bad level scale");
   if (p->table_precision != CINR_PREC_FP32 && p->table_precision != CINR_PREC_FP16)
     return set_error(CINR_ERR_ARG, "table_precision must be FP32 or FP16");
-  if (p->mlp_precision < CINR_PREC_FP32 || p->mlp_precision > CINR_PREC_BF16)
-    return set_error(CINR_ERR_ARG, "mlp_precision must be FP32, FP16 or BF16");
+  if (p->mlp_precision < CINR_PREC_FP32 || p->mlp_precision > CINR_PREC_FP8)
+    return set_error(CINR_ERR_ARG, "mlp_precision must be FP32, FP16, BF16 or FP8");
   return CINR_OK;
 }
 

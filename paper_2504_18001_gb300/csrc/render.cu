@@ -108,7 +108,7 @@ __device__ __forceinline__ float brick_sample(const CacheDev& c, int l, uint32_t
   return fmaf(f[2], y1 - y0, y0);
 }
 
-// MLPP: 0 = FP32 SIMT MLP, 1 = FP16 tensor cores, 2 = BF16 tensor cores.
+// MLPP: 0 = FP32 SIMT MLP, 1 / 2 / 3 = FP16 / BF16 / FP8 tensor cores.
 template <int IN, int H, bool CACHED, int MLPP>
 __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
     frame_kernel(const __grid_constant__ FrameParams P) {
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
   // memory stays small, leaving the SM's L1 to the brick voxels.
   const float* wmlp = CACHED ? P.inr.w : sw;
   if (MLPP) {
-    tc::load_tc_weights(tcs, P.w16, P.inr.w);
+    tc::load_tc_weights<IN, H, (MLPP > 0 ? MLPP - 1 : 0)>(tcs, P.w16, P.inr.w);
     tc::tc_setup(tcs);
   } else {
     if (!CACHED) load_weights(sw, P.inr.w, mlp_floats<IN, H>());
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
       } else {
         float feat[IN];
         if (mine) encode_point<IN / 2>(P.inr, m.x, m.y, m.z, feat);
-        r = tc::mlp_tile<IN, H, MLPP == 2>(tcs, feat, mine, phase, P.err);
+        r = tc::mlp_tile<IN, H, (MLPP > 0 ? MLPP - 1 : 0)>(tcs, feat, mine, phase, P.err);
       }
       if (mine) {
         const int slot = __float_as_int(m.w);
@@ -434,8 +434,6 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
   const size_t S3 = (size_t)S * S * S;
   const void* pool = c.pool;
   uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0;
-  uint32_t memo_key = 0xFFFFFFFFu, memo_e = 0u;  // last page-table lookup of this lane
-  uint32_t stamped = 0xFFFFFFFFu;                // last slot this lane saw stamped
   const uint32_t n_tiles = P.n_rays >> 5;
   while (true) {
     uint32_t tile = 0;
@@ -482,13 +480,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           b1 = min(max(b1, 0), g.nb1 - 1);
           b2 = min(max(b2, 0), g.nb2 - 1);
           const uint32_t key = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
-          // page tables change only between frames: the lane's last lookup
-          // is reused while consecutive samples stay in one brick
-          if (key != memo_key) {
-            memo_key = key;
-            memo_e = __ldg(c.pt + key);
-          }
-          const uint32_t e = memo_e;
+          const uint32_t e = __ldg(c.pt + key);
           if (!(e & kMapped)) {
             if (lev == l) {
               want_req = true;
@@ -539,11 +531,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           atomicMin(c.rank + req_key, P.Tf + 1000u);
         }
       }
-      // LRU stamp: a lane checks a slot again only when it changes (a slot
-      // stamped this frame stays stamped until the frame ends)
-      const bool fresh = hit && hit_slot != stamped;
-      if (fresh) stamped = hit_slot;
-      const bool stale = fresh && c.stamp[hit_slot] != P.frame;
+      const bool stale = hit && c.stamp[hit_slot] != P.frame;
       const unsigned hm = __ballot_sync(kFull, stale);
       if (stale) {
         const unsigned peers = __match_any_sync(hm, hit_slot);
@@ -731,6 +719,7 @@ int launch_frame_shape(const FrameParams& P, int mlp_precision, cudaStream_t s) 
   if constexpr (CACHED) return launch_frame_prec<CACHED, 0>(P, s);
   if (mlp_precision == CINR_PREC_FP16) return launch_frame_prec<CACHED, 1>(P, s);
   if (mlp_precision == CINR_PREC_BF16) return launch_frame_prec<CACHED, 2>(P, s);
+  if (mlp_precision == CINR_PREC_FP8) return launch_frame_prec<CACHED, 3>(P, s);
   return launch_frame_prec<CACHED, 0>(P, s);
 }
 

@@ -62,13 +62,13 @@ __global__ void __launch_bounds__(128) debug_mma_kernel(const float* __restrict_
   if (threadIdx.x < 32) tc::tmem_dealloc(s.tmem, tc::kTmemCols);
 }
 
-template <int IN, int H, bool BF16>
+template <int IN, int H, int FMT>
 __global__ void __launch_bounds__(128) infer_tc_kernel(InrDev q, const uint16_t* __restrict__ w16,
                                                        const float* __restrict__ xyz, long n,
                                                        float* __restrict__ out, int* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   tc::TcSmem<IN, H>& s = *reinterpret_cast<tc::TcSmem<IN, H>*>(smem_raw);
-  tc::load_tc_weights(s, w16, q.w);
+  tc::load_tc_weights<IN, H, FMT>(s, w16, q.w);
   tc::tc_setup(s);
   uint32_t phase = 0;
   const long tiles = (n + 127) / 128;
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(128) infer_tc_kernel(InrDev q, const uint16_t*
       encode_point<IN / 2>(q, clamp01(__ldg(xyz + 3 * i)), clamp01(__ldg(xyz + 3 * i + 1)),
                            clamp01(__ldg(xyz + 3 * i + 2)), feat);
     }
-    const float y = tc::mlp_tile<IN, H, BF16>(s, feat, valid, phase, err);
+    const float y = tc::mlp_tile<IN, H, FMT>(s, feat, valid, phase, err);
     if (valid) out[i] = fmaf(q.vscale, y, q.vmin);
   }
   tc::tc_teardown(s);
@@ -97,9 +97,9 @@ int num_sms() {
   return n;
 }
 
-template <int IN, int H, bool BF16>
+template <int IN, int H, int FMT>
 int launch_infer_tc(const cinr_inr_s* inr, const float* xyz, long n, float* out, cudaStream_t s) {
-  auto k = infer_tc_kernel<IN, H, BF16>;
+  auto k = infer_tc_kernel<IN, H, FMT>;
   // Each resident CTA holds 64 of the SM's 512 TMEM columns: asking for at
   // least 1/8 of the SM's shared memory keeps at most 8 CTAs resident.
   int smem = (int)sizeof(tc::TcSmem<IN, H>);
@@ -120,18 +120,21 @@ int launch_infer_tc(const cinr_inr_s* inr, const float* xyz, long n, float* out,
 
 }  // namespace
 
-// Used by cinr_infer for FP16/BF16 MLPs.
-int cinr_infer_tc(const cinr_inr_s* inr, const float* xyz, long n, float* out, cudaStream_t s) {
-  const bool bf16 = inr->p.mlp_precision == CINR_PREC_BF16;
+template <int FMT>
+int infer_tc_fmt(const cinr_inr_s* inr, const float* xyz, long n, float* out, cudaStream_t s) {
   switch (shape_of(inr->dev.IN, inr->dev.H)) {
-    case Shape::S16x32:
-      return bf16 ? launch_infer_tc<16, 32, true>(inr, xyz, n, out, s) : launch_infer_tc<16, 32, false>(inr, xyz, n, out, s);
-    case Shape::S32x64:
-      return bf16 ? launch_infer_tc<32, 64, true>(inr, xyz, n, out, s) : launch_infer_tc<32, 64, false>(inr, xyz, n, out, s);
-    case Shape::S48x64:
-      return bf16 ? launch_infer_tc<48, 64, true>(inr, xyz, n, out, s) : launch_infer_tc<48, 64, false>(inr, xyz, n, out, s);
+    case Shape::S16x32: return launch_infer_tc<16, 32, FMT>(inr, xyz, n, out, s);
+    case Shape::S32x64: return launch_infer_tc<32, 64, FMT>(inr, xyz, n, out, s);
+    case Shape::S48x64: return launch_infer_tc<48, 64, FMT>(inr, xyz, n, out, s);
     default: return set_error(CINR_ERR_ARG, "unsupported shape");
   }
+}
+
+// Used by cinr_infer for FP16 / BF16 / FP8 MLPs.
+int cinr_infer_tc(const cinr_inr_s* inr, const float* xyz, long n, float* out, cudaStream_t s) {
+  if (inr->p.mlp_precision == CINR_PREC_BF16) return infer_tc_fmt<1>(inr, xyz, n, out, s);
+  if (inr->p.mlp_precision == CINR_PREC_FP8) return infer_tc_fmt<2>(inr, xyz, n, out, s);
+  return infer_tc_fmt<0>(inr, xyz, n, out, s);
 }
 
 extern "C" int cinr_debug_mma_tile(const float* a_dev, const float* b_dev, int K, int bf16, float* d_dev,

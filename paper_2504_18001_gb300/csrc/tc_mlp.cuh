@@ -1,14 +1,17 @@
 // Tensor-core MLP for tiles of 128 queries on sm_103a: tcgen05.mma with
 // operands in shared memory and the FP32 accumulator in tensor memory
 // (TMEM), read back with tcgen05.ld.  The MLP is in -> H (ReLU) -> H (ReLU)
-// -> 1 with FP16 or BF16 operands and FP32 accumulation; the last layer
-// (H -> 1) is a per-thread FP32 dot product.
+// -> 1 with FP16, BF16 or FP8 (E4M3) operands and FP32 accumulation; the
+// last layer (H -> 1) is a per-thread FP32 dot product.
 //
 // Shared-memory operand layout (no swizzle, K-major): 8-row x 16-byte core
-// matrices, stored 128 contiguous bytes each; core (r, k) of a rows x K
-// matrix sits at ((r/8) * (K/8) + k/8) * 128 bytes, so the core matrices
-// adjacent along K are 128 B apart (leading-dimension byte offset) and the
-// 8-row groups are (K/8) * 128 B apart (stride-dimension byte offset).
+// matrices, stored 128 contiguous bytes each; the core matrix of rows
+// r..r+7 and bytes kb..kb+15 of a rows x Kb-byte matrix sits at
+// ((r/8) * (Kb/16) + kb/16) * 128 bytes, so the core matrices adjacent
+// along K are 128 B apart (leading-dimension byte offset) and the 8-row
+// groups are (Kb/16) * 128 B apart (stride-dimension byte offset).  One MMA
+// consumes 32 bytes of K (16 FP16/BF16 or 32 FP8 elements); FP8 operands
+// are zero-padded to a multiple of 32 elements.
 //
 // Every wait on an mbarrier is bounded; on a timeout the routine records an
 // error word and carries on, so that the kernel always frees its TMEM and
@@ -17,6 +20,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 namespace cinr {
@@ -28,6 +32,19 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // Dynamic shared memory per CTA (bytes) that keeps at most 8 CTAs (8 x 64
 // TMEM columns = 512) resident on an SM of 228 KB shared memory.
 constexpr int kMinSmemPerCta = 29 * 1024;
+
+// Operand formats: 0 = FP16, 1 = BF16, 2 = FP8 E4M3.
+template <int FMT>
+struct Fmt {
+  static constexpr int bytes = FMT == 2 ? 1 : 2;
+  static constexpr uint32_t code = FMT == 1 ? 1u : 0u;  // instruction-descriptor A/B format
+};
+
+// K of an operand in bytes, padded to the 32-byte MMA step.
+template <int FMT>
+__host__ __device__ constexpr int kbytes(int K) {
+  return ((K * Fmt<FMT>::bytes + 31) / 32) * 32;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -90,21 +107,35 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
   return d;
 }
 
-// Instruction descriptor of kind::f16: D F32, A and B both FP16 (fmt 0) or
-// both BF16 (fmt 1), K-major, N and M.
+// Instruction descriptor: D F32, A and B of one format, K-major, N and M.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int fmt) {
   return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
 
+template <int FMT>
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                    uint32_t accumulate) {
+  if (FMT == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+
 __device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+  mma<0>(dtmem, adesc, bdesc, idesc, accumulate);
 }
 
 __device__ __forceinline__ void commit(uint64_t* bar) {
@@ -129,10 +160,13 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
 
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Byte offset of element (r, k) of a K-major operand with K columns.
-__device__ __forceinline__ uint32_t core_off(int r, int k, int K) {
-  return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+// Byte offset of byte kb of row r in a K-major operand of Kb bytes per row.
+__device__ __forceinline__ uint32_t core_off_b(int r, int kb, int Kb) {
+  return (uint32_t)((((r >> 3) * (Kb >> 4) + (kb >> 4)) << 7) + ((r & 7) << 4) + (kb & 15));
 }
+
+// Byte offset of 16-bit element (r, k) of a K-major operand with K columns.
+__device__ __forceinline__ uint32_t core_off(int r, int k, int K) { return core_off_b(r, k * 2, K * 2); }
 
 template <bool BF16>
 __device__ __forceinline__ uint16_t to16(float x) {
@@ -144,7 +178,11 @@ __device__ __forceinline__ uint16_t to16(float x) {
   return *reinterpret_cast<uint16_t*>(&h);
 }
 
-// Row r (8 values at k0..k0+7) of a K-major operand, one 16-byte store.
+__device__ __forceinline__ uint32_t to8(float x) {
+  return (uint32_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+
+// Row r (8 values at k0..k0+7) of a 16-bit K-major operand, one 16-byte store.
 template <bool BF16>
 __device__ __forceinline__ void store8(unsigned char* base, int r, int k0, int K, const float* v) {
   uint4 q;
@@ -155,11 +193,39 @@ __device__ __forceinline__ void store8(unsigned char* base, int r, int k0, int K
   *reinterpret_cast<uint4*>(base + core_off(r, k0, K)) = q;
 }
 
-// Shared memory of one CTA's tensor-core MLP.
+// Row r of an operand in format FMT: n values (a multiple of 8), zero-padded
+// to the padded K; 16-byte stores.
+template <int FMT, int N>
+__device__ __forceinline__ void store_row(unsigned char* base, int r, const float* v) {
+  constexpr int Kb = kbytes<FMT>(N);
+  if (FMT == 2) {
+#pragma unroll
+    for (int k0 = 0; k0 < Kb; k0 += 16) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t x = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int k = k0 + q * 4 + b;
+          x |= (k < N ? to8(v[k]) : 0u) << (8 * b);
+        }
+        w[q] = x;
+      }
+      *reinterpret_cast<uint4*>(base + core_off_b(r, k0, Kb)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+#pragma unroll
+    for (int k0 = 0; k0 < N; k0 += 8) store8<FMT == 1>(base, r, k0, N, v + k0);
+  }
+}
+
+// Shared memory of one CTA's tensor-core MLP (sized for 16-bit operands,
+// which also holds the zero-padded FP8 operands).
 template <int IN, int H>
 struct TcSmem {
-  alignas(128) unsigned char a[kM * IN * 2];   // features, K = IN
-  alignas(128) unsigned char a2[kM * H * 2];   // hidden layer 1, K = H
+  alignas(128) unsigned char a[kM * IN * 2];   // features
+  alignas(128) unsigned char a2[kM * H * 2];   // hidden layer 1
   alignas(128) unsigned char w1[H * IN * 2];   // W1 [H][IN]
   alignas(128) unsigned char w2[H * H * 2];    // W2 [H][H]
   float w3[H];
@@ -167,18 +233,30 @@ struct TcSmem {
   uint32_t tmem;
 };
 
-// Stage the half-precision weights (row-major [out][in] in global memory)
-// into the core-matrix layout and W3 (FP32) into shared memory.  All
-// threads of the CTA.
-template <int IN, int H>
+// Stage the weights into the core-matrix layout of format FMT and W3 (FP32)
+// into shared memory: 16-bit formats from the half-precision copy w16
+// (row-major [out][in]), FP8 converted from the FP32 weights.  All threads.
+template <int IN, int H, int FMT>
 __device__ __forceinline__ void load_tc_weights(TcSmem<IN, H>& s, const uint16_t* w16, const float* w32) {
-  for (int e = threadIdx.x; e < H * IN; e += blockDim.x) {
-    const int r = e / IN, k = e % IN;
-    *reinterpret_cast<uint16_t*>(s.w1 + core_off(r, k, IN)) = __ldg(w16 + e);
-  }
-  for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
-    const int r = e / H, k = e % H;
-    *reinterpret_cast<uint16_t*>(s.w2 + core_off(r, k, H)) = __ldg(w16 + H * IN + e);
+  if (FMT == 2) {
+    constexpr int K1 = kbytes<2>(IN), K2 = kbytes<2>(H);
+    for (int e = threadIdx.x; e < H * K1; e += blockDim.x) {
+      const int r = e / K1, k = e % K1;
+      s.w1[core_off_b(r, k, K1)] = (unsigned char)(k < IN ? to8(__ldg(w32 + r * IN + k)) : 0u);
+    }
+    for (int e = threadIdx.x; e < H * K2; e += blockDim.x) {
+      const int r = e / K2, k = e % K2;
+      s.w2[core_off_b(r, k, K2)] = (unsigned char)(k < H ? to8(__ldg(w32 + H * IN + r * H + k)) : 0u);
+    }
+  } else {
+    for (int e = threadIdx.x; e < H * IN; e += blockDim.x) {
+      const int r = e / IN, k = e % IN;
+      *reinterpret_cast<uint16_t*>(s.w1 + core_off(r, k, IN)) = __ldg(w16 + e);
+    }
+    for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
+      const int r = e / H, k = e % H;
+      *reinterpret_cast<uint16_t*>(s.w2 + core_off(r, k, H)) = __ldg(w16 + H * IN + e);
+    }
   }
   for (int e = threadIdx.x; e < H; e += blockDim.x) s.w3[e] = __ldg(w32 + H * IN + H * H + e);
 }
@@ -207,46 +285,45 @@ __device__ __forceinline__ void tc_teardown(TcSmem<IN, H>& s) {
 // when !valid) and gets the raw network output of row t.  All 128 threads
 // of the CTA (4 warps) must call it together.  `phase` is the mbarrier
 // parity this CTA waits for next (starts at 0); *err is set on a timeout.
-template <int IN, int H, bool BF16>
+template <int IN, int H, int FMT>
 __device__ __forceinline__ float mlp_tile(TcSmem<IN, H>& s, const float* feat, bool valid, uint32_t& phase,
                                           int* err) {
   const int t = threadIdx.x;
   const int warp = t >> 5;
+  constexpr int K1 = kbytes<FMT>(IN), K2 = kbytes<FMT>(H);
   {
-    float z[8];
+    float z[IN];
 #pragma unroll
-    for (int k0 = 0; k0 < IN; k0 += 8) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) z[i] = valid ? feat[k0 + i] : 0.0f;
-      store8<BF16>(s.a, t, k0, IN, z);
-    }
+    for (int i = 0; i < IN; ++i) z[i] = valid ? feat[i] : 0.0f;
+    store_row<FMT, IN>(s.a, t, z);
   }
   fence_proxy_async();
   __syncthreads();
-  constexpr uint32_t idesc = idesc_f16(kM, H, BF16 ? 1 : 0);
+  constexpr uint32_t idesc = idesc_f16(kM, H, Fmt<FMT>::code);
   const uint32_t dt = s.tmem;
   if (t == 0) {
     fence_after();
     const uint32_t a0 = smem_u32(s.a), b0 = smem_u32(s.w1);
 #pragma unroll
-    for (int kk = 0; kk < IN / 16; ++kk)
-      mma_f16(dt, sdesc(a0 + kk * 256, 128, (IN / 8) * 128), sdesc(b0 + kk * 256, 128, (IN / 8) * 128), idesc,
-              kk > 0 ? 1u : 0u);
+    for (int kk = 0; kk < K1 / 32; ++kk)
+      mma<FMT>(dt, sdesc(a0 + kk * 256, 128, (K1 / 16) * 128), sdesc(b0 + kk * 256, 128, (K1 / 16) * 128), idesc,
+               kk > 0 ? 1u : 0u);
     commit(&s.bar);
   }
   bool ok = mbar_wait(&s.bar, phase);
   phase ^= 1u;
   fence_after();
   const uint32_t lane_addr = dt + ((uint32_t)(warp * 32) << 16);
+  {
+    float h[H];
 #pragma unroll
-  for (int c0 = 0; c0 < H; c0 += 16) {
-    float v[16];
-    ld16(lane_addr + c0, v);
-    wait_ld();
+    for (int c0 = 0; c0 < H; c0 += 16) {
+      ld16(lane_addr + c0, h + c0);
+      wait_ld();
+    }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
-    store8<BF16>(s.a2, t, c0, H, v);
-    store8<BF16>(s.a2, t, c0 + 8, H, v + 8);
+    for (int i = 0; i < H; ++i) h[i] = fmaxf(h[i], 0.0f);
+    store_row<FMT, H>(s.a2, t, h);
   }
   fence_before();
   fence_proxy_async();
@@ -255,9 +332,9 @@ __device__ __forceinline__ float mlp_tile(TcSmem<IN, H>& s, const float* feat, b
     fence_after();
     const uint32_t a0 = smem_u32(s.a2), b0 = smem_u32(s.w2);
 #pragma unroll
-    for (int kk = 0; kk < H / 16; ++kk)
-      mma_f16(dt, sdesc(a0 + kk * 256, 128, (H / 8) * 128), sdesc(b0 + kk * 256, 128, (H / 8) * 128), idesc,
-              kk > 0 ? 1u : 0u);
+    for (int kk = 0; kk < K2 / 32; ++kk)
+      mma<FMT>(dt, sdesc(a0 + kk * 256, 128, (K2 / 16) * 128), sdesc(b0 + kk * 256, 128, (K2 / 16) * 128), idesc,
+               kk > 0 ? 1u : 0u);
     commit(&s.bar);
   }
   ok = mbar_wait(&s.bar, phase) && ok;
