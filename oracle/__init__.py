@@ -61,13 +61,18 @@ class Camera(C.Structure):
 class MarchOpts(C.Structure):
     _fields_ = [("K", C.c_int), ("eps_T", C.c_float), ("lod_mode", C.c_int),
                 ("lod_scale", C.c_float), ("seed", C.c_uint64), ("step_mode", C.c_int),
-                ("step_lod_max", C.c_int)]
+                ("step_lod_max", C.c_int), ("macro", C.c_void_p)]
+
+
+class Macro(C.Structure):
+    _fields_ = [("cell", C.c_int), ("dims", C.c_int * 3), ("skip", C.POINTER(C.c_uint8))]
 
 
 class Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "samples", "inr_queries_direct", "inr_queries_decode", "true_misses",
-        "fallback_hits", "hits", "bricks_requested", "bricks_decoded", "evictions")]
+        "fallback_hits", "hits", "bricks_requested", "bricks_decoded", "evictions",
+        "samples_skipped")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -126,6 +131,13 @@ _SIGS = {
     "orc_resident_sample": (C.c_double, [_P(InrParams), _dp, _dp, _ip, C.c_int, _fp]),
     "orc_brick_sample": (C.c_double, [_P(InrParams), _dp, _dp, _ip, C.c_int, C.c_int, _fp]),
     "orc_psnr": (C.c_double, [_dp, _dp, C.c_long]),
+    "orc_macro_dims": (None, [_ip, C.c_int, _ip]),
+    "orc_macro_ranges_inr": (None, [_P(InrParams), _dp, _dp, _ip, C.c_int, C.c_int, C.c_int,
+                                    _fp]),
+    "orc_macro_ranges_field": (None, [_fp, _ip, C.c_int, _fp]),
+    "orc_macro_skip": (None, [_fp, C.c_long, _dp, _P(C.c_uint8)]),
+    "orc_macro_cell_of": (C.c_long, [_P(Macro), _ip, _fp]),
+    "orc_cache_set_macro": (None, [C.c_void_p, C.c_void_p]),
     "orc_field_trilinear": (C.c_double, [_fp, _ip, _fp]),
     "orc_loss_grad": (C.c_double, [_P(InrParams), _dp, _dp, _fp, _dp, C.c_long, _dp, _dp]),
     "orc_adam": (None, [_dp, _dp, _dp, _dp, C.c_long, C.c_double, C.c_double, C.c_double,
@@ -182,9 +194,67 @@ def camera(eye, target, up, fov_y_deg, width, height, step_voxels) -> Camera:
 
 
 def march_opts(K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0, step_mode=0,
-               step_lod_max=0) -> MarchOpts:
-    return MarchOpts(int(K), float(eps_T), int(lod_mode), float(lod_scale), int(seed),
-                     int(step_mode), int(step_lod_max))
+               step_lod_max=0, macro=None) -> MarchOpts:
+    mo = MarchOpts(int(K), float(eps_T), int(lod_mode), float(lod_scale), int(seed),
+                   int(step_mode), int(step_lod_max), None)
+    if macro is not None:
+        mo.macro = C.cast(C.pointer(macro), C.c_void_p)
+        mo._keep = macro
+    return mo
+
+
+# ------------------------------------------------------------- macro cells
+def macro_dims(vol, cell):
+    v, vp = _i3(vol)
+    out = np.zeros(3, np.int32)
+    lib().orc_macro_dims(vp, int(cell), out.ctypes.data_as(_ip))
+    return tuple(int(a) for a in out)
+
+
+def macro_ranges_inr(p: InrParams, table, w, vol, cell, levels, min_level=0):
+    """Per-cell (min, max) over the cache's LoD voxels; float32 [cells, 2]."""
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    v, vp = _i3(vol)
+    n = int(np.prod(macro_dims(vol, cell)))
+    out = np.zeros((n, 2), np.float32)
+    lib().orc_macro_ranges_inr(C.byref(p), tp, wp, vp, int(cell), int(levels), int(min_level),
+                               out.ctypes.data_as(_fp))
+    return out
+
+
+def macro_ranges_field(field, cell):
+    """Per-cell (min, max) of an explicit field [z, y, x]; float32 [cells, 2]."""
+    fa, fp = _f(field)
+    fd, fdp = _i3(fa.shape[::-1])
+    n = int(np.prod(macro_dims(fa.shape[::-1], cell)))
+    out = np.zeros((n, 2), np.float32)
+    lib().orc_macro_ranges_field(fp, fdp, int(cell), out.ctypes.data_as(_fp))
+    return out
+
+
+def macro_skip(ranges, tf):
+    r, rp = _f(ranges)
+    tfa, tfp = _d(tf)
+    n = r.size // 2
+    out = np.zeros(n, np.uint8)
+    lib().orc_macro_skip(rp, n, tfp, out.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return out
+
+
+def macro(vol, cell, skip) -> Macro:
+    """Skip-flag structure for march_opts(macro=...) / Cache.render(macro=...)."""
+    sk = np.ascontiguousarray(skip, dtype=np.uint8)
+    m = Macro(int(cell), (C.c_int * 3)(*macro_dims(vol, cell)),
+              sk.ctypes.data_as(C.POINTER(C.c_uint8)))
+    m._keep = sk
+    return m
+
+
+def macro_cell_of(m: Macro, vol, x):
+    v, vp = _i3(vol)
+    xa, xp = _f(np.asarray(x, np.float32).reshape(3))
+    return int(lib().orc_macro_cell_of(C.byref(m), vp, xp))
 
 
 def splitmix64(x: int) -> int:
@@ -381,13 +451,18 @@ class Cache:
         lib().orc_cache_level_dims(self.h, level, d.ctypes.data_as(_ip), nb.ctypes.data_as(_ip))
         return d, nb
 
-    def render(self, cam: Camera, tf, window=None):
+    def render(self, cam: Camera, tf, window=None, macro=None):
+        """One cached frame; macro = skip flags of this frame's TF (or None)."""
         px0, py0, pw, ph = window if window is not None else (0, 0, cam.width, cam.height)
         tfa, tfp = _d(tf)
         out = np.zeros((ph, pw, 4), np.float64)
         st = Stats()
-        lib().orc_render_cached(self.h, C.byref(cam), tfp, px0, py0, pw, ph,
-                                out.ctypes.data_as(_dp), C.byref(st))
+        lib().orc_cache_set_macro(self.h, C.cast(C.pointer(macro), C.c_void_p) if macro else None)
+        try:
+            lib().orc_render_cached(self.h, C.byref(cam), tfp, px0, py0, pw, ph,
+                                    out.ctypes.data_as(_dp), C.byref(st))
+        finally:
+            lib().orc_cache_set_macro(self.h, None)
         return out, st.as_dict()
 
     def dump(self, what):

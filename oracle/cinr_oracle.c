@@ -520,6 +520,131 @@ static void composite(const double* tf, double v, double len, double C[3],
   *T = (*T) * (1.0 - alpha);
 }
 
+/* ===================================================================== */
+/* Macro cells (Sec. 5.2, adaptive sampling)                               */
+/* ===================================================================== */
+
+/* The volume is cut into ceil(V/N) cubes of N LoD-0 voxels per axis. */
+void orc_macro_dims(const int vol[3], int cell, int out[3]) {
+  for (int a = 0; a < 3; ++a) out[a] = (vol[a] + cell - 1) / cell;
+}
+
+/* Cell of a normalised position: floor(x V) / N per axis (binary32 product,
+ * the same LoD-0 coordinate that addresses the bricks), clamped to the last
+ * cell at the far faces. */
+long orc_macro_cell_of(const orc_macro* m, const int vol[3], const float x[3]) {
+  long ci[3];
+  for (int a = 0; a < 3; ++a) {
+    float pv = x[a] * (float)vol[a];
+    long i = (long)floorf(pv) / m->cell;
+    if (i > m->dims[a] - 1) i = m->dims[a] - 1;
+    ci[a] = i;
+  }
+  return ci[0] + (long)m->dims[0] * (ci[1] + (long)m->dims[1] * ci[2]);
+}
+
+static int macro_skips(const orc_march_opts* mo, const int vol[3],
+                       const float x[3]) {
+  return mo->macro && mo->macro->skip[orc_macro_cell_of(mo->macro, vol, x)];
+}
+
+/* LoD-l voxels a trilinear sample at LoD-0 edge coordinate e in [e0, e1] can
+ * read: the lower corner floor(clamp(e 2^-l - 1/2, 0, dims-1)) and the one
+ * above it, clamped to the grid. */
+static void macro_box(int e0, int e1, int l, int dim_l, int* lo, int* hi) {
+  float sc = 1.0f / (float)(1 << l), dmax = (float)(dim_l - 1);
+  float q0 = fminf(fmaxf((float)e0 * sc - 0.5f, 0.0f), dmax);
+  float q1 = fminf(fmaxf((float)e1 * sc - 0.5f, 0.0f), dmax);
+  int h = (int)floorf(q1) + 1;
+  *lo = (int)floorf(q0);
+  *hi = h > dim_l - 1 ? dim_l - 1 : h;
+}
+
+static float round_down_f(double d) {
+  float f = (float)d;
+  return (double)f > d ? nextafterf(f, -INFINITY) : f;
+}
+
+static float round_up_f(double d) {
+  float f = (float)d;
+  return (double)f < d ? nextafterf(f, INFINITY) : f;
+}
+
+/* Min / max of grid values g (dims, x fastest) over each cell's box at LoD l,
+ * merged into mn / mx. */
+static void macro_merge_level(const double* g, const int dims[3], int l,
+                              const int vol[3], int cell, const int md[3],
+                              double* mn, double* mx) {
+  for (int cz = 0; cz < md[2]; ++cz)
+    for (int cy = 0; cy < md[1]; ++cy)
+      for (int cx = 0; cx < md[0]; ++cx) {
+        int c3[3] = {cx, cy, cz}, lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+          int e1 = (c3[a] + 1) * cell;
+          macro_box(c3[a] * cell, e1 < vol[a] ? e1 : vol[a], l, dims[a], &lo[a], &hi[a]);
+        }
+        long ci = cx + (long)md[0] * (cy + (long)md[1] * cz);
+        for (int k = lo[2]; k <= hi[2]; ++k)
+          for (int j = lo[1]; j <= hi[1]; ++j)
+            for (int i = lo[0]; i <= hi[0]; ++i) {
+              double v = g[((long)k * dims[1] + j) * dims[0] + i];
+              if (v < mn[ci]) mn[ci] = v;
+              if (v > mx[ci]) mx[ci] = v;
+            }
+      }
+}
+
+static void macro_store(const double* mn, const double* mx, long n,
+                        float* ranges) {
+  for (long i = 0; i < n; ++i) {
+    ranges[2 * i] = round_down_f(mn[i]);
+    ranges[2 * i + 1] = round_up_f(mx[i]);
+  }
+}
+
+/* Skip rule.  A sample of value v reads transfer-function entries floor(x)
+ * and floor(x)+1, x = clamp(v,0,1) 255, so over a cell whose values lie in
+ * [lo, hi] it can only reach entries floor(x_lo) .. floor(x_hi)+1.  When all
+ * of them have zero extinction every sample in the cell has alpha = 0 and
+ * leaves colour and transmittance unchanged: the cell is skipped (mu_max = 0,
+ * Sec. 5.2).  READING: the range is widened by 2^-20 on both sides (binary32)
+ * so that rounding in a trilinear sample or in x never leaves it. */
+void orc_macro_skip(const float* ranges, long n_cells, const double* tf,
+                    uint8_t* skip) {
+  const float margin = 9.5367431640625e-07f; /* 2^-20 */
+  for (long c = 0; c < n_cells; ++c) {
+    float lo = clamp01(ranges[2 * c] - margin);
+    float hi = clamp01(ranges[2 * c + 1] + margin);
+    int i0 = (int)floorf(lo * 255.0f);
+    int i1 = (int)floorf(hi * 255.0f) + 1;
+    if (i1 > 255) i1 = 255;
+    uint8_t s = 1;
+    for (int i = i0; i <= i1; ++i)
+      if (tf[i * 4 + 3] != 0.0) s = 0;
+    skip[c] = s;
+  }
+}
+
+void orc_macro_ranges_field(const float* field, const int dims[3], int cell,
+                            float* ranges) {
+  int md[3];
+  orc_macro_dims(dims, cell, md);
+  long n = (long)md[0] * md[1] * md[2], nv = (long)dims[0] * dims[1] * dims[2];
+  double* mn = (double*)malloc(sizeof(double) * n);
+  double* mx = (double*)malloc(sizeof(double) * n);
+  double* g = (double*)malloc(sizeof(double) * nv);
+  for (long i = 0; i < n; ++i) {
+    mn[i] = INFINITY;
+    mx[i] = -INFINITY;
+  }
+  for (long i = 0; i < nv; ++i) g[i] = (double)field[i];
+  macro_merge_level(g, dims, 0, dims, cell, md, mn, mx);
+  macro_store(mn, mx, n, ranges);
+  free(mn);
+  free(mx);
+  free(g);
+}
+
 /* Cache-off rendering: every sample is inferred directly by the INR
  * (Alg. 1 with every sample a miss).  Termination is tested only after each
  * segment of K samples (wavefront loop of Sec. 5.1).  Renders the pixel
@@ -544,11 +669,15 @@ void orc_render_direct(const orc_inr_params* p, const double* table,
         float x[3], tm, len;
         if (!orc_sample_sched(cam, vol, mo, o, d, tn, tf_, k, &sc, x, &tm, &len))
           break;
-        double v = inr_one(p, table, w, x, feat, act);
-        st->samples++;
-        st->inr_queries_direct++;
-        st->true_misses++;
-        composite(tf, v, (double)len, C, &T);
+        if (macro_skips(mo, vol, x)) {
+          st->samples_skipped++;
+        } else {
+          double v = inr_one(p, table, w, x, feat, act);
+          st->samples++;
+          st->inr_queries_direct++;
+          st->true_misses++;
+          composite(tf, v, (double)len, C, &T);
+        }
         if ((k + 1) % mo->K == 0 && T < (double)mo->eps_T) break;
       }
       out[0] = C[0];
@@ -583,9 +712,13 @@ void orc_render_field(const float* field, const int fdims[3],
         float x[3], tm, len;
         if (!orc_sample_sched(cam, vol, mo, o, d, tn, tf_, k, &sc, x, &tm, &len))
           break;
-        double v = orc_field_trilinear(field, fdims, x);
-        st->samples++;
-        composite(tf, v, (double)len, C, &T);
+        if (macro_skips(mo, vol, x)) {
+          st->samples_skipped++;
+        } else {
+          double v = orc_field_trilinear(field, fdims, x);
+          st->samples++;
+          composite(tf, v, (double)len, C, &T);
+        }
         if ((k + 1) % mo->K == 0 && T < (double)mo->eps_T) break;
       }
       out[0] = C[0];
@@ -657,6 +790,48 @@ static float voxel_centre(int j, int l, int dim_l, int V) {
   if (j > dim_l - 1) j = dim_l - 1;
   float t = ((float)j + 0.5f) * (float)(1 << l);
   return clamp01(t / (float)V);
+}
+
+/* Cell ranges from the INR: every LoD-l voxel grid (l in [min_level,
+ * levels)) evaluated at its voxel centres, then min / max over each cell's
+ * box.  READING: the paper builds the ranges during training from the data;
+ * without the data they are taken from the voxels the cache serves, which
+ * bounds every cached sample (a trilinear blend of them). */
+void orc_macro_ranges_inr(const orc_inr_params* p, const double* table,
+                          const double* w, const int vol[3], int cell,
+                          int levels, int min_level, float* ranges) {
+  int md[3];
+  orc_macro_dims(vol, cell, md);
+  long n = (long)md[0] * md[1] * md[2];
+  double* mn = (double*)malloc(sizeof(double) * n);
+  double* mx = (double*)malloc(sizeof(double) * n);
+  for (long i = 0; i < n; ++i) {
+    mn[i] = INFINITY;
+    mx[i] = -INFINITY;
+  }
+  double* feat = (double*)malloc(sizeof(double) * p->in_dim);
+  double* act = (double*)malloc(sizeof(double) * 2 * p->hidden);
+  for (int l = min_level; l < levels; ++l) {
+    int dims[3], nb[3];
+    level_geometry(vol, 1, l, dims, nb);
+    long nv = (long)dims[0] * dims[1] * dims[2];
+    double* g = (double*)malloc(sizeof(double) * nv);
+    for (int k = 0; k < dims[2]; ++k)
+      for (int j = 0; j < dims[1]; ++j)
+        for (int i = 0; i < dims[0]; ++i) {
+          float x[3] = {voxel_centre(i, l, dims[0], vol[0]),
+                        voxel_centre(j, l, dims[1], vol[1]),
+                        voxel_centre(k, l, dims[2], vol[2])};
+          g[((long)k * dims[1] + j) * dims[0] + i] = inr_one(p, table, w, x, feat, act);
+        }
+    macro_merge_level(g, dims, l, vol, cell, md, mn, mx);
+    free(g);
+  }
+  macro_store(mn, mx, n, ranges);
+  free(feat);
+  free(act);
+  free(mn);
+  free(mx);
 }
 
 /* Brick (bx,by,bz) at LoD l stores voxels [b*B - 1, b*B + B] per axis, i.e.
@@ -943,49 +1118,54 @@ void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
         if (!orc_sample_sched(cam, c->vol, &c->mo, o, d, tn, tf_, k, &sc, x, &tm,
                               &len))
           break;
-        st->samples++;
-        int l = orc_sample_lod(cam, c->vol, &c->mo, L, 0,
-                               orc_sample_state(rs, (uint32_t)k), tm);
-        double v = 0.0;
-        int found = 0;
-        for (int lev = l; lev < L; ++lev) {
-          float s[3];
-          int b[3];
-          level_coord(x, c->vol, lev, s);
-          brick_of(s, B, c->nb[lev], b);
-          long key = c->off[lev] +
-                     b[0] + (long)c->nb[lev][0] * (b[1] + (long)c->nb[lev][1] * b[2]);
-          uint32_t e = c->pt[key];
-          if (!(e & PT_MAPPED)) {
-            if (lev == l) {
-              uint32_t r = c->rank[key];
-              if (r < Tf) {
-                r = Tf;
-                st->bricks_requested++;
+        if (macro_skips(&c->mo, c->vol, x)) {
+          /* transparent cell (Sec. 5.2): no LoD, no lookup, no request */
+          st->samples_skipped++;
+        } else {
+          st->samples++;
+          int l = orc_sample_lod(cam, c->vol, &c->mo, L, 0,
+                                 orc_sample_state(rs, (uint32_t)k), tm);
+          double v = 0.0;
+          int found = 0;
+          for (int lev = l; lev < L; ++lev) {
+            float s[3];
+            int b[3];
+            level_coord(x, c->vol, lev, s);
+            brick_of(s, B, c->nb[lev], b);
+            long key = c->off[lev] +
+                       b[0] + (long)c->nb[lev][0] * (b[1] + (long)c->nb[lev][1] * b[2]);
+            uint32_t e = c->pt[key];
+            if (!(e & PT_MAPPED)) {
+              if (lev == l) {
+                uint32_t r = c->rank[key];
+                if (r < Tf) {
+                  r = Tf;
+                  st->bricks_requested++;
+                }
+                r = r + 1u;
+                if (r > Tf + 1000u) r = Tf + 1000u;
+                c->rank[key] = r;
               }
-              r = r + 1u;
-              if (r > Tf + 1000u) r = Tf + 1000u;
-              c->rank[key] = r;
+              continue;
             }
-            continue;
+            long slot = (long)(e & ~PT_MAPPED);
+            v = brick_trilinear(c->pool + slot * S3, S, B, b, c->dims[lev], s);
+            c->stamp[slot] = (uint32_t)f;
+            if (lev == l)
+              st->hits++;
+            else
+              st->fallback_hits++;
+            found = 1;
+            break;
           }
-          long slot = (long)(e & ~PT_MAPPED);
-          v = brick_trilinear(c->pool + slot * S3, S, B, b, c->dims[lev], s);
-          c->stamp[slot] = (uint32_t)f;
-          if (lev == l)
-            st->hits++;
-          else
-            st->fallback_hits++;
-          found = 1;
-          break;
+          if (!found) {
+            st->true_misses++;
+            st->inr_queries_direct++;
+            push_miss(c, pixel, (uint32_t)k);
+            v = inr_one(&c->p, c->table, c->w, x, feat, act);
+          }
+          composite(tf, v, (double)len, C, &T);
         }
-        if (!found) {
-          st->true_misses++;
-          st->inr_queries_direct++;
-          push_miss(c, pixel, (uint32_t)k);
-          v = inr_one(&c->p, c->table, c->w, x, feat, act);
-        }
-        composite(tf, v, (double)len, C, &T);
         if ((k + 1) % c->mo.K == 0 && T < (double)c->mo.eps_T) break;
       }
       out[0] = C[0];
@@ -1053,6 +1233,8 @@ void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
   st->bricks_decoded = (uint64_t)m;
   st->inr_queries_decode = (uint64_t)m * (uint64_t)S3;
 }
+
+void orc_cache_set_macro(orc_cache* c, const orc_macro* m) { c->mo.macro = m; }
 
 long orc_cache_dump(const orc_cache* c, int what, uint32_t* out, long cap) {
   const uint32_t* src = NULL;

@@ -53,7 +53,16 @@ typedef struct {
   uint64_t seed;       /* per-run seed of the per-frame dither seed */
   int step_mode;       /* 0 fixed step, 1 LoD-scaled 32-sample segments */
   int step_lod_max;    /* highest LoD that scales the step (mode 1) */
+  const struct orc_macro* macro; /* macro-cell skip flags, NULL = off */
 } orc_march_opts;
+
+/* Macro cells (Sec. 5.2): ceil(V/cell) cubes per axis; skip[c] = 1 when the
+ * current transfer function is transparent over cell c's value range. */
+typedef struct orc_macro {
+  int cell;            /* edge in LoD-0 voxels */
+  int dims[3];         /* cells per axis */
+  const uint8_t* skip; /* one flag per cell, x fastest */
+} orc_macro;
 
 typedef struct {
   float ts, dts;       /* segment start and step (schedule state of a ray) */
@@ -61,7 +70,8 @@ typedef struct {
 
 typedef struct {
   uint64_t samples, inr_queries_direct, inr_queries_decode, true_misses,
-      fallback_hits, hits, bricks_requested, bricks_decoded, evictions;
+      fallback_hits, hits, bricks_requested, bricks_decoded, evictions,
+      samples_skipped;
 } orc_stats;
 
 /* ---- random generators (published definitions) ---- */
@@ -122,6 +132,22 @@ void orc_render_field(const float* field, const int fdims[3],
                       const orc_march_opts* mo, const double* tf, int px0,
                       int py0, int pw, int ph, double* rgba, orc_stats* st);
 
+/* ---- macro cells for adaptive sampling (Sec. 5.2) ---- */
+void orc_macro_dims(const int vol[3], int cell, int out[3]);
+/* Value range of each cell: min and max over every LoD-l voxel (l in
+ * [min_level, levels)) that a trilinear sample inside the cell can read,
+ * INR values at the voxel centres; float pairs rounded outwards. */
+void orc_macro_ranges_inr(const orc_inr_params* p, const double* table,
+                          const double* w, const int vol[3], int cell,
+                          int levels, int min_level, float* ranges);
+/* The same over the voxels of an explicit field (LoD 0). */
+void orc_macro_ranges_field(const float* field, const int dims[3], int cell,
+                            float* ranges);
+/* Skip flags of a transfer function (256 x rgba, a = extinction). */
+void orc_macro_skip(const float* ranges, long n_cells, const double* tf,
+                    uint8_t* skip);
+long orc_macro_cell_of(const orc_macro* m, const int vol[3], const float x[3]);
+
 /* ---- multi-resolution brick cache (Sec. 4.3) ---- */
 typedef struct orc_cache orc_cache;
 typedef struct {
@@ -141,6 +167,8 @@ long orc_cache_num_bricks(const orc_cache* c);
 long orc_cache_level_offset(const orc_cache* c, int level);
 void orc_cache_level_dims(const orc_cache* c, int level, int dims[3],
                           int nb[3]);
+/* Macro-cell skip flags used by the following renders (NULL = off). */
+void orc_cache_set_macro(orc_cache* c, const orc_macro* m);
 void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
                        int px0, int py0, int pw, int ph, double* rgba,
                        orc_stats* st);

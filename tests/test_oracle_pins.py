@@ -548,3 +548,141 @@ def test_field_render_constant_field_closed_form():
             a = 1.0 - math.exp(-6.0 * (tf_ - tn)) if hit else 0.0
             assert img[py, px, 3] == pytest.approx(a, abs=1e-12)
     assert st["samples"] > 0
+
+
+# ------------------------------------------------------------ macro cells
+def _step_tf(first_opaque, sigma=25.0):
+    # transparent below entry `first_opaque`, constant extinction above
+    tf = np.zeros((256, 4), np.float64)
+    tf[:, 0], tf[:, 1], tf[:, 2] = 1.0, 0.6, 0.3
+    tf[first_opaque:, 3] = sigma
+    return tf
+
+
+def test_macro_dims_and_cell_of_hand_computed():
+    # ceil(V/N) cells per axis; cell = floor(x V) / N, far faces clamped
+    assert O.macro_dims((64, 40, 17), 16) == (4, 3, 2)
+    m = O.macro((64, 40, 17), 16, np.zeros(24, np.uint8))
+    assert O.macro_cell_of(m, (64, 40, 17), (0.0, 0.0, 0.0)) == 0
+    assert O.macro_cell_of(m, (64, 40, 17), (1.0, 1.0, 1.0)) == 3 + 4 * (2 + 3 * 1)
+    # x = 0.25 -> 16 voxels: cell 1; y = 0.39 -> 15.6: cell 0; z = 0.95 -> 16.15: cell 1
+    assert O.macro_cell_of(m, (64, 40, 17), (0.25, 0.39, 0.95)) == 1 + 4 * (0 + 3 * 1)
+
+
+def test_macro_field_ranges_bound_samples_and_are_tight():
+    # Every trilinear sample of the field lies inside its cell's range (a
+    # convex blend of the voxels the range covers); the range covers at least
+    # the voxels centred inside the cell and at most those within one voxel of
+    # it.  Catches a box that is too small (bound fails) or too wide.
+    rng = np.random.default_rng(5)
+    dims, N = (20, 12, 16), 4
+    z, y, x = np.meshgrid(*[np.arange(d) for d in dims[::-1]], indexing="ij")
+    ramp = (x + 2 * y + 3 * z).astype(np.float32)  # extremes at the box corners
+    for f in (rng.normal(size=dims[::-1]).astype(np.float32), ramp):
+        _check_field_ranges(f, dims, N)
+
+
+def _check_field_ranges(f, dims, N):
+    r = O.macro_ranges_field(f, N)
+    md = O.macro_dims(dims, N)
+    m = O.macro(dims, N, np.zeros(int(np.prod(md)), np.uint8))
+    for x in S.random_points(4000, seed=3):
+        v = O.field_trilinear(f, x)
+        c = O.macro_cell_of(m, dims, x)
+        assert r[c, 0] <= v <= r[c, 1]
+    centres = [np.arange(d) + 0.5 for d in dims]
+    for cz in range(md[2]):
+        for cy in range(md[1]):
+            for cx in range(md[0]):
+                c3 = (cx, cy, cz)
+                inner = [(cc >= c * N) & (cc < min((c + 1) * N, d)) for cc, c, d in zip(centres, c3, dims)]
+                outer = [(cc >= c * N - 1) & (cc <= min((c + 1) * N, d) + 1) for cc, c, d in zip(centres, c3, dims)]
+                fi = f[np.ix_(inner[2], inner[1], inner[0])]
+                fo = f[np.ix_(outer[2], outer[1], outer[0])]
+                ci = cx + md[0] * (cy + md[1] * cz)
+                assert fo.min() <= r[ci, 0] <= fi.min()
+                assert fi.max() <= r[ci, 1] <= fo.max()
+
+
+def test_macro_inr_ranges_bound_resident_samples_at_every_lod():
+    # The ranges from the INR's LoD voxels bound every fully resident sample
+    # (brute-force whole-grid trilinear, no cache code) at every LoD.
+    p, table, w = _small_inr(seed=1)
+    vol, N, levels = (32, 24, 40), 8, 3
+    r = O.macro_ranges_inr(p, table, w, vol, N, levels)
+    m = O.macro(vol, N, np.zeros(len(r), np.uint8))
+    for x in S.random_points(300, seed=8):
+        c = O.macro_cell_of(m, vol, x)
+        for lev in range(levels):
+            v = O.resident_sample(p, table, w, vol, lev, x)
+            assert r[c, 0] <= v <= r[c, 1]
+    # fewer levels give narrower (or equal) ranges
+    r1 = O.macro_ranges_inr(p, table, w, vol, N, levels, min_level=1)
+    assert np.all(r1[:, 0] >= r[:, 0]) and np.all(r1[:, 1] <= r[:, 1])
+
+
+def test_macro_skip_rule_sound_and_near_tight():
+    # Skip only when the TF has zero extinction at every value of the range
+    # (dense check through the oracle's TF lookup); keep a cell only when some
+    # value within one TF entry (plus the 2^-20 margin) of the range is opaque.
+    tf = np.zeros((256, 4), np.float64)
+    tf[100:121, 3] = 7.0
+    tf[200, 3] = 3.0
+    rng = np.random.default_rng(2)
+    lo = rng.uniform(-0.1, 1.0, 400)
+    hi = lo + rng.uniform(0.0, 0.3, 400) ** 2
+    ranges = np.stack([lo, hi], 1).astype(np.float32)
+    skip = O.macro_skip(ranges, tf)
+    pad = 2.0 ** -20 + 1.0 / 255 + 1e-9
+    for (a, b), s in zip(ranges.astype(np.float64), skip):
+        vs = np.concatenate([[a, b], np.linspace(a, b, 3000)])
+        sig = [O.tf_lookup(tf, v)[3] for v in vs]
+        if s:
+            assert max(sig) == 0.0
+        else:
+            wide = np.linspace(a - pad, b + pad, 6000)
+            assert max(O.tf_lookup(tf, v)[3] for v in wide) > 0.0
+    assert 0 < skip.sum() < len(skip)
+
+
+def _blob_field(dims=(48, 40, 32)):
+    z, y, x = np.meshgrid(*[(np.arange(d) + 0.5) / d for d in dims[::-1]], indexing="ij")
+    r2 = (x - 0.45) ** 2 + (y - 0.55) ** 2 + (z - 0.5) ** 2
+    return np.exp(-r2 / 0.02).astype(np.float32)
+
+
+def test_macro_skip_leaves_field_render_unchanged():
+    # Skipped samples have alpha = 0 exactly: the image is identical and only
+    # the sample count drops (and termination is unaffected).
+    f = _blob_field()
+    vol = f.shape[::-1]
+    tf = _step_tf(80)
+    cam = O.camera((1.2, 0.6, 1.6), (0, 0, 0), (0, 1, 0), 40.0, 24, 20, 0.5)
+    for eps in (0.0, 1e-2):
+        mo = O.march_opts(K=32, eps_T=eps)
+        ref, st0 = O.render_field(f, cam, vol, mo, tf)
+        mac = O.macro(vol, 8, O.macro_skip(O.macro_ranges_field(f, 8), tf))
+        img, st1 = O.render_field(f, cam, vol, O.march_opts(K=32, eps_T=eps, macro=mac), tf)
+        assert np.array_equal(img, ref)
+        assert st1["samples_skipped"] > 0.3 * st0["samples"]
+        assert st1["samples"] + st1["samples_skipped"] == st0["samples"]
+
+
+def test_macro_skip_leaves_first_cached_frame_unchanged():
+    # A fresh cache with the coarsest LoD preloaded has no true misses, so
+    # every sample is a trilinear blend of LoD voxels that the INR ranges
+    # bound: skipping changes neither the image nor the hit samples; it only
+    # withholds the requests of transparent cells.
+    c0, cam, _, p, table, w, vol = _cache_scene(n_req=6)
+    c1, *_ = _cache_scene(n_req=6)
+    r = O.macro_ranges_inr(p, table, w, vol, 8, 3)
+    theta = float(np.median(r[:, 1]))
+    tf = _step_tf(int(np.clip(theta, 0, 1) * 255) + 1)
+    mac = O.macro(vol, 8, O.macro_skip(r, tf))
+    ref, st0 = c0.render(cam, tf)
+    img, st1 = c1.render(cam, tf, macro=mac)
+    assert st1["samples_skipped"] > 0
+    assert np.array_equal(img, ref)
+    assert st1["samples"] + st1["samples_skipped"] == st0["samples"]
+    assert st1["true_misses"] == st0["true_misses"] == 0
+    assert st1["bricks_requested"] <= st0["bricks_requested"]
