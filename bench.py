@@ -191,6 +191,15 @@ def run_gpu(args, wl):
     rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
                          ray_layout=args.ray_layout, seed=args.seed, step_mode=wl["step_mode"],
                          step_lod_max=wl["step_lod_max"], use_graph=args.graph, device=device)
+    macro_ms = None
+    if args.macro:
+        # macro cells (Sec. 5.2) built from the cache's own decode arithmetic:
+        # skipping transparent cells leaves cached samples unchanged
+        t0 = time.perf_counter()
+        mac = cinr.Macro(vol, args.macro, inr=inr_c, cache=cache, min_level=args.macro_min_level)
+        torch.cuda.synchronize()
+        macro_ms = (time.perf_counter() - t0) * 1e3
+        rend.set_macro(mac)
     img = torch.empty((H, W, 4), dtype=torch.float32, device=device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
@@ -295,6 +304,7 @@ def run_gpu(args, wl):
                    "step_mode": wl["step_mode"], "step_lod_max": wl["step_lod_max"],
                    "ray_layout": "thread per ray" if args.ray_layout == 0 else "warp per ray",
                    "cuda_graph": bool(args.graph),
+                   "macro_cell": args.macro or None,
                    "timed_frames": [args.warmup, last_f],
                    "l2": "flushed (256 MiB write) before every timed frame",
                    "parallelism": f"replicas x{world}"},
@@ -305,6 +315,10 @@ def run_gpu(args, wl):
         "uncached": {"ms_per_frame": uncached_ms,
                      "inr_queries_per_s": un_q / (sum(un_ms) * 1e-3), "frames": n_un},
         "speedup_cached_vs_uncached": uncached_ms / cached_ms,
+        "macro": ({"cell": args.macro, "min_level": args.macro_min_level, "build_ms": macro_ms,
+                   "skipped_fraction": sum(s["samples_skipped"] for s in stats)
+                   / max(1, sum(s["samples_skipped"] + s["samples"] for s in stats))}
+                  if args.macro else None),
         "frame_stats_last": stats[-1],
         "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": 4096 + 64,
                 "d2h_bytes_per_step": W * H * 16 + 104},
@@ -503,15 +517,59 @@ def run_learned(args):
     }
 
 
+def run_infer(args):
+    """Direct INR inference throughput (InferINR of Alg. 1) per MLP precision:
+    FP32 SIMT and FP16 / BF16 / FP8 tensor cores, the 512^3 scene's INR
+    (L=16, T=2^19, MLP 32-64-64-1, FP16 table for the tensor-core paths) on
+    2^22 random points; MLP FLOP/s against the measured dense BF16 peak."""
+    import torch
+    from paper_2504_18001_gb300 import cinr
+    torch.cuda.set_device(0)
+    wl = WORKLOADS["orbit"]
+    cfg, table, w = scene_weights(args, wl)
+    n = args.points
+    pts = torch.rand((n, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    out = torch.empty(n, device="cuda")
+    peaks, kind = load_peaks()
+    flops_q = 2 * (cfg.in_dim * cfg.hidden + cfg.hidden * cfg.hidden + cfg.hidden)
+    rows = {}
+    for prec, tab in (("fp32", "fp32"), ("fp16", "fp16"), ("bf16", "fp16"), ("fp8", "fp16")):
+        inr = cinr.Inr(cinr.make_inr_params(cfg, mlp_precision=prec, table_precision=tab), table, w)
+        for _ in range(3):
+            inr.infer(pts, out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps or 10):
+            inr.infer(pts, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (args.steps or 10)
+        qps = n / (ms * 1e-3)
+        rows[prec] = {"ms": ms, "queries_per_s": qps, "mlp_tflops": qps * flops_q / 1e12,
+                      "frac_of_bf16_peak": qps * flops_q / 1e12 / peaks["bf16_tflops"]}
+    return {"metric": "INR queries/s (direct inference)", "value": rows["bf16"]["queries_per_s"],
+            "unit": "queries/s", "higher_is_better": True, "n_gpus": 1, "dtype": "bf16",
+            "data": "synthetic", "config": {"workload": "infer_512cube_inr", "points": n,
+                                            "mlp_flop_per_query": flops_q, "peak_kind": kind},
+            "by_precision": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None, help="timed frames (workload default)")
     ap.add_argument("--warmup", type=int, default=None, help="warm-up frames (workload default)")
     ap.add_argument("--impl", default="cinr", choices=["cinr", "reference"])
-    ap.add_argument("--workload", default="orbit", choices=["orbit", "terascale", "learned"])
+    ap.add_argument("--workload", default="orbit",
+                    choices=["orbit", "terascale", "learned", "infer"])
+    ap.add_argument("--points", type=int, default=1 << 22, help="infer: batch size")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
     ap.add_argument("--ray-layout", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--macro", type=int, default=0,
+                    help="macro-cell edge for empty-space skipping (0 = off)")
+    ap.add_argument("--macro-min-level", type=int, default=0,
+                    help="finest LoD whose voxels enter the macro-cell ranges")
     ap.add_argument("--graph", type=int, default=0, choices=[0, 1],
                     help="run each frame's launch sequence as a CUDA graph")
     ap.add_argument("--autotune", action="store_true",
@@ -530,6 +588,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "learned":
         res = run_learned(args)
+    elif args.workload == "infer":
+        res = run_infer(args)
     else:
         wl = WORKLOADS[args.workload]
         if args.steps is None:

@@ -44,6 +44,7 @@ typedef struct cinr_inr_s* cinr_inr_t;
 typedef struct cinr_cache_s* cinr_cache_t;
 typedef struct cinr_renderer_s* cinr_renderer_t;
 typedef struct cinr_trainer_s* cinr_trainer_t;
+typedef struct cinr_macro_s* cinr_macro_t;
 typedef void* cinr_stream_t;
 
 #define CINR_PREC_FP32 0
@@ -145,13 +146,15 @@ typedef struct {
  * written back; evictions = decoded bricks that replaced a resident one;
  * misses_recorded = entries of the miss record (capped); slots_touched =
  * distinct pool slots that served samples; kernel_launches = kernels the
- * library launched for the frame.  ms_frame_kernel and ms_cache_update are
+ * library launched for the frame; samples_skipped = samples in macro cells
+ * that are transparent under the frame's transfer function (not counted in
+ * samples; no lookup, request or inference).  ms_frame_kernel and ms_cache_update are
  * device times (CUDA events on the frame's stream) of the marching kernel
  * and of the end-of-frame cache update. */
 typedef struct {
   uint64_t samples, inr_queries_direct, inr_queries_decode, true_misses,
       fallback_hits, hits, bricks_requested, bricks_decoded, evictions,
-      misses_recorded, slots_touched, kernel_launches;
+      misses_recorded, slots_touched, kernel_launches, samples_skipped;
   float ms_frame_kernel, ms_cache_update;
 } cinr_frame_stats;
 
@@ -275,6 +278,79 @@ int cinr_render_field(cinr_renderer_t r, const float* field_dev,
                       cinr_frame_stats* stats, cinr_stream_t stream);
 
 int cinr_destroy_renderer(cinr_renderer_t r);
+
+/* -------------------------------------------------------- macro cells --- */
+
+/* Macro cells for adaptive sampling (Sec. 5.2).  The volume is cut into
+ * ceil(dims/cell) cubes of cell^3 LoD-0 voxels; each holds the minimum and
+ * maximum data value of its region.  Whenever a frame's transfer function
+ * is applied, a cell whose value range meets only entries of zero extinction
+ * (mu_max = 0) is marked transparent, and samples whose LoD-0 position
+ * floor(x*dims) falls into a marked cell are skipped: no LoD pick, page-table
+ * lookup, request, inference or compositing.  The skip rule: a value v reads
+ * TF entries floor(x) and floor(x)+1, x = clamp(v,0,1)*255 (binary32), so a
+ * cell with range [lo, hi] is transparent when the extinction of entries
+ * floor(X(lo - 2^-20)) .. floor(X(hi + 2^-20)) + 1 (capped at 255) is zero.
+ * With ranges that bound every value a sample in the cell can take (true
+ * for CINR_MACRO_FROM_INR with a cache and for CINR_MACRO_FROM_FIELD with
+ * cinr_render_field), skipping leaves the image unchanged. */
+#define CINR_MACRO_FROM_INR 0    /* min/max of the INR at LoD voxel centres */
+#define CINR_MACRO_FROM_RANGES 1 /* caller-provided ranges (host)           */
+#define CINR_MACRO_FROM_FIELD 2  /* min/max of an explicit device field     */
+
+/* source FROM_INR: for every LoD l in [min_level, levels), the LoD-l voxels
+ * that a trilinear sample inside the cell can read -- per axis from
+ * floor(clamp(c*cell/2^l - 1/2)) to floor(clamp(min((c+1)*cell, dims)/2^l -
+ * 1/2)) + 1, clamped to the LoD-l grid -- are evaluated by the INR at their
+ * voxel centres.  With cache != NULL the values are computed exactly as that
+ * cache decodes and stores bricks (its LoD count, the INR's MLP precision
+ * and the storage precision), so the ranges bound every cached sample;
+ * `levels` is then ignored.  With cache == NULL the INR is evaluated as by
+ * cinr_infer.  source FROM_RANGES: ranges_host holds 2 floats (min, max) per
+ * cell, x fastest.  source FROM_FIELD: field_dev is a device array of
+ * dims[0]*dims[1]*dims[2] floats (x fastest) and the ranges cover the LoD-0
+ * voxels as above.  cell: a power of two in [2, 1024]. */
+typedef struct {
+  int dims[3];
+  int cell;
+  int source;
+  cinr_inr_t inr;
+  cinr_cache_t cache;
+  int levels;
+  int min_level;
+  const float* ranges_host;
+  const float* field_dev;
+} cinr_macro_desc;
+
+/* Device bytes of a macro-cell structure: 8 bytes of range and 1 byte of
+ * skip flag per cell. */
+int cinr_macro_bytes(const int dims[3], int cell, size_t* bytes);
+
+/* Builds the ranges in dev_mem (enqueued on `stream`; FROM_RANGES copies
+ * synchronously).  Errors: CINR_ERR_ARG (bad cell, dims or source
+ * arguments), CINR_ERR_NOMEM (buffer too small). */
+int cinr_create_macro(const cinr_macro_desc* d, void* dev_mem, size_t bytes,
+                      cinr_stream_t stream, cinr_macro_t* out);
+
+/* Copies the ranges (2 floats per cell) or the skip flags of the last
+ * applied transfer function (1 byte per cell) to host memory; synchronises
+ * `stream`.  n = capacity in elements. */
+int cinr_macro_ranges(cinr_macro_t m, float* host_out, size_t n,
+                      cinr_stream_t stream);
+int cinr_macro_skip_flags(cinr_macro_t m, uint8_t* host_out, size_t n,
+                          cinr_stream_t stream);
+
+/* Recomputes the skip flags for `tf` (one kernel, enqueued on `stream`). */
+int cinr_macro_apply_tf(cinr_macro_t m, const cinr_tf* tf,
+                        cinr_stream_t stream);
+
+int cinr_destroy_macro(cinr_macro_t m);
+
+/* Attaches m (NULL detaches) to the renderer: every following frame
+ * (cinr_render_frame, cinr_render_frame_host, cinr_render_field) first
+ * applies its transfer function to m (one extra kernel) and skips the
+ * samples of transparent cells.  m's dims must equal the renderer's dims. */
+int cinr_renderer_set_macro(cinr_renderer_t r, cinr_macro_t m);
 
 /* Allocation-free uncached render.  The paper has no counterpart: this is a
  * convenience for callers that cannot allocate device memory -- a real-time

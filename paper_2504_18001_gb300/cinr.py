@@ -61,13 +61,21 @@ class cinr_frame_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "samples", "inr_queries_direct", "inr_queries_decode", "true_misses", "fallback_hits",
         "hits", "bricks_requested", "bricks_decoded", "evictions", "misses_recorded",
-        "slots_touched", "kernel_launches")] + [("ms_frame_kernel", C.c_float),
-                                                ("ms_cache_update", C.c_float)]
+        "slots_touched", "kernel_launches", "samples_skipped")] + [
+            ("ms_frame_kernel", C.c_float), ("ms_cache_update", C.c_float)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if t is C.c_float else int(getattr(self, n)))
                 for n, t in self._fields_}
 
+
+class cinr_macro_desc(C.Structure):
+    _fields_ = [("dims", C.c_int * 3), ("cell", C.c_int), ("source", C.c_int),
+                ("inr", C.c_void_p), ("cache", C.c_void_p), ("levels", C.c_int),
+                ("min_level", C.c_int), ("ranges_host", C.c_void_p), ("field_dev", C.c_void_p)]
+
+
+MACRO_FROM_INR, MACRO_FROM_RANGES, MACRO_FROM_FIELD = 0, 1, 2
 
 _vp = C.c_void_p
 _P = C.POINTER
@@ -108,6 +116,13 @@ _SIGS = {
     "cinr_debug_mma_tile": [_vp, _vp, C.c_int, C.c_int, _vp, _vp],
     "cinr_inr_status": [_vp, _vp],
     "cinr_cache_level_info": [_vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_long)],
+    "cinr_macro_bytes": [_P(C.c_int), C.c_int, _P(C.c_size_t)],
+    "cinr_create_macro": [_P(cinr_macro_desc), _vp, C.c_size_t, _vp, _P(_vp)],
+    "cinr_macro_ranges": [_vp, _vp, C.c_size_t, _vp],
+    "cinr_macro_skip_flags": [_vp, _vp, C.c_size_t, _vp],
+    "cinr_macro_apply_tf": [_vp, _vp, _vp],
+    "cinr_destroy_macro": [_vp],
+    "cinr_renderer_set_macro": [_vp, _vp],
 }
 
 
@@ -282,6 +297,68 @@ class Cache:
             pass
 
 
+class Macro:
+    """Macro cells of Sec. 5.2 (per-cell value ranges; skip flags per TF).
+
+    source: Inr (with an optional Cache whose stored values the ranges must
+    bound), a float32 array of ranges [cells, 2] (host), or a device field
+    tensor [z, y, x]."""
+
+    def __init__(self, dims, cell=16, inr: Inr | None = None, cache: Cache | None = None,
+                 levels=1, min_level=0, ranges=None, field=None, device="cuda", stream=None):
+        L = lib()
+        d = cinr_macro_desc()
+        d.dims[:] = [int(v) for v in dims]
+        d.cell = int(cell)
+        d.levels, d.min_level = int(levels), int(min_level)
+        keep = None
+        if ranges is not None:
+            keep = np.ascontiguousarray(ranges, dtype=np.float32)
+            d.source, d.ranges_host = MACRO_FROM_RANGES, keep.ctypes.data
+        elif field is not None:
+            d.source, d.field_dev = MACRO_FROM_FIELD, field.data_ptr()
+        else:
+            d.source = MACRO_FROM_INR
+            d.inr = inr.h.value if inr is not None else None
+            d.cache = cache.h.value if cache is not None else None
+        nbytes = C.c_size_t()
+        check(L.cinr_macro_bytes(d.dims, d.cell, C.byref(nbytes)), "cinr_macro_bytes")
+        self.mem = _dev_buffer(nbytes.value, device)
+        h = C.c_void_p()
+        check(L.cinr_create_macro(C.byref(d), C.c_void_p(self.mem.data_ptr()), nbytes.value,
+                                  _stream(stream), C.byref(h)), "cinr_create_macro")
+        self.h = h
+        self.dims = tuple(int(v) for v in dims)
+        self.cell = int(cell)
+        self.cdims = tuple((v + self.cell - 1) // self.cell for v in self.dims)
+        self.n = int(np.prod(self.cdims))
+        self._refs = (inr, cache, field, keep)
+
+    def ranges(self, stream=None):
+        out = np.zeros((self.n, 2), np.float32)
+        check(lib().cinr_macro_ranges(self.h, C.c_void_p(out.ctypes.data), out.size,
+                                      _stream(stream)), "cinr_macro_ranges")
+        return out
+
+    def apply_tf(self, tf, stream=None):
+        t = tf if isinstance(tf, cinr_tf) else make_tf(tf)
+        check(lib().cinr_macro_apply_tf(self.h, C.byref(t), _stream(stream)), "cinr_macro_apply_tf")
+
+    def skip_flags(self, stream=None):
+        out = np.zeros(self.n, np.uint8)
+        check(lib().cinr_macro_skip_flags(self.h, C.c_void_p(out.ctypes.data), out.size,
+                                          _stream(stream)), "cinr_macro_skip_flags")
+        return out
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().cinr_destroy_macro(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
 def debug_dump(handle, what, stream=None, pool_half=False):
     L = lib()
     n = C.c_size_t()
@@ -423,6 +500,12 @@ class Renderer:
 
     def misses(self, stream=None):
         return debug_dump(self.h, DUMP_MISSES, stream).reshape(-1, 2)
+
+    def set_macro(self, macro: Macro | None):
+        """Attach macro cells (None detaches): transparent cells are skipped."""
+        check(lib().cinr_renderer_set_macro(self.h, macro.h if macro is not None else None),
+              "cinr_renderer_set_macro")
+        self._macro = macro
 
     def __del__(self):
         try:

@@ -421,8 +421,17 @@ int launch_decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys
   static int per_sm = 0;
   if (!per_sm) {
     CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // tensor-core path: the largest shared-memory carveout, so that the
+    // occupancy query (and the launch) see every CTA that fits
+    if (MLPP)
+      CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared));
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem));
     if (per_sm < 1) return set_error(CINR_ERR_CUDA, "decode kernel cannot be resident");
+    if (MLPP) {
+      const int fit = tc::resident_ctas(k, smem);
+      per_sm = fit > per_sm ? fit : per_sm;
+    }
   }
   const int S3 = c.S * c.S * c.S;
   const long work = (long)n_grid * ((S3 + 127) / 128);

@@ -101,6 +101,14 @@ struct CacheDev {
   uint32_t* touched_count;
 };
 
+// Macro-cell skip flags of the current transfer function (Sec. 5.2);
+// skip == nullptr turns skipping off.  Cells are 2^shift LoD-0 voxels wide.
+struct MacroDev {
+  const uint8_t* skip;
+  int shift;
+  int dims[3];
+};
+
 // ------------------------------------------------- binary32 primitives
 __device__ __forceinline__ float f_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float f_add(float a, float b) { return __fadd_rn(a, b); }
@@ -203,6 +211,17 @@ __device__ __forceinline__ bool next_segment_exists(const CamDev& c, float tn, f
                                                     const Sched& s) {
   if (c.step_mode == 0) return f_add(tn, f_mul((float)(k0 + 32), c.dt)) < tf;
   return f_add(s.ts, f_mul(32.0f, s.dts)) < tf;
+}
+
+// Whether the sample at LoD-0 position pv (= x * dims in binary32, >= 0)
+// lies in a transparent macro cell: cell = floor(pv) >> shift per axis,
+// clamped to the last cell at the far faces.
+__device__ __forceinline__ bool macro_skips(const MacroDev& m, float pv0, float pv1, float pv2) {
+  if (!m.skip) return false;
+  const int c0 = min((int)pv0 >> m.shift, m.dims[0] - 1);
+  const int c1 = min((int)pv1 >> m.shift, m.dims[1] - 1);
+  const int c2 = min((int)pv2 >> m.shift, m.dims[2] - 1);
+  return __ldg(m.skip + ((size_t)c2 * m.dims[1] + c1) * m.dims[0] + c0) != 0;
 }
 
 __device__ __forceinline__ uint32_t xorshift32(uint32_t s) {
@@ -407,7 +426,7 @@ inline Shape shape_of(int IN, int H) {
 namespace cinr {
 enum StatIdx {
   ST_SAMPLES = 0, ST_DIRECT, ST_DECODE, ST_MISSES, ST_FALLBACK, ST_HITS, ST_REQ,
-  ST_DECODED, ST_EVICT, ST_RECORDED, ST_SLOTS, ST_COUNT
+  ST_DECODED, ST_EVICT, ST_RECORDED, ST_SLOTS, ST_SKIPPED, ST_COUNT
 };
 
 // Radix-select state (find the n smallest unique 64-bit keys).
@@ -452,6 +471,26 @@ struct cinr_cache_s {
   int slot_bits, key_bits;
   uint32_t last_launches;  // kernels of the last end-of-frame update
 };
+
+struct cinr_macro_s {
+  int vol[3];
+  int cell, shift;
+  int dims[3];
+  size_t n;        // cells
+  float* ranges;   // 2 per cell: min, max (x fastest)
+  uint8_t* skip;   // 1 per cell
+  int device;
+  cinr::MacroDev dev() const {
+    cinr::MacroDev m;
+    m.skip = skip;
+    m.shift = shift;
+    for (int a = 0; a < 3; ++a) m.dims[a] = dims[a];
+    return m;
+  }
+};
+
+// Skip flags of `tf` for macro m, enqueued on `s` (one kernel).
+int cinr_macro_apply(cinr_macro_s* m, const float (*rgba)[4], cudaStream_t s);
 
 // Cache update at the end of a frame (request selection, victims, commit,
 // decode), enqueued on `s`; stats_dev receives decoded/evicted counts.

@@ -37,6 +37,7 @@ struct cinr_renderer_s {
   cudaEvent_t ev[3];             // frame kernel start/end, cache update end
   cudaStream_t cap = nullptr;    // capture stream of the per-frame CUDA graph
   cudaGraphExec_t exec = nullptr;
+  cinr_macro_s* macro = nullptr; // attached macro cells (Sec. 5.2)
 };
 
 namespace {
@@ -61,6 +62,7 @@ struct FrameParams {
   uint32_t* miss_count;
   const uint16_t* w16;  // half-precision MLP weights (tensor-core path)
   int* err;             // set when a bounded device-side wait gives up
+  MacroDev mac;         // transparent macro cells (skip == nullptr: off)
 };
 
 // Bytes of the frame kernel's shared memory before the MLP region (TF,
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
   float d[3] = {0.f, 0.f, 0.f}, tn = 0.f, tf = 0.f, T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
   int k0 = 0;
   Sched sch = {0.f, 0.f};
-  uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0;
+  uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0, n_skip = 0;
   int parity = 0;
 
   while (true) {
@@ -181,6 +183,11 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
     if (active) {
       sched_segment(cam, tn, k0, sch);
       has = sample_in(cam, d, tn, tf, k0 + lane, sch, x, tm, len);
+      if (has && macro_skips(P.mac, f_mul(x[0], (float)cam.vol[0]), f_mul(x[1], (float)cam.vol[1]),
+                             f_mul(x[2], (float)cam.vol[2]))) {
+        has = false;  // transparent cell (Sec. 5.2): alpha = 0, nothing to look up
+        ++n_skip;
+      }
       if (has) {
         ++n_samp;
         if (!CACHED) miss = true;
@@ -351,9 +358,9 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
   if (MLPP) tc::tc_teardown(tcs);
 
   // ---- per-CTA statistics
-  unsigned long long a[6] = {n_samp, n_hit, n_fb, n_miss, n_req, n_slot};
+  unsigned long long a[7] = {n_samp, n_hit, n_fb, n_miss, n_req, n_slot, n_skip};
 #pragma unroll
-  for (int j = 0; j < 6; ++j)
+  for (int j = 0; j < 7; ++j)
     for (int o = 16; o > 0; o >>= 1) a[j] += __shfl_xor_sync(kFull, a[j], o);
   if (lane == 0) {
     if (a[0]) atomicAdd(P.stats + ST_SAMPLES, a[0]);
@@ -366,6 +373,7 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
     }
     if (a[4]) atomicAdd(P.stats + ST_REQ, a[4]);
     if (a[5]) atomicAdd(P.stats + ST_SLOTS, a[5]);
+    if (a[6]) atomicAdd(P.stats + ST_SKIPPED, a[6]);
   }
 }
 
@@ -406,7 +414,9 @@ __device__ __forceinline__ float pool_ld(const void* pool, size_t i) {
   return __ldg(reinterpret_cast<const float*>(pool) + i);
 }
 
-template <int IN, int H, bool F16POOL>
+// MACRO: macro-cell skipping compiled in (a separate instantiation keeps the
+// plain loop free of the test).
+template <int IN, int H, bool F16POOL, bool MACRO>
 __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __grid_constant__ FrameParams P) {
   __shared__ float4 s_tf[256];
   __shared__ LevelGeo s_geo[kMaxLod];
@@ -433,7 +443,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
   const float invB = c.invB, fB = (float)c.B;
   const size_t S3 = (size_t)S * S * S;
   const void* pool = c.pool;
-  uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0;
+  uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0, n_skip = 0;
   const uint32_t n_tiles = P.n_rays >> 5;
   while (true) {
     uint32_t tile = 0;
@@ -464,12 +474,20 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           active = false;
         }
       }
-      bool want_req = false, hit = false, miss = false;
+      bool want_req = false, hit = false, miss = false, take = false;
       uint32_t req_key = 0, hit_slot = 0;
+      float pv0 = 0.f, pv1 = 0.f, pv2 = 0.f;
       if (has) {
+        pv0 = f_mul(x[0], volf[0]);
+        pv1 = f_mul(x[1], volf[1]);
+        pv2 = f_mul(x[2], volf[2]);
+        // transparent macro cell (Sec. 5.2): alpha = 0, nothing to look up
+        take = !MACRO || !macro_skips(P.mac, pv0, pv1, pv2);
+        if (!take) ++n_skip;
+      }
+      if (take) {
         ++n_samp;
         const int l = sample_lod(cam, L, 0, rseed, (uint32_t)k, tm);
-        const float pv0 = f_mul(x[0], volf[0]), pv1 = f_mul(x[1], volf[1]), pv2 = f_mul(x[2], volf[2]);
         for (int lev = l; lev < L; ++lev) {
           const LevelGeo g = s_geo[lev];
           const float s0 = f_mul(pv0, g.scale), s1 = f_mul(pv1, g.scale), s2 = f_mul(pv2, g.scale);
@@ -554,13 +572,15 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
         }
       }
       if (has) {
-        const float4 e4 = tf_lookup(s_tf, v);
-        const float alpha = 1.0f - __expf(-e4.w * len);
-        const float wgt = T * alpha;
-        Cr = fmaf(wgt, e4.x, Cr);
-        Cg = fmaf(wgt, e4.y, Cg);
-        Cb = fmaf(wgt, e4.z, Cb);
-        T *= 1.0f - alpha;
+        if (take) {
+          const float4 e4 = tf_lookup(s_tf, v);
+          const float alpha = 1.0f - __expf(-e4.w * len);
+          const float wgt = T * alpha;
+          Cr = fmaf(wgt, e4.x, Cr);
+          Cg = fmaf(wgt, e4.y, Cg);
+          Cb = fmaf(wgt, e4.z, Cb);
+          T *= 1.0f - alpha;
+        }
         ++k;
         if (--seg == 0) {
           seg = P.K;
@@ -572,9 +592,9 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
       }
     }
   }
-  unsigned long long a[6] = {n_samp, n_hit, n_fb, n_miss, n_req, n_slot};
+  unsigned long long a[7] = {n_samp, n_hit, n_fb, n_miss, n_req, n_slot, n_skip};
 #pragma unroll
-  for (int j = 0; j < 6; ++j)
+  for (int j = 0; j < 7; ++j)
     for (int o = 16; o > 0; o >>= 1) a[j] += __shfl_xor_sync(kFull, a[j], o);
   if (lane == 0) {
     if (a[0]) atomicAdd(P.stats + ST_SAMPLES, a[0]);
@@ -586,12 +606,13 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
     }
     if (a[4]) atomicAdd(P.stats + ST_REQ, a[4]);
     if (a[5]) atomicAdd(P.stats + ST_SLOTS, a[5]);
+    if (a[6]) atomicAdd(P.stats + ST_SKIPPED, a[6]);
   }
 }
 
-template <int IN, int H, bool F16POOL>
+template <int IN, int H, bool F16POOL, bool MACRO>
 int launch_march_cached(const FrameParams& P, cudaStream_t s) {
-  auto k = march_cached_kernel<IN, H, F16POOL>;
+  auto k = march_cached_kernel<IN, H, F16POOL, MACRO>;
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
@@ -602,19 +623,21 @@ int launch_march_cached(const FrameParams& P, cudaStream_t s) {
   return CINR_OK;
 }
 
-template <bool F16POOL>
+template <bool F16POOL, bool MACRO>
 int launch_march_cached_pool(const FrameParams& P, cudaStream_t s) {
   switch (shape_of(P.inr.IN, P.inr.H)) {
-    case Shape::S16x32: return launch_march_cached<16, 32, F16POOL>(P, s);
-    case Shape::S32x64: return launch_march_cached<32, 64, F16POOL>(P, s);
-    case Shape::S48x64: return launch_march_cached<48, 64, F16POOL>(P, s);
+    case Shape::S16x32: return launch_march_cached<16, 32, F16POOL, MACRO>(P, s);
+    case Shape::S32x64: return launch_march_cached<32, 64, F16POOL, MACRO>(P, s);
+    case Shape::S48x64: return launch_march_cached<48, 64, F16POOL, MACRO>(P, s);
     default: return set_error(CINR_ERR_ARG, "unsupported shape");
   }
 }
 
 int launch_march_cached_shape(const FrameParams& P, cudaStream_t s) {
-  return P.cache.pool_prec == CINR_PREC_FP16 ? launch_march_cached_pool<true>(P, s)
-                                             : launch_march_cached_pool<false>(P, s);
+  const bool f16 = P.cache.pool_prec == CINR_PREC_FP16;
+  if (P.mac.skip)
+    return f16 ? launch_march_cached_pool<true, true>(P, s) : launch_march_cached_pool<false, true>(P, s);
+  return f16 ? launch_march_cached_pool<true, false>(P, s) : launch_march_cached_pool<false, false>(P, s);
 }
 
 // ----------------------------------------------------------- host side
@@ -693,8 +716,18 @@ int launch_frame(const FrameParams& P, cudaStream_t s) {
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // tensor-core path: the largest shared-memory carveout, so that the
+    // occupancy query (and the launch) see every CTA that fits; the other
+    // paths keep the default split (L1 serves the bricks and hash tables)
+    if (MLPP)
+      CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared));
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, smem));
     if (blocks_per_sm < 1) return set_error(CINR_ERR_CUDA, "frame kernel cannot be resident");
+    if (MLPP) {
+      const int fit = tc::resident_ctas(k, smem);
+      blocks_per_sm = fit > blocks_per_sm ? fit : blocks_per_sm;
+    }
   }
   k<<<(unsigned)(blocks_per_sm * num_sms()), kFrameThreads, smem, s>>>(P);
   CINR_CK(cudaGetLastError());
@@ -833,13 +866,28 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
 
   P.w16 = inr->w16;
   P.err = reinterpret_cast<int*>(r->counters + 2);
+  cinr_macro_s* mac = r->macro;
+  if (mac) {
+    for (int a = 0; a < 3; ++a)
+      if (mac->vol[a] != r->o.dims[a]) return set_error(CINR_ERR_ARG, "macro-cell dims differ from renderer dims");
+    P.mac = mac->dev();
+  }
   // The frame's device work, enqueued on q: the caller's stream, or the
   // renderer's capture stream when the frame runs as a CUDA graph.
+  // Inside a stream capture a plain event record only orders streams, so the
+  // split between frame kernel and cache update is taken by an external event
+  // node, and the frame's start and end events sit on the caller's stream
+  // around the graph launch.
+  const bool graph = r->o.use_graph != 0;
   auto enqueue = [&](cudaStream_t q) -> int {
     CINR_CK(cudaMemsetAsync(r->counters, 0, 64 * 4, q));
     CINR_CK(cudaMemsetAsync(r->stats, 0, ST_COUNT * 8, q));
     if (cache) CINR_CK(cudaMemsetAsync(cache->dev.touched_count, 0, 4, q));
-    CINR_CK(cudaEventRecord(r->ev[0], q));
+    if (mac) {
+      const int em = cinr_macro_apply(mac, tf->rgba, q);
+      if (em) return em;
+    }
+    if (!graph) CINR_CK(cudaEventRecord(r->ev[0], q));
     int ee;
     if (!cache)
       ee = launch_frame_shape<false>(P, inr->p.mlp_precision, q);
@@ -848,15 +896,22 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
     else
       ee = launch_march_cached_shape(P, q);
     if (ee) return ee;
-    CINR_CK(cudaEventRecord(r->ev[1], q));
+    CINR_CK(cudaEventRecordWithFlags(r->ev[1], q, graph ? cudaEventRecordExternal : cudaEventRecordDefault));
     if (cache) {
       ee = cinr_cache_end_frame(cache, r->stats, q);
       if (ee) return ee;
     }
-    CINR_CK(cudaEventRecord(r->ev[2], q));
+    if (!graph) CINR_CK(cudaEventRecord(r->ev[2], q));
     return CINR_OK;
   };
-  int e = r->o.use_graph ? launch_as_graph(r, enqueue, s) : enqueue(s);
+  int e;
+  if (graph) {
+    CINR_CK(cudaEventRecord(r->ev[0], s));
+    e = launch_as_graph(r, enqueue, s);
+    if (!e) CINR_CK(cudaEventRecord(r->ev[2], s));
+  } else {
+    e = enqueue(s);
+  }
   if (e) return e;
   unsigned long long h[ST_COUNT];
   uint32_t cnt[3] = {0, 0, 0};  // ray counter, miss-record count, device error word
@@ -877,7 +932,8 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
     stats->evictions = h[ST_EVICT];
     stats->misses_recorded = P.miss_rec ? (rec < P.miss_cap ? rec : P.miss_cap) : 0;
     stats->slots_touched = h[ST_SLOTS];
-    stats->kernel_launches = 1u + (cache ? cache->last_launches : 0u);
+    stats->kernel_launches = 1u + (cache ? cache->last_launches : 0u) + (mac ? 1u : 0u);
+    stats->samples_skipped = h[ST_SKIPPED];
     float ms0 = 0.f, ms1 = 0.f;
     CINR_CK(cudaEventElapsedTime(&ms0, r->ev[0], r->ev[1]));
     CINR_CK(cudaEventElapsedTime(&ms1, r->ev[1], r->ev[2]));
@@ -1135,6 +1191,7 @@ struct FieldParams {
   unsigned long long* stats;
   int K;
   float eps;
+  MacroDev mac;
 };
 
 __global__ void __launch_bounds__(kFrameThreads, 8) march_field_kernel(const __grid_constant__ FieldParams P) {
@@ -1143,7 +1200,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_field_kernel(const __g
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const CamDev& cam = P.cam;
-  uint32_t n_samp = 0;
+  uint32_t n_samp = 0, n_skip = 0;
   const uint32_t n_tiles = P.n_rays >> 5;
   while (true) {
     uint32_t tile = 0;
@@ -1165,15 +1222,20 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_field_kernel(const __g
         float x[3], tm, len;
         if ((k & 31) == 0) sched_segment(cam, tn, k, sch);
         if (!sample_in(cam, d, tn, tf, k, sch, x, tm, len)) break;
-        ++n_samp;
-        const float v = field_trilinear(P.field, P.fdims, x[0], x[1], x[2]);
-        const float4 e4 = tf_lookup(s_tf, v);
-        const float alpha = 1.0f - __expf(-e4.w * len);
-        const float wgt = T * alpha;
-        Cr = fmaf(wgt, e4.x, Cr);
-        Cg = fmaf(wgt, e4.y, Cg);
-        Cb = fmaf(wgt, e4.z, Cb);
-        T *= 1.0f - alpha;
+        if (macro_skips(P.mac, f_mul(x[0], (float)cam.vol[0]), f_mul(x[1], (float)cam.vol[1]),
+                        f_mul(x[2], (float)cam.vol[2]))) {
+          ++n_skip;  // transparent cell (Sec. 5.2)
+        } else {
+          ++n_samp;
+          const float v = field_trilinear(P.field, P.fdims, x[0], x[1], x[2]);
+          const float4 e4 = tf_lookup(s_tf, v);
+          const float alpha = 1.0f - __expf(-e4.w * len);
+          const float wgt = T * alpha;
+          Cr = fmaf(wgt, e4.x, Cr);
+          Cg = fmaf(wgt, e4.y, Cg);
+          Cb = fmaf(wgt, e4.z, Cb);
+          T *= 1.0f - alpha;
+        }
         if (--seg == 0) {
           seg = P.K;
           if (T < P.eps) break;
@@ -1182,9 +1244,13 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_field_kernel(const __g
     }
     P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
   }
-  unsigned long long a = n_samp;
-  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+  unsigned long long a = n_samp, b = n_skip;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(kFull, a, o);
+    b += __shfl_xor_sync(kFull, b, o);
+  }
   if (lane == 0 && a) atomicAdd(P.stats + ST_SAMPLES, a);
+  if (lane == 0 && b) atomicAdd(P.stats + ST_SKIPPED, b);
 }
 
 }  // namespace
@@ -1212,8 +1278,18 @@ extern "C" int cinr_render_field(cinr_renderer_t r, const float* field_dev, cons
   P.stats = r->stats;
   P.K = r->o.K;
   P.eps = r->o.eps_T;
+  if (r->macro) {
+    for (int a = 0; a < 3; ++a)
+      if (r->macro->vol[a] != r->o.dims[a] || fdims[a] != r->o.dims[a])
+        return set_error(CINR_ERR_ARG, "with macro cells the field and macro dims must equal the renderer dims");
+    P.mac = r->macro->dev();
+  }
   CINR_CK(cudaMemsetAsync(r->counters, 0, 64 * 4, s));
   CINR_CK(cudaMemsetAsync(r->stats, 0, ST_COUNT * 8, s));
+  if (r->macro) {
+    const int em = cinr_macro_apply(r->macro, tf->rgba, s);
+    if (em) return em;
+  }
   static int per_sm = 0;
   if (!per_sm) {
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_field_kernel, kFrameThreads, 0));
@@ -1227,6 +1303,16 @@ extern "C" int cinr_render_field(cinr_renderer_t r, const float* field_dev, cons
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->samples = h[ST_SAMPLES];
+    stats->samples_skipped = h[ST_SKIPPED];
   }
+  return CINR_OK;
+}
+
+extern "C" int cinr_renderer_set_macro(cinr_renderer_t r, cinr_macro_t m) {
+  if (!r) return set_error(CINR_ERR_ARG, "renderer is NULL");
+  if (m)
+    for (int a = 0; a < 3; ++a)
+      if (m->vol[a] != r->o.dims[a]) return set_error(CINR_ERR_ARG, "macro-cell dims differ from renderer dims");
+  r->macro = m;
   return CINR_OK;
 }

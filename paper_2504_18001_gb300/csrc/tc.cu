@@ -106,8 +106,14 @@ int launch_infer_tc(const cinr_inr_s* inr, const float* xyz, long n, float* out,
   if (smem < tc::kMinSmemPerCta) smem = tc::kMinSmemPerCta;
   CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
+  // the largest shared-memory carveout: the occupancy query (and the
+  // launch) then see every CTA that fits, not the default split
+  CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared));
   CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem));
   if (per_sm < 1) return set_error(CINR_ERR_CUDA, "tensor-core inference kernel cannot be resident");
+  const int fit = tc::resident_ctas(k, smem);
+  if (fit > per_sm) per_sm = fit;
   // each resident CTA holds 64 of the SM's 512 TMEM columns
   if (per_sm > 8) per_sm = 8;
   long tiles = (n + 127) / 128;

@@ -18,6 +18,7 @@
 // returns.
 #pragma once
 
+#include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -32,6 +33,30 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // Dynamic shared memory per CTA (bytes) that keeps at most 8 CTAs (8 x 64
 // TMEM columns = 512) resident on an SM of 228 KB shared memory.
 constexpr int kMinSmemPerCta = 29 * 1024;
+
+// Resident CTAs per SM of a tensor-core kernel of 128 threads with `smem`
+// bytes of dynamic shared memory: the SM's shared memory and registers
+// decide, at most 8 (8 x 64 TMEM columns).  The runtime's occupancy query
+// answers 1 for kernels that allocate tensor memory; a grid of one CTA per
+// SM leaves 3/4 of the warp slots empty while the encoder waits on its
+// gathers.  A grid sized from this count is safe either way: CTAs beyond
+// those resident wait for a free slot, and no CTA waits on another.
+template <class K>
+inline int resident_ctas(K kernel, int smem) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 1;
+  int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  int n = 8;
+  const int cta_smem = smem + (int)fa.sharedSizeBytes + reserved;
+  if (cta_smem > 0 && smem_sm / cta_smem < n) n = smem_sm / cta_smem;
+  const int cta_regs = ((fa.numRegs + 7) / 8) * 8 * 128;  // 256-register warp granules
+  if (cta_regs > 0 && regs_sm / cta_regs < n) n = regs_sm / cta_regs;
+  return n < 1 ? 1 : n;
+}
 
 // Operand formats: 0 = FP16, 1 = BF16, 2 = FP8 E4M3.
 template <int FMT>

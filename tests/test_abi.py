@@ -68,3 +68,34 @@ def test_cache_option_checks(L):
     assert L.cinr_cache_bytes(dims, 1 << 20, C.byref(o), C.byref(nb), C.byref(ns)) == -1
     o = cinr.cinr_cache_opts(8, 3, 10000, 1, 1, 0)  # n_req above the limit (8192)
     assert L.cinr_cache_bytes(dims, 1 << 20, C.byref(o), C.byref(nb), C.byref(ns)) == -1
+
+
+def test_macro_cell_size_query_and_checks(L):
+    # Sec. 6.3: 16^3 cells over a 4096^3 volume = 256^3 = 16.8 M cells; the
+    # structure holds 8 B of range + 1 B of flag per cell
+    dims = (C.c_int * 3)(4096, 4096, 4096)
+    n = C.c_size_t()
+    assert L.cinr_macro_bytes(dims, 16, C.byref(n)) == 0
+    assert 256 ** 3 == 16_777_216
+    assert 9 * 256 ** 3 <= n.value < 9 * 256 ** 3 + 1024
+    # ragged: ceil(V / cell) per axis
+    dims2 = (C.c_int * 3)(100, 17, 33)
+    assert L.cinr_macro_bytes(dims2, 16, C.byref(n)) == 0
+    assert n.value >= 9 * 7 * 2 * 3
+    for bad in (1, 12, 2048):
+        assert L.cinr_macro_bytes(dims2, bad, C.byref(n)) == -1
+        assert "power of two" in cinr.last_error()
+    d = cinr.cinr_macro_desc()
+    d.dims[:] = [64, 64, 64]
+    d.cell, d.source = 16, 7
+    h = C.c_void_p()
+    assert L.cinr_create_macro(C.byref(d), None, 0, None, C.byref(h)) == -1
+    d.source = cinr.MACRO_FROM_INR  # no INR given
+    assert L.cinr_create_macro(C.byref(d), None, 0, None, C.byref(h)) == -1
+    assert "needs an INR" in cinr.last_error()
+
+
+def test_frame_stats_layout_matches_header(L):
+    # 13 counters of 8 bytes, then two float timings
+    assert C.sizeof(cinr.cinr_frame_stats) == 13 * 8 + 8
+    assert cinr.cinr_frame_stats.samples_skipped.offset == 12 * 8

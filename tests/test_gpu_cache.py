@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_req=40, ranking=1,
          preload=1, lod_scale=1.0, lod_mode=0, storage="fp32", K=32, eps=0.0, check_pixels=2e-3,
          cam_fn=None, mlp="fp32", tab="fp32", ray_layout=0, step_mode=0, step_lod_max=0,
-         use_graph=0):
+         use_graph=0, tf=None, macro_cell=0):
     from paper_2504_18001_gb300 import cinr
     cfg = S.INR_64
     table, w = scene(cfg)
@@ -33,15 +33,26 @@ def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_r
     r = cinr.Renderer(W, H, vol, K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
                       ray_layout=ray_layout, step_mode=step_mode, step_lod_max=step_lod_max,
                       use_graph=use_graph, miss_record_cap=W * H * 4000)
-    tf = S.tf_ramps(2)
+    tf = S.tf_ramps(2) if tf is None else tf
+    omac = None
+    if macro_cell:
+        # the oracle's ranges feed both sides, so the skip flags agree bit for bit
+        ranges = O.macro_ranges_inr(p, table, w, vol, macro_cell, levels)
+        mac = cinr.Macro(vol, macro_cell, ranges=ranges)
+        r.set_macro(mac)
+        omac = O.macro(vol, macro_cell, O.macro_skip(ranges, tf.astype(np.float64)))
+        assert np.array_equal(mac.skip_flags(), np.zeros(mac.n, np.uint8))
     worst = 0.0
     history = []
     for f in range(frames):
         cam = cam_fn(f, W, H) if cam_fn else S.orbit_camera(4 * f, W, H, distance=1.6 + 0.05 * f)
         img, st = r.render(inr, cam, tf, cache=cache)
-        ref, rst = oc.render(ocam(cam), tf.astype(np.float64))
+        ref, rst = oc.render(ocam(cam), tf.astype(np.float64), macro=omac)
+        if macro_cell:
+            assert np.array_equal(mac.skip_flags(), omac._keep)
         for k in ("samples", "hits", "fallback_hits", "true_misses", "bricks_requested",
-                  "bricks_decoded", "evictions", "inr_queries_direct", "inr_queries_decode"):
+                  "bricks_decoded", "evictions", "inr_queries_direct", "inr_queries_decode",
+                  "samples_skipped"):
             assert st[k] == rst[k], (f, k, st[k], rst[k])
         for g, o in ((cinr.DUMP_PAGE_TABLE, O.DUMP_PT), (cinr.DUMP_STAMPS, O.DUMP_STAMP),
                      (cinr.DUMP_OWNERS, O.DUMP_OWNER), (cinr.DUMP_RANK, O.DUMP_RANK),
