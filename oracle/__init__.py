@@ -64,6 +64,11 @@ class MarchOpts(C.Structure):
                 ("step_lod_max", C.c_int), ("macro", C.c_void_p)]
 
 
+class PtOpts(C.Structure):
+    _fields_ = [("light_dir", C.c_float * 3), ("light", C.c_float * 3), ("ambient", C.c_float * 3),
+                ("max_bounces", C.c_int), ("sigma_max", C.c_float)]
+
+
 class Macro(C.Structure):
     _fields_ = [("cell", C.c_int), ("dims", C.c_int * 3), ("skip", C.POINTER(C.c_uint8))]
 
@@ -80,7 +85,7 @@ class Stats(C.Structure):
 
 class CacheOpts(C.Structure):
     _fields_ = [("brick", C.c_int), ("levels", C.c_int), ("n_slots", C.c_long),
-                ("n_req", C.c_int), ("ranking", C.c_int), ("preload", C.c_int)]
+                ("n_req", C.c_int), ("ranking", C.c_int), ("preload", C.c_int), ("lag", C.c_int)]
 
 
 _P = C.POINTER
@@ -138,6 +143,14 @@ _SIGS = {
     "orc_macro_skip": (None, [_fp, C.c_long, _dp, _P(C.c_uint8)]),
     "orc_macro_cell_of": (C.c_long, [_P(Macro), _ip, _fp]),
     "orc_cache_set_macro": (None, [C.c_void_p, C.c_void_p]),
+    "orc_neg_log1m": (C.c_float, [C.c_float]),
+    "orc_pt_uniform": (C.c_float, [C.c_uint64, C.c_uint32]),
+    "orc_pt_sphere": (None, [C.c_uint64, _up, _fp]),
+    "orc_render_pt_direct": (None, [_P(InrParams), _dp, _dp, _P(Camera), _ip, _P(MarchOpts), _dp,
+                                    _P(PtOpts), C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int,
+                                    _dp, _P(Stats)]),
+    "orc_render_pt_cached": (None, [C.c_void_p, _P(Camera), _dp, _P(PtOpts), C.c_int, C.c_int,
+                                    C.c_int, C.c_int, _dp, _P(Stats)]),
     "orc_field_trilinear": (C.c_double, [_fp, _ip, _fp]),
     "orc_loss_grad": (C.c_double, [_P(InrParams), _dp, _dp, _fp, _dp, C.c_long, _dp, _dp]),
     "orc_adam": (None, [_dp, _dp, _dp, _dp, C.c_long, C.c_double, C.c_double, C.c_double,
@@ -201,6 +214,44 @@ def march_opts(K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0, step_mode=0,
         mo.macro = C.cast(C.pointer(macro), C.c_void_p)
         mo._keep = macro
     return mo
+
+
+# ----------------------------------------------------------- path tracing
+def pt_opts(light_dir=(0.3, -1.0, -0.4), light=(3.0, 3.0, 3.0), ambient=(0.0, 0.0, 0.0),
+            max_bounces=3, sigma_max=0.0) -> PtOpts:
+    return PtOpts((C.c_float * 3)(*light_dir), (C.c_float * 3)(*light), (C.c_float * 3)(*ambient),
+                  int(max_bounces), float(sigma_max))
+
+
+def neg_log1m(u: float) -> float:
+    return float(lib().orc_neg_log1m(float(u)))
+
+
+def pt_uniform(key: int, j: int) -> float:
+    return float(lib().orc_pt_uniform(C.c_uint64(key & (2**64 - 1)), j))
+
+
+def pt_sphere(key: int, j: int):
+    jj = C.c_uint32(j)
+    d = np.zeros(3, np.float32)
+    lib().orc_pt_sphere(C.c_uint64(key & (2**64 - 1)), C.byref(jj), d.ctypes.data_as(_fp))
+    return d, int(jj.value)
+
+
+def render_pt_direct(p: InrParams, table, w, cam: Camera, vol, mo: MarchOpts, tf, pt: PtOpts,
+                     frame, window=None):
+    """One path per pixel, every density lookup by direct INR inference."""
+    px0, py0, pw, ph = window if window is not None else (0, 0, cam.width, cam.height)
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    v, vp = _i3(vol)
+    tfa, tfp = _d(tf)
+    out = np.zeros((ph, pw, 4), np.float64)
+    st = Stats()
+    lib().orc_render_pt_direct(C.byref(p), tp, wp, C.byref(cam), vp, C.byref(mo), tfp,
+                               C.byref(pt), int(frame), px0, py0, pw, ph,
+                               out.ctypes.data_as(_dp), C.byref(st))
+    return out, st.as_dict()
 
 
 # ------------------------------------------------------------- macro cells
@@ -414,14 +465,14 @@ class Cache:
     """Oracle brick cache (owns its own host memory)."""
 
     def __init__(self, p: InrParams, table, w, vol, brick, levels, n_slots, mo: MarchOpts,
-                 n_req=40, ranking=1, preload=1):
+                 n_req=40, ranking=1, preload=1, lag=1):
         self._t, tp = _d(table)
         self._w, wp = _d(w)
         self._v, vp = _i3(vol)
         self.p = p
         self.mo = mo
         self.co = CacheOpts(int(brick), int(levels), int(n_slots), int(n_req), int(ranking),
-                            int(preload))
+                            int(preload), int(lag))
         h = lib().orc_cache_create(C.byref(p), tp, wp, vp, C.byref(self.co), C.byref(mo))
         if not h:
             raise ValueError("orc_cache_create failed (levels or pool too small for preload)")
@@ -463,6 +514,16 @@ class Cache:
                                     out.ctypes.data_as(_dp), C.byref(st))
         finally:
             lib().orc_cache_set_macro(self.h, None)
+        return out, st.as_dict()
+
+    def render_pt(self, cam: Camera, tf, pt: PtOpts, window=None):
+        """One path-traced frame through the cache."""
+        px0, py0, pw, ph = window if window is not None else (0, 0, cam.width, cam.height)
+        tfa, tfp = _d(tf)
+        out = np.zeros((ph, pw, 4), np.float64)
+        st = Stats()
+        lib().orc_render_pt_cached(self.h, C.byref(cam), tfp, C.byref(pt), px0, py0, pw, ph,
+                                   out.ctypes.data_as(_dp), C.byref(st))
         return out, st.as_dict()
 
     def dump(self, what):

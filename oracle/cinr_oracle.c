@@ -757,6 +757,7 @@ struct orc_cache {
   long n_last_req;
   uint32_t* last_vict;
   long n_last_vict;
+  long n_pending; /* lag 2: last_req/last_vict pairs decoded, not yet mapped */
   uint32_t* miss;
   long n_miss, cap_miss;
 };
@@ -992,6 +993,7 @@ orc_cache* orc_cache_create(const orc_inr_params* p, const double* table,
                             const orc_cache_opts* co,
                             const orc_march_opts* mo) {
   if (co->levels < 1 || co->levels > 16) return NULL;
+  if (co->lag != 1 && co->lag != 2) return NULL;
   orc_cache* c = (orc_cache*)calloc(1, sizeof(orc_cache));
   c->p = *p;
   c->table = table;
@@ -1077,113 +1079,82 @@ static int cmp_u64_key(const void* x, const void* y) {
   return 0;
 }
 
-/* Cached rendering of frame f (Fig. 1; Alg. 1 and 2; Sec. 4.3).
- * Per sample: stochastic LoD l; page-table lookup at l; if the brick is
- * Unmapped a request is raised for it (priority rank, Sec. 4.3.3) and the
- * lookup falls back to l+1, l+2, ... (Sec. 4.3); the first Mapped brick is
- * sampled trilinearly and its slot stamped with f (LRU); no Mapped brick at
- * any level = true miss, recorded and inferred directly by the INR (Alg. 1).
- * End of frame: top-n requests, victims, decode + write-back, map (lag-1:
- * the new bricks serve frame f+1). */
-void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
-                       int px0, int py0, int pw, int ph, double* rgba,
-                       orc_stats* st) {
-  memset(st, 0, sizeof(*st));
-  c->frame += 1;
-  uint64_t f = c->frame;
-  /* READING of the ranking rule (Sec. 4.3.3): the frame timestamp advances
-   * by 1001 per frame; a request sets r = max(r, T_f) + 1, clamped at
-   * T_f + 1000, so the score of a brick this frame is min(#requests, 1000)
-   * and stale ranks never outrank fresh requests. */
-  uint32_t Tf = (uint32_t)(1001u * (uint32_t)f);
-  uint32_t fseed = orc_frame_seed(c->mo.seed, f);
+/* One cached sample (Alg. 2, Sec. 4.3): stochastic LoD from the distance
+ * `dist` to the eye; page-table lookup at that LoD; an Unmapped brick raises
+ * a ranked request (Sec. 4.3.3) and the lookup falls back to coarser LoDs;
+ * the first Mapped brick is sampled trilinearly and its slot stamped with
+ * the frame (LRU); no Mapped brick at any LoD = true miss, recorded as
+ * (pixel, k) and inferred directly by the INR (Alg. 1). */
+static double cache_lookup(orc_cache* c, const orc_camera* cam, const float x[3],
+                           float dist, uint32_t state, uint32_t Tf, uint64_t f,
+                           uint32_t pixel, uint32_t k, double* feat, double* act,
+                           orc_stats* st) {
   int L = c->co.levels, B = c->co.brick, S = c->S;
   long S3 = (long)S * S * S;
-  c->n_miss = 0;
-  double* feat = (double*)malloc(sizeof(double) * c->p.in_dim);
-  double* act = (double*)malloc(sizeof(double) * 2 * c->p.hidden);
-  for (int yy = 0; yy < ph; ++yy)
-    for (int xx = 0; xx < pw; ++xx) {
-      double* out = rgba + ((long)yy * pw + xx) * 4;
-      out[0] = out[1] = out[2] = out[3] = 0.0;
-      int px = px0 + xx, py = py0 + yy;
-      uint32_t pixel = (uint32_t)(py * cam->width + px);
-      float o[3], d[3], tn, tf_;
-      if (!orc_ray(cam, c->vol, px, py, o, d, &tn, &tf_)) continue;
-      double C[3] = {0, 0, 0}, T = 1.0;
-      uint32_t rs = orc_ray_seed(fseed, pixel);
-      orc_sched sc = {0.0f, 0.0f};
-      for (int k = 0;; ++k) {
-        float x[3], tm, len;
-        if (!orc_sample_sched(cam, c->vol, &c->mo, o, d, tn, tf_, k, &sc, x, &tm,
-                              &len))
-          break;
-        if (macro_skips(&c->mo, c->vol, x)) {
-          /* transparent cell (Sec. 5.2): no LoD, no lookup, no request */
-          st->samples_skipped++;
-        } else {
-          st->samples++;
-          int l = orc_sample_lod(cam, c->vol, &c->mo, L, 0,
-                                 orc_sample_state(rs, (uint32_t)k), tm);
-          double v = 0.0;
-          int found = 0;
-          for (int lev = l; lev < L; ++lev) {
-            float s[3];
-            int b[3];
-            level_coord(x, c->vol, lev, s);
-            brick_of(s, B, c->nb[lev], b);
-            long key = c->off[lev] +
-                       b[0] + (long)c->nb[lev][0] * (b[1] + (long)c->nb[lev][1] * b[2]);
-            uint32_t e = c->pt[key];
-            if (!(e & PT_MAPPED)) {
-              if (lev == l) {
-                uint32_t r = c->rank[key];
-                if (r < Tf) {
-                  r = Tf;
-                  st->bricks_requested++;
-                }
-                r = r + 1u;
-                if (r > Tf + 1000u) r = Tf + 1000u;
-                c->rank[key] = r;
-              }
-              continue;
-            }
-            long slot = (long)(e & ~PT_MAPPED);
-            v = brick_trilinear(c->pool + slot * S3, S, B, b, c->dims[lev], s);
-            c->stamp[slot] = (uint32_t)f;
-            if (lev == l)
-              st->hits++;
-            else
-              st->fallback_hits++;
-            found = 1;
-            break;
-          }
-          if (!found) {
-            st->true_misses++;
-            st->inr_queries_direct++;
-            push_miss(c, pixel, (uint32_t)k);
-            v = inr_one(&c->p, c->table, c->w, x, feat, act);
-          }
-          composite(tf, v, (double)len, C, &T);
+  int l = orc_sample_lod(cam, c->vol, &c->mo, L, 0, state, dist);
+  for (int lev = l; lev < L; ++lev) {
+    float s[3];
+    int b[3];
+    level_coord(x, c->vol, lev, s);
+    brick_of(s, B, c->nb[lev], b);
+    long key = c->off[lev] +
+               b[0] + (long)c->nb[lev][0] * (b[1] + (long)c->nb[lev][1] * b[2]);
+    uint32_t e = c->pt[key];
+    if (!(e & PT_MAPPED)) {
+      if (lev == l) {
+        uint32_t r = c->rank[key];
+        if (r < Tf) {
+          r = Tf;
+          st->bricks_requested++;
         }
-        if ((k + 1) % c->mo.K == 0 && T < (double)c->mo.eps_T) break;
+        r = r + 1u;
+        if (r > Tf + 1000u) r = Tf + 1000u;
+        c->rank[key] = r;
       }
-      out[0] = C[0];
-      out[1] = C[1];
-      out[2] = C[2];
-      out[3] = 1.0 - T;
+      continue;
     }
-  free(feat);
-  free(act);
+    long slot = (long)(e & ~PT_MAPPED);
+    double v = brick_trilinear(c->pool + slot * S3, S, B, b, c->dims[lev], s);
+    c->stamp[slot] = (uint32_t)f;
+    if (lev == l)
+      st->hits++;
+    else
+      st->fallback_hits++;
+    return v;
+  }
+  st->true_misses++;
+  st->inr_queries_direct++;
+  push_miss(c, pixel, k);
+  return inr_one(&c->p, c->table, c->w, x, feat, act);
+}
+
+/* End of frame f: the Cache Manager's request list, the LRU victims and the
+ * Request Handler's decode + write-back (Fig. 1, Sec. 4.3.2-4.3.3). */
+static void cache_end_frame(orc_cache* c, uint32_t Tf, uint64_t f, orc_stats* st) {
+  long S3 = (long)c->S * c->S * c->S;
+  /* ---- lag 2 (asynchronous request handling, Sec. 4.3 / Sarton's RH):
+   * the bricks selected and unmapped at the end of the previous frame were
+   * decoded while this frame rendered; they are mapped now, before this
+   * frame's selection.  READING: a fixed lag of two frames keeps the state
+   * deterministic. ---- */
+  for (long i = 0; i < c->n_pending; ++i) {
+    uint32_t slot = c->last_vict[i], key = c->last_req[i];
+    c->pt[key] = PT_MAPPED | slot;
+    c->owner[slot] = key;
+    c->stamp[slot] = (uint32_t)f;
+  }
+  c->n_pending = 0;
 
   /* ---- Cache Manager: request list (Sec. 4.3.3; Sarton first-n when the
-   * ranking is off) ---- */
+   * ranking is off).  Candidates are bricks requested this frame that are
+   * not mapped now (with lag 2 a brick in flight during the frame was
+   * requested again and has just been mapped). ---- */
   long nb = c->n_bricks;
   sort_pair* cand = (sort_pair*)malloc(sizeof(sort_pair) * (size_t)(nb + 1));
   long nc = 0;
   for (long key = 0; key < nb; ++key) {
     uint32_t r = c->rank[key];
-    if (r > Tf) {
+    if (r > Tf && !(c->pt[key] & PT_MAPPED)) {
       uint64_t score = (uint64_t)(r - Tf);
       uint64_t sk = c->co.ranking ? ((1000u - score) << 32) | (uint64_t)key
                                   : (uint64_t)key;
@@ -1226,12 +1197,332 @@ void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
       st->evictions++;
     }
     decode_into(c, key, (long)slot);
-    c->pt[key] = PT_MAPPED | slot;
-    c->owner[slot] = key;
-    c->stamp[slot] = (uint32_t)f;
+    if (c->co.lag == 1) {
+      c->pt[key] = PT_MAPPED | slot;
+      c->owner[slot] = key;
+      c->stamp[slot] = (uint32_t)f;
+    } else {
+      c->owner[slot] = NO_OWNER; /* in flight: unmapped until the next frame ends */
+    }
   }
+  if (c->co.lag == 2) c->n_pending = m;
   st->bricks_decoded = (uint64_t)m;
   st->inr_queries_decode = (uint64_t)m * (uint64_t)S3;
+}
+
+/* Cached rendering of frame f (Fig. 1; Alg. 1 and 2; Sec. 4.3).
+ * Per sample: stochastic LoD l; page-table lookup at l; if the brick is
+ * Unmapped a request is raised for it (priority rank, Sec. 4.3.3) and the
+ * lookup falls back to l+1, l+2, ... (Sec. 4.3); the first Mapped brick is
+ * sampled trilinearly and its slot stamped with f (LRU); no Mapped brick at
+ * any level = true miss, recorded and inferred directly by the INR (Alg. 1).
+ * End of frame: top-n requests, victims, decode + write-back, map (lag-1:
+ * the new bricks serve frame f+1). */
+void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
+                       int px0, int py0, int pw, int ph, double* rgba,
+                       orc_stats* st) {
+  memset(st, 0, sizeof(*st));
+  c->frame += 1;
+  uint64_t f = c->frame;
+  /* READING of the ranking rule (Sec. 4.3.3): the frame timestamp advances
+   * by 1001 per frame; a request sets r = max(r, T_f) + 1, clamped at
+   * T_f + 1000, so the score of a brick this frame is min(#requests, 1000)
+   * and stale ranks never outrank fresh requests. */
+  uint32_t Tf = (uint32_t)(1001u * (uint32_t)f);
+  uint32_t fseed = orc_frame_seed(c->mo.seed, f);
+  c->n_miss = 0;
+  double* feat = (double*)malloc(sizeof(double) * c->p.in_dim);
+  double* act = (double*)malloc(sizeof(double) * 2 * c->p.hidden);
+  for (int yy = 0; yy < ph; ++yy)
+    for (int xx = 0; xx < pw; ++xx) {
+      double* out = rgba + ((long)yy * pw + xx) * 4;
+      out[0] = out[1] = out[2] = out[3] = 0.0;
+      int px = px0 + xx, py = py0 + yy;
+      uint32_t pixel = (uint32_t)(py * cam->width + px);
+      float o[3], d[3], tn, tf_;
+      if (!orc_ray(cam, c->vol, px, py, o, d, &tn, &tf_)) continue;
+      double C[3] = {0, 0, 0}, T = 1.0;
+      uint32_t rs = orc_ray_seed(fseed, pixel);
+      orc_sched sc = {0.0f, 0.0f};
+      for (int k = 0;; ++k) {
+        float x[3], tm, len;
+        if (!orc_sample_sched(cam, c->vol, &c->mo, o, d, tn, tf_, k, &sc, x, &tm,
+                              &len))
+          break;
+        if (macro_skips(&c->mo, c->vol, x)) {
+          /* transparent cell (Sec. 5.2): no LoD, no lookup, no request */
+          st->samples_skipped++;
+        } else {
+          st->samples++;
+          double v = cache_lookup(c, cam, x, tm, orc_sample_state(rs, (uint32_t)k), Tf, f,
+                                  pixel, (uint32_t)k, feat, act, st);
+          composite(tf, v, (double)len, C, &T);
+        }
+        if ((k + 1) % c->mo.K == 0 && T < (double)c->mo.eps_T) break;
+      }
+      out[0] = C[0];
+      out[1] = C[1];
+      out[2] = C[2];
+      out[3] = 1.0 - T;
+    }
+  free(feat);
+  free(act);
+
+  cache_end_frame(c, Tf, f, st);
+}
+
+/* ===================================================================== */
+/* Path tracing with Woodcock delta tracking (Sec. 5.1)                    */
+/* ===================================================================== */
+/* READING: the paper names the estimator (Woodcock delta tracking on the
+ * same sampler as ray marching) but no light transport details.  This
+ * reading: one path per pixel and frame; free paths -ln(1-u)/sigma_bar with
+ * the TF's largest extinction as majorant sigma_bar; a tentative collision
+ * at value v is real with probability sigma(v)/sigma_bar; at a real
+ * collision the throughput takes the TF colour as albedo, a directional
+ * light is added by next-event estimation (isotropic phase 1/4pi, shadow
+ * transmittance by ratio tracking), and the path scatters into a uniform
+ * direction; paths that leave the volume collect the ambient radiance.
+ * Every quantity that positions a lookup is binary32 in a fixed order
+ * (this log, the sphere sampler and the box exits use +,-,*,/,sqrt only),
+ * so the lookups, requests and stamps are reproducible bit for bit. */
+
+#define PT_MAX_STEPS 4096
+#define ORC_PI 3.14159265358979323846
+
+float orc_neg_log1m(float u) {
+  /* y = 1 - u = m 2^e with m in [sqrt(2)/2, sqrt(2)) (no cancellation for y
+   * near 1); ln y = e ln2 + 2 atanh(z), z = (m-1)/(m+1), |z| < 0.172,
+   * series to z^15 (truncation < 1e-12). */
+  float y = 1.0f - u;
+  uint32_t bits;
+  memcpy(&bits, &y, 4);
+  int e = (int)((bits >> 23) & 0xFFu) - 127;
+  uint32_t mb = (bits & 0x7FFFFFu) | 0x3F800000u;
+  float m;
+  memcpy(&m, &mb, 4);
+  if (m > 1.41421356f) {
+    m = m * 0.5f;
+    e = e + 1;
+  }
+  float z = (m - 1.0f) / (m + 1.0f);
+  float z2 = z * z;
+  float q = 1.0f / 15.0f;
+  q = q * z2 + 1.0f / 13.0f;
+  q = q * z2 + 1.0f / 11.0f;
+  q = q * z2 + 1.0f / 9.0f;
+  q = q * z2 + 1.0f / 7.0f;
+  q = q * z2 + 1.0f / 5.0f;
+  q = q * z2 + 1.0f / 3.0f;
+  q = q * z2 + 1.0f;
+  float lm = (2.0f * z) * q;
+  float ln = (float)e * 0.693147180559945309f + lm;
+  return -ln;
+}
+
+/* The j-th output of a SplitMix64 generator started at state `key`
+ * (Steele et al. 2014: output j = mix(key + (j+1) gamma)), top 24 bits. */
+float orc_pt_uniform(uint64_t key, uint32_t j) {
+  uint64_t x = orc_splitmix64(key + 0x9E3779B97F4A7C15ull * (uint64_t)j);
+  return (float)(x >> 40) * (1.0f / 16777216.0f);
+}
+
+/* Uniform direction on the unit sphere (Marsaglia 1972): (x1, x2) uniform
+ * in the unit disc by rejection, then (2 x1 r, 2 x2 r, 1 - 2 s) with
+ * s = x1^2 + x2^2 and r = sqrt(1 - s). */
+void orc_pt_sphere(uint64_t key, uint32_t* j, float dir[3]) {
+  for (int tries = 0; tries < 64; ++tries) {
+    float x1 = orc_pt_uniform(key, (*j)++) * 2.0f - 1.0f;
+    float x2 = orc_pt_uniform(key, (*j)++) * 2.0f - 1.0f;
+    float s = x1 * x1 + x2 * x2;
+    if (s < 1.0f) {
+      float r = 2.0f * sqrtf(1.0f - s);
+      dir[0] = x1 * r;
+      dir[1] = x2 * r;
+      dir[2] = 1.0f - 2.0f * s;
+      return;
+    }
+  }
+  dir[0] = 0.0f;
+  dir[1] = 0.0f;
+  dir[2] = 1.0f;
+}
+
+/* Distance from a point inside the box [-h, h] to its boundary along d. */
+static float box_exit(const float h[3], const float o[3], const float d[3]) {
+  float t = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    if (d[a] == 0.0f) continue;
+    float inv = 1.0f / d[a];
+    float t0 = (-h[a] - o[a]) * inv;
+    float t1 = (h[a] - o[a]) * inv;
+    t = fminf(t, fmaxf(t0, t1));
+  }
+  return t;
+}
+
+typedef struct {
+  orc_cache* c;                 /* NULL: direct inference */
+  const orc_inr_params* p;
+  const double* table;
+  const double* w;
+  uint32_t Tf;
+  uint64_t f;
+  double* feat;
+  double* act;
+} pt_ctx;
+
+static double pt_lookup(pt_ctx* ctx, const orc_camera* cam, const float x[3],
+                        float dist, uint32_t state, uint32_t pixel, uint32_t k,
+                        orc_stats* st) {
+  st->samples++;
+  if (ctx->c)
+    return cache_lookup(ctx->c, cam, x, dist, state, ctx->Tf, ctx->f, pixel, k,
+                        ctx->feat, ctx->act, st);
+  st->inr_queries_direct++;
+  st->true_misses++;
+  return inr_one(ctx->p, ctx->table, ctx->w, x, ctx->feat, ctx->act);
+}
+
+/* World point o + t d: normalised coordinate (as the ray-marching samples)
+ * and binary32 distance to the eye. */
+static void pt_point(const orc_camera* cam, const float e[3], const float h[3],
+                     const float o[3], const float d[3], float t, float p[3],
+                     float x[3], float* dist) {
+  for (int q = 0; q < 3; ++q) {
+    p[q] = o[q] + t * d[q];
+    float num = p[q] + h[q];
+    x[q] = clamp01(e[q] == 1.0f ? num : num / e[q]);
+  }
+  float dx = p[0] - cam->eye[0], dy = p[1] - cam->eye[1], dz = p[2] - cam->eye[2];
+  float s2 = dx * dx + dy * dy;
+  s2 = s2 + dz * dz;
+  *dist = sqrtf(s2);
+}
+
+static void pt_path(pt_ctx* ctx, const orc_camera* cam, const int vol[3],
+                    const orc_march_opts* mo, const double* tf,
+                    const orc_pt_opts* pt, const float ls[3], float sbar,
+                    uint32_t fseed, int px, int py, double out[4],
+                    orc_stats* st) {
+  uint32_t pixel = (uint32_t)(py * cam->width + px);
+  for (int q = 0; q < 3; ++q) out[q] = (double)pt->ambient[q];
+  out[3] = 0.0;
+  float o[3], d[3], t0, t1;
+  if (!orc_ray(cam, vol, px, py, o, d, &t0, &t1)) return;
+  (void)mo;
+  float e[3], h[3];
+  box_extent(vol, e, h);
+  uint64_t key = ((uint64_t)fseed << 32) | (uint64_t)pixel;
+  uint32_t rs = orc_ray_seed(fseed, pixel);
+  float inv = sbar > 0.0f ? 1.0f / sbar : 0.0f;
+  double beta[3] = {1.0, 1.0, 1.0}, L[3] = {0.0, 0.0, 0.0};
+  uint32_t j = 0, k = 0;
+  for (int b = 0;; ++b) {
+    int hit = 0;
+    float t = t0, p[3] = {0, 0, 0};
+    double v = 0.0;
+    for (int step = 0; sbar > 0.0f && step < PT_MAX_STEPS; ++step) {
+      float u = orc_pt_uniform(key, j++);
+      t = t + orc_neg_log1m(u) * inv;
+      if (!(t < t1)) break;
+      float x[3], dist;
+      pt_point(cam, e, h, o, d, t, p, x, &dist);
+      v = pt_lookup(ctx, cam, x, dist, orc_sample_state(rs, k), pixel, k, st);
+      ++k;
+      double ev[4];
+      orc_tf_lookup(tf, v, ev);
+      float u2 = orc_pt_uniform(key, j++);
+      if ((double)u2 * (double)sbar < ev[3]) {
+        hit = 1;
+        break;
+      }
+    }
+    if (!hit) {
+      for (int q = 0; q < 3; ++q) L[q] += beta[q] * (double)pt->ambient[q];
+      break;
+    }
+    if (b == 0) out[3] = 1.0;
+    double alb[4];
+    orc_tf_lookup(tf, v, alb);
+    for (int q = 0; q < 3; ++q) beta[q] *= alb[q];
+    /* next-event estimation: shadow transmittance by ratio tracking */
+    float ts1 = box_exit(h, p, ls), ts = 0.0f;
+    double Tr = 1.0;
+    for (int step = 0; sbar > 0.0f && step < PT_MAX_STEPS; ++step) {
+      float u = orc_pt_uniform(key, j++);
+      ts = ts + orc_neg_log1m(u) * inv;
+      if (!(ts < ts1)) break;
+      float pq[3], x[3], dist;
+      pt_point(cam, e, h, p, ls, ts, pq, x, &dist);
+      double v2 = pt_lookup(ctx, cam, x, dist, orc_sample_state(rs, k), pixel, k, st);
+      ++k;
+      double ev[4];
+      orc_tf_lookup(tf, v2, ev);
+      Tr *= 1.0 - ev[3] / (double)sbar;
+    }
+    for (int q = 0; q < 3; ++q)
+      L[q] += beta[q] * (double)pt->light[q] * Tr / (4.0 * ORC_PI);
+    if (b + 1 >= pt->max_bounces) break;
+    orc_pt_sphere(key, &j, d);
+    for (int q = 0; q < 3; ++q) o[q] = p[q];
+    t0 = 0.0f;
+    t1 = box_exit(h, o, d);
+  }
+  for (int q = 0; q < 3; ++q) out[q] = L[q];
+}
+
+/* Majorant and direction to the light (binary32, as the GPU's host code). */
+static float pt_setup(const double* tf, const orc_pt_opts* pt, float ls[3]) {
+  float neg[3] = {-pt->light_dir[0], -pt->light_dir[1], -pt->light_dir[2]};
+  normalize3(neg, ls);
+  if (pt->sigma_max > 0.0f) return pt->sigma_max;
+  float m = 0.0f;
+  for (int i = 0; i < 256; ++i) m = fmaxf(m, (float)tf[i * 4 + 3]);
+  return m;
+}
+
+void orc_render_pt_direct(const orc_inr_params* p, const double* table,
+                          const double* w, const orc_camera* cam,
+                          const int vol[3], const orc_march_opts* mo,
+                          const double* tf, const orc_pt_opts* pt,
+                          uint64_t frame, int px0, int py0, int pw, int ph,
+                          double* rgba, orc_stats* st) {
+  memset(st, 0, sizeof(*st));
+  pt_ctx ctx = {NULL, p, table, w, 0u, frame, NULL, NULL};
+  ctx.feat = (double*)malloc(sizeof(double) * p->in_dim);
+  ctx.act = (double*)malloc(sizeof(double) * 2 * p->hidden);
+  float ls[3];
+  float sbar = pt_setup(tf, pt, ls);
+  uint32_t fseed = orc_frame_seed(mo->seed, frame);
+  for (int yy = 0; yy < ph; ++yy)
+    for (int xx = 0; xx < pw; ++xx)
+      pt_path(&ctx, cam, vol, mo, tf, pt, ls, sbar, fseed, px0 + xx, py0 + yy,
+              rgba + ((long)yy * pw + xx) * 4, st);
+  free(ctx.feat);
+  free(ctx.act);
+}
+
+void orc_render_pt_cached(orc_cache* c, const orc_camera* cam, const double* tf,
+                          const orc_pt_opts* pt, int px0, int py0, int pw,
+                          int ph, double* rgba, orc_stats* st) {
+  memset(st, 0, sizeof(*st));
+  c->frame += 1;
+  uint64_t f = c->frame;
+  pt_ctx ctx = {c, &c->p, c->table, c->w, (uint32_t)(1001u * (uint32_t)f), f, NULL, NULL};
+  ctx.feat = (double*)malloc(sizeof(double) * c->p.in_dim);
+  ctx.act = (double*)malloc(sizeof(double) * 2 * c->p.hidden);
+  c->n_miss = 0;
+  float ls[3];
+  float sbar = pt_setup(tf, pt, ls);
+  uint32_t fseed = orc_frame_seed(c->mo.seed, f);
+  for (int yy = 0; yy < ph; ++yy)
+    for (int xx = 0; xx < pw; ++xx)
+      pt_path(&ctx, cam, c->vol, &c->mo, tf, pt, ls, sbar, fseed, px0 + xx,
+              py0 + yy, rgba + ((long)yy * pw + xx) * 4, st);
+  free(ctx.feat);
+  free(ctx.act);
+  cache_end_frame(c, ctx.Tf, f, st);
 }
 
 void orc_cache_set_macro(orc_cache* c, const orc_macro* m) { c->mo.macro = m; }

@@ -56,6 +56,15 @@ typedef struct {
   const struct orc_macro* macro; /* macro-cell skip flags, NULL = off */
 } orc_march_opts;
 
+/* Path-tracing options (Sec. 5.1, Woodcock delta tracking). */
+typedef struct {
+  float light_dir[3]; /* direction the directional light travels */
+  float light[3];     /* its irradiance (rgb) */
+  float ambient[3];   /* radiance of paths leaving the volume (rgb) */
+  int max_bounces;    /* scattering events per path, >= 1 */
+  float sigma_max;    /* majorant of the extinction; <= 0: max of the TF */
+} orc_pt_opts;
+
 /* Macro cells (Sec. 5.2): ceil(V/cell) cubes per axis; skip[c] = 1 when the
  * current transfer function is transparent over cell c's value range. */
 typedef struct orc_macro {
@@ -157,6 +166,7 @@ typedef struct {
   int n_req;         /* maxNumRequests per frame */
   int ranking;       /* 1 = priority ranking (Sec. 4.3.3), 0 = first-n */
   int preload;       /* 1 = decode + pin every coarsest brick at creation */
+  int lag;           /* frames from request to use: 1 (default) or 2 */
 } orc_cache_opts;
 
 orc_cache* orc_cache_create(const orc_inr_params* p, const double* table,
@@ -172,6 +182,11 @@ void orc_cache_set_macro(orc_cache* c, const orc_macro* m);
 void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
                        int px0, int py0, int pw, int ph, double* rgba,
                        orc_stats* st);
+/* Path-traced frame through the cache (requests, stamps, end-of-frame
+ * update as for orc_render_cached). */
+void orc_render_pt_cached(orc_cache* c, const orc_camera* cam, const double* tf,
+                          const orc_pt_opts* pt, int px0, int py0, int pw,
+                          int ph, double* rgba, orc_stats* st);
 /* what: 0 page table (u32 per brick), 1 slot stamps (u32 per slot),
  *       2 slot owners (u32 per slot), 3 rank (u32 per brick),
  *       4 last requests (u32 keys), 5 last victims (u32 slots),
@@ -197,6 +212,22 @@ double orc_brick_sample(const orc_inr_params* p, const double* table,
 double orc_resident_sample(const orc_inr_params* p, const double* table,
                            const double* w, const int vol[3], int level,
                            const float x[3]);
+
+/* ---- path tracing with Woodcock delta tracking (Sec. 5.1) ---- */
+
+/* -ln(1 - u) in binary32 (fixed operation order, +,-,*,/ only). */
+float orc_neg_log1m(float u);
+/* j-th uniform of the SplitMix64 stream seeded with key: top 24 bits. */
+float orc_pt_uniform(uint64_t key, uint32_t j);
+/* Uniform direction on the sphere (Marsaglia 1972) from the stream. */
+void orc_pt_sphere(uint64_t key, uint32_t* j, float dir[3]);
+/* One path per pixel of frame `frame`; lookups by direct INR inference. */
+void orc_render_pt_direct(const orc_inr_params* p, const double* table,
+                          const double* w, const orc_camera* cam,
+                          const int vol[3], const orc_march_opts* mo,
+                          const double* tf, const orc_pt_opts* pt,
+                          uint64_t frame, int px0, int py0, int pw, int ph,
+                          double* rgba, orc_stats* st);
 
 double orc_psnr(const double* a, const double* b, long n_pixels);
 

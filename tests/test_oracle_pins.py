@@ -317,12 +317,12 @@ def test_brick_sample_equals_whole_grid_trilinear(level, vol):
         assert a == pytest.approx(b, rel=1e-12, abs=1e-13)
 
 
-def _cache_scene(preload=1, n_slots=200, n_req=6, ranking=1, lod_scale=1.0, lod_mode=0):
+def _cache_scene(preload=1, n_slots=200, n_req=6, ranking=1, lod_scale=1.0, lod_mode=0, lag=1):
     p, table, w = _small_inr(seed=2)
     vol = (32, 32, 32)
     mo = O.march_opts(K=8, eps_T=0.0, lod_mode=lod_mode, lod_scale=lod_scale, seed=9)
     c = O.Cache(p, table, w, vol, brick=8, levels=3, n_slots=n_slots, mo=mo, n_req=n_req,
-                ranking=ranking, preload=preload)
+                ranking=ranking, preload=preload, lag=lag)
     cam = O.camera((0.6, 0.5, 1.6), (0, 0, 0), (0, 1, 0), 45.0, 24, 24, 0.5)
     tf = S.tf_ramps(2).astype(np.float64)
     return c, cam, tf, p, table, w, vol
@@ -686,3 +686,144 @@ def test_macro_skip_leaves_first_cached_frame_unchanged():
     assert st1["samples"] + st1["samples_skipped"] == st0["samples"]
     assert st1["true_misses"] == st0["true_misses"] == 0
     assert st1["bricks_requested"] <= st0["bricks_requested"]
+
+
+def test_cache_lag2_maps_a_frame_later_and_never_reselects_in_flight_bricks():
+    # Lag 2: the bricks selected at the end of frame f stay unmapped through
+    # frame f+1 (its samples fall back and request them again) and are mapped
+    # at the end of f+1, before f+1's own selection, which must not pick them.
+    # LoD 0 everywhere (distance mode, scale 0): no dither, a static camera
+    # renders the same image while the state is unchanged.
+    c1, cam, tf, *_ = _cache_scene(n_req=6, lod_mode=1, lod_scale=0.0, lag=1)
+    c2, *_ = _cache_scene(n_req=6, lod_mode=1, lod_scale=0.0, lag=2)
+    a1, s1 = c1.render(cam, tf)
+    b1, t1 = c2.render(cam, tf)
+    assert np.array_equal(a1, b1) and s1 == t1
+    req1, vic1 = c2.dump(O.DUMP_REQ), c2.dump(O.DUMP_VICT)
+    assert np.array_equal(req1, c1.dump(O.DUMP_REQ)) and np.array_equal(vic1, c1.dump(O.DUMP_VICT))
+    assert len(req1) == 6
+    pt1 = c2.dump(O.DUMP_PT)
+    assert np.all(pt1[req1] == 0)                       # in flight: not mapped
+    assert np.all(c2.dump(O.DUMP_OWNER)[vic1] == 0xFFFFFFFF)
+    # frame 2 sees the frame-1 state: same image, the same bricks requested again
+    b2, t2 = c2.render(cam, tf)
+    assert np.array_equal(b2, b1)
+    assert t2["bricks_requested"] == t1["bricks_requested"]
+    pt2 = c2.dump(O.DUMP_PT)
+    assert np.all(pt2[req1] == (0x80000000 | vic1))     # mapped at the end of frame 2
+    assert np.all(c2.dump(O.DUMP_OWNER)[vic1] == req1)
+    assert np.all(c2.dump(O.DUMP_STAMP)[vic1] == 2)
+    req2 = c2.dump(O.DUMP_REQ)
+    assert len(req2) == 6 and not set(req2.tolist()) & set(req1.tolist())
+    assert not set(c2.dump(O.DUMP_VICT).tolist()) & set(vic1.tolist())
+    # lag 1 had mapped the same bricks into the same slots one frame earlier
+    pa = c1.dump(O.DUMP_PT)
+    assert np.array_equal(pa[req1], pt2[req1])
+    # frame 3 hits them: fewer fallback samples than frame 2
+    b3, t3 = c2.render(cam, tf)
+    assert t3["fallback_hits"] < t2["fallback_hits"] and t3["hits"] > t2["hits"]
+
+
+# ------------------------------------------------------------ path tracing
+def test_neg_log1m_close_to_log_and_exact_at_zero():
+    # the binary32 series log against the library log: within 2 ulp
+    assert O.neg_log1m(0.0) == 0.0
+    for u in list(np.arange(1, 1 << 24, 7919) / 2.0**24) + [0.5, 1 - 2.0**-24]:
+        ref = -math.log1p(-u)
+        assert abs(O.neg_log1m(u) - ref) <= 2.5e-7 * ref
+
+
+def test_pt_uniform_is_the_splitmix64_stream():
+    # element 0 of the stream from state 0 is the top 24 bits of SplitMix64's
+    # published first output 0xE220A8397B1DCDAF; element j of key k is
+    # element j-1 of key k + gamma; uniform mean
+    assert O.pt_uniform(0, 0) == 0xE220A8 / 2.0**24
+    g = 0x9E3779B97F4A7C15
+    for key in (1, 12345, 2**63 + 7):
+        for j in (1, 2, 17):
+            assert O.pt_uniform(key, j) == O.pt_uniform((key + g) % 2**64, j - 1)
+    u = np.array([O.pt_uniform(99, j) for j in range(20000)])
+    assert abs(u.mean() - 0.5) < 0.01 and u.min() >= 0.0 and u.max() < 1.0
+
+
+def test_pt_sphere_directions_are_uniform_unit_vectors():
+    d = []
+    j = 0
+    for _ in range(20000):
+        v, j = O.pt_sphere(777, j)
+        d.append(v)
+    d = np.array(d, np.float64)
+    assert np.abs(np.linalg.norm(d, axis=1) - 1).max() < 1e-6
+    assert np.abs(d.mean(0)).max() < 0.02
+    assert np.abs((d ** 2).mean(0) - 1 / 3).max() < 0.01
+    assert abs((d[:, 0] * d[:, 1]).mean()) < 0.01
+    assert j >= 2 * 20000  # two uniforms per try, rejection ~21%
+
+
+def _pt_scene():
+    p, table, w = _small_inr(seed=3)
+    vol = (32, 32, 32)
+    cam = O.camera((0.2, 0.3, 1.8), (0, 0, 0), (0, 1, 0), 30.0, 8, 8, 0.5)
+    return p, table, w, vol, cam
+
+
+def test_pt_delta_tracking_transmittance_closed_form():
+    # constant extinction c, black albedo, ambient radiance 1, one bounce:
+    # a path returns 1 exactly when it crosses the volume without a real
+    # collision, so the mean over frames is exp(-c L)
+    p, table, w, vol, cam = _pt_scene()
+    c = 2.5
+    tf = S.tf_constant((0.0, 0.0, 0.0), c).astype(np.float64)
+    pt = O.pt_opts(light=(0, 0, 0), ambient=(1, 1, 1), max_bounces=1)
+    mo = O.march_opts(seed=5)
+    px, py = 4, 3
+    hit, o, d, tn, tf_ = O.ray(cam, vol, px, py)
+    assert hit
+    n = 3000
+    acc = np.zeros(4)
+    for f in range(1, n + 1):
+        img, st = O.render_pt_direct(p, table, w, cam, vol, mo, tf, pt, f, window=(px, py, 1, 1))
+        acc += img[0, 0]
+    mean = acc / n
+    T = math.exp(-c * (tf_ - tn))
+    sd = math.sqrt(T * (1 - T) / n)
+    assert abs(mean[0] - T) < 4 * sd
+    assert abs(mean[3] - (1 - T)) < 4 * sd
+
+
+def test_pt_single_scatter_with_ratio_tracking_closed_form():
+    # constant extinction c, white albedo, light along the pixel's ray (the
+    # shadow ray runs back to the entry point), majorant 3c (ratio tracking
+    # gives a continuous transmittance), irradiance 4 pi: the expected
+    # radiance is int_0^L c exp(-c t) exp(-c t) dt = (1 - exp(-2 c L)) / 2
+    p, table, w, vol, cam = _pt_scene()
+    c = 1.5
+    tf = S.tf_constant((1.0, 1.0, 1.0), c).astype(np.float64)
+    px, py = 4, 3
+    hit, o, d, tn, tf_ = O.ray(cam, vol, px, py)
+    pt = O.pt_opts(light_dir=tuple(float(v) for v in d), light=(4 * math.pi,) * 3,
+                   ambient=(0, 0, 0), max_bounces=1, sigma_max=3 * c)
+    mo = O.march_opts(seed=6)
+    n = 4000
+    vals = np.array([O.render_pt_direct(p, table, w, cam, vol, mo, tf, pt, f,
+                                        window=(px, py, 1, 1))[0][0, 0, 0] for f in range(1, n + 1)])
+    L = tf_ - tn
+    ref = (1 - math.exp(-2 * c * L)) / 2
+    assert abs(vals.mean() - ref) < 4 * vals.std() / math.sqrt(n) + 1e-3
+
+
+def test_pt_cached_frames_deterministic_and_preloaded():
+    # two fresh caches render identical frames and states; with the coarsest
+    # LoD preloaded no lookup is a true miss
+    runs = []
+    for _ in range(2):
+        c, cam, tf, *_ = _cache_scene(n_req=8)
+        pt = O.pt_opts(max_bounces=2)
+        imgs = [c.render_pt(cam, tf, pt) for _ in range(2)]
+        runs.append((imgs, c.dump(O.DUMP_PT), c.dump(O.DUMP_STAMP), c.dump(O.DUMP_RANK)))
+    (i0, pt0, s0, r0), (i1, pt1, s1, r1) = runs
+    for (a, sa), (b, sb) in zip(i0, i1):
+        assert np.array_equal(a, b) and sa == sb
+        assert sa["true_misses"] == 0 and sa["hits"] + sa["fallback_hits"] == sa["samples"] > 0
+    assert np.array_equal(pt0, pt1) and np.array_equal(s0, s1) and np.array_equal(r0, r1)
+    assert i0[0][1]["bricks_requested"] > 0
