@@ -57,6 +57,15 @@ WORKLOADS = {
 }
 
 
+# DRAM bytes (read + write) of one marching-kernel launch on the default
+# orbit configuration, from one ncu capture of the current kernel (frame 91);
+# a workload or option without such a capture reports null.
+PROFILED_TRAFFIC = {"orbit": 450.3e6}
+# path-tracing light: a directional light from above-front, dim blue ambient
+PT_OPTS = dict(light_dir=(0.3, -1.0, -0.4), light=(3.0, 3.0, 3.0), ambient=(0.05, 0.06, 0.08),
+               max_bounces=3)
+
+
 def frame_inputs(f, W, H, camera="orbit"):
     from paper_2504_18001_gb300 import synthetic as S
     tf = S.tf_ramps(2)
@@ -187,7 +196,7 @@ def run_gpu(args, wl):
     S3 = (wl["brick"] + 2) ** 3
     cache = cinr.Cache(inr_c, vol, pool_bytes=wl["pool_mib"] << 20, brick=wl["brick"],
                        levels=wl["levels"], storage=storage, n_req=wl["n_req"], ranking=1,
-                       preload=1, device=device)
+                       preload=1, lag=args.lag, device=device)
     rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
                          ray_layout=args.ray_layout, seed=args.seed, step_mode=wl["step_mode"],
                          step_lod_max=wl["step_lod_max"], use_graph=args.graph, device=device)
@@ -209,7 +218,11 @@ def run_gpu(args, wl):
         flush.random_(0, 255)  # L2 flush between timed iterations
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        if use_cache:
+        if args.pt:
+            # path tracing (Woodcock delta tracking), one path per pixel per frame
+            _, st = rend.render_pt(inr_c if use_cache else inr32, cam, tf, PT_OPTS,
+                                   cache=cache if use_cache else None, out=img)
+        elif use_cache:
             _, st = rend.render(inr_c, cam, tf, cache=cache, out=img)
         else:
             _, st = rend.render(inr32, cam, tf, cache=None, out=img)
@@ -254,9 +267,14 @@ def run_gpu(args, wl):
     for i in range(max(3, min(args.steps, 10))):
         cam, tf = frame_inputs(last_f + 1 + i, W, H, wl["camera"])
         flush.random_(0, 255)
-        torch.cuda.synchronize()
+        stream.synchronize()  # the frame's stream only: a lag-2 decode may still run
         t0 = time.perf_counter()
-        rend.render_host(inr_c, cam, tf, host, cache=cache)
+        if args.pt:
+            rend.render_pt(inr_c, cam, tf, PT_OPTS, cache=cache, out=img)
+            host.copy_(img, non_blocking=True)
+            stream.synchronize()
+        else:
+            rend.render_host(inr_c, cam, tf, host, cache=cache)
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = float(sum(e2e)) / len(e2e)
 
@@ -277,6 +295,9 @@ def run_gpu(args, wl):
     elem = 2 if args.precision == "mixed" else 4
     alg_bytes = [sl * (S3 * elem + 4) + W * H * 16 for sl in slots]
     achieved = sum(alg_bytes) / (sum(k_ms) * 1e-3) / 1e9
+    default_cfg = (args.precision == "mixed" and not args.macro and args.ray_layout == 0 and not args.pt
+                   and args.lod_scale == 1.0 and args.lag == 1 and not args.autotune)
+    traffic = PROFILED_TRAFFIC.get(args.workload) if default_cfg else None
     un_q = sum(s["inr_queries_direct"] for s in un_st)
     prec = args.precision
     res = {
@@ -305,6 +326,8 @@ def run_gpu(args, wl):
                    "ray_layout": "thread per ray" if args.ray_layout == 0 else "warp per ray",
                    "cuda_graph": bool(args.graph),
                    "macro_cell": args.macro or None,
+                   "lag": args.lag,
+                   "renderer": "path tracing (delta tracking)" if args.pt else "ray marching",
                    "timed_frames": [args.warmup, last_f],
                    "l2": "flushed (256 MiB write) before every timed frame",
                    "parallelism": f"replicas x{world}"},
@@ -324,7 +347,8 @@ def run_gpu(args, wl):
                 "d2h_bytes_per_step": W * H * 16 + 104},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "algorithmic_bytes_per_launch": sum(alg_bytes) / len(alg_bytes),
                      "kernel": ("march_cached_kernel<%d,%d,%s pool>"
                                 % (cfg.in_dim, cfg.hidden, "fp16" if prec == "mixed" else "fp32")),
                      "peak_kind": peak_kind},
@@ -378,8 +402,12 @@ def cpu_baseline(args, wl, table, w, f, cached_img, uncached_img, un_stats):
     mo = O.march_opts(K=32, eps_T=1e-3, lod_scale=args.lod_scale, step_mode=wl["step_mode"],
                       step_lod_max=wl["step_lod_max"])
     t0 = time.perf_counter()
-    ref, st = O.render_direct(p, table, w, oc, vol, mo, tf.astype(np.float64),
-                              window=(x0, y0, cw, cw))
+    if args.pt:
+        ref, st = O.render_pt_direct(p, table, w, oc, vol, mo, tf.astype(np.float64),
+                                     O.pt_opts(**PT_OPTS), f + 1, window=(x0, y0, cw, cw))
+    else:
+        ref, st = O.render_direct(p, table, w, oc, vol, mo, tf.astype(np.float64),
+                                  window=(x0, y0, cw, cw))
     dt = time.perf_counter() - t0
     mask = uncached_img[..., 3].cpu().numpy() > 0
     hit_full = int(mask.sum())
@@ -566,6 +594,10 @@ def main():
     ap.add_argument("--points", type=int, default=1 << 22, help="infer: batch size")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
     ap.add_argument("--ray-layout", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--pt", action="store_true",
+                    help="path-trace (Woodcock delta tracking) instead of ray marching")
+    ap.add_argument("--lag", type=int, default=1, choices=[1, 2],
+                    help="frames from a brick request to its use (2: decode on a second stream)")
     ap.add_argument("--macro", type=int, default=0,
                     help="macro-cell edge for empty-space skipping (0 = off)")
     ap.add_argument("--macro-min-level", type=int, default=0,

@@ -128,7 +128,15 @@ typedef struct {
  * per frame (Sec. 6.4); ranking = 1 for the priority ranking of
  * Sec. 4.3.3, 0 for first-n by brick key; preload = 1 decodes and pins
  * every brick of the coarsest LoD at creation (Sec. 4.3.4);
- * storage_precision = CINR_PREC_FP32 | CINR_PREC_FP16 for brick voxels. */
+ * storage_precision = CINR_PREC_FP32 | CINR_PREC_FP16 for brick voxels;
+ * lag = frames from a request to its first use: 1 (0 means 1): the bricks
+ * selected at the end of frame f are decoded on the frame's stream and serve
+ * frame f+1; 2: asynchronous request handling (Sec. 4.3.3, after Sarton's
+ * request handler) -- the selected bricks' slots are unmapped at the end of
+ * frame f, decoded on a second stream while frame f+1 renders, and mapped at
+ * the end of frame f+1 (before its own selection, which skips bricks mapped
+ * that way), serving frame f+2.  Both are deterministic.  A lag-2 cache
+ * cannot be used with use_graph. */
 typedef struct {
   int brick;
   int levels;
@@ -136,6 +144,7 @@ typedef struct {
   int ranking;
   int preload;
   int storage_precision;
+  int lag;
 } cinr_cache_opts;
 
 /* Per-frame counters.  samples = samples marched; inr_queries_direct = true
@@ -278,6 +287,36 @@ int cinr_render_field(cinr_renderer_t r, const float* field_dev,
                       cinr_frame_stats* stats, cinr_stream_t stream);
 
 int cinr_destroy_renderer(cinr_renderer_t r);
+
+/* Path tracing with Woodcock delta tracking (Sec. 5.1: the path-tracing
+ * pipeline uses the same sampler as ray marching).  One path per pixel and
+ * frame: free paths -ln(1-u)/sigma_bar (majorant sigma_bar = sigma_max, or
+ * the TF's largest extinction when sigma_max <= 0); a tentative collision at
+ * value v is real with probability sigma(v)/sigma_bar; at a real collision
+ * the throughput takes the TF colour as albedo, the directional light is
+ * added by next-event estimation (isotropic phase 1/(4 pi), shadow
+ * transmittance by ratio tracking) and the path scatters into a uniform
+ * direction, up to max_bounces collisions; paths that leave the volume (and
+ * pixels whose ray misses it) collect `ambient`.  The random numbers of
+ * pixel p in frame f are the SplitMix64 stream started at state
+ * (frame_seed << 32) | p; every volume lookup goes through the cache exactly
+ * as a ray-marching sample does (stochastic LoD from the distance to the
+ * eye, fallback, ranked requests, LRU stamps, true misses inferred) and the
+ * frame ends with the same cache update.  out_rgba_dev receives the path's
+ * radiance and alpha = 1 when the camera ray collided (average frames for a
+ * converged image).  Macro cells are not used. */
+typedef struct {
+  float light_dir[3]; /* direction the light travels */
+  float light[3];     /* irradiance (rgb) */
+  float ambient[3];   /* radiance of escaping paths (rgb) */
+  int max_bounces;    /* >= 1 */
+  float sigma_max;    /* majorant; <= 0: the TF's largest extinction */
+} cinr_pt_opts;
+
+int cinr_render_frame_pt(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr,
+                         const cinr_camera* cam, const cinr_tf* tf,
+                         const cinr_pt_opts* pt, float* out_rgba_dev,
+                         cinr_frame_stats* stats, cinr_stream_t stream);
 
 /* -------------------------------------------------------- macro cells --- */
 

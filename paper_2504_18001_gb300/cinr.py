@@ -54,7 +54,8 @@ class cinr_march_opts(C.Structure):
 
 class cinr_cache_opts(C.Structure):
     _fields_ = [("brick", C.c_int), ("levels", C.c_int), ("n_req", C.c_int),
-                ("ranking", C.c_int), ("preload", C.c_int), ("storage_precision", C.c_int)]
+                ("ranking", C.c_int), ("preload", C.c_int), ("storage_precision", C.c_int),
+                ("lag", C.c_int)]
 
 
 class cinr_frame_stats(C.Structure):
@@ -67,6 +68,17 @@ class cinr_frame_stats(C.Structure):
     def as_dict(self):
         return {n: (float(getattr(self, n)) if t is C.c_float else int(getattr(self, n)))
                 for n, t in self._fields_}
+
+
+class cinr_pt_opts(C.Structure):
+    _fields_ = [("light_dir", C.c_float * 3), ("light", C.c_float * 3), ("ambient", C.c_float * 3),
+                ("max_bounces", C.c_int), ("sigma_max", C.c_float)]
+
+
+def make_pt_opts(light_dir=(0.3, -1.0, -0.4), light=(3.0, 3.0, 3.0), ambient=(0.0, 0.0, 0.0),
+                 max_bounces=3, sigma_max=0.0) -> cinr_pt_opts:
+    return cinr_pt_opts((C.c_float * 3)(*light_dir), (C.c_float * 3)(*light),
+                        (C.c_float * 3)(*ambient), int(max_bounces), float(sigma_max))
 
 
 class cinr_macro_desc(C.Structure):
@@ -123,6 +135,7 @@ _SIGS = {
     "cinr_macro_apply_tf": [_vp, _vp, _vp],
     "cinr_destroy_macro": [_vp],
     "cinr_renderer_set_macro": [_vp, _vp],
+    "cinr_render_frame_pt": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _P(cinr_frame_stats), _vp],
 }
 
 
@@ -261,10 +274,10 @@ class Inr:
 
 class Cache:
     def __init__(self, inr: Inr, dims, pool_bytes, brick=8, levels=4, n_req=40, ranking=1,
-                 preload=1, storage="fp32", device="cuda", stream=None):
+                 preload=1, storage="fp32", lag=1, device="cuda", stream=None):
         L = lib()
         self.opts = cinr_cache_opts(int(brick), int(levels), int(n_req), int(ranking), int(preload),
-                                    PREC[storage])
+                                    PREC[storage], int(lag))
         self.dims = (C.c_int * 3)(*dims)
         nbytes, nslots = C.c_size_t(), C.c_long()
         check(L.cinr_cache_bytes(self.dims, int(pool_bytes), C.byref(self.opts), C.byref(nbytes),
@@ -500,6 +513,22 @@ class Renderer:
 
     def misses(self, stream=None):
         return debug_dump(self.h, DUMP_MISSES, stream).reshape(-1, 2)
+
+    def render_pt(self, inr: Inr, camera, tf, pt=None, cache: Cache | None = None, out=None,
+                  stream=None):
+        """One path-traced frame (Woodcock delta tracking); returns (rgba, stats)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.H, self.W, 4), dtype=torch.float32, device=self.device)
+        cam = camera if isinstance(camera, cinr_camera) else make_camera(camera)
+        t = tf if isinstance(tf, cinr_tf) else make_tf(tf)
+        o = pt if isinstance(pt, cinr_pt_opts) else make_pt_opts(**(pt or {}))
+        st = cinr_frame_stats()
+        check(lib().cinr_render_frame_pt(self.h, cache.h if cache is not None else None, inr.h,
+                                         C.byref(cam), C.byref(t), C.byref(o),
+                                         C.c_void_p(out.data_ptr()), C.byref(st), _stream(stream)),
+              "cinr_render_frame_pt")
+        return out, st.as_dict()
 
     def set_macro(self, macro: Macro | None):
         """Attach macro cells (None detaches): transparent cells are skipped."""

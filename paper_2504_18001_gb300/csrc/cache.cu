@@ -46,6 +46,7 @@ int geometry(const int vol[3], const cinr_cache_opts* o, Geometry* g) {
     return set_error(CINR_ERR_ARG, "n_req must be in [1, %d]", kMaxReq);
   if (o->storage_precision != CINR_PREC_FP32 && o->storage_precision != CINR_PREC_FP16)
     return set_error(CINR_ERR_ARG, "storage_precision must be FP32 or FP16");
+  if (o->lag < 0 || o->lag > 2) return set_error(CINR_ERR_ARG, "lag must be 1 or 2 (0 means 1)");
   g->L = o->levels;
   g->B = o->brick;
   g->S = o->brick + 2;
@@ -191,12 +192,14 @@ struct ReqKeys {
   const uint32_t* touched;
   const uint32_t* count;
   const uint32_t* rank;
+  const uint32_t* pt;
   uint32_t Tf;
   int key_bits;
   int ranking;
   __device__ bool operator()(uint32_t i, unsigned long long& key, uint32_t& val) const {
     if (i >= *count) return false;
     uint32_t b = touched[i];
+    if (pt[b] & kMapped) return false;  // mapped since its request (lag 2)
     uint32_t score = rank[b] - Tf;
     score = score > 1000u ? 1000u : score;
     key = ranking ? ((unsigned long long)(1000u - score) << key_bits) | b : (unsigned long long)b;
@@ -351,9 +354,11 @@ __global__ void sel_reset(SelState* st) {
 
 // Commit (Fig. 1 step 5): request i gets victim i; the victim's previous
 // brick is unmapped, the requested brick mapped, the slot stamped.
+// With map == false (lag 2) the victims are only unmapped: the requested
+// bricks are mapped by map_pending_kernel once decoded.
 __global__ void commit_kernel(CacheDev c, const uint32_t* req, const uint32_t* req_n,
                               const uint32_t* vic, const uint32_t* vic_n, uint32_t frame,
-                              uint32_t* decode_n, unsigned long long* stats, uint32_t S3) {
+                              uint32_t* decode_n, unsigned long long* stats, uint32_t S3, bool map) {
   const uint32_t m = *req_n < *vic_n ? *req_n : *vic_n;
   uint32_t ev = 0;
   for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
@@ -363,9 +368,13 @@ __global__ void commit_kernel(CacheDev c, const uint32_t* req, const uint32_t* r
       c.pt[old] = 0u;
       ++ev;
     }
-    c.pt[key] = kMapped | slot;
-    c.owner[slot] = key;
-    c.stamp[slot] = frame;
+    if (map) {
+      c.pt[key] = kMapped | slot;
+      c.owner[slot] = key;
+      c.stamp[slot] = frame;
+    } else {
+      c.owner[slot] = kNoOwner;  // in flight until the next frame's end
+    }
   }
   for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
   if ((threadIdx.x & 31) == 0 && ev) atomicAdd(&stats[ST_EVICT], (unsigned long long)ev);
@@ -373,6 +382,19 @@ __global__ void commit_kernel(CacheDev c, const uint32_t* req, const uint32_t* r
     *decode_n = m;
     stats[ST_DECODED] += m;
     stats[ST_DECODE] += (unsigned long long)m * S3;
+  }
+}
+
+// Lag 2: maps the bricks decoded during this frame (the previous frame's
+// selection) and stamps their slots with this frame.
+__global__ void map_pending_kernel(CacheDev c, const uint32_t* req, const uint32_t* vic,
+                                   const uint32_t* decode_n, uint32_t frame) {
+  const uint32_t m = *decode_n;
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const uint32_t slot = vic[i], key = req[i];
+    c.pt[key] = kMapped | slot;
+    c.owner[slot] = key;
+    c.stamp[slot] = frame;
   }
 }
 
@@ -413,7 +435,7 @@ int radix_select(const KF& kf, uint32_t n, int key_bits, uint32_t want, SelState
 // per work item.
 template <int IN, int H, int MLPP>
 int launch_decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys, const uint32_t* slots,
-                  const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s) {
+                  const uint32_t* n_dev, uint32_t n_grid, int cap_per_sm, cudaStream_t s) {
   if (n_grid == 0) return CINR_OK;
   auto k = decode_kernel<IN, H, MLPP>;
   int smem = MLPP ? (int)sizeof(tc::TcSmem<IN, H>) : mlp_floats<IN, H>() * 4;
@@ -435,7 +457,7 @@ int launch_decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys
   }
   const int S3 = c.S * c.S * c.S;
   const long work = (long)n_grid * ((S3 + 127) / 128);
-  long grid = (long)per_sm * num_sms();
+  long grid = (long)(cap_per_sm > 0 && cap_per_sm < per_sm ? cap_per_sm : per_sm) * num_sms();
   if (grid > work) grid = work;
   k<<<(unsigned)grid, 128, smem, s>>>(inr->dev, c, inr->w16, keys, slots, n_dev, n_grid,
                                       reinterpret_cast<int*>(inr->scratch + 16));
@@ -445,21 +467,23 @@ int launch_decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys
 
 template <int MLPP>
 int decode_prec(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys, const uint32_t* slots,
-                const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s) {
+                const uint32_t* n_dev, uint32_t n_grid, int cap, cudaStream_t s) {
   switch (shape_of(inr->dev.IN, inr->dev.H)) {
-    case Shape::S16x32: return launch_decode<16, 32, MLPP>(inr, c, keys, slots, n_dev, n_grid, s);
-    case Shape::S32x64: return launch_decode<32, 64, MLPP>(inr, c, keys, slots, n_dev, n_grid, s);
-    case Shape::S48x64: return launch_decode<48, 64, MLPP>(inr, c, keys, slots, n_dev, n_grid, s);
+    case Shape::S16x32: return launch_decode<16, 32, MLPP>(inr, c, keys, slots, n_dev, n_grid, cap, s);
+    case Shape::S32x64: return launch_decode<32, 64, MLPP>(inr, c, keys, slots, n_dev, n_grid, cap, s);
+    case Shape::S48x64: return launch_decode<48, 64, MLPP>(inr, c, keys, slots, n_dev, n_grid, cap, s);
     default: return set_error(CINR_ERR_ARG, "unsupported shape");
   }
 }
 
+// cap > 0 limits the decode to cap CTAs per SM (lag 2: the decode shares
+// the SMs with the next frame's marching kernel).
 int decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys, const uint32_t* slots,
-           const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s) {
-  if (inr->p.mlp_precision == CINR_PREC_FP16) return decode_prec<1>(inr, c, keys, slots, n_dev, n_grid, s);
-  if (inr->p.mlp_precision == CINR_PREC_BF16) return decode_prec<2>(inr, c, keys, slots, n_dev, n_grid, s);
-  if (inr->p.mlp_precision == CINR_PREC_FP8) return decode_prec<3>(inr, c, keys, slots, n_dev, n_grid, s);
-  return decode_prec<0>(inr, c, keys, slots, n_dev, n_grid, s);
+           const uint32_t* n_dev, uint32_t n_grid, cudaStream_t s, int cap = 0) {
+  if (inr->p.mlp_precision == CINR_PREC_FP16) return decode_prec<1>(inr, c, keys, slots, n_dev, n_grid, cap, s);
+  if (inr->p.mlp_precision == CINR_PREC_BF16) return decode_prec<2>(inr, c, keys, slots, n_dev, n_grid, cap, s);
+  if (inr->p.mlp_precision == CINR_PREC_FP8) return decode_prec<3>(inr, c, keys, slots, n_dev, n_grid, cap, s);
+  return decode_prec<0>(inr, c, keys, slots, n_dev, n_grid, cap, s);
 }
 
 }  // namespace
@@ -557,12 +581,32 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
     preload_map<<<(unsigned)((n_coarse + 255) / 256), 256, 0, s>>>(d, (uint32_t)n_coarse);
     CINR_CK(cudaGetLastError());
   }
+  if (o->lag == 2) {
+    cudaError_t ce = cudaStreamCreateWithFlags(&c->dstream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->e_sel, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->e_dec, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+      cinr_destroy_cache(c);
+      return cuda_error(ce, "lag-2 stream or events");
+    }
+  }
   *out = c;
   return CINR_OK;
 }
 
 extern "C" int cinr_destroy_cache(cinr_cache_t cache) {
+  if (cache && cache->dstream) {
+    cudaStreamSynchronize(cache->dstream);
+    if (cache->e_sel) cudaEventDestroy(cache->e_sel);
+    if (cache->e_dec) cudaEventDestroy(cache->e_dec);
+    cudaStreamDestroy(cache->dstream);
+  }
   delete cache;
+  return CINR_OK;
+}
+
+int cinr_cache_wait_decode(cinr_cache_s* c, cudaStream_t s) {
+  if (c->pending) CINR_CK(cudaStreamWaitEvent(s, c->e_dec, 0));
   return CINR_OK;
 }
 
@@ -570,7 +614,18 @@ int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStr
   const uint32_t frame = (uint32_t)c->frame;
   const uint32_t Tf = (uint32_t)(1001ull * c->frame);
   const uint32_t want = (uint32_t)c->o.n_req;
-  ReqKeys rk{c->dev.touched, c->dev.touched_count, c->dev.rank, Tf, c->key_bits, c->o.ranking};
+  const bool lag2 = c->o.lag == 2;
+  uint32_t extra = 0;
+  if (lag2 && c->pending) {
+    // the bricks decoded on the second stream during this frame are mapped
+    // first: they serve the next frame and are no request candidates
+    CINR_CK(cudaStreamWaitEvent(s, c->e_dec, 0));
+    map_pending_kernel<<<1, 1024, 0, s>>>(c->dev, c->req_sorted, c->vic_sorted, c->decode_n, frame);
+    CINR_CK(cudaGetLastError());
+    c->pending = false;
+    extra = 1;
+  }
+  ReqKeys rk{c->dev.touched, c->dev.touched_count, c->dev.rank, c->dev.pt, Tf, c->key_bits, c->o.ranking};
   const int rbits = c->o.ranking ? c->key_bits + 10 : c->key_bits;
   int e = radix_select(rk, (uint32_t)c->n_bricks, rbits, want, c->sel_req, c->req_keys,
                        c->req_vals, c->req_sorted, c->req_n, s);
@@ -581,13 +636,21 @@ int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStr
                    c->vic_sorted, c->vic_n, s);
   if (e) return e;
   commit_kernel<<<1, 1024, 0, s>>>(c->dev, c->req_sorted, c->req_n, c->vic_sorted, c->vic_n, frame,
-                                   c->decode_n, stats_dev, (uint32_t)(c->dev.S * c->dev.S * c->dev.S));
+                                   c->decode_n, stats_dev, (uint32_t)(c->dev.S * c->dev.S * c->dev.S),
+                                   !lag2);
   CINR_CK(cudaGetLastError());
   // kernels of this update: per radix select reset + (hist, pick) per pass +
-  // gather + sort; commit; decode
+  // gather + sort; commit; decode (+ the map of lag 2)
   auto sel = [](int bits) { return 3 + 2 * (bits <= 11 ? 1 : (bits + 10) / 11); };
-  c->last_launches = (uint32_t)(sel(rbits) + sel(vbits) + 2);
-  return decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, s);
+  c->last_launches = (uint32_t)(sel(rbits) + sel(vbits) + 2) + extra;
+  if (!lag2) return decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, s);
+  CINR_CK(cudaEventRecord(c->e_sel, s));
+  CINR_CK(cudaStreamWaitEvent(c->dstream, c->e_sel, 0));
+  int e2 = decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, c->dstream, 2);
+  if (e2) return e2;
+  CINR_CK(cudaEventRecord(c->e_dec, c->dstream));
+  c->pending = true;
+  return CINR_OK;
 }
 
 extern "C" int cinr_cache_level_info(cinr_cache_t cache, int level, int dims[3], int nbricks[3],

@@ -470,6 +470,11 @@ struct cinr_cache_s {
   uint32_t* decode_n;
   int slot_bits, key_bits;
   uint32_t last_launches;  // kernels of the last end-of-frame update
+  // lag 2: decode stream, "selection done" and "decode done" events, and
+  // whether a decoded batch waits to be mapped
+  cudaStream_t dstream = nullptr;
+  cudaEvent_t e_sel = nullptr, e_dec = nullptr;
+  bool pending = false;
 };
 
 struct cinr_macro_s {
@@ -495,6 +500,10 @@ int cinr_macro_apply(cinr_macro_s* m, const float (*rgba)[4], cudaStream_t s);
 // Cache update at the end of a frame (request selection, victims, commit,
 // decode), enqueued on `s`; stats_dev receives decoded/evicted counts.
 int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStream_t s);
+
+// Makes `s` wait for a lag-2 decode still running on the cache's second
+// stream (before reading the pool).
+int cinr_cache_wait_decode(cinr_cache_s* c, cudaStream_t s);
 
 // Tensor-core direct inference (FP16/BF16 MLP), used by cinr_infer.
 int cinr_infer_tc(const cinr_inr_s* inr, const float* xyz, long n, float* out, cudaStream_t s);

@@ -43,6 +43,7 @@ struct cinr_renderer_s {
 namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
+constexpr int kPtMaxSteps = 4096;  // tracking steps per path segment
 
 struct FrameParams {
   CamDev cam;
@@ -63,6 +64,11 @@ struct FrameParams {
   const uint16_t* w16;  // half-precision MLP weights (tensor-core path)
   int* err;             // set when a bounded device-side wait gives up
   MacroDev mac;         // transparent macro cells (skip == nullptr: off)
+  // path tracing (Sec. 5.1): direction to the light, its irradiance, the
+  // ambient radiance, the majorant and its reciprocal, bounces
+  float pt_ls[3], pt_light[3], pt_amb[3];
+  float pt_sbar, pt_inv;
+  int pt_bounces;
 };
 
 // Bytes of the frame kernel's shared memory before the MLP region (TF,
@@ -640,6 +646,317 @@ int launch_march_cached_shape(const FrameParams& P, cudaStream_t s) {
   return f16 ? launch_march_cached_pool<true, false>(P, s) : launch_march_cached_pool<false, false>(P, s);
 }
 
+// ---------------------------------------------------------------------------
+// Path tracing with Woodcock delta tracking (Sec. 5.1), one path per pixel
+// and frame, thread per path (warps take 8 x 4 pixel tiles).  Every
+// quantity that positions a lookup is binary32 in a fixed order (the series
+// log, the sphere sampler and the box exits use +,-,*,/,sqrt only), so the
+// lookups, requests, stamps and misses match the oracle bit for bit; the
+// collision decisions compare u * sigma_bar with the sampled extinction.
+
+// j-th uniform of the SplitMix64 generator started at state key (top 24 bits).
+__device__ __forceinline__ float pt_uniform(uint64_t key, uint32_t j) {
+  uint64_t z = key + 0x9E3779B97F4A7C15ull * (uint64_t)j + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (float)(z >> 40) * (1.0f / 16777216.0f);
+}
+
+// -ln(1 - u): y = m 2^e with m in [sqrt(2)/2, sqrt(2)), ln y = e ln2 +
+// 2 atanh((m-1)/(m+1)) by its series to z^15.
+__device__ __forceinline__ float neg_log1m(float u) {
+  const float y = f_sub(1.0f, u);
+  const uint32_t bits = __float_as_uint(y);
+  int e = (int)((bits >> 23) & 0xFFu) - 127;
+  float m = __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+  if (m > 1.41421356f) {
+    m = f_mul(m, 0.5f);
+    e = e + 1;
+  }
+  const float z = f_div(f_sub(m, 1.0f), f_add(m, 1.0f));
+  const float z2 = f_mul(z, z);
+  float q = f_div(1.0f, 15.0f);
+  q = f_add(f_mul(q, z2), f_div(1.0f, 13.0f));
+  q = f_add(f_mul(q, z2), f_div(1.0f, 11.0f));
+  q = f_add(f_mul(q, z2), f_div(1.0f, 9.0f));
+  q = f_add(f_mul(q, z2), f_div(1.0f, 7.0f));
+  q = f_add(f_mul(q, z2), f_div(1.0f, 5.0f));
+  q = f_add(f_mul(q, z2), f_div(1.0f, 3.0f));
+  q = f_add(f_mul(q, z2), 1.0f);
+  const float lm = f_mul(f_mul(2.0f, z), q);
+  return -f_add(f_mul((float)e, 0.693147180559945309f), lm);
+}
+
+// Uniform direction on the sphere (Marsaglia 1972), rejection in the disc.
+__device__ __forceinline__ void pt_sphere(uint64_t key, uint32_t& j, float d[3]) {
+  for (int tries = 0; tries < 64; ++tries) {
+    const float x1 = f_sub(f_mul(pt_uniform(key, j++), 2.0f), 1.0f);
+    const float x2 = f_sub(f_mul(pt_uniform(key, j++), 2.0f), 1.0f);
+    const float s = f_add(f_mul(x1, x1), f_mul(x2, x2));
+    if (s < 1.0f) {
+      const float r = f_mul(2.0f, __fsqrt_rn(f_sub(1.0f, s)));
+      d[0] = f_mul(x1, r);
+      d[1] = f_mul(x2, r);
+      d[2] = f_sub(1.0f, f_mul(2.0f, s));
+      return;
+    }
+  }
+  d[0] = 0.0f;
+  d[1] = 0.0f;
+  d[2] = 1.0f;
+}
+
+// Distance from a point inside the box [-h, h] to its boundary along d.
+__device__ __forceinline__ float box_exit(const CamDev& c, const float o[3], const float d[3]) {
+  float t = INFINITY;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (d[a] == 0.0f) continue;
+    const float inv = f_div(1.0f, d[a]);
+    const float t0 = f_mul(f_sub(-c.h[a], o[a]), inv);
+    const float t1 = f_mul(f_sub(c.h[a], o[a]), inv);
+    t = fminf(t, fmaxf(t0, t1));
+  }
+  return t;
+}
+
+// World point o + t d, its normalised coordinate and distance to the eye.
+__device__ __forceinline__ void pt_point(const CamDev& c, const float o[3], const float d[3], float t,
+                                         float p[3], float x[3], float& dist) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    p[q] = f_add(o[q], f_mul(t, d[q]));
+    const float num = f_add(p[q], c.h[q]);
+    x[q] = clamp01(c.e[q] == 1.0f ? num : f_div(num, c.e[q]));
+  }
+  const float dx = f_sub(p[0], c.o[0]), dy = f_sub(p[1], c.o[1]), dz = f_sub(p[2], c.o[2]);
+  dist = __fsqrt_rn(f_add(f_add(f_mul(dx, dx), f_mul(dy, dy)), f_mul(dz, dz)));
+}
+
+struct PtCounts {
+  uint32_t samp, hit, fb, miss, req, slot;
+};
+
+// One lookup of the path tracer: through the cache (stochastic LoD from
+// the distance to the eye, page-table walk with fallback, ranked request,
+// LRU stamp, true miss inferred in place and recorded) or, without a
+// cache, by direct inference.  Atomics are per lane: the rank update
+// max(r, T_f) + 1 clamped at T_f + 1000 and the stamp reach the same final
+// state in any order.
+template <int IN, int H, bool CACHED, bool F16POOL>
+__device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const float x[3], float dist,
+                          uint32_t rseed, uint32_t k, uint32_t pixel, PtCounts& n) {
+  ++n.samp;
+  if (CACHED) {
+    const CacheDev& c = P.cache;
+    const int L = c.L, B = c.B, S = c.S;
+    const size_t S3 = (size_t)S * S * S;
+    const int l = sample_lod(P.cam, L, 0, rseed, k, dist);
+    const float pv0 = f_mul(x[0], (float)c.vol[0]), pv1 = f_mul(x[1], (float)c.vol[1]),
+                pv2 = f_mul(x[2], (float)c.vol[2]);
+    for (int lev = l; lev < L; ++lev) {
+      const LevelGeo g = s_geo[lev];
+      const float s0 = f_mul(pv0, g.scale), s1 = f_mul(pv1, g.scale), s2 = f_mul(pv2, g.scale);
+      int b0 = (int)floorf(c.invB > 0.0f ? f_mul(s0, c.invB) : f_div(s0, (float)B));
+      int b1 = (int)floorf(c.invB > 0.0f ? f_mul(s1, c.invB) : f_div(s1, (float)B));
+      int b2 = (int)floorf(c.invB > 0.0f ? f_mul(s2, c.invB) : f_div(s2, (float)B));
+      b0 = min(max(b0, 0), g.nb0 - 1);
+      b1 = min(max(b1, 0), g.nb1 - 1);
+      b2 = min(max(b2, 0), g.nb2 - 1);
+      const uint32_t key = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
+      const uint32_t e = __ldg(c.pt + key);
+      if (!(e & kMapped)) {
+        if (lev == l) {
+          const uint32_t old = atomicMax(c.rank + key, P.Tf);
+          if (old < P.Tf) {
+            ++n.req;
+            c.touched[atomicAdd(c.touched_count, 1u)] = key;
+          }
+          atomicAdd(c.rank + key, 1u);
+          atomicMin(c.rank + key, P.Tf + 1000u);
+        }
+        continue;
+      }
+      const uint32_t slot = e & ~kMapped;
+      if (c.stamp[slot] != P.frame && atomicExch(c.stamp + slot, P.frame) != P.frame) ++n.slot;
+      const float q0 = fminf(fmaxf(f_sub(s0, 0.5f), 0.0f), g.dmax0);
+      const float q1 = fminf(fmaxf(f_sub(s1, 0.5f), 0.0f), g.dmax1);
+      const float q2 = fminf(fmaxf(f_sub(s2, 0.5f), 0.0f), g.dmax2);
+      const int i0 = (int)floorf(q0), i1 = (int)floorf(q1), i2 = (int)floorf(q2);
+      const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
+      const int l0 = i0 - (b0 * B - 1), l1 = i1 - (b1 * B - 1), l2 = i2 - (b2 * B - 1);
+      const size_t base = (size_t)slot * S3 + (size_t)((l2 * S + l1) * S + l0);
+      const void* pool = c.pool;
+      const float v000 = pool_ld<F16POOL>(pool, base), v100 = pool_ld<F16POOL>(pool, base + 1);
+      const float v010 = pool_ld<F16POOL>(pool, base + S), v110 = pool_ld<F16POOL>(pool, base + S + 1);
+      const float v001 = pool_ld<F16POOL>(pool, base + S * S), v101 = pool_ld<F16POOL>(pool, base + S * S + 1);
+      const float v011 = pool_ld<F16POOL>(pool, base + S * S + S),
+                  v111 = pool_ld<F16POOL>(pool, base + S * S + S + 1);
+      const float x00 = fmaf(f0, v100 - v000, v000), x10 = fmaf(f0, v110 - v010, v010);
+      const float x01 = fmaf(f0, v101 - v001, v001), x11 = fmaf(f0, v111 - v011, v011);
+      const float y0 = fmaf(f1, x10 - x00, x00), y1 = fmaf(f1, x11 - x01, x01);
+      if (lev == l)
+        ++n.hit;
+      else
+        ++n.fb;
+      return fmaf(f2, y1 - y0, y0);
+    }
+  }
+  ++n.miss;
+  if (P.miss_rec) {
+    const uint32_t at = atomicAdd(P.miss_count, 1u);
+    if (at < P.miss_cap) {
+      P.miss_rec[2 * at] = pixel;
+      P.miss_rec[2 * at + 1] = k;
+    }
+  }
+  return infer_miss<IN, H>(P.inr, x[0], x[1], x[2]);
+}
+
+template <int IN, int H, bool CACHED, bool F16POOL>
+__global__ void __launch_bounds__(kFrameThreads, 6) pt_kernel(const __grid_constant__ FrameParams P) {
+  __shared__ float4 s_tf[256];
+  __shared__ LevelGeo s_geo[kMaxLod];
+  for (int i = threadIdx.x; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
+  if (CACHED && threadIdx.x < P.cache.L) {
+    const CacheDev& c = P.cache;
+    const int l = threadIdx.x;
+    LevelGeo g;
+    g.nb0 = c.nb[l][0];
+    g.nb1 = c.nb[l][1];
+    g.nb2 = c.nb[l][2];
+    g.off = c.off[l];
+    g.dmax0 = (float)(c.dims[l][0] - 1);
+    g.dmax1 = (float)(c.dims[l][1] - 1);
+    g.dmax2 = (float)(c.dims[l][2] - 1);
+    g.scale = __int_as_float((127 - l) << 23);
+    s_geo[l] = g;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const CamDev& cam = P.cam;
+  PtCounts n = {0, 0, 0, 0, 0, 0};
+  const uint32_t n_tiles = P.n_rays >> 5;
+  while (true) {
+    uint32_t tile = 0;
+    if (lane == 0) tile = atomicAdd(P.ray_counter, 1u);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= n_tiles) break;
+    const uint32_t r = tile * 32u + (uint32_t)lane;
+    const uint32_t t64 = r >> 6, w = r & 63u;
+    const int px = (int)((t64 % P.tiles_x) * 8 + (w & 7u));
+    const int py = (int)((t64 / P.tiles_x) * 8 + (w >> 3));
+    if (px >= cam.W || py >= cam.H) continue;
+    const uint32_t pixel = (uint32_t)(py * cam.W + px);
+    float o[3] = {cam.o[0], cam.o[1], cam.o[2]}, d[3], t0 = 0.f, t1 = 0.f;
+    float Lr = P.pt_amb[0], Lg = P.pt_amb[1], Lb = P.pt_amb[2], alpha = 0.f;
+    if (ray_setup(cam, px, py, d, t0, t1)) {
+      const uint64_t key = ((uint64_t)P.fseed << 32) | (uint64_t)pixel;
+      const uint32_t rseed = ray_seed(P.fseed, pixel);
+      float br = 1.f, bg = 1.f, bb = 1.f;
+      Lr = Lg = Lb = 0.f;
+      uint32_t j = 0, k = 0;
+      for (int b = 0;; ++b) {
+        bool hit = false;
+        float t = t0, p[3] = {0.f, 0.f, 0.f}, v = 0.f;
+        for (int step = 0; P.pt_sbar > 0.0f && step < kPtMaxSteps; ++step) {
+          t = f_add(t, f_mul(neg_log1m(pt_uniform(key, j++)), P.pt_inv));
+          if (!(t < t1)) break;
+          float x[3], dist;
+          pt_point(cam, o, d, t, p, x, dist);
+          v = pt_value<IN, H, CACHED, F16POOL>(P, s_geo, x, dist, rseed, k, pixel, n);
+          ++k;
+          const float sig = tf_lookup(s_tf, v).w;
+          if (pt_uniform(key, j++) * P.pt_sbar < sig) {
+            hit = true;
+            break;
+          }
+        }
+        if (!hit) {
+          Lr = fmaf(br, P.pt_amb[0], Lr);
+          Lg = fmaf(bg, P.pt_amb[1], Lg);
+          Lb = fmaf(bb, P.pt_amb[2], Lb);
+          break;
+        }
+        if (b == 0) alpha = 1.f;
+        const float4 alb = tf_lookup(s_tf, v);
+        br *= alb.x;
+        bg *= alb.y;
+        bb *= alb.z;
+        // next-event estimation: shadow transmittance by ratio tracking
+        const float ts1 = box_exit(cam, p, P.pt_ls);
+        float ts = 0.f, Tr = 1.f;
+        for (int step = 0; P.pt_sbar > 0.0f && step < kPtMaxSteps; ++step) {
+          ts = f_add(ts, f_mul(neg_log1m(pt_uniform(key, j++)), P.pt_inv));
+          if (!(ts < ts1)) break;
+          float pq[3], x[3], dist;
+          pt_point(cam, p, P.pt_ls, ts, pq, x, dist);
+          const float v2 = pt_value<IN, H, CACHED, F16POOL>(P, s_geo, x, dist, rseed, k, pixel, n);
+          ++k;
+          Tr *= 1.0f - tf_lookup(s_tf, v2).w * P.pt_inv;
+        }
+        const float ne = Tr * 0.0795774715459476679f;  // 1 / (4 pi)
+        Lr = fmaf(br * P.pt_light[0], ne, Lr);
+        Lg = fmaf(bg * P.pt_light[1], ne, Lg);
+        Lb = fmaf(bb * P.pt_light[2], ne, Lb);
+        if (b + 1 >= P.pt_bounces) break;
+        pt_sphere(key, j, d);
+        o[0] = p[0];
+        o[1] = p[1];
+        o[2] = p[2];
+        t0 = 0.f;
+        t1 = box_exit(cam, o, d);
+      }
+    }
+    P.out[pixel] = make_float4(Lr, Lg, Lb, alpha);
+  }
+  unsigned long long a[6] = {n.samp, n.hit, n.fb, n.miss, n.req, n.slot};
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    for (int off = 16; off > 0; off >>= 1) a[i] += __shfl_xor_sync(kFull, a[i], off);
+  if (lane == 0) {
+    if (a[0]) atomicAdd(P.stats + ST_SAMPLES, a[0]);
+    if (a[1]) atomicAdd(P.stats + ST_HITS, a[1]);
+    if (a[2]) atomicAdd(P.stats + ST_FALLBACK, a[2]);
+    if (a[3]) {
+      atomicAdd(P.stats + ST_MISSES, a[3]);
+      atomicAdd(P.stats + ST_DIRECT, a[3]);
+    }
+    if (a[4]) atomicAdd(P.stats + ST_REQ, a[4]);
+    if (a[5]) atomicAdd(P.stats + ST_SLOTS, a[5]);
+  }
+}
+
+template <int IN, int H, bool CACHED, bool F16POOL>
+int launch_pt(const FrameParams& P, cudaStream_t s) {
+  auto k = pt_kernel<IN, H, CACHED, F16POOL>;
+  static int blocks_per_sm = 0;
+  if (!blocks_per_sm) {
+    CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
+    if (blocks_per_sm < 1) return set_error(CINR_ERR_CUDA, "path-tracing kernel cannot be resident");
+  }
+  k<<<(unsigned)(blocks_per_sm * num_sms()), kFrameThreads, 0, s>>>(P);
+  CINR_CK(cudaGetLastError());
+  return CINR_OK;
+}
+
+template <bool CACHED, bool F16POOL>
+int launch_pt_pool(const FrameParams& P, cudaStream_t s) {
+  switch (shape_of(P.inr.IN, P.inr.H)) {
+    case Shape::S16x32: return launch_pt<16, 32, CACHED, F16POOL>(P, s);
+    case Shape::S32x64: return launch_pt<32, 64, CACHED, F16POOL>(P, s);
+    case Shape::S48x64: return launch_pt<48, 64, CACHED, F16POOL>(P, s);
+    default: return set_error(CINR_ERR_ARG, "unsupported shape");
+  }
+}
+
+int launch_pt_shape(const FrameParams& P, bool cached, cudaStream_t s) {
+  if (!cached) return launch_pt_pool<false, false>(P, s);
+  return P.cache.pool_prec == CINR_PREC_FP16 ? launch_pt_pool<true, true>(P, s)
+                                             : launch_pt_pool<true, false>(P, s);
+}
+
 // ----------------------------------------------------------- host side
 void normalize3(const float a[3], float out[3]) {
   float l2 = a[0] * a[0] + a[1] * a[1];
@@ -827,7 +1144,8 @@ int launch_as_graph(cinr_renderer_s* r, F&& enqueue, cudaStream_t s) {
 }
 
 int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_camera* cam,
-           const cinr_tf* tf, float4* out, cinr_frame_stats* stats, cudaStream_t s) {
+           const cinr_tf* tf, float4* out, cinr_frame_stats* stats, cudaStream_t s,
+           const cinr_pt_opts* pt = nullptr) {
   if (!r || !inr || !cam || !tf) return set_error(CINR_ERR_ARG, "NULL argument");
   if (cam->width != r->W || cam->height != r->H)
     return set_error(CINR_ERR_ARG, "camera is %dx%d, renderer %dx%d", cam->width, cam->height, r->W, r->H);
@@ -837,6 +1155,8 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
     for (int a = 0; a < 3; ++a)
       if (cache->dev.vol[a] != r->o.dims[a]) return set_error(CINR_ERR_ARG, "cache dims differ from renderer dims");
     if (cache->inr != inr) return set_error(CINR_ERR_ARG, "cache was built for another INR");
+    if (cache->o.lag == 2 && r->o.use_graph)
+      return set_error(CINR_ERR_ARG, "a lag-2 cache decodes across frames and cannot run as a per-frame graph");
   }
   FrameParams P;
   memset(&P, 0, sizeof(P));
@@ -866,7 +1186,23 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
 
   P.w16 = inr->w16;
   P.err = reinterpret_cast<int*>(r->counters + 2);
-  cinr_macro_s* mac = r->macro;
+  if (pt) {
+    if (pt->max_bounces < 1) return set_error(CINR_ERR_ARG, "max_bounces must be >= 1");
+    const float neg[3] = {-pt->light_dir[0], -pt->light_dir[1], -pt->light_dir[2]};
+    if (!(neg[0] != 0.0f || neg[1] != 0.0f || neg[2] != 0.0f))
+      return set_error(CINR_ERR_ARG, "light_dir must be non-zero");
+    normalize3(neg, P.pt_ls);
+    float m = 0.0f;
+    for (int i = 0; i < 256; ++i) m = fmaxf(m, tf->rgba[i][3]);
+    P.pt_sbar = pt->sigma_max > 0.0f ? pt->sigma_max : m;
+    P.pt_inv = P.pt_sbar > 0.0f ? 1.0f / P.pt_sbar : 0.0f;
+    for (int a = 0; a < 3; ++a) {
+      P.pt_light[a] = pt->light[a];
+      P.pt_amb[a] = pt->ambient[a];
+    }
+    P.pt_bounces = pt->max_bounces;
+  }
+  cinr_macro_s* mac = pt ? nullptr : r->macro;  // delta tracking does not skip cells
   if (mac) {
     for (int a = 0; a < 3; ++a)
       if (mac->vol[a] != r->o.dims[a]) return set_error(CINR_ERR_ARG, "macro-cell dims differ from renderer dims");
@@ -889,7 +1225,9 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
     }
     if (!graph) CINR_CK(cudaEventRecord(r->ev[0], q));
     int ee;
-    if (!cache)
+    if (pt)
+      ee = launch_pt_shape(P, cache != nullptr, q);
+    else if (!cache)
       ee = launch_frame_shape<false>(P, inr->p.mlp_precision, q);
     else if (r->o.ray_layout == 1)
       ee = launch_frame_shape<true>(P, inr->p.mlp_precision, q);
@@ -1002,6 +1340,14 @@ extern "C" int cinr_render_frame(cinr_renderer_t r, cinr_cache_t cache, cinr_inr
                 static_cast<cudaStream_t>(stream));
 }
 
+extern "C" int cinr_render_frame_pt(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr,
+                                    const cinr_camera* cam, const cinr_tf* tf, const cinr_pt_opts* pt,
+                                    float* out_rgba_dev, cinr_frame_stats* stats, cinr_stream_t stream) {
+  if (!out_rgba_dev || !pt) return set_error(CINR_ERR_ARG, "NULL argument");
+  return render(r, cache, inr, cam, tf, reinterpret_cast<float4*>(out_rgba_dev), stats,
+                static_cast<cudaStream_t>(stream), pt);
+}
+
 extern "C" int cinr_render_frame_host(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr,
                                       const cinr_camera* cam, const cinr_tf* tf, float* out_rgba_host,
                                       cinr_frame_stats* stats, cinr_stream_t stream) {
@@ -1033,6 +1379,8 @@ extern "C" int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap, 
   } else {
     cinr_cache_s* c = static_cast<cinr_cache_s*>(obj);
     uint32_t cnt = 0;
+    const int ew = cinr_cache_wait_decode(c, s);
+    if (ew) return ew;
     switch (what) {
       case CINR_DUMP_PAGE_TABLE: src = c->dev.pt; n = (size_t)c->n_bricks; break;
       case CINR_DUMP_STAMPS: src = c->dev.stamp; n = (size_t)c->n_slots; break;

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_req=40, ranking=1,
          preload=1, lod_scale=1.0, lod_mode=0, storage="fp32", K=32, eps=0.0, check_pixels=2e-3,
          cam_fn=None, mlp="fp32", tab="fp32", ray_layout=0, step_mode=0, step_lod_max=0,
-         use_graph=0, tf=None, macro_cell=0):
+         use_graph=0, tf=None, macro_cell=0, lag=1):
     from paper_2504_18001_gb300 import cinr
     cfg = S.INR_64
     table, w = scene(cfg)
@@ -24,12 +24,12 @@ def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_r
     S3 = (brick + 2) ** 3
     cache = cinr.Cache(inr, vol, pool_bytes=slots * S3 * (2 if storage == "fp16" else 4),
                        brick=brick, levels=levels, n_req=n_req, ranking=ranking, preload=preload,
-                       storage=storage)
+                       storage=storage, lag=lag)
     assert cache.n_slots == slots
     mo = O.march_opts(K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
                       step_mode=step_mode, step_lod_max=step_lod_max)
     oc = O.Cache(p, table, w, vol, brick, levels, slots, mo, n_req=n_req, ranking=ranking,
-                 preload=preload)
+                 preload=preload, lag=lag)
     r = cinr.Renderer(W, H, vol, K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
                       ray_layout=ray_layout, step_mode=step_mode, step_lod_max=step_lod_max,
                       use_graph=use_graph, miss_record_cap=W * H * 4000)
@@ -196,3 +196,24 @@ def test_lod_scaled_steps_uncached_and_field():
     ref, rst = O.render_field(field, ocam(cam), vol, mo, tf.astype(np.float64))
     assert st["samples"] == rst["samples"]
     assert np.abs(img.cpu().numpy() - ref).max() < 2e-3
+
+
+@pytest.mark.parametrize("preload", [1, 0])
+def test_cached_lag2_async_decode_state_bit_exact(preload):
+    # lag 2: victims unmapped at the end of frame f, decoded on a second
+    # stream during frame f+1, mapped at its end; state bit-exact per frame
+    cache, oc, hist, worst = _run(6, slots=60 if preload else 400, n_req=30, preload=preload, lag=2)
+    assert sum(h["bricks_decoded"] for h in hist) > 0
+
+
+def test_cached_lag2_under_pressure_and_decoded_bricks():
+    from paper_2504_18001_gb300 import cinr
+    def cam_fn(f, W, H):
+        return S.orbit_camera(0, W, H, start_deg=75.0 * f, distance=1.3, fov_y_deg=12.0)
+    cache, oc, hist, worst = _run(6, slots=60, n_req=30, lod_mode=1, lod_scale=0.0, levels=3,
+                                  cam_fn=cam_fn, lag=2)
+    assert sum(h["evictions"] for h in hist) > 0
+    pool = cache.dump(cinr.DUMP_POOL).reshape(cache.n_slots, -1)
+    own = cache.dump(cinr.DUMP_OWNERS)
+    for s in np.nonzero(own != 0xFFFFFFFF)[0][:30]:
+        assert np.abs(pool[s] - oc.slot_values(int(s))).max() < 1e-4

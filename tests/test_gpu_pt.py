@@ -1,0 +1,124 @@
+"""Path tracing with Woodcock delta tracking (Sec. 5.1) on the GPU against
+the oracle: with a constant extinction every collision decision is the same
+on both sides, so the cache state after every frame is bit-exact and the
+radiance agrees within FP32 rounding; with a varying transfer function the
+same random streams give the same paths except where a decision sits within
+rounding of its threshold."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_18001_gb300 import synthetic as S
+
+from _scenes import gpu_inr, ocam, oracle_inr, scene, sorted_pairs
+
+pytestmark = pytest.mark.gpu
+
+PT = dict(light_dir=(0.3, -1.0, -0.4), light=(3.0, 2.5, 2.0), ambient=(0.05, 0.07, 0.1), max_bounces=3)
+
+
+def _pt_pair():
+    from paper_2504_18001_gb300 import cinr
+    return cinr.make_pt_opts(**PT), O.pt_opts(**PT)
+
+
+@pytest.mark.parametrize("preload,lag", [(1, 1), (0, 1), (1, 2)])
+def test_cached_pt_constant_extinction_state_bit_exact(preload, lag):
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.INR_64
+    vol = (64, 64, 64)
+    table, w = scene(cfg)
+    inr = gpu_inr(cfg, table, w, vol=vol)
+    p = oracle_inr(cfg, table, w, vol=vol)
+    slots, n_req = (60, 30) if preload else (400, 100)
+    cache = cinr.Cache(inr, vol, pool_bytes=slots * 4000, brick=8, levels=3, n_req=n_req,
+                       preload=preload, lag=lag)
+    mo = O.march_opts(K=32, eps_T=0.0, seed=13)
+    oc = O.Cache(p, table, w, vol, 8, 3, slots, mo, n_req=n_req, preload=preload, lag=lag)
+    r = cinr.Renderer(40, 32, vol, K=32, eps_T=0.0, seed=13, miss_record_cap=1 << 20)
+    tf = S.tf_constant((0.9, 0.7, 0.5), 6.0)
+    gpt, opt = _pt_pair()
+    for f in range(4):
+        cam = S.orbit_camera(5 * f, 40, 32, distance=1.7)
+        img, st = r.render_pt(inr, cam, tf, gpt, cache=cache)
+        ref, rst = oc.render_pt(ocam(cam), tf.astype(np.float64), opt)
+        for k in ("samples", "hits", "fallback_hits", "true_misses", "bricks_requested",
+                  "bricks_decoded", "evictions"):
+            assert st[k] == rst[k], (f, k, st[k], rst[k])
+        for g, o in ((cinr.DUMP_PAGE_TABLE, O.DUMP_PT), (cinr.DUMP_STAMPS, O.DUMP_STAMP),
+                     (cinr.DUMP_OWNERS, O.DUMP_OWNER), (cinr.DUMP_RANK, O.DUMP_RANK),
+                     (cinr.DUMP_REQUESTS, O.DUMP_REQ), (cinr.DUMP_VICTIMS, O.DUMP_VICT)):
+            assert np.array_equal(cache.dump(g), oc.dump(o)), (f, g)
+        assert np.array_equal(sorted_pairs(r.misses()), sorted_pairs(oc.dump(O.DUMP_MISS)))
+        got = img.cpu().numpy()
+        assert np.abs(got - ref).max() < 1e-3 * max(1.0, np.abs(ref).max()), f
+        assert st["samples"] > 0 and got[..., 3].sum() > 0
+
+
+def test_uncached_pt_constant_extinction_matches_oracle():
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.INR_64
+    vol = (48, 40, 56)
+    table, w = scene(cfg)
+    inr = gpu_inr(cfg, table, w, vol=vol)
+    p = oracle_inr(cfg, table, w, vol=vol)
+    r = cinr.Renderer(24, 20, vol, K=32, eps_T=0.0, seed=3)
+    tf = S.tf_constant((0.8, 0.8, 0.6), 4.0)
+    gpt, opt = _pt_pair()
+    mo = O.march_opts(seed=3)
+    for f in range(1, 3):
+        cam = S.orbit_camera(11 * f, 24, 20)
+        img, st = r.render_pt(inr, cam, tf, gpt)
+        ref, rst = O.render_pt_direct(p, table, w, ocam(cam), vol, mo, tf.astype(np.float64), opt, f)
+        assert st["samples"] == rst["samples"] == st["inr_queries_direct"]
+        assert np.abs(img.cpu().numpy() - ref).max() < 1e-3
+
+
+def test_pt_varying_extinction_paths_agree_except_near_thresholds():
+    # same random streams: a path diverges only where u * sigma_bar sits within
+    # rounding of sigma(v); nearly every pixel agrees to FP32 rounding
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.INR_64
+    vol = (64, 64, 64)
+    table, w = scene(cfg)
+    inr = gpu_inr(cfg, table, w, vol=vol)
+    p = oracle_inr(cfg, table, w, vol=vol)
+    r = cinr.Renderer(32, 32, vol, K=32, eps_T=0.0, seed=21)
+    tf = S.tf_ramps(2)
+    gpt, opt = _pt_pair()
+    mo = O.march_opts(seed=21)
+    agree, total = 0, 0
+    for f in range(1, 4):
+        cam = S.orbit_camera(7 * f, 32, 32)
+        img, st = r.render_pt(inr, cam, tf, gpt)
+        ref, rst = O.render_pt_direct(p, table, w, ocam(cam), vol, mo, tf.astype(np.float64), opt, f)
+        d = np.abs(img.cpu().numpy() - ref).max(axis=2)
+        agree += int((d < 1e-3).sum())
+        total += d.size
+        assert abs(st["samples"] - rst["samples"]) <= 0.02 * rst["samples"]
+    assert agree >= 0.98 * total, (agree, total)
+
+
+def test_cached_pt_mixed_precision_converges_to_fp32():
+    # FP16 bricks + BF16 decode: the frame average over many frames stays
+    # close to the FP32 cached path tracer's (same streams, same cache policy)
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.INR_64
+    vol = (64, 64, 64)
+    table, w = scene(cfg)
+    tf = S.tf_ramps(2)
+    gpt, _ = _pt_pair()
+    means = []
+    for mlp, tab, sto in (("fp32", "fp32", "fp32"), ("bf16", "fp16", "fp16")):
+        inr = gpu_inr(cfg, table, w, vol=vol, mlp=mlp, tab=tab)
+        cache = cinr.Cache(inr, vol, pool_bytes=300 * 4000, brick=8, levels=3, n_req=200,
+                           storage=sto)
+        r = cinr.Renderer(32, 32, vol, K=32, eps_T=0.0, seed=5)
+        acc = 0.0
+        for f in range(24):
+            img, st = r.render_pt(inr, S.orbit_camera(0, 32, 32), tf, gpt, cache=cache)
+            if f >= 8:
+                acc = acc + img.cpu().numpy()
+        means.append(acc / 16)
+    diff = np.abs(means[0] - means[1])
+    assert diff[..., :3].mean() < 0.02 * max(1e-3, means[0][..., :3].mean()) + 2e-3
