@@ -324,12 +324,22 @@ __device__ __forceinline__ void grid_cell(float x, int N, int& i, float& w) {
   w = f_sub(xl, (float)ii);
 }
 
+template <bool F16>
+__device__ __forceinline__ float2 load_entry_t(const void* table, uint32_t i) {
+  if (F16) return __half22float2(__ldg(reinterpret_cast<const __half2*>(table) + i));
+  return __ldg(reinterpret_cast<const float2*>(table) + i);
+}
+
 // Features of one point (levels concatenated, 2 per level): trilinear blend
-// of the 8 vertex entries of each level (Sec. 3, Fig. 2).
-template <int L>
-__device__ __forceinline__ void encode_point(const InrDev& q, float x, float y, float z,
-                                             float* feat) {
-  const uint32_t T = 1u << q.log2T;
+// of the 8 vertex entries of each level (Sec. 3, Fig. 2).  The per-axis
+// parts of the vertex index are formed once per level (dense: ix, iy (N+1),
+// iz (N+1)^2 summed; hashed: ix, iy p2, iz p3 xor-ed, the +1 vertex by adding
+// the row stride or the prime), the x-y weight products once per pair; the
+// products, the corner order and the accumulation are those of the plain
+// formula, so the features are unchanged bit for bit.
+template <int L, bool F16>
+__device__ __forceinline__ void encode_point_t(const InrDev& q, float x, float y, float z, float* feat) {
+  const uint32_t T = 1u << q.log2T, Tm = T - 1u;
 #pragma unroll
   for (int l = 0; l < L; ++l) {
     const int N = q.res[l];
@@ -340,20 +350,33 @@ __device__ __forceinline__ void encode_point(const InrDev& q, float x, float y, 
     grid_cell(z, N, iz, wz);
     const bool dense = (q.dense_mask >> l) & 1u;
     const uint32_t n1 = (uint32_t)N + 1u;
-    const uint32_t base = (uint32_t)l * T;
+    const uint32_t sy = dense ? n1 : 2654435761u, sz = dense ? n1 * n1 : 805459861u;
+    const uint32_t ax[2] = {(uint32_t)ix, (uint32_t)ix + 1u};
+    const uint32_t ay0 = (uint32_t)iy * sy, az0 = (uint32_t)iz * sz;
+    const uint32_t ay[2] = {ay0, ay0 + sy}, az[2] = {az0, az0 + sz};
+    const float wxs[2] = {1.0f - wx, wx}, wys[2] = {1.0f - wy, wy}, wzs[2] = {1.0f - wz, wz};
+    const void* table = reinterpret_cast<const char*>(q.table) + (size_t)l * T * (F16 ? 4 : 8);
     float f0 = 0.0f, f1 = 0.0f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      const uint32_t cx = ix + (c & 1), cy = iy + ((c >> 1) & 1), cz = iz + ((c >> 2) & 1);
-      const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) *
-                      ((c & 4) ? wz : 1.0f - wz);
-      const float2 e = load_entry(q.table, q.table_prec, base + vertex_index(dense, n1, T, cx, cy, cz));
+      const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
+      const uint32_t idx = dense ? ax[bx] + ay[by] + az[bz] : ((ax[bx] ^ ay[by] ^ az[bz]) & Tm);
+      const float w = wxs[bx] * wys[by] * wzs[bz];
+      const float2 e = load_entry_t<F16>(table, idx);
       f0 = fmaf(w, e.x, f0);
       f1 = fmaf(w, e.y, f1);
     }
     feat[2 * l] = f0;
     feat[2 * l + 1] = f1;
   }
+}
+
+template <int L>
+__device__ __forceinline__ void encode_point(const InrDev& q, float x, float y, float z, float* feat) {
+  if (q.table_prec == CINR_PREC_FP16)
+    encode_point_t<L, true>(q, x, y, z, feat);
+  else
+    encode_point_t<L, false>(q, x, y, z, feat);
 }
 
 // FP32 SIMT MLP (in -> H -> H -> 1, ReLU, no biases); weights in shared
