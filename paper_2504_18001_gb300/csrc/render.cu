@@ -420,9 +420,11 @@ __device__ __forceinline__ float pool_ld(const void* pool, size_t i) {
   return __ldg(reinterpret_cast<const float*>(pool) + i);
 }
 
-// MACRO: macro-cell skipping compiled in (a separate instantiation keeps the
-// plain loop free of the test).
-template <int IN, int H, bool F16POOL, bool MACRO>
+// MISS: true misses possible (a cache without the coarsest-LoD preload).
+// With the preload every fallback walk ends at a mapped brick, and the
+// instantiation without the (out-of-line) inference call keeps the marching
+// loop free of the register spills that the call's convention forces.
+template <int IN, int H, bool F16POOL, bool MISS>
 __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __grid_constant__ FrameParams P) {
   __shared__ float4 s_tf[256];
   __shared__ LevelGeo s_geo[kMaxLod];
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
         pv1 = f_mul(x[1], volf[1]);
         pv2 = f_mul(x[2], volf[2]);
         // transparent macro cell (Sec. 5.2): alpha = 0, nothing to look up
-        take = !MACRO || !macro_skips(P.mac, pv0, pv1, pv2);
+        take = !macro_skips(P.mac, pv0, pv1, pv2);
         if (!take) ++n_skip;
       }
       if (take) {
@@ -561,8 +563,8 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
         const unsigned peers = __match_any_sync(hm, hit_slot);
         if (lane == __ffs(peers) - 1 && atomicExch(c.stamp + hit_slot, P.frame) != P.frame) ++n_slot;
       }
-      const unsigned mm = __ballot_sync(kFull, miss);
-      if (mm) {
+      const unsigned mm = MISS ? __ballot_sync(kFull, miss) : 0u;
+      if (MISS && mm) {
         if (miss) v = infer_miss<IN, H>(P.inr, x[0], x[1], x[2]);
         if (P.miss_rec) {
           uint32_t base = 0;
@@ -616,9 +618,9 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
   }
 }
 
-template <int IN, int H, bool F16POOL, bool MACRO>
+template <int IN, int H, bool F16POOL, bool MISS>
 int launch_march_cached(const FrameParams& P, cudaStream_t s) {
-  auto k = march_cached_kernel<IN, H, F16POOL, MACRO>;
+  auto k = march_cached_kernel<IN, H, F16POOL, MISS>;
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
@@ -629,19 +631,19 @@ int launch_march_cached(const FrameParams& P, cudaStream_t s) {
   return CINR_OK;
 }
 
-template <bool F16POOL, bool MACRO>
+template <bool F16POOL, bool MISS>
 int launch_march_cached_pool(const FrameParams& P, cudaStream_t s) {
   switch (shape_of(P.inr.IN, P.inr.H)) {
-    case Shape::S16x32: return launch_march_cached<16, 32, F16POOL, MACRO>(P, s);
-    case Shape::S32x64: return launch_march_cached<32, 64, F16POOL, MACRO>(P, s);
-    case Shape::S48x64: return launch_march_cached<48, 64, F16POOL, MACRO>(P, s);
+    case Shape::S16x32: return launch_march_cached<16, 32, F16POOL, MISS>(P, s);
+    case Shape::S32x64: return launch_march_cached<32, 64, F16POOL, MISS>(P, s);
+    case Shape::S48x64: return launch_march_cached<48, 64, F16POOL, MISS>(P, s);
     default: return set_error(CINR_ERR_ARG, "unsupported shape");
   }
 }
 
-int launch_march_cached_shape(const FrameParams& P, cudaStream_t s) {
+int launch_march_cached_shape(const FrameParams& P, bool miss, cudaStream_t s) {
   const bool f16 = P.cache.pool_prec == CINR_PREC_FP16;
-  if (P.mac.skip)
+  if (miss)
     return f16 ? launch_march_cached_pool<true, true>(P, s) : launch_march_cached_pool<false, true>(P, s);
   return f16 ? launch_march_cached_pool<true, false>(P, s) : launch_march_cached_pool<false, false>(P, s);
 }
@@ -744,7 +746,7 @@ struct PtCounts {
 // cache, by direct inference.  Atomics are per lane: the rank update
 // max(r, T_f) + 1 clamped at T_f + 1000 and the stamp reach the same final
 // state in any order.
-template <int IN, int H, bool CACHED, bool F16POOL>
+template <int IN, int H, bool CACHED, bool F16POOL, bool MISS>
 __device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const float x[3], float dist,
                           uint32_t rseed, uint32_t k, uint32_t pixel, PtCounts& n) {
   ++n.samp;
@@ -804,6 +806,7 @@ __device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const flo
     }
   }
   ++n.miss;
+  if (!MISS) return 0.0f;  // unreachable: the preloaded coarsest LoD is always mapped
   if (P.miss_rec) {
     const uint32_t at = atomicAdd(P.miss_count, 1u);
     if (at < P.miss_cap) {
@@ -814,7 +817,9 @@ __device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const flo
   return infer_miss<IN, H>(P.inr, x[0], x[1], x[2]);
 }
 
-template <int IN, int H, bool CACHED, bool F16POOL>
+// MISS: lookups that can end in direct inference (no cache, or a cache
+// without the coarsest-LoD preload).
+template <int IN, int H, bool CACHED, bool F16POOL, bool MISS>
 __global__ void __launch_bounds__(kFrameThreads, 6) pt_kernel(const __grid_constant__ FrameParams P) {
   __shared__ float4 s_tf[256];
   __shared__ LevelGeo s_geo[kMaxLod];
@@ -865,7 +870,7 @@ __global__ void __launch_bounds__(kFrameThreads, 6) pt_kernel(const __grid_const
           if (!(t < t1)) break;
           float x[3], dist;
           pt_point(cam, o, d, t, p, x, dist);
-          v = pt_value<IN, H, CACHED, F16POOL>(P, s_geo, x, dist, rseed, k, pixel, n);
+          v = pt_value<IN, H, CACHED, F16POOL, MISS>(P, s_geo, x, dist, rseed, k, pixel, n);
           ++k;
           const float sig = tf_lookup(s_tf, v).w;
           if (pt_uniform(key, j++) * P.pt_sbar < sig) {
@@ -892,7 +897,7 @@ __global__ void __launch_bounds__(kFrameThreads, 6) pt_kernel(const __grid_const
           if (!(ts < ts1)) break;
           float pq[3], x[3], dist;
           pt_point(cam, p, P.pt_ls, ts, pq, x, dist);
-          const float v2 = pt_value<IN, H, CACHED, F16POOL>(P, s_geo, x, dist, rseed, k, pixel, n);
+          const float v2 = pt_value<IN, H, CACHED, F16POOL, MISS>(P, s_geo, x, dist, rseed, k, pixel, n);
           ++k;
           Tr *= 1.0f - tf_lookup(s_tf, v2).w * P.pt_inv;
         }
@@ -928,9 +933,9 @@ __global__ void __launch_bounds__(kFrameThreads, 6) pt_kernel(const __grid_const
   }
 }
 
-template <int IN, int H, bool CACHED, bool F16POOL>
+template <int IN, int H, bool CACHED, bool F16POOL, bool MISS>
 int launch_pt(const FrameParams& P, cudaStream_t s) {
-  auto k = pt_kernel<IN, H, CACHED, F16POOL>;
+  auto k = pt_kernel<IN, H, CACHED, F16POOL, MISS>;
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
@@ -941,20 +946,21 @@ int launch_pt(const FrameParams& P, cudaStream_t s) {
   return CINR_OK;
 }
 
-template <bool CACHED, bool F16POOL>
+template <bool CACHED, bool F16POOL, bool MISS>
 int launch_pt_pool(const FrameParams& P, cudaStream_t s) {
   switch (shape_of(P.inr.IN, P.inr.H)) {
-    case Shape::S16x32: return launch_pt<16, 32, CACHED, F16POOL>(P, s);
-    case Shape::S32x64: return launch_pt<32, 64, CACHED, F16POOL>(P, s);
-    case Shape::S48x64: return launch_pt<48, 64, CACHED, F16POOL>(P, s);
+    case Shape::S16x32: return launch_pt<16, 32, CACHED, F16POOL, MISS>(P, s);
+    case Shape::S32x64: return launch_pt<32, 64, CACHED, F16POOL, MISS>(P, s);
+    case Shape::S48x64: return launch_pt<48, 64, CACHED, F16POOL, MISS>(P, s);
     default: return set_error(CINR_ERR_ARG, "unsupported shape");
   }
 }
 
-int launch_pt_shape(const FrameParams& P, bool cached, cudaStream_t s) {
-  if (!cached) return launch_pt_pool<false, false>(P, s);
-  return P.cache.pool_prec == CINR_PREC_FP16 ? launch_pt_pool<true, true>(P, s)
-                                             : launch_pt_pool<true, false>(P, s);
+int launch_pt_shape(const FrameParams& P, bool cached, bool miss, cudaStream_t s) {
+  if (!cached) return launch_pt_pool<false, false, true>(P, s);
+  const bool f16 = P.cache.pool_prec == CINR_PREC_FP16;
+  if (miss) return f16 ? launch_pt_pool<true, true, true>(P, s) : launch_pt_pool<true, false, true>(P, s);
+  return f16 ? launch_pt_pool<true, true, false>(P, s) : launch_pt_pool<true, false, false>(P, s);
 }
 
 // ----------------------------------------------------------- host side
@@ -1226,13 +1232,13 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
     if (!graph) CINR_CK(cudaEventRecord(r->ev[0], q));
     int ee;
     if (pt)
-      ee = launch_pt_shape(P, cache != nullptr, q);
+      ee = launch_pt_shape(P, cache != nullptr, cache && !cache->o.preload, q);
     else if (!cache)
       ee = launch_frame_shape<false>(P, inr->p.mlp_precision, q);
     else if (r->o.ray_layout == 1)
       ee = launch_frame_shape<true>(P, inr->p.mlp_precision, q);
     else
-      ee = launch_march_cached_shape(P, q);
+      ee = launch_march_cached_shape(P, !cache->o.preload, q);
     if (ee) return ee;
     CINR_CK(cudaEventRecordWithFlags(r->ev[1], q, graph ? cudaEventRecordExternal : cudaEventRecordDefault));
     if (cache) {
