@@ -346,7 +346,7 @@ int orc_sample(const orc_camera* cam, const int vol[3], const float o[3],
   box_extent(vol, e, h);
   for (int c = 0; c < 3; ++c) {
     float pc = o[c] + tm * d[c];
-    x[c] = clamp01((pc + h[c]) / e[c]);
+    x[c] = clamp01((pc + h[c]) * (1.0f / e[c]));
   }
   return 1;
 }
@@ -413,7 +413,7 @@ int orc_sample_sched(const orc_camera* cam, const int vol[3],
   box_extent(vol, e, h);
   for (int c = 0; c < 3; ++c) {
     float pc = o[c] + tm * d[c];
-    x[c] = clamp01((pc + h[c]) / e[c]);
+    x[c] = clamp01((pc + h[c]) * (1.0f / e[c]));
   }
   return 1;
 }
@@ -1392,7 +1392,7 @@ static void pt_point(const orc_camera* cam, const float e[3], const float h[3],
   for (int q = 0; q < 3; ++q) {
     p[q] = o[q] + t * d[q];
     float num = p[q] + h[q];
-    x[q] = clamp01(e[q] == 1.0f ? num : num / e[q]);
+    x[q] = clamp01(num * (1.0f / e[q]));
   }
   float dx = p[0] - cam->eye[0], dy = p[1] - cam->eye[1], dz = p[2] - cam->eye[2];
   float s2 = dx * dx + dy * dy;

@@ -69,6 +69,7 @@ struct CamDev {
   float ax, ay;        // tan(fov/2) * aspect, tan(fov/2)
   int W, H;
   float e[3], h[3];    // box extent and half extent
+  float inv_e[3];      // 1 / e (binary32): normalised coordinate = (p + h) * inv_e
   float dt;            // step in world units
   float lodc;          // footprint constant: t * lodc = pixel footprint in LoD-0 voxels
   float lod_scale;
@@ -159,7 +160,7 @@ __device__ __forceinline__ bool sample_at(const CamDev& c, const float d[3], flo
     float p = f_add(c.o[q], f_mul(tm, d[q]));
     const float num = f_add(p, c.h[q]);
     // division by an extent of exactly 1 (the longest axis) is the identity
-    x[q] = clamp01(c.e[q] == 1.0f ? num : f_div(num, c.e[q]));
+    x[q] = clamp01(f_mul(num, c.inv_e[q]));
   }
   return true;
 }
@@ -200,7 +201,7 @@ __device__ __forceinline__ bool sample_in(const CamDev& c, const float d[3], flo
   for (int q = 0; q < 3; ++q) {
     const float p = f_add(c.o[q], f_mul(tm, d[q]));
     const float num = f_add(p, c.h[q]);
-    x[q] = clamp01(c.e[q] == 1.0f ? num : f_div(num, c.e[q]));
+    x[q] = clamp01(f_mul(num, c.inv_e[q]));
   }
   return true;
 }

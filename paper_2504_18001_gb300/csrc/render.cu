@@ -36,6 +36,7 @@ struct cinr_renderer_s {
   int device;
   cudaEvent_t ev[3];             // frame kernel start/end, cache update end
   cudaStream_t cap = nullptr;    // capture stream of the per-frame CUDA graph
+  cudaStream_t copy = nullptr;   // image read-back of cinr_render_frame_host
   cudaGraphExec_t exec = nullptr;
   cinr_macro_s* macro = nullptr; // attached macro cells (Sec. 5.2)
 };
@@ -414,8 +415,8 @@ struct LevelGeo {
   float scale;                // 2^-level, exact
 };
 
-template <bool F16POOL>
-__device__ __forceinline__ float pool_ld(const void* pool, size_t i) {
+template <bool F16POOL, class I>
+__device__ __forceinline__ float pool_ld(const void* pool, I i) {
   if (F16POOL) return __half2float(__ldg(reinterpret_cast<const __half*>(pool) + i));
   return __ldg(reinterpret_cast<const float*>(pool) + i);
 }
@@ -522,12 +523,13 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           const int i0 = (int)floorf(q0), i1 = (int)floorf(q1), i2 = (int)floorf(q2);
           const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
           const int l0 = i0 - (b0 * B - 1), l1 = i1 - (b1 * B - 1), l2 = i2 - (b2 * B - 1);
-          const size_t base = (size_t)hit_slot * S3 + (size_t)((l2 * S + l1) * S + l0);
-          const float v000 = pool_ld<F16POOL>(pool, base), v100 = pool_ld<F16POOL>(pool, base + 1);
-          const float v010 = pool_ld<F16POOL>(pool, base + S), v110 = pool_ld<F16POOL>(pool, base + S + 1);
-          const float v001 = pool_ld<F16POOL>(pool, base + S * S), v101 = pool_ld<F16POOL>(pool, base + S * S + 1);
-          const float v011 = pool_ld<F16POOL>(pool, base + S * S + S),
-                      v111 = pool_ld<F16POOL>(pool, base + S * S + S + 1);
+          // the slot's base pointer once, then 32-bit offsets inside the brick
+          const void* bp = static_cast<const char*>(pool) + (size_t)hit_slot * S3 * (F16POOL ? 2 : 4);
+          const int o = (l2 * S + l1) * S + l0, SS = S * S;
+          const float v000 = pool_ld<F16POOL>(bp, o), v100 = pool_ld<F16POOL>(bp, o + 1);
+          const float v010 = pool_ld<F16POOL>(bp, o + S), v110 = pool_ld<F16POOL>(bp, o + S + 1);
+          const float v001 = pool_ld<F16POOL>(bp, o + SS), v101 = pool_ld<F16POOL>(bp, o + SS + 1);
+          const float v011 = pool_ld<F16POOL>(bp, o + SS + S), v111 = pool_ld<F16POOL>(bp, o + SS + S + 1);
           const float x00 = fmaf(f0, v100 - v000, v000), x10 = fmaf(f0, v110 - v010, v010);
           const float x01 = fmaf(f0, v101 - v001, v001), x11 = fmaf(f0, v111 - v011, v011);
           const float y0 = fmaf(f1, x10 - x00, x00), y1 = fmaf(f1, x11 - x01, x01);
@@ -730,7 +732,7 @@ __device__ __forceinline__ void pt_point(const CamDev& c, const float o[3], cons
   for (int q = 0; q < 3; ++q) {
     p[q] = f_add(o[q], f_mul(t, d[q]));
     const float num = f_add(p[q], c.h[q]);
-    x[q] = clamp01(c.e[q] == 1.0f ? num : f_div(num, c.e[q]));
+    x[q] = clamp01(f_mul(num, c.inv_e[q]));
   }
   const float dx = f_sub(p[0], c.o[0]), dy = f_sub(p[1], c.o[1]), dz = f_sub(p[2], c.o[2]);
   dist = __fsqrt_rn(f_add(f_add(f_mul(dx, dx), f_mul(dy, dy)), f_mul(dz, dz)));
@@ -1000,6 +1002,7 @@ void camera_consts(const cinr_camera* cam, const cinr_march_opts* o, CamDev* c) 
     c->o[a] = cam->eye[a];
     c->e[a] = (float)o->dims[a] / mf;
     c->h[a] = c->e[a] * 0.5f;
+    c->inv_e[a] = 1.0f / c->e[a];
     c->vol[a] = o->dims[a];
   }
   c->dt = cam->step_voxels / mf;
@@ -1149,9 +1152,12 @@ int launch_as_graph(cinr_renderer_s* r, F&& enqueue, cudaStream_t s) {
   return CINR_OK;
 }
 
+// host_img != nullptr: the image is also copied to host memory, on a second
+// stream that starts when the marching kernel ends (overlapping the cache
+// update), and the call returns once both streams are done.
 int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_camera* cam,
            const cinr_tf* tf, float4* out, cinr_frame_stats* stats, cudaStream_t s,
-           const cinr_pt_opts* pt = nullptr) {
+           const cinr_pt_opts* pt = nullptr, float* host_img = nullptr) {
   if (!r || !inr || !cam || !tf) return set_error(CINR_ERR_ARG, "NULL argument");
   if (cam->width != r->W || cam->height != r->H)
     return set_error(CINR_ERR_ARG, "camera is %dx%d, renderer %dx%d", cam->width, cam->height, r->W, r->H);
@@ -1257,11 +1263,18 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
     e = enqueue(s);
   }
   if (e) return e;
+  if (host_img) {
+    if (!r->copy) CINR_CK(cudaStreamCreateWithFlags(&r->copy, cudaStreamNonBlocking));
+    // (a graph's frame: after the whole graph, whose end event is on `s`)
+    CINR_CK(cudaStreamWaitEvent(r->copy, graph ? r->ev[2] : r->ev[1], 0));
+    CINR_CK(cudaMemcpyAsync(host_img, out, (size_t)r->W * r->H * 16, cudaMemcpyDeviceToHost, r->copy));
+  }
   unsigned long long h[ST_COUNT];
   uint32_t cnt[3] = {0, 0, 0};  // ray counter, miss-record count, device error word
   CINR_CK(cudaMemcpyAsync(h, r->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
   CINR_CK(cudaMemcpyAsync(cnt, r->counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
   CINR_CK(cudaStreamSynchronize(s));
+  if (host_img) CINR_CK(cudaStreamSynchronize(r->copy));
   const uint32_t rec = cnt[1];
   if (cnt[2]) return set_error(CINR_ERR_TIMEOUT, "a bounded device-side wait gave up in the frame kernel");
   if (stats) {
@@ -1333,6 +1346,7 @@ extern "C" int cinr_destroy_renderer(cinr_renderer_t r) {
     for (int i = 0; i < 3; ++i) cudaEventDestroy(r->ev[i]);
     if (r->exec) cudaGraphExecDestroy(r->exec);
     if (r->cap) cudaStreamDestroy(r->cap);
+    if (r->copy) cudaStreamDestroy(r->copy);
   }
   delete r;
   return CINR_OK;
@@ -1358,14 +1372,8 @@ extern "C" int cinr_render_frame_host(cinr_renderer_t r, cinr_cache_t cache, cin
                                       const cinr_camera* cam, const cinr_tf* tf, float* out_rgba_host,
                                       cinr_frame_stats* stats, cinr_stream_t stream) {
   if (!r || !out_rgba_host) return set_error(CINR_ERR_ARG, "NULL argument");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cinr_frame_stats st;
-  int e = render(r, cache, inr, cam, tf, r->image, &st, s);
-  if (e) return e;
-  CINR_CK(cudaMemcpyAsync(out_rgba_host, r->image, (size_t)r->W * r->H * 16, cudaMemcpyDeviceToHost, s));
-  CINR_CK(cudaStreamSynchronize(s));
-  if (stats) *stats = st;
-  return CINR_OK;
+  return render(r, cache, inr, cam, tf, r->image, stats, static_cast<cudaStream_t>(stream), nullptr,
+                out_rgba_host);
 }
 
 extern "C" int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap, size_t* count,
