@@ -85,7 +85,8 @@ class Stats(C.Structure):
 
 class CacheOpts(C.Structure):
     _fields_ = [("brick", C.c_int), ("levels", C.c_int), ("n_slots", C.c_long),
-                ("n_req", C.c_int), ("ranking", C.c_int), ("preload", C.c_int), ("lag", C.c_int)]
+                ("n_req", C.c_int), ("ranking", C.c_int), ("preload", C.c_int), ("lag", C.c_int),
+                ("page", C.c_int), ("n_pages", C.c_long)]
 
 
 _P = C.POINTER
@@ -459,20 +460,21 @@ def render_field(field, cam: Camera, vol, mo: MarchOpts, tf, window=None):
 
 
 DUMP_PT, DUMP_STAMP, DUMP_OWNER, DUMP_RANK, DUMP_REQ, DUMP_VICT, DUMP_MISS, DUMP_PINNED = range(8)
+DUMP_PAGE_DIR, DUMP_PAGES, DUMP_PAGE_KEY, DUMP_PAGE_REF = range(8, 12)
 
 
 class Cache:
     """Oracle brick cache (owns its own host memory)."""
 
     def __init__(self, p: InrParams, table, w, vol, brick, levels, n_slots, mo: MarchOpts,
-                 n_req=40, ranking=1, preload=1, lag=1):
+                 n_req=40, ranking=1, preload=1, lag=1, page=0, n_pages=0):
         self._t, tp = _d(table)
         self._w, wp = _d(w)
         self._v, vp = _i3(vol)
         self.p = p
         self.mo = mo
         self.co = CacheOpts(int(brick), int(levels), int(n_slots), int(n_req), int(ranking),
-                            int(preload), int(lag))
+                            int(preload), int(lag), int(page), int(n_pages))
         h = lib().orc_cache_create(C.byref(p), tp, wp, vp, C.byref(self.co), C.byref(mo))
         if not h:
             raise ValueError("orc_cache_create failed (levels or pool too small for preload)")

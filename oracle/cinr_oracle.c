@@ -758,6 +758,14 @@ struct orc_cache {
   uint32_t* last_vict;
   long n_last_vict;
   long n_pending; /* lag 2: last_req/last_vict pairs decoded, not yet mapped */
+  /* virtualised page tables (co.page = P > 0) */
+  int pg[16][3];       /* pages per axis and LoD */
+  long pd_off[17];     /* first page key of each LoD */
+  uint32_t* pd;        /* page directory: Mapped | page slot */
+  uint32_t* pages;     /* page pool: n_pages * P^3 entries */
+  uint32_t* page_key;  /* page key held by each page slot, NO_OWNER if free */
+  uint32_t* page_ref;  /* mapped bricks in each page slot */
+  uint32_t* pt_view;   /* scratch of orc_cache_dump(0) in paged mode */
   uint32_t* miss;
   long n_miss, cap_miss;
 };
@@ -976,6 +984,103 @@ double orc_brick_sample(const orc_inr_params* p, const double* table,
   return v;
 }
 
+/* ---- page-table access (Sec. 4.3.1) ----------------------------------
+ * Flat: one u32 entry per brick.  Paged (co.page = P): per LoD a page
+ * directory over pages of P^3 bricks; a resident page lives in one of
+ * n_pages page slots and holds the bricks' entries; a brick whose page is
+ * not resident reads as Unmapped.  READING: the paper gives the structure,
+ * not its management.  Pages are allocated when a brick in them is mapped
+ * and freed when their last mapped brick is unmapped; at the end of a frame
+ * all unmaps come first, then the pages left empty are freed, then the
+ * pages the frame's mappings need are allocated -- in ascending page key,
+ * into the free page slots in ascending order -- and then the bricks are
+ * mapped; a brick whose page finds no free slot is dropped for the frame. */
+static long page_index(const orc_cache* c, uint32_t key, long* local) {
+  int l = 0;
+  while (l + 1 < c->co.levels && (long)key >= c->off[l + 1]) ++l;
+  long loc = (long)key - c->off[l];
+  long bx = loc % c->nb[l][0];
+  long by = (loc / c->nb[l][0]) % c->nb[l][1];
+  long bz = loc / ((long)c->nb[l][0] * c->nb[l][1]);
+  long P = c->co.page;
+  *local = (bx % P) + P * ((by % P) + P * (bz % P));
+  return c->pd_off[l] + bx / P + (long)c->pg[l][0] * (by / P + (long)c->pg[l][1] * (bz / P));
+}
+
+static uint32_t pt_get(const orc_cache* c, uint32_t key) {
+  if (!c->co.page) return c->pt[key];
+  long local, pk = page_index(c, key, &local);
+  uint32_t e = c->pd[pk];
+  if (!(e & PT_MAPPED)) return 0u;
+  long P3 = (long)c->co.page * c->co.page * c->co.page;
+  return c->pages[(long)(e & ~PT_MAPPED) * P3 + local];
+}
+
+static void pt_unmap(orc_cache* c, uint32_t key) {
+  if (!c->co.page) {
+    c->pt[key] = 0u;
+    return;
+  }
+  long local, pk = page_index(c, key, &local);
+  uint32_t ps = c->pd[pk] & ~PT_MAPPED;
+  long P3 = (long)c->co.page * c->co.page * c->co.page;
+  c->pages[(long)ps * P3 + local] = 0u;
+  c->page_ref[ps]--;
+}
+
+/* Maps key -> slot; returns 0 when its page is not resident (paged). */
+static int pt_map(orc_cache* c, uint32_t key, uint32_t slot) {
+  if (!c->co.page) {
+    c->pt[key] = PT_MAPPED | slot;
+    return 1;
+  }
+  long local, pk = page_index(c, key, &local);
+  uint32_t e = c->pd[pk];
+  if (!(e & PT_MAPPED)) return 0;
+  uint32_t ps = e & ~PT_MAPPED;
+  long P3 = (long)c->co.page * c->co.page * c->co.page;
+  c->pages[(long)ps * P3 + local] = PT_MAPPED | slot;
+  c->page_ref[ps]++;
+  return 1;
+}
+
+static void pages_free_empty(orc_cache* c) {
+  if (!c->co.page) return;
+  for (long ps = 0; ps < c->co.n_pages; ++ps)
+    if (c->page_key[ps] != NO_OWNER && c->page_ref[ps] == 0) {
+      c->pd[c->page_key[ps]] = 0u;
+      c->page_key[ps] = NO_OWNER;
+    }
+}
+
+static int cmp_u32(const void* x, const void* y) {
+  uint32_t a = *(const uint32_t*)x, b = *(const uint32_t*)y;
+  return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* Allocates the non-resident pages of keys[0..n): ascending page keys into
+ * ascending free page slots. */
+static void pages_alloc(orc_cache* c, const uint32_t* keys, long n) {
+  if (!c->co.page || n == 0) return;
+  uint32_t* need = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n);
+  long nn = 0;
+  for (long i = 0; i < n; ++i) {
+    long local, pk = page_index(c, keys[i], &local);
+    if (!(c->pd[pk] & PT_MAPPED)) need[nn++] = (uint32_t)pk;
+  }
+  qsort(need, (size_t)nn, sizeof(uint32_t), cmp_u32);
+  long ps = 0;
+  for (long i = 0; i < nn; ++i) {
+    if (i > 0 && need[i] == need[i - 1]) continue;
+    while (ps < c->co.n_pages && c->page_key[ps] != NO_OWNER) ++ps;
+    if (ps == c->co.n_pages) break;
+    c->pd[need[i]] = PT_MAPPED | (uint32_t)ps;
+    c->page_key[ps] = need[i];
+    c->page_ref[ps] = 0;
+  }
+  free(need);
+}
+
 static void decode_into(orc_cache* c, uint32_t key, long slot) {
   int l = 0;
   while (l + 1 <= c->co.levels - 1 && (long)key >= c->off[l + 1]) ++l;
@@ -1009,6 +1114,23 @@ orc_cache* orc_cache_create(const orc_inr_params* p, const double* table,
         c->off[l] + (long)c->nb[l][0] * c->nb[l][1] * c->nb[l][2];
   }
   c->n_bricks = c->off[co->levels];
+  if (co->page < 0 || (co->page > 0 && co->n_pages < 1)) {
+    free(c);
+    return NULL;
+  }
+  if (co->page > 0) {
+    long P = co->page;
+    c->pd_off[0] = 0;
+    for (int l = 0; l < co->levels; ++l) {
+      for (int a = 0; a < 3; ++a) c->pg[l][a] = (int)((c->nb[l][a] + P - 1) / P);
+      c->pd_off[l + 1] = c->pd_off[l] + (long)c->pg[l][0] * c->pg[l][1] * c->pg[l][2];
+    }
+    c->pd = (uint32_t*)calloc((size_t)c->pd_off[co->levels], 4);
+    c->pages = (uint32_t*)calloc((size_t)(co->n_pages * P * P * P), 4);
+    c->page_key = (uint32_t*)malloc((size_t)co->n_pages * 4);
+    c->page_ref = (uint32_t*)calloc((size_t)co->n_pages, 4);
+    for (long i = 0; i < co->n_pages; ++i) c->page_key[i] = NO_OWNER;
+  }
   c->pt = (uint32_t*)calloc((size_t)c->n_bricks, 4);
   c->rank = (uint32_t*)calloc((size_t)c->n_bricks, 4);
   c->stamp = (uint32_t*)calloc((size_t)co->n_slots, 4);
@@ -1031,19 +1153,32 @@ orc_cache* orc_cache_create(const orc_inr_params* p, const double* table,
       orc_cache_destroy(c);
       return NULL;
     }
+    uint32_t* keys = (uint32_t*)calloc((size_t)nc + 1, sizeof(uint32_t));
+    for (long i = 0; i < nc; ++i) keys[i] = (uint32_t)(c->off[L] + i);
+    pages_alloc(c, keys, nc);
     for (long i = 0; i < nc; ++i) {
-      uint32_t key = (uint32_t)(c->off[L] + i);
+      uint32_t key = keys[i];
       decode_into(c, key, i);
-      c->pt[key] = PT_MAPPED | (uint32_t)i;
+      if (!pt_map(c, key, (uint32_t)i)) {
+        free(keys);
+        orc_cache_destroy(c);
+        return NULL; /* the page pool cannot hold the coarsest LoD */
+      }
       c->owner[i] = key;
       c->pinned[i] = 1;
     }
+    free(keys);
   }
   return c;
 }
 
 void orc_cache_destroy(orc_cache* c) {
   if (!c) return;
+  free(c->pd);
+  free(c->pages);
+  free(c->page_key);
+  free(c->page_ref);
+  free(c->pt_view);
   free(c->pt);
   free(c->rank);
   free(c->stamp);
@@ -1099,7 +1234,7 @@ static double cache_lookup(orc_cache* c, const orc_camera* cam, const float x[3]
     brick_of(s, B, c->nb[lev], b);
     long key = c->off[lev] +
                b[0] + (long)c->nb[lev][0] * (b[1] + (long)c->nb[lev][1] * b[2]);
-    uint32_t e = c->pt[key];
+    uint32_t e = pt_get(c, (uint32_t)key);
     if (!(e & PT_MAPPED)) {
       if (lev == l) {
         uint32_t r = c->rank[key];
@@ -1137,9 +1272,10 @@ static void cache_end_frame(orc_cache* c, uint32_t Tf, uint64_t f, orc_stats* st
    * decoded while this frame rendered; they are mapped now, before this
    * frame's selection.  READING: a fixed lag of two frames keeps the state
    * deterministic. ---- */
+  pages_alloc(c, c->last_req, c->n_pending);
   for (long i = 0; i < c->n_pending; ++i) {
     uint32_t slot = c->last_vict[i], key = c->last_req[i];
-    c->pt[key] = PT_MAPPED | slot;
+    if (!pt_map(c, key, slot)) continue; /* no page slot: dropped */
     c->owner[slot] = key;
     c->stamp[slot] = (uint32_t)f;
   }
@@ -1154,7 +1290,7 @@ static void cache_end_frame(orc_cache* c, uint32_t Tf, uint64_t f, orc_stats* st
   long nc = 0;
   for (long key = 0; key < nb; ++key) {
     uint32_t r = c->rank[key];
-    if (r > Tf && !(c->pt[key] & PT_MAPPED)) {
+    if (r > Tf && !(pt_get(c, (uint32_t)key) & PT_MAPPED)) {
       uint64_t score = (uint64_t)(r - Tf);
       uint64_t sk = c->co.ranking ? ((1000u - score) << 32) | (uint64_t)key
                                   : (uint64_t)key;
@@ -1191,21 +1327,26 @@ static void cache_end_frame(orc_cache* c, uint32_t Tf, uint64_t f, orc_stats* st
    * Fig. 1) ---- */
   for (long i = 0; i < m; ++i) {
     uint32_t slot = c->last_vict[i];
-    uint32_t key = c->last_req[i];
     if (c->owner[slot] != NO_OWNER) {
-      c->pt[c->owner[slot]] = 0u;
+      pt_unmap(c, c->owner[slot]);
       st->evictions++;
     }
-    decode_into(c, key, (long)slot);
-    if (c->co.lag == 1) {
-      c->pt[key] = PT_MAPPED | slot;
+    /* lag 2: in flight, unmapped until the next frame ends */
+    c->owner[slot] = NO_OWNER;
+  }
+  pages_free_empty(c);
+  for (long i = 0; i < m; ++i) decode_into(c, c->last_req[i], (long)c->last_vict[i]);
+  if (c->co.lag == 1) {
+    pages_alloc(c, c->last_req, m);
+    for (long i = 0; i < m; ++i) {
+      uint32_t slot = c->last_vict[i], key = c->last_req[i];
+      if (!pt_map(c, key, slot)) continue; /* no page slot: dropped */
       c->owner[slot] = key;
       c->stamp[slot] = (uint32_t)f;
-    } else {
-      c->owner[slot] = NO_OWNER; /* in flight: unmapped until the next frame ends */
     }
+  } else {
+    c->n_pending = m;
   }
-  if (c->co.lag == 2) c->n_pending = m;
   st->bricks_decoded = (uint64_t)m;
   st->inr_queries_decode = (uint64_t)m * (uint64_t)S3;
 }
@@ -1530,8 +1671,23 @@ void orc_cache_set_macro(orc_cache* c, const orc_macro* m) { c->mo.macro = m; }
 long orc_cache_dump(const orc_cache* c, int what, uint32_t* out, long cap) {
   const uint32_t* src = NULL;
   long n = 0;
+  long P3 = (long)c->co.page * c->co.page * c->co.page;
   switch (what) {
-    case 0: src = c->pt; n = c->n_bricks; break;
+    case 0:
+      if (c->co.page) {
+        orc_cache* mc = (orc_cache*)c;
+        if (!mc->pt_view) mc->pt_view = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)c->n_bricks);
+        for (long k = 0; k < c->n_bricks; ++k) mc->pt_view[k] = pt_get(c, (uint32_t)k);
+        src = c->pt_view;
+      } else {
+        src = c->pt;
+      }
+      n = c->n_bricks;
+      break;
+    case 8: src = c->pd; n = c->co.page ? c->pd_off[c->co.levels] : 0; break;
+    case 9: src = c->pages; n = c->co.page ? c->co.n_pages * P3 : 0; break;
+    case 10: src = c->page_key; n = c->co.page ? c->co.n_pages : 0; break;
+    case 11: src = c->page_ref; n = c->co.page ? c->co.n_pages : 0; break;
     case 1: src = c->stamp; n = c->co.n_slots; break;
     case 2: src = c->owner; n = c->co.n_slots; break;
     case 3: src = c->rank; n = c->n_bricks; break;

@@ -167,6 +167,9 @@ typedef struct {
   int ranking;       /* 1 = priority ranking (Sec. 4.3.3), 0 = first-n */
   int preload;       /* 1 = decode + pin every coarsest brick at creation */
   int lag;           /* frames from request to use: 1 (default) or 2 */
+  int page;          /* 0: flat page tables; P > 0: virtualised 2-level
+                        tables, pages of P^3 bricks (Sec. 4.3.1) */
+  long n_pages;      /* PT pages the page pool holds (page > 0) */
 } orc_cache_opts;
 
 orc_cache* orc_cache_create(const orc_inr_params* p, const double* table,
@@ -187,10 +190,14 @@ void orc_render_cached(orc_cache* c, const orc_camera* cam, const double* tf,
 void orc_render_pt_cached(orc_cache* c, const orc_camera* cam, const double* tf,
                           const orc_pt_opts* pt, int px0, int py0, int pw,
                           int ph, double* rgba, orc_stats* st);
-/* what: 0 page table (u32 per brick), 1 slot stamps (u32 per slot),
+/* what: 0 page table (u32 per brick; paged: the entries the two levels
+ *       resolve to), 1 slot stamps (u32 per slot),
  *       2 slot owners (u32 per slot), 3 rank (u32 per brick),
  *       4 last requests (u32 keys), 5 last victims (u32 slots),
- *       6 last true-miss list (u32 pairs pixel,k), 7 pinned (u32 per slot).
+ *       6 last true-miss list (u32 pairs pixel,k), 7 pinned (u32 per slot),
+ *       8 page directory (u32 per page: Mapped | page slot),
+ *       9 page pool (u32 per entry, n_pages * P^3),
+ *       10 page slot keys (u32 per page slot), 11 page refcounts.
  * Returns the element count; copies min(count, cap) elements. */
 long orc_cache_dump(const orc_cache* c, int what, uint32_t* out, long cap);
 void orc_cache_slot_values(const orc_cache* c, long slot, double* out);

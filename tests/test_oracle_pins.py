@@ -317,12 +317,13 @@ def test_brick_sample_equals_whole_grid_trilinear(level, vol):
         assert a == pytest.approx(b, rel=1e-12, abs=1e-13)
 
 
-def _cache_scene(preload=1, n_slots=200, n_req=6, ranking=1, lod_scale=1.0, lod_mode=0, lag=1):
+def _cache_scene(preload=1, n_slots=200, n_req=6, ranking=1, lod_scale=1.0, lod_mode=0, lag=1,
+                 page=0, n_pages=0):
     p, table, w = _small_inr(seed=2)
     vol = (32, 32, 32)
     mo = O.march_opts(K=8, eps_T=0.0, lod_mode=lod_mode, lod_scale=lod_scale, seed=9)
     c = O.Cache(p, table, w, vol, brick=8, levels=3, n_slots=n_slots, mo=mo, n_req=n_req,
-                ranking=ranking, preload=preload, lag=lag)
+                ranking=ranking, preload=preload, lag=lag, page=page, n_pages=n_pages)
     cam = O.camera((0.6, 0.5, 1.6), (0, 0, 0), (0, 1, 0), 45.0, 24, 24, 0.5)
     tf = S.tf_ramps(2).astype(np.float64)
     return c, cam, tf, p, table, w, vol
@@ -827,3 +828,91 @@ def test_pt_cached_frames_deterministic_and_preloaded():
         assert sa["true_misses"] == 0 and sa["hits"] + sa["fallback_hits"] == sa["samples"] > 0
     assert np.array_equal(pt0, pt1) and np.array_equal(s0, s1) and np.array_equal(r0, r1)
     assert i0[0][1]["bricks_requested"] > 0
+
+
+# --------------------------------------------------- virtualised page tables
+def _paged_check(c):
+    # page accounting: refcount = mapped entries of the page; directory and
+    # slot keys agree; no resident page is empty
+    P3 = c.co.page ** 3
+    pd, pages = c.dump(O.DUMP_PAGE_DIR), c.dump(O.DUMP_PAGES).reshape(-1, P3)
+    keys, refs = c.dump(O.DUMP_PAGE_KEY), c.dump(O.DUMP_PAGE_REF)
+    for ps in range(len(keys)):
+        mapped = int(np.count_nonzero(pages[ps] & 0x80000000))
+        if keys[ps] == 0xFFFFFFFF:
+            assert mapped == 0 and refs[ps] == 0
+        else:
+            assert pd[keys[ps]] == (0x80000000 | ps)
+            assert refs[ps] == mapped > 0
+    assert np.count_nonzero(pd & 0x80000000) == np.count_nonzero(keys != 0xFFFFFFFF)
+
+
+@pytest.mark.parametrize("page", [1, 2, 4])
+def test_paged_tables_equal_flat_tables_with_room(page):
+    # with enough page slots the two-level tables resolve every brick as the
+    # flat table does: same images, statistics, requests, victims and state
+    runs = []
+    for pg in (0, page):
+        c, cam0, tf, *_ = _cache_scene(n_slots=14, n_req=6, page=pg, n_pages=4096 if pg else 0,
+                                       lod_mode=1, lod_scale=0.0)
+        out = []
+        for f in range(1, 7):
+            a = 1.3 * f
+            cam = O.camera((1.4 * math.cos(a), 0.3, 1.4 * math.sin(a)), (0, 0, 0), (0, 1, 0),
+                           14.0, 24, 24, 0.5)
+            img, st = c.render(cam, tf)
+            out.append((img, st, c.dump(O.DUMP_PT), c.dump(O.DUMP_OWNER), c.dump(O.DUMP_STAMP),
+                        c.dump(O.DUMP_REQ), c.dump(O.DUMP_VICT)))
+            if pg:
+                _paged_check(c)
+        runs.append(out)
+    for a, b in zip(*runs):
+        assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+        for x, y in zip(a[2:], b[2:]):
+            assert np.array_equal(x, y)
+    assert sum(o[1]["evictions"] for o in runs[1]) > 0
+
+
+def test_paged_tables_under_page_pressure_allocate_lowest_page_keys_first():
+    # two page slots beyond the coarsest LoD's: the frame's mappings need
+    # more pages than are free; the ascending page keys get the free slots
+    # in ascending order and the other requests are dropped (their victim
+    # slots stay free); the accounting stays consistent
+    c, cam, tf, *_ = _cache_scene(n_slots=60, n_req=20, page=2, n_pages=3)
+    keys0 = c.dump(O.DUMP_PAGE_KEY)
+    assert keys0[0] != 0xFFFFFFFF and np.all(keys0[1:] == 0xFFFFFFFF)  # coarsest LoD: one page
+    img, st = c.render(cam, tf)
+    _paged_check(c)
+    req, vic = c.dump(O.DUMP_REQ), c.dump(O.DUMP_VICT)
+    own, pt = c.dump(O.DUMP_OWNER), c.dump(O.DUMP_PT)
+    P = 2
+    def page_key(k):
+        l = 0
+        while l + 1 < 3 and k >= c.level_offset(l + 1):
+            l += 1
+        loc = k - c.level_offset(l)
+        _, nb = c.level_dims(l)
+        b = (loc % nb[0], (loc // nb[0]) % nb[1], loc // (nb[0] * nb[1]))
+        pg = [(n + P - 1) // P for n in nb]
+        off = sum(int(np.prod([(n + P - 1) // P for n in c.level_dims(j)[1]])) for j in range(l))
+        return off + b[0] // P + pg[0] * (b[1] // P + pg[1] * (b[2] // P))
+    need = sorted({page_key(int(k)) for k in req})
+    assert len(need) > 2
+    keys = c.dump(O.DUMP_PAGE_KEY)
+    assert keys[1] == need[0] and keys[2] == need[1]
+    pages = c.dump(O.DUMP_PAGES).reshape(-1, P ** 3)
+    for k, s in zip(req, vic):
+        if page_key(int(k)) in need[:2]:
+            assert pt[k] == (0x80000000 | s) and own[s] == k
+            # the entry sits at (bx%P) + P ((by%P) + P (bz%P)) of its page
+            l = 0
+            while l + 1 < 3 and k >= c.level_offset(l + 1):
+                l += 1
+            loc = int(k) - c.level_offset(l)
+            _, nb = c.level_dims(l)
+            b = (loc % nb[0], (loc // nb[0]) % nb[1], loc // (nb[0] * nb[1]))
+            local = b[0] % P + P * (b[1] % P + P * (b[2] % P))
+            ps = int(np.nonzero(keys == page_key(int(k)))[0][0])
+            assert pages[ps, local] == (0x80000000 | s)
+        else:
+            assert pt[k] == 0 and own[s] == 0xFFFFFFFF
