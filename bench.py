@@ -196,7 +196,8 @@ def run_gpu(args, wl):
     S3 = (wl["brick"] + 2) ** 3
     cache = cinr.Cache(inr_c, vol, pool_bytes=wl["pool_mib"] << 20, brick=wl["brick"],
                        levels=wl["levels"], storage=storage, n_req=wl["n_req"], ranking=1,
-                       preload=1, lag=args.lag, device=device)
+                       preload=1, lag=args.lag, page=args.page, n_pages=args.n_pages,
+                       device=device)
     rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
                          ray_layout=args.ray_layout, seed=args.seed, step_mode=wl["step_mode"],
                          step_lod_max=wl["step_lod_max"], use_graph=args.graph, device=device)
@@ -296,6 +297,7 @@ def run_gpu(args, wl):
     alg_bytes = [sl * (S3 * elem + 4) + W * H * 16 for sl in slots]
     achieved = sum(alg_bytes) / (sum(k_ms) * 1e-3) / 1e9
     default_cfg = (args.precision == "mixed" and not args.macro and args.ray_layout == 0 and not args.pt
+                   and not args.page
                    and args.lod_scale == 1.0 and args.lag == 1 and not args.autotune)
     traffic = PROFILED_TRAFFIC.get(args.workload) if default_cfg else None
     un_q = sum(s["inr_queries_direct"] for s in un_st)
@@ -327,6 +329,8 @@ def run_gpu(args, wl):
                    "cuda_graph": bool(args.graph),
                    "macro_cell": args.macro or None,
                    "lag": args.lag,
+                   "page_tables": (f"two-level, pages of {args.page}^3 bricks, {args.n_pages} page slots"
+                                   if args.page else "flat"),
                    "renderer": "path tracing (delta tracking)" if args.pt else "ray marching",
                    "timed_frames": [args.warmup, last_f],
                    "l2": "flushed (256 MiB write) before every timed frame",
@@ -596,6 +600,9 @@ def main():
     ap.add_argument("--ray-layout", type=int, default=0, choices=[0, 1])
     ap.add_argument("--pt", action="store_true",
                     help="path-trace (Woodcock delta tracking) instead of ray marching")
+    ap.add_argument("--page", type=int, default=0,
+                    help="virtualised page tables: page edge in bricks (0 = flat tables)")
+    ap.add_argument("--n-pages", type=int, default=0, help="page slots of the page pool")
     ap.add_argument("--lag", type=int, default=1, choices=[1, 2],
                     help="frames from a brick request to its use (2: decode on a second stream)")
     ap.add_argument("--macro", type=int, default=0,

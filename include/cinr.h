@@ -136,7 +136,17 @@ typedef struct {
  * frame f, decoded on a second stream while frame f+1 renders, and mapped at
  * the end of frame f+1 (before its own selection, which skips bricks mapped
  * that way), serving frame f+2.  Both are deterministic.  A lag-2 cache
- * cannot be used with use_graph. */
+ * cannot be used with use_graph.
+ * page = 0: one page-table entry per brick (flat tables).  page = P (a power
+ * of two, 1..16): virtualised two-level page tables (Sec. 4.3.1) -- per LoD
+ * a page directory over pages of P^3 bricks, resident pages held in a pool
+ * of n_pages page slots; a brick whose page is not resident reads as
+ * Unmapped.  At the end of a frame the victims are unmapped first, the
+ * pages left without a mapped brick are freed, the pages the new mappings
+ * need are allocated (ascending page key into ascending free page slots)
+ * and the bricks are mapped; a brick whose page finds no free slot is
+ * dropped for the frame (its victim slot stays free).  n_pages must hold
+ * at least the coarsest LoD's pages when preload = 1. */
 typedef struct {
   int brick;
   int levels;
@@ -145,6 +155,8 @@ typedef struct {
   int preload;
   int storage_precision;
   int lag;
+  int page;
+  long n_pages;
 } cinr_cache_opts;
 
 /* Per-frame counters.  samples = samples marched; inr_queries_direct = true
@@ -471,6 +483,10 @@ int cinr_inr_export(cinr_inr_t inr, float* host_table, float* host_mlp,
 #define CINR_DUMP_MISSES 6     /* u32 pairs (pixel, sample), renderer   */
 #define CINR_DUMP_PINNED 7     /* u32 per slot: 1 if pinned             */
 #define CINR_DUMP_POOL 8       /* brick pool voxels (float or half bits) */
+#define CINR_DUMP_PAGE_DIR 9   /* u32 per page: Mapped | page slot (paged) */
+#define CINR_DUMP_PAGES 10     /* u32 per page entry, n_pages * P^3      */
+#define CINR_DUMP_PAGE_KEYS 11 /* u32 per page slot: page key or ~0      */
+#define CINR_DUMP_PAGE_REFS 12 /* u32 per page slot: mapped bricks       */
 
 /* Copies a piece of state to host memory (synchronises `stream`).  For
  * CINR_DUMP_MISSES pass the renderer as `obj`, for the others the cache.

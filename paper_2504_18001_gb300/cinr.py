@@ -21,7 +21,8 @@ _lib = None
 CINR_OK = 0
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3}
 DUMP_PAGE_TABLE, DUMP_STAMPS, DUMP_OWNERS, DUMP_RANK, DUMP_REQUESTS, DUMP_VICTIMS, \
-    DUMP_MISSES, DUMP_PINNED, DUMP_POOL = range(9)
+    DUMP_MISSES, DUMP_PINNED, DUMP_POOL, DUMP_PAGE_DIR, DUMP_PAGES, DUMP_PAGE_KEYS, \
+    DUMP_PAGE_REFS = range(13)
 
 
 class CinrError(RuntimeError):
@@ -55,7 +56,7 @@ class cinr_march_opts(C.Structure):
 class cinr_cache_opts(C.Structure):
     _fields_ = [("brick", C.c_int), ("levels", C.c_int), ("n_req", C.c_int),
                 ("ranking", C.c_int), ("preload", C.c_int), ("storage_precision", C.c_int),
-                ("lag", C.c_int)]
+                ("lag", C.c_int), ("page", C.c_int), ("n_pages", C.c_long)]
 
 
 class cinr_frame_stats(C.Structure):
@@ -274,10 +275,10 @@ class Inr:
 
 class Cache:
     def __init__(self, inr: Inr, dims, pool_bytes, brick=8, levels=4, n_req=40, ranking=1,
-                 preload=1, storage="fp32", lag=1, device="cuda", stream=None):
+                 preload=1, storage="fp32", lag=1, page=0, n_pages=0, device="cuda", stream=None):
         L = lib()
         self.opts = cinr_cache_opts(int(brick), int(levels), int(n_req), int(ranking), int(preload),
-                                    PREC[storage], int(lag))
+                                    PREC[storage], int(lag), int(page), int(n_pages))
         self.dims = (C.c_int * 3)(*dims)
         nbytes, nslots = C.c_size_t(), C.c_long()
         check(L.cinr_cache_bytes(self.dims, int(pool_bytes), C.byref(self.opts), C.byref(nbytes),

@@ -23,6 +23,7 @@ int bits_for(unsigned long long v) {
 
 struct CacheLayout {
   uint32_t *pt, *rank, *touched, *counters, *stamp, *owner, *pinned;
+  uint32_t *pd, *pages, *page_key, *page_ref;
   void* pool;
   SelState *sel_req, *sel_vic;
   unsigned long long *req_keys, *vic_keys;
@@ -34,6 +35,10 @@ struct Geometry {
   int L, B, S;
   int dims[kMaxLod][3], nb[kMaxLod][3];
   unsigned long long off[kMaxLod + 1];
+  int page_shift;  // -1: flat page tables
+  int pg[kMaxLod][3];
+  unsigned long long pd_off[kMaxLod + 1];
+  long n_pages;
 };
 
 int geometry(const int vol[3], const cinr_cache_opts* o, Geometry* g) {
@@ -47,6 +52,17 @@ int geometry(const int vol[3], const cinr_cache_opts* o, Geometry* g) {
   if (o->storage_precision != CINR_PREC_FP32 && o->storage_precision != CINR_PREC_FP16)
     return set_error(CINR_ERR_ARG, "storage_precision must be FP32 or FP16");
   if (o->lag < 0 || o->lag > 2) return set_error(CINR_ERR_ARG, "lag must be 1 or 2 (0 means 1)");
+  g->page_shift = -1;
+  g->n_pages = 0;
+  if (o->page != 0) {
+    int sh = 0;
+    while (sh <= 4 && (1 << sh) != o->page) ++sh;
+    if (sh > 4) return set_error(CINR_ERR_ARG, "page must be 0 or a power of two in [1, 16]");
+    if (o->n_pages < 1 || o->n_pages >= (1l << 31) - 1)
+      return set_error(CINR_ERR_ARG, "n_pages must be in [1, 2^31 - 1) with paged tables");
+    g->page_shift = sh;
+    g->n_pages = o->n_pages;
+  }
   g->L = o->levels;
   g->B = o->brick;
   g->S = o->brick + 2;
@@ -59,6 +75,14 @@ int geometry(const int vol[3], const cinr_cache_opts* o, Geometry* g) {
     g->off[l + 1] = g->off[l] + (unsigned long long)g->nb[l][0] * g->nb[l][1] * g->nb[l][2];
   }
   if (g->off[g->L] >= (1ull << 31)) return set_error(CINR_ERR_ARG, "too many bricks (>= 2^31)");
+  g->pd_off[0] = 0;
+  for (int l = 0; l < g->L; ++l) {
+    for (int a = 0; a < 3; ++a)
+      g->pg[l][a] = g->page_shift < 0 ? 0 : (g->nb[l][a] + (1 << g->page_shift) - 1) >> g->page_shift;
+    g->pd_off[l + 1] = g->pd_off[l] + (unsigned long long)g->pg[l][0] * g->pg[l][1] * g->pg[l][2];
+  }
+  if (g->page_shift >= 0 && (unsigned long long)g->n_pages << (3 * g->page_shift) >= (1ull << 40))
+    return set_error(CINR_ERR_ARG, "page pool too large");
   return CINR_OK;
 }
 
@@ -66,7 +90,12 @@ CacheLayout layout(const Geometry& g, long n_slots, int prec, void* base) {
   Carver c(base);
   CacheLayout L;
   size_t nb = (size_t)g.off[g.L];
-  L.pt = c.take<uint32_t>(nb);
+  const bool paged = g.page_shift >= 0;
+  L.pt = c.take<uint32_t>(paged ? 0 : nb);
+  L.pd = c.take<uint32_t>(paged ? (size_t)g.pd_off[g.L] : 0);
+  L.pages = c.take<uint32_t>(paged ? (size_t)g.n_pages << (3 * g.page_shift) : 0);
+  L.page_key = c.take<uint32_t>(paged ? (size_t)g.n_pages : 0);
+  L.page_ref = c.take<uint32_t>(paged ? (size_t)g.n_pages : 0);
   L.rank = c.take<uint32_t>(nb);
   L.touched = c.take<uint32_t>(nb);
   L.counters = c.take<uint32_t>(64);
@@ -82,9 +111,7 @@ CacheLayout layout(const Geometry& g, long n_slots, int prec, void* base) {
   L.vic_vals = c.take<uint32_t>(kMaxReq);
   L.vic_sorted = c.take<uint32_t>(kMaxReq);
   size_t S3 = (size_t)g.S * g.S * g.S;
-  // + 256 B: the paired voxel loads of the marching kernel may read one
-  // element past the last slot
-  L.pool = c.take<char>((size_t)n_slots * S3 * (prec == CINR_PREC_FP16 ? 2 : 4) + 256);
+  L.pool = c.take<char>((size_t)n_slots * S3 * (prec == CINR_PREC_FP16 ? 2 : 4));
   L.bytes = align_up(c.off, 256);
   return L;
 }
@@ -175,11 +202,23 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
   if (MLPP) tc::tc_teardown(tcs);
 }
 
+// Preload map: brick i of the coarsest LoD into slot i.  Paged tables: the
+// coarsest LoD's pages take page slots 0.. in ascending page key.
 __global__ void preload_map(CacheDev c, uint32_t n) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t key = c.off[c.L - 1] + i;
-  c.pt[key] = kMapped | i;
+  if (c.pd) {
+    uint32_t local;
+    const uint32_t pk = key_page(c, key, local);
+    const uint32_t ps = pk - c.pd_off[c.L - 1];
+    c.pd[pk] = kMapped | ps;
+    c.page_key[ps] = pk;
+    c.pages[((size_t)ps << (3 * c.page_shift)) + local] = kMapped | i;
+    atomicAdd(c.page_ref + ps, 1u);
+  } else {
+    c.pt[key] = kMapped | i;
+  }
   c.owner[i] = key;
   c.pinned[i] = 1u;
 }
@@ -192,14 +231,14 @@ struct ReqKeys {
   const uint32_t* touched;
   const uint32_t* count;
   const uint32_t* rank;
-  const uint32_t* pt;
+  CacheDev c;
   uint32_t Tf;
   int key_bits;
   int ranking;
   __device__ bool operator()(uint32_t i, unsigned long long& key, uint32_t& val) const {
     if (i >= *count) return false;
     uint32_t b = touched[i];
-    if (pt[b] & kMapped) return false;  // mapped since its request (lag 2)
+    if (pt_entry_key(c, b) & kMapped) return false;  // mapped since its request (lag 2)
     uint32_t score = rank[b] - Tf;
     score = score > 1000u ? 1000u : score;
     key = ranking ? ((unsigned long long)(1000u - score) << key_bits) | b : (unsigned long long)b;
@@ -365,7 +404,14 @@ __global__ void commit_kernel(CacheDev c, const uint32_t* req, const uint32_t* r
     const uint32_t slot = vic[i], key = req[i];
     const uint32_t old = c.owner[slot];
     if (old != kNoOwner) {
-      c.pt[old] = 0u;
+      if (c.pd) {
+        uint32_t local;
+        const uint32_t ps = c.pd[key_page(c, old, local)] & ~kMapped;
+        c.pages[((size_t)ps << (3 * c.page_shift)) + local] = 0u;
+        atomicSub(c.page_ref + ps, 1u);
+      } else {
+        c.pt[old] = 0u;
+      }
       ++ev;
     }
     if (map) {
@@ -387,16 +433,119 @@ __global__ void commit_kernel(CacheDev c, const uint32_t* req, const uint32_t* r
 
 // Lag 2: maps the bricks decoded during this frame (the previous frame's
 // selection) and stamps their slots with this frame.
+// With paged tables a brick whose page found no page slot is dropped (its
+// slot stays free).  Used for lag 2, and for lag 1 with paged tables.
 __global__ void map_pending_kernel(CacheDev c, const uint32_t* req, const uint32_t* vic,
                                    const uint32_t* decode_n, uint32_t frame) {
   const uint32_t m = *decode_n;
   for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
     const uint32_t slot = vic[i], key = req[i];
-    c.pt[key] = kMapped | slot;
+    if (c.pd) {
+      uint32_t local;
+      const uint32_t e = c.pd[key_page(c, key, local)];
+      if (!(e & kMapped)) continue;  // no page slot: dropped
+      const uint32_t ps = e & ~kMapped;
+      c.pages[((size_t)ps << (3 * c.page_shift)) + local] = kMapped | slot;
+      atomicAdd(c.page_ref + ps, 1u);
+    } else {
+      c.pt[key] = kMapped | slot;
+    }
     c.owner[slot] = key;
     c.stamp[slot] = frame;
   }
 }
+
+// Paged tables: frees the page slots left without a mapped brick.
+__global__ void free_pages_kernel(CacheDev c) {
+  for (uint32_t ps = blockIdx.x * blockDim.x + threadIdx.x; ps < c.n_pages; ps += gridDim.x * blockDim.x) {
+    const uint32_t k = c.page_key[ps];
+    if (k != kNoOwner && c.page_ref[ps] == 0u) {
+      c.pd[k] = 0u;
+      c.page_key[ps] = kNoOwner;
+    }
+  }
+}
+
+constexpr int kAllocThreads = 1024;
+constexpr int kAllocCap = 8192;  // >= kMaxReq
+
+// Paged tables: allocates the pages that requests 0..m-1 need and do not
+// have: the distinct page keys in ascending order get the free page slots
+// in ascending order (one CTA: bitonic sort in shared memory, then a
+// block-wide running count of free slots).
+__global__ void __launch_bounds__(kAllocThreads) alloc_pages_kernel(CacheDev c, const uint32_t* req,
+                                                                     const uint32_t* n_dev) {
+  __shared__ uint32_t keys[kAllocCap];
+  __shared__ uint32_t n_need, n_uniq, base;
+  __shared__ uint32_t wsum[kAllocThreads / 32];
+  const uint32_t m = *n_dev;
+  const int t = threadIdx.x;
+  if (t == 0) n_need = 0;
+  __syncthreads();
+  for (uint32_t i = t; i < m; i += kAllocThreads) {
+    uint32_t local;
+    const uint32_t pk = key_page(c, req[i], local);
+    if (!(c.pd[pk] & kMapped)) keys[atomicAdd(&n_need, 1u)] = pk;
+  }
+  __syncthreads();
+  const uint32_t n = n_need;
+  if (n == 0) return;  // block-uniform
+  uint32_t np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  for (uint32_t i = n + t; i < np2; i += kAllocThreads) keys[i] = 0xFFFFFFFFu;
+  __syncthreads();
+  for (uint32_t k = 2; k <= np2; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = t; i < np2; i += kAllocThreads) {
+        const uint32_t p = i ^ j;
+        if (p > i) {
+          const bool up = (i & k) == 0;
+          const uint32_t a = keys[i], b = keys[p];
+          if ((a > b) == up) {
+            keys[i] = b;
+            keys[p] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // unique, in place, by one thread (n <= 8192)
+  if (t == 0) {
+    uint32_t u = 0;
+    for (uint32_t i = 0; i < n; ++i)
+      if (i == 0 || keys[i] != keys[i - 1]) keys[u++] = keys[i];
+    n_uniq = u;
+    base = 0;
+  }
+  __syncthreads();
+  const uint32_t u = n_uniq;
+  // free page slots in ascending order: chunk of kAllocThreads slots per
+  // pass, a block prefix count of the free ones
+  for (uint32_t start = 0; start < c.n_pages; start += kAllocThreads) {
+    if (base >= u) break;  // block-uniform (read after the barrier)
+    const uint32_t ps = start + t;
+    const bool is_free = ps < c.n_pages && c.page_key[ps] == kNoOwner;
+    const unsigned bal = __ballot_sync(0xffffffffu, is_free);
+    if ((t & 31) == 0) wsum[t >> 5] = __popc(bal);
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int w = 0; w < kAllocThreads / 32; ++w) {
+      before += w < (t >> 5) ? wsum[w] : 0u;
+      total += wsum[w];
+    }
+    const uint32_t r = base + before + __popc(bal & ((1u << (t & 31)) - 1u));
+    if (is_free && r < u) {
+      c.pd[keys[r]] = kMapped | ps;
+      c.page_key[ps] = keys[r];
+      c.page_ref[ps] = 0u;
+    }
+    __syncthreads();
+    if (t == 0) base += total;
+    __syncthreads();
+  }
+}
+
+int num_sms();
 
 int num_sms() {
   static int n = 0;
@@ -520,6 +669,9 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
   if (o->preload && (long)n_coarse > ns)
     return set_error(CINR_ERR_NOMEM, "pool of %ld bricks cannot hold the %llu coarsest bricks", ns,
                      n_coarse);
+  if (o->preload && g.page_shift >= 0 && (long)(g.pd_off[g.L] - g.pd_off[g.L - 1]) > g.n_pages)
+    return set_error(CINR_ERR_ARG, "n_pages (%ld) cannot hold the coarsest LoD's %llu pages", g.n_pages,
+                     g.pd_off[g.L] - g.pd_off[g.L - 1]);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cinr_cache_s* c = new cinr_cache_s();
   c->o = *o;
@@ -548,6 +700,15 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
   for (int l = 0; l <= kMaxLod; ++l) d.off[l] = (uint32_t)(l <= g.L ? g.off[l] : g.off[g.L]);
   d.touched = L.touched;
   d.touched_count = L.counters;
+  d.pd = g.page_shift >= 0 ? L.pd : nullptr;
+  d.pages = L.pages;
+  d.page_key = L.page_key;
+  d.page_ref = L.page_ref;
+  d.page_shift = g.page_shift < 0 ? 0 : g.page_shift;
+  d.n_pages = (uint32_t)g.n_pages;
+  for (int l = 0; l < kMaxLod; ++l)
+    for (int a = 0; a < 3; ++a) d.pg[l][a] = l < g.L ? g.pg[l][a] : 1;
+  for (int l = 0; l <= kMaxLod; ++l) d.pd_off[l] = (uint32_t)(l <= g.L ? g.pd_off[l] : g.pd_off[g.L]);
   c->sel_req = L.sel_req;
   c->sel_vic = L.sel_vic;
   c->req_keys = L.req_keys;
@@ -563,7 +724,14 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
   c->slot_bits = bits_for((unsigned long long)ns);
 
   size_t nb = (size_t)c->n_bricks;
-  CINR_CK(cudaMemsetAsync(L.pt, 0, nb * 4, s));
+  if (g.page_shift >= 0) {
+    CINR_CK(cudaMemsetAsync(L.pd, 0, (size_t)g.pd_off[g.L] * 4, s));
+    CINR_CK(cudaMemsetAsync(L.pages, 0, ((size_t)g.n_pages << (3 * g.page_shift)) * 4, s));
+    CINR_CK(cudaMemsetAsync(L.page_key, 0xFF, (size_t)g.n_pages * 4, s));
+    CINR_CK(cudaMemsetAsync(L.page_ref, 0, (size_t)g.n_pages * 4, s));
+  } else {
+    CINR_CK(cudaMemsetAsync(L.pt, 0, nb * 4, s));
+  }
   CINR_CK(cudaMemsetAsync(L.rank, 0, nb * 4, s));
   CINR_CK(cudaMemsetAsync(L.counters, 0, 64 * 4, s));
   CINR_CK(cudaMemsetAsync(L.stamp, 0, (size_t)ns * 4, s));
@@ -615,17 +783,29 @@ int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStr
   const uint32_t Tf = (uint32_t)(1001ull * c->frame);
   const uint32_t want = (uint32_t)c->o.n_req;
   const bool lag2 = c->o.lag == 2;
+  const bool paged = c->dev.pd != nullptr;
   uint32_t extra = 0;
+  // paged tables: the pages the mappings need, then the mappings
+  auto map_selected = [&](uint32_t f) -> int {
+    if (paged) {
+      alloc_pages_kernel<<<1, kAllocThreads, 0, s>>>(c->dev, c->req_sorted, c->decode_n);
+      CINR_CK(cudaGetLastError());
+      ++extra;
+    }
+    map_pending_kernel<<<1, 1024, 0, s>>>(c->dev, c->req_sorted, c->vic_sorted, c->decode_n, f);
+    CINR_CK(cudaGetLastError());
+    ++extra;
+    return CINR_OK;
+  };
   if (lag2 && c->pending) {
     // the bricks decoded on the second stream during this frame are mapped
     // first: they serve the next frame and are no request candidates
     CINR_CK(cudaStreamWaitEvent(s, c->e_dec, 0));
-    map_pending_kernel<<<1, 1024, 0, s>>>(c->dev, c->req_sorted, c->vic_sorted, c->decode_n, frame);
-    CINR_CK(cudaGetLastError());
+    const int em = map_selected(frame);
+    if (em) return em;
     c->pending = false;
-    extra = 1;
   }
-  ReqKeys rk{c->dev.touched, c->dev.touched_count, c->dev.rank, c->dev.pt, Tf, c->key_bits, c->o.ranking};
+  ReqKeys rk{c->dev.touched, c->dev.touched_count, c->dev.rank, c->dev, Tf, c->key_bits, c->o.ranking};
   const int rbits = c->o.ranking ? c->key_bits + 10 : c->key_bits;
   int e = radix_select(rk, (uint32_t)c->n_bricks, rbits, want, c->sel_req, c->req_keys,
                        c->req_vals, c->req_sorted, c->req_n, s);
@@ -635,15 +815,31 @@ int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStr
   e = radix_select(vk, (uint32_t)c->n_slots, vbits, want, c->sel_vic, c->vic_keys, c->vic_vals,
                    c->vic_sorted, c->vic_n, s);
   if (e) return e;
+  // commit: unmap the victims (and, flat lag 1, map the requests at once)
   commit_kernel<<<1, 1024, 0, s>>>(c->dev, c->req_sorted, c->req_n, c->vic_sorted, c->vic_n, frame,
                                    c->decode_n, stats_dev, (uint32_t)(c->dev.S * c->dev.S * c->dev.S),
-                                   !lag2);
+                                   !lag2 && !paged);
   CINR_CK(cudaGetLastError());
+  if (paged) {
+    const int grid = (int)((c->dev.n_pages + 255) / 256 < 1024 ? (c->dev.n_pages + 255) / 256 : 1024);
+    free_pages_kernel<<<grid, 256, 0, s>>>(c->dev);
+    CINR_CK(cudaGetLastError());
+    ++extra;
+  }
   // kernels of this update: per radix select reset + (hist, pick) per pass +
-  // gather + sort; commit; decode (+ the map of lag 2)
+  // gather + sort; commit; decode (+ page and map kernels)
   auto sel = [](int bits) { return 3 + 2 * (bits <= 11 ? 1 : (bits + 10) / 11); };
+  if (!lag2) {
+    int ed = decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, s);
+    if (ed) return ed;
+    if (paged) {
+      ed = map_selected(frame);
+      if (ed) return ed;
+    }
+    c->last_launches = (uint32_t)(sel(rbits) + sel(vbits) + 2) + extra;
+    return CINR_OK;
+  }
   c->last_launches = (uint32_t)(sel(rbits) + sel(vbits) + 2) + extra;
-  if (!lag2) return decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, s);
   CINR_CK(cudaEventRecord(c->e_sel, s));
   CINR_CK(cudaStreamWaitEvent(c->dstream, c->e_sel, 0));
   int e2 = decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, c->dstream, 2);

@@ -100,7 +100,62 @@ struct CacheDev {
   uint32_t off[kMaxLod + 1];
   uint32_t* touched;
   uint32_t* touched_count;
+  // virtualised page tables (pd != nullptr; pt is then unused): per-LoD
+  // page directory over pages of 2^page_shift bricks per axis, page pool,
+  // page slot keys and refcounts
+  uint32_t* pd;
+  uint32_t* pages;
+  uint32_t* page_key;
+  uint32_t* page_ref;
+  int page_shift;
+  int pg[kMaxLod][3];
+  uint32_t pd_off[kMaxLod + 1];
+  uint32_t n_pages;
 };
+
+// Page-table entry of brick (b0, b1, b2) at LoD lev (key = its flat key):
+// the flat table, or the entry in its page when the page is resident.
+__device__ __forceinline__ uint32_t pt_entry(const CacheDev& c, int lev, uint32_t key, int b0, int b1,
+                                             int b2) {
+  if (!c.pd) return __ldg(c.pt + key);
+  const int sh = c.page_shift, m = (1 << sh) - 1;
+  const uint32_t pk = c.pd_off[lev] + (uint32_t)(b0 >> sh) +
+                      (uint32_t)c.pg[lev][0] * ((uint32_t)(b1 >> sh) + (uint32_t)c.pg[lev][1] * (uint32_t)(b2 >> sh));
+  const uint32_t e = __ldg(c.pd + pk);
+  if (!(e & kMapped)) return 0u;
+  const uint32_t local = (uint32_t)(b0 & m) + ((uint32_t)(b1 & m) << sh) + ((uint32_t)(b2 & m) << (2 * sh));
+  return __ldg(c.pages + (((size_t)(e & ~kMapped)) << (3 * sh)) + local);
+}
+
+// Level and brick coordinates of a flat brick key.
+__device__ __forceinline__ int key_brick(const CacheDev& c, uint32_t key, int b[3]) {
+  int l = 0;
+  while (l + 1 < c.L && key >= c.off[l + 1]) ++l;
+  const uint32_t loc = key - c.off[l];
+  b[0] = (int)(loc % (uint32_t)c.nb[l][0]);
+  b[1] = (int)((loc / (uint32_t)c.nb[l][0]) % (uint32_t)c.nb[l][1]);
+  b[2] = (int)(loc / ((uint32_t)c.nb[l][0] * (uint32_t)c.nb[l][1]));
+  return l;
+}
+
+// Page key and in-page index of a brick key (paged tables).
+__device__ __forceinline__ uint32_t key_page(const CacheDev& c, uint32_t key, uint32_t& local) {
+  int b[3];
+  const int l = key_brick(c, key, b);
+  const int sh = c.page_shift, m = (1 << sh) - 1;
+  local = (uint32_t)(b[0] & m) + ((uint32_t)(b[1] & m) << sh) + ((uint32_t)(b[2] & m) << (2 * sh));
+  return c.pd_off[l] + (uint32_t)(b[0] >> sh) +
+         (uint32_t)c.pg[l][0] * ((uint32_t)(b[1] >> sh) + (uint32_t)c.pg[l][1] * (uint32_t)(b[2] >> sh));
+}
+
+__device__ __forceinline__ uint32_t pt_entry_key(const CacheDev& c, uint32_t key) {
+  if (!c.pd) return c.pt[key];
+  uint32_t local;
+  const uint32_t pk = key_page(c, key, local);
+  const uint32_t e = c.pd[pk];
+  if (!(e & kMapped)) return 0u;
+  return c.pages[(((size_t)(e & ~kMapped)) << (3 * c.page_shift)) + local];
+}
 
 // Macro-cell skip flags of the current transfer function (Sec. 5.2);
 // skip == nullptr turns skipping off.  Cells are 2^shift LoD-0 voxels wide.

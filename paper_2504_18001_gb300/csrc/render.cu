@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
           }
           const uint32_t key =
               c.off[lev] + (uint32_t)b[0] + (uint32_t)c.nb[lev][0] * ((uint32_t)b[1] + (uint32_t)c.nb[lev][1] * (uint32_t)b[2]);
-          const uint32_t e = __ldg(c.pt + key);
+          const uint32_t e = pt_entry(c, lev, key, b[0], b[1], b[2]);
           if (!(e & kMapped)) {
             if (lev == l) {
               want_req = true;
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           b1 = min(max(b1, 0), g.nb1 - 1);
           b2 = min(max(b2, 0), g.nb2 - 1);
           const uint32_t key = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
-          const uint32_t e = __ldg(c.pt + key);
+          const uint32_t e = pt_entry(c, lev, key, b0, b1, b2);
           if (!(e & kMapped)) {
             if (lev == l) {
               want_req = true;
@@ -769,7 +769,7 @@ __device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const flo
       b1 = min(max(b1, 0), g.nb1 - 1);
       b2 = min(max(b2, 0), g.nb2 - 1);
       const uint32_t key = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
-      const uint32_t e = __ldg(c.pt + key);
+      const uint32_t e = pt_entry(c, lev, key, b0, b1, b2);
       if (!(e & kMapped)) {
         if (lev == l) {
           const uint32_t old = atomicMax(c.rank + key, P.Tf);
@@ -1396,7 +1396,21 @@ extern "C" int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap, 
     const int ew = cinr_cache_wait_decode(c, s);
     if (ew) return ew;
     switch (what) {
-      case CINR_DUMP_PAGE_TABLE: src = c->dev.pt; n = (size_t)c->n_bricks; break;
+      case CINR_DUMP_PAGE_TABLE:
+        if (c->dev.pd) return set_error(CINR_ERR_ARG, "paged tables: dump the page directory and pages");
+        src = c->dev.pt;
+        n = (size_t)c->n_bricks;
+        break;
+      case CINR_DUMP_PAGE_DIR:
+        src = c->dev.pd;
+        n = c->dev.pd ? (size_t)c->dev.pd_off[c->dev.L] : 0;
+        break;
+      case CINR_DUMP_PAGES:
+        src = c->dev.pages;
+        n = c->dev.pd ? (size_t)c->dev.n_pages << (3 * c->dev.page_shift) : 0;
+        break;
+      case CINR_DUMP_PAGE_KEYS: src = c->dev.page_key; n = c->dev.pd ? c->dev.n_pages : 0; break;
+      case CINR_DUMP_PAGE_REFS: src = c->dev.page_ref; n = c->dev.pd ? c->dev.n_pages : 0; break;
       case CINR_DUMP_STAMPS: src = c->dev.stamp; n = (size_t)c->n_slots; break;
       case CINR_DUMP_OWNERS: src = c->dev.owner; n = (size_t)c->n_slots; break;
       case CINR_DUMP_RANK: src = c->dev.rank; n = (size_t)c->n_bricks; break;

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_req=40, ranking=1,
          preload=1, lod_scale=1.0, lod_mode=0, storage="fp32", K=32, eps=0.0, check_pixels=2e-3,
          cam_fn=None, mlp="fp32", tab="fp32", ray_layout=0, step_mode=0, step_lod_max=0,
-         use_graph=0, tf=None, macro_cell=0, lag=1):
+         use_graph=0, tf=None, macro_cell=0, lag=1, page=0, n_pages=0):
     from paper_2504_18001_gb300 import cinr
     cfg = S.INR_64
     table, w = scene(cfg)
@@ -24,12 +24,12 @@ def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_r
     S3 = (brick + 2) ** 3
     cache = cinr.Cache(inr, vol, pool_bytes=slots * S3 * (2 if storage == "fp16" else 4),
                        brick=brick, levels=levels, n_req=n_req, ranking=ranking, preload=preload,
-                       storage=storage, lag=lag)
+                       storage=storage, lag=lag, page=page, n_pages=n_pages)
     assert cache.n_slots == slots
     mo = O.march_opts(K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
                       step_mode=step_mode, step_lod_max=step_lod_max)
     oc = O.Cache(p, table, w, vol, brick, levels, slots, mo, n_req=n_req, ranking=ranking,
-                 preload=preload, lag=lag)
+                 preload=preload, lag=lag, page=page, n_pages=n_pages)
     r = cinr.Renderer(W, H, vol, K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
                       ray_layout=ray_layout, step_mode=step_mode, step_lod_max=step_lod_max,
                       use_graph=use_graph, miss_record_cap=W * H * 4000)
@@ -54,10 +54,13 @@ def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_r
                   "bricks_decoded", "evictions", "inr_queries_direct", "inr_queries_decode",
                   "samples_skipped"):
             assert st[k] == rst[k], (f, k, st[k], rst[k])
-        for g, o in ((cinr.DUMP_PAGE_TABLE, O.DUMP_PT), (cinr.DUMP_STAMPS, O.DUMP_STAMP),
-                     (cinr.DUMP_OWNERS, O.DUMP_OWNER), (cinr.DUMP_RANK, O.DUMP_RANK),
-                     (cinr.DUMP_REQUESTS, O.DUMP_REQ), (cinr.DUMP_VICTIMS, O.DUMP_VICT),
-                     (cinr.DUMP_PINNED, O.DUMP_PINNED)):
+        tables = (((cinr.DUMP_PAGE_DIR, O.DUMP_PAGE_DIR), (cinr.DUMP_PAGES, O.DUMP_PAGES),
+                   (cinr.DUMP_PAGE_KEYS, O.DUMP_PAGE_KEY), (cinr.DUMP_PAGE_REFS, O.DUMP_PAGE_REF))
+                  if page else ((cinr.DUMP_PAGE_TABLE, O.DUMP_PT),))
+        for g, o in tables + ((cinr.DUMP_STAMPS, O.DUMP_STAMP),
+                              (cinr.DUMP_OWNERS, O.DUMP_OWNER), (cinr.DUMP_RANK, O.DUMP_RANK),
+                              (cinr.DUMP_REQUESTS, O.DUMP_REQ), (cinr.DUMP_VICTIMS, O.DUMP_VICT),
+                              (cinr.DUMP_PINNED, O.DUMP_PINNED)):
             a, b = cache.dump(g), oc.dump(o)
             assert np.array_equal(a, b), (f, g, np.nonzero(a != b)[0][:10] if a.shape == b.shape else (a.shape, b.shape))
         gm = sorted_pairs(r.misses())
@@ -217,3 +220,21 @@ def test_cached_lag2_under_pressure_and_decoded_bricks():
     own = cache.dump(cinr.DUMP_OWNERS)
     for s in np.nonzero(own != 0xFFFFFFFF)[0][:30]:
         assert np.abs(pool[s] - oc.slot_values(int(s))).max() < 1e-4
+
+
+@pytest.mark.parametrize("page,n_pages,lag", [(2, 4096, 1), (4, 64, 1), (2, 6, 1), (2, 40, 2)])
+def test_cached_paged_tables_state_bit_exact(page, n_pages, lag):
+    # virtualised two-level page tables: page directory, page pool, page
+    # keys and refcounts bit-exact against the oracle after every frame, also
+    # with a page pool too small for the frame's mappings (dropped requests)
+    def cam_fn(f, W, H):
+        return S.orbit_camera(0, W, H, start_deg=75.0 * f, distance=1.3, fov_y_deg=12.0)
+    cache, oc, hist, worst = _run(6, slots=60, n_req=30, lod_mode=1, lod_scale=0.0, levels=3,
+                                  cam_fn=cam_fn, page=page, n_pages=n_pages, lag=lag)
+    assert sum(h["bricks_decoded"] for h in hist) > 0
+
+
+def test_cached_paged_tables_mixed_precision_orbit():
+    cache, oc, hist, worst = _run(4, storage="fp16", mlp="bf16", tab="fp16", check_pixels=None,
+                                  page=4, n_pages=200, slots=120)
+    assert worst < 6e-2
