@@ -293,12 +293,16 @@ __global__ void __launch_bounds__(kSelThreads) sel_hist(KF kf, uint32_t n, SelSt
 }
 
 // Picks the digit holding the k-th smallest key; one block of 1024 threads.
-__global__ void __launch_bounds__(1024) sel_pick(SelState* st, int shift, int pass, uint32_t want) {
+// cap (device, may be null): a further bound on the selected count, read on
+// the device (the victim selection selects no more slots than requests).
+__global__ void __launch_bounds__(1024) sel_pick(SelState* st, int shift, int pass, uint32_t want,
+                                                 const uint32_t* cap) {
   __shared__ unsigned int warp_sum[32];
   __shared__ unsigned int s_k;
   const int t = threadIdx.x;
   if (pass == 0 && t == 0) {
     uint32_t k = st->total < want ? st->total : want;
+    if (cap && *cap < k) k = *cap;
     st->none = (k == 0u);
     st->k = k;
     st->prefix = 0ull;
@@ -561,7 +565,7 @@ int num_sms() {
 template <class KF>
 int radix_select(const KF& kf, uint32_t n, int key_bits, uint32_t want, SelState* st,
                  unsigned long long* keys, uint32_t* vals, uint32_t* sorted, uint32_t* n_out,
-                 cudaStream_t s) {
+                 cudaStream_t s, const uint32_t* k_cap = nullptr) {
   const int passes = key_bits <= 11 ? 1 : (key_bits + 10) / 11;
   unsigned blocks = (unsigned)((n + kSelThreads - 1) / kSelThreads);
   unsigned cap = (unsigned)num_sms() * 4;
@@ -571,7 +575,7 @@ int radix_select(const KF& kf, uint32_t n, int key_bits, uint32_t want, SelState
   for (int p = 0; p < passes; ++p) {
     const int shift = 11 * (passes - 1 - p);
     sel_hist<KF><<<blocks, kSelThreads, 0, s>>>(kf, n, st, shift, p);
-    sel_pick<<<1, 1024, 0, s>>>(st, shift, p, want);
+    sel_pick<<<1, 1024, 0, s>>>(st, shift, p, want, k_cap);
   }
   sel_gather<KF><<<blocks, kSelThreads, 0, s>>>(kf, n, st, keys, vals);
   sel_sort<<<(want + 255) / 256, 256, 0, s>>>(st, keys, vals, sorted, n_out);
@@ -813,7 +817,7 @@ int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStr
   VicKeys vk{c->dev.stamp, c->dev.pinned, (uint32_t)c->n_slots, frame, c->slot_bits};
   const int vbits = c->slot_bits + bits_for((unsigned long long)frame);
   e = radix_select(vk, (uint32_t)c->n_slots, vbits, want, c->sel_vic, c->vic_keys, c->vic_vals,
-                   c->vic_sorted, c->vic_n, s);
+                   c->vic_sorted, c->vic_n, s, c->req_n);
   if (e) return e;
   // commit: unmap the victims (and, flat lag 1, map the requests at once)
   commit_kernel<<<1, 1024, 0, s>>>(c->dev, c->req_sorted, c->req_n, c->vic_sorted, c->vic_n, frame,
