@@ -66,6 +66,20 @@ PT_OPTS = dict(light_dir=(0.3, -1.0, -0.4), light=(3.0, 3.0, 3.0), ambient=(0.05
                max_bounces=3)
 
 
+def replica_reduce(local_total_ms, n_frames, device=None):
+    """N independent replicas (one per rank): the timed region's wall time is
+    the maximum over ranks, and the aggregate ms per frame divides it by the
+    frames all ranks rendered.  Returns (max total ms, ms per frame)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([float(local_total_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total = float(t.item())
+    return total, total / (n_frames * world)
+
+
 def frame_inputs(f, W, H, camera="orbit"):
     from paper_2504_18001_gb300 import synthetic as S
     tf = S.tf_ramps(2)
@@ -279,10 +293,7 @@ def run_gpu(args, wl):
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = float(sum(e2e)) / len(e2e)
 
-    t_local = torch.tensor([cached_ms * len(ms)], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    total_ms = float(t_local.item())
+    total_ms, value_ms = replica_reduce(cached_ms * len(ms), len(ms), device)
 
     peaks, peak_kind = load_peaks()
     q_direct = sum(s["inr_queries_direct"] for s in stats)
@@ -304,7 +315,7 @@ def run_gpu(args, wl):
     prec = args.precision
     res = {
         "metric": METRIC,
-        "value": total_ms / (len(ms) * world),
+        "value": value_ms,
         "unit": "ms/frame",
         "n_gpus": world,
         "steps": args.steps,
