@@ -201,7 +201,8 @@ def run_gpu(args, wl):
         from paper_2504_18001_gb300 import autotune
         best, trials = autotune.tune(
             inr_c, inr32, vol, lambda f: frame_inputs(f, W, H, wl["camera"]), W, H,
-            bricks=(wl["brick"],), levels=wl["levels"], pool_mib=wl["pool_mib"], storage=storage,
+            bricks=(8, 16) if wl["camera"] == "orbit" else (wl["brick"],), levels=wl["levels"],
+            pool_mib=wl["pool_mib"], storage=storage,
             lod_scale=args.lod_scale, step_mode=wl["step_mode"],
             step_lod_max=wl["step_lod_max"], device=device)
         wl = dict(wl, n_req=best["n_req"], brick=best["brick"])

@@ -8,8 +8,11 @@ decode batch that the persistent decode kernel takes), the ray layout of the
 marching kernel (one ray per thread or per warp), whether each frame runs as
 a CUDA graph, and the brick edge -- and returns the fastest setting whose
 cached frame stays within `min_psnr` dB of the uncached FP32 frame.
-All timing is on the device (CUDA events around the frame's launch
-sequence); every candidate builds its own cache and renderer.
+Each candidate first renders until its cache has caught up with the camera
+(a frame that decodes fewer bricks than the request budget, three times in
+a row, or `max_warmup` frames), then times `timed` frames on the device
+(CUDA events around the frame's launch sequence); every candidate builds
+its own cache and renderer.
 """
 from __future__ import annotations
 
@@ -26,8 +29,8 @@ def _psnr(a, b):
 
 
 def tune(inr_cached, inr_fp32, vol, frame_inputs, W, H, *, bricks=(8,), n_reqs=(1024, 4096, 8192),
-         layouts=(0, 1), graphs=(0, 1), levels=4, pool_mib=1024, storage="fp16", warmup=40, timed=10,
-         lod_scale=1.0, step_mode=0, step_lod_max=0, min_psnr=40.0, device="cuda"):
+         layouts=(0, 1), graphs=(0, 1), levels=4, pool_mib=1024, storage="fp16", max_warmup=160,
+         timed=10, lod_scale=1.0, step_mode=0, step_lod_max=0, min_psnr=40.0, device="cuda"):
     """Returns (best, results): best is the chosen knob dict; results lists
     every candidate with its mean ms/frame and PSNR."""
     import torch
@@ -43,9 +46,14 @@ def tune(inr_cached, inr_fp32, vol, frame_inputs, W, H, *, bricks=(8,), n_reqs=(
         rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_scale=lod_scale, ray_layout=layout,
                              step_mode=step_mode, step_lod_max=step_lod_max, use_graph=graph,
                              device=device)
-        for f in range(warmup):
+        caught_up, warmup = 0, max_warmup
+        for f in range(max_warmup):
             cam, tf = frame_inputs(f)
-            rend.render(inr_cached, cam, tf, cache=cache, out=img)
+            _, st = rend.render(inr_cached, cam, tf, cache=cache, out=img)
+            caught_up = caught_up + 1 if st["bricks_decoded"] < n_req else 0
+            if caught_up == 3:
+                warmup = f + 1
+                break
         ms = []
         for f in range(warmup, warmup + timed):
             cam, tf = frame_inputs(f)
@@ -59,7 +67,7 @@ def tune(inr_cached, inr_fp32, vol, frame_inputs, W, H, *, bricks=(8,), n_reqs=(
         rend.render(inr_fp32, cam, tf, cache=None, out=ref)
         psnr = _psnr(img, ref)
         results.append(dict(brick=brick, n_req=n_req, ray_layout=layout, use_graph=graph,
-                            ms_per_frame=float(np.mean(ms)), psnr_db=psnr,
+                            ms_per_frame=float(np.mean(ms)), psnr_db=psnr, warmup_frames=warmup,
                             tune_s=time.perf_counter() - t0))
         del cache, rend
         torch.cuda.synchronize()

@@ -46,11 +46,33 @@ __device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+// Coordinates of sample s: given, or the counter-based uniform of the step.
+__device__ __forceinline__ void train_point(const float* xyz_in, uint64_t seed, uint64_t first, long s,
+                                            float& x, float& y, float& z) {
+  if (xyz_in) {
+    x = xyz_in[3 * s];
+    y = xyz_in[3 * s + 1];
+    z = xyz_in[3 * s + 2];
+  } else {
+    const uint64_t c0 = 3ull * (first + (uint64_t)s);
+    x = (float)(splitmix64_dev(seed + c0) >> 40) * (1.0f / 16777216.0f);
+    y = (float)(splitmix64_dev(seed + c0 + 1) >> 40) * (1.0f / 16777216.0f);
+    z = (float)(splitmix64_dev(seed + c0 + 2) >> 40) * (1.0f / 16777216.0f);
+  }
+  x = clamp01(x);
+  y = clamp01(y);
+  z = clamp01(z);
+}
+
+// Forward pass of a batch (Sec. 4.1): encode, two ReLU layers, linear
+// output, squared error against the target; the activations (features,
+// h1, h2, dL/dy) go to the feature-major buffers of the weight gradients.
 template <int IN, int H>
-__global__ void __launch_bounds__(kFwdThreads) fwd_bwd_kernel(
-    InrDev q, long n, const float* __restrict__ xyz_in, const float* __restrict__ tgt_in,
-    const float* __restrict__ field, int3 dims, uint64_t seed, uint64_t first, float* __restrict__ act,
-    float* __restrict__ g_table, float* __restrict__ loss) {
+__global__ void __launch_bounds__(kFwdThreads) fwd_kernel(InrDev q, long n, const float* __restrict__ xyz_in,
+                                                          const float* __restrict__ tgt_in,
+                                                          const float* __restrict__ field, int3 dims,
+                                                          uint64_t seed, uint64_t first, float* __restrict__ act,
+                                                          float* __restrict__ loss) {
   extern __shared__ float4 smem4[];
   float* sw = reinterpret_cast<float*>(smem4);
   load_weights(sw, q.w, mlp_floats<IN, H>());
@@ -62,30 +84,13 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_bwd_kernel(
   float r2 = 0.0f;
   if (s < n) {
     float x, y, z;
-    if (xyz_in) {
-      x = xyz_in[3 * s];
-      y = xyz_in[3 * s + 1];
-      z = xyz_in[3 * s + 2];
-    } else {
-      const uint64_t c0 = 3ull * (first + (uint64_t)s);
-      x = (float)(splitmix64_dev(seed + c0) >> 40) * (1.0f / 16777216.0f);
-      y = (float)(splitmix64_dev(seed + c0 + 1) >> 40) * (1.0f / 16777216.0f);
-      z = (float)(splitmix64_dev(seed + c0 + 2) >> 40) * (1.0f / 16777216.0f);
-    }
-    x = clamp01(x);
-    y = clamp01(y);
-    z = clamp01(z);
+    train_point(xyz_in, seed, first, s, x, y, z);
     const float t = tgt_in ? tgt_in[s] : field_trilinear(field, dims, x, y, z);
     float* a_feat = act;
     float* a_h1 = act + (size_t)IN * n;
     float* a_h2 = a_h1 + (size_t)H * n;
-    float* a_dh1 = a_h2 + (size_t)H * n;
-    float* a_dh2 = a_dh1 + (size_t)H * n;
-    float* a_dy = a_dh2 + (size_t)H * n;
-
-    // forward
+    float* a_dy = a_h2 + (size_t)3 * H * n;
     float h1[H];
-    uint64_t m1 = 0ull, m2 = 0ull;
     {
       float feat[IN];
       encode_point<IN / 2>(q, x, y, z, feat);
@@ -97,7 +102,6 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_bwd_kernel(
 #pragma unroll
         for (int k = 0; k < IN; ++k) acc = fmaf(W1[o * IN + k], feat[k], acc);
         h1[o] = fmaxf(acc, 0.0f);
-        if (acc > 0.0f) m1 |= 1ull << o;
         a_h1[(size_t)o * n + s] = h1[o];
       }
     }
@@ -108,64 +112,88 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_bwd_kernel(
 #pragma unroll
       for (int k = 0; k < H; ++k) acc = fmaf(W2[o * H + k], h1[k], acc);
       const float h2 = fmaxf(acc, 0.0f);
-      if (acc > 0.0f) m2 |= 1ull << o;
       a_h2[(size_t)o * n + s] = h2;
       yv = fmaf(W3[o], h2, yv);
     }
     const float r = yv - t;
     r2 = r * r;
-    const float dy = 2.0f * r / (float)n;
-    a_dy[s] = dy;
-    // backward through the MLP
-    float dh1[H];
-#pragma unroll
-    for (int k = 0; k < H; ++k) dh1[k] = 0.0f;
-#pragma unroll 4
-    for (int o = 0; o < H; ++o) {
-      const float dh2 = ((m2 >> o) & 1ull) ? dy * W3[o] : 0.0f;
-      a_dh2[(size_t)o * n + s] = dh2;
-#pragma unroll
-      for (int k = 0; k < H; ++k) dh1[k] = fmaf(W2[o * H + k], dh2, dh1[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      dh1[k] = ((m1 >> k) & 1ull) ? dh1[k] : 0.0f;
-      a_dh1[(size_t)k * n + s] = dh1[k];
-    }
-    float dfeat[IN];
-#pragma unroll
-    for (int k = 0; k < IN; ++k) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int o = 0; o < H; ++o) acc = fmaf(W1[o * IN + k], dh1[o], acc);
-      dfeat[k] = acc;
-    }
-    // backward through the hash grid: scatter-add into the table gradient
-    const uint32_t T = 1u << q.log2T;
-#pragma unroll
-    for (int l = 0; l < IN / 2; ++l) {
-      const int N = q.res[l];
-      int ix, iy, iz;
-      float wx, wy, wz;
-      grid_cell(x, N, ix, wx);
-      grid_cell(y, N, iy, wy);
-      grid_cell(z, N, iz, wz);
-      const bool dense = (q.dense_mask >> l) & 1u;
-      const uint32_t n1 = (uint32_t)N + 1u;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) *
-                        ((c & 4) ? wz : 1.0f - wz);
-        const uint32_t idx = (uint32_t)l * T + vertex_index(dense, n1, T, ix + (c & 1),
-                                                            iy + ((c >> 1) & 1), iz + ((c >> 2) & 1));
-        atomicAdd(g_table + 2 * (size_t)idx, w * dfeat[2 * l]);
-        atomicAdd(g_table + 2 * (size_t)idx + 1, w * dfeat[2 * l + 1]);
-      }
-    }
+    a_dy[s] = 2.0f * r / (float)n;
   }
   if (loss) {
     for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
     if ((threadIdx.x & 31) == 0 && r2 != 0.0f) atomicAdd(loss, r2 / (float)n);
+  }
+}
+
+// Backward pass: through the output and second layer (dh2 = dy W3 on the
+// active units, dh1 = W2^T dh2 on the active units of h1), the first layer
+// (dfeat = W1^T dh1), then through the trilinear hash-grid interpolation:
+// each vertex entry receives weight * dfeat by atomicAdd.  h1 > 0 and
+// h2 > 0 are the ReLU masks (a unit is active exactly when its output is
+// positive).
+template <int IN, int H>
+__global__ void __launch_bounds__(kFwdThreads) bwd_kernel(InrDev q, long n, const float* __restrict__ xyz_in,
+                                                          uint64_t seed, uint64_t first, float* __restrict__ act,
+                                                          float* __restrict__ g_table) {
+  extern __shared__ float4 smem4[];
+  float* sw = reinterpret_cast<float*>(smem4);
+  load_weights(sw, q.w, mlp_floats<IN, H>());
+  __syncthreads();
+  const float* W1 = sw;
+  const float* W2 = sw + IN * H;
+  const float* W3 = W2 + H * H;
+  const long s = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const float* a_h1 = act + (size_t)IN * n;
+  const float* a_h2 = a_h1 + (size_t)H * n;
+  float* a_dh1 = const_cast<float*>(a_h2) + (size_t)H * n;
+  float* a_dh2 = a_dh1 + (size_t)H * n;
+  const float dy = act[(size_t)IN * n + (size_t)4 * H * n + s];
+  float dh1[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) dh1[k] = 0.0f;
+#pragma unroll 4
+  for (int o = 0; o < H; ++o) {
+    const float dh2 = a_h2[(size_t)o * n + s] > 0.0f ? dy * W3[o] : 0.0f;
+    a_dh2[(size_t)o * n + s] = dh2;
+#pragma unroll
+    for (int k = 0; k < H; ++k) dh1[k] = fmaf(W2[o * H + k], dh2, dh1[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    dh1[k] = a_h1[(size_t)k * n + s] > 0.0f ? dh1[k] : 0.0f;
+    a_dh1[(size_t)k * n + s] = dh1[k];
+  }
+  float dfeat[IN];
+#pragma unroll
+  for (int k = 0; k < IN; ++k) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int o = 0; o < H; ++o) acc = fmaf(W1[o * IN + k], dh1[o], acc);
+    dfeat[k] = acc;
+  }
+  float x, y, z;
+  train_point(xyz_in, seed, first, s, x, y, z);
+  const uint32_t T = 1u << q.log2T;
+#pragma unroll
+  for (int l = 0; l < IN / 2; ++l) {
+    const int N = q.res[l];
+    int ix, iy, iz;
+    float wx, wy, wz;
+    grid_cell(x, N, ix, wx);
+    grid_cell(y, N, iy, wy);
+    grid_cell(z, N, iz, wz);
+    const bool dense = (q.dense_mask >> l) & 1u;
+    const uint32_t n1 = (uint32_t)N + 1u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) *
+                      ((c & 4) ? wz : 1.0f - wz);
+      const uint32_t idx = (uint32_t)l * T + vertex_index(dense, n1, T, ix + (c & 1),
+                                                          iy + ((c >> 1) & 1), iz + ((c >> 2) & 1));
+      atomicAdd(g_table + 2 * (size_t)idx, w * dfeat[2 * l]);
+      atomicAdd(g_table + 2 * (size_t)idx + 1, w * dfeat[2 * l + 1]);
+    }
   }
 }
 
@@ -324,10 +352,13 @@ int grads(cinr_trainer_s* t, const float* xyz, const float* tgt, long n, const f
   const InrDev& q = t->inr->dev;
   CINR_CK(cudaMemsetAsync(g_table, 0, sizeof(float) * t->n_table, s));
   const int smem = mlp_floats<IN, H>() * 4;
-  auto k = fwd_bwd_kernel<IN, H>;
-  CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k<<<(unsigned)((n + kFwdThreads - 1) / kFwdThreads), kFwdThreads, smem, s>>>(
-      q, n, xyz, tgt, field, dims, t->o.seed, first, t->act, g_table, t->loss);
+  auto kf = fwd_kernel<IN, H>;
+  auto kb = bwd_kernel<IN, H>;
+  CINR_CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  CINR_CK(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const unsigned grid = (unsigned)((n + kFwdThreads - 1) / kFwdThreads);
+  kf<<<grid, kFwdThreads, smem, s>>>(q, n, xyz, tgt, field, dims, t->o.seed, first, t->act, t->loss);
+  kb<<<grid, kFwdThreads, smem, s>>>(q, n, xyz, t->o.seed, first, t->act, g_table);
   CINR_CK(cudaGetLastError());
   const int blocks = (int)((n + kChunk - 1) / kChunk);
   const float* a_feat = t->act;
