@@ -36,7 +36,7 @@ struct cinr_trainer_s {
 
 namespace {
 
-constexpr int kChunk = 2048;     // samples per block in the weight-gradient reduction
+constexpr int kChunk = 512;      // samples per block in the weight-gradient reduction
 constexpr int kFwdThreads = 128;
 
 __device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
@@ -68,7 +68,7 @@ __device__ __forceinline__ void train_point(const float* xyz_in, uint64_t seed, 
 // output, squared error against the target; the activations (features,
 // h1, h2, dL/dy) go to the feature-major buffers of the weight gradients.
 template <int IN, int H>
-__global__ void __launch_bounds__(kFwdThreads) fwd_kernel(InrDev q, long n, const float* __restrict__ xyz_in,
+__global__ void __launch_bounds__(kFwdThreads, IN <= 32 ? 4 : 2) fwd_kernel(InrDev q, long n, const float* __restrict__ xyz_in,
                                                           const float* __restrict__ tgt_in,
                                                           const float* __restrict__ field, int3 dims,
                                                           uint64_t seed, uint64_t first, float* __restrict__ act,
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(InrDev q, long n, cons
 // h2 > 0 are the ReLU masks (a unit is active exactly when its output is
 // positive).
 template <int IN, int H>
-__global__ void __launch_bounds__(kFwdThreads) bwd_kernel(InrDev q, long n, const float* __restrict__ xyz_in,
+__global__ void __launch_bounds__(kFwdThreads, IN <= 32 ? 4 : 2) bwd_kernel(InrDev q, long n, const float* __restrict__ xyz_in,
                                                           uint64_t seed, uint64_t first, float* __restrict__ act,
                                                           float* __restrict__ g_table) {
   extern __shared__ float4 smem4[];
@@ -191,8 +191,8 @@ __global__ void __launch_bounds__(kFwdThreads) bwd_kernel(InrDev q, long n, cons
                       ((c & 4) ? wz : 1.0f - wz);
       const uint32_t idx = (uint32_t)l * T + vertex_index(dense, n1, T, ix + (c & 1),
                                                           iy + ((c >> 1) & 1), iz + ((c >> 2) & 1));
-      atomicAdd(g_table + 2 * (size_t)idx, w * dfeat[2 * l]);
-      atomicAdd(g_table + 2 * (size_t)idx + 1, w * dfeat[2 * l + 1]);
+      // both features of the entry in one 8-byte vector atomic
+      atomicAdd(reinterpret_cast<float2*>(g_table) + idx, make_float2(w * dfeat[2 * l], w * dfeat[2 * l + 1]));
     }
   }
 }
