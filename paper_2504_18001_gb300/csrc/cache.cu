@@ -727,31 +727,37 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
   c->key_bits = bits_for((unsigned long long)c->n_bricks);
   c->slot_bits = bits_for((unsigned long long)ns);
 
-  size_t nb = (size_t)c->n_bricks;
-  if (g.page_shift >= 0) {
-    CINR_CK(cudaMemsetAsync(L.pd, 0, (size_t)g.pd_off[g.L] * 4, s));
-    CINR_CK(cudaMemsetAsync(L.pages, 0, ((size_t)g.n_pages << (3 * g.page_shift)) * 4, s));
-    CINR_CK(cudaMemsetAsync(L.page_key, 0xFF, (size_t)g.n_pages * 4, s));
-    CINR_CK(cudaMemsetAsync(L.page_ref, 0, (size_t)g.n_pages * 4, s));
-  } else {
-    CINR_CK(cudaMemsetAsync(L.pt, 0, nb * 4, s));
-  }
-  CINR_CK(cudaMemsetAsync(L.rank, 0, nb * 4, s));
-  CINR_CK(cudaMemsetAsync(L.counters, 0, 64 * 4, s));
-  CINR_CK(cudaMemsetAsync(L.stamp, 0, (size_t)ns * 4, s));
-  CINR_CK(cudaMemsetAsync(L.pinned, 0, (size_t)ns * 4, s));
-  CINR_CK(cudaMemsetAsync(L.sel_req, 0, sizeof(SelState), s));
-  CINR_CK(cudaMemsetAsync(L.sel_vic, 0, sizeof(SelState), s));
-  fill_u32<<<256, 256, 0, s>>>(L.owner, (size_t)ns, kNoOwner);
-  CINR_CK(cudaGetLastError());
-  if (o->preload) {
-    e = decode(inr, d, nullptr, nullptr, nullptr, (uint32_t)n_coarse, s);
-    if (e) {
-      delete c;
-      return e;
+  // device initialisation; on any failure the handle is released
+  auto init = [&]() -> int {
+    size_t nb = (size_t)c->n_bricks;
+    if (g.page_shift >= 0) {
+      CINR_CK(cudaMemsetAsync(L.pd, 0, (size_t)g.pd_off[g.L] * 4, s));
+      CINR_CK(cudaMemsetAsync(L.pages, 0, ((size_t)g.n_pages << (3 * g.page_shift)) * 4, s));
+      CINR_CK(cudaMemsetAsync(L.page_key, 0xFF, (size_t)g.n_pages * 4, s));
+      CINR_CK(cudaMemsetAsync(L.page_ref, 0, (size_t)g.n_pages * 4, s));
+    } else {
+      CINR_CK(cudaMemsetAsync(L.pt, 0, nb * 4, s));
     }
-    preload_map<<<(unsigned)((n_coarse + 255) / 256), 256, 0, s>>>(d, (uint32_t)n_coarse);
+    CINR_CK(cudaMemsetAsync(L.rank, 0, nb * 4, s));
+    CINR_CK(cudaMemsetAsync(L.counters, 0, 64 * 4, s));
+    CINR_CK(cudaMemsetAsync(L.stamp, 0, (size_t)ns * 4, s));
+    CINR_CK(cudaMemsetAsync(L.pinned, 0, (size_t)ns * 4, s));
+    CINR_CK(cudaMemsetAsync(L.sel_req, 0, sizeof(SelState), s));
+    CINR_CK(cudaMemsetAsync(L.sel_vic, 0, sizeof(SelState), s));
+    fill_u32<<<256, 256, 0, s>>>(L.owner, (size_t)ns, kNoOwner);
     CINR_CK(cudaGetLastError());
+    if (o->preload) {
+      const int ed = decode(inr, d, nullptr, nullptr, nullptr, (uint32_t)n_coarse, s);
+      if (ed) return ed;
+      preload_map<<<(unsigned)((n_coarse + 255) / 256), 256, 0, s>>>(d, (uint32_t)n_coarse);
+      CINR_CK(cudaGetLastError());
+    }
+    return CINR_OK;
+  };
+  e = init();
+  if (e) {
+    cinr_destroy_cache(c);
+    return e;
   }
   if (o->lag == 2) {
     cudaError_t ce = cudaStreamCreateWithFlags(&c->dstream, cudaStreamNonBlocking);

@@ -103,13 +103,15 @@ extern "C" int cinr_create_inr(const cinr_inr_params* p, void* dev_mem, size_t b
   CINR_CK(cudaMemsetAsync(L.scratch, 0, 1024 * sizeof(float), s));
   CINR_CK(cudaStreamSynchronize(s));
 
+  int device = 0;
+  CINR_CK(cudaGetDevice(&device));
   cinr_inr_s* h = new cinr_inr_s();
   h->p = *p;
   h->mem = dev_mem;
   h->bytes = bytes;
   h->scratch = L.scratch;
   h->w16 = L.w16;
-  CINR_CK(cudaGetDevice(&h->device));
+  h->device = device;
   InrDev& d = h->dev;
   d.table = L.table;
   d.w = L.w;

@@ -410,6 +410,8 @@ extern "C" int cinr_create_trainer(cinr_inr_t inr, const cinr_train_opts* o, voi
   TrainLayout L = tlayout(inr, o->batch, dev_mem);
   if (bytes < L.bytes) return set_error(CINR_ERR_NOMEM, "trainer needs %zu bytes, got %zu", L.bytes, bytes);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CINR_CK(cudaMemsetAsync(L.m_t, 0, sizeof(float) * (size_t)inr->p.levels * ((size_t)1 << inr->p.log2_table) * 2, s));
+  CINR_CK(cudaMemsetAsync(L.v_t, 0, sizeof(float) * (size_t)inr->p.levels * ((size_t)1 << inr->p.log2_table) * 2, s));
   cinr_trainer_s* t = new cinr_trainer_s();
   t->inr = inr;
   t->o = *o;
@@ -426,10 +428,12 @@ extern "C" int cinr_create_trainer(cinr_inr_t inr, const cinr_train_opts* o, voi
   t->loss = L.loss;
   t->step = 0;
   t->n_part = (int)((o->batch + kChunk - 1) / kChunk);
-  CINR_CK(cudaMemsetAsync(L.m_t, 0, sizeof(float) * t->n_table, s));
-  CINR_CK(cudaMemsetAsync(L.v_t, 0, sizeof(float) * t->n_table, s));
-  CINR_CK(cudaMemsetAsync(L.m_w, 0, sizeof(float) * t->n_w, s));
-  CINR_CK(cudaMemsetAsync(L.v_w, 0, sizeof(float) * t->n_w, s));
+  const cudaError_t ce1 = cudaMemsetAsync(L.m_w, 0, sizeof(float) * t->n_w, s);
+  const cudaError_t ce2 = ce1 == cudaSuccess ? cudaMemsetAsync(L.v_w, 0, sizeof(float) * t->n_w, s) : ce1;
+  if (ce2 != cudaSuccess) {
+    delete t;
+    return cuda_error(ce2, "cudaMemsetAsync");
+  }
   *out = t;
   return CINR_OK;
 }
