@@ -280,6 +280,32 @@ __device__ __forceinline__ bool macro_skips(const MacroDev& m, float pv0, float 
   return __ldg(m.skip + ((size_t)c2 * m.dims[1] + c1) * m.dims[0] + c0) != 0;
 }
 
+// Samples after the current one (LoD-0 position pv, spacing `step` along a
+// ray of direction d) that certainly lie in the same macro cell: the
+// distance to the cell's exit in whole steps, less one step of margin.
+// The jump it allows skips exactly the samples that would be skipped one by
+// one (the margin exceeds any rounding of the sample positions by orders of
+// magnitude), so that a lane in empty space moves on to useful samples.
+__device__ __forceinline__ int macro_run(const MacroDev& m, const CamDev& c, const float d[3], float pv0,
+                                         float pv1, float pv2, float step) {
+  const float pv[3] = {pv0, pv1, pv2};
+  float texit = INFINITY;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float dv = d[a] * c.inv_e[a] * (float)c.vol[a];  // d(pv)/dt
+    const int ci = min((int)pv[a] >> m.shift, m.dims[a] - 1);
+    if (dv > 0.0f) {
+      const float edge = (float)min((ci + 1) << m.shift, c.vol[a]);
+      texit = fminf(texit, (edge - pv[a]) / dv);
+    } else if (dv < 0.0f) {
+      texit = fminf(texit, ((float)(ci << m.shift) - pv[a]) / dv);
+    }
+  }
+  const float steps = texit / step;
+  if (!(steps < 1.0e6f)) return 1000000;
+  return max((int)steps - 1, 0);
+}
+
 __device__ __forceinline__ uint32_t xorshift32(uint32_t s) {
   s ^= s << 13;
   s ^= s >> 17;

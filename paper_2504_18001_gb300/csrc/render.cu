@@ -590,6 +590,18 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           Cg = fmaf(wgt, e4.y, Cg);
           Cb = fmaf(wgt, e4.z, Cb);
           T *= 1.0f - alpha;
+        } else {
+          // transparent cell: the next samples in the same cell are skipped
+          // at once, up to the K-segment end (the termination test stays on
+          // its boundary) and, with LoD-scaled steps, the 32-sample segment
+          int jump = macro_run(P.mac, cam, d, pv0, pv1, pv2, cam.step_mode ? sch.dts : cam.dt);
+          jump = min(jump, seg - 1);
+          if (cam.step_mode) jump = min(jump, 31 - (k & 31));
+          if (jump > 0) {
+            k += jump;
+            seg -= jump;
+            n_skip += (uint32_t)jump;
+          }
         }
         ++k;
         if (--seg == 0) {

@@ -152,3 +152,14 @@ def test_field_render_with_macro_cells_identical_and_matches_oracle():
                               tf.astype(np.float64))
     assert rst["samples_skipped"] == st1["samples_skipped"]
     assert np.abs(img1.cpu().numpy() - ref).max() < 2e-3
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-2])
+def test_cached_macro_cells_with_lod_scaled_steps(eps):
+    # the jump over a transparent cell stays inside the 32-sample segment and
+    # the termination boundary: counts and state stay bit-exact
+    cfg, table, w, inr, p = _scene64()
+    theta = float(np.median(O.macro_ranges_inr(p, table, w, (64, 64, 64), 8, 3)[:, 1]))
+    cache, oc, hist, worst = _run(3, tf=_gated_tf(theta), macro_cell=8, slots=80, step_mode=1,
+                                  step_lod_max=2, lod_mode=1, lod_scale=12.0, eps=eps)
+    assert all(h["samples_skipped"] > 0 for h in hist)
