@@ -60,7 +60,7 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one marching-kernel launch on the default
 # orbit configuration, from one ncu capture of the current kernel (frame 91);
 # a workload or option without such a capture reports null.
-PROFILED_TRAFFIC = {"orbit": 452.7e6}
+PROFILED_TRAFFIC = {"orbit": 444.5e6}
 # path-tracing light: a directional light from above-front, dim blue ambient
 PT_OPTS = dict(light_dir=(0.3, -1.0, -0.4), light=(3.0, 3.0, 3.0), ambient=(0.05, 0.06, 0.08),
                max_bounces=3)
@@ -306,12 +306,17 @@ def run_gpu(args, wl):
     samples = sum(s["samples"] for s in stats)
     k_ms = [s["ms_frame_kernel"] for s in stats]
     slots = [s["slots_touched"] for s in stats]
-    # algorithmic bytes of the marching kernel: every distinct brick that
-    # served a sample read once from HBM (+ its page-table entry) and the
-    # image written once
+    # algorithmic bytes of the marching kernel, per sample: one page-table
+    # entry (one more for a sample served by a coarser LoD: the walk's
+    # shortest fallback) and the 8 voxels of the trilinear; the image
+    # written once.  Neighbouring samples share voxels, so the bytes of the
+    # distinct bricks that served samples are reported beside them: those
+    # are what has to come from HBM at the least.
     elem = 2 if args.precision == "mixed" else 4
-    alg_bytes = [sl * (S3 * elem + 4) + W * H * 16 for sl in slots]
+    alg_bytes = [s["samples"] * (4 + 8 * elem) + s["fallback_hits"] * 4 + W * H * 16 for s in stats]
+    uniq_bytes = [sl * (S3 * elem + 4) + W * H * 16 for sl in slots]
     achieved = sum(alg_bytes) / (sum(k_ms) * 1e-3) / 1e9
+    achieved_uniq = sum(uniq_bytes) / (sum(k_ms) * 1e-3) / 1e9
     default_cfg = (args.precision == "mixed" and not args.macro and args.ray_layout == 0 and not args.pt
                    and not args.page
                    and args.lod_scale == 1.0 and args.lag == 1 and not args.autotune)
@@ -369,8 +374,11 @@ def run_gpu(args, wl):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "algorithmic_bytes_per_launch": sum(alg_bytes) / len(alg_bytes),
-                     "kernel": ("march_cached_kernel<%d,%d,%s pool>"
-                                % (cfg.in_dim, cfg.hidden, "fp16" if prec == "mixed" else "fp32")),
+                     "per_unit": "%d B per sample (+4 B per fallback sample)" % (4 + 8 * elem),
+                     "distinct_brick_bytes_per_launch": sum(uniq_bytes) / len(uniq_bytes),
+                     "distinct_brick_frac": achieved_uniq / peaks["hbm_gbs"],
+                     "kernel": ("march_cached_kernel (%s pool, brick %d)"
+                                % ("fp16" if prec == "mixed" else "fp32", wl["brick"])),
                      "peak_kind": peak_kind},
         "clocks": clk,
     }

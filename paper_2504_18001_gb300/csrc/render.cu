@@ -425,7 +425,11 @@ __device__ __forceinline__ float pool_ld(const void* pool, I i) {
 // With the preload every fallback walk ends at a mapped brick, and the
 // instantiation without the (out-of-line) inference call keeps the marching
 // loop free of the register spills that the call's convention forces.
-template <int IN, int H, bool F16POOL, bool MISS>
+//
+// BB: the brick size when it is a compile-time constant (8 or 16; 0 = read
+// from the cache): the voxel offsets inside a brick then become immediates
+// and the brick index a multiplication by the exact power-of-two 1/B.
+template <int IN, int H, bool F16POOL, bool MISS, int BB>
 __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __grid_constant__ FrameParams P) {
   __shared__ float4 s_tf[256];
   __shared__ LevelGeo s_geo[kMaxLod];
@@ -448,11 +452,15 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
   const int lane = threadIdx.x & 31;
   const CamDev& cam = P.cam;
   const float volf[3] = {(float)c.vol[0], (float)c.vol[1], (float)c.vol[2]};
-  const int L = c.L, B = c.B, S = c.S;
-  const float invB = c.invB, fB = (float)c.B;
+  static_assert(BB == 0 || (BB & (BB - 1)) == 0, "compile-time brick sizes are powers of two");
+  const int L = c.L, B = BB ? BB : c.B, S = BB ? BB + 2 : c.S;
+  const float invB = BB ? 1.0f / (float)BB : c.invB, fB = (float)B;
   const size_t S3 = (size_t)S * S * S;
   const void* pool = c.pool;
   uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0, n_skip = 0;
+  // the slot this lane last saw stamped with this frame (stamps change only
+  // between frames): runs of samples in one brick check the stamp once
+  uint32_t stamped = 0xFFFFFFFFu;
   const uint32_t n_tiles = P.n_rays >> 5;
   while (true) {
     uint32_t tile = 0;
@@ -500,9 +508,9 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
         for (int lev = l; lev < L; ++lev) {
           const LevelGeo g = s_geo[lev];
           const float s0 = f_mul(pv0, g.scale), s1 = f_mul(pv1, g.scale), s2 = f_mul(pv2, g.scale);
-          int b0 = (int)floorf(invB > 0.0f ? f_mul(s0, invB) : f_div(s0, fB));
-          int b1 = (int)floorf(invB > 0.0f ? f_mul(s1, invB) : f_div(s1, fB));
-          int b2 = (int)floorf(invB > 0.0f ? f_mul(s2, invB) : f_div(s2, fB));
+          int b0 = (int)floorf(BB || invB > 0.0f ? f_mul(s0, invB) : f_div(s0, fB));
+          int b1 = (int)floorf(BB || invB > 0.0f ? f_mul(s1, invB) : f_div(s1, fB));
+          int b2 = (int)floorf(BB || invB > 0.0f ? f_mul(s2, invB) : f_div(s2, fB));
           b0 = min(max(b0, 0), g.nb0 - 1);
           b1 = min(max(b1, 0), g.nb1 - 1);
           b2 = min(max(b2, 0), g.nb2 - 1);
@@ -559,12 +567,13 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           atomicMin(c.rank + req_key, P.Tf + 1000u);
         }
       }
-      const bool stale = hit && c.stamp[hit_slot] != P.frame;
+      const bool stale = hit && hit_slot != stamped && c.stamp[hit_slot] != P.frame;
       const unsigned hm = __ballot_sync(kFull, stale);
       if (stale) {
         const unsigned peers = __match_any_sync(hm, hit_slot);
         if (lane == __ffs(peers) - 1 && atomicExch(c.stamp + hit_slot, P.frame) != P.frame) ++n_slot;
       }
+      if (hit) stamped = hit_slot;
       const unsigned mm = MISS ? __ballot_sync(kFull, miss) : 0u;
       if (MISS && mm) {
         if (miss) v = infer_miss<IN, H>(P.inr, x[0], x[1], x[2]);
@@ -632,9 +641,9 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
   }
 }
 
-template <int IN, int H, bool F16POOL, bool MISS>
+template <int IN, int H, bool F16POOL, bool MISS, int BB>
 int launch_march_cached(const FrameParams& P, cudaStream_t s) {
-  auto k = march_cached_kernel<IN, H, F16POOL, MISS>;
+  auto k = march_cached_kernel<IN, H, F16POOL, MISS, BB>;
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
@@ -645,21 +654,28 @@ int launch_march_cached(const FrameParams& P, cudaStream_t s) {
   return CINR_OK;
 }
 
-template <bool F16POOL, bool MISS>
-int launch_march_cached_pool(const FrameParams& P, cudaStream_t s) {
+// With true misses possible the kernel infers them with the INR's shape;
+// without, the shape plays no part and the brick size is specialised.
+template <bool F16POOL>
+int launch_march_cached_pool(const FrameParams& P, bool miss, cudaStream_t s) {
+  if (!miss) {
+    switch (P.cache.B) {
+      case 8: return launch_march_cached<16, 32, F16POOL, false, 8>(P, s);
+      case 16: return launch_march_cached<16, 32, F16POOL, false, 16>(P, s);
+      default: return launch_march_cached<16, 32, F16POOL, false, 0>(P, s);
+    }
+  }
   switch (shape_of(P.inr.IN, P.inr.H)) {
-    case Shape::S16x32: return launch_march_cached<16, 32, F16POOL, MISS>(P, s);
-    case Shape::S32x64: return launch_march_cached<32, 64, F16POOL, MISS>(P, s);
-    case Shape::S48x64: return launch_march_cached<48, 64, F16POOL, MISS>(P, s);
+    case Shape::S16x32: return launch_march_cached<16, 32, F16POOL, true, 0>(P, s);
+    case Shape::S32x64: return launch_march_cached<32, 64, F16POOL, true, 0>(P, s);
+    case Shape::S48x64: return launch_march_cached<48, 64, F16POOL, true, 0>(P, s);
     default: return set_error(CINR_ERR_ARG, "unsupported shape");
   }
 }
 
 int launch_march_cached_shape(const FrameParams& P, bool miss, cudaStream_t s) {
   const bool f16 = P.cache.pool_prec == CINR_PREC_FP16;
-  if (miss)
-    return f16 ? launch_march_cached_pool<true, true>(P, s) : launch_march_cached_pool<false, true>(P, s);
-  return f16 ? launch_march_cached_pool<true, false>(P, s) : launch_march_cached_pool<false, false>(P, s);
+  return f16 ? launch_march_cached_pool<true>(P, miss, s) : launch_march_cached_pool<false>(P, miss, s);
 }
 
 // ---------------------------------------------------------------------------
