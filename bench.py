@@ -60,7 +60,7 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one marching-kernel launch on the default
 # orbit configuration, from one ncu capture of the current kernel (frame 91);
 # a workload or option without such a capture reports null.
-PROFILED_TRAFFIC = {"orbit": 444.5e6}
+PROFILED_TRAFFIC = {}
 # path-tracing light: a directional light from above-front, dim blue ambient
 PT_OPTS = dict(light_dir=(0.3, -1.0, -0.4), light=(3.0, 3.0, 3.0), ambient=(0.05, 0.06, 0.08),
                max_bounces=3)

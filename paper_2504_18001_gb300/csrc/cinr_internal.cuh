@@ -172,6 +172,19 @@ __device__ __forceinline__ float f_sub(float a, float b) { return __fsub_rn(a, b
 __device__ __forceinline__ float f_div(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
 
+// Pairs of binary32 operations in one instruction (FADD2 / FMUL2 / FFMA2 of
+// sm_100 and later): each component is rounded as the scalar operation, so
+// results are bit-identical to two scalar instructions.
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
 // Primary ray of pixel (px, py) clipped to the volume box (slab test).
 // Returns true when the ray hits; o is the camera position.
 __device__ __forceinline__ bool ray_setup(const CamDev& c, int px, int py, float d[3],

@@ -84,8 +84,11 @@ __device__ __forceinline__ float4 tf_lookup(const float4* s_tf, float v) {
   const int i1 = i + 1 > 255 ? 255 : i + 1;
   const float fr = x - (float)i;
   const float4 a = s_tf[i], b = s_tf[i1];
-  return make_float4(fmaf(fr, b.x - a.x, a.x), fmaf(fr, b.y - a.y, a.y), fmaf(fr, b.z - a.z, a.z),
-                     fmaf(fr, b.w - a.w, a.w));
+  // (r, g) and (b, extinction) as packed pairs: fr * (b - a) + a per channel
+  const float2 fr2 = make_float2(fr, fr);
+  const float2 lo = f2_fma(fr2, f2_sub(make_float2(b.x, b.y), make_float2(a.x, a.y)), make_float2(a.x, a.y));
+  const float2 hi = f2_fma(fr2, f2_sub(make_float2(b.z, b.w), make_float2(a.z, a.w)), make_float2(a.z, a.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 __device__ __forceinline__ float pool_at(const CacheDev& c, size_t i) {
@@ -433,7 +436,10 @@ template <int IN, int H, bool F16POOL, bool MISS, int BB>
 __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __grid_constant__ FrameParams P) {
   __shared__ float4 s_tf[256];
   __shared__ LevelGeo s_geo[kMaxLod];
+  // rare events (new requests, first stamps) count in shared memory
+  __shared__ uint32_t s_rare[2];
   const CacheDev& c = P.cache;
+  if (threadIdx.x < 2) s_rare[threadIdx.x] = 0u;
   for (int i = threadIdx.x; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
   if (threadIdx.x < c.L) {
     const int l = threadIdx.x;
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
   const float invB = BB ? 1.0f / (float)BB : c.invB, fB = (float)B;
   const size_t S3 = (size_t)S * S * S;
   const void* pool = c.pool;
-  uint32_t n_samp = 0, n_hit = 0, n_fb = 0, n_miss = 0, n_req = 0, n_slot = 0, n_skip = 0;
+  uint32_t n_samp = 0, n_fb = 0, n_miss = 0, n_skip = 0;  // hits = samples - fallbacks - misses
   // the slot this lane last saw stamped with this frame (stamps change only
   // between frames): runs of samples in one brick check the stamp once
   uint32_t stamped = 0xFFFFFFFFu;
@@ -538,15 +544,16 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           const float v010 = pool_ld<F16POOL>(bp, o + S), v110 = pool_ld<F16POOL>(bp, o + S + 1);
           const float v001 = pool_ld<F16POOL>(bp, o + SS), v101 = pool_ld<F16POOL>(bp, o + SS + 1);
           const float v011 = pool_ld<F16POOL>(bp, o + SS + S), v111 = pool_ld<F16POOL>(bp, o + SS + S + 1);
-          const float x00 = fmaf(f0, v100 - v000, v000), x10 = fmaf(f0, v110 - v010, v010);
-          const float x01 = fmaf(f0, v101 - v001, v001), x11 = fmaf(f0, v111 - v011, v011);
-          const float y0 = fmaf(f1, x10 - x00, x00), y1 = fmaf(f1, x11 - x01, x01);
-          v = fmaf(f2, y1 - y0, y0);
+          // x-lerps and the y-lerp on (z = 0, z = 1) pairs, then the z-lerp
+          const float2 a0 = make_float2(v000, v001), a1 = make_float2(v100, v101);
+          const float2 c0 = make_float2(v010, v011), c1 = make_float2(v110, v111);
+          const float2 ff0 = make_float2(f0, f0);
+          const float2 X0 = f2_fma(ff0, f2_sub(a1, a0), a0);                 // (x00, x01)
+          const float2 X1 = f2_fma(ff0, f2_sub(c1, c0), c0);                 // (x10, x11)
+          const float2 Y = f2_fma(make_float2(f1, f1), f2_sub(X1, X0), X0);  // (y0, y1)
+          v = fmaf(f2, Y.y - Y.x, Y.x);
           hit = true;
-          if (lev == l)
-            ++n_hit;
-          else
-            ++n_fb;
+          if (lev != l) ++n_fb;
           break;
         }
         if (!hit) {
@@ -560,7 +567,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
         if (lane == __ffs(peers) - 1) {
           const uint32_t old = atomicMax(c.rank + req_key, P.Tf);
           if (old < P.Tf) {
-            ++n_req;
+            atomicAdd(&s_rare[0], 1u);
             c.touched[atomicAdd(c.touched_count, 1u)] = req_key;
           }
           atomicAdd(c.rank + req_key, (uint32_t)__popc(peers));
@@ -571,7 +578,8 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
       const unsigned hm = __ballot_sync(kFull, stale);
       if (stale) {
         const unsigned peers = __match_any_sync(hm, hit_slot);
-        if (lane == __ffs(peers) - 1 && atomicExch(c.stamp + hit_slot, P.frame) != P.frame) ++n_slot;
+        if (lane == __ffs(peers) - 1 && atomicExch(c.stamp + hit_slot, P.frame) != P.frame)
+          atomicAdd(&s_rare[1], 1u);
       }
       if (hit) stamped = hit_slot;
       const unsigned mm = MISS ? __ballot_sync(kFull, miss) : 0u;
@@ -623,10 +631,19 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
       }
     }
   }
-  unsigned long long a[7] = {n_samp, n_hit, n_fb, n_miss, n_req, n_slot, n_skip};
+  unsigned long long a[5] = {n_samp, n_fb, n_miss, n_skip, 0ull};
 #pragma unroll
-  for (int j = 0; j < 7; ++j)
+  for (int j = 0; j < 4; ++j)
     for (int o = 16; o > 0; o >>= 1) a[j] += __shfl_xor_sync(kFull, a[j], o);
+  a[4] = a[3];                      // skipped
+  a[3] = a[2];                      // misses
+  a[2] = a[1];                      // fallbacks
+  a[1] = a[0] - a[2] - a[3];        // hits
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_rare[0]) atomicAdd(P.stats + ST_REQ, (unsigned long long)s_rare[0]);
+    if (s_rare[1]) atomicAdd(P.stats + ST_SLOTS, (unsigned long long)s_rare[1]);
+  }
   if (lane == 0) {
     if (a[0]) atomicAdd(P.stats + ST_SAMPLES, a[0]);
     if (a[1]) atomicAdd(P.stats + ST_HITS, a[1]);
@@ -635,9 +652,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
       atomicAdd(P.stats + ST_MISSES, a[3]);
       atomicAdd(P.stats + ST_DIRECT, a[3]);
     }
-    if (a[4]) atomicAdd(P.stats + ST_REQ, a[4]);
-    if (a[5]) atomicAdd(P.stats + ST_SLOTS, a[5]);
-    if (a[6]) atomicAdd(P.stats + ST_SKIPPED, a[6]);
+    if (a[4]) atomicAdd(P.stats + ST_SKIPPED, a[4]);
   }
 }
 

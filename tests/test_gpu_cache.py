@@ -90,6 +90,19 @@ def test_cached_replacement_under_pressure():
     assert sum(h["evictions"] for h in hist) > 0
 
 
+@pytest.mark.parametrize("brick,storage,slots,n_req", [(16, "fp32", 24, 12), (16, "fp16", 24, 12),
+                                                        (4, "fp32", 900, 300), (6, "fp32", 400, 120)],
+                         ids=["b16", "b16-fp16", "b4", "b6"])
+def test_cached_brick_sizes_state_bit_exact(brick, storage, slots, n_req):
+    # the marching kernel is specialised for 8^3 and 16^3 bricks; other
+    # sizes (a power of two, and 6 with its exact division) take the generic
+    # instantiation
+    _, _, hist, worst = _run(4, brick=brick, storage=storage, slots=slots, n_req=n_req,
+                             check_pixels=2e-2 if storage == "fp16" else 2e-3)
+    assert sum(h["bricks_decoded"] for h in hist) > 0
+    assert sum(h["hits"] for h in hist) > 0
+
+
 def test_cached_orbit_ranking_off():
     _run(4, ranking=0)
 
