@@ -60,7 +60,7 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one marching-kernel launch on the default
 # orbit configuration, from one ncu capture of the current kernel (frame 91);
 # a workload or option without such a capture reports null.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {"orbit": 436.3e6}
 # path-tracing light: a directional light from above-front, dim blue ambient
 PT_OPTS = dict(light_dir=(0.3, -1.0, -0.4), light=(3.0, 3.0, 3.0), ambient=(0.05, 0.06, 0.08),
                max_bounces=3)
@@ -352,7 +352,9 @@ def run_gpu(args, wl):
                    "lag": args.lag,
                    "page_tables": (f"two-level, pages of {args.page}^3 bricks, {args.n_pages} page slots"
                                    if args.page else "flat"),
-                   "renderer": "path tracing (delta tracking)" if args.pt else "ray marching",
+                   "renderer": (("path tracing (delta tracking, %s majorants)"
+                                 % ("local macro-cell" if args.macro else "global"))
+                                if args.pt else "ray marching"),
                    "timed_frames": [args.warmup, last_f],
                    "l2": "flushed (256 MiB write) before every timed frame",
                    "parallelism": f"replicas x{world}"},
@@ -643,7 +645,8 @@ def main():
     ap.add_argument("--lag", type=int, default=1, choices=[1, 2],
                     help="frames from a brick request to its use (2: decode on a second stream)")
     ap.add_argument("--macro", type=int, default=0,
-                    help="macro-cell edge for empty-space skipping (0 = off)")
+                    help="macro-cell edge (0 = off): empty-space skipping when ray marching, "
+                         "local majorants when path tracing")
     ap.add_argument("--macro-min-level", type=int, default=0,
                     help="finest LoD whose voxels enter the macro-cell ranges")
     ap.add_argument("--graph", type=int, default=0, choices=[0, 1],

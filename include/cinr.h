@@ -373,8 +373,8 @@ typedef struct {
   const float* field_dev;
 } cinr_macro_desc;
 
-/* Device bytes of a macro-cell structure: 8 bytes of range and 1 byte of
- * skip flag per cell. */
+/* Device bytes of a macro-cell structure: 8 bytes of range, 4 bytes of
+ * majorant and 1 byte of skip flag per cell. */
 int cinr_macro_bytes(const int dims[3], int cell, size_t* bytes);
 
 /* Builds the ranges in dev_mem (enqueued on `stream`; FROM_RANGES copies
@@ -391,16 +391,40 @@ int cinr_macro_ranges(cinr_macro_t m, float* host_out, size_t n,
 int cinr_macro_skip_flags(cinr_macro_t m, uint8_t* host_out, size_t n,
                           cinr_stream_t stream);
 
-/* Recomputes the skip flags for `tf` (one kernel, enqueued on `stream`). */
+/* Copies the majorants of the last applied transfer function (1 float per
+ * cell, x fastest) to host memory; synchronises `stream`.  A cell's
+ * majorant is the largest extinction among the TF entries of the skip rule
+ * (floor(X(lo - 2^-20)) .. floor(X(hi + 2^-20)) + 1): it bounds the
+ * extinction of every value in the cell's range and is 0 exactly for
+ * transparent cells.  Before the first cinr_macro_apply_tf all are 0. */
+int cinr_macro_majorants(cinr_macro_t m, float* host_out, size_t n,
+                         cinr_stream_t stream);
+
+/* Recomputes the skip flags and the majorants for `tf` (one kernel,
+ * enqueued on `stream`). */
 int cinr_macro_apply_tf(cinr_macro_t m, const cinr_tf* tf,
                         cinr_stream_t stream);
 
 int cinr_destroy_macro(cinr_macro_t m);
 
 /* Attaches m (NULL detaches) to the renderer: every following frame
- * (cinr_render_frame, cinr_render_frame_host, cinr_render_field) first
- * applies its transfer function to m (one extra kernel) and skips the
- * samples of transparent cells.  m's dims must equal the renderer's dims. */
+ * (cinr_render_frame, cinr_render_frame_host, cinr_render_field,
+ * cinr_render_frame_pt) first applies its transfer function to m (one extra
+ * kernel).  Ray marching then skips the samples of transparent cells.  Path
+ * tracing with sigma_max <= 0 then tracks with local majorants (Sec. 5.2:
+ * each cell's largest opacity sets the sampling rate of the rays through
+ * it): a free flight draws its optical depth -ln(1-u) once and spends it
+ * cell by cell along a 3D DDA over the cells, a tentative collision in a
+ * cell with majorant m is real with probability sigma/m and ratio tracking
+ * multiplies by 1 - sigma/m; cells with majorant 0 are crossed without a
+ * lookup.  The walk's arithmetic (binary32, in this order): entry at p =
+ * o + t d: x = clamp01((p + h) (1/e)), pv = x dims, cell c = min(floor(pv)
+ * / cell, cells - 1), dv = (d (1/e)) dims; dv > 0: t_max = t + ((c+1) cell
+ * - pv)/dv, t_delta = cell/dv; dv < 0: t_max = t + (c cell - pv)/dv,
+ * t_delta = cell/(-dv); step: t_exit = min(t_max x, y, z, t1), the axis of
+ * the smallest t_max (x before y before z) moves; in a cell with m > 0 the
+ * collision is at t + tau/m if that precedes t_exit, else tau = max(tau -
+ * m (t_exit - t), 0).  m's dims must equal the renderer's dims. */
 int cinr_renderer_set_macro(cinr_renderer_t r, cinr_macro_t m);
 
 /* Allocation-free uncached render.  The paper has no counterpart: this is a

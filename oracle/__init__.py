@@ -70,7 +70,8 @@ class PtOpts(C.Structure):
 
 
 class Macro(C.Structure):
-    _fields_ = [("cell", C.c_int), ("dims", C.c_int * 3), ("skip", C.POINTER(C.c_uint8))]
+    _fields_ = [("cell", C.c_int), ("dims", C.c_int * 3), ("skip", C.POINTER(C.c_uint8)),
+                ("major", C.POINTER(C.c_float))]
 
 
 class Stats(C.Structure):
@@ -142,6 +143,9 @@ _SIGS = {
                                     _fp]),
     "orc_macro_ranges_field": (None, [_fp, _ip, C.c_int, _fp]),
     "orc_macro_skip": (None, [_fp, C.c_long, _dp, _P(C.c_uint8)]),
+    "orc_macro_majorant": (None, [_fp, C.c_long, _dp, _fp]),
+    "orc_pt_walk_test": (C.c_int, [C.c_void_p, _ip, _fp, _fp, C.c_float, C.c_float, _fp, C.c_int,
+                                   _fp, _fp]),
     "orc_macro_cell_of": (C.c_long, [_P(Macro), _ip, _fp]),
     "orc_cache_set_macro": (None, [C.c_void_p, C.c_void_p]),
     "orc_neg_log1m": (C.c_float, [C.c_float]),
@@ -294,13 +298,42 @@ def macro_skip(ranges, tf):
     return out
 
 
-def macro(vol, cell, skip) -> Macro:
-    """Skip-flag structure for march_opts(macro=...) / Cache.render(macro=...)."""
+def macro_majorant(ranges, tf):
+    """Per-cell extinction majorant under tf (0 exactly where the skip rule
+    marks the cell transparent); float32 [cells]."""
+    r, rp = _f(ranges)
+    tfa, tfp = _d(tf)
+    n = r.size // 2
+    out = np.zeros(n, np.float32)
+    lib().orc_macro_majorant(rp, n, tfp, out.ctypes.data_as(_fp))
+    return out
+
+
+def macro(vol, cell, skip, major=None) -> Macro:
+    """Macro-cell structure for march_opts(macro=...) / Cache.render(macro=...)
+    / Cache.render_pt(macro=...): skip flags, and per-cell majorants (or None)
+    for the path tracer's local-majorant tracking."""
     sk = np.ascontiguousarray(skip, dtype=np.uint8)
+    mj = None if major is None else np.ascontiguousarray(major, dtype=np.float32)
     m = Macro(int(cell), (C.c_int * 3)(*macro_dims(vol, cell)),
-              sk.ctypes.data_as(C.POINTER(C.c_uint8)))
-    m._keep = sk
+              sk.ctypes.data_as(C.POINTER(C.c_uint8)),
+              mj.ctypes.data_as(C.POINTER(C.c_float)) if mj is not None else None)
+    m._keep = (sk, mj)
     return m
+
+
+def pt_walk_test(m: Macro, vol, o, d, t0, t1, taus):
+    """Tentative collisions (t, majorant) of successive free flights of
+    optical depths taus along o + t d through the cells' majorants."""
+    v, vp = _i3(vol)
+    oa, op = _f(np.asarray(o, np.float32).reshape(3))
+    da, dp = _f(np.asarray(d, np.float32).reshape(3))
+    ta, tp = _f(np.asarray(taus, np.float32).reshape(-1))
+    tout = np.zeros(ta.size, np.float32)
+    mout = np.zeros(ta.size, np.float32)
+    n = lib().orc_pt_walk_test(C.cast(C.pointer(m), C.c_void_p), vp, op, dp, float(t0), float(t1), tp,
+                               ta.size, tout.ctypes.data_as(_fp), mout.ctypes.data_as(_fp))
+    return tout[:n], mout[:n]
 
 
 def macro_cell_of(m: Macro, vol, x):
@@ -518,14 +551,19 @@ class Cache:
             lib().orc_cache_set_macro(self.h, None)
         return out, st.as_dict()
 
-    def render_pt(self, cam: Camera, tf, pt: PtOpts, window=None):
-        """One path-traced frame through the cache."""
+    def render_pt(self, cam: Camera, tf, pt: PtOpts, window=None, macro=None):
+        """One path-traced frame through the cache; macro with majorants
+        switches delta and ratio tracking to the cells' local majorants."""
         px0, py0, pw, ph = window if window is not None else (0, 0, cam.width, cam.height)
         tfa, tfp = _d(tf)
         out = np.zeros((ph, pw, 4), np.float64)
         st = Stats()
-        lib().orc_render_pt_cached(self.h, C.byref(cam), tfp, C.byref(pt), px0, py0, pw, ph,
-                                   out.ctypes.data_as(_dp), C.byref(st))
+        lib().orc_cache_set_macro(self.h, C.cast(C.pointer(macro), C.c_void_p) if macro else None)
+        try:
+            lib().orc_render_pt_cached(self.h, C.byref(cam), tfp, C.byref(pt), px0, py0, pw, ph,
+                                       out.ctypes.data_as(_dp), C.byref(st))
+        finally:
+            lib().orc_cache_set_macro(self.h, None)
         return out, st.as_dict()
 
     def dump(self, what):

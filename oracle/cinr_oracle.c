@@ -625,6 +625,29 @@ void orc_macro_skip(const float* ranges, long n_cells, const double* tf,
   }
 }
 
+/* Majorant of a cell for delta tracking (Sec. 5.2: the largest opacity a
+ * cell's value range reaches under the current TF sets the sampling rate of
+ * rays through it; Sec. 5.1: Woodcock tracking samples tentative collisions
+ * at the rate of a majorant of the extinction).  The entries a sample of
+ * the cell can read are those of the skip rule, floor(X(lo - 2^-20)) ..
+ * floor(X(hi + 2^-20)) + 1, so the largest of their extinctions bounds the
+ * extinction of every such sample; it is 0 exactly for the cells the skip
+ * rule marks transparent. */
+void orc_macro_majorant(const float* ranges, long n_cells, const double* tf,
+                        float* major) {
+  const float margin = 9.5367431640625e-07f; /* 2^-20 */
+  for (long c = 0; c < n_cells; ++c) {
+    float lo = clamp01(ranges[2 * c] - margin);
+    float hi = clamp01(ranges[2 * c + 1] + margin);
+    int i0 = (int)floorf(lo * 255.0f);
+    int i1 = (int)floorf(hi * 255.0f) + 1;
+    if (i1 > 255) i1 = 255;
+    float m = 0.0f;
+    for (int i = i0; i <= i1; ++i) m = fmaxf(m, (float)tf[i * 4 + 3]);
+    major[c] = m;
+  }
+}
+
 void orc_macro_ranges_field(const float* field, const int dims[3], int cell,
                             float* ranges) {
   int md[3];
@@ -1541,6 +1564,115 @@ static void pt_point(const orc_camera* cam, const float e[3], const float h[3],
   *dist = sqrtf(s2);
 }
 
+/* READING (local majorants): Sec. 5.2 says each macro cell's largest
+ * opacity under the TF sets the sampling rate of rays through that cell;
+ * for Woodcock tracking that rate is the majorant.  With a macro-cell
+ * structure carrying majorants, a free flight draws its optical depth
+ * tau = -ln(1-u) once and spends it along the ray cell by cell (a 3D DDA
+ * over the cells): in a cell with majorant m entered at t and left at t_e,
+ * the tentative collision is at t + tau/m when that lies before t_e,
+ * otherwise tau -= m (t_e - t) and the flight enters the next cell.  Cells
+ * with m = 0 are crossed without a lookup.  A tentative collision at value v
+ * is real with probability sigma(v)/m of its cell, and ratio tracking
+ * multiplies by 1 - sigma(v)/m.  All of it binary32 in this order:
+ *   entry: p = o + t d, x = clamp01((p + h) (1/e)), pv = x V, cell c =
+ *          min(floor(pv) / N, dims - 1); dv = (d (1/e)) V per axis;
+ *          dv > 0: t_max = t + ((c+1) N - pv)/dv, t_delta = N/dv;
+ *          dv < 0: t_max = t + (c N - pv)/dv, t_delta = N/(-dv);
+ *          dv = 0: both infinite;
+ *   step:  t_e = min(t_max_x, t_max_y, t_max_z, t1); the axis of the
+ *          smallest t_max (x before y before z on ties) moves one cell,
+ *          t_max += t_delta; leaving the grid ends the flight. */
+typedef struct {
+  const orc_macro* m;
+  int c[3], step[3], live;
+  float tmax[3], tdelta[3];
+} pt_walk;
+
+static void walk_init(pt_walk* w, const orc_macro* m, const int vol[3],
+                      const float e[3], const float h[3], const float o[3],
+                      const float d[3], float t) {
+  w->m = m;
+  w->live = 1;
+  float N = (float)m->cell;
+  for (int a = 0; a < 3; ++a) {
+    float inv_e = 1.0f / e[a];
+    float p = o[a] + t * d[a];
+    float num = p + h[a];
+    float x = clamp01(num * inv_e);
+    float pv = x * (float)vol[a];
+    int ci = (int)floorf(pv) / m->cell;
+    if (ci > m->dims[a] - 1) ci = m->dims[a] - 1;
+    w->c[a] = ci;
+    float dv = (d[a] * inv_e) * (float)vol[a];
+    if (dv > 0.0f) {
+      w->step[a] = 1;
+      w->tmax[a] = t + ((float)((ci + 1) * m->cell) - pv) / dv;
+      w->tdelta[a] = N / dv;
+    } else if (dv < 0.0f) {
+      w->step[a] = -1;
+      w->tmax[a] = t + ((float)(ci * m->cell) - pv) / dv;
+      w->tdelta[a] = N / -dv;
+    } else {
+      w->step[a] = 0;
+      w->tmax[a] = INFINITY;
+      w->tdelta[a] = INFINITY;
+    }
+  }
+}
+
+/* Spends optical depth tau from *t: 1 with the tentative collision in *t and
+ * its cell's majorant in *maj, 0 when t1 (or the grid's end) comes first. */
+static int walk_flight(pt_walk* w, float tau, float* t, float t1, float* maj) {
+  const orc_macro* m = w->m;
+  float tt = *t;
+  int guard = 3 * (m->dims[0] + m->dims[1] + m->dims[2]) + 8;
+  while (w->live && guard-- > 0) {
+    long cell = ((long)w->c[2] * m->dims[1] + w->c[1]) * m->dims[0] + w->c[0];
+    float mj = m->major[cell];
+    float te = fminf(fminf(fminf(w->tmax[0], w->tmax[1]), w->tmax[2]), t1);
+    if (mj > 0.0f) {
+      float tc = tt + tau / mj;
+      if (tc < te) {
+        *t = tc;
+        *maj = mj;
+        return 1;
+      }
+      tau = fmaxf(tau - mj * (te - tt), 0.0f);
+    }
+    tt = te;
+    if (!(tt < t1)) break;
+    int a = w->tmax[0] <= w->tmax[1] ? (w->tmax[0] <= w->tmax[2] ? 0 : 2)
+                                     : (w->tmax[1] <= w->tmax[2] ? 1 : 2);
+    w->c[a] += w->step[a];
+    w->tmax[a] = w->tmax[a] + w->tdelta[a];
+    if (w->c[a] < 0 || w->c[a] >= m->dims[a]) w->live = 0;
+  }
+  *t = t1;
+  return 0;
+}
+
+/* Test hook: successive flights of the given optical depths along one ray;
+ * returns the number of tentative collisions (t_out, maj_out per flight). */
+int orc_pt_walk_test(const orc_macro* m, const int vol[3], const float o[3],
+                     const float d[3], float t0, float t1, const float* taus,
+                     int n_taus, float* t_out, float* maj_out) {
+  float e[3], h[3];
+  box_extent(vol, e, h);
+  pt_walk w;
+  walk_init(&w, m, vol, e, h, o, d, t0);
+  float t = t0;
+  int n = 0;
+  for (int i = 0; i < n_taus; ++i) {
+    float mj = 0.0f;
+    if (!walk_flight(&w, taus[i], &t, t1, &mj)) break;
+    t_out[n] = t;
+    maj_out[n] = mj;
+    ++n;
+  }
+  return n;
+}
+
 static void pt_path(pt_ctx* ctx, const orc_camera* cam, const int vol[3],
                     const orc_march_opts* mo, const double* tf,
                     const orc_pt_opts* pt, const float ls[3], float sbar,
@@ -1551,9 +1683,11 @@ static void pt_path(pt_ctx* ctx, const orc_camera* cam, const int vol[3],
   out[3] = 0.0;
   float o[3], d[3], t0, t1;
   if (!orc_ray(cam, vol, px, py, o, d, &t0, &t1)) return;
-  (void)mo;
+  const orc_macro* mac =
+      (mo->macro && mo->macro->major && !(pt->sigma_max > 0.0f)) ? mo->macro : NULL;
   float e[3], h[3];
   box_extent(vol, e, h);
+  pt_walk W;
   uint64_t key = ((uint64_t)fseed << 32) | (uint64_t)pixel;
   uint32_t rs = orc_ray_seed(fseed, pixel);
   float inv = sbar > 0.0f ? 1.0f / sbar : 0.0f;
@@ -1563,10 +1697,16 @@ static void pt_path(pt_ctx* ctx, const orc_camera* cam, const int vol[3],
     int hit = 0;
     float t = t0, p[3] = {0, 0, 0};
     double v = 0.0;
-    for (int step = 0; sbar > 0.0f && step < PT_MAX_STEPS; ++step) {
+    if (mac) walk_init(&W, mac, vol, e, h, o, d, t0);
+    for (int step = 0; (mac || sbar > 0.0f) && step < PT_MAX_STEPS; ++step) {
       float u = orc_pt_uniform(key, j++);
-      t = t + orc_neg_log1m(u) * inv;
-      if (!(t < t1)) break;
+      float maj = sbar;
+      if (mac) {
+        if (!walk_flight(&W, orc_neg_log1m(u), &t, t1, &maj)) break;
+      } else {
+        t = t + orc_neg_log1m(u) * inv;
+        if (!(t < t1)) break;
+      }
       float x[3], dist;
       pt_point(cam, e, h, o, d, t, p, x, &dist);
       v = pt_lookup(ctx, cam, x, dist, orc_sample_state(rs, k), pixel, k, st);
@@ -1574,7 +1714,7 @@ static void pt_path(pt_ctx* ctx, const orc_camera* cam, const int vol[3],
       double ev[4];
       orc_tf_lookup(tf, v, ev);
       float u2 = orc_pt_uniform(key, j++);
-      if ((double)u2 * (double)sbar < ev[3]) {
+      if ((double)u2 * (double)maj < ev[3]) {
         hit = 1;
         break;
       }
@@ -1590,17 +1730,23 @@ static void pt_path(pt_ctx* ctx, const orc_camera* cam, const int vol[3],
     /* next-event estimation: shadow transmittance by ratio tracking */
     float ts1 = box_exit(h, p, ls), ts = 0.0f;
     double Tr = 1.0;
-    for (int step = 0; sbar > 0.0f && step < PT_MAX_STEPS; ++step) {
+    if (mac) walk_init(&W, mac, vol, e, h, p, ls, 0.0f);
+    for (int step = 0; (mac || sbar > 0.0f) && step < PT_MAX_STEPS; ++step) {
       float u = orc_pt_uniform(key, j++);
-      ts = ts + orc_neg_log1m(u) * inv;
-      if (!(ts < ts1)) break;
+      float maj = sbar;
+      if (mac) {
+        if (!walk_flight(&W, orc_neg_log1m(u), &ts, ts1, &maj)) break;
+      } else {
+        ts = ts + orc_neg_log1m(u) * inv;
+        if (!(ts < ts1)) break;
+      }
       float pq[3], x[3], dist;
       pt_point(cam, e, h, p, ls, ts, pq, x, &dist);
       double v2 = pt_lookup(ctx, cam, x, dist, orc_sample_state(rs, k), pixel, k, st);
       ++k;
       double ev[4];
       orc_tf_lookup(tf, v2, ev);
-      Tr *= 1.0 - ev[3] / (double)sbar;
+      Tr *= 1.0 - ev[3] / (double)maj;
     }
     for (int q = 0; q < 3; ++q)
       L[q] += beta[q] * (double)pt->light[q] * Tr / (4.0 * ORC_PI);

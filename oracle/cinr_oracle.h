@@ -71,6 +71,8 @@ typedef struct orc_macro {
   int cell;            /* edge in LoD-0 voxels */
   int dims[3];         /* cells per axis */
   const uint8_t* skip; /* one flag per cell, x fastest */
+  const float* major;  /* per-cell extinction majorant for path tracing
+                          (orc_macro_majorant), NULL = the TF's maximum */
 } orc_macro;
 
 typedef struct {
@@ -156,6 +158,11 @@ void orc_macro_ranges_field(const float* field, const int dims[3], int cell,
 void orc_macro_skip(const float* ranges, long n_cells, const double* tf,
                     uint8_t* skip);
 long orc_macro_cell_of(const orc_macro* m, const int vol[3], const float x[3]);
+void orc_macro_majorant(const float* ranges, long n_cells, const double* tf,
+                        float* major);
+int orc_pt_walk_test(const orc_macro* m, const int vol[3], const float o[3],
+                     const float d[3], float t0, float t1, const float* taus,
+                     int n_taus, float* t_out, float* maj_out);
 
 /* ---- multi-resolution brick cache (Sec. 4.3) ---- */
 typedef struct orc_cache orc_cache;

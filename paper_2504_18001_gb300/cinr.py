@@ -133,6 +133,7 @@ _SIGS = {
     "cinr_create_macro": [_P(cinr_macro_desc), _vp, C.c_size_t, _vp, _P(_vp)],
     "cinr_macro_ranges": [_vp, _vp, C.c_size_t, _vp],
     "cinr_macro_skip_flags": [_vp, _vp, C.c_size_t, _vp],
+    "cinr_macro_majorants": [_vp, _vp, C.c_size_t, _vp],
     "cinr_macro_apply_tf": [_vp, _vp, _vp],
     "cinr_destroy_macro": [_vp],
     "cinr_renderer_set_macro": [_vp, _vp],
@@ -362,6 +363,12 @@ class Macro:
         out = np.zeros(self.n, np.uint8)
         check(lib().cinr_macro_skip_flags(self.h, C.c_void_p(out.ctypes.data), out.size,
                                           _stream(stream)), "cinr_macro_skip_flags")
+        return out
+
+    def majorants(self, stream=None):
+        out = np.zeros(self.n, np.float32)
+        check(lib().cinr_macro_majorants(self.h, C.c_void_p(out.ctypes.data), out.size,
+                                         _stream(stream)), "cinr_macro_majorants")
         return out
 
     def __del__(self):

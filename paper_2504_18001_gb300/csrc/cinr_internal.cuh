@@ -161,6 +161,7 @@ __device__ __forceinline__ uint32_t pt_entry_key(const CacheDev& c, uint32_t key
 // skip == nullptr turns skipping off.  Cells are 2^shift LoD-0 voxels wide.
 struct MacroDev {
   const uint8_t* skip;
+  const float* major;  // per-cell extinction majorant (path tracing); nullptr: global
   int shift;
   int dims[3];
 };
@@ -602,10 +603,12 @@ struct cinr_macro_s {
   size_t n;        // cells
   float* ranges;   // 2 per cell: min, max (x fastest)
   uint8_t* skip;   // 1 per cell
+  float* major;    // 1 per cell: largest extinction the cell's range reaches
   int device;
   cinr::MacroDev dev() const {
     cinr::MacroDev m;
     m.skip = skip;
+    m.major = major;
     m.shift = shift;
     for (int a = 0; a < 3; ++a) m.dims[a] = dims[a];
     return m;

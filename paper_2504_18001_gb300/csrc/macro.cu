@@ -188,23 +188,43 @@ __global__ void macro_decode(uint32_t* enc, unsigned long long n) {
 
 // Skip rule: entries floor(X(lo - 2^-20)) .. floor(X(hi + 2^-20)) + 1 of
 // the TF (X(v) = clamp(v,0,1)*255 in binary32) all have zero extinction;
-// nz[i] = number of entries below i with non-zero extinction.
+// nz[i] = number of entries below i with non-zero extinction.  The cell's
+// majorant (Sec. 5.2's largest opacity of the cell, the tracking rate of
+// the path tracer) is the largest extinction over the same entries: a
+// range maximum from a sparse table of the 256 extinctions in shared
+// memory (level k holds the maxima of 2^k consecutive entries).
 struct SkipParams {
   const float* ranges;
   uint8_t* skip;
+  float* major;
   unsigned long long n;
   uint32_t nz[257];
+  float ext[256];
 };
 
-__global__ void macro_skip_kernel(const __grid_constant__ SkipParams p) {
+constexpr int kSkipThreads = 256;
+
+__global__ void __launch_bounds__(kSkipThreads) macro_skip_kernel(const __grid_constant__ SkipParams p) {
+  __shared__ float st[9][256];
+  const int t = threadIdx.x;
+  st[0][t] = p.ext[t];
+  __syncthreads();
+#pragma unroll 1
+  for (int k = 1; k < 9; ++k) {
+    const int j = t + (1 << (k - 1));
+    st[k][t] = fmaxf(st[k - 1][t], st[k - 1][j < 256 ? j : 255]);
+    __syncthreads();
+  }
   const float margin = 9.5367431640625e-07f;  // 2^-20
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < p.n;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + t; i < p.n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const float lo = clamp01(f_sub(p.ranges[2 * i], margin));
     const float hi = clamp01(f_add(p.ranges[2 * i + 1], margin));
     const int i0 = (int)floorf(f_mul(lo, 255.0f));
     const int i1 = min((int)floorf(f_mul(hi, 255.0f)) + 1, 255);
     p.skip[i] = p.nz[i1 + 1] == p.nz[i0] ? 1 : 0;
+    const int k = 31 - __clz(i1 - i0 + 1);
+    p.major[i] = fmaxf(st[k][i0], st[k][i1 - (1 << k) + 1]);
   }
 }
 
@@ -245,6 +265,7 @@ int check_geom(const int dims[3], int cell, int* shift, int mdims[3], size_t* n)
 
 struct MacroLayout {
   float* ranges;
+  float* major;
   uint8_t* skip;
   size_t bytes;
 };
@@ -253,6 +274,7 @@ MacroLayout mlayout(size_t n, void* base) {
   Carver c(base);
   MacroLayout L;
   L.ranges = c.take<float>(2 * n);
+  L.major = c.take<float>(n);
   L.skip = c.take<uint8_t>(n);
   L.bytes = align_up(c.off, 256);
   return L;
@@ -336,10 +358,14 @@ int cinr_macro_apply(cinr_macro_s* m, const float (*rgba)[4], cudaStream_t s) {
   SkipParams p;
   p.ranges = m->ranges;
   p.skip = m->skip;
+  p.major = m->major;
   p.n = m->n;
   p.nz[0] = 0;
-  for (int i = 0; i < 256; ++i) p.nz[i + 1] = p.nz[i] + (rgba[i][3] != 0.0f ? 1u : 0u);
-  macro_skip_kernel<<<grid_for(m->n, 256), 256, 0, s>>>(p);
+  for (int i = 0; i < 256; ++i) {
+    p.nz[i + 1] = p.nz[i] + (rgba[i][3] != 0.0f ? 1u : 0u);
+    p.ext[i] = rgba[i][3];
+  }
+  macro_skip_kernel<<<grid_for(m->n, kSkipThreads), kSkipThreads, 0, s>>>(p);
   CINR_CK(cudaGetLastError());
   return CINR_OK;
 }
@@ -401,12 +427,14 @@ extern "C" int cinr_create_macro(const cinr_macro_desc* d, void* dev_mem, size_t
   m->n = n;
   m->ranges = L.ranges;
   m->skip = L.skip;
+  m->major = L.major;
   cudaGetDevice(&m->device);
   auto fail = [&](int code) {
     delete m;
     return code;
   };
   cudaError_t ce = cudaMemsetAsync(m->skip, 0, n, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(m->major, 0, n * sizeof(float), s);
   if (ce != cudaSuccess) return fail(cuda_error(ce, "cudaMemsetAsync"));
   if (d->source == CINR_MACRO_FROM_RANGES) {
     ce = cudaMemcpyAsync(m->ranges, d->ranges_host, 2 * n * sizeof(float), cudaMemcpyHostToDevice, s);
@@ -448,6 +476,15 @@ extern "C" int cinr_macro_skip_flags(cinr_macro_t m, uint8_t* host_out, size_t n
   if (n < m->n) return set_error(CINR_ERR_NOMEM, "need %zu bytes", m->n);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CINR_CK(cudaMemcpyAsync(host_out, m->skip, m->n, cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaStreamSynchronize(s));
+  return CINR_OK;
+}
+
+extern "C" int cinr_macro_majorants(cinr_macro_t m, float* host_out, size_t n, cinr_stream_t stream) {
+  if (!m || !host_out) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (n < m->n) return set_error(CINR_ERR_NOMEM, "need %zu floats", m->n);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CINR_CK(cudaMemcpyAsync(host_out, m->major, m->n * sizeof(float), cudaMemcpyDeviceToHost, s));
   CINR_CK(cudaStreamSynchronize(s));
   return CINR_OK;
 }

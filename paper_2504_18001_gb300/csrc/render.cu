@@ -785,6 +785,89 @@ struct PtCounts {
   uint32_t samp, hit, fb, miss, req, slot;
 };
 
+// Local-majorant tracking (Sec. 5.2: a macro cell's largest opacity sets
+// the sampling rate of the rays through it; for Woodcock tracking that rate
+// is the majorant).  A free flight spends its optical depth cell by cell
+// along a 3D DDA over the macro cells; every step below is binary32 in the
+// order the oracle takes it, so both sides place the same collisions.
+struct PtWalk {
+  int c0, c1, c2, s0, s1, s2;
+  float tm0, tm1, tm2, td0, td1, td2;
+  bool live;
+};
+
+__device__ __forceinline__ void walk_axis(const MacroDev& m, const CamDev& cam, int a, float o, float d,
+                                          float t, int& c, int& st, float& tm, float& td) {
+  const float p = f_add(o, f_mul(t, d));
+  const float x = clamp01(f_mul(f_add(p, cam.h[a]), cam.inv_e[a]));
+  const float pv = f_mul(x, (float)cam.vol[a]);
+  c = min((int)pv >> m.shift, m.dims[a] - 1);
+  const float dv = f_mul(f_mul(d, cam.inv_e[a]), (float)cam.vol[a]);
+  const float N = (float)(1 << m.shift);
+  if (dv > 0.0f) {
+    st = 1;
+    tm = f_add(t, f_div(f_sub((float)((c + 1) << m.shift), pv), dv));
+    td = f_div(N, dv);
+  } else if (dv < 0.0f) {
+    st = -1;
+    tm = f_add(t, f_div(f_sub((float)(c << m.shift), pv), dv));
+    td = f_div(N, -dv);
+  } else {
+    st = 0;
+    tm = INFINITY;
+    td = INFINITY;
+  }
+}
+
+// Enters the cell grid at the point o + t d.
+__device__ __forceinline__ void walk_init(PtWalk& w, const MacroDev& m, const CamDev& cam, const float o[3],
+                                          const float d[3], float t) {
+  walk_axis(m, cam, 0, o[0], d[0], t, w.c0, w.s0, w.tm0, w.td0);
+  walk_axis(m, cam, 1, o[1], d[1], t, w.c1, w.s1, w.tm1, w.td1);
+  walk_axis(m, cam, 2, o[2], d[2], t, w.c2, w.s2, w.tm2, w.td2);
+  w.live = true;
+}
+
+// Spends optical depth tau from t: true with the tentative collision in t
+// and its cell's majorant in maj; false when t1 (or the grid's end) comes
+// first.  Cells of majorant 0 are crossed without a collision.
+__device__ __forceinline__ bool walk_flight(PtWalk& w, const MacroDev& m, float tau, float& t, float t1,
+                                            float& maj) {
+  float tt = t;
+  int guard = 3 * (m.dims[0] + m.dims[1] + m.dims[2]) + 8;
+  while (w.live && guard-- > 0) {
+    const size_t cell = ((size_t)w.c2 * (size_t)m.dims[1] + (size_t)w.c1) * (size_t)m.dims[0] + (size_t)w.c0;
+    const float mj = __ldg(m.major + cell);
+    const float te = fminf(fminf(fminf(w.tm0, w.tm1), w.tm2), t1);
+    if (mj > 0.0f) {
+      const float tc = f_add(tt, f_div(tau, mj));
+      if (tc < te) {
+        t = tc;
+        maj = mj;
+        return true;
+      }
+      tau = fmaxf(f_sub(tau, f_mul(mj, f_sub(te, tt))), 0.0f);
+    }
+    tt = te;
+    if (!(tt < t1)) break;
+    if (w.tm0 <= w.tm1 && w.tm0 <= w.tm2) {
+      w.c0 += w.s0;
+      w.tm0 = f_add(w.tm0, w.td0);
+      w.live = w.c0 >= 0 && w.c0 < m.dims[0];
+    } else if (w.tm1 <= w.tm2) {
+      w.c1 += w.s1;
+      w.tm1 = f_add(w.tm1, w.td1);
+      w.live = w.c1 >= 0 && w.c1 < m.dims[1];
+    } else {
+      w.c2 += w.s2;
+      w.tm2 = f_add(w.tm2, w.td2);
+      w.live = w.c2 >= 0 && w.c2 < m.dims[2];
+    }
+  }
+  t = t1;
+  return false;
+}
+
 // One lookup of the path tracer: through the cache (stochastic LoD from
 // the distance to the eye, page-table walk with fallback, ranked request,
 // LRU stamp, true miss inferred in place and recorded) or, without a
@@ -865,7 +948,7 @@ __device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const flo
 // MISS: lookups that can end in direct inference (no cache, or a cache
 // without the coarsest-LoD preload).
 template <int IN, int H, bool CACHED, bool F16POOL, bool MISS>
-__global__ void __launch_bounds__(kFrameThreads, 6) pt_kernel(const __grid_constant__ FrameParams P) {
+__global__ void __launch_bounds__(kFrameThreads, 5) pt_kernel(const __grid_constant__ FrameParams P) {
   __shared__ float4 s_tf[256];
   __shared__ LevelGeo s_geo[kMaxLod];
   for (int i = threadIdx.x; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
@@ -907,18 +990,27 @@ __global__ void __launch_bounds__(kFrameThreads, 6) pt_kernel(const __grid_const
       float br = 1.f, bg = 1.f, bb = 1.f;
       Lr = Lg = Lb = 0.f;
       uint32_t j = 0, k = 0;
+      const bool local = P.mac.major != nullptr;  // per-cell majorants
+      PtWalk W;
       for (int b = 0;; ++b) {
         bool hit = false;
         float t = t0, p[3] = {0.f, 0.f, 0.f}, v = 0.f;
-        for (int step = 0; P.pt_sbar > 0.0f && step < kPtMaxSteps; ++step) {
-          t = f_add(t, f_mul(neg_log1m(pt_uniform(key, j++)), P.pt_inv));
-          if (!(t < t1)) break;
+        if (local) walk_init(W, P.mac, cam, o, d, t0);
+        for (int step = 0; (local || P.pt_sbar > 0.0f) && step < kPtMaxSteps; ++step) {
+          const float tau = neg_log1m(pt_uniform(key, j++));
+          float maj = P.pt_sbar;
+          if (local) {
+            if (!walk_flight(W, P.mac, tau, t, t1, maj)) break;
+          } else {
+            t = f_add(t, f_mul(tau, P.pt_inv));
+            if (!(t < t1)) break;
+          }
           float x[3], dist;
           pt_point(cam, o, d, t, p, x, dist);
           v = pt_value<IN, H, CACHED, F16POOL, MISS>(P, s_geo, x, dist, rseed, k, pixel, n);
           ++k;
           const float sig = tf_lookup(s_tf, v).w;
-          if (pt_uniform(key, j++) * P.pt_sbar < sig) {
+          if (pt_uniform(key, j++) * maj < sig) {
             hit = true;
             break;
           }
@@ -937,14 +1029,22 @@ __global__ void __launch_bounds__(kFrameThreads, 6) pt_kernel(const __grid_const
         // next-event estimation: shadow transmittance by ratio tracking
         const float ts1 = box_exit(cam, p, P.pt_ls);
         float ts = 0.f, Tr = 1.f;
-        for (int step = 0; P.pt_sbar > 0.0f && step < kPtMaxSteps; ++step) {
-          ts = f_add(ts, f_mul(neg_log1m(pt_uniform(key, j++)), P.pt_inv));
-          if (!(ts < ts1)) break;
+        if (local) walk_init(W, P.mac, cam, p, P.pt_ls, 0.f);
+        for (int step = 0; (local || P.pt_sbar > 0.0f) && step < kPtMaxSteps; ++step) {
+          const float tau = neg_log1m(pt_uniform(key, j++));
+          float maj = P.pt_sbar;
+          if (local) {
+            if (!walk_flight(W, P.mac, tau, ts, ts1, maj)) break;
+          } else {
+            ts = f_add(ts, f_mul(tau, P.pt_inv));
+            if (!(ts < ts1)) break;
+          }
           float pq[3], x[3], dist;
           pt_point(cam, p, P.pt_ls, ts, pq, x, dist);
           const float v2 = pt_value<IN, H, CACHED, F16POOL, MISS>(P, s_geo, x, dist, rseed, k, pixel, n);
           ++k;
-          Tr *= 1.0f - tf_lookup(s_tf, v2).w * P.pt_inv;
+          const float sig2 = tf_lookup(s_tf, v2).w;
+          Tr *= 1.0f - (local ? f_div(sig2, maj) : sig2 * P.pt_inv);
         }
         const float ne = Tr * 0.0795774715459476679f;  // 1 / (4 pi)
         Lr = fmaf(br * P.pt_light[0], ne, Lr);
@@ -1257,7 +1357,9 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
     }
     P.pt_bounces = pt->max_bounces;
   }
-  cinr_macro_s* mac = pt ? nullptr : r->macro;  // delta tracking does not skip cells
+  // ray marching skips transparent cells; path tracing with an automatic
+  // majorant tracks with the cells' local majorants
+  cinr_macro_s* mac = (pt && pt->sigma_max > 0.0f) ? nullptr : r->macro;
   if (mac) {
     for (int a = 0; a < 3; ++a)
       if (mac->vol[a] != r->o.dims[a]) return set_error(CINR_ERR_ARG, "macro-cell dims differ from renderer dims");

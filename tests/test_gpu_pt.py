@@ -122,3 +122,89 @@ def test_cached_pt_mixed_precision_converges_to_fp32():
         means.append(acc / 16)
     diff = np.abs(means[0] - means[1])
     assert diff[..., :3].mean() < 0.02 * max(1e-3, means[0][..., :3].mean()) + 2e-3
+
+
+def _gated_pt_tf(theta, c=30.0):
+    tf = np.zeros((256, 4), np.float32)
+    i0 = int(np.clip(theta, 0, 1) * 255) + 1
+    tf[i0:, :3] = (0.9, 0.8, 0.6)
+    tf[i0:, 3] = c
+    return tf
+
+
+def test_macro_majorants_match_oracle():
+    # skip flags and majorants of the apply-TF kernel (sparse-table range
+    # maximum) against the oracle's per-cell loop, bit for bit
+    from paper_2504_18001_gb300 import cinr
+    vol = (72, 40, 56)
+    rng = np.random.default_rng(8)
+    n = int(np.prod(O.macro_dims(vol, 8)))
+    lo = rng.uniform(-0.05, 1.0, n)
+    ranges = np.stack([lo, lo + rng.uniform(0, 0.4, n) ** 2], 1).astype(np.float32)
+    mac = cinr.Macro(vol, 8, ranges=ranges)
+    for seed in (2, 5):
+        tf = S.tf_ramps(seed)
+        tf[:40, 3] = 0.0
+        mac.apply_tf(tf)
+        assert np.array_equal(mac.skip_flags(), O.macro_skip(ranges, tf.astype(np.float64)))
+        assert np.array_equal(mac.majorants(), O.macro_majorant(ranges, tf.astype(np.float64)))
+
+
+def _pt_macro_run(tf, frames, check_state):
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.INR_64
+    vol = (64, 64, 64)
+    table, w = scene(cfg)
+    inr = gpu_inr(cfg, table, w, vol=vol)
+    p = oracle_inr(cfg, table, w, vol=vol)
+    cache = cinr.Cache(inr, vol, pool_bytes=120 * 4000, brick=8, levels=3, n_req=40)
+    mo = O.march_opts(K=32, eps_T=0.0, seed=17)
+    oc = O.Cache(p, table, w, vol, 8, 3, 120, mo, n_req=40)
+    r = cinr.Renderer(40, 32, vol, K=32, eps_T=0.0, seed=17)
+    ranges = O.macro_ranges_inr(p, table, w, vol, 8, 3)
+    mac = cinr.Macro(vol, 8, ranges=ranges)
+    r.set_macro(mac)
+    tfd = tf.astype(np.float64)
+    omac = O.macro(vol, 8, O.macro_skip(ranges, tfd), O.macro_majorant(ranges, tfd))
+    gpt, opt = _pt_pair()
+    agree = total = 0
+    for f in range(frames):
+        cam = S.orbit_camera(5 * f, 40, 32, distance=1.7)
+        img, st = r.render_pt(inr, cam, tf, gpt, cache=cache)
+        ref, rst = oc.render_pt(ocam(cam), tfd, opt, macro=omac)
+        assert np.array_equal(mac.majorants(), omac._keep[1])
+        d = np.abs(img.cpu().numpy() - ref).max(axis=2)
+        agree += int((d < 1e-3 * max(1.0, np.abs(ref).max())).sum())
+        total += d.size
+        if check_state:
+            for k in ("samples", "hits", "fallback_hits", "true_misses", "bricks_requested",
+                      "bricks_decoded", "evictions"):
+                assert st[k] == rst[k], (f, k, st[k], rst[k])
+            for g, o in ((cinr.DUMP_PAGE_TABLE, O.DUMP_PT), (cinr.DUMP_STAMPS, O.DUMP_STAMP),
+                         (cinr.DUMP_RANK, O.DUMP_RANK), (cinr.DUMP_REQUESTS, O.DUMP_REQ)):
+                assert np.array_equal(cache.dump(g), oc.dump(o)), (f, g)
+        else:
+            assert abs(st["samples"] - rst["samples"]) <= 0.02 * rst["samples"] + 10
+    return agree, total
+
+
+def test_cached_pt_local_majorants_constant_extinction_state_bit_exact():
+    # every cell's majorant is the constant extinction: every tentative
+    # collision is real on both sides and the walk through the cells places
+    # the same collisions, so the cache state is bit-exact
+    agree, total = _pt_macro_run(S.tf_constant((0.9, 0.7, 0.5), 6.0), 3, check_state=True)
+    assert agree == total
+
+
+def test_cached_pt_local_majorants_gated_tf_paths_agree():
+    # transparent below a threshold: cells below it are crossed without a
+    # lookup; paths agree except where a collision decision sits within
+    # rounding of its threshold
+    cfg = S.INR_64
+    table, w = scene(cfg)
+    p = oracle_inr(cfg, table, w, vol=(64, 64, 64))
+    r = O.macro_ranges_inr(p, table, w, (64, 64, 64), 8, 3)
+    tf = _gated_pt_tf(float(np.median(r[:, 1])))
+    assert (O.macro_majorant(r, tf.astype(np.float64)) == 0).any()
+    agree, total = _pt_macro_run(tf, 3, check_state=False)
+    assert agree >= 0.98 * total, (agree, total)

@@ -646,6 +646,152 @@ def test_macro_skip_rule_sound_and_near_tight():
     assert 0 < skip.sum() < len(skip)
 
 
+def test_macro_majorant_bounds_every_value_and_is_zero_exactly_when_skipped():
+    # The majorant of a cell bounds the extinction at every value of its
+    # range (dense check through the oracle's TF lookup), is reached within
+    # one TF entry (plus the 2^-20 margin) of the range, and is 0 exactly for
+    # the cells the skip rule marks transparent.
+    rng = np.random.default_rng(5)
+    tf = np.zeros((256, 4), np.float64)
+    tf[60:90, 3] = rng.uniform(1.0, 9.0, 30).astype(np.float32)
+    tf[150:170, 3] = 4.0
+    tf[230, 3] = 11.0
+    lo = rng.uniform(-0.1, 1.0, 300)
+    hi = lo + rng.uniform(0.0, 0.3, 300) ** 2
+    ranges = np.stack([lo, hi], 1).astype(np.float32)
+    major = O.macro_majorant(ranges, tf)
+    skip = O.macro_skip(ranges, tf)
+    assert np.array_equal(major == 0.0, skip == 1)
+    pad = 2.0 ** -20 + 1.0 / 255 + 1e-9
+    for (a, b), m in zip(ranges.astype(np.float64), major):
+        vs = np.concatenate([[a, b], np.linspace(a, b, 2000)])
+        assert max(O.tf_lookup(tf, v)[3] for v in vs) <= m
+        ks = np.arange(256) / 255.0  # the values that read one entry exactly
+        wide = np.concatenate([np.linspace(a - pad, b + pad, 2000),
+                               ks[(ks >= a - pad) & (ks <= b + pad)]])
+        assert max(O.tf_lookup(tf, v)[3] for v in wide) >= m
+    assert 0 < skip.sum() < len(skip)
+
+
+def _cell_of_point(m_dims, cell, vol, o, d, t):
+    # macro cell of the point o + t d, in double precision
+    e = np.asarray(vol, np.float64) / max(vol)
+    x = np.clip((np.asarray(o) + t * np.asarray(d) + e / 2) / e, 0.0, 1.0)
+    c = np.minimum((x * np.asarray(vol)) // cell, np.asarray(m_dims) - 1).astype(int)
+    return (c[2] * m_dims[1] + c[1]) * m_dims[0] + c[0]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_pt_walk_spends_optical_depth_cell_by_cell(seed):
+    # Each free flight of optical depth tau ends where the integral of the
+    # cells' majorants along the ray since the previous collision reaches
+    # tau (brute-force quadrature in double); zero-majorant cells hold no
+    # collision, and the depth left after the last one exceeds the integral
+    # to the ray's exit.
+    rng = np.random.default_rng(seed)
+    vol, cell = (40, 24, 56), 8
+    dims = O.macro_dims(vol, cell)
+    n = int(np.prod(dims))
+    major = rng.uniform(2.0, 12.0, n).astype(np.float32)
+    major[rng.random(n) < 0.3] = 0.0
+    mac = O.macro(vol, cell, np.zeros(n, np.uint8), major)
+    cam = O.camera((1.1 - 0.3 * seed, 0.4, 1.7), (0.05, -0.02, 0.0), (0, 1, 0), 30.0, 16, 16, 0.5)
+    hit, o, d, t0, t1 = O.ray(cam, vol, 7 + seed, 9)
+    assert hit
+    taus = rng.exponential(1.0, 64).astype(np.float32)
+    ts, ms = O.pt_walk_test(mac, vol, o, d, t0, t1, taus)
+    assert len(ts) >= 3
+
+    def integral(a, b, steps=20000):
+        s = np.linspace(a, b, steps + 1)
+        mid = (s[:-1] + s[1:]) / 2
+        vals = np.array([major[_cell_of_point(dims, cell, vol, o, d, t)] for t in mid])
+        return float(vals.sum() * (b - a) / steps), vals
+
+    prev = t0
+    for i, (t, m) in enumerate(zip(ts, ms)):
+        assert prev <= t < t1
+        got, _ = integral(prev, float(t))
+        assert abs(got - taus[i]) < 2e-3 * max(1.0, taus[i]) + 0.02, (i, got, taus[i])
+        near = {major[_cell_of_point(dims, cell, vol, o, d, float(t) + dt)] for dt in (-1e-5, 0.0, 1e-5)}
+        assert m > 0 and m in near, (i, m, near)
+        prev = float(t)
+    if len(ts) < len(taus):
+        rest, _ = integral(prev, t1)
+        assert rest < taus[len(ts)] + 0.02
+
+
+def test_pt_local_majorants_transmittance_closed_form():
+    # Constant extinction c under per-cell majorants drawn from [c, 3c]
+    # (some equal to c): delta tracking stays unbiased, so the escape
+    # probability of a pixel's path is exp(-c L), as with the global
+    # majorant.
+    p, table, w, vol, cam = _pt_scene()
+    c = 2.5
+    tf = S.tf_constant((0.0, 0.0, 0.0), c).astype(np.float64)
+    cell = 8
+    n = int(np.prod(O.macro_dims(vol, cell)))
+    rng = np.random.default_rng(4)
+    major = (c * rng.uniform(1.0, 3.0, n)).astype(np.float32)
+    major[::3] = c
+    mac = O.macro(vol, cell, np.zeros(n, np.uint8), major)
+    pt = O.pt_opts(light=(0, 0, 0), ambient=(1, 1, 1), max_bounces=1)
+    mo = O.march_opts(seed=5, macro=mac)
+    px, py = 4, 3
+    hit, o, d, tn, tf_ = O.ray(cam, vol, px, py)
+    frames = 3000
+    acc = np.zeros(4)
+    samples = 0
+    for f in range(1, frames + 1):
+        img, st = O.render_pt_direct(p, table, w, cam, vol, mo, tf, pt, f, window=(px, py, 1, 1))
+        acc += img[0, 0]
+        samples += st["samples"]
+    mean = acc / frames
+    T = math.exp(-c * (tf_ - tn))
+    sd = math.sqrt(T * (1 - T) / frames)
+    assert abs(mean[0] - T) < 4 * sd
+    assert abs(mean[3] - (1 - T)) < 4 * sd
+    # more tentative collisions than real ones: the majorants exceed c
+    assert samples > frames * (1 - T) * 1.2
+
+
+def test_pt_cached_local_majorants_skip_empty_cells_and_stay_unbiased():
+    # A TF that is transparent below a threshold: cells whose range lies
+    # below it get majorant 0 and are crossed without lookups.  With the
+    # cache fully resident at every LoD (every sample a trilinear of the
+    # voxels the ranges bound), the frame means of local- and global-
+    # majorant tracking agree within their statistical error.
+    c0, cam, _, p, table, w, vol = _cache_scene(n_slots=700, n_req=700)
+    c1, *_ = _cache_scene(n_slots=700, n_req=700)
+    r = O.macro_ranges_inr(p, table, w, vol, 8, 3)
+    theta = float(np.median(r[:, 1]))
+    tf = np.zeros((256, 4), np.float64)
+    i0 = int(np.clip(theta, 0, 1) * 255) + 1
+    tf[i0:, :3] = 0.8
+    tf[i0:, 3] = 30.0
+    major = O.macro_majorant(r, tf)
+    assert (major == 0).sum() > 0
+    mac = O.macro(vol, 8, O.macro_skip(r, tf), major)
+    pt = O.pt_opts(max_bounces=2, ambient=(0.2, 0.2, 0.2))
+    win = (8, 8, 8, 8)
+    for cc in (c0, c1):  # warm-up: bring every requested brick in
+        for _ in range(6):
+            cc.render_pt(cam, tf, pt)
+    a0, a1, s0, s1 = [], [], 0, 0
+    for _ in range(150):
+        img0, st0 = c0.render_pt(cam, tf, pt, window=win)
+        img1, st1 = c1.render_pt(cam, tf, pt, window=win, macro=mac)
+        assert st0["true_misses"] == st1["true_misses"] == 0
+        a0.append(img0.mean(axis=(0, 1)))
+        a1.append(img1.mean(axis=(0, 1)))
+        s0 += st0["samples"]
+        s1 += st1["samples"]
+    a0, a1 = np.array(a0), np.array(a1)
+    se = np.sqrt(a0.var(axis=0) / len(a0) + a1.var(axis=0) / len(a1))
+    assert np.all(np.abs(a0.mean(axis=0) - a1.mean(axis=0)) < 4 * se + 1e-3)
+    assert s1 < s0
+
+
 def _blob_field(dims=(48, 40, 32)):
     z, y, x = np.meshgrid(*[(np.arange(d) + 0.5) / d for d in dims[::-1]], indexing="ij")
     r2 = (x - 0.45) ** 2 + (y - 0.55) ** 2 + (z - 0.5) ** 2
