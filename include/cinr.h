@@ -417,14 +417,16 @@ int cinr_destroy_macro(cinr_macro_t m);
  * cell by cell along a 3D DDA over the cells, a tentative collision in a
  * cell with majorant m is real with probability sigma/m and ratio tracking
  * multiplies by 1 - sigma/m; cells with majorant 0 are crossed without a
- * lookup.  The walk's arithmetic (binary32, in this order): entry at p =
- * o + t d: x = clamp01((p + h) (1/e)), pv = x dims, cell c = min(floor(pv)
- * / cell, cells - 1), dv = (d (1/e)) dims; dv > 0: t_max = t + ((c+1) cell
- * - pv)/dv, t_delta = cell/dv; dv < 0: t_max = t + (c cell - pv)/dv,
- * t_delta = cell/(-dv); step: t_exit = min(t_max x, y, z, t1), the axis of
- * the smallest t_max (x before y before z) moves; in a cell with m > 0 the
- * collision is at t + tau/m if that precedes t_exit, else tau = max(tau -
- * m (t_exit - t), 0).  m's dims must equal the renderer's dims. */
+ * lookup.  The walk's arithmetic (binary32, in this order): start at
+ * o + t d of a segment ending at t1, per axis p = o + t d, x = clamp01((p
+ * + h) (1/e)), pv = x dims, cell c = min(floor(pv) / cell, cells - 1),
+ * dv = (d (1/e)) dims, r = 1/dv; dv > 0: t_max = t + ((c+1) cell - pv) r,
+ * t_delta = cell r; dv < 0: t_max = t + (c cell - pv) r, t_delta = cell
+ * (-r); entering a cell: m, r_m = 1/m (0 for m = 0), t_exit = min(t_max
+ * x, y, z, t1); a flight with m > 0 and tau < dd = m (t_exit - t) collides
+ * at min(t + tau r_m, t_exit), else tau -= dd, t = t_exit and the axis of
+ * the smallest t_max (x before y before z) moves, t_max += t_delta.
+ * m's dims must equal the renderer's dims. */
 int cinr_renderer_set_macro(cinr_renderer_t r, cinr_macro_t m);
 
 /* Allocation-free uncached render.  The paper has no counterpart: this is a

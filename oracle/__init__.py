@@ -318,7 +318,7 @@ def macro(vol, cell, skip, major=None) -> Macro:
     m = Macro(int(cell), (C.c_int * 3)(*macro_dims(vol, cell)),
               sk.ctypes.data_as(C.POINTER(C.c_uint8)),
               mj.ctypes.data_as(C.POINTER(C.c_float)) if mj is not None else None)
-    m._keep = (sk, mj)
+    m.skip_flags, m.majorants = sk, mj  # the arrays the structure points to
     return m
 
 

@@ -1570,30 +1570,45 @@ static void pt_point(const orc_camera* cam, const float e[3], const float h[3],
  * structure carrying majorants, a free flight draws its optical depth
  * tau = -ln(1-u) once and spends it along the ray cell by cell (a 3D DDA
  * over the cells): in a cell with majorant m entered at t and left at t_e,
- * the tentative collision is at t + tau/m when that lies before t_e,
+ * the tentative collision lies at t + tau/m when tau < m (t_e - t),
  * otherwise tau -= m (t_e - t) and the flight enters the next cell.  Cells
  * with m = 0 are crossed without a lookup.  A tentative collision at value v
  * is real with probability sigma(v)/m of its cell, and ratio tracking
  * multiplies by 1 - sigma(v)/m.  All of it binary32 in this order:
- *   entry: p = o + t d, x = clamp01((p + h) (1/e)), pv = x V, cell c =
- *          min(floor(pv) / N, dims - 1); dv = (d (1/e)) V per axis;
- *          dv > 0: t_max = t + ((c+1) N - pv)/dv, t_delta = N/dv;
- *          dv < 0: t_max = t + (c N - pv)/dv, t_delta = N/(-dv);
+ *   start at o + t d (segment end t1): per axis p = o + t d,
+ *          x = clamp01((p + h) (1/e)), pv = x V, c = min(floor(pv) / N,
+ *          dims - 1), dv = (d (1/e)) V, r = 1/dv;
+ *          dv > 0: t_max = t + ((c+1) N - pv) r, t_delta = N r;
+ *          dv < 0: t_max = t + (c N - pv) r, t_delta = N (-r);
  *          dv = 0: both infinite;
- *   step:  t_e = min(t_max_x, t_max_y, t_max_z, t1); the axis of the
- *          smallest t_max (x before y before z on ties) moves one cell,
- *          t_max += t_delta; leaving the grid ends the flight. */
+ *   enter a cell: m = its majorant, r_m = 1/m (0 when m = 0),
+ *          t_e = min(t_max_x, t_max_y, t_max_z, t1);
+ *   flight from t: while m > 0 and tau >= dd = m (t_e - t): tau -= dd;
+ *          with tau < dd the collision is at min(t + tau r_m, t_e);
+ *          else t = t_e, the axis of the smallest t_max (x before y before
+ *          z on ties) moves one cell, t_max += t_delta, and the next cell
+ *          is entered; leaving the grid or reaching t1 ends the flight. */
 typedef struct {
   const orc_macro* m;
   int c[3], step[3], live;
   float tmax[3], tdelta[3];
+  float mj, rj, te, t1;
 } pt_walk;
+
+static void walk_enter(pt_walk* w) {
+  const orc_macro* m = w->m;
+  long cell = ((long)w->c[2] * m->dims[1] + w->c[1]) * m->dims[0] + w->c[0];
+  w->mj = m->major[cell];
+  w->rj = w->mj > 0.0f ? 1.0f / w->mj : 0.0f;
+  w->te = fminf(fminf(fminf(w->tmax[0], w->tmax[1]), w->tmax[2]), w->t1);
+}
 
 static void walk_init(pt_walk* w, const orc_macro* m, const int vol[3],
                       const float e[3], const float h[3], const float o[3],
-                      const float d[3], float t) {
+                      const float d[3], float t, float t1) {
   w->m = m;
   w->live = 1;
+  w->t1 = t1;
   float N = (float)m->cell;
   for (int a = 0; a < 3; ++a) {
     float inv_e = 1.0f / e[a];
@@ -1606,49 +1621,53 @@ static void walk_init(pt_walk* w, const orc_macro* m, const int vol[3],
     w->c[a] = ci;
     float dv = (d[a] * inv_e) * (float)vol[a];
     if (dv > 0.0f) {
+      float r = 1.0f / dv;
       w->step[a] = 1;
-      w->tmax[a] = t + ((float)((ci + 1) * m->cell) - pv) / dv;
-      w->tdelta[a] = N / dv;
+      w->tmax[a] = t + ((float)((ci + 1) * m->cell) - pv) * r;
+      w->tdelta[a] = N * r;
     } else if (dv < 0.0f) {
+      float r = 1.0f / dv;
       w->step[a] = -1;
-      w->tmax[a] = t + ((float)(ci * m->cell) - pv) / dv;
-      w->tdelta[a] = N / -dv;
+      w->tmax[a] = t + ((float)(ci * m->cell) - pv) * r;
+      w->tdelta[a] = N * -r;
     } else {
       w->step[a] = 0;
       w->tmax[a] = INFINITY;
       w->tdelta[a] = INFINITY;
     }
   }
+  walk_enter(w);
 }
 
 /* Spends optical depth tau from *t: 1 with the tentative collision in *t and
- * its cell's majorant in *maj, 0 when t1 (or the grid's end) comes first. */
-static int walk_flight(pt_walk* w, float tau, float* t, float t1, float* maj) {
+ * its cell's majorant in *maj, 0 when the segment's end (or the grid's)
+ * comes first. */
+static int walk_flight(pt_walk* w, float tau, float* t, float* maj) {
   const orc_macro* m = w->m;
   float tt = *t;
   int guard = 3 * (m->dims[0] + m->dims[1] + m->dims[2]) + 8;
   while (w->live && guard-- > 0) {
-    long cell = ((long)w->c[2] * m->dims[1] + w->c[1]) * m->dims[0] + w->c[0];
-    float mj = m->major[cell];
-    float te = fminf(fminf(fminf(w->tmax[0], w->tmax[1]), w->tmax[2]), t1);
-    if (mj > 0.0f) {
-      float tc = tt + tau / mj;
-      if (tc < te) {
-        *t = tc;
-        *maj = mj;
+    if (w->mj > 0.0f) {
+      float dd = w->mj * (w->te - tt); /* optical depth of the cell's stretch */
+      if (tau < dd) {
+        *t = fminf(tt + tau * w->rj, w->te);
+        *maj = w->mj;
         return 1;
       }
-      tau = fmaxf(tau - mj * (te - tt), 0.0f);
+      tau = tau - dd;
     }
-    tt = te;
-    if (!(tt < t1)) break;
+    tt = w->te;
+    if (!(tt < w->t1)) break;
     int a = w->tmax[0] <= w->tmax[1] ? (w->tmax[0] <= w->tmax[2] ? 0 : 2)
                                      : (w->tmax[1] <= w->tmax[2] ? 1 : 2);
     w->c[a] += w->step[a];
     w->tmax[a] = w->tmax[a] + w->tdelta[a];
-    if (w->c[a] < 0 || w->c[a] >= m->dims[a]) w->live = 0;
+    if (w->c[a] < 0 || w->c[a] >= m->dims[a])
+      w->live = 0;
+    else
+      walk_enter(w);
   }
-  *t = t1;
+  *t = w->t1;
   return 0;
 }
 
@@ -1660,12 +1679,12 @@ int orc_pt_walk_test(const orc_macro* m, const int vol[3], const float o[3],
   float e[3], h[3];
   box_extent(vol, e, h);
   pt_walk w;
-  walk_init(&w, m, vol, e, h, o, d, t0);
+  walk_init(&w, m, vol, e, h, o, d, t0, t1);
   float t = t0;
   int n = 0;
   for (int i = 0; i < n_taus; ++i) {
     float mj = 0.0f;
-    if (!walk_flight(&w, taus[i], &t, t1, &mj)) break;
+    if (!walk_flight(&w, taus[i], &t, &mj)) break;
     t_out[n] = t;
     maj_out[n] = mj;
     ++n;
@@ -1697,12 +1716,12 @@ static void pt_path(pt_ctx* ctx, const orc_camera* cam, const int vol[3],
     int hit = 0;
     float t = t0, p[3] = {0, 0, 0};
     double v = 0.0;
-    if (mac) walk_init(&W, mac, vol, e, h, o, d, t0);
+    if (mac) walk_init(&W, mac, vol, e, h, o, d, t0, t1);
     for (int step = 0; (mac || sbar > 0.0f) && step < PT_MAX_STEPS; ++step) {
       float u = orc_pt_uniform(key, j++);
       float maj = sbar;
       if (mac) {
-        if (!walk_flight(&W, orc_neg_log1m(u), &t, t1, &maj)) break;
+        if (!walk_flight(&W, orc_neg_log1m(u), &t, &maj)) break;
       } else {
         t = t + orc_neg_log1m(u) * inv;
         if (!(t < t1)) break;
@@ -1730,12 +1749,12 @@ static void pt_path(pt_ctx* ctx, const orc_camera* cam, const int vol[3],
     /* next-event estimation: shadow transmittance by ratio tracking */
     float ts1 = box_exit(h, p, ls), ts = 0.0f;
     double Tr = 1.0;
-    if (mac) walk_init(&W, mac, vol, e, h, p, ls, 0.0f);
+    if (mac) walk_init(&W, mac, vol, e, h, p, ls, 0.0f, ts1);
     for (int step = 0; (mac || sbar > 0.0f) && step < PT_MAX_STEPS; ++step) {
       float u = orc_pt_uniform(key, j++);
       float maj = sbar;
       if (mac) {
-        if (!walk_flight(&W, orc_neg_log1m(u), &ts, ts1, &maj)) break;
+        if (!walk_flight(&W, orc_neg_log1m(u), &ts, &maj)) break;
       } else {
         ts = ts + orc_neg_log1m(u) * inv;
         if (!(ts < ts1)) break;

@@ -793,6 +793,7 @@ struct PtCounts {
 struct PtWalk {
   int c0, c1, c2, s0, s1, s2;
   float tm0, tm1, tm2, td0, td1, td2;
+  float mj, rj, te, t1;  // current cell's majorant, its reciprocal, exit; segment end
   bool live;
 };
 
@@ -805,13 +806,15 @@ __device__ __forceinline__ void walk_axis(const MacroDev& m, const CamDev& cam, 
   const float dv = f_mul(f_mul(d, cam.inv_e[a]), (float)cam.vol[a]);
   const float N = (float)(1 << m.shift);
   if (dv > 0.0f) {
+    const float r = f_div(1.0f, dv);
     st = 1;
-    tm = f_add(t, f_div(f_sub((float)((c + 1) << m.shift), pv), dv));
-    td = f_div(N, dv);
+    tm = f_add(t, f_mul(f_sub((float)((c + 1) << m.shift), pv), r));
+    td = f_mul(N, r);
   } else if (dv < 0.0f) {
+    const float r = f_div(1.0f, dv);
     st = -1;
-    tm = f_add(t, f_div(f_sub((float)(c << m.shift), pv), dv));
-    td = f_div(N, -dv);
+    tm = f_add(t, f_mul(f_sub((float)(c << m.shift), pv), r));
+    td = f_mul(N, -r);
   } else {
     st = 0;
     tm = INFINITY;
@@ -819,37 +822,44 @@ __device__ __forceinline__ void walk_axis(const MacroDev& m, const CamDev& cam, 
   }
 }
 
-// Enters the cell grid at the point o + t d.
+// Enters the current cell: its majorant, the reciprocal, its exit.
+__device__ __forceinline__ void walk_enter(PtWalk& w, const MacroDev& m) {
+  // fewer than 2^31 cells (checked when the structure is created)
+  const uint32_t cell = ((uint32_t)w.c2 * (uint32_t)m.dims[1] + (uint32_t)w.c1) * (uint32_t)m.dims[0] + (uint32_t)w.c0;
+  w.mj = __ldg(m.major + cell);
+  w.rj = w.mj > 0.0f ? f_div(1.0f, w.mj) : 0.0f;
+  w.te = fminf(fminf(fminf(w.tm0, w.tm1), w.tm2), w.t1);
+}
+
+// Enters the cell grid at the point o + t d of a segment that ends at t1.
 __device__ __forceinline__ void walk_init(PtWalk& w, const MacroDev& m, const CamDev& cam, const float o[3],
-                                          const float d[3], float t) {
+                                          const float d[3], float t, float t1) {
   walk_axis(m, cam, 0, o[0], d[0], t, w.c0, w.s0, w.tm0, w.td0);
   walk_axis(m, cam, 1, o[1], d[1], t, w.c1, w.s1, w.tm1, w.td1);
   walk_axis(m, cam, 2, o[2], d[2], t, w.c2, w.s2, w.tm2, w.td2);
+  w.t1 = t1;
   w.live = true;
+  walk_enter(w, m);
 }
 
 // Spends optical depth tau from t: true with the tentative collision in t
-// and its cell's majorant in maj; false when t1 (or the grid's end) comes
-// first.  Cells of majorant 0 are crossed without a collision.
-__device__ __forceinline__ bool walk_flight(PtWalk& w, const MacroDev& m, float tau, float& t, float t1,
-                                            float& maj) {
+// and its cell's majorant in maj; false when the segment's end (or the
+// grid's) comes first.  Cells of majorant 0 are crossed without a collision.
+__device__ __forceinline__ bool walk_flight(PtWalk& w, const MacroDev& m, float tau, float& t, float& maj) {
   float tt = t;
   int guard = 3 * (m.dims[0] + m.dims[1] + m.dims[2]) + 8;
   while (w.live && guard-- > 0) {
-    const size_t cell = ((size_t)w.c2 * (size_t)m.dims[1] + (size_t)w.c1) * (size_t)m.dims[0] + (size_t)w.c0;
-    const float mj = __ldg(m.major + cell);
-    const float te = fminf(fminf(fminf(w.tm0, w.tm1), w.tm2), t1);
-    if (mj > 0.0f) {
-      const float tc = f_add(tt, f_div(tau, mj));
-      if (tc < te) {
-        t = tc;
-        maj = mj;
+    if (w.mj > 0.0f) {
+      const float dd = f_mul(w.mj, f_sub(w.te, tt));  // optical depth of the cell's stretch
+      if (tau < dd) {
+        t = fminf(f_add(tt, f_mul(tau, w.rj)), w.te);
+        maj = w.mj;
         return true;
       }
-      tau = fmaxf(f_sub(tau, f_mul(mj, f_sub(te, tt))), 0.0f);
+      tau = f_sub(tau, dd);
     }
-    tt = te;
-    if (!(tt < t1)) break;
+    tt = w.te;
+    if (!(tt < w.t1)) break;
     if (w.tm0 <= w.tm1 && w.tm0 <= w.tm2) {
       w.c0 += w.s0;
       w.tm0 = f_add(w.tm0, w.td0);
@@ -863,8 +873,9 @@ __device__ __forceinline__ bool walk_flight(PtWalk& w, const MacroDev& m, float 
       w.tm2 = f_add(w.tm2, w.td2);
       w.live = w.c2 >= 0 && w.c2 < m.dims[2];
     }
+    if (w.live) walk_enter(w, m);
   }
-  t = t1;
+  t = w.t1;
   return false;
 }
 
@@ -995,12 +1006,12 @@ __global__ void __launch_bounds__(kFrameThreads, 5) pt_kernel(const __grid_const
       for (int b = 0;; ++b) {
         bool hit = false;
         float t = t0, p[3] = {0.f, 0.f, 0.f}, v = 0.f;
-        if (local) walk_init(W, P.mac, cam, o, d, t0);
+        if (local) walk_init(W, P.mac, cam, o, d, t0, t1);
         for (int step = 0; (local || P.pt_sbar > 0.0f) && step < kPtMaxSteps; ++step) {
           const float tau = neg_log1m(pt_uniform(key, j++));
           float maj = P.pt_sbar;
           if (local) {
-            if (!walk_flight(W, P.mac, tau, t, t1, maj)) break;
+            if (!walk_flight(W, P.mac, tau, t, maj)) break;
           } else {
             t = f_add(t, f_mul(tau, P.pt_inv));
             if (!(t < t1)) break;
@@ -1029,12 +1040,12 @@ __global__ void __launch_bounds__(kFrameThreads, 5) pt_kernel(const __grid_const
         // next-event estimation: shadow transmittance by ratio tracking
         const float ts1 = box_exit(cam, p, P.pt_ls);
         float ts = 0.f, Tr = 1.f;
-        if (local) walk_init(W, P.mac, cam, p, P.pt_ls, 0.f);
+        if (local) walk_init(W, P.mac, cam, p, P.pt_ls, 0.f, ts1);
         for (int step = 0; (local || P.pt_sbar > 0.0f) && step < kPtMaxSteps; ++step) {
           const float tau = neg_log1m(pt_uniform(key, j++));
           float maj = P.pt_sbar;
           if (local) {
-            if (!walk_flight(W, P.mac, tau, ts, ts1, maj)) break;
+            if (!walk_flight(W, P.mac, tau, ts, maj)) break;
           } else {
             ts = f_add(ts, f_mul(tau, P.pt_inv));
             if (!(ts < ts1)) break;

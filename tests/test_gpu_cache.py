@@ -49,7 +49,7 @@ def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_r
         img, st = r.render(inr, cam, tf, cache=cache)
         ref, rst = oc.render(ocam(cam), tf.astype(np.float64), macro=omac)
         if macro_cell:
-            assert np.array_equal(mac.skip_flags(), omac._keep)
+            assert np.array_equal(mac.skip_flags(), omac.skip_flags)
         for k in ("samples", "hits", "fallback_hits", "true_misses", "bricks_requested",
                   "bricks_decoded", "evictions", "inr_queries_direct", "inr_queries_decode",
                   "samples_skipped"):

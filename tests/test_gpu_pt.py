@@ -172,7 +172,7 @@ def _pt_macro_run(tf, frames, check_state):
         cam = S.orbit_camera(5 * f, 40, 32, distance=1.7)
         img, st = r.render_pt(inr, cam, tf, gpt, cache=cache)
         ref, rst = oc.render_pt(ocam(cam), tfd, opt, macro=omac)
-        assert np.array_equal(mac.majorants(), omac._keep[1])
+        assert np.array_equal(mac.majorants(), omac.majorants)
         d = np.abs(img.cpu().numpy() - ref).max(axis=2)
         agree += int((d < 1e-3 * max(1.0, np.abs(ref).max())).sum())
         total += d.size
