@@ -993,81 +993,95 @@ __global__ void __launch_bounds__(kFrameThreads, 5) pt_kernel(const __grid_const
     const int py = (int)((t64 / P.tiles_x) * 8 + (w >> 3));
     if (px >= cam.W || py >= cam.H) continue;
     const uint32_t pixel = (uint32_t)(py * cam.W + px);
-    float o[3] = {cam.o[0], cam.o[1], cam.o[2]}, d[3], t0 = 0.f, t1 = 0.f;
+    float o[3] = {cam.o[0], cam.o[1], cam.o[2]}, d[3], t = 0.f, t1 = 0.f;
     float Lr = P.pt_amb[0], Lg = P.pt_amb[1], Lb = P.pt_amb[2], alpha = 0.f;
-    if (ray_setup(cam, px, py, d, t0, t1)) {
+    if (ray_setup(cam, px, py, d, t, t1)) {
+      // One loop over tracking steps with a per-lane mode, so that the free
+      // flight, the walk and the lookup exist once in the code: lanes
+      // tracking a camera or scattered segment (delta tracking) and lanes
+      // tracking a shadow segment (ratio tracking) share those
+      // instructions.  Random numbers and lookups come in the order of the
+      // nested formulation: per bounce the segment's flights and decisions,
+      // then the shadow segment's flights, then the scattering direction.
       const uint64_t key = ((uint64_t)P.fseed << 32) | (uint64_t)pixel;
       const uint32_t rseed = ray_seed(P.fseed, pixel);
-      float br = 1.f, bg = 1.f, bb = 1.f;
+      const bool local = P.mac.major != nullptr;  // per-cell majorants
+      float br = 1.f, bg = 1.f, bb = 1.f, Tr = 1.f, p[3] = {0.f, 0.f, 0.f};
       Lr = Lg = Lb = 0.f;
       uint32_t j = 0, k = 0;
-      const bool local = P.mac.major != nullptr;  // per-cell majorants
+      int b = 0, steps = 0;
+      bool shadow = false, begin = true;
       PtWalk W;
-      for (int b = 0;; ++b) {
-        bool hit = false;
-        float t = t0, p[3] = {0.f, 0.f, 0.f}, v = 0.f;
-        if (local) walk_init(W, P.mac, cam, o, d, t0, t1);
-        for (int step = 0; (local || P.pt_sbar > 0.0f) && step < kPtMaxSteps; ++step) {
+      while (true) {
+        if (begin) {  // a segment o + t d, t in [t, t1), starts
+          if (local) walk_init(W, P.mac, cam, o, d, t, t1);
+          steps = 0;
+          begin = false;
+        }
+        bool got = false;
+        float maj = P.pt_sbar;
+        if ((local || P.pt_sbar > 0.0f) && steps < kPtMaxSteps) {
+          ++steps;
           const float tau = neg_log1m(pt_uniform(key, j++));
-          float maj = P.pt_sbar;
           if (local) {
-            if (!walk_flight(W, P.mac, tau, t, maj)) break;
+            got = walk_flight(W, P.mac, tau, t, maj);
           } else {
             t = f_add(t, f_mul(tau, P.pt_inv));
-            if (!(t < t1)) break;
-          }
-          float x[3], dist;
-          pt_point(cam, o, d, t, p, x, dist);
-          v = pt_value<IN, H, CACHED, F16POOL, MISS>(P, s_geo, x, dist, rseed, k, pixel, n);
-          ++k;
-          const float sig = tf_lookup(s_tf, v).w;
-          if (pt_uniform(key, j++) * maj < sig) {
-            hit = true;
-            break;
+            got = t < t1;
           }
         }
-        if (!hit) {
+        if (got) {
+          float q[3], x[3], dist;
+          pt_point(cam, o, d, t, q, x, dist);
+          const float v = pt_value<IN, H, CACHED, F16POOL, MISS>(P, s_geo, x, dist, rseed, k, pixel, n);
+          ++k;
+          const float4 e4 = tf_lookup(s_tf, v);
+          if (shadow) {
+            Tr *= 1.0f - (local ? f_div(e4.w, maj) : e4.w * P.pt_inv);
+          } else if (pt_uniform(key, j++) * maj < e4.w) {
+            // real collision: albedo, then next-event estimation along the
+            // shadow segment towards the light
+            if (b == 0) alpha = 1.f;
+            br *= e4.x;
+            bg *= e4.y;
+            bb *= e4.z;
+            p[0] = q[0];
+            p[1] = q[1];
+            p[2] = q[2];
+            o[0] = q[0];
+            o[1] = q[1];
+            o[2] = q[2];
+            d[0] = P.pt_ls[0];
+            d[1] = P.pt_ls[1];
+            d[2] = P.pt_ls[2];
+            t = 0.f;
+            t1 = box_exit(cam, o, d);
+            Tr = 1.f;
+            shadow = begin = true;
+          }
+          continue;
+        }
+        // the segment ended without a (further) collision
+        if (!shadow) {  // escaped: ambient radiance
           Lr = fmaf(br, P.pt_amb[0], Lr);
           Lg = fmaf(bg, P.pt_amb[1], Lg);
           Lb = fmaf(bb, P.pt_amb[2], Lb);
           break;
-        }
-        if (b == 0) alpha = 1.f;
-        const float4 alb = tf_lookup(s_tf, v);
-        br *= alb.x;
-        bg *= alb.y;
-        bb *= alb.z;
-        // next-event estimation: shadow transmittance by ratio tracking
-        const float ts1 = box_exit(cam, p, P.pt_ls);
-        float ts = 0.f, Tr = 1.f;
-        if (local) walk_init(W, P.mac, cam, p, P.pt_ls, 0.f, ts1);
-        for (int step = 0; (local || P.pt_sbar > 0.0f) && step < kPtMaxSteps; ++step) {
-          const float tau = neg_log1m(pt_uniform(key, j++));
-          float maj = P.pt_sbar;
-          if (local) {
-            if (!walk_flight(W, P.mac, tau, ts, maj)) break;
-          } else {
-            ts = f_add(ts, f_mul(tau, P.pt_inv));
-            if (!(ts < ts1)) break;
-          }
-          float pq[3], x[3], dist;
-          pt_point(cam, p, P.pt_ls, ts, pq, x, dist);
-          const float v2 = pt_value<IN, H, CACHED, F16POOL, MISS>(P, s_geo, x, dist, rseed, k, pixel, n);
-          ++k;
-          const float sig2 = tf_lookup(s_tf, v2).w;
-          Tr *= 1.0f - (local ? f_div(sig2, maj) : sig2 * P.pt_inv);
         }
         const float ne = Tr * 0.0795774715459476679f;  // 1 / (4 pi)
         Lr = fmaf(br * P.pt_light[0], ne, Lr);
         Lg = fmaf(bg * P.pt_light[1], ne, Lg);
         Lb = fmaf(bb * P.pt_light[2], ne, Lb);
         if (b + 1 >= P.pt_bounces) break;
+        ++b;
         pt_sphere(key, j, d);
         o[0] = p[0];
         o[1] = p[1];
         o[2] = p[2];
-        t0 = 0.f;
+        t = 0.f;
         t1 = box_exit(cam, o, d);
+        shadow = false;
+        begin = true;
       }
     }
     P.out[pixel] = make_float4(Lr, Lg, Lb, alpha);
