@@ -80,9 +80,9 @@ def replica_reduce(local_total_ms, n_frames, device=None):
     return total, total / (n_frames * world)
 
 
-def frame_inputs(f, W, H, camera="orbit"):
+def frame_inputs(f, W, H, camera="orbit", n_ramps=4):
     from paper_2504_18001_gb300 import synthetic as S
-    tf = S.tf_ramps(2)
+    tf = S.tf_ramps(2, n_ramps=n_ramps)
     if camera == "fly":
         return S.flythrough_camera(f % FLY_FRAMES, FLY_FRAMES, W, H), tf
     if f < ORBIT_FRAMES:
@@ -90,7 +90,8 @@ def frame_inputs(f, W, H, camera="orbit"):
     else:
         g = f - ORBIT_FRAMES + 1
         cam = S.orbit_camera(ORBIT_FRAMES - 1, W, H)
-        tf = S.tf_ramps(2, shift=0.01 * (g % TF_FRAMES) * (1 if (g // TF_FRAMES) % 2 == 0 else -1))
+        tf = S.tf_ramps(2, n_ramps=n_ramps,
+                        shift=0.01 * (g % TF_FRAMES) * (1 if (g // TF_FRAMES) % 2 == 0 else -1))
     return cam, tf
 
 
@@ -200,7 +201,7 @@ def run_gpu(args, wl):
     if args.autotune:
         from paper_2504_18001_gb300 import autotune
         best, trials = autotune.tune(
-            inr_c, inr32, vol, lambda f: frame_inputs(f, W, H, wl["camera"]), W, H,
+            inr_c, inr32, vol, lambda f: frame_inputs(f, W, H, wl["camera"], args.tf_ramps), W, H,
             bricks=(8, 16) if wl["camera"] == "orbit" else (wl["brick"],), levels=wl["levels"],
             pool_mib=wl["pool_mib"], storage=storage,
             lod_scale=args.lod_scale, step_mode=wl["step_mode"],
@@ -230,7 +231,7 @@ def run_gpu(args, wl):
     stream = torch.cuda.current_stream()
 
     def step(f, use_cache=True):
-        cam, tf = frame_inputs(f, W, H, wl["camera"])
+        cam, tf = frame_inputs(f, W, H, wl["camera"], args.tf_ramps)
         flush.random_(0, 255)  # L2 flush between timed iterations
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -285,7 +286,7 @@ def run_gpu(args, wl):
     n_e2e = max(3, min(args.steps, 10))
     stride = max(1, args.steps // n_e2e)
     for i in range(n_e2e):
-        cam, tf = frame_inputs(args.warmup + (i * stride) % args.steps, W, H, wl["camera"])
+        cam, tf = frame_inputs(args.warmup + (i * stride) % args.steps, W, H, wl["camera"], args.tf_ramps)
         flush.random_(0, 255)
         stream.synchronize()  # the frame's stream only: a lag-2 decode may still run
         t0 = time.perf_counter()
@@ -319,7 +320,8 @@ def run_gpu(args, wl):
     achieved_uniq = sum(uniq_bytes) / (sum(k_ms) * 1e-3) / 1e9
     default_cfg = (args.precision == "mixed" and not args.macro and args.ray_layout == 0 and not args.pt
                    and not args.page
-                   and args.lod_scale == 1.0 and args.lag == 1 and not args.autotune)
+                   and args.lod_scale == 1.0 and args.lag == 1 and not args.autotune
+                   and args.tf_ramps == 4)
     traffic = PROFILED_TRAFFIC.get(args.workload) if default_cfg else None
     un_q = sum(s["inr_queries_direct"] for s in un_st)
     prec = args.precision
@@ -348,6 +350,7 @@ def run_gpu(args, wl):
                    "step_mode": wl["step_mode"], "step_lod_max": wl["step_lod_max"],
                    "ray_layout": "thread per ray" if args.ray_layout == 0 else "warp per ray",
                    "cuda_graph": bool(args.graph),
+                   "tf_ramps": args.tf_ramps,
                    "macro_cell": args.macro or None,
                    "lag": args.lag,
                    "page_tables": (f"two-level, pages of {args.page}^3 bricks, {args.n_pages} page slots"
@@ -414,7 +417,7 @@ def cpu_baseline(args, wl, table, w, f, cached_img, uncached_img, un_stats):
     table = np.ascontiguousarray(table, np.float64)  # converted once, outside the timing
     w = np.ascontiguousarray(w, np.float64)
     vol = wl["vol"]
-    cam, tf = frame_inputs(f, W, H, wl["camera"])
+    cam, tf = frame_inputs(f, W, H, wl["camera"], args.tf_ramps)
     if wl["camera"] == "fly":
         pts = np.random.default_rng(0).uniform(0, 1, (4000, 3)).astype(np.float32)
         t0 = time.perf_counter()
@@ -480,7 +483,7 @@ def run_reference(args, wl):
     # the oracle keeps no state between frames: only the last 3 warm-up
     # frames are run (untimed)
     for i in range(max(args.warmup - 3, 0), args.warmup + args.steps):
-        cam, tf = frame_inputs(i, W, H, wl["camera"])
+        cam, tf = frame_inputs(i, W, H, wl["camera"], args.tf_ramps)
         oc = O.camera(**cam)
         t0 = time.perf_counter()
         for gy in range(cw):
@@ -644,6 +647,8 @@ def main():
     ap.add_argument("--n-pages", type=int, default=0, help="page slots of the page pool")
     ap.add_argument("--lag", type=int, default=1, choices=[1, 2],
                     help="frames from a brick request to its use (2: decode on a second stream)")
+    ap.add_argument("--tf-ramps", type=int, default=4,
+                    help="tent ramps of the seeded transfer function (fewer = sparser)")
     ap.add_argument("--macro", type=int, default=0,
                     help="macro-cell edge (0 = off): empty-space skipping when ray marching, "
                          "local majorants when path tracing")

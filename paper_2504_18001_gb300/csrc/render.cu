@@ -806,12 +806,12 @@ __device__ __forceinline__ void walk_axis(const MacroDev& m, const CamDev& cam, 
   const float dv = f_mul(f_mul(d, cam.inv_e[a]), (float)cam.vol[a]);
   const float N = (float)(1 << m.shift);
   if (dv > 0.0f) {
-    const float r = f_div(1.0f, dv);
+    const float r = __frcp_rn(dv);  // correctly rounded 1/dv
     st = 1;
     tm = f_add(t, f_mul(f_sub((float)((c + 1) << m.shift), pv), r));
     td = f_mul(N, r);
   } else if (dv < 0.0f) {
-    const float r = f_div(1.0f, dv);
+    const float r = __frcp_rn(dv);
     st = -1;
     tm = f_add(t, f_mul(f_sub((float)(c << m.shift), pv), r));
     td = f_mul(N, -r);
@@ -827,7 +827,7 @@ __device__ __forceinline__ void walk_enter(PtWalk& w, const MacroDev& m) {
   // fewer than 2^31 cells (checked when the structure is created)
   const uint32_t cell = ((uint32_t)w.c2 * (uint32_t)m.dims[1] + (uint32_t)w.c1) * (uint32_t)m.dims[0] + (uint32_t)w.c0;
   w.mj = __ldg(m.major + cell);
-  w.rj = w.mj > 0.0f ? f_div(1.0f, w.mj) : 0.0f;
+  w.rj = w.mj > 0.0f ? __frcp_rn(w.mj) : 0.0f;
   w.te = fminf(fminf(fminf(w.tm0, w.tm1), w.tm2), w.t1);
 }
 
