@@ -1,0 +1,112 @@
+"""Parity at the benchmark's full size and launch configuration (512^3
+volume, L=16 T=2^19 INR with FP16 table and BF16 tensor-core MLP, 1024^2
+image, 8^3 bricks, 4 LoDs, 1 GiB FP16 pool, 4096 requests per frame), on
+outputs the FP64 oracle computes one window at a time:
+- the first frame (fresh cache, coarsest LoD preloaded) against the
+  oracle's cached render of a pixel window: every sample there reads the
+  same preloaded bricks, so the window is that of the full frame;
+- a frame after the cache has warmed up against the oracle's cache-off
+  render of a window (the property that holds at any size: the cached
+  image stays within the stated mixed-precision error, PSNR >= 40 dB)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_18001_gb300 import synthetic as S
+
+from _scenes import ocam, oracle_inr
+
+pytestmark = pytest.mark.gpu
+
+VOL = (512, 512, 512)
+W = H = 1024
+WIN = (500, 500, 24, 24)  # pixel window at the image centre
+
+
+def _gpu_setup():
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.INR_512
+    table, w = S.inr_init(cfg, seed=0, table_scale=1.0, level_decay=0.5)
+    inr = cinr.Inr(cinr.make_inr_params(cfg, mlp_precision="bf16", table_precision="fp16"), table, w)
+    lo, hi = inr.raw_range(VOL, stride=8)
+    inr.set_range(-lo / (hi - lo), (1.0 - lo) / (hi - lo))
+    cache = cinr.Cache(inr, VOL, pool_bytes=1024 << 20, brick=8, levels=4, storage="fp16",
+                       n_req=4096, ranking=1, preload=1)
+    r = cinr.Renderer(W, H, VOL, K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0)
+    return cfg, table, w, inr, cache, r
+
+
+def _window(img):
+    x, y, pw, ph = WIN
+    return img[y:y + ph, x:x + pw]
+
+
+def test_orbit_full_size_first_frame_window_matches_oracle_cache():
+    cfg, table, w, inr, cache, r = _gpu_setup()
+    cam = S.orbit_camera(0, W, H)
+    tf = S.tf_ramps(2)
+    img, st = r.render(inr, cam, tf, cache=cache)
+    assert st["true_misses"] == 0
+    assert st["hits"] + st["fallback_hits"] == st["samples"] > 0
+    assert 0 < st["bricks_decoded"] <= 4096
+    # the oracle's cache: same geometry and preload; its capacity and
+    # request budget play no part in the first frame's image
+    p = oracle_inr(cfg, table, w, vol=VOL, stride=8)
+    mo = O.march_opts(K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0)
+    oc = O.Cache(p, table.astype(np.float64), w.astype(np.float64), VOL, 8, 4, 700, mo, n_req=1)
+    ref, rst = oc.render(ocam(cam), tf.astype(np.float64), window=WIN)
+    assert rst["true_misses"] == 0 and rst["samples"] > 0
+    got = _window(img.cpu().numpy()).astype(np.float64)
+    # FP16 table + BF16 MLP + FP16 bricks against FP64: the stated
+    # mixed-precision bound
+    assert np.abs(got - ref).max() < 6e-2
+    assert O.psnr(got, ref) > 40.0
+
+
+def test_orbit_full_size_warm_cache_window_within_error_of_uncached_oracle():
+    cfg, table, w, inr, cache, r = _gpu_setup()
+    tf = S.tf_ramps(2)
+    for f in range(90):  # the benchmark's warm-up: the cache fills at 4096 bricks per frame
+        img, st = r.render(inr, S.orbit_camera(f, W, H), tf, cache=cache)
+        assert st["true_misses"] == 0
+    assert st["hits"] > 100 * st["fallback_hits"]
+    p = oracle_inr(cfg, table, w, vol=VOL, stride=8)
+    mo = O.march_opts(K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0)
+    ref, rst = O.render_direct(p, table.astype(np.float64), w.astype(np.float64),
+                               ocam(S.orbit_camera(89, W, H)), VOL, mo, tf.astype(np.float64),
+                               window=WIN)
+    got = _window(img.cpu().numpy()).astype(np.float64)
+    assert O.psnr(got, ref) > 40.0
+
+
+def test_terascale_full_size_first_frame_window_matches_oracle_cache():
+    # 10240 x 7680 x 1536 virtual volume, L=24 T=2^22 INR (FP16 table, BF16
+    # MLP), 1920x1080, 16^3 bricks, 6 LoDs, 40 GiB FP16 pool, 8192 requests,
+    # LoD-scaled steps: the first frame's centre window against the oracle
+    from paper_2504_18001_gb300 import cinr
+    vol = (10240, 7680, 1536)
+    cfg = S.INR_TERA
+    table, w = S.inr_init(cfg, seed=0, table_scale=1.0, level_decay=0.5)
+    inr = cinr.Inr(cinr.make_inr_params(cfg, mlp_precision="bf16", table_precision="fp16"), table, w)
+    lo, hi = inr.raw_range(vol, stride=64)
+    inr.set_range(-lo / (hi - lo), (1.0 - lo) / (hi - lo))
+    cache = cinr.Cache(inr, vol, pool_bytes=40 << 30, brick=16, levels=6, storage="fp16",
+                       n_req=8192, ranking=1, preload=1)
+    r = cinr.Renderer(1920, 1080, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0,
+                      step_mode=1, step_lod_max=5)
+    cam = S.flythrough_camera(0, 300, 1920, 1080)
+    tf = S.tf_ramps(2)
+    img, st = r.render(inr, cam, tf, cache=cache)
+    assert st["true_misses"] == 0
+    assert st["hits"] + st["fallback_hits"] == st["samples"] > 0
+    p = oracle_inr(cfg, table, w, vol=vol, stride=64)
+    mo = O.march_opts(K=32, eps_T=1e-3, lod_mode=0, lod_scale=1.0, seed=0, step_mode=1,
+                      step_lod_max=5)
+    oc = O.Cache(p, table.astype(np.float64), w.astype(np.float64), vol, 16, 6, 1000, mo, n_req=1)
+    win = (948, 528, 24, 24)
+    ref, rst = oc.render(ocam(cam), tf.astype(np.float64), window=win)
+    assert rst["true_misses"] == 0 and rst["samples"] > 0
+    x, y, pw, ph = win
+    got = img.cpu().numpy()[y:y + ph, x:x + pw].astype(np.float64)
+    assert np.abs(got - ref).max() < 6e-2
+    assert O.psnr(got, ref) > 40.0
