@@ -198,15 +198,18 @@ __global__ void __launch_bounds__(kFwdThreads, IN <= 32 ? 4 : 2) bwd_kernel(InrD
 }
 
 // partial[blk][i][j] = sum over the block's samples of A[i][s] * B[j][s]
-// (A: M x n, B: N x n, feature-major).  Thread tile 4 x 4.
+// (A: M x n, B: N x n, feature-major).  Thread tile 4 x 4; the staged
+// tiles are sample-major in shared memory so that a thread reads its four
+// rows of A and four columns of B as one 16-byte load each (the loads, not
+// the FMAs, bounded the scalar-load version).
 template <int M, int N>
 __global__ void __launch_bounds__((M / 4) * (N / 4)) outer_kernel(const float* __restrict__ A,
                                                                   const float* __restrict__ B, long n,
                                                                   float* __restrict__ partial) {
   constexpr int TPB = (M / 4) * (N / 4);
   constexpr int SUB = 32;
-  __shared__ float sa[M][SUB + 1];
-  __shared__ float sb[N][SUB + 1];
+  __shared__ __align__(16) float sa[SUB][M + 4];
+  __shared__ __align__(16) float sb[SUB][N + 4];
   const int tid = threadIdx.x;
   const int ti = (tid / (N / 4)) * 4, tj = (tid % (N / 4)) * 4;
   float acc[4][4] = {};
@@ -215,21 +218,18 @@ __global__ void __launch_bounds__((M / 4) * (N / 4)) outer_kernel(const float* _
   for (long base = s0; base < s1; base += SUB) {
     for (int e = tid; e < M * SUB; e += TPB) {
       const int i = e / SUB, k = e % SUB;
-      sa[i][k] = base + k < s1 ? A[(size_t)i * n + base + k] : 0.0f;
+      sa[k][i] = base + k < s1 ? A[(size_t)i * n + base + k] : 0.0f;
     }
     for (int e = tid; e < N * SUB; e += TPB) {
       const int j = e / SUB, k = e % SUB;
-      sb[j][k] = base + k < s1 ? B[(size_t)j * n + base + k] : 0.0f;
+      sb[k][j] = base + k < s1 ? B[(size_t)j * n + base + k] : 0.0f;
     }
     __syncthreads();
 #pragma unroll 8
     for (int k = 0; k < SUB; ++k) {
-      float a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = sa[ti + u][k];
-        b[u] = sb[tj + u][k];
-      }
+      const float4 a4 = *reinterpret_cast<const float4*>(&sa[k][ti]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&sb[k][tj]);
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -244,25 +244,28 @@ __global__ void __launch_bounds__((M / 4) * (N / 4)) outer_kernel(const float* _
     for (int v = 0; v < 4; ++v) out[(ti + u) * N + tj + v] = acc[u][v];
 }
 
-// partial[blk][j] = sum over the block's samples of a[s] * B[j][s].
+// partial[blk][j] = sum over the block's samples of a[s] * B[j][s]: each
+// warp takes N/8 of the outputs, its lanes stride over the block's samples
+// (a[s] read once per lane for all of the warp's outputs), then a warp sum.
 template <int N>
 __global__ void __launch_bounds__(256) vec_kernel(const float* __restrict__ a, const float* __restrict__ B,
                                                   long n, float* __restrict__ partial) {
-  __shared__ float red[256 / 32][N];
+  static_assert(N % 8 == 0, "8 warps share the outputs");
+  constexpr int J = N / 8;
   const long s0 = (long)blockIdx.x * kChunk;
   const long s1 = s0 + kChunk < n ? s0 + kChunk : n;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int j = 0; j < N; ++j) {
-    float acc = 0.0f;
-    for (long s = s0 + threadIdx.x; s < s1; s += 256) acc = fmaf(a[s], B[(size_t)j * n + s], acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) red[w][j] = acc;
+  float acc[J] = {};
+  for (long s = s0 + lane; s < s1; s += 32) {
+    const float as = a[s];
+#pragma unroll
+    for (int q = 0; q < J; ++q) acc[q] = fmaf(as, B[(size_t)(w * J + q) * n + s], acc[q]);
   }
-  __syncthreads();
-  for (int j = threadIdx.x; j < N; j += 256) {
-    float t = 0.0f;
-    for (int q = 0; q < 256 / 32; ++q) t += red[q][j];
-    partial[(size_t)blockIdx.x * N + j] = t;
+#pragma unroll
+  for (int q = 0; q < J; ++q) {
+    float t = acc[q];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) partial[(size_t)blockIdx.x * N + w * J + q] = t;
   }
 }
 
