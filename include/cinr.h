@@ -38,6 +38,7 @@ extern "C" {
 #define CINR_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up     */
 #define CINR_ERR_DEVICE_CHECK (-5) /* a device-side bounds check tripped     */
 #define CINR_ERR_UNSUPPORTED (-6)  /* valid request this build cannot run    */
+#define CINR_ERR_NAN (-7)          /* a training step met a non-finite value */
 
 /* -------------------------------------------------------------- types --- */
 typedef struct cinr_inr_s* cinr_inr_t;
@@ -482,6 +483,25 @@ int cinr_create_trainer(cinr_inr_t inr, const cinr_train_opts* o,
  * loss_dev is not NULL it receives the step's mean squared error. */
 int cinr_train_step(cinr_trainer_t t, const float* field_dev,
                     const int dims[3], float* loss_dev, cinr_stream_t stream);
+
+/* Sets the Adam learning rate of the following steps (a schedule is the
+ * caller's: the paper gives none).  Host-side only. */
+int cinr_trainer_set_lr(cinr_trainer_t t, float lr);
+
+/* Whether any training step since the last call produced a non-finite
+ * gradient (a NaN or infinite field value, or a diverged run): CINR_OK or
+ * CINR_ERR_NAN (the flag is then cleared).  Synchronises `stream`. */
+int cinr_trainer_status(cinr_trainer_t t, cinr_stream_t stream);
+
+/* One call for `steps` training steps (Sec. 4.1): creates a trainer in
+ * `workspace` (ws_bytes >= cinr_trainer_bytes), runs the steps on
+ * field_dev, checks cinr_trainer_status and releases the trainer (the
+ * workspace may then be reused; the INR keeps the trained parameters).
+ * Adam's moments start from zero, as for a new trainer.  Errors: those of
+ * cinr_create_trainer and cinr_train_step, CINR_ERR_NAN. */
+int cinr_train(cinr_inr_t inr, const float* field_dev, const int dims[3],
+               const cinr_train_opts* o, long steps, void* workspace,
+               size_t ws_bytes, cinr_stream_t stream);
 
 /* Gradient of the mean squared error (1/n) sum (y_i - target_i)^2 of the
  * raw network output at n given points (no parameter update): g_table_dev

@@ -19,6 +19,7 @@ from . import build as _build
 _lib = None
 
 CINR_OK = 0
+ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_CHECK, ERR_UNSUPPORTED, ERR_NAN = range(-1, -8, -1)
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3}
 DUMP_PAGE_TABLE, DUMP_STAMPS, DUMP_OWNERS, DUMP_RANK, DUMP_REQUESTS, DUMP_VICTIMS, \
     DUMP_MISSES, DUMP_PINNED, DUMP_POOL, DUMP_PAGE_DIR, DUMP_PAGES, DUMP_PAGE_KEYS, \
@@ -26,7 +27,9 @@ DUMP_PAGE_TABLE, DUMP_STAMPS, DUMP_OWNERS, DUMP_RANK, DUMP_REQUESTS, DUMP_VICTIM
 
 
 class CinrError(RuntimeError):
-    pass
+    def __init__(self, msg, code=None):
+        super().__init__(msg)
+        self.code = code
 
 
 class cinr_inr_params(C.Structure):
@@ -124,6 +127,9 @@ _SIGS = {
     "cinr_train_step": [_vp, _vp, _P(C.c_int), _vp, _vp],
     "cinr_inr_loss_grad": [_vp, _vp, _vp, C.c_long, _vp, _vp, _vp, _vp],
     "cinr_destroy_trainer": [_vp],
+    "cinr_trainer_status": [_vp, _vp],
+    "cinr_trainer_set_lr": [_vp, C.c_float],
+    "cinr_train": [_vp, _vp, _P(C.c_int), _vp, C.c_long, _vp, C.c_size_t, _vp],
     "cinr_inr_export": [_vp, _vp, _vp, _vp],
     "cinr_debug_dump": [_vp, C.c_int, _vp, C.c_size_t, _P(C.c_size_t), _vp],
     "cinr_debug_mma_tile": [_vp, _vp, C.c_int, C.c_int, _vp, _vp],
@@ -172,7 +178,7 @@ def last_error() -> str:
 
 def check(rc: int, what: str = ""):
     if rc != CINR_OK:
-        raise CinrError(f"{what} failed ({rc}): {last_error()}")
+        raise CinrError(f"{what} failed ({rc}): {last_error()}", rc)
 
 
 def _stream(stream):
@@ -411,6 +417,21 @@ def inr_export(inr: Inr, stream=None):
     return table, mlp
 
 
+def train(inr: "Inr", field, steps, batch=1 << 18, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15, seed=0,
+          stream=None):
+    """cinr_train: `steps` Adam steps on field (torch float32 [z, y, x] on the
+    device) in a temporary workspace; raises CinrError(ERR_NAN) on a
+    non-finite gradient."""
+    L = lib()
+    opts = cinr_train_opts(int(batch), float(lr), float(beta1), float(beta2), float(eps), int(seed))
+    nbytes = C.c_size_t()
+    check(L.cinr_trainer_bytes(inr.h, C.byref(opts), C.byref(nbytes)), "cinr_trainer_bytes")
+    ws = _dev_buffer(nbytes.value, field.device)
+    dims = (C.c_int * 3)(field.shape[2], field.shape[1], field.shape[0])
+    check(L.cinr_train(inr.h, C.c_void_p(field.data_ptr()), dims, C.byref(opts), int(steps),
+                       C.c_void_p(ws.data_ptr()), nbytes.value, _stream(stream)), "cinr_train")
+
+
 class Trainer:
     """INR training on an explicit field (Sec. 4.1): Adam steps on batches of
     counter-based random coordinates; updates the INR in place."""
@@ -438,6 +459,14 @@ class Trainer:
                                     C.c_void_p(self.loss.data_ptr()), _stream(stream)),
               "cinr_train_step")
         return self.loss
+
+    def set_lr(self, lr):
+        check(lib().cinr_trainer_set_lr(self.h, float(lr)), "cinr_trainer_set_lr")
+
+    def status(self, stream=None):
+        """Raises CinrError (CINR_ERR_NAN) when a step since the last check
+        produced a non-finite gradient."""
+        check(lib().cinr_trainer_status(self.h, _stream(stream)), "cinr_trainer_status")
 
     def loss_grad(self, xyz, target, stream=None):
         import torch

@@ -215,16 +215,35 @@ __global__ void __launch_bounds__((M / 4) * (N / 4)) outer_kernel(const float* _
   float acc[4][4] = {};
   const long s0 = (long)blockIdx.x * kChunk;
   const long s1 = s0 + kChunk < n ? s0 + kChunk : n;
-  for (long base = s0; base < s1; base += SUB) {
-    for (int e = tid; e < M * SUB; e += TPB) {
-      const int i = e / SUB, k = e % SUB;
-      sa[k][i] = base + k < s1 ? A[(size_t)i * n + base + k] : 0.0f;
+  // the next tile is fetched into registers while the current one is used
+  constexpr int PA = (M * SUB + TPB - 1) / TPB, PB = (N * SUB + TPB - 1) / TPB;
+  float ra[PA], rb[PB];
+  auto fetch = [&](long base) {
+#pragma unroll
+    for (int q = 0; q < PA; ++q) {
+      const int e = tid + q * TPB, i = e / SUB, k = e % SUB;
+      ra[q] = e < M * SUB && base + k < s1 ? A[(size_t)i * n + base + k] : 0.0f;
     }
-    for (int e = tid; e < N * SUB; e += TPB) {
-      const int j = e / SUB, k = e % SUB;
-      sb[k][j] = base + k < s1 ? B[(size_t)j * n + base + k] : 0.0f;
+#pragma unroll
+    for (int q = 0; q < PB; ++q) {
+      const int e = tid + q * TPB, j = e / SUB, k = e % SUB;
+      rb[q] = e < N * SUB && base + k < s1 ? B[(size_t)j * n + base + k] : 0.0f;
+    }
+  };
+  fetch(s0);
+  for (long base = s0; base < s1; base += SUB) {
+#pragma unroll
+    for (int q = 0; q < PA; ++q) {
+      const int e = tid + q * TPB;
+      if (e < M * SUB) sa[e % SUB][e / SUB] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < PB; ++q) {
+      const int e = tid + q * TPB;
+      if (e < N * SUB) sb[e % SUB][e / SUB] = rb[q];
     }
     __syncthreads();
+    if (base + SUB < s1) fetch(base + SUB);
 #pragma unroll 8
     for (int k = 0; k < SUB; ++k) {
       const float4 a4 = *reinterpret_cast<const float4*>(&sa[k][ti]);
@@ -269,21 +288,35 @@ __global__ void __launch_bounds__(256) vec_kernel(const float* __restrict__ a, c
   }
 }
 
-__global__ void reduce_kernel(const float* __restrict__ partial, int blocks, int count,
-                              float* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
+// out[i] = sum over b of partial[b][i]: a CTA takes 32 outputs (one per
+// lane), its 8 warps sum interleaved eighths of the partials, then the
+// warps' sums are added in a fixed order.
+__global__ void __launch_bounds__(256) reduce_kernel(const float* __restrict__ partial, int blocks, int count,
+                                                     float* __restrict__ out) {
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
   float t = 0.0f;
-  for (int b = 0; b < blocks; ++b) t += partial[(size_t)b * count + i];
-  out[i] = t;
+  if (i < count)
+    for (int b = w; b < blocks; b += 8) t += partial[(size_t)b * count + i];
+  red[w][lane] = t;
+  __syncthreads();
+  if (w == 0 && i < count) {
+    float u = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) u += red[q][lane];
+    out[i] = u;
+  }
 }
 
-// Bias-corrected Adam (Kingma & Ba): c1 = 1 - b1^t, c2 = 1 - b2^t.
+// Bias-corrected Adam (Kingma & Ba): c1 = 1 - b1^t, c2 = 1 - b2^t.  A
+// non-finite gradient sets *bad (read by cinr_trainer_status).
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, long n, float lr, float b1, float b2, float eps,
-                            float c1, float c2) {
+                            float c1, float c2, int* __restrict__ bad) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const float gi = g[i];
+    if (!isfinite(gi)) atomicOr(bad, 1);
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
@@ -376,9 +409,9 @@ int grads(cinr_trainer_s* t, const float* xyz, const float* tgt, long n, const f
   outer_kernel<H, IN><<<blocks, (H / 4) * (IN / 4), 0, s>>>(a_dh1, a_feat, n, p1);
   outer_kernel<H, H><<<blocks, (H / 4) * (H / 4), 0, s>>>(a_dh2, a_h1, n, p2);
   vec_kernel<H><<<blocks, 256, 0, s>>>(a_dy, a_h2, n, p3);
-  reduce_kernel<<<(H * IN + 255) / 256, 256, 0, s>>>(p1, blocks, H * IN, g_w);
-  reduce_kernel<<<(H * H + 255) / 256, 256, 0, s>>>(p2, blocks, H * H, g_w + H * IN);
-  reduce_kernel<<<(H + 255) / 256, 256, 0, s>>>(p3, blocks, H, g_w + H * IN + H * H);
+  reduce_kernel<<<(H * IN + 31) / 32, 256, 0, s>>>(p1, blocks, H * IN, g_w);
+  reduce_kernel<<<(H * H + 31) / 32, 256, 0, s>>>(p2, blocks, H * H, g_w + H * IN);
+  reduce_kernel<<<(H + 31) / 32, 256, 0, s>>>(p3, blocks, H, g_w + H * IN + H * H);
   CINR_CK(cudaGetLastError());
   return CINR_OK;
 }
@@ -431,11 +464,12 @@ extern "C" int cinr_create_trainer(cinr_inr_t inr, const cinr_train_opts* o, voi
   t->loss = L.loss;
   t->step = 0;
   t->n_part = (int)((o->batch + kChunk - 1) / kChunk);
-  const cudaError_t ce1 = cudaMemsetAsync(L.m_w, 0, sizeof(float) * t->n_w, s);
-  const cudaError_t ce2 = ce1 == cudaSuccess ? cudaMemsetAsync(L.v_w, 0, sizeof(float) * t->n_w, s) : ce1;
-  if (ce2 != cudaSuccess) {
+  cudaError_t ce = cudaMemsetAsync(L.m_w, 0, sizeof(float) * t->n_w, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(L.v_w, 0, sizeof(float) * t->n_w, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(L.loss, 0, 64 * sizeof(float), s);
+  if (ce != cudaSuccess) {
     delete t;
-    return cuda_error(ce2, "cudaMemsetAsync");
+    return cuda_error(ce, "cudaMemsetAsync");
   }
   *out = t;
   return CINR_OK;
@@ -444,6 +478,37 @@ extern "C" int cinr_create_trainer(cinr_inr_t inr, const cinr_train_opts* o, voi
 extern "C" int cinr_destroy_trainer(cinr_trainer_t t) {
   delete t;
   return CINR_OK;
+}
+
+extern "C" int cinr_trainer_set_lr(cinr_trainer_t t, float lr) {
+  if (!t) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (!(lr > 0.0f)) return set_error(CINR_ERR_ARG, "lr must be positive");
+  t->o.lr = lr;
+  return CINR_OK;
+}
+
+extern "C" int cinr_trainer_status(cinr_trainer_t t, cinr_stream_t stream) {
+  if (!t) return set_error(CINR_ERR_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* bad = reinterpret_cast<int*>(t->loss + 1);
+  int h = 0;
+  CINR_CK(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaStreamSynchronize(s));
+  if (!h) return CINR_OK;
+  CINR_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  return set_error(CINR_ERR_NAN, "a training step produced a non-finite gradient");
+}
+
+extern "C" int cinr_train(cinr_inr_t inr, const float* field_dev, const int dims[3], const cinr_train_opts* o,
+                          long steps, void* workspace, size_t ws_bytes, cinr_stream_t stream) {
+  if (steps < 0) return set_error(CINR_ERR_ARG, "steps must be >= 0");
+  cinr_trainer_t t = nullptr;
+  int e = cinr_create_trainer(inr, o, workspace, ws_bytes, stream, &t);
+  if (e) return e;
+  for (long i = 0; i < steps && !e; ++i) e = cinr_train_step(t, field_dev, dims, nullptr, stream);
+  if (!e) e = cinr_trainer_status(t, stream);
+  cinr_destroy_trainer(t);
+  return e;
 }
 
 extern "C" int cinr_train_step(cinr_trainer_t t, const float* field_dev, const int dims[3], float* loss_dev,
@@ -462,11 +527,12 @@ extern "C" int cinr_train_step(cinr_trainer_t t, const float* field_dev, const i
   float* table = const_cast<float*>(static_cast<const float*>(t->inr->dev.table));
   float* w = const_cast<float*>(t->inr->dev.w);
   const unsigned gb = (unsigned)num_sms() * 8;
+  int* bad = reinterpret_cast<int*>(t->loss + 1);
   adam_kernel<<<gb, 256, 0, s>>>(table, t->g_t, t->m_t, t->v_t, t->n_table, t->o.lr, t->o.beta1, t->o.beta2,
-                                 t->o.eps, (float)c1, (float)c2);
+                                 t->o.eps, (float)c1, (float)c2, bad);
   adam_kernel<<<(unsigned)((t->n_w + 255) / 256), 256, 0, s>>>(w, t->g_w, t->m_w, t->v_w, t->n_w, t->o.lr,
                                                               t->o.beta1, t->o.beta2, t->o.eps, (float)c1,
-                                                              (float)c2);
+                                                              (float)c2, bad);
   half_copy_kernel<<<(unsigned)((t->n_w + 255) / 256), 256, 0, s>>>(
       w, t->inr->w16, (int)t->n_w, t->inr->p.mlp_precision == CINR_PREC_BF16);
   CINR_CK(cudaGetLastError());

@@ -84,3 +84,46 @@ def test_training_gains_over_untrained_network():
     assert losses[-1] < 0.05 * losses[0]
     assert after > before + 15.0, (before, after)
     assert after > 30.0, after
+
+
+def test_one_call_train_matches_oracle_adam():
+    # cinr_train = a fresh trainer's steps: after 3 steps the parameters
+    # follow the oracle's Adam path as the step-by-step trainer's do
+    import torch
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.InrConfig(levels=8, feats=2, log2_table=12, base_res=4, growth=1.5, hidden=32)
+    table, w = scene(cfg, seed=5, table_scale=0.2)
+    field = S.explicit_field((24, 20, 16), S.field_params(1, n_gaussians=6))
+    inr = _inr(cfg, table, w)
+    cinr.train(inr, torch.from_numpy(field).cuda(), 3, batch=2048, seed=77)
+    otr = O.Trainer(oracle_params(cfg), table, w, field, 0.0, 1.0, batch=2048, seed=77)
+    for _ in range(3):
+        otr.step()
+    gt, gw = cinr.inr_export(inr)
+    assert np.mean(np.abs(gt - otr.table) < 1e-4) > 0.95
+    assert np.mean(np.abs(gw - otr.w) < 1e-3) > 0.95
+
+
+def test_non_finite_field_reports_nan_status():
+    # a NaN in the ground truth makes the gradient non-finite: the step runs,
+    # the status call reports CINR_ERR_NAN once and clears the flag; the
+    # one-call trainer returns the same error
+    import torch
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.InrConfig(levels=8, feats=2, log2_table=12, base_res=4, growth=1.5, hidden=32)
+    table, w = scene(cfg, seed=5, table_scale=0.2)
+    field = S.explicit_field((24, 20, 16), S.field_params(1, n_gaussians=6))
+    f_dev = torch.from_numpy(field).cuda()
+    tr = cinr.Trainer(_inr(cfg, table, w), batch=2048, seed=1)
+    tr.step(f_dev)
+    tr.status()  # finite: no error
+    bad = f_dev.clone()
+    bad.fill_(float("nan"))
+    tr.step(bad)
+    with pytest.raises(cinr.CinrError) as ei:
+        tr.status()
+    assert ei.value.code == cinr.ERR_NAN
+    tr.status()  # cleared
+    with pytest.raises(cinr.CinrError) as ei:
+        cinr.train(_inr(cfg, table, w), bad, 2, batch=2048)
+    assert ei.value.code == cinr.ERR_NAN

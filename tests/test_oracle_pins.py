@@ -279,6 +279,35 @@ def test_stochastic_lod_footprint_mode_piecewise_linear_log2():
 
 
 # ------------------------------------------------------------------ cache
+def _golden_rows(kind):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_examples.txt")
+    rows = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, args, want, cite = line.rstrip("\n").split("\t")
+        if k == kind:
+            kv = lambda t: {a.split("=")[0]: a.split("=")[1] for a in t.split()}
+            rows.append((kv(args), kv(want), cite))
+    assert rows, kind
+    return rows
+
+
+def test_paper_printed_examples():
+    # the worked brick mapping of Sec. 4.3.2 and the macro-cell sizes of
+    # Sec. 6.3, from the golden fixture
+    ints = lambda t: tuple(int(v) for v in t.split(","))
+    for a, want, cite in _golden_rows("brick_origin"):
+        o = O.brick_origin(ints(a["vol"]), int(a["brick"]), int(a["level"]), ints(a["id"]))
+        assert tuple(o) == tuple(float(v) for v in want["origin"].split(",")), cite
+    for a, want, cite in _golden_rows("macro_cells"):
+        n = int(np.prod(O.macro_dims(ints(a["vol"]), int(a["cell"]))))
+        assert n == int(want["cells"]), cite
+        # the ranges are two binary32 per cell (float32 [cells, 2] here too)
+        assert 8 * n == int(want["range_bytes"]), cite
+
+
 def test_brick_origin_worked_example():
     # Sec. 4.3.2: request id (0,1,2) at LoD 1 with brick side 40 starts at
     # (0, 79, 159) in LoD-0 voxel coordinates.  y and z must match exactly.
