@@ -555,6 +555,15 @@ int cinr_debug_mma_tile(const float* a_dev, const float* b_dev, int K,
  * (CINR_ERR_TIMEOUT), clearing the flag. */
 int cinr_inr_status(cinr_inr_t inr, cinr_stream_t stream);
 
+/* Failure-detection self-test (enqueued on `stream`): one warp waits, with
+ * `limit` polls (1 .. 2^22), for an mbarrier phase that nothing completes,
+ * gives up, and sets this INR's status word the way the tensor-core MLP
+ * kernels do when a wait runs out; the next cinr_inr_status reports
+ * CINR_ERR_TIMEOUT.  The kernel ends by itself and the context stays
+ * usable. */
+int cinr_debug_wait_timeout(cinr_inr_t inr, unsigned limit,
+                            cinr_stream_t stream);
+
 /* Geometry of the cache's LoD `level`: voxel dims, brick counts per axis and
  * the key of its first brick (keys are level-major, x fastest). */
 int cinr_cache_level_info(cinr_cache_t cache, int level, int dims[3],

@@ -134,6 +134,7 @@ _SIGS = {
     "cinr_debug_dump": [_vp, C.c_int, _vp, C.c_size_t, _P(C.c_size_t), _vp],
     "cinr_debug_mma_tile": [_vp, _vp, C.c_int, C.c_int, _vp, _vp],
     "cinr_inr_status": [_vp, _vp],
+    "cinr_debug_wait_timeout": [_vp, C.c_uint, _vp],
     "cinr_cache_level_info": [_vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_long)],
     "cinr_macro_bytes": [_P(C.c_int), C.c_int, _P(C.c_size_t)],
     "cinr_create_macro": [_P(cinr_macro_desc), _vp, C.c_size_t, _vp, _P(_vp)],

@@ -167,6 +167,26 @@ extern "C" int cinr_debug_mma_tile(const float* a_dev, const float* b_dev, int K
   return CINR_OK;
 }
 
+// Failure-detection self-test: one warp waits, with `limit` polls, for a
+// phase of an mbarrier that nothing arrives at, and records the timeout in
+// the status word the MLP kernels use.  No tensor memory is allocated.
+__global__ void debug_wait_kernel(int* err, uint32_t limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+  __syncthreads();
+  const bool ok = tc::mbar_wait(&bar, 0, limit);
+  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+extern "C" int cinr_debug_wait_timeout(cinr_inr_t inr, unsigned limit, cinr_stream_t stream) {
+  if (!inr) return set_error(CINR_ERR_ARG, "inr is NULL");
+  if (limit < 1 || limit > (1u << 22)) return set_error(CINR_ERR_ARG, "limit must be in [1, 2^22]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  debug_wait_kernel<<<1, 32, 0, s>>>(reinterpret_cast<int*>(inr->scratch + 16), limit);
+  CINR_CK(cudaGetLastError());
+  return CINR_OK;
+}
+
 extern "C" int cinr_inr_status(cinr_inr_t inr, cinr_stream_t stream) {
   if (!inr) return set_error(CINR_ERR_ARG, "inr is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -2,7 +2,8 @@
 the volume (no samples, nothing requested), a single-pixel image, a volume
 smaller than one brick, a one-LoD cache (everything preloaded: no request),
 a request budget of one brick, termination at the first segment boundary,
-and the largest request budget the library accepts."""
+the largest request budget the library accepts, and a bounded device-side
+wait that runs out (reported, not faulted)."""
 import numpy as np
 import pytest
 
@@ -61,3 +62,27 @@ def test_largest_request_budget():
     cinr.Cache(inr, (64, 64, 64), pool_bytes=600 * 4000, brick=8, levels=3, n_req=8192)
     with pytest.raises(cinr.CinrError):
         cinr.Cache(inr, (64, 64, 64), pool_bytes=600 * 4000, brick=8, levels=3, n_req=8193)
+
+
+def test_bounded_wait_runs_out_and_reports_timeout():
+    # failure detection without a fault: a wait on an mbarrier phase that
+    # nothing completes gives up after its poll limit, the status call
+    # reports CINR_ERR_TIMEOUT once (then clears), and the context stays
+    # usable for inference
+    import ctypes as C
+    import torch
+    from paper_2504_18001_gb300 import cinr
+    from _scenes import gpu_inr, scene
+    cfg = S.INR_64
+    table, w = scene(cfg)
+    inr = gpu_inr(cfg, table, w, vol=(32, 32, 32), mlp="bf16")
+    L = cinr.lib()
+    s = cinr._stream(None)
+    assert L.cinr_inr_status(inr.h, s) == 0
+    cinr.check(L.cinr_debug_wait_timeout(inr.h, 256, s), "cinr_debug_wait_timeout")
+    assert L.cinr_inr_status(inr.h, s) == cinr.ERR_TIMEOUT
+    assert "wait gave up" in cinr.last_error()
+    assert L.cinr_inr_status(inr.h, s) == 0
+    v = inr.infer(torch.from_numpy(S.random_points(1000, 3)).cuda())
+    assert torch.isfinite(v).all()
+    assert L.cinr_inr_status(inr.h, s) == 0
