@@ -981,110 +981,146 @@ __global__ void __launch_bounds__(kFrameThreads, 5) pt_kernel(const __grid_const
   const int lane = threadIdx.x & 31;
   const CamDev& cam = P.cam;
   PtCounts n = {0, 0, 0, 0, 0, 0};
-  const uint32_t n_tiles = P.n_rays >> 5;
+  const bool local = P.mac.major != nullptr;  // per-cell majorants
+  // Path regeneration: a lane whose path has ended takes the next ray at
+  // once (rays handed out from the frame's counter, a warp's requests in
+  // one atomic), so no lane idles while the others of its warp finish
+  // longer paths.  A ray's path depends only on its pixel: images and
+  // cache state are those of one path per pixel in any order.
+  //
+  // Per path, one loop over tracking steps with a per-lane mode, so that
+  // the free flight, the walk and the lookup exist once in the code: lanes
+  // tracking a camera or scattered segment (delta tracking) and lanes
+  // tracking a shadow segment (ratio tracking) share those instructions.
+  // Random numbers and lookups come in the order of the nested
+  // formulation: per bounce the segment's flights and decisions, then the
+  // shadow segment's flights, then the scattering direction.
+  bool live = false, exhausted = false;
+  uint32_t pixel = 0, rseed = 0, j = 0, k = 0;
+  uint64_t key = 0;
+  float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f}, t = 0.f, t1 = 0.f;
+  float Lr = 0.f, Lg = 0.f, Lb = 0.f, alpha = 0.f, br = 1.f, bg = 1.f, bb = 1.f, Tr = 1.f;
+  float p[3] = {0.f, 0.f, 0.f};
+  int b = 0, steps = 0;
+  bool shadow = false, begin = false;
+  PtWalk W;
   while (true) {
-    uint32_t tile = 0;
-    if (lane == 0) tile = atomicAdd(P.ray_counter, 1u);
-    tile = __shfl_sync(kFull, tile, 0);
-    if (tile >= n_tiles) break;
-    const uint32_t r = tile * 32u + (uint32_t)lane;
-    const uint32_t t64 = r >> 6, w = r & 63u;
-    const int px = (int)((t64 % P.tiles_x) * 8 + (w & 7u));
-    const int py = (int)((t64 / P.tiles_x) * 8 + (w >> 3));
-    if (px >= cam.W || py >= cam.H) continue;
-    const uint32_t pixel = (uint32_t)(py * cam.W + px);
-    float o[3] = {cam.o[0], cam.o[1], cam.o[2]}, d[3], t = 0.f, t1 = 0.f;
-    float Lr = P.pt_amb[0], Lg = P.pt_amb[1], Lb = P.pt_amb[2], alpha = 0.f;
-    if (ray_setup(cam, px, py, d, t, t1)) {
-      // One loop over tracking steps with a per-lane mode, so that the free
-      // flight, the walk and the lookup exist once in the code: lanes
-      // tracking a camera or scattered segment (delta tracking) and lanes
-      // tracking a shadow segment (ratio tracking) share those
-      // instructions.  Random numbers and lookups come in the order of the
-      // nested formulation: per bounce the segment's flights and decisions,
-      // then the shadow segment's flights, then the scattering direction.
-      const uint64_t key = ((uint64_t)P.fseed << 32) | (uint64_t)pixel;
-      const uint32_t rseed = ray_seed(P.fseed, pixel);
-      const bool local = P.mac.major != nullptr;  // per-cell majorants
-      float br = 1.f, bg = 1.f, bb = 1.f, Tr = 1.f, p[3] = {0.f, 0.f, 0.f};
-      Lr = Lg = Lb = 0.f;
-      uint32_t j = 0, k = 0;
-      int b = 0, steps = 0;
-      bool shadow = false, begin = true;
-      PtWalk W;
-      while (true) {
-        if (begin) {  // a segment o + t d, t in [t, t1), starts
-          if (local) walk_init(W, P.mac, cam, o, d, t, t1);
-          steps = 0;
-          begin = false;
-        }
-        bool got = false;
-        float maj = P.pt_sbar;
-        if ((local || P.pt_sbar > 0.0f) && steps < kPtMaxSteps) {
-          ++steps;
-          const float tau = neg_log1m(pt_uniform(key, j++));
-          if (local) {
-            got = walk_flight(W, P.mac, tau, t, maj);
-          } else {
-            t = f_add(t, f_mul(tau, P.pt_inv));
-            got = t < t1;
+    const bool need = !live && !exhausted;
+    const unsigned nm = __ballot_sync(kFull, need);
+    if (nm) {
+      const int leader = __ffs(nm) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(P.ray_counter, (uint32_t)__popc(nm));
+      base = __shfl_sync(kFull, base, leader);
+      if (need) {
+        const uint32_t r = base + (uint32_t)__popc(nm & ((1u << lane) - 1u));
+        if (r >= P.n_rays) {
+          exhausted = true;
+        } else {
+          const uint32_t t64 = r >> 6, w = r & 63u;  // rays in 8x8 pixel tiles
+          const int px = (int)((t64 % P.tiles_x) * 8 + (w & 7u));
+          const int py = (int)((t64 / P.tiles_x) * 8 + (w >> 3));
+          if (px < cam.W && py < cam.H) {
+            pixel = (uint32_t)(py * cam.W + px);
+            o[0] = cam.o[0];
+            o[1] = cam.o[1];
+            o[2] = cam.o[2];
+            if (ray_setup(cam, px, py, d, t, t1)) {
+              key = ((uint64_t)P.fseed << 32) | (uint64_t)pixel;
+              rseed = ray_seed(P.fseed, pixel);
+              br = bg = bb = Tr = 1.f;
+              Lr = Lg = Lb = alpha = 0.f;
+              j = k = 0;
+              b = 0;
+              shadow = false;
+              begin = live = true;
+            } else {
+              P.out[pixel] = make_float4(P.pt_amb[0], P.pt_amb[1], P.pt_amb[2], 0.f);
+            }
           }
         }
-        if (got) {
-          float q[3], x[3], dist;
-          pt_point(cam, o, d, t, q, x, dist);
-          const float v = pt_value<IN, H, CACHED, F16POOL, MISS>(P, s_geo, x, dist, rseed, k, pixel, n);
-          ++k;
-          const float4 e4 = tf_lookup(s_tf, v);
-          if (shadow) {
-            Tr *= 1.0f - (local ? f_div(e4.w, maj) : e4.w * P.pt_inv);
-          } else if (pt_uniform(key, j++) * maj < e4.w) {
-            // real collision: albedo, then next-event estimation along the
-            // shadow segment towards the light
-            if (b == 0) alpha = 1.f;
-            br *= e4.x;
-            bg *= e4.y;
-            bb *= e4.z;
-            p[0] = q[0];
-            p[1] = q[1];
-            p[2] = q[2];
-            o[0] = q[0];
-            o[1] = q[1];
-            o[2] = q[2];
-            d[0] = P.pt_ls[0];
-            d[1] = P.pt_ls[1];
-            d[2] = P.pt_ls[2];
-            t = 0.f;
-            t1 = box_exit(cam, o, d);
-            Tr = 1.f;
-            shadow = begin = true;
-          }
-          continue;
-        }
-        // the segment ended without a (further) collision
-        if (!shadow) {  // escaped: ambient radiance
-          Lr = fmaf(br, P.pt_amb[0], Lr);
-          Lg = fmaf(bg, P.pt_amb[1], Lg);
-          Lb = fmaf(bb, P.pt_amb[2], Lb);
-          break;
-        }
-        const float ne = Tr * 0.0795774715459476679f;  // 1 / (4 pi)
-        Lr = fmaf(br * P.pt_light[0], ne, Lr);
-        Lg = fmaf(bg * P.pt_light[1], ne, Lg);
-        Lb = fmaf(bb * P.pt_light[2], ne, Lb);
-        if (b + 1 >= P.pt_bounces) break;
-        ++b;
-        pt_sphere(key, j, d);
-        o[0] = p[0];
-        o[1] = p[1];
-        o[2] = p[2];
-        t = 0.f;
-        t1 = box_exit(cam, o, d);
-        shadow = false;
-        begin = true;
       }
     }
-    P.out[pixel] = make_float4(Lr, Lg, Lb, alpha);
+    if (!__any_sync(kFull, live)) {
+      if (__all_sync(kFull, exhausted)) break;
+      continue;
+    }
+    if (!live) continue;
+    if (begin) {  // a segment o + t d, t in [t, t1), starts
+      if (local) walk_init(W, P.mac, cam, o, d, t, t1);
+      steps = 0;
+      begin = false;
+    }
+    bool got = false;
+    float maj = P.pt_sbar;
+    if ((local || P.pt_sbar > 0.0f) && steps < kPtMaxSteps) {
+      ++steps;
+      const float tau = neg_log1m(pt_uniform(key, j++));
+      if (local) {
+        got = walk_flight(W, P.mac, tau, t, maj);
+      } else {
+        t = f_add(t, f_mul(tau, P.pt_inv));
+        got = t < t1;
+      }
+    }
+    if (got) {
+      float q[3], x[3], dist;
+      pt_point(cam, o, d, t, q, x, dist);
+      const float v = pt_value<IN, H, CACHED, F16POOL, MISS>(P, s_geo, x, dist, rseed, k, pixel, n);
+      ++k;
+      const float4 e4 = tf_lookup(s_tf, v);
+      if (shadow) {
+        Tr *= 1.0f - (local ? f_div(e4.w, maj) : e4.w * P.pt_inv);
+      } else if (pt_uniform(key, j++) * maj < e4.w) {
+        // real collision: albedo, then next-event estimation along the
+        // shadow segment towards the light
+        if (b == 0) alpha = 1.f;
+        br *= e4.x;
+        bg *= e4.y;
+        bb *= e4.z;
+        p[0] = q[0];
+        p[1] = q[1];
+        p[2] = q[2];
+        o[0] = q[0];
+        o[1] = q[1];
+        o[2] = q[2];
+        d[0] = P.pt_ls[0];
+        d[1] = P.pt_ls[1];
+        d[2] = P.pt_ls[2];
+        t = 0.f;
+        t1 = box_exit(cam, o, d);
+        Tr = 1.f;
+        shadow = begin = true;
+      }
+      continue;
+    }
+    // the segment ended without a (further) collision
+    if (!shadow) {  // escaped: ambient radiance; the path is complete
+      Lr = fmaf(br, P.pt_amb[0], Lr);
+      Lg = fmaf(bg, P.pt_amb[1], Lg);
+      Lb = fmaf(bb, P.pt_amb[2], Lb);
+      P.out[pixel] = make_float4(Lr, Lg, Lb, alpha);
+      live = false;
+      continue;
+    }
+    const float ne = Tr * 0.0795774715459476679f;  // 1 / (4 pi)
+    Lr = fmaf(br * P.pt_light[0], ne, Lr);
+    Lg = fmaf(bg * P.pt_light[1], ne, Lg);
+    Lb = fmaf(bb * P.pt_light[2], ne, Lb);
+    if (b + 1 >= P.pt_bounces) {
+      P.out[pixel] = make_float4(Lr, Lg, Lb, alpha);
+      live = false;
+      continue;
+    }
+    ++b;
+    pt_sphere(key, j, d);
+    o[0] = p[0];
+    o[1] = p[1];
+    o[2] = p[2];
+    t = 0.f;
+    t1 = box_exit(cam, o, d);
+    shadow = false;
+    begin = true;
   }
   unsigned long long a[6] = {n.samp, n.hit, n.fb, n.miss, n.req, n.slot};
 #pragma unroll
