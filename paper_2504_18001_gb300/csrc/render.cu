@@ -885,13 +885,14 @@ __device__ __forceinline__ bool walk_flight(PtWalk& w, const MacroDev& m, float 
 // cache, by direct inference.  Atomics are per lane: the rank update
 // max(r, T_f) + 1 clamped at T_f + 1000 and the stamp reach the same final
 // state in any order.
-template <int IN, int H, bool CACHED, bool F16POOL, bool MISS>
+template <int IN, int H, bool CACHED, bool F16POOL, bool MISS, int BB>
 __device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const float x[3], float dist,
                           uint32_t rseed, uint32_t k, uint32_t pixel, PtCounts& n) {
   ++n.samp;
   if (CACHED) {
     const CacheDev& c = P.cache;
-    const int L = c.L, B = c.B, S = c.S;
+    const int L = c.L, B = BB ? BB : c.B, S = BB ? BB + 2 : c.S;
+    const float invB = BB ? 1.0f / (float)BB : c.invB;
     const size_t S3 = (size_t)S * S * S;
     const int l = sample_lod(P.cam, L, 0, rseed, k, dist);
     const float pv0 = f_mul(x[0], (float)c.vol[0]), pv1 = f_mul(x[1], (float)c.vol[1]),
@@ -899,9 +900,9 @@ __device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const flo
     for (int lev = l; lev < L; ++lev) {
       const LevelGeo g = s_geo[lev];
       const float s0 = f_mul(pv0, g.scale), s1 = f_mul(pv1, g.scale), s2 = f_mul(pv2, g.scale);
-      int b0 = (int)floorf(c.invB > 0.0f ? f_mul(s0, c.invB) : f_div(s0, (float)B));
-      int b1 = (int)floorf(c.invB > 0.0f ? f_mul(s1, c.invB) : f_div(s1, (float)B));
-      int b2 = (int)floorf(c.invB > 0.0f ? f_mul(s2, c.invB) : f_div(s2, (float)B));
+      int b0 = (int)floorf(BB || invB > 0.0f ? f_mul(s0, invB) : f_div(s0, (float)B));
+      int b1 = (int)floorf(BB || invB > 0.0f ? f_mul(s1, invB) : f_div(s1, (float)B));
+      int b2 = (int)floorf(BB || invB > 0.0f ? f_mul(s2, invB) : f_div(s2, (float)B));
       b0 = min(max(b0, 0), g.nb0 - 1);
       b1 = min(max(b1, 0), g.nb1 - 1);
       b2 = min(max(b2, 0), g.nb2 - 1);
@@ -958,7 +959,7 @@ __device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const flo
 
 // MISS: lookups that can end in direct inference (no cache, or a cache
 // without the coarsest-LoD preload).
-template <int IN, int H, bool CACHED, bool F16POOL, bool MISS>
+template <int IN, int H, bool CACHED, bool F16POOL, bool MISS, int BB>
 __global__ void __launch_bounds__(kFrameThreads, 5) pt_kernel(const __grid_constant__ FrameParams P) {
   __shared__ float4 s_tf[256];
   __shared__ LevelGeo s_geo[kMaxLod];
@@ -1066,7 +1067,7 @@ __global__ void __launch_bounds__(kFrameThreads, 5) pt_kernel(const __grid_const
     if (got) {
       float q[3], x[3], dist;
       pt_point(cam, o, d, t, q, x, dist);
-      const float v = pt_value<IN, H, CACHED, F16POOL, MISS>(P, s_geo, x, dist, rseed, k, pixel, n);
+      const float v = pt_value<IN, H, CACHED, F16POOL, MISS, BB>(P, s_geo, x, dist, rseed, k, pixel, n);
       ++k;
       const float4 e4 = tf_lookup(s_tf, v);
       if (shadow) {
@@ -1139,9 +1140,9 @@ __global__ void __launch_bounds__(kFrameThreads, 5) pt_kernel(const __grid_const
   }
 }
 
-template <int IN, int H, bool CACHED, bool F16POOL, bool MISS>
+template <int IN, int H, bool CACHED, bool F16POOL, bool MISS, int BB>
 int launch_pt(const FrameParams& P, cudaStream_t s) {
-  auto k = pt_kernel<IN, H, CACHED, F16POOL, MISS>;
+  auto k = pt_kernel<IN, H, CACHED, F16POOL, MISS, BB>;
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
@@ -1152,13 +1153,23 @@ int launch_pt(const FrameParams& P, cudaStream_t s) {
   return CINR_OK;
 }
 
+// Lookups that can end in direct inference use the INR's shape; cached
+// lookups without true misses specialise the brick size instead.
 template <bool CACHED, bool F16POOL, bool MISS>
 int launch_pt_pool(const FrameParams& P, cudaStream_t s) {
-  switch (shape_of(P.inr.IN, P.inr.H)) {
-    case Shape::S16x32: return launch_pt<16, 32, CACHED, F16POOL, MISS>(P, s);
-    case Shape::S32x64: return launch_pt<32, 64, CACHED, F16POOL, MISS>(P, s);
-    case Shape::S48x64: return launch_pt<48, 64, CACHED, F16POOL, MISS>(P, s);
-    default: return set_error(CINR_ERR_ARG, "unsupported shape");
+  if constexpr (CACHED && !MISS) {
+    switch (P.cache.B) {
+      case 8: return launch_pt<16, 32, CACHED, F16POOL, false, 8>(P, s);
+      case 16: return launch_pt<16, 32, CACHED, F16POOL, false, 16>(P, s);
+      default: return launch_pt<16, 32, CACHED, F16POOL, false, 0>(P, s);
+    }
+  } else {
+    switch (shape_of(P.inr.IN, P.inr.H)) {
+      case Shape::S16x32: return launch_pt<16, 32, CACHED, F16POOL, MISS, 0>(P, s);
+      case Shape::S32x64: return launch_pt<32, 64, CACHED, F16POOL, MISS, 0>(P, s);
+      case Shape::S48x64: return launch_pt<48, 64, CACHED, F16POOL, MISS, 0>(P, s);
+      default: return set_error(CINR_ERR_ARG, "unsupported shape");
+    }
   }
 }
 

@@ -55,6 +55,35 @@ def test_cached_pt_constant_extinction_state_bit_exact(preload, lag):
         assert st["samples"] > 0 and got[..., 3].sum() > 0
 
 
+@pytest.mark.parametrize("brick,slots,n_req", [(16, 30, 12), (6, 300, 80)], ids=["b16", "b6"])
+def test_cached_pt_brick_sizes_state_bit_exact(brick, slots, n_req):
+    # the path tracer's lookups are specialised for 8^3 and 16^3 bricks;
+    # 6^3 takes the generic instantiation (exact division)
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.INR_64
+    vol = (64, 64, 64)
+    table, w = scene(cfg)
+    inr = gpu_inr(cfg, table, w, vol=vol)
+    p = oracle_inr(cfg, table, w, vol=vol)
+    S3 = (brick + 2) ** 3
+    cache = cinr.Cache(inr, vol, pool_bytes=slots * S3 * 4, brick=brick, levels=3, n_req=n_req)
+    mo = O.march_opts(K=32, eps_T=0.0, seed=13)
+    oc = O.Cache(p, table, w, vol, brick, 3, slots, mo, n_req=n_req)
+    r = cinr.Renderer(40, 32, vol, K=32, eps_T=0.0, seed=13)
+    tf = S.tf_constant((0.9, 0.7, 0.5), 6.0)
+    gpt, opt = _pt_pair()
+    for f in range(3):
+        cam = S.orbit_camera(5 * f, 40, 32, distance=1.7)
+        img, st = r.render_pt(inr, cam, tf, gpt, cache=cache)
+        ref, rst = oc.render_pt(ocam(cam), tf.astype(np.float64), opt)
+        for k in ("samples", "hits", "fallback_hits", "bricks_requested", "bricks_decoded"):
+            assert st[k] == rst[k], (f, k, st[k], rst[k])
+        for g, o in ((cinr.DUMP_PAGE_TABLE, O.DUMP_PT), (cinr.DUMP_STAMPS, O.DUMP_STAMP),
+                     (cinr.DUMP_RANK, O.DUMP_RANK)):
+            assert np.array_equal(cache.dump(g), oc.dump(o)), (f, g)
+        assert np.abs(img.cpu().numpy() - ref).max() < 1e-3 * max(1.0, np.abs(ref).max())
+
+
 def test_uncached_pt_constant_extinction_matches_oracle():
     from paper_2504_18001_gb300 import cinr
     cfg = S.INR_64
