@@ -99,3 +99,24 @@ def test_frame_stats_layout_matches_header(L):
     # 13 counters of 8 bytes, then two float timings
     assert C.sizeof(cinr.cinr_frame_stats) == 13 * 8 + 8
     assert cinr.cinr_frame_stats.samples_skipped.offset == 12 * 8
+
+
+def test_null_handles_are_rejected_without_device_work(L):
+    # every entry point that takes a handle checks it before any CUDA call
+    assert L.cinr_trainer_set_lr(None, C.c_float(1e-3)) == cinr.ERR_ARG
+    assert L.cinr_trainer_status(None, None) == cinr.ERR_ARG
+    assert L.cinr_debug_wait_timeout(None, 16, None) == cinr.ERR_ARG
+    assert L.cinr_macro_majorants(None, None, 0, None) == cinr.ERR_ARG
+    assert L.cinr_inr_status(None, None) == cinr.ERR_ARG
+    assert L.cinr_train(None, None, None, None, 1, None, 0, None) == cinr.ERR_ARG
+    assert "NULL" in cinr.last_error()
+
+
+def test_error_codes_match_header():
+    import os
+    import re
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "cinr.h")).read()
+    codes = dict((m.group(1), int(m.group(2))) for m in re.finditer(r"#define CINR_(ERR_\w+) \((-\d+)\)", text))
+    for name, val in codes.items():
+        assert getattr(cinr, name) == val, name
+    assert "ERR_NAN" in codes and "ERR_TIMEOUT" in codes
