@@ -35,9 +35,10 @@ uint32_t orc_xorshift32(uint32_t s) {
   return s;
 }
 
-/* Counter-based uniform coordinates in [0,1)^3 for training batches
- * (Sec. 4.1 "a batch of random coordinates").  Coordinate c of element j is
- * the top 24 bits of splitmix64(seed + 3*(first+j) + c), times 2^-24. */
+/* Counter-based uniform coordinates in [0,1)^3 for training batches (Sec.
+ * 4.1: each step draws a batch of random coordinates).  Coordinate c of
+ * element j is the top 24 bits of splitmix64(seed + 3*(first+j) + c),
+ * times 2^-24. */
 void orc_uniform_coords(uint64_t seed, uint64_t first, long n, float* xyz) {
   for (long j = 0; j < n; ++j)
     for (int c = 0; c < 3; ++c) {
@@ -452,8 +453,9 @@ uint32_t orc_sample_state(uint32_t ray_seed, uint32_t k) {
  * the log2 of the pixel footprint in LoD-0 voxels, with log2* the exact
  * piecewise-linear log2 read off the binary32 exponent and mantissa.
  * LoD = floor(D), plus 1 when u < frac(D) for u = (state >> 8) * 2^-24.
- * READING: Alg. 2 prints "xorshift > fraction", which would jump two levels
- * at integer D and contradict the smoothing purpose of Sec. 5.3; the
+ * READING: Alg. 2 increments when the random number exceeds the fraction,
+ * which would jump two levels at integer D and contradict the smoothing
+ * purpose of Sec. 5.3; the
  * increment is taken with probability frac(D) (stochastic rounding).
  * READING: per sample (Alg. 2), keyed by (frame, pixel, sample). */
 int orc_sample_lod(const orc_camera* cam, const int vol[3],
