@@ -395,9 +395,10 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
 // sampling, sequential front-to-back compositing and termination after every
 // K samples.  A true miss (rare: none once the coarsest LoD is preloaded) is
 // inferred in place by its lane with the FP32 weights (read through L1) and
-// recorded in the miss list with one atomic per warp.  No CTA barrier: warps
-// never wait for each other.  The discrete state and the sample set are those
-// of the segment-wise formulation.
+// recorded in the miss list with one atomic per warp.  Warps meet only at
+// the end, where the CTA adds its shared counts of rare events (new
+// requests, first stamps) to the frame statistics.  The discrete state and
+// the sample set are those of the segment-wise formulation.
 int num_sms();
 
 // A true miss of the thread-per-ray kernel: the INR at x with FP32 weights
@@ -695,11 +696,12 @@ int launch_march_cached_shape(const FrameParams& P, bool miss, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Path tracing with Woodcock delta tracking (Sec. 5.1), one path per pixel
-// and frame, thread per path (warps take 8 x 4 pixel tiles).  Every
-// quantity that positions a lookup is binary32 in a fixed order (the series
-// log, the sphere sampler and the box exits use +,-,*,/,sqrt only), so the
-// lookups, requests, stamps and misses match the oracle bit for bit; the
-// collision decisions compare u * sigma_bar with the sampled extinction.
+// and frame, thread per path (a lane takes the next ray when its path
+// ends).  Every quantity that positions a lookup is binary32 in a fixed
+// order (the series log, the sphere sampler, the box exits and the cell
+// walk use +,-,*,/,sqrt only), so the lookups, requests, stamps and misses
+// match the oracle bit for bit; the collision decisions compare u times the
+// majorant with the sampled extinction.
 
 // j-th uniform of the SplitMix64 generator started at state key (top 24 bits).
 __device__ __forceinline__ float pt_uniform(uint64_t key, uint32_t j) {
