@@ -47,20 +47,31 @@ FLY_FRAMES = 300
 WORKLOADS = {
     "orbit": dict(name="cached_{prec}_512cube_1024px_orbit", vol=(512, 512, 512), inr="INR_512",
                   brick=8, levels=4, pool_mib=1024, W=1024, H=1024, n_req=4096, step_mode=0,
-                  step_lod_max=0, warmup=90, steps=60, camera="orbit", range_stride=8,
+                  step_lod_max=0, fill=90, warmup=5, steps=60, camera="orbit", range_stride=8,
                   uncached_steps=5),
     "terascale": dict(name="terascale_{prec}_10240x7680x1536_1080p_flythrough",
                       vol=(10240, 7680, 1536), inr="INR_TERA", brick=16, levels=6,
                       pool_mib=40 * 1024, W=1920, H=1080, n_req=8192, step_mode=1,
-                      step_lod_max=5, warmup=100, steps=50, camera="fly", range_stride=64,
+                      step_lod_max=5, fill=100, warmup=5, steps=50, camera="fly", range_stride=64,
                       uncached_steps=2),
 }
 
 
-# DRAM bytes (read + write) of one marching-kernel launch on the default
-# orbit configuration, from one ncu capture of the current kernel (frame 91);
-# a workload or option without such a capture reports null.
-PROFILED_TRAFFIC = {"orbit": 436.3e6}
+# ncu summaries of one marching-kernel launch inside the timed region of the
+# default configuration (DRAM bytes, warp instructions, samples of that
+# frame), and the sources whose hash each summary records: counters taken on
+# another version of the kernel are not reported.
+PROFILE_FILES = {"orbit": "march_cached_kernel_orbit_512cube_1024px.md"}
+KERNEL_SOURCES = ("paper_2504_18001_gb300/csrc/render.cu",
+                  "paper_2504_18001_gb300/csrc/cinr_internal.cuh")
+# warp instructions a GB300 can issue per cycle: 152 SMs x 4 schedulers
+ISSUE_SLOTS = 152 * 4
+# warp instructions of one ray-marching sample served at its requested LoD
+# that the binary32 numeric contract needs at the least, counted per
+# operation: sample position and normalised coordinate 26, stochastic LoD
+# 21, page-table lookup 23, brick trilinear (8 FP16 voxels) 52, request and
+# stamp votes 3, transfer function and compositing 24, loop control 9
+CONTRACT_INST_PER_SAMPLE = 158
 # path-tracing light: a directional light from above-front, dim blue ambient
 PT_OPTS = dict(light_dir=(0.3, -1.0, -0.4), light=(3.0, 3.0, 3.0), ambient=(0.05, 0.06, 0.08),
                max_bounces=3)
@@ -182,6 +193,36 @@ def build_scene(args, wl, device):
     return cfg, table, w, inr32, inr_c, vol
 
 
+def profiled_counters(workload):
+    """ncu counters of one marching-kernel launch inside the benchmark's timed
+    region (profiles/<kernel>_<workload>.md), if they were taken on the
+    current kernel source: each summary records a hash of the sources that
+    make up the kernel, and counters from another source are not used."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", PROFILE_FILES.get(workload, ""))
+    if not os.path.isfile(path):
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            m = re.match(r"^- (\w+): (\S+)", line.strip())
+            if m:
+                vals[m.group(1)] = m.group(2)
+    if vals.get("kernel_source_sha256_12") != h.hexdigest()[:12]:
+        return None
+    try:
+        return {"frame": int(vals["frame"]), "dram_bytes": float(vals["dram_bytes"]),
+                "warp_instructions": float(vals["warp_instructions"]),
+                "samples": float(vals["samples"]), "file": os.path.join("profiles", PROFILE_FILES[workload])}
+    except (KeyError, ValueError):
+        return None
+
+
 def run_gpu(args, wl):
     import torch
     import torch.distributed as dist
@@ -210,14 +251,24 @@ def run_gpu(args, wl):
         args.ray_layout, args.graph = best["ray_layout"], best["use_graph"]
         tuned = {"chosen": best, "trials": trials}
     S3 = (wl["brick"] + 2) ** 3
-    cache = cinr.Cache(inr_c, vol, pool_bytes=wl["pool_mib"] << 20, brick=wl["brick"],
-                       levels=wl["levels"], storage=storage, n_req=wl["n_req"], ranking=1,
-                       preload=1, lag=args.lag, page=args.page, n_pages=args.n_pages,
-                       device=device)
-    rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
-                         ray_layout=args.ray_layout, seed=args.seed, step_mode=wl["step_mode"],
-                         step_lod_max=wl["step_lod_max"], use_graph=args.graph, device=device)
-    macro_ms = None
+    fill = args.fill if args.fill is not None else wl["fill"]
+    first = fill + args.warmup          # first timed frame
+    last_f = first + args.steps - 1     # last timed frame
+
+    def make_cache():
+        return cinr.Cache(inr_c, vol, pool_bytes=wl["pool_mib"] << 20, brick=wl["brick"],
+                          levels=wl["levels"], storage=storage, n_req=wl["n_req"], ranking=1,
+                          preload=1, lag=args.lag, page=args.page, n_pages=args.n_pages,
+                          device=device)
+
+    def make_renderer():
+        return cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
+                             ray_layout=args.ray_layout, seed=args.seed, step_mode=wl["step_mode"],
+                             step_lod_max=wl["step_lod_max"], use_graph=args.graph, device=device)
+
+    cache = make_cache()
+    rend = make_renderer()
+    macro_ms, mac = None, None
     if args.macro:
         # macro cells (Sec. 5.2) built from the cache's own decode arithmetic:
         # skipping transparent cells leaves cached samples unchanged
@@ -230,74 +281,103 @@ def run_gpu(args, wl):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def step(f, use_cache=True):
+    def step(f, use_cache=True, c=None, r=None):
+        c = cache if c is None else c
+        r = rend if r is None else r
         cam, tf = frame_inputs(f, W, H, wl["camera"], args.tf_ramps)
         flush.random_(0, 255)  # L2 flush between timed iterations
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         if args.pt:
             # path tracing (Woodcock delta tracking), one path per pixel per frame
-            _, st = rend.render_pt(inr_c if use_cache else inr32, cam, tf, PT_OPTS,
-                                   cache=cache if use_cache else None, out=img)
+            _, st = r.render_pt(inr_c if use_cache else inr32, cam, tf, PT_OPTS,
+                                cache=c if use_cache else None, out=img)
         elif use_cache:
-            _, st = rend.render(inr_c, cam, tf, cache=cache, out=img)
+            _, st = r.render(inr_c, cam, tf, cache=c, out=img)
         else:
-            _, st = rend.render(inr32, cam, tf, cache=None, out=img)
+            _, st = r.render(inr32, cam, tf, cache=None, out=img)
         e1.record(stream)
         return e0, e1, st
 
-    for f in range(args.warmup):
+    # 1. cache fill: the paper measures steady state (mean over the last
+    #    frames of a long run); the cache is filled by the first `fill`
+    #    frames of the camera path before the warm-up and timed frames
+    fill_decoded = []
+    for f in range(fill):
+        fill_decoded.append(step(f)[2]["bricks_decoded"])
+    # 2. warm-up frames, 3. timed frames (the camera path continues)
+    for f in range(fill, first):
         step(f)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    n_un = min(args.steps, args.uncached_steps or wl["uncached_steps"])
     clocks = ClockSampler(local)
     clocks.start()
-    times, stats = [], []
+    times, stats, kept = [], [], {}
     for i in range(args.steps):
-        e0, e1, st = step(args.warmup + i)
+        f = first + i
+        e0, e1, st = step(f)
         times.append((e0, e1))
         stats.append(st)
+        if f > last_f - n_un:
+            kept[f] = img.clone()  # for the quality gate (after the frame's end event)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in times]
     cached_ms = float(sum(ms)) / len(ms)
-    last_f = args.warmup + args.steps - 1
-    cached_img = img.clone()
+    cached_img = kept[last_f]
 
-    # uncached baseline on the last timed frames (direct INR for every sample)
-    un_ms, un_st = [], []
-    n_un = min(args.steps, args.uncached_steps or wl["uncached_steps"])
-    for i in range(n_un):
-        e0, e1, st = step(last_f - n_un + 1 + i, use_cache=False)
+    # uncached baseline on the last timed frames (direct INR for every
+    # sample; the cache is not touched), and the cached-vs-uncached PSNR of
+    # each of those frames
+    un_ms, un_st, psnr_frames = [], [], []
+    for f in range(last_f - n_un + 1, last_f + 1):
+        e0, e1, st = step(f, use_cache=False)
         torch.cuda.synchronize()
         un_ms.append(e0.elapsed_time(e1))
         un_st.append(st)
+        mse = torch.mean((kept[f][..., :3].double() - img[..., :3].double()) ** 2).item()
+        psnr_frames.append(10 * np.log10(1.0 / max(mse, 1e-30)))
     uncached_ms = float(sum(un_ms)) / len(un_ms)
     uncached_img = img.clone()
+    del kept
 
-    # end-to-end through the C ABI with host buffers (pinned), copies inside
-    host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
-    e2e = []
-    # the same frames as the timed region (every stride-th one, cache warm),
-    # so that the end-to-end number measures the same workload
-    n_e2e = max(3, min(args.steps, 10))
-    stride = max(1, args.steps // n_e2e)
-    for i in range(n_e2e):
-        cam, tf = frame_inputs(args.warmup + (i * stride) % args.steps, W, H, wl["camera"], args.tf_ramps)
-        flush.random_(0, 255)
-        stream.synchronize()  # the frame's stream only: a lag-2 decode may still run
-        t0 = time.perf_counter()
-        if args.pt:
-            rend.render_pt(inr_c, cam, tf, PT_OPTS, cache=cache, out=img)
-            host.copy_(img, non_blocking=True)
-            stream.synchronize()
-        else:
-            rend.render_host(inr_c, cam, tf, host, cache=cache)
-        e2e.append((time.perf_counter() - t0) * 1e3)
-    e2e_ms = float(sum(e2e)) / len(e2e)
+    # end-to-end through the C ABI with host buffers (pinned): a second cache
+    # replays the same fill and warm-up frames, then the timed frames are
+    # rendered again with the camera and transfer function from host memory
+    # and the image read back into pinned host memory inside the timed
+    # region.  The cache state is deterministic, so every frame meets the
+    # same cache state as in the device-timed pass (checked on the counts).
+    e2e, e2e_same = [], True
+    if not args.no_e2e:
+        del cache
+        torch.cuda.empty_cache()
+        cache2 = make_cache()
+        rend2 = make_renderer()
+        if mac is not None:
+            rend2.set_macro(mac)
+        for f in range(first):
+            step(f, c=cache2, r=rend2)
+        host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+        for i in range(args.steps):
+            cam, tf = frame_inputs(first + i, W, H, wl["camera"], args.tf_ramps)
+            flush.random_(0, 255)
+            stream.synchronize()  # the frame's stream only: a lag-2 decode may still run
+            t0 = time.perf_counter()
+            if args.pt:
+                _, st = rend2.render_pt(inr_c, cam, tf, PT_OPTS, cache=cache2, out=img)
+                host.copy_(img, non_blocking=True)
+                stream.synchronize()
+            else:
+                _, st = rend2.render_host(inr_c, cam, tf, host, cache=cache2)
+            e2e.append((time.perf_counter() - t0) * 1e3)
+            e2e_same = e2e_same and all(st[k] == stats[i][k] for k in
+                                        ("samples", "hits", "fallback_hits", "bricks_decoded"))
+        del cache2, rend2
+    e2e_ms = float(sum(e2e)) / len(e2e) if e2e else None
 
     total_ms, value_ms = replica_reduce(cached_ms * len(ms), len(ms), device)
 
@@ -322,7 +402,29 @@ def run_gpu(args, wl):
                    and not args.page
                    and args.lod_scale == 1.0 and args.lag == 1 and not args.autotune
                    and args.tf_ramps == 4)
-    traffic = PROFILED_TRAFFIC.get(args.workload) if default_cfg else None
+    prof = profiled_counters(args.workload) if default_cfg else None
+    if prof is not None and not (first <= prof["frame"] <= last_f):
+        prof = None  # counters of a frame outside this run's timed region
+    traffic = None
+    issue = None
+    if prof is not None:
+        # the profiled frame's DRAM bytes, and its warp instructions per
+        # sample against the contract's minimum (the issue roofline)
+        traffic = prof["dram_bytes"]
+        inst_ps = prof["warp_instructions"] / prof["samples"]
+        sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        issue_peak = ISSUE_SLOTS * sm_mhz * 1e6  # warp instructions per second
+        mean_samples = samples / len(stats)
+        issue = {"unit": "warp instructions/s", "peak": issue_peak,
+                 "peak_rule": "152 SMs x 4 schedulers x 1 warp instruction/cycle x median SM clock",
+                 "contract_min_per_sample": CONTRACT_INST_PER_SAMPLE,
+                 "measured_per_sample": inst_ps,
+                 "achieved": CONTRACT_INST_PER_SAMPLE * samples / (sum(k_ms) * 1e-3),
+                 "frac": CONTRACT_INST_PER_SAMPLE * samples / (sum(k_ms) * 1e-3) / issue_peak,
+                 "measured_frac": inst_ps * samples / (sum(k_ms) * 1e-3) / issue_peak,
+                 "ms_at_full_issue_measured_inst": inst_ps * mean_samples / issue_peak * 1e3,
+                 "ms_at_full_issue_contract_min": CONTRACT_INST_PER_SAMPLE * mean_samples / issue_peak * 1e3,
+                 "profiled_frame": prof["frame"], "profile": prof["file"]}
     un_q = sum(s["inr_queries_direct"] for s in un_st)
     prec = args.precision
     res = {
@@ -358,13 +460,21 @@ def run_gpu(args, wl):
                    "renderer": (("path tracing (delta tracking, %s majorants)"
                                  % ("local macro-cell" if args.macro else "global"))
                                 if args.pt else "ray marching"),
-                   "timed_frames": [args.warmup, last_f],
+                   "cache_fill_frames": fill,
+                   "warmup_frames": [fill, first - 1],
+                   "timed_frames": [first, last_f],
+                   "frames_of_camera_path": (f"{ORBIT_FRAMES} orbit + {TF_FRAMES} TF-edit, repeating edits"
+                                             if wl["camera"] == "orbit" else f"{FLY_FRAMES} fly-through, cyclic"),
                    "l2": "flushed (256 MiB write) before every timed frame",
                    "parallelism": f"replicas x{world}"},
         "inr_queries_per_s": (q_direct + q_decode) / (sum(ms) * 1e-3),
         "samples_per_s": samples / (sum(ms) * 1e-3),
         "ms_per_frame_p50": float(np.percentile(ms, 50)),
         "ms_per_frame_p90": float(np.percentile(ms, 90)),
+        "ms_march_kernel_mean": float(np.mean(k_ms)),
+        "ms_cache_update_mean": float(np.mean([s["ms_cache_update"] for s in stats])),
+        "cache_fill": {"frames": fill, "bricks_decoded_last5": fill_decoded[-5:],
+                       "converged_at": converged_at(fill_decoded, wl["n_req"])},
         "uncached": {"ms_per_frame": uncached_ms,
                      "inr_queries_per_s": un_q / (sum(un_ms) * 1e-3), "frames": n_un},
         "speedup_cached_vs_uncached": uncached_ms / cached_ms,
@@ -373,8 +483,16 @@ def run_gpu(args, wl):
                    / max(1, sum(s["samples_skipped"] + s["samples"] for s in stats))}
                   if args.macro else None),
         "frame_stats_last": stats[-1],
+        "timed_totals": {k: int(sum(s[k] for s in stats)) for k in
+                         ("samples", "hits", "fallback_hits", "true_misses", "bricks_requested",
+                          "bricks_decoded", "inr_queries_decode")},
         "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": 4096 + 64,
-                "d2h_bytes_per_step": W * H * 16 + 104},
+                "d2h_bytes_per_step": W * H * 16 + 104,
+                "frames": [first, last_f] if e2e else None,
+                "same_cache_state_as_timed_frames": e2e_same if e2e else None,
+                "how": "cinr_render_frame_host into pinned host memory, wall clock per frame, "
+                       "camera + TF from host memory, image read back inside the timed region, "
+                       "replayed fill and warm-up on a second cache"},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -384,20 +502,43 @@ def run_gpu(args, wl):
                      "distinct_brick_frac": achieved_uniq / peaks["hbm_gbs"],
                      "kernel": ("march_cached_kernel (%s pool, brick %d)"
                                 % ("fp16" if prec == "mixed" else "fp32", wl["brick"])),
+                     "kernel_ms_mean": float(np.mean(k_ms)),
+                     "traffic_from": prof["file"] + " (frame %d)" % prof["frame"] if prof else None,
+                     "issue": issue,
                      "peak_kind": peak_kind},
         "clocks": clk,
     }
     if tuned is not None:
         res["autotune"] = tuned
     mse = torch.mean((cached_img[..., :3].double() - uncached_img[..., :3].double()) ** 2).item()
-    res["psnr_db"] = {"cached_vs_uncached_full_frame": 10 * np.log10(1.0 / max(mse, 1e-30))}
+    res["psnr_db"] = {"cached_vs_uncached_full_frame": 10 * np.log10(1.0 / max(mse, 1e-30)),
+                      "cached_vs_uncached_min_over_frames": float(min(psnr_frames)),
+                      "frames": [last_f - n_un + 1, last_f]}
     if rank == 0 and not args.no_cpu:
         res["cpu_baseline"], p = cpu_baseline(args, wl, table, w, last_f, cached_img, uncached_img,
                                               un_st[-1])
         res["psnr_db"].update(p)
+    gate = [res["psnr_db"]["cached_vs_uncached_min_over_frames"]]
+    if "cached_vs_oracle" in res["psnr_db"]:
+        gate.append(res["psnr_db"]["cached_vs_oracle"])
+    res["quality_gate"] = {"min_db": 40.0, "ok": bool(min(gate) >= 40.0), "worst_db": float(min(gate)),
+                           "checked": "cached vs uncached FP32 GPU frames (full frames, last "
+                                      f"{n_un} timed) and cached vs the FP64 oracle (pixel window "
+                                      "of the last timed frame)"}
     if world > 1:
         dist.destroy_process_group()
     return res if rank == 0 else None
+
+
+def converged_at(decoded, n_req):
+    """First frame of three in a row that decoded fewer bricks than the
+    per-frame request budget (the cache keeps up with the camera), or None."""
+    run = 0
+    for f, d in enumerate(decoded):
+        run = run + 1 if d < n_req else 0
+        if run == 3:
+            return f - 2
+    return None
 
 
 def oracle_scene(args, wl):
@@ -407,16 +548,43 @@ def oracle_scene(args, wl):
     return cfg, table, w, p
 
 
+def host_cpu():
+    """Host CPU model and core count (the machine's cores the oracle runs on)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            model = "unknown"
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def cpu_baseline(args, wl, table, w, f, cached_img, uncached_img, un_stats):
-    """The oracle (single-threaded C, FP64) on a pixel window of frame f; for
-    the tera-scale volume (too large for a normalisation pass and a window in
-    a bounded CPU budget) its per-query rate times the frame's queries."""
+    """The oracle (C, FP64) on frame f: single-threaded on a centre pixel
+    window (also the PSNR reference of the quality gate), and the same source
+    built with OpenMP on all host cores over a larger window, rows spread
+    over the cores; both scaled by hit pixels to the full frame.  For the
+    tera-scale volume (too large for a normalisation pass and a window in a
+    bounded CPU budget) the per-query rate times the frame's queries."""
     import oracle as O
     W, H = wl["W"], wl["H"]
     cfg, table, w, p = oracle_scene(args, wl)
     table = np.ascontiguousarray(table, np.float64)  # converted once, outside the timing
     w = np.ascontiguousarray(w, np.float64)
     vol = wl["vol"]
+    cpu_info = host_cpu()
     cam, tf = frame_inputs(f, W, H, wl["camera"], args.tf_ramps)
     if wl["camera"] == "fly":
         pts = np.random.default_rng(0).uniform(0, 1, (4000, 3)).astype(np.float32)
@@ -425,45 +593,71 @@ def cpu_baseline(args, wl, table, w, f, cached_img, uncached_img, un_stats):
         dt = time.perf_counter() - t0
         qps = len(pts) / dt
         cpu = {"value": un_stats["inr_queries_direct"] / qps * 1e3, "unit": "ms/frame", "cores": 1,
-               "kind": "oracle", "inr_queries_per_s": qps,
+               "kind": "oracle", "inr_queries_per_s": qps, "cpu": cpu_info,
                "sample": f"{len(pts)} FP64 oracle INR queries ({dt:.1f} s), scaled to the "
                          f"{un_stats['inr_queries_direct']} queries of an uncached frame"}
         return cpu, {}
     lo, hi = O.inr_raw_range(p, table, w, vol, wl["range_stride"])  # the GPU side's lattice
     p.vmin, p.vmax = -lo / (hi - lo), (1.0 - lo) / (hi - lo)
     oc = O.camera(**cam)
-    cw = args.cpu_crop
-    x0, y0 = W // 2 - cw // 2, H // 2 - cw // 2
     mo = O.march_opts(K=32, eps_T=1e-3, lod_scale=args.lod_scale, step_mode=wl["step_mode"],
                       step_lod_max=wl["step_lod_max"])
-    t0 = time.perf_counter()
-    if args.pt:
-        ref, st = O.render_pt_direct(p, table, w, oc, vol, mo, tf.astype(np.float64),
-                                     O.pt_opts(**PT_OPTS), f + 1, window=(x0, y0, cw, cw))
-    else:
-        ref, st = O.render_direct(p, table, w, oc, vol, mo, tf.astype(np.float64),
-                                  window=(x0, y0, cw, cw))
-    dt = time.perf_counter() - t0
     mask = uncached_img[..., 3].cpu().numpy() > 0
     hit_full = int(mask.sum())
+    tf64 = tf.astype(np.float64)
+
+    def window(cw):
+        x0, y0 = W // 2 - cw // 2, H // 2 - cw // 2
+        return x0, y0, cw, cw
+
+    # single thread: the PSNR window
+    x0, y0, cw, _ = window(args.cpu_crop)
+    t0 = time.perf_counter()
+    if args.pt:
+        ref, st = O.render_pt_direct(p, table, w, oc, vol, mo, tf64, O.pt_opts(**PT_OPTS), f + 1,
+                                     window=(x0, y0, cw, cw))
+    else:
+        ref, st = O.render_direct(p, table, w, oc, vol, mo, tf64, window=(x0, y0, cw, cw))
+    dt1 = time.perf_counter() - t0
     hit_crop = int(mask[y0:y0 + cw, x0:x0 + cw].sum())
-    ms_frame = dt * 1e3 * hit_full / max(hit_crop, 1)
+    ms1 = dt1 * 1e3 * hit_full / max(hit_crop, 1)
+    single = {"value": ms1, "unit": "ms/frame", "cores": 1,
+              "sample": f"{cw}x{cw} pixel window of frame {f} ({st['samples']} samples, {dt1:.1f} s), "
+                        f"scaled by hit pixels {hit_full}/{hit_crop}",
+              "inr_queries_per_s": st["inr_queries_direct"] / dt1}
     crop_c = cached_img[y0:y0 + cw, x0:x0 + cw].cpu().numpy().astype(np.float64)
     crop_u = uncached_img[y0:y0 + cw, x0:x0 + cw].cpu().numpy().astype(np.float64)
-    cpu = {"value": ms_frame, "unit": "ms/frame", "cores": 1, "kind": "oracle",
-           "sample": f"uncached FP64 oracle on a {cw}x{cw} pixel window of frame {f} "
-                     f"({st['samples']} samples, {dt:.1f} s), scaled by hit pixels "
-                     f"{hit_full}/{hit_crop} to a full {W}x{H} frame",
-           "inr_queries_per_s": st["inr_queries_direct"] / dt}
-    return cpu, {"cached_vs_oracle": O.psnr(crop_c, ref), "uncached_vs_oracle": O.psnr(crop_u, ref),
-                 "window": [x0, y0, cw, cw]}
+    psnr = {"cached_vs_oracle": O.psnr(crop_c, ref), "uncached_vs_oracle": O.psnr(crop_u, ref),
+            "window": [x0, y0, cw, cw]}
+    cpu = dict(single, kind="oracle", cpu=cpu_info)
+    threads = O.omp_threads()
+    if not args.pt and threads > 1:
+        # all cores: the same oracle source built with OpenMP, pixel rows
+        # spread over the cores; the window grows with the thread count so
+        # that the work stays in a bounded budget (~cpu_crop^2 pixels a core)
+        cwa = min(int(args.cpu_crop * threads ** 0.5 + 0.5), W)
+        xa, ya, _, _ = window(cwa)
+        t0 = time.perf_counter()
+        _, sta = O.render_direct_rows(p, table, w, oc, vol, mo, tf64, window=(xa, ya, cwa, cwa))
+        dta = time.perf_counter() - t0
+        hit_a = int(mask[ya:ya + cwa, xa:xa + cwa].sum())
+        cpu = {"value": dta * 1e3 * hit_full / max(hit_a, 1), "unit": "ms/frame", "cores": threads,
+               "kind": "oracle", "cpu": cpu_info,
+               "sample": f"uncached FP64 oracle (OpenMP build of the same source, rows over "
+                         f"{threads} threads) on a {cwa}x{cwa} pixel window of frame {f} "
+                         f"({sta['samples']} samples, {dta:.1f} s), scaled by hit pixels "
+                         f"{hit_full}/{hit_a} to a full {W}x{H} frame",
+               "inr_queries_per_s": sta["inr_queries_direct"] / dta,
+               "single_thread": single}
+    return cpu, psnr
 
 
 def run_reference(args, wl):
     """The oracle as the reference arm: ms/frame on the machine's host cores
-    (uncached FP64; a grid of ref_crop x ref_crop pixels spread evenly over
-    each frame, so that rays that miss the volume are sampled in proportion,
-    scaled by pixel count)."""
+    (uncached FP64, the OpenMP build over all cores; a grid of ref_crop x
+    ref_crop pixels spread evenly over each frame, so that rays that miss the
+    volume are sampled in proportion, scaled by pixel count), on the frames
+    the GPU arm times."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -479,29 +673,35 @@ def run_reference(args, wl):
     cw = args.ref_crop
     mo = O.march_opts(K=32, eps_T=1e-3, lod_scale=args.lod_scale, step_mode=wl["step_mode"],
                       step_lod_max=wl["step_lod_max"])
+    threads = O.omp_threads()
+    fill = args.fill if args.fill is not None else wl["fill"]
+    first = fill + args.warmup
     per = []
     # the oracle keeps no state between frames: only the last 3 warm-up
     # frames are run (untimed)
-    for i in range(max(args.warmup - 3, 0), args.warmup + args.steps):
+    gx, gy = np.meshgrid(np.arange(cw), np.arange(cw))
+    pxs = ((gx.ravel() + 0.5) * W / cw).astype(np.int32)
+    pys = ((gy.ravel() + 0.5) * H / cw).astype(np.int32)
+    for i in range(first - 3, first + args.steps):
         cam, tf = frame_inputs(i, W, H, wl["camera"], args.tf_ramps)
         oc = O.camera(**cam)
+        tf64 = tf.astype(np.float64)
         t0 = time.perf_counter()
-        for gy in range(cw):
-            for gx in range(cw):
-                px, py = int((gx + 0.5) * W / cw), int((gy + 0.5) * H / cw)
-                O.render_direct(p, table, w, oc, vol, mo, tf.astype(np.float64),
-                                window=(px, py, 1, 1))
+        O.render_direct_pixels(p, table, w, oc, vol, mo, tf64, pxs, pys)
         dt = time.perf_counter() - t0
-        if i >= args.warmup:
+        if i >= first:
             per.append(dt * 1e3 * (W * H) / (cw * cw))
     val = float(sum(per) / len(per))
     return {"impl": "reference", "metric": METRIC, "value": val, "unit": "ms/frame",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": val,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl["name"].format(prec=args.precision),
-                                            "reference": "CPU FP64 oracle, uncached"},
-            "cpu_baseline": {"value": val, "unit": "ms/frame", "cores": 1, "kind": "oracle",
-                             "sample": f"{cw}x{cw} pixels on an even grid per frame, scaled by pixel "
+                                            "reference": "CPU FP64 oracle, uncached",
+                                            "timed_frames": [first, first + args.steps - 1]},
+            "cpu_baseline": {"value": val, "unit": "ms/frame", "cores": threads, "kind": "oracle",
+                             "cpu": host_cpu(),
+                             "sample": f"{cw}x{cw} pixels on an even grid per frame (OpenMP build of "
+                                       f"the oracle, pixels over {threads} threads), scaled by pixel "
                                        f"count to {W}x{H}"},
             "e2e": {"value": val, "unit": "ms/frame", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -643,6 +843,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None, help="timed frames (workload default)")
     ap.add_argument("--warmup", type=int, default=None, help="warm-up frames (workload default)")
+    ap.add_argument("--fill", type=int, default=None,
+                    help="cache-fill frames before the warm-up frames (workload default)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
     ap.add_argument("--impl", default="cinr", choices=["cinr", "reference"])
     ap.add_argument("--workload", default="orbit",
                     choices=["orbit", "terascale", "learned", "infer"])
@@ -672,7 +875,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--uncached-steps", type=int, default=None)
     ap.add_argument("--cpu-crop", type=int, default=24)
-    ap.add_argument("--ref-crop", type=int, default=8)
+    ap.add_argument("--ref-crop", type=int, default=32)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--res", type=int, default=1024, help="learned: image edge")
     ap.add_argument("--field", type=int, default=1024, help="learned: explicit field edge")

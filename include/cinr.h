@@ -443,7 +443,11 @@ int cinr_renderer_set_macro(cinr_renderer_t r, cinr_macro_t m);
  * Limits: width*height <= 262144 (512 x 512) and o->miss_record_cap == 0;
  * larger requests return CINR_ERR_ARG with a message naming the limit.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and make no call after cudaDeviceReset or
+ * another teardown of the device's primary context (the kept address would
+ * then be stale).  A bounded device-side wait that gives up in a tensor-core
+ * MLP returns CINR_ERR_TIMEOUT, as cinr_render_frame does.  Every
  * call uses the same array: calls that overlap on the GPU (different
  * streams or threads) race and must be serialised by the caller.
  * It calls no cudaMalloc, cudaFree or allocating library routine.

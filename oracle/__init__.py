@@ -45,6 +45,27 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_SRC_OMP = os.path.join(_HERE, "cinr_oracle_omp.c")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile liboracle_omp.so: the same oracle source plus the row-parallel
+    timing driver (cinr_oracle_omp.c), with -fopenmp.  Used only to time the
+    oracle on all host cores; returns "" when gcc has no OpenMP."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(x) for x in (_SRC, _HDR, _SRC_OMP))
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < newest:
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        r = subprocess.run(["gcc", *CFLAGS, "-fopenmp", "-o", tmp, _SRC, _SRC_OMP, "-lm"],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            return ""
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
 class InrParams(C.Structure):
     _fields_ = [("levels", C.c_int), ("feats", C.c_int), ("log2_table", C.c_int),
                 ("base_res", C.c_int), ("growth", C.c_double), ("in_dim", C.c_int),
@@ -178,6 +199,77 @@ def lib():
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+def lib_omp():
+    """The OpenMP build (None when it cannot be built)."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            path = build_omp()
+            if not path:
+                return None
+            L = C.CDLL(path)
+            L.orc_omp_threads.restype = C.c_int
+            L.orc_omp_threads.argtypes = []
+            L.orc_render_direct_rows.restype = None
+            L.orc_render_direct_rows.argtypes = _SIGS["orc_render_direct"][1]
+            L.orc_render_direct_pixels.restype = None
+            L.orc_render_direct_pixels.argtypes = [
+                _P(InrParams), _dp, _dp, _P(Camera), _ip, _P(MarchOpts), _dp, _ip, _ip, C.c_long,
+                _dp, _P(Stats)]
+            _lib_omp = L
+    return _lib_omp
+
+
+def omp_threads() -> int:
+    L = lib_omp()
+    return int(L.orc_omp_threads()) if L is not None else 1
+
+
+def render_direct_rows(p, table, w, cam, vol, mo, tf, window=None):
+    """render_direct with the window's rows spread over all host cores (the
+    same per-pixel arithmetic; falls back to one thread without OpenMP)."""
+    L = lib_omp()
+    if L is None:
+        return render_direct(p, table, w, cam, vol, mo, tf, window)
+    px0, py0, pw, ph = window if window is not None else (0, 0, cam.width, cam.height)
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    v, vp = _i3(vol)
+    tfa, tfp = _d(tf)
+    out = np.zeros((ph, pw, 4), np.float64)
+    st = Stats()
+    L.orc_render_direct_rows(C.byref(p), tp, wp, C.byref(cam), vp, C.byref(mo), tfp,
+                             px0, py0, pw, ph, out.ctypes.data_as(_dp), C.byref(st))
+    return out, st.as_dict()
+
+
+def render_direct_pixels(p, table, w, cam, vol, mo, tf, px, py):
+    """Cache-off render of scattered pixels (px[i], py[i]) on all host cores
+    (one thread without OpenMP); returns (rgba[n, 4], stats)."""
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    n = len(px)
+    out = np.zeros((n, 4), np.float64)
+    L = lib_omp()
+    if L is None:
+        st = {}
+        for i in range(n):
+            o, s1 = render_direct(p, table, w, cam, vol, mo, tf, (int(px[i]), int(py[i]), 1, 1))
+            out[i] = o[0, 0]
+            for k, v in s1.items():
+                st[k] = st.get(k, 0) + v
+        return out, st
+    t, tp = _d(table)
+    wa, wp = _d(w)
+    v, vp = _i3(vol)
+    tfa, tfp = _d(tf)
+    st = Stats()
+    L.orc_render_direct_pixels(C.byref(p), tp, wp, C.byref(cam), vp, C.byref(mo), tfp,
+                               px.ctypes.data_as(_ip), py.ctypes.data_as(_ip), n,
+                               out.ctypes.data_as(_dp), C.byref(st))
+    return out, st.as_dict()
 
 
 # ----------------------------------------------------------------- helpers

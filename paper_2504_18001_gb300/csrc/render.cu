@@ -1687,7 +1687,10 @@ std::mutex g_noalloc_mu;
 
 // Device address of the scratch array on the current device, looked up once
 // per device with that device current (in host code the array's name is only
-// a host-side stand-in, not a device address).
+// a host-side stand-in, not a device address).  The address is kept for the
+// life of the process: it does not survive cudaDeviceReset (or any teardown
+// of the device's primary context), after which this entry point must not
+// be called again in the process.
 int noalloc_scratch(unsigned char** out) {
   int dev = 0;
   CINR_CK(cudaGetDevice(&dev));
@@ -1754,10 +1757,14 @@ extern "C" int cinr_render_frame_noalloc(cinr_inr_t inr, const cinr_camera* cam,
   e = launch_frame_shape<false>(P, inr->p.mlp_precision, s);
   if (e) return e;
   unsigned long long h[ST_COUNT];
+  uint32_t cnt[3] = {0, 0, 0};  // ray counter, miss-record count, device error word
   CINR_CK(cudaMemcpyAsync(out_rgba_host, image, (size_t)cam->width * cam->height * sizeof(float4),
                           cudaMemcpyDeviceToHost, s));
   CINR_CK(cudaMemcpyAsync(h, st_dev, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CINR_CK(cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
   CINR_CK(cudaStreamSynchronize(s));
+  // a bounded tensor-core wait that gave up leaves the image incomplete
+  if (cnt[2]) return set_error(CINR_ERR_TIMEOUT, "a bounded device-side wait gave up in the frame kernel");
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->samples = h[ST_SAMPLES];

@@ -54,3 +54,10 @@ def test_gpu_arm_line():
     assert d["gpu_launches"] >= 3
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]
+    # the timed frames follow the cache-fill phase and pass the quality gate;
+    # the end-to-end pass replays the same cache states
+    c = d["config"]
+    assert c["cache_fill_frames"] >= 1 and c["timed_frames"][0] == c["cache_fill_frames"] + 3
+    g = d["quality_gate"]
+    assert g["ok"] and g["worst_db"] >= 40.0 and g["min_db"] == 40.0
+    assert e["same_cache_state_as_timed_frames"] is True
