@@ -657,6 +657,217 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
   }
 }
 
+// The marching kernel specialised on the common configuration: fixed steps
+// (step_mode 0), footprint LoD (lod_mode 0), flat page tables, no macro
+// cells, the coarsest LoD preloaded (every fallback walk ends at a mapped
+// brick) and the brick size BB a compile-time power of two.  It takes the
+// same samples, LoDs, lookups, requests, stamps and values as
+// march_cached_kernel, in the same binary32 operations; what it saves is
+// bookkeeping: no per-sample tests of the run-time modes, the start of the
+// next sample carried over from this sample's unclipped end (the same
+// tn + (k+1) dt), the dither key k * 0x9E3779B9 advanced by addition, brick
+// and voxel coordinates of non-negative values truncated (the floor of a
+// non-negative binary32), and the sample count of a ray taken from its last
+// sample index.
+template <bool F16POOL, int BB>
+__global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __grid_constant__ FrameParams P) {
+  static_assert(BB > 0 && (BB & (BB - 1)) == 0, "brick size must be a power of two");
+  __shared__ float4 s_tf[256];
+  __shared__ LevelGeo s_geo[kMaxLod];
+  __shared__ uint32_t s_rare[2];
+  const CacheDev& c = P.cache;
+  if (threadIdx.x < 2) s_rare[threadIdx.x] = 0u;
+  for (int i = threadIdx.x; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
+  if (threadIdx.x < c.L) {
+    const int l = threadIdx.x;
+    LevelGeo g;
+    g.nb0 = c.nb[l][0];
+    g.nb1 = c.nb[l][1];
+    g.nb2 = c.nb[l][2];
+    g.off = c.off[l];
+    g.dmax0 = (float)(c.dims[l][0] - 1);
+    g.dmax1 = (float)(c.dims[l][1] - 1);
+    g.dmax2 = (float)(c.dims[l][2] - 1);
+    g.scale = __int_as_float((127 - l) << 23);
+    s_geo[l] = g;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const CamDev& cam = P.cam;
+  const float volf0 = (float)c.vol[0], volf1 = (float)c.vol[1], volf2 = (float)c.vol[2];
+  constexpr int B = BB, S = BB + 2, SS = S * S;
+  constexpr float invB = 1.0f / (float)BB;
+  constexpr uint32_t S3 = (uint32_t)(S * S * S);
+  const int Lm1 = c.L - 1;
+  const void* pool = c.pool;
+  const uint32_t* pt = c.pt;
+  uint32_t n_samp = 0, n_fb = 0, n_miss = 0;
+  uint32_t stamped = 0xFFFFFFFFu;  // the slot this lane last saw stamped this frame
+  const uint32_t n_tiles = P.n_rays >> 5;
+  while (true) {
+    uint32_t tile = 0;
+    if (lane == 0) tile = atomicAdd(P.ray_counter, 1u);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= n_tiles) break;
+    const uint32_t r = tile * 32u + (uint32_t)lane;  // ray index in 8x8 tiles
+    const uint32_t t64 = r >> 6, w = r & 63u;
+    const int px = (int)((t64 % P.tiles_x) * 8 + (w & 7u));
+    const int py = (int)((t64 / P.tiles_x) * 8 + (w >> 3));
+    const bool inside = px < cam.W && py < cam.H;
+    const uint32_t pixel = inside ? (uint32_t)(py * cam.W + px) : 0u;
+    float d[3], tn = 0.f, tf = 0.f;
+    bool active = inside && ray_setup(cam, px, py, d, tn, tf);
+    if (inside && !active) P.out[pixel] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t rseed = ray_seed(P.fseed, pixel);
+    float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
+    int k = 0, seg = P.K;
+    float a = tn;         // start of sample k: tn + k dt (tn + 0 dt = tn)
+    float kf1 = 1.0f;     // k + 1 as binary32 (exact below 2^24)
+    uint32_t kh = 0u;     // k * 0x9E3779B9
+    while (__any_sync(kFull, active)) {
+      bool want_req = false, hit = false;
+      uint32_t req_key = 0, hit_slot = 0;
+      float v = 0.f, len = 0.f;
+      if (active && !(a < tf)) {
+        P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
+        active = false;
+      }
+      const bool took = active;  // this lane takes sample k
+      if (took) {
+        // sample k: midpoint of [a, min(tn + (k+1) dt, tf)] (sample_at)
+        const float an = f_add(tn, f_mul(kf1, cam.dt));
+        const float bnd = fminf(an, tf);
+        const float tm = f_mul(f_add(a, bnd), 0.5f);
+        len = f_sub(bnd, a);
+        a = an;
+        kf1 = f_add(kf1, 1.0f);
+        const float pv0 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[0], f_mul(tm, d[0])), cam.h[0]), cam.inv_e[0])), volf0);
+        const float pv1 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[1], f_mul(tm, d[1])), cam.h[1]), cam.inv_e[1])), volf1);
+        const float pv2 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[2], f_mul(tm, d[2])), cam.h[2]), cam.inv_e[2])), volf2);
+        // stochastic LoD, footprint mode (sample_lod)
+        uint32_t st = rseed ^ kh;
+        if (st == 0u) st = 0x6D2B79F5u;
+        const uint32_t u24 = xorshift32(st) >> 8;
+        const float xf = f_mul(tm, cam.lodc);
+        int l = 0;
+        if (xf >= 1.0f) {
+          const uint32_t bits = __float_as_uint(xf);
+          l = (int)(bits >> 23) - 127 + (u24 < 2u * (bits & 0x7FFFFFu) ? 1 : 0);
+          l = l > Lm1 ? Lm1 : l;
+        }
+        for (int lev = l; lev <= Lm1; ++lev) {
+          const LevelGeo g = s_geo[lev];
+          const float s0 = f_mul(pv0, g.scale), s1 = f_mul(pv1, g.scale), s2 = f_mul(pv2, g.scale);
+          const int b0 = min((int)f_mul(s0, invB), g.nb0 - 1);
+          const int b1 = min((int)f_mul(s1, invB), g.nb1 - 1);
+          const int b2 = min((int)f_mul(s2, invB), g.nb2 - 1);
+          const uint32_t key = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
+          const uint32_t e = __ldg(pt + key);
+          if (!(e & kMapped)) {
+            if (lev == l) {
+              want_req = true;
+              req_key = key;
+            }
+            continue;  // the preloaded coarsest LoD ends the walk
+          }
+          hit_slot = e & ~kMapped;
+          const float q0 = fminf(fmaxf(f_sub(s0, 0.5f), 0.0f), g.dmax0);
+          const float q1 = fminf(fmaxf(f_sub(s1, 0.5f), 0.0f), g.dmax1);
+          const float q2 = fminf(fmaxf(f_sub(s2, 0.5f), 0.0f), g.dmax2);
+          const int i0 = (int)q0, i1 = (int)q1, i2 = (int)q2;
+          const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
+          const int o = ((i2 - b2 * B + 1) * S + (i1 - b1 * B + 1)) * S + (i0 - b0 * B + 1);
+          const void* bp = static_cast<const char*>(pool) + (size_t)hit_slot * S3 * (F16POOL ? 2u : 4u);
+          const float v000 = pool_ld<F16POOL>(bp, o), v100 = pool_ld<F16POOL>(bp, o + 1);
+          const float v010 = pool_ld<F16POOL>(bp, o + S), v110 = pool_ld<F16POOL>(bp, o + S + 1);
+          const float v001 = pool_ld<F16POOL>(bp, o + SS), v101 = pool_ld<F16POOL>(bp, o + SS + 1);
+          const float v011 = pool_ld<F16POOL>(bp, o + SS + S), v111 = pool_ld<F16POOL>(bp, o + SS + S + 1);
+          const float2 a0 = make_float2(v000, v001), a1 = make_float2(v100, v101);
+          const float2 c0 = make_float2(v010, v011), c1 = make_float2(v110, v111);
+          const float2 ff0 = make_float2(f0, f0);
+          const float2 X0 = f2_fma(ff0, f2_sub(a1, a0), a0);
+          const float2 X1 = f2_fma(ff0, f2_sub(c1, c0), c0);
+          const float2 Y = f2_fma(make_float2(f1, f1), f2_sub(X1, X0), X0);
+          v = fmaf(f2, Y.y - Y.x, Y.x);
+          hit = true;
+          if (lev != l) ++n_fb;
+          break;
+        }
+        if (!hit) ++n_miss;  // not reached while the coarsest LoD stays mapped (v = 0)
+      }
+      const unsigned rq = __ballot_sync(kFull, want_req);
+      if (want_req) {
+        const unsigned peers = __match_any_sync(rq, req_key);
+        if (lane == __ffs(peers) - 1) {
+          const uint32_t old = atomicMax(c.rank + req_key, P.Tf);
+          if (old < P.Tf) {
+            atomicAdd(&s_rare[0], 1u);
+            c.touched[atomicAdd(c.touched_count, 1u)] = req_key;
+          }
+          atomicAdd(c.rank + req_key, (uint32_t)__popc(peers));
+          atomicMin(c.rank + req_key, P.Tf + 1000u);
+        }
+      }
+      const bool stale = hit && hit_slot != stamped && c.stamp[hit_slot] != P.frame;
+      const unsigned hm = __ballot_sync(kFull, stale);
+      if (stale) {
+        const unsigned peers = __match_any_sync(hm, hit_slot);
+        if (lane == __ffs(peers) - 1 && atomicExch(c.stamp + hit_slot, P.frame) != P.frame)
+          atomicAdd(&s_rare[1], 1u);
+      }
+      if (hit) stamped = hit_slot;
+      if (took) {
+        const float4 e4 = tf_lookup(s_tf, v);
+        const float alpha = 1.0f - __expf(-e4.w * len);
+        const float wgt = T * alpha;
+        Cr = fmaf(wgt, e4.x, Cr);
+        Cg = fmaf(wgt, e4.y, Cg);
+        Cb = fmaf(wgt, e4.z, Cb);
+        T *= 1.0f - alpha;
+        ++k;
+        kh += 0x9E3779B9u;
+        if (--seg == 0) {
+          seg = P.K;
+          if (T < P.eps) {
+            P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
+            active = false;
+          }
+        }
+      }
+    }
+    n_samp += (uint32_t)k;
+  }
+  unsigned long long a3[3] = {n_samp, n_fb, n_miss};
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    for (int o = 16; o > 0; o >>= 1) a3[j] += __shfl_xor_sync(kFull, a3[j], o);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_rare[0]) atomicAdd(P.stats + ST_REQ, (unsigned long long)s_rare[0]);
+    if (s_rare[1]) atomicAdd(P.stats + ST_SLOTS, (unsigned long long)s_rare[1]);
+  }
+  if (lane == 0) {
+    const unsigned long long hits = a3[0] - a3[1] - a3[2];
+    if (a3[0]) atomicAdd(P.stats + ST_SAMPLES, a3[0]);
+    if (hits) atomicAdd(P.stats + ST_HITS, hits);
+    if (a3[1]) atomicAdd(P.stats + ST_FALLBACK, a3[1]);
+    if (a3[2]) atomicAdd(P.stats + ST_MISSES, a3[2]);
+  }
+}
+
+template <bool F16POOL, int BB>
+int launch_march_fast(const FrameParams& P, cudaStream_t s) {
+  auto k = march_fast_kernel<F16POOL, BB>;
+  static int blocks_per_sm = 0;
+  if (!blocks_per_sm) {
+    CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
+    if (blocks_per_sm < 1) return set_error(CINR_ERR_CUDA, "march kernel cannot be resident");
+  }
+  k<<<(unsigned)(blocks_per_sm * num_sms()), kFrameThreads, 0, s>>>(P);
+  CINR_CK(cudaGetLastError());
+  return CINR_OK;
+}
+
 template <int IN, int H, bool F16POOL, bool MISS, int BB>
 int launch_march_cached(const FrameParams& P, cudaStream_t s) {
   auto k = march_cached_kernel<IN, H, F16POOL, MISS, BB>;
@@ -674,6 +885,9 @@ int launch_march_cached(const FrameParams& P, cudaStream_t s) {
 // without, the shape plays no part and the brick size is specialised.
 template <bool F16POOL>
 int launch_march_cached_pool(const FrameParams& P, bool miss, cudaStream_t s) {
+  const bool common = !miss && P.cam.step_mode == 0 && P.cam.lod_mode == 0 && !P.cache.pd && !P.mac.skip;
+  if (common && P.cache.B == 8) return launch_march_fast<F16POOL, 8>(P, s);
+  if (common && P.cache.B == 16) return launch_march_fast<F16POOL, 16>(P, s);
   if (!miss) {
     switch (P.cache.B) {
       case 8: return launch_march_cached<16, 32, F16POOL, false, 8>(P, s);

@@ -23,10 +23,18 @@ def _points(cfg, n, seed):
 
 @pytest.mark.parametrize("cfg", CFGS, ids=["L8", "L16", "L24"])
 def test_hash_indices_bit_exact(cfg):
+    """Vertex indices of every level and corner, GPU against the oracle, bit
+    for bit: 10^6 random points (a ragged count) plus, at every level, points
+    on that level's grid lines (x = k / N_l exactly, where the floor and the
+    upper clamp decide the cell)."""
     import torch
     table, w = scene(cfg)
     inr = gpu_inr(cfg, table, w)
-    pts = _points(cfg, 20011, seed=5)
+    res = O.level_res(oracle_params(cfg))
+    pts = [S.random_points(1_000_003, 5)]
+    for l, N in enumerate(res):
+        pts.append(S.grid_aligned_points(int(N), 2000, 100 + l))
+    pts = np.concatenate(pts).astype(np.float32)
     x = torch.from_numpy(pts).cuda()
     feats, idx = inr.encode(x, with_indices=True)
     ref = O.encode_indices(oracle_params(cfg), pts)

@@ -1114,3 +1114,60 @@ def test_row_parallel_oracle_equals_the_plain_oracle():
     c, sc = O.render_direct_pixels(p, table, w, oc, (64, 64, 64), mo, tf, xs.ravel(), ys.ravel())
     assert np.array_equal(c.reshape(a.shape), a)
     assert sc == sa
+
+
+def test_request_ranks_equal_an_independent_count_of_unmapped_lookups():
+    """Sec. 4.3 / 4.3.3: every sample whose requested-LoD brick is Unmapped
+    raises one request for that brick, also when a coarser LoD then serves
+    the sample, and a brick's score in a frame is its request count capped
+    at 1000 above the frame's timestamp T_f = 1001 f.  The samples are
+    enumerated here from the ray, sample-schedule and LoD primitives (pinned
+    above), the brick key of each is computed in numpy binary32, and the
+    lookups that meet an Unmapped entry of the page table as it stood at the
+    frame's start are counted per brick.  No termination (eps_T = 0), so the
+    sample set does not depend on the composited values.  The scene is sized
+    so that some bricks take more than 1000 requests in the first frame (the
+    clamp) and others fewer."""
+    cfg = S.INR_64
+    table, w = S.inr_init(cfg, seed=1, table_scale=0.5)
+    p = O.inr_params(cfg.levels, cfg.feats, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden)
+    vol, Wd, Hd, B, L = (64, 64, 64), 36, 36, 8, 4
+    mo = O.march_opts(K=32, eps_T=0.0)
+    cache = O.Cache(p, table, w, vol, B, L, 600, mo, n_req=40)
+    offs = [cache.level_offset(l) for l in range(L)]
+    nbs = [cache.level_dims(l)[1] for l in range(L)]
+    volf = np.array(vol, np.float32)
+    clamped = unclamped = 0
+    for f in (1, 2):
+        pt = cache.dump(O.DUMP_PT)  # the page table the frame's lookups see
+        cam = O.camera(**S.orbit_camera(f, Wd, Hd))
+        fseed = O.frame_seed(0, f)
+        counts = {}
+        for py in range(Hd):
+            for px in range(Wd):
+                hit, o, d, tn, tf = O.ray(cam, vol, px, py)
+                if not hit:
+                    continue
+                rs = O.ray_seed(fseed, py * Wd + px)
+                k = 0
+                while True:
+                    ok, x, tm, _ = O.sample(cam, vol, o, d, tn, tf, k)
+                    if not ok:
+                        break
+                    l = O.sample_lod(cam, vol, mo, L, 0, int(O.lib().orc_sample_state(rs, k)), tm)
+                    s = (x.astype(np.float32) * volf) * np.float32(1.0 / (1 << l))
+                    b = np.clip(np.floor(s / np.float32(B)).astype(np.int64), 0, nbs[l] - 1)
+                    key = int(offs[l] + b[0] + nbs[l][0] * (b[1] + nbs[l][1] * b[2]))
+                    if not pt[key] & 0x80000000:
+                        counts[key] = counts.get(key, 0) + 1
+                    k += 1
+        cache.render(cam, S.tf_ramps(2).astype(np.float64))
+        rank = cache.dump(O.DUMP_RANK).astype(np.int64)
+        Tf = 1001 * f
+        expect = np.zeros_like(rank)
+        for key, n in counts.items():
+            expect[key] = min(n, 1000)
+        assert np.array_equal(np.where(rank > Tf, rank - Tf, 0), expect)
+        clamped += sum(1 for n in counts.values() if n > 1000)
+        unclamped += sum(1 for n in counts.values() if n < 1000)
+    assert clamped > 0 and unclamped > 0
