@@ -54,11 +54,12 @@ def test_train_steps_match_oracle_adam():
         ol = otr.step()
         assert abs(gl - ol) <= 2e-3 * ol, (step, gl, ol)
     gt, gw = cinr.inr_export(inr)
-    # Adam moves every parameter by at most lr per step; entries whose
-    # gradients are far from zero follow the same path on both sides
-    assert np.abs(gt - otr.table).max() <= 3 * 1e-2 + 1e-6
-    assert np.mean(np.abs(gt - otr.table) < 1e-4) > 0.95
-    assert np.mean(np.abs(gw - otr.w) < 1e-3) > 0.95
+    # every table entry and weight on the oracle's Adam path, element by
+    # element, with no entry exempt (measured on GB300: at most 1.9e-7 for
+    # the table and 6.7e-8 for the weights after 3 steps, also for entries
+    # whose gradient is 1e-7 of the largest)
+    assert np.abs(gt - otr.table).max() <= 1e-5
+    assert np.abs(gw - otr.w).max() <= 1e-5
 
 
 def test_training_gains_over_untrained_network():
@@ -100,8 +101,8 @@ def test_one_call_train_matches_oracle_adam():
     for _ in range(3):
         otr.step()
     gt, gw = cinr.inr_export(inr)
-    assert np.mean(np.abs(gt - otr.table) < 1e-4) > 0.95
-    assert np.mean(np.abs(gw - otr.w) < 1e-3) > 0.95
+    assert np.abs(gt - otr.table).max() <= 1e-5
+    assert np.abs(gw - otr.w).max() <= 1e-5
 
 
 def test_non_finite_field_reports_nan_status():
