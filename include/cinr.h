@@ -546,6 +546,27 @@ int cinr_inr_export(cinr_inr_t inr, float* host_table, float* host_mlp,
 int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap,
                     size_t* count, cinr_stream_t stream);
 
+/* Writes one u32 entry of a cache's page tables (what = CINR_DUMP_PAGE_TABLE,
+ * CINR_DUMP_PAGE_DIR or CINR_DUMP_PAGES; index < the count that
+ * cinr_debug_dump reports for it), enqueued on `stream` and synchronised.
+ * For tests of the device bounds checks: an entry naming a slot beyond the
+ * pool is caught by a library built with device checks (see
+ * cinr_device_checks) and reported as CINR_ERR_DEVICE_CHECK by the next
+ * cinr_render_frame.  A library built without them would read past the
+ * pool: plant such entries only with a checked build.
+ * Errors: CINR_ERR_ARG for another table or an index out of range. */
+int cinr_debug_set_entry(cinr_cache_t cache, int what, size_t index,
+                         uint32_t value, cinr_stream_t stream);
+
+/* 1 if this library was built with device bounds checks (-DCINR_CHECK=1),
+ * else 0.  A checked build tests every page-table, page, slot, pool and
+ * hash-table index on the device before the access it guards; an index out
+ * of range skips the access and sets the kernel's error word, which
+ * cinr_render_frame (frame kernels) and cinr_inr_status (INR inference and
+ * the cache update kernels) report as CINR_ERR_DEVICE_CHECK.  The checks
+ * stand in for a memory checker where none can run. */
+int cinr_device_checks(void);
+
 /* Tensor-core self-test of one 128 x 64 tile: d_dev[128][64] = A B^T with
  * a_dev [128][K] and b_dev [64][K] (row-major FP32, rounded to BF16 when
  * bf16 != 0, else FP16), accumulated in FP32 by tcgen05.mma in tensor

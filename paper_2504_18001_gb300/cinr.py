@@ -132,6 +132,8 @@ _SIGS = {
     "cinr_train": [_vp, _vp, _P(C.c_int), _vp, C.c_long, _vp, C.c_size_t, _vp],
     "cinr_inr_export": [_vp, _vp, _vp, _vp],
     "cinr_debug_dump": [_vp, C.c_int, _vp, C.c_size_t, _P(C.c_size_t), _vp],
+    "cinr_debug_set_entry": [_vp, C.c_int, C.c_size_t, C.c_uint32, _vp],
+    "cinr_device_checks": [],
     "cinr_debug_mma_tile": [_vp, _vp, C.c_int, C.c_int, _vp, _vp],
     "cinr_inr_status": [_vp, _vp],
     "cinr_debug_wait_timeout": [_vp, C.c_uint, _vp],
@@ -156,10 +158,16 @@ def header_symbols():
 
 
 def lib(build_if_missing: bool = True):
-    """Load libcinr.so (building it with nvcc when stale)."""
+    """Load libcinr.so (building it with nvcc when stale).  With the
+    environment variable CINR_CHECKED=1 the process loads the build with
+    device bounds checks instead (paper_2504_18001_gb300/_build_check/)."""
     global _lib
     if _lib is None:
-        path = _build.build() if build_if_missing else _build.LIB
+        checked = os.environ.get("CINR_CHECKED", "0") == "1"
+        if checked:
+            path = _build.build(checked=True) if build_if_missing else _build.LIB_CHECK
+        else:
+            path = _build.build() if build_if_missing else _build.LIB
         if not os.path.exists(path):
             raise CinrError(f"libcinr.so not found at {path}; run __graft_entry__.build()")
         L = C.CDLL(path)
@@ -283,7 +291,8 @@ class Inr:
 
 class Cache:
     def __init__(self, inr: Inr, dims, pool_bytes, brick=8, levels=4, n_req=40, ranking=1,
-                 preload=1, storage="fp32", lag=1, page=0, n_pages=0, device="cuda", stream=None):
+                 preload=1, storage="fp32", lag=1, page=0, n_pages=0, device="cuda", stream=None,
+                 slack_bytes=0):
         L = lib()
         self.opts = cinr_cache_opts(int(brick), int(levels), int(n_req), int(ranking), int(preload),
                                     PREC[storage], int(lag), int(page), int(n_pages))
@@ -292,7 +301,9 @@ class Cache:
         check(L.cinr_cache_bytes(self.dims, int(pool_bytes), C.byref(self.opts), C.byref(nbytes),
                                  C.byref(nslots)), "cinr_cache_bytes")
         self.n_slots = nslots.value
-        self.mem = _dev_buffer(nbytes.value, device)
+        # slack_bytes: unused bytes after the cache's own (tests of the device
+        # bounds checks keep even an unchecked stray read inside the buffer)
+        self.mem = _dev_buffer(nbytes.value + int(slack_bytes), device)
         h = C.c_void_p()
         check(L.cinr_create_cache(inr.h, self.dims, C.c_void_p(self.mem.data_ptr()), nbytes.value,
                                   int(pool_bytes), C.byref(self.opts), _stream(stream), C.byref(h)),
@@ -306,6 +317,11 @@ class Cache:
         off = C.c_long()
         check(lib().cinr_cache_level_info(self.h, level, d, nb, C.byref(off)), "level_info")
         return tuple(d), tuple(nb), off.value
+
+    def set_entry(self, what, index, value, stream=None):
+        """Writes one u32 page-table entry (tests of the device checks)."""
+        check(lib().cinr_debug_set_entry(self.h, what, int(index), int(value) & 0xFFFFFFFF,
+                                         _stream(stream)), "cinr_debug_set_entry")
 
     def dump(self, what, stream=None):
         return debug_dump(self.h, what, stream, pool_half=self.opts.storage_precision == 1)

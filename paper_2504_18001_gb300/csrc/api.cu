@@ -32,3 +32,5 @@ extern "C" int cinr_last_error(char* buf, size_t n) {
 }
 
 extern "C" int cinr_version(void) { return 100; }
+
+extern "C" int cinr_device_checks(void) { return CINR_CHECK ? 1 : 0; }

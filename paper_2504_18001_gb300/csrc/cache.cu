@@ -166,8 +166,10 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
     const uint32_t r = wi / tiles_per;
     const int v = (int)(wi % tiles_per) * 128 + (int)threadIdx.x;
     const bool valid = v < S3;
-    const uint32_t key = keys ? keys[r] : c.off[c.L - 1] + r;
+    uint32_t key = keys ? keys[r] : c.off[c.L - 1] + r;
     const uint32_t slot = keys ? slots[r] : r;
+    const bool in_pool = in_range(slot, c.n_slots, c.err);  // checked builds: skip the write
+    if (!in_range(key, c.n_bricks, c.err)) key = 0u;
     const int l = key_level(c, key);
     const uint32_t local = key - c.off[l];
     const int b[3] = {(int)(local % c.nb[l][0]), (int)((local / c.nb[l][0]) % c.nb[l][1]),
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
       encode_point<IN / 2>(q, x[0], x[1], x[2], feat);
       y = tc::mlp_tile<IN, H, (MLPP > 0 ? MLPP - 1 : 0)>(tcs, feat, valid, phase, err);
     }
-    if (valid) {
+    if (valid && in_pool) {
       const float val = fmaf(q.vscale, y, q.vmin);
       const size_t o = (size_t)slot * S3 + v;
       if (c.pool_prec == CINR_PREC_FP16)
@@ -406,11 +408,14 @@ __global__ void commit_kernel(CacheDev c, const uint32_t* req, const uint32_t* r
   uint32_t ev = 0;
   for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
     const uint32_t slot = vic[i], key = req[i];
+    if (!in_range(slot, c.n_slots, c.err) || !in_range(key, c.n_bricks, c.err)) continue;
     const uint32_t old = c.owner[slot];
+    if (old != kNoOwner && !in_range(old, c.n_bricks, c.err)) continue;
     if (old != kNoOwner) {
       if (c.pd) {
         uint32_t local;
         const uint32_t ps = c.pd[key_page(c, old, local)] & ~kMapped;
+        if (!in_range(ps, c.n_pages, c.err)) continue;
         c.pages[((size_t)ps << (3 * c.page_shift)) + local] = 0u;
         atomicSub(c.page_ref + ps, 1u);
       } else {
@@ -444,11 +449,13 @@ __global__ void map_pending_kernel(CacheDev c, const uint32_t* req, const uint32
   const uint32_t m = *decode_n;
   for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
     const uint32_t slot = vic[i], key = req[i];
+    if (!in_range(slot, c.n_slots, c.err) || !in_range(key, c.n_bricks, c.err)) continue;
     if (c.pd) {
       uint32_t local;
       const uint32_t e = c.pd[key_page(c, key, local)];
       if (!(e & kMapped)) continue;  // no page slot: dropped
       const uint32_t ps = e & ~kMapped;
+      if (!in_range(ps, c.n_pages, c.err)) continue;
       c.pages[((size_t)ps << (3 * c.page_shift)) + local] = kMapped | slot;
       atomicAdd(c.page_ref + ps, 1u);
     } else {
@@ -710,6 +717,9 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
   d.page_ref = L.page_ref;
   d.page_shift = g.page_shift < 0 ? 0 : g.page_shift;
   d.n_pages = (uint32_t)g.n_pages;
+  d.n_slots = (uint32_t)ns;
+  d.n_bricks = (uint32_t)g.off[g.L];
+  d.err = reinterpret_cast<int*>(inr->scratch + 16);  // update kernels report to the INR's status word
   for (int l = 0; l < kMaxLod; ++l)
     for (int a = 0; a < 3; ++a) d.pg[l][a] = l < g.L ? g.pg[l][a] : 1;
   for (int l = 0; l <= kMaxLod; ++l) d.pd_off[l] = (uint32_t)(l <= g.L ? g.pd_off[l] : g.pd_off[g.L]);
@@ -868,5 +878,34 @@ extern "C" int cinr_cache_level_info(cinr_cache_t cache, int level, int dims[3],
     if (nbricks) nbricks[a] = cache->dev.nb[level][a];
   }
   if (key_offset) *key_offset = (long)cache->dev.off[level];
+  return CINR_OK;
+}
+
+extern "C" int cinr_debug_set_entry(cinr_cache_t c, int what, size_t index, uint32_t value,
+                                    cinr_stream_t stream) {
+  if (!c) return set_error(CINR_ERR_ARG, "cache is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t* dst = nullptr;
+  size_t n = 0;
+  switch (what) {
+    case CINR_DUMP_PAGE_TABLE:
+      dst = c->dev.pd ? nullptr : c->dev.pt;
+      n = c->dev.pd ? 0 : (size_t)c->n_bricks;
+      break;
+    case CINR_DUMP_PAGE_DIR:
+      dst = c->dev.pd;
+      n = c->dev.pd ? (size_t)c->dev.pd_off[c->dev.L] : 0;
+      break;
+    case CINR_DUMP_PAGES:
+      dst = c->dev.pages;
+      n = c->dev.pd ? (size_t)c->dev.n_pages << (3 * c->dev.page_shift) : 0;
+      break;
+    default: return set_error(CINR_ERR_ARG, "entry writes go to the page tables only (what = %d)", what);
+  }
+  if (!dst || index >= n) return set_error(CINR_ERR_ARG, "index %zu out of range (%zu entries)", index, n);
+  const int ew = cinr_cache_wait_decode(c, s);
+  if (ew) return ew;
+  CINR_CK(cudaMemcpyAsync(dst + index, &value, 4, cudaMemcpyHostToDevice, s));
+  CINR_CK(cudaStreamSynchronize(s));
   return CINR_OK;
 }

@@ -26,6 +26,41 @@ constexpr uint32_t kMapped = 0x80000000u;
 constexpr uint32_t kNoOwner = 0xFFFFFFFFu;
 constexpr int kFrameThreads = 128;  // 4 warps per CTA in the frame kernel
 
+// ------------------------------------------------ device bounds checks
+// A library built with -DCINR_CHECK=1 checks every page-table, page,
+// slot, pool and hash-table index before the access it guards: an index out
+// of range sets kErrCheck in the kernel's error word (reported on the host
+// as CINR_ERR_DEVICE_CHECK) and the access is skipped.  The default build
+// compiles the checks away.
+#ifndef CINR_CHECK
+#define CINR_CHECK 0
+#endif
+constexpr int kErrTimeout = 1;  // a bounded device-side wait gave up
+constexpr int kErrCheck = 2;    // a device bounds check tripped
+
+// Whether i < n; in a checked build an index out of range sets kErrCheck
+// in *err (when err is not null).
+__device__ __forceinline__ bool in_range(unsigned long long i, unsigned long long n, int* err) {
+#if CINR_CHECK
+  if (i >= n) {
+    if (err) atomicOr(err, kErrCheck);
+    return false;
+  }
+#else
+  (void)i;
+  (void)n;
+  (void)err;
+#endif
+  return true;
+}
+
+// Host side: the status code of a device error word.
+inline int device_status(int word) {
+  if (word & kErrCheck) return CINR_ERR_DEVICE_CHECK;
+  if (word) return CINR_ERR_TIMEOUT;
+  return CINR_OK;
+}
+
 // ---------------------------------------------------------------- errors
 int set_error(int code, const char* fmt, ...);
 int cuda_error(cudaError_t e, const char* what);
@@ -61,6 +96,7 @@ struct InrDev {
   int IN, H, NH;
   int table_prec;
   float vmin, vscale;  // v = vmin + vscale * y
+  int* err;            // error word of the bounds checks (checked builds)
 };
 
 // Camera and marching constants, computed on the host in binary32.
@@ -111,20 +147,37 @@ struct CacheDev {
   int pg[kMaxLod][3];
   uint32_t pd_off[kMaxLod + 1];
   uint32_t n_pages;
+  uint32_t n_slots, n_bricks;
+  int* err;  // error word of the bounds checks (checked builds)
 };
 
 // Page-table entry of brick (b0, b1, b2) at LoD lev (key = its flat key):
 // the flat table, or the entry in its page when the page is resident.
+// In a checked build an entry whose slot lies beyond the pool, or a key or
+// page out of range, reads as Unmapped after setting the error word.
 __device__ __forceinline__ uint32_t pt_entry(const CacheDev& c, int lev, uint32_t key, int b0, int b1,
                                              int b2) {
-  if (!c.pd) return __ldg(c.pt + key);
+  if (!c.pd) {
+    if (!in_range(key, c.n_bricks, c.err)) return 0u;
+    const uint32_t e = __ldg(c.pt + key);
+    return (!(e & kMapped) || in_range(e & ~kMapped, c.n_slots, c.err)) ? e : 0u;
+  }
   const int sh = c.page_shift, m = (1 << sh) - 1;
   const uint32_t pk = c.pd_off[lev] + (uint32_t)(b0 >> sh) +
                       (uint32_t)c.pg[lev][0] * ((uint32_t)(b1 >> sh) + (uint32_t)c.pg[lev][1] * (uint32_t)(b2 >> sh));
+  if (!in_range(pk, c.pd_off[c.L], c.err)) return 0u;
   const uint32_t e = __ldg(c.pd + pk);
   if (!(e & kMapped)) return 0u;
+  if (!in_range(e & ~kMapped, c.n_pages, c.err)) return 0u;
   const uint32_t local = (uint32_t)(b0 & m) + ((uint32_t)(b1 & m) << sh) + ((uint32_t)(b2 & m) << (2 * sh));
-  return __ldg(c.pages + (((size_t)(e & ~kMapped)) << (3 * sh)) + local);
+  const uint32_t be = __ldg(c.pages + (((size_t)(e & ~kMapped)) << (3 * sh)) + local);
+  return (!(be & kMapped) || in_range(be & ~kMapped, c.n_slots, c.err)) ? be : 0u;
+}
+
+// Appends a brick first requested this frame to the touched list.
+__device__ __forceinline__ void push_touched(const CacheDev& c, uint32_t key) {
+  const uint32_t i = atomicAdd(c.touched_count, 1u);
+  if (in_range(i, c.n_bricks, c.err)) c.touched[i] = key;
 }
 
 // Level and brick coordinates of a flat brick key.
@@ -149,11 +202,13 @@ __device__ __forceinline__ uint32_t key_page(const CacheDev& c, uint32_t key, ui
 }
 
 __device__ __forceinline__ uint32_t pt_entry_key(const CacheDev& c, uint32_t key) {
+  if (!in_range(key, c.n_bricks, c.err)) return 0u;
   if (!c.pd) return c.pt[key];
   uint32_t local;
   const uint32_t pk = key_page(c, key, local);
   const uint32_t e = c.pd[pk];
   if (!(e & kMapped)) return 0u;
+  if (!in_range(e & ~kMapped, c.n_pages, c.err)) return 0u;
   return c.pages[(((size_t)(e & ~kMapped)) << (3 * c.page_shift)) + local];
 }
 
@@ -456,7 +511,8 @@ __device__ __forceinline__ void encode_point_t(const InrDev& q, float x, float y
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
-      const uint32_t idx = dense ? ax[bx] + ay[by] + az[bz] : ((ax[bx] ^ ay[by] ^ az[bz]) & Tm);
+      uint32_t idx = dense ? ax[bx] + ay[by] + az[bz] : ((ax[bx] ^ ay[by] ^ az[bz]) & Tm);
+      if (!in_range(idx, T, q.err)) idx = 0u;
       const float w = wxs[bx] * wys[by] * wzs[bz];
       const float2 e = load_entry_t<F16>(table, idx);
       f0 = fmaf(w, e.x, f0);

@@ -113,6 +113,7 @@ extern "C" int cinr_create_inr(const cinr_inr_params* p, void* dev_mem, size_t b
   h->w16 = L.w16;
   h->device = device;
   InrDev& d = h->dev;
+  d.err = reinterpret_cast<int*>(L.scratch + 16);  // the INR's status word
   d.table = L.table;
   d.w = L.w;
   d.L = p->levels;

@@ -91,6 +91,25 @@ __device__ __forceinline__ float4 tf_lookup(const float4* s_tf, float v) {
   return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
+// tf_lookup for v clamped to [0,1]: x = v 255 <= 255, so floor(x) <= 255
+__device__ __forceinline__ float4 tf_lookup_fast(const float4* s_tf, float v) {
+  const float x = __saturatef(v) * 255.0f;
+  const int i = (int)x;
+  const int i1 = min(i + 1, 255);
+  const float fr = x - (float)i;
+  const float4 a = s_tf[i], b = s_tf[i1];
+  const float2 fr2 = make_float2(fr, fr);
+  const float2 lo = f2_fma(fr2, f2_sub(make_float2(b.x, b.y), make_float2(a.x, a.y)), make_float2(a.x, a.y));
+  const float2 hi = f2_fma(fr2, f2_sub(make_float2(b.z, b.w), make_float2(a.z, a.w)), make_float2(a.z, a.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float pool_at(const CacheDev& c, size_t i) {
   if (c.pool_prec == CINR_PREC_FP16) return __half2float(__ldg(reinterpret_cast<const __half*>(c.pool) + i));
   return __ldg(reinterpret_cast<const float*>(c.pool) + i);
@@ -109,7 +128,9 @@ __device__ __forceinline__ float brick_sample(const CacheDev& c, int l, uint32_t
     li[a] = i0 - (b[a] * c.B - 1);
   }
   const int S = c.S;
-  const size_t base = (size_t)slot * (size_t)(S * S * S) + (size_t)((li[2] * S + li[1]) * S + li[0]);
+  const int o = (li[2] * S + li[1]) * S + li[0];
+  if (!in_range((uint32_t)o, (uint32_t)(S * S * S - S * S - S - 1), c.err)) return 0.0f;
+  const size_t base = (size_t)slot * (size_t)(S * S * S) + (size_t)o;
   const float v000 = pool_at(c, base), v100 = pool_at(c, base + 1);
   const float v010 = pool_at(c, base + S), v110 = pool_at(c, base + S + 1);
   const float v001 = pool_at(c, base + S * S), v101 = pool_at(c, base + S * S + 1);
@@ -258,7 +279,7 @@ __global__ void __launch_bounds__(kFrameThreads, (CACHED || MLPP) ? 6 : 4)
           const uint32_t old = atomicMax(c.rank + req_key, P.Tf);
           if (old < P.Tf) {
             ++n_req;
-            c.touched[atomicAdd(c.touched_count, 1u)] = req_key;
+            push_touched(c, req_key);
           }
           atomicAdd(c.rank + req_key, (uint32_t)__popc(peers));
           atomicMin(c.rank + req_key, P.Tf + 1000u);
@@ -417,6 +438,7 @@ struct LevelGeo {
   uint32_t off;
   float dmax0, dmax1, dmax2;  // dims - 1
   float scale;                // 2^-level, exact
+  float scale_b;              // 2^-level / B (B a power of two), exact
 };
 
 template <bool F16POOL, class I>
@@ -541,6 +563,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           // the slot's base pointer once, then 32-bit offsets inside the brick
           const void* bp = static_cast<const char*>(pool) + (size_t)hit_slot * S3 * (F16POOL ? 2 : 4);
           const int o = (l2 * S + l1) * S + l0, SS = S * S;
+          if (!in_range((uint32_t)o, (uint32_t)(S3 - SS - S - 1), c.err)) continue;
           const float v000 = pool_ld<F16POOL>(bp, o), v100 = pool_ld<F16POOL>(bp, o + 1);
           const float v010 = pool_ld<F16POOL>(bp, o + S), v110 = pool_ld<F16POOL>(bp, o + S + 1);
           const float v001 = pool_ld<F16POOL>(bp, o + SS), v101 = pool_ld<F16POOL>(bp, o + SS + 1);
@@ -569,7 +592,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
           const uint32_t old = atomicMax(c.rank + req_key, P.Tf);
           if (old < P.Tf) {
             atomicAdd(&s_rare[0], 1u);
-            c.touched[atomicAdd(c.touched_count, 1u)] = req_key;
+            push_touched(c, req_key);
           }
           atomicAdd(c.rank + req_key, (uint32_t)__popc(peers));
           atomicMin(c.rank + req_key, P.Tf + 1000u);
@@ -689,6 +712,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
     g.dmax1 = (float)(c.dims[l][1] - 1);
     g.dmax2 = (float)(c.dims[l][2] - 1);
     g.scale = __int_as_float((127 - l) << 23);
+    g.scale_b = __int_as_float((127 - l) << 23) * (1.0f / (float)BB);
     s_geo[l] = g;
   }
   __syncthreads();
@@ -757,11 +781,12 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
         }
         for (int lev = l; lev <= Lm1; ++lev) {
           const LevelGeo g = s_geo[lev];
-          const float s0 = f_mul(pv0, g.scale), s1 = f_mul(pv1, g.scale), s2 = f_mul(pv2, g.scale);
-          const int b0 = min((int)f_mul(s0, invB), g.nb0 - 1);
-          const int b1 = min((int)f_mul(s1, invB), g.nb1 - 1);
-          const int b2 = min((int)f_mul(s2, invB), g.nb2 - 1);
+          // (pv 2^-l) / B = pv (2^-l / B): products with powers of two are exact
+          const int b0 = min((int)f_mul(pv0, g.scale_b), g.nb0 - 1);
+          const int b1 = min((int)f_mul(pv1, g.scale_b), g.nb1 - 1);
+          const int b2 = min((int)f_mul(pv2, g.scale_b), g.nb2 - 1);
           const uint32_t key = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
+          if (!in_range(key, c.n_bricks, c.err)) continue;
           const uint32_t e = __ldg(pt + key);
           if (!(e & kMapped)) {
             if (lev == l) {
@@ -770,13 +795,16 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
             }
             continue;  // the preloaded coarsest LoD ends the walk
           }
+          if (!in_range(e & ~kMapped, c.n_slots, c.err)) continue;  // checked builds: read as Unmapped
           hit_slot = e & ~kMapped;
+          const float s0 = f_mul(pv0, g.scale), s1 = f_mul(pv1, g.scale), s2 = f_mul(pv2, g.scale);
           const float q0 = fminf(fmaxf(f_sub(s0, 0.5f), 0.0f), g.dmax0);
           const float q1 = fminf(fmaxf(f_sub(s1, 0.5f), 0.0f), g.dmax1);
           const float q2 = fminf(fmaxf(f_sub(s2, 0.5f), 0.0f), g.dmax2);
           const int i0 = (int)q0, i1 = (int)q1, i2 = (int)q2;
           const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
           const int o = ((i2 - b2 * B + 1) * S + (i1 - b1 * B + 1)) * S + (i0 - b0 * B + 1);
+          if (!in_range((uint32_t)o, S3 - SS - S - 1, c.err)) continue;
           const void* bp = static_cast<const char*>(pool) + (size_t)hit_slot * S3 * (F16POOL ? 2u : 4u);
           const float v000 = pool_ld<F16POOL>(bp, o), v100 = pool_ld<F16POOL>(bp, o + 1);
           const float v010 = pool_ld<F16POOL>(bp, o + S), v110 = pool_ld<F16POOL>(bp, o + S + 1);
@@ -802,23 +830,21 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
           const uint32_t old = atomicMax(c.rank + req_key, P.Tf);
           if (old < P.Tf) {
             atomicAdd(&s_rare[0], 1u);
-            c.touched[atomicAdd(c.touched_count, 1u)] = req_key;
+            push_touched(c, req_key);
           }
           atomicAdd(c.rank + req_key, (uint32_t)__popc(peers));
           atomicMin(c.rank + req_key, P.Tf + 1000u);
         }
       }
-      const bool stale = hit && hit_slot != stamped && c.stamp[hit_slot] != P.frame;
-      const unsigned hm = __ballot_sync(kFull, stale);
-      if (stale) {
-        const unsigned peers = __match_any_sync(hm, hit_slot);
-        if (lane == __ffs(peers) - 1 && atomicExch(c.stamp + hit_slot, P.frame) != P.frame)
+      // LRU stamp: once per slot and frame (the first exchange counts it)
+      if (hit && hit_slot != stamped) {
+        if (c.stamp[hit_slot] != P.frame && atomicExch(c.stamp + hit_slot, P.frame) != P.frame)
           atomicAdd(&s_rare[1], 1u);
+        stamped = hit_slot;
       }
-      if (hit) stamped = hit_slot;
       if (took) {
-        const float4 e4 = tf_lookup(s_tf, v);
-        const float alpha = 1.0f - __expf(-e4.w * len);
+        const float4 e4 = tf_lookup_fast(s_tf, v);
+        const float alpha = 1.0f - ex2_approx(e4.w * (len * -1.4426950408889634f));
         const float wgt = T * alpha;
         Cr = fmaf(wgt, e4.x, Cr);
         Cg = fmaf(wgt, e4.y, Cg);
@@ -1129,7 +1155,7 @@ __device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const flo
           const uint32_t old = atomicMax(c.rank + key, P.Tf);
           if (old < P.Tf) {
             ++n.req;
-            c.touched[atomicAdd(c.touched_count, 1u)] = key;
+            push_touched(c, key);
           }
           atomicAdd(c.rank + key, 1u);
           atomicMin(c.rank + key, P.Tf + 1000u);
@@ -1144,7 +1170,9 @@ __device__ float pt_value(const FrameParams& P, const LevelGeo* s_geo, const flo
       const int i0 = (int)floorf(q0), i1 = (int)floorf(q1), i2 = (int)floorf(q2);
       const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
       const int l0 = i0 - (b0 * B - 1), l1 = i1 - (b1 * B - 1), l2 = i2 - (b2 * B - 1);
-      const size_t base = (size_t)slot * S3 + (size_t)((l2 * S + l1) * S + l0);
+      const int ob = (l2 * S + l1) * S + l0;
+      if (!in_range((uint32_t)ob, (uint32_t)(S3 - S * S - S - 1), c.err)) return 0.0f;
+      const size_t base = (size_t)slot * S3 + (size_t)ob;
       const void* pool = c.pool;
       const float v000 = pool_ld<F16POOL>(pool, base), v100 = pool_ld<F16POOL>(pool, base + 1);
       const float v010 = pool_ld<F16POOL>(pool, base + S), v110 = pool_ld<F16POOL>(pool, base + S + 1);
@@ -1629,6 +1657,8 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
 
   P.w16 = inr->w16;
   P.err = reinterpret_cast<int*>(r->counters + 2);
+  P.inr.err = P.err;  // the frame kernels' bounds checks report to the frame
+  if (cache) P.cache.err = P.err;
   if (pt) {
     if (pt->max_bounces < 1) return set_error(CINR_ERR_ARG, "max_bounces must be >= 1");
     const float neg[3] = {-pt->light_dir[0], -pt->light_dir[1], -pt->light_dir[2]};
@@ -1709,6 +1739,8 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
   CINR_CK(cudaStreamSynchronize(s));
   if (host_img) CINR_CK(cudaStreamSynchronize(r->copy));
   const uint32_t rec = cnt[1];
+  if (device_status((int)cnt[2]) == CINR_ERR_DEVICE_CHECK)
+    return set_error(CINR_ERR_DEVICE_CHECK, "a device bounds check tripped in the frame kernel");
   if (cnt[2]) return set_error(CINR_ERR_TIMEOUT, "a bounded device-side wait gave up in the frame kernel");
   if (stats) {
     stats->samples = h[ST_SAMPLES];
@@ -1968,6 +2000,7 @@ extern "C" int cinr_render_frame_noalloc(cinr_inr_t inr, const cinr_camera* cam,
   CINR_CK(cudaMemsetAsync(scratch, 0, kNoAllocHeader, s));
   P.w16 = inr->w16;
   P.err = reinterpret_cast<int*>(counters + 2);
+  P.inr.err = P.err;
   e = launch_frame_shape<false>(P, inr->p.mlp_precision, s);
   if (e) return e;
   unsigned long long h[ST_COUNT];
@@ -1978,6 +2011,8 @@ extern "C" int cinr_render_frame_noalloc(cinr_inr_t inr, const cinr_camera* cam,
   CINR_CK(cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
   CINR_CK(cudaStreamSynchronize(s));
   // a bounded tensor-core wait that gave up leaves the image incomplete
+  if (device_status((int)cnt[2]) == CINR_ERR_DEVICE_CHECK)
+    return set_error(CINR_ERR_DEVICE_CHECK, "a device bounds check tripped in the frame kernel");
   if (cnt[2]) return set_error(CINR_ERR_TIMEOUT, "a bounded device-side wait gave up in the frame kernel");
   if (stats) {
     memset(stats, 0, sizeof(*stats));

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(128) debug_mma_kernel(const float* __restrict_
     tc::wait_ld();
     for (int i = 0; i < 16; ++i) D[t * 64 + c0 + i] = v[i];
   }
-  if (!ok && err) atomicExch(err, 1);
+  if (!ok && err) atomicOr(err, kErrTimeout);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -175,7 +175,7 @@ __global__ void debug_wait_kernel(int* err, uint32_t limit) {
   if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
   __syncthreads();
   const bool ok = tc::mbar_wait(&bar, 0, limit);
-  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+  if (!ok && threadIdx.x == 0) atomicOr(err, kErrTimeout);
 }
 
 extern "C" int cinr_debug_wait_timeout(cinr_inr_t inr, unsigned limit, cinr_stream_t stream) {
@@ -195,6 +195,8 @@ extern "C" int cinr_inr_status(cinr_inr_t inr, cinr_stream_t stream) {
   CINR_CK(cudaMemcpyAsync(&flag, dev, 4, cudaMemcpyDeviceToHost, s));
   CINR_CK(cudaMemsetAsync(dev, 0, 4, s));
   CINR_CK(cudaStreamSynchronize(s));
+  if (device_status(flag) == CINR_ERR_DEVICE_CHECK)
+    return set_error(CINR_ERR_DEVICE_CHECK, "a device bounds check tripped (INR or cache update kernel)");
   if (flag) return set_error(CINR_ERR_TIMEOUT, "a device-side wait gave up (tensor-core MLP)");
   return CINR_OK;
 }

@@ -24,6 +24,8 @@
 #include <cuda_fp8.h>
 #include <stdint.h>
 
+#include "cinr_internal.cuh"
+
 namespace cinr {
 namespace tc {
 
@@ -375,7 +377,7 @@ __device__ __forceinline__ float mlp_tile(TcSmem<IN, H>& s, const float* feat, b
     for (int i = 0; i < 16; ++i) y = fmaf(s.w3[c0 + i], fmaxf(v[i], 0.0f), y);
   }
   fence_before();
-  if (!ok && err) atomicExch(err, 1);
+  if (!ok && err) atomicOr(err, kErrTimeout);
   return y;
 }
 

@@ -120,3 +120,10 @@ def test_error_codes_match_header():
     for name, val in codes.items():
         assert getattr(cinr, name) == val, name
     assert "ERR_NAN" in codes and "ERR_TIMEOUT" in codes
+
+
+def test_default_build_has_no_device_checks_and_entry_writes_check_arguments(L):
+    # the product build compiles the device bounds checks away; the checked
+    # build (-DCINR_CHECK=1) is exercised by tests/test_gpu_checks.py
+    assert L.cinr_device_checks() == 0
+    assert L.cinr_debug_set_entry(None, cinr.DUMP_PAGE_TABLE, 0, 0, None) == cinr.ERR_ARG
