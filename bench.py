@@ -250,6 +250,7 @@ def run_gpu(args, wl):
             step_lod_max=wl["step_lod_max"], device=device)
         wl = dict(wl, n_req=best["n_req"], brick=best["brick"])
         args.ray_layout, args.graph = best["ray_layout"], best["use_graph"]
+        args.decode_ctas = best["decode_ctas"]
         tuned = {"chosen": best, "trials": trials}
     S3 = (wl["brick"] + 2) ** 3
     fill = args.fill if args.fill is not None else wl["fill"]
@@ -257,10 +258,12 @@ def run_gpu(args, wl):
     last_f = first + args.steps - 1     # last timed frame
 
     def make_cache():
-        return cinr.Cache(inr_c, vol, pool_bytes=wl["pool_mib"] << 20, brick=wl["brick"],
-                          levels=wl["levels"], storage=storage, n_req=wl["n_req"], ranking=1,
-                          preload=1, lag=args.lag, page=args.page, n_pages=args.n_pages,
-                          device=device)
+        cc = cinr.Cache(inr_c, vol, pool_bytes=wl["pool_mib"] << 20, brick=wl["brick"],
+                        levels=wl["levels"], storage=storage, n_req=wl["n_req"], ranking=1,
+                        preload=1, lag=args.lag, page=args.page, n_pages=args.n_pages,
+                        device=device)
+        cc.set_decode_ctas(getattr(args, "decode_ctas", 0))
+        return cc
 
     def make_renderer():
         return cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_mode=0, lod_scale=args.lod_scale,
@@ -844,6 +847,49 @@ def run_infer(args):
             "by_precision": rows}
 
 
+def other_configs(args):
+    """Short driver-visible runs of the tera-scale and learned configurations
+    after the headline measurement: the tera-scale fly-through (full size:
+    10240x7680x1536 virtual volume, 40 GiB FP16 pool, 1080p, LoD-scaled
+    steps) with a 30-frame fill, 3 warm-up and 10 timed frames and one
+    uncached frame, and the learned INR at full size (1024^3 field, 5000
+    Adam steps of 2^18 samples, 20 cached frames judged against the
+    explicit-voxel render).  A failure is reported in the line instead of
+    ending the run."""
+    import copy
+    import torch
+    out = {}
+    try:
+        a = copy.copy(args)
+        a.workload, a.fill, a.warmup, a.steps, a.uncached_steps = "terascale", 30, 3, 10, 1
+        a.no_cpu, a.no_e2e = True, True
+        r = run_gpu(a, WORKLOADS["terascale"])
+        out["terascale"] = {
+            "workload": r["config"]["workload"], "ms_per_frame": r["value"],
+            "ms_march_kernel_mean": r["ms_march_kernel_mean"],
+            "ms_cache_update_mean": r["ms_cache_update_mean"],
+            "timed_frames": r["config"]["timed_frames"], "uncached_ms_per_frame": r["uncached"]["ms_per_frame"],
+            "speedup_cached_vs_uncached": r["speedup_cached_vs_uncached"],
+            "psnr_db_cached_vs_uncached": r["psnr_db"]["cached_vs_uncached_min_over_frames"],
+            "inr_queries_per_s": r["inr_queries_per_s"], "samples_per_s": r["samples_per_s"],
+            "timed_totals": r["timed_totals"], "clocks": r["clocks"]}
+    except Exception as e:  # reported, not fatal
+        out["terascale"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    torch.cuda.empty_cache()
+    try:
+        a = copy.copy(args)
+        a.field, a.train_steps, a.res, a.learned_frames = 1024, 5000, 1024, 20
+        r = run_learned(a)
+        out["learned"] = {"workload": r["config"]["workload"], "psnr_db": r["value"],
+                          "psnr_untrained_db": r["psnr_untrained_db"], "train": r["train"],
+                          "cached_ms_per_frame_last5": r["cached_ms_per_frame_last5"],
+                          "quality_gate_ok": bool(r["value"] >= 40.0)}
+    except Exception as e:
+        out["learned"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -852,6 +898,8 @@ def main():
     ap.add_argument("--fill", type=int, default=None,
                     help="cache-fill frames before the warm-up frames (workload default)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the short tera-scale and learned runs after the headline")
     ap.add_argument("--impl", default="cinr", choices=["cinr", "reference"])
     ap.add_argument("--workload", default="orbit",
                     choices=["orbit", "terascale", "learned", "infer"])
@@ -901,6 +949,9 @@ def main():
         if args.warmup < 3:
             ap.error("--warmup must be >= 3")
         res = run_reference(args, wl) if args.impl == "reference" else run_gpu(args, wl)
+        if (res is not None and args.impl != "reference" and args.workload == "orbit"
+                and int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_other):
+            res["other_configs"] = other_configs(args)
     if res is not None:
         print(json.dumps(res))
 

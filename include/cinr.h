@@ -546,6 +546,14 @@ int cinr_inr_export(cinr_inr_t inr, float* host_table, float* host_mlp,
 int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap,
                     size_t* count, cinr_stream_t stream);
 
+/* Caps the brick decode at ctas_per_sm CTAs per SM (1 .. 8; 0, the
+ * default, launches as many as the SM's registers and shared memory hold).
+ * A tuning knob of the tensor-core decode (Sec. 4.3.2): fewer CTAs leave
+ * SM slots to work that runs beside the decode (the lag-2 decode runs at
+ * most 2 per SM next to the next frame's marching kernel).
+ * Errors: CINR_ERR_ARG for a NULL cache or a count out of range. */
+int cinr_cache_set_decode_ctas(cinr_cache_t cache, int ctas_per_sm);
+
 /* Writes one u32 entry of a cache's page tables (what = CINR_DUMP_PAGE_TABLE,
  * CINR_DUMP_PAGE_DIR or CINR_DUMP_PAGES; index < the count that
  * cinr_debug_dump reports for it), enqueued on `stream` and synchronised.

@@ -134,6 +134,7 @@ _SIGS = {
     "cinr_debug_dump": [_vp, C.c_int, _vp, C.c_size_t, _P(C.c_size_t), _vp],
     "cinr_debug_set_entry": [_vp, C.c_int, C.c_size_t, C.c_uint32, _vp],
     "cinr_device_checks": [],
+    "cinr_cache_set_decode_ctas": [_vp, C.c_int],
     "cinr_debug_mma_tile": [_vp, _vp, C.c_int, C.c_int, _vp, _vp],
     "cinr_inr_status": [_vp, _vp],
     "cinr_debug_wait_timeout": [_vp, C.c_uint, _vp],
@@ -317,6 +318,10 @@ class Cache:
         off = C.c_long()
         check(lib().cinr_cache_level_info(self.h, level, d, nb, C.byref(off)), "level_info")
         return tuple(d), tuple(nb), off.value
+
+    def set_decode_ctas(self, ctas_per_sm):
+        """Decode CTAs per SM (0: as many as fit)."""
+        check(lib().cinr_cache_set_decode_ctas(self.h, int(ctas_per_sm)), "cinr_cache_set_decode_ctas")
 
     def set_entry(self, what, index, value, stream=None):
         """Writes one u32 page-table entry (tests of the device checks)."""

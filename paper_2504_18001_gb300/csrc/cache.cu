@@ -134,6 +134,167 @@ __device__ __forceinline__ int key_level(const CacheDev& c, uint32_t key) {
   return l;
 }
 
+// ------------------------------------------------ brick-tile hash encoder
+// The voxels of a brick lie on a lattice, so along each axis a voxel's
+// grid cell and weight at every hash-grid level depend on that axis's
+// voxel coordinate alone: a tile computes them once per (level, axis,
+// coordinate) into shared memory (binary32, as grid_cell).  At each level
+// the corner vertices the tile can touch form a box; where the boxes fit,
+// their table entries are staged into shared memory by coalesced loads
+// (consecutive threads, consecutive vertices along x, dense rows
+// contiguous in the table) and every voxel reads its 8 corners from there;
+// finer levels, whose boxes outgrow the buffer, are gathered from the
+// table directly.  Each voxel combines its corners by lerps along x, then
+// y, then z (the trilinear weights of Sec. 3 in separable form).
+constexpr int kDecMaxS = 18;  // the staged encoder serves bricks up to 16^3 + apron
+constexpr int kDecMaxL = 24;  // and up to 24 levels
+
+struct AxisCell {
+  int i;    // cell index along the axis
+  float w;  // weight of the upper vertex
+};
+struct LevelBox {
+  int lo0, lo1, lo2;  // lowest vertex of the box
+  int n0, n1, n2;     // box extent (vertices)
+  int base;           // first entry in the stage buffer; -1: not staged
+};
+
+// Shared-memory bytes of the encoder's tables for L levels and bricks of S
+// voxels per edge.
+__host__ __device__ constexpr int dec_tables_bytes(int L, int S) {
+  return L * 3 * S * (int)sizeof(AxisCell) + L * (int)sizeof(LevelBox);
+}
+
+// Voxel-centre coordinate of LoD-l voxel j (clamped to the grid) along an
+// axis of V LoD-0 voxels: ((j + 0.5) 2^l) / V in binary32.
+__device__ __forceinline__ float voxel_coord(int j, int dim_l, int l, int V) {
+  j = j < 0 ? 0 : (j > dim_l - 1 ? dim_l - 1 : j);
+  const float t = f_mul(f_add((float)j, 0.5f), (float)(1 << l));
+  return clamp01(f_div(t, (float)V));
+}
+
+template <bool F16>
+__device__ __forceinline__ float2 lerp_corners(const float2 e[8], float wx, float wy, float wz) {
+  const float2 X = make_float2(wx, wx), Y = make_float2(wy, wy), Z = make_float2(wz, wz);
+  const float2 x00 = f2_fma(X, f2_sub(e[1], e[0]), e[0]);
+  const float2 x10 = f2_fma(X, f2_sub(e[3], e[2]), e[2]);
+  const float2 x01 = f2_fma(X, f2_sub(e[5], e[4]), e[4]);
+  const float2 x11 = f2_fma(X, f2_sub(e[7], e[6]), e[6]);
+  const float2 y0 = f2_fma(Y, f2_sub(x10, x00), x00);
+  const float2 y1 = f2_fma(Y, f2_sub(x11, x01), x01);
+  return f2_fma(Z, f2_sub(y1, y0), y0);
+}
+
+// Stages the tile's boxes and fills the axis tables; all 128 threads.
+// b: brick coordinates, l: its LoD, v0 / v1: the tile's voxel range.
+template <bool F16>
+__device__ __forceinline__ void stage_tile(const InrDev& q, const CacheDev& c, int l, const int b[3], int v0,
+                                           int v1, AxisCell* tab, LevelBox* box, float2* stage, int cap) {
+  const int S = c.S, SS = S * S, L = q.L;
+  const int t = threadIdx.x;
+  __syncthreads();  // the previous tile's voxels have read the tables
+  for (int e = t; e < L * 3 * S; e += blockDim.x) {
+    const int j = e / (3 * S), a = (e / S) % 3, lv = e % S;
+    const float x = voxel_coord(b[a] * c.B - 1 + lv, c.dims[l][a], l, c.vol[a]);
+    int ii;
+    float w;
+    grid_cell(x, q.res[j], ii, w);
+    tab[e] = AxisCell{ii, w};
+  }
+  __syncthreads();
+  if (t < 32) {
+    // level t's box: full x rows; the y and z coordinates the tile covers
+    int size = 0;
+    LevelBox bx{0, 0, 0, 0, 0, 0, -1};
+    if (t < L) {
+      const int z0 = v0 / SS, z1 = (v1 - 1) / SS;
+      const int y0 = z0 == z1 ? (v0 / S) % S : 0, y1 = z0 == z1 ? ((v1 - 1) / S) % S : S - 1;
+      const AxisCell* ta = tab + t * 3 * S;
+      bx.lo0 = ta[0].i;
+      bx.lo1 = ta[S + y0].i;
+      bx.lo2 = ta[2 * S + z0].i;
+      bx.n0 = ta[S - 1].i + 2 - bx.lo0;
+      bx.n1 = ta[S + y1].i + 2 - bx.lo1;
+      bx.n2 = ta[2 * S + z1].i + 2 - bx.lo2;
+      size = bx.n0 * bx.n1 * bx.n2;
+    }
+    // coarse levels first, while the stage buffer has room
+    int scan = size;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, scan, o);
+      if (t >= o) scan += u;
+    }
+    const bool staged = t < L && scan <= cap;
+    bx.base = staged ? scan - size : -1;
+    if (t < L) box[t] = bx;
+  }
+  __syncthreads();
+  const uint32_t T = 1u << q.log2T;
+  for (int j = 0; j < L; ++j) {  // block-uniform loop
+    const LevelBox bx = box[j];
+    if (bx.base < 0) continue;
+    const int N = q.res[j];
+    const int nb01 = bx.n0 * bx.n1;
+    const int size = nb01 * bx.n2;
+    const bool dense = (q.dense_mask >> j) & 1u;
+    const uint32_t n1 = (uint32_t)N + 1u;
+    const char* table = reinterpret_cast<const char*>(q.table) + (size_t)j * T * (F16 ? 4 : 8);
+    for (int e = t; e < size; e += blockDim.x) {
+      const uint32_t cx = (uint32_t)(bx.lo0 + e % bx.n0);
+      const uint32_t cy = (uint32_t)(bx.lo1 + (e / bx.n0) % bx.n1);
+      const uint32_t cz = (uint32_t)(bx.lo2 + e / nb01);
+      uint32_t idx = vertex_index(dense, n1, T, cx, cy, cz);
+      if (!in_range(idx, T, q.err)) idx = 0u;
+      stage[bx.base + e] = load_entry_t<F16>(table, idx);
+    }
+  }
+  __syncthreads();
+}
+
+// Features of voxel (lx, ly, lz) of the tile (levels concatenated, 2 per
+// level) from the axis tables, the staged boxes and the table.
+template <int LV, bool F16>
+__device__ __forceinline__ void encode_voxel(const InrDev& q, int S, int lx, int ly, int lz, const AxisCell* tab,
+                                             const LevelBox* box, const float2* stage, float* feat) {
+  const uint32_t T = 1u << q.log2T, Tm = T - 1u;
+#pragma unroll
+  for (int j = 0; j < LV; ++j) {
+    const AxisCell ax = tab[(j * 3 + 0) * S + lx], ay = tab[(j * 3 + 1) * S + ly], az = tab[(j * 3 + 2) * S + lz];
+    const LevelBox bx = box[j];
+    float2 e[8];
+    if (bx.base >= 0) {
+      const int n01 = bx.n0 * bx.n1;
+      const float2* p = stage + bx.base + (ax.i - bx.lo0) + bx.n0 * ((ay.i - bx.lo1) + bx.n1 * (az.i - bx.lo2));
+      e[0] = p[0];
+      e[1] = p[1];
+      e[2] = p[bx.n0];
+      e[3] = p[bx.n0 + 1];
+      e[4] = p[n01];
+      e[5] = p[n01 + 1];
+      e[6] = p[n01 + bx.n0];
+      e[7] = p[n01 + bx.n0 + 1];
+    } else {
+      const bool dense = (q.dense_mask >> j) & 1u;
+      const uint32_t n1 = (uint32_t)q.res[j] + 1u;
+      const uint32_t sy = dense ? n1 : 2654435761u, sz = dense ? n1 * n1 : 805459861u;
+      const uint32_t x0 = (uint32_t)ax.i, x1 = x0 + 1u;
+      const uint32_t y0 = (uint32_t)ay.i * sy, y1 = y0 + sy;
+      const uint32_t z0 = (uint32_t)az.i * sz, z1 = z0 + sz;
+      const void* table = reinterpret_cast<const char*>(q.table) + (size_t)j * T * (F16 ? 4 : 8);
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        const uint32_t xx = (cc & 1) ? x1 : x0, yy = (cc & 2) ? y1 : y0, zz = (cc & 4) ? z1 : z0;
+        uint32_t idx = dense ? xx + yy + zz : ((xx ^ yy ^ zz) & Tm);
+        if (!in_range(idx, T, q.err)) idx = 0u;
+        e[cc] = load_entry_t<F16>(table, idx);
+      }
+    }
+    const float2 r = lerp_corners<F16>(e, ax.w, ay.w, az.w);
+    feat[2 * j] = r.x;
+    feat[2 * j + 1] = r.y;
+  }
+}
+
 // Decode (persistent): every stored voxel of a requested brick is inferred
 // by the INR at its LoD-l voxel centre (clamp-to-edge) and written into the
 // victim slot.  Work items are (request, 128-voxel tile) pairs, taken by the
@@ -142,6 +303,21 @@ __device__ __forceinline__ int key_level(const CacheDev& c, uint32_t key) {
 // Mode list: request i of *n_dev uses keys[i] and slots[i].  Mode preload
 // (keys == nullptr): request i is brick off[L-1] + i into slot i.
 // MLPP: 0 = FP32 SIMT MLP, 1 / 2 / 3 = FP16 / BF16 / FP8 tensor cores.
+// Dynamic shared memory of the decode kernel: the MLP's (tensor-core tile
+// state or FP32 weights), then the staged encoder's axis tables and level
+// boxes, then (FP32 MLP only) its stage buffer; the tensor-core path stages
+// into the hidden-layer operand buffer, which is free while a tile encodes.
+constexpr int kDecStageFp32 = 1024;  // float2 entries
+template <int IN, int H, int MLPP>
+__host__ __device__ constexpr int dec_mlp_bytes() {
+  return (int)(((MLPP ? sizeof(tc::TcSmem<IN, H>) : (size_t)mlp_floats<IN, H>() * 4) + 127) / 128 * 128);
+}
+template <int IN, int H, int MLPP>
+__host__ __device__ constexpr int dec_smem_bytes(int L, int S) {
+  return dec_mlp_bytes<IN, H, MLPP>() +
+         ((S <= kDecMaxS && L <= kDecMaxL) ? dec_tables_bytes(L, S) + (MLPP ? 0 : kDecStageFp32 * 8) : 0);
+}
+
 template <int IN, int H, int MLPP>
 __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const uint16_t* w16,
                                                      const uint32_t* keys, const uint32_t* slots,
@@ -154,6 +330,15 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
   const uint32_t tiles_per = (uint32_t)((S3 + 127) / 128);
   const uint32_t work = n * tiles_per;
   if (blockIdx.x >= work) return;  // block-uniform, before any barrier
+  // the staged encoder's shared memory (bricks up to 16^3 + apron, up to
+  // 24 levels; otherwise every voxel encodes its own point)
+  const bool staged = S <= kDecMaxS && q.L <= kDecMaxL;
+  char* extra = reinterpret_cast<char*>(smem4) + dec_mlp_bytes<IN, H, MLPP>();
+  AxisCell* tab = reinterpret_cast<AxisCell*>(extra);
+  LevelBox* box = reinterpret_cast<LevelBox*>(extra + q.L * 3 * S * (int)sizeof(AxisCell));
+  float2* stage = MLPP ? reinterpret_cast<float2*>(tcs.a2)
+                       : reinterpret_cast<float2*>(extra + dec_tables_bytes(q.L, S));
+  const int cap = MLPP ? (int)(sizeof(tcs.a2) / sizeof(float2)) : kDecStageFp32;
   uint32_t phase = 0;
   if (MLPP) {
     tc::load_tc_weights<IN, H, (MLPP > 0 ? MLPP - 1 : 0)>(tcs, w16, q.w);
@@ -164,7 +349,8 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
   }
   for (uint32_t wi = blockIdx.x; wi < work; wi += gridDim.x) {
     const uint32_t r = wi / tiles_per;
-    const int v = (int)(wi % tiles_per) * 128 + (int)threadIdx.x;
+    const int v0 = (int)(wi % tiles_per) * 128;
+    const int v = v0 + (int)threadIdx.x;
     const bool valid = v < S3;
     uint32_t key = keys ? keys[r] : c.off[c.L - 1] + r;
     const uint32_t slot = keys ? slots[r] : r;
@@ -174,24 +360,29 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
     const uint32_t local = key - c.off[l];
     const int b[3] = {(int)(local % c.nb[l][0]), (int)((local / c.nb[l][0]) % c.nb[l][1]),
                       (int)(local / ((uint32_t)c.nb[l][0] * c.nb[l][1]))};
-    const int vv = valid ? v : 0;
+    const int vv = valid ? v : v0;  // past the brick's end: any voxel of the tile
     const int lv[3] = {vv % S, (vv / S) % S, vv / (S * S)};
-    float x[3];
+    float feat[IN];
+    if (staged) {
+      const int v1 = v0 + 128 < S3 ? v0 + 128 : S3;
+      if (q.table_prec == CINR_PREC_FP16) {
+        stage_tile<true>(q, c, l, b, v0, v1, tab, box, stage, cap);
+        encode_voxel<IN / 2, true>(q, S, lv[0], lv[1], lv[2], tab, box, stage, feat);
+      } else {
+        stage_tile<false>(q, c, l, b, v0, v1, tab, box, stage, cap);
+        encode_voxel<IN / 2, false>(q, S, lv[0], lv[1], lv[2], tab, box, stage, feat);
+      }
+    } else {
+      float x[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      int j = b[a] * c.B - 1 + lv[a];
-      j = j < 0 ? 0 : (j > c.dims[l][a] - 1 ? c.dims[l][a] - 1 : j);
-      float t = f_mul(f_add((float)j, 0.5f), (float)(1 << l));
-      x[a] = clamp01(f_div(t, (float)c.vol[a]));
+      for (int a = 0; a < 3; ++a) x[a] = voxel_coord(b[a] * c.B - 1 + lv[a], c.dims[l][a], l, c.vol[a]);
+      encode_point<IN / 2>(q, x[0], x[1], x[2], feat);
     }
     float y;
-    if (MLPP == 0) {
-      y = valid ? inr_raw_fp32<IN, H>(q, sw, x[0], x[1], x[2]) : 0.0f;
-    } else {
-      float feat[IN];
-      encode_point<IN / 2>(q, x[0], x[1], x[2], feat);
+    if (MLPP == 0)
+      y = valid ? mlp_fp32<IN, H>(sw, feat) : 0.0f;
+    else
       y = tc::mlp_tile<IN, H, (MLPP > 0 ? MLPP - 1 : 0)>(tcs, feat, valid, phase, err);
-    }
     if (valid && in_pool) {
       const float val = fmaf(q.vscale, y, q.vmin);
       const size_t o = (size_t)slot * S3 + v;
@@ -598,10 +789,14 @@ int launch_decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys
                   const uint32_t* n_dev, uint32_t n_grid, int cap_per_sm, cudaStream_t s) {
   if (n_grid == 0) return CINR_OK;
   auto k = decode_kernel<IN, H, MLPP>;
-  int smem = MLPP ? (int)sizeof(tc::TcSmem<IN, H>) : mlp_floats<IN, H>() * 4;
+  int smem = dec_smem_bytes<IN, H, MLPP>(inr->dev.L, c.S);
   if (MLPP && smem < tc::kMinSmemPerCta) smem = tc::kMinSmemPerCta;  // <= 8 TMEM users per SM
-  static int per_sm = 0;
-  if (!per_sm) {
+  // residency depends on the shared memory, which depends on the INR's
+  // levels and the brick size: recomputed when they change
+  static int per_sm = 0, per_sm_smem = -1;
+  if (per_sm_smem != smem) {
+    per_sm = 0;
+    per_sm_smem = smem;
     CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     // tensor-core path: the largest shared-memory carveout, so that the
     // occupancy query (and the launch) see every CTA that fits
@@ -850,7 +1045,7 @@ int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStr
   // gather + sort; commit; decode (+ page and map kernels)
   auto sel = [](int bits) { return 3 + 2 * (bits <= 11 ? 1 : (bits + 10) / 11); };
   if (!lag2) {
-    int ed = decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, s);
+    int ed = decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, s, c->decode_ctas);
     if (ed) return ed;
     if (paged) {
       ed = map_selected(frame);
@@ -862,7 +1057,8 @@ int cinr_cache_end_frame(cinr_cache_s* c, unsigned long long* stats_dev, cudaStr
   c->last_launches = (uint32_t)(sel(rbits) + sel(vbits) + 2) + extra;
   CINR_CK(cudaEventRecord(c->e_sel, s));
   CINR_CK(cudaStreamWaitEvent(c->dstream, c->e_sel, 0));
-  int e2 = decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, c->dstream, 2);
+  int e2 = decode(c->inr, c->dev, c->req_sorted, c->vic_sorted, c->decode_n, want, c->dstream,
+                  c->decode_ctas > 0 && c->decode_ctas < 2 ? c->decode_ctas : 2);
   if (e2) return e2;
   CINR_CK(cudaEventRecord(c->e_dec, c->dstream));
   c->pending = true;
@@ -907,5 +1103,12 @@ extern "C" int cinr_debug_set_entry(cinr_cache_t c, int what, size_t index, uint
   if (ew) return ew;
   CINR_CK(cudaMemcpyAsync(dst + index, &value, 4, cudaMemcpyHostToDevice, s));
   CINR_CK(cudaStreamSynchronize(s));
+  return CINR_OK;
+}
+
+extern "C" int cinr_cache_set_decode_ctas(cinr_cache_t c, int ctas_per_sm) {
+  if (!c) return set_error(CINR_ERR_ARG, "cache is NULL");
+  if (ctas_per_sm < 0 || ctas_per_sm > 8) return set_error(CINR_ERR_ARG, "ctas_per_sm must be in [0, 8]");
+  c->decode_ctas = ctas_per_sm;
   return CINR_OK;
 }

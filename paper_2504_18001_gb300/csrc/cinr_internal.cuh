@@ -645,6 +645,7 @@ struct cinr_cache_s {
   uint32_t* decode_n;
   int slot_bits, key_bits;
   uint32_t last_launches;  // kernels of the last end-of-frame update
+  int decode_ctas = 0;     // decode CTAs per SM (0: as many as fit)
   // lag 2: decode stream, "selection done" and "decode done" events, and
   // whether a decoded batch waits to be mapped
   cudaStream_t dstream = nullptr;

@@ -686,12 +686,17 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
 // brick) and the brick size BB a compile-time power of two.  It takes the
 // same samples, LoDs, lookups, requests, stamps and values as
 // march_cached_kernel, in the same binary32 operations; what it saves is
-// bookkeeping: no per-sample tests of the run-time modes, the start of the
-// next sample carried over from this sample's unclipped end (the same
-// tn + (k+1) dt), the dither key k * 0x9E3779B9 advanced by addition, brick
-// and voxel coordinates of non-negative values truncated (the floor of a
-// non-negative binary32), and the sample count of a ray taken from its last
-// sample index.
+// bookkeeping and control flow: no per-sample tests of the run-time modes;
+// the start of the next sample carried over from this sample's unclipped
+// end (the same tn + (k+1) dt); the dither key k * 0x9E3779B9 advanced by
+// addition; brick and voxel coordinates of non-negative values truncated
+// (the floor of a non-negative binary32); brick indices from one product
+// with 2^-l / B (products with powers of two are exact); the sample count
+// of a ray taken from its last sample index; and one straight-line pass
+// per sample that every lane of the warp runs, with the rare events --
+// fallback walks, requests, first stamps of a slot, ray ends -- behind
+// warp-uniform votes, so that the warp issues no divergent branches on
+// its common path (all lanes of a warp march the same sample index k).
 template <bool F16POOL, int BB>
 __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __grid_constant__ FrameParams P) {
   static_assert(BB > 0 && (BB & (BB - 1)) == 0, "brick size must be a power of two");
@@ -739,7 +744,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
     const int py = (int)((t64 / P.tiles_x) * 8 + (w >> 3));
     const bool inside = px < cam.W && py < cam.H;
     const uint32_t pixel = inside ? (uint32_t)(py * cam.W + px) : 0u;
-    float d[3], tn = 0.f, tf = 0.f;
+    float d[3] = {0.f, 0.f, 0.f}, tn = 0.f, tf = 0.f;
     bool active = inside && ray_setup(cam, px, py, d, tn, tf);
     if (inside && !active) P.out[pixel] = make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t rseed = ray_seed(P.fseed, pixel);
@@ -748,116 +753,129 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
     float a = tn;         // start of sample k: tn + k dt (tn + 0 dt = tn)
     float kf1 = 1.0f;     // k + 1 as binary32 (exact below 2^24)
     uint32_t kh = 0u;     // k * 0x9E3779B9
+    if (active && !(a < tf)) {  // (tn < tf for a hit: not reached)
+      P.out[pixel] = make_float4(0.f, 0.f, 0.f, 0.f);
+      active = false;
+    }
+    // Every lane runs the sample code each step, active or not (an
+    // inactive lane's coordinates stay clamped inside the volume, its
+    // lookups inside the tables and the pool); what an inactive lane
+    // computes is discarded.  The rare events -- fallback walks, requests,
+    // first stamps, ray ends -- sit behind warp-uniform tests.
     while (__any_sync(kFull, active)) {
-      bool want_req = false, hit = false;
-      uint32_t req_key = 0, hit_slot = 0;
-      float v = 0.f, len = 0.f;
-      if (active && !(a < tf)) {
-        P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
-        active = false;
-      }
-      const bool took = active;  // this lane takes sample k
-      if (took) {
-        // sample k: midpoint of [a, min(tn + (k+1) dt, tf)] (sample_at)
-        const float an = f_add(tn, f_mul(kf1, cam.dt));
-        const float bnd = fminf(an, tf);
-        const float tm = f_mul(f_add(a, bnd), 0.5f);
-        len = f_sub(bnd, a);
-        a = an;
-        kf1 = f_add(kf1, 1.0f);
-        const float pv0 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[0], f_mul(tm, d[0])), cam.h[0]), cam.inv_e[0])), volf0);
-        const float pv1 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[1], f_mul(tm, d[1])), cam.h[1]), cam.inv_e[1])), volf1);
-        const float pv2 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[2], f_mul(tm, d[2])), cam.h[2]), cam.inv_e[2])), volf2);
-        // stochastic LoD, footprint mode (sample_lod)
+      // sample k: midpoint of [a, min(tn + (k+1) dt, tf)] (sample_at)
+      const float an = f_add(tn, f_mul(kf1, cam.dt));
+      const float bnd = fminf(an, tf);
+      const float tm = f_mul(f_add(a, bnd), 0.5f);
+      const float len = f_sub(bnd, a);
+      const float pv0 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[0], f_mul(tm, d[0])), cam.h[0]), cam.inv_e[0])), volf0);
+      const float pv1 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[1], f_mul(tm, d[1])), cam.h[1]), cam.inv_e[1])), volf1);
+      const float pv2 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[2], f_mul(tm, d[2])), cam.h[2]), cam.inv_e[2])), volf2);
+      // stochastic LoD, footprint mode (sample_lod)
+      const float xf = f_mul(tm, cam.lodc);
+      int l = 0;
+      if (xf >= 1.0f) {
         uint32_t st = rseed ^ kh;
         if (st == 0u) st = 0x6D2B79F5u;
         const uint32_t u24 = xorshift32(st) >> 8;
-        const float xf = f_mul(tm, cam.lodc);
-        int l = 0;
-        if (xf >= 1.0f) {
-          const uint32_t bits = __float_as_uint(xf);
-          l = (int)(bits >> 23) - 127 + (u24 < 2u * (bits & 0x7FFFFFu) ? 1 : 0);
-          l = l > Lm1 ? Lm1 : l;
-        }
-        for (int lev = l; lev <= Lm1; ++lev) {
-          const LevelGeo g = s_geo[lev];
-          // (pv 2^-l) / B = pv (2^-l / B): products with powers of two are exact
-          const int b0 = min((int)f_mul(pv0, g.scale_b), g.nb0 - 1);
-          const int b1 = min((int)f_mul(pv1, g.scale_b), g.nb1 - 1);
-          const int b2 = min((int)f_mul(pv2, g.scale_b), g.nb2 - 1);
-          const uint32_t key = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
-          if (!in_range(key, c.n_bricks, c.err)) continue;
-          const uint32_t e = __ldg(pt + key);
-          if (!(e & kMapped)) {
-            if (lev == l) {
-              want_req = true;
-              req_key = key;
-            }
-            continue;  // the preloaded coarsest LoD ends the walk
-          }
-          if (!in_range(e & ~kMapped, c.n_slots, c.err)) continue;  // checked builds: read as Unmapped
-          hit_slot = e & ~kMapped;
-          const float s0 = f_mul(pv0, g.scale), s1 = f_mul(pv1, g.scale), s2 = f_mul(pv2, g.scale);
-          const float q0 = fminf(fmaxf(f_sub(s0, 0.5f), 0.0f), g.dmax0);
-          const float q1 = fminf(fmaxf(f_sub(s1, 0.5f), 0.0f), g.dmax1);
-          const float q2 = fminf(fmaxf(f_sub(s2, 0.5f), 0.0f), g.dmax2);
-          const int i0 = (int)q0, i1 = (int)q1, i2 = (int)q2;
-          const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
-          const int o = ((i2 - b2 * B + 1) * S + (i1 - b1 * B + 1)) * S + (i0 - b0 * B + 1);
-          if (!in_range((uint32_t)o, S3 - SS - S - 1, c.err)) continue;
-          const void* bp = static_cast<const char*>(pool) + (size_t)hit_slot * S3 * (F16POOL ? 2u : 4u);
-          const float v000 = pool_ld<F16POOL>(bp, o), v100 = pool_ld<F16POOL>(bp, o + 1);
-          const float v010 = pool_ld<F16POOL>(bp, o + S), v110 = pool_ld<F16POOL>(bp, o + S + 1);
-          const float v001 = pool_ld<F16POOL>(bp, o + SS), v101 = pool_ld<F16POOL>(bp, o + SS + 1);
-          const float v011 = pool_ld<F16POOL>(bp, o + SS + S), v111 = pool_ld<F16POOL>(bp, o + SS + S + 1);
-          const float2 a0 = make_float2(v000, v001), a1 = make_float2(v100, v101);
-          const float2 c0 = make_float2(v010, v011), c1 = make_float2(v110, v111);
-          const float2 ff0 = make_float2(f0, f0);
-          const float2 X0 = f2_fma(ff0, f2_sub(a1, a0), a0);
-          const float2 X1 = f2_fma(ff0, f2_sub(c1, c0), c0);
-          const float2 Y = f2_fma(make_float2(f1, f1), f2_sub(X1, X0), X0);
-          v = fmaf(f2, Y.y - Y.x, Y.x);
-          hit = true;
-          if (lev != l) ++n_fb;
-          break;
-        }
-        if (!hit) ++n_miss;  // not reached while the coarsest LoD stays mapped (v = 0)
+        const uint32_t bits = __float_as_uint(xf);
+        l = (int)(bits >> 23) - 127 + (u24 < 2u * (bits & 0x7FFFFFu) ? 1 : 0);
+        l = l > Lm1 ? Lm1 : l;
       }
+      // page-table lookup at the requested LoD
+      LevelGeo g = s_geo[l];
+      int b0 = min((int)f_mul(pv0, g.scale_b), g.nb0 - 1);
+      int b1 = min((int)f_mul(pv1, g.scale_b), g.nb1 - 1);
+      int b2 = min((int)f_mul(pv2, g.scale_b), g.nb2 - 1);
+      const uint32_t key = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
+      uint32_t e = in_range(key, c.n_bricks, c.err) ? __ldg(pt + key) : 0u;
+      if ((e & kMapped) && !in_range(e & ~kMapped, c.n_slots, c.err)) e = 0u;
+      const bool want_req = active && !(e & kMapped);
       const unsigned rq = __ballot_sync(kFull, want_req);
-      if (want_req) {
-        const unsigned peers = __match_any_sync(rq, req_key);
-        if (lane == __ffs(peers) - 1) {
-          const uint32_t old = atomicMax(c.rank + req_key, P.Tf);
-          if (old < P.Tf) {
-            atomicAdd(&s_rare[0], 1u);
-            push_touched(c, req_key);
+      if (rq) {
+        // requests (Sec. 4.3.3), aggregated over the lanes naming one brick
+        if (want_req) {
+          const unsigned peers = __match_any_sync(rq, key);
+          if (lane == __ffs(peers) - 1) {
+            const uint32_t old = atomicMax(c.rank + key, P.Tf);
+            if (old < P.Tf) {
+              atomicAdd(&s_rare[0], 1u);
+              push_touched(c, key);
+            }
+            atomicAdd(c.rank + key, (uint32_t)__popc(peers));
+            atomicMin(c.rank + key, P.Tf + 1000u);
           }
-          atomicAdd(c.rank + req_key, (uint32_t)__popc(peers));
-          atomicMin(c.rank + req_key, P.Tf + 1000u);
+          // fallback to coarser LoDs (Sec. 4.3); the preloaded coarsest
+          // LoD ends the walk
+          int lev = l;
+          while (!(e & kMapped) && lev < Lm1) {
+            ++lev;
+            g = s_geo[lev];
+            b0 = min((int)f_mul(pv0, g.scale_b), g.nb0 - 1);
+            b1 = min((int)f_mul(pv1, g.scale_b), g.nb1 - 1);
+            b2 = min((int)f_mul(pv2, g.scale_b), g.nb2 - 1);
+            const uint32_t fk = g.off + (uint32_t)b0 + (uint32_t)g.nb0 * ((uint32_t)b1 + (uint32_t)g.nb1 * (uint32_t)b2);
+            e = in_range(fk, c.n_bricks, c.err) ? __ldg(pt + fk) : 0u;
+            if ((e & kMapped) && !in_range(e & ~kMapped, c.n_slots, c.err)) e = 0u;
+          }
+          if (e & kMapped) ++n_fb; else ++n_miss;  // a miss: not reached while the coarsest LoD stays mapped
         }
       }
+      // trilinear inside the stored brick at the level that serves the
+      // sample (an unmapped entry of an inactive lane reads slot 0)
+      const uint32_t hit_slot = e & ~kMapped;
+      const float s0 = f_mul(pv0, g.scale), s1 = f_mul(pv1, g.scale), s2 = f_mul(pv2, g.scale);
+      const float q0 = fminf(fmaxf(f_sub(s0, 0.5f), 0.0f), g.dmax0);
+      const float q1 = fminf(fmaxf(f_sub(s1, 0.5f), 0.0f), g.dmax1);
+      const float q2 = fminf(fmaxf(f_sub(s2, 0.5f), 0.0f), g.dmax2);
+      const int i0 = (int)q0, i1 = (int)q1, i2 = (int)q2;
+      const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
+      int o = ((i2 - b2 * B + 1) * S + (i1 - b1 * B + 1)) * S + (i0 - b0 * B + 1);
+      if (!in_range((uint32_t)o, S3 - SS - S - 1, c.err)) o = 0;
+      const void* bp = static_cast<const char*>(pool) + (size_t)hit_slot * S3 * (F16POOL ? 2u : 4u);
+      const float v000 = pool_ld<F16POOL>(bp, o), v100 = pool_ld<F16POOL>(bp, o + 1);
+      const float v010 = pool_ld<F16POOL>(bp, o + S), v110 = pool_ld<F16POOL>(bp, o + S + 1);
+      const float v001 = pool_ld<F16POOL>(bp, o + SS), v101 = pool_ld<F16POOL>(bp, o + SS + 1);
+      const float v011 = pool_ld<F16POOL>(bp, o + SS + S), v111 = pool_ld<F16POOL>(bp, o + SS + S + 1);
+      const float2 a0 = make_float2(v000, v001), a1 = make_float2(v100, v101);
+      const float2 c0 = make_float2(v010, v011), c1 = make_float2(v110, v111);
+      const float2 ff0 = make_float2(f0, f0);
+      const float2 X0 = f2_fma(ff0, f2_sub(a1, a0), a0);
+      const float2 X1 = f2_fma(ff0, f2_sub(c1, c0), c0);
+      const float2 Y = f2_fma(make_float2(f1, f1), f2_sub(X1, X0), X0);
+      const float v = (e & kMapped) ? fmaf(f2, Y.y - Y.x, Y.x) : 0.0f;
       // LRU stamp: once per slot and frame (the first exchange counts it)
-      if (hit && hit_slot != stamped) {
-        if (c.stamp[hit_slot] != P.frame && atomicExch(c.stamp + hit_slot, P.frame) != P.frame)
+      const bool changed = active && (e & kMapped) && hit_slot != stamped;
+      if (__any_sync(kFull, changed)) {
+        if (changed && c.stamp[hit_slot] != P.frame && atomicExch(c.stamp + hit_slot, P.frame) != P.frame)
           atomicAdd(&s_rare[1], 1u);
-        stamped = hit_slot;
       }
-      if (took) {
-        const float4 e4 = tf_lookup_fast(s_tf, v);
-        const float alpha = 1.0f - ex2_approx(e4.w * (len * -1.4426950408889634f));
-        const float wgt = T * alpha;
-        Cr = fmaf(wgt, e4.x, Cr);
-        Cg = fmaf(wgt, e4.y, Cg);
-        Cb = fmaf(wgt, e4.z, Cb);
+      if (changed) stamped = hit_slot;
+      // transfer function and front-to-back compositing
+      const float4 e4 = tf_lookup_fast(s_tf, v);
+      const float alpha = 1.0f - ex2_approx(e4.w * (len * -1.4426950408889634f));
+      const float wgt = active ? T * alpha : 0.0f;
+      Cr = fmaf(wgt, e4.x, Cr);
+      Cg = fmaf(wgt, e4.y, Cg);
+      Cb = fmaf(wgt, e4.z, Cb);
+      if (active) {
         T *= 1.0f - alpha;
+        a = an;
+        kf1 = f_add(kf1, 1.0f);
         ++k;
         kh += 0x9E3779B9u;
-        if (--seg == 0) {
-          seg = P.K;
-          if (T < P.eps) {
-            P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
-            active = false;
-          }
+      }
+      // termination after every K samples (k is the same for the warp's
+      // active lanes) and the end of the ray
+      bool ended = active && !(a < tf);
+      if (--seg == 0) {
+        seg = P.K;
+        ended = ended || (active && T < P.eps);
+      }
+      if (__any_sync(kFull, ended)) {
+        if (ended) {
+          P.out[pixel] = make_float4(Cr, Cg, Cb, 1.0f - T);
+          active = false;
         }
       }
     }

@@ -40,7 +40,7 @@ def test_reference_arm_line():
 
 @pytest.mark.gpu
 def test_gpu_arm_line():
-    d = _run(["--steps", "3", "--warmup", "3", "--uncached-steps", "1"])
+    d = _run(["--steps", "3", "--warmup", "3", "--uncached-steps", "1", "--no-other"])
     for k in BASE_KEYS + ("roofline", "cpu_baseline", "clocks", "gpu_launches"):
         assert k in d, k
     assert d["n_gpus"] == 1 and d["steps"] == 3 and d["warmup"] == 3 and d["value"] > 0

@@ -91,6 +91,11 @@ assert len(mapped) > 0
 for k in mapped:  # every resident page names the page slot one past the page pool
     cache.set_entry(cinr.DUMP_PAGE_DIR, int(k), 0x80000000 | 64)
 expect_check(lambda: frame(rend, cache, 1))
+# the frame's cache update may have met the planted entries too (request
+# candidates and evictions read the page directory): those checks report to
+# the INR's status word, which the status call reads and clears
+rc = L.cinr_inr_status(inr.h, cinr._stream(None))
+assert rc in (0, cinr.ERR_DEVICE_CHECK), rc
 for k in mapped:
     cache.set_entry(cinr.DUMP_PAGE_DIR, int(k), int(pd[k]))
 frame(rend, cache, 2)
