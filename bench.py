@@ -951,7 +951,10 @@ def main():
         res = run_reference(args, wl) if args.impl == "reference" else run_gpu(args, wl)
         if (res is not None and args.impl != "reference" and args.workload == "orbit"
                 and int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_other):
-            res["other_configs"] = other_configs(args)
+            try:  # the headline line is printed whatever happens here
+                res["other_configs"] = other_configs(args)
+            except Exception as e:
+                res["other_configs"] = {"error": f"{type(e).__name__}: {e}"[:300]}
     if res is not None:
         print(json.dumps(res))
 

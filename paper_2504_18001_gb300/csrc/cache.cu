@@ -216,7 +216,11 @@ __device__ __forceinline__ void stage_tile(const InrDev& q, const CacheDev& c, i
       bx.n0 = ta[S - 1].i + 2 - bx.lo0;
       bx.n1 = ta[S + y1].i + 2 - bx.lo1;
       bx.n2 = ta[2 * S + z1].i + 2 - bx.lo2;
-      size = bx.n0 * bx.n1 * bx.n2;
+      // a fine level's box at a coarse LoD can hold ~10^10 vertices: the
+      // product in 64 bits, and anything beyond the buffer counts as cap + 1
+      // (never staged; the scan of 32 such sizes stays far inside an int)
+      const long long n = (long long)bx.n0 * (long long)bx.n1 * (long long)bx.n2;
+      size = n > (long long)cap ? cap + 1 : (int)n;
     }
     // coarse levels first, while the stage buffer has room
     int scan = size;
