@@ -165,6 +165,13 @@ __host__ __device__ constexpr int dec_tables_bytes(int L, int S) {
   return L * 3 * S * (int)sizeof(AxisCell) + L * (int)sizeof(LevelBox);
 }
 
+// e / n for 0 <= e < 2^22 and n >= 1, with inv = 1/n rounded: (e + 1/2) / n
+// lies at least 1/(2n) from an integer, and the two roundings move it by
+// less than (e + 1/2) 2^-23 / n < 1/(2n), so the truncation is exact.
+__device__ __forceinline__ int div_small(int e, float inv) {
+  return (int)(((float)e + 0.5f) * inv);
+}
+
 // Voxel-centre coordinate of LoD-l voxel j (clamped to the grid) along an
 // axis of V LoD-0 voxels: ((j + 0.5) 2^l) / V in binary32.
 __device__ __forceinline__ float voxel_coord(int j, int dim_l, int l, int V) {
@@ -187,14 +194,18 @@ __device__ __forceinline__ float2 lerp_corners(const float2 e[8], float wx, floa
 
 // Stages the tile's boxes and fills the axis tables; all 128 threads.
 // b: brick coordinates, l: its LoD, v0 / v1: the tile's voxel range.
-template <bool F16>
+// TC_BARRIERS: the tensor-core MLP's barriers already separate one tile's
+// reads of the tables from the next tile's writes.
+template <bool F16, bool TC_BARRIERS>
 __device__ __forceinline__ void stage_tile(const InrDev& q, const CacheDev& c, int l, const int b[3], int v0,
                                            int v1, AxisCell* tab, LevelBox* box, float2* stage, int cap) {
   const int S = c.S, SS = S * S, L = q.L;
   const int t = threadIdx.x;
-  __syncthreads();  // the previous tile's voxels have read the tables
+  if (!TC_BARRIERS) __syncthreads();  // the previous tile's voxels have read the tables
+  const float inv_s = 1.0f / (float)S;
   for (int e = t; e < L * 3 * S; e += blockDim.x) {
-    const int j = e / (3 * S), a = (e / S) % 3, lv = e % S;
+    const int ja = div_small(e, inv_s), lv = e - ja * S;
+    const int j = div_small(ja, 1.0f / 3.0f), a = ja - 3 * j;
     const float x = voxel_coord(b[a] * c.B - 1 + lv, c.dims[l][a], l, c.vol[a]);
     int ii;
     float w;
@@ -234,19 +245,21 @@ __device__ __forceinline__ void stage_tile(const InrDev& q, const CacheDev& c, i
   }
   __syncthreads();
   const uint32_t T = 1u << q.log2T;
-  for (int j = 0; j < L; ++j) {  // block-uniform loop
+  const int warp = t >> 5, lane = t & 31, n_warps = blockDim.x >> 5;
+  for (int j = warp; j < L; j += n_warps) {  // a level per warp; its lanes along the box
     const LevelBox bx = box[j];
     if (bx.base < 0) continue;
-    const int N = q.res[j];
     const int nb01 = bx.n0 * bx.n1;
     const int size = nb01 * bx.n2;
+    const float inv0 = 1.0f / (float)bx.n0, inv1 = 1.0f / (float)bx.n1;
     const bool dense = (q.dense_mask >> j) & 1u;
-    const uint32_t n1 = (uint32_t)N + 1u;
+    const uint32_t n1 = (uint32_t)q.res[j] + 1u;
     const char* table = reinterpret_cast<const char*>(q.table) + (size_t)j * T * (F16 ? 4 : 8);
-    for (int e = t; e < size; e += blockDim.x) {
-      const uint32_t cx = (uint32_t)(bx.lo0 + e % bx.n0);
-      const uint32_t cy = (uint32_t)(bx.lo1 + (e / bx.n0) % bx.n1);
-      const uint32_t cz = (uint32_t)(bx.lo2 + e / nb01);
+    for (int e = lane; e < size; e += 32) {
+      const int yz = div_small(e, inv0), z = div_small(yz, inv1);
+      const uint32_t cx = (uint32_t)(bx.lo0 + e - yz * bx.n0);
+      const uint32_t cy = (uint32_t)(bx.lo1 + yz - z * bx.n1);
+      const uint32_t cz = (uint32_t)(bx.lo2 + z);
       uint32_t idx = vertex_index(dense, n1, T, cx, cy, cz);
       if (!in_range(idx, T, q.err)) idx = 0u;
       stage[bx.base + e] = load_entry_t<F16>(table, idx);
@@ -370,10 +383,10 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
     if (staged) {
       const int v1 = v0 + 128 < S3 ? v0 + 128 : S3;
       if (q.table_prec == CINR_PREC_FP16) {
-        stage_tile<true>(q, c, l, b, v0, v1, tab, box, stage, cap);
+        stage_tile<true, (MLPP > 0)>(q, c, l, b, v0, v1, tab, box, stage, cap);
         encode_voxel<IN / 2, true>(q, S, lv[0], lv[1], lv[2], tab, box, stage, feat);
       } else {
-        stage_tile<false>(q, c, l, b, v0, v1, tab, box, stage, cap);
+        stage_tile<false, (MLPP > 0)>(q, c, l, b, v0, v1, tab, box, stage, cap);
         encode_voxel<IN / 2, false>(q, S, lv[0], lv[1], lv[2], tab, box, stage, feat);
       }
     } else {
