@@ -251,6 +251,7 @@ def run_gpu(args, wl):
         wl = dict(wl, n_req=best["n_req"], brick=best["brick"])
         args.ray_layout, args.graph = best["ray_layout"], best["use_graph"]
         args.decode_ctas = best["decode_ctas"]
+        args.decode_encoder = best["decode_encoder"]
         tuned = {"chosen": best, "trials": trials}
     S3 = (wl["brick"] + 2) ** 3
     fill = args.fill if args.fill is not None else wl["fill"]
@@ -263,6 +264,7 @@ def run_gpu(args, wl):
                         preload=1, lag=args.lag, page=args.page, n_pages=args.n_pages,
                         device=device)
         cc.set_decode_ctas(getattr(args, "decode_ctas", 0))
+        cc.set_decode_encoder(args.decode_encoder)
         return cc
 
     def make_renderer():
@@ -461,6 +463,7 @@ def run_gpu(args, wl):
                    "step_mode": wl["step_mode"], "step_lod_max": wl["step_lod_max"],
                    "ray_layout": "thread per ray" if args.ray_layout == 0 else "warp per ray",
                    "cuda_graph": bool(args.graph),
+                   "decode_encoder": "staged tile encoder" if args.decode_encoder else "per-voxel gathers",
                    "tf_ramps": args.tf_ramps,
                    "macro_cell": args.macro or None,
                    "lag": args.lag,
@@ -898,6 +901,8 @@ def main():
     ap.add_argument("--fill", type=int, default=None,
                     help="cache-fill frames before the warm-up frames (workload default)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
+    ap.add_argument("--decode-encoder", type=int, default=1, choices=[0, 1],
+                    help="brick decode encoder: 1 staged tile encoder, 0 per-voxel gathers")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the short tera-scale and learned runs after the headline")
     ap.add_argument("--impl", default="cinr", choices=["cinr", "reference"])

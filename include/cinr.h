@@ -554,6 +554,14 @@ int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap,
  * Errors: CINR_ERR_ARG for a NULL cache or a count out of range. */
 int cinr_cache_set_decode_ctas(cinr_cache_t cache, int ctas_per_sm);
 
+/* Chooses the hash-grid encoder of the brick decode: 1 (the default) the
+ * tile encoder -- per-axis cell tables of the brick's voxel lattice, each
+ * level's corner box staged into shared memory by coalesced loads where it
+ * fits, corners combined by separable lerps --, 0 every voxel gathering its
+ * 8 corners per level from the table.  Both give the same voxels up to FP32
+ * rounding; an autotuner knob.  Errors: CINR_ERR_ARG. */
+int cinr_cache_set_decode_encoder(cinr_cache_t cache, int staged);
+
 /* Writes one u32 entry of a cache's page tables (what = CINR_DUMP_PAGE_TABLE,
  * CINR_DUMP_PAGE_DIR or CINR_DUMP_PAGES; index < the count that
  * cinr_debug_dump reports for it), enqueued on `stream` and synchronised.

@@ -6,8 +6,10 @@ tuner times short runs of a workload for every candidate setting of the
 knobs the workload leaves free -- requests per frame (which also sets the
 decode batch that the persistent decode kernel takes), the ray layout of the
 marching kernel (one ray per thread or per warp), whether each frame runs as
-a CUDA graph, the brick edge, and how many CTAs per SM the tensor-core
-decode runs with (its 128-row MLP tiles per SM; 0 = as many as fit) -- and
+a CUDA graph, the brick edge, how many CTAs per SM the tensor-core decode
+runs with (its 128-row MLP tiles per SM; 0 = as many as fit) and which
+hash-grid encoder the decode uses (the staged tile encoder or per-voxel
+gathers) -- and
 returns the fastest setting whose cached frame stays within `min_psnr` dB of
 the uncached FP32 frame.
 Each candidate first renders until its cache has caught up with the camera
@@ -31,7 +33,8 @@ def _psnr(a, b):
 
 
 def tune(inr_cached, inr_fp32, vol, frame_inputs, W, H, *, bricks=(8,), n_reqs=(1024, 4096, 8192),
-         layouts=(0, 1), graphs=(0, 1), decode_ctas=(0, 2), levels=4, pool_mib=1024, storage="fp16",
+         layouts=(0, 1), graphs=(0, 1), decode_ctas=(0, 2), decode_encoders=(1, 0), levels=4,
+         pool_mib=1024, storage="fp16",
          max_warmup=160, timed=10, lod_scale=1.0, step_mode=0, step_lod_max=0, min_psnr=40.0,
          device="cuda"):
     """Returns (best, results): best is the chosen knob dict; results lists
@@ -42,12 +45,13 @@ def tune(inr_cached, inr_fp32, vol, frame_inputs, W, H, *, bricks=(8,), n_reqs=(
     img = torch.empty((H, W, 4), dtype=torch.float32, device=device)
     ref = torch.empty_like(img)
     results = []
-    for brick, n_req, layout, graph, dctas in itertools.product(bricks, n_reqs, layouts, graphs,
-                                                                decode_ctas):
+    for brick, n_req, layout, graph, dctas, denc in itertools.product(bricks, n_reqs, layouts, graphs,
+                                                                      decode_ctas, decode_encoders):
         t0 = time.perf_counter()
         cache = cinr.Cache(inr_cached, vol, pool_bytes=pool_mib << 20, brick=brick, levels=levels,
                            n_req=n_req, storage=storage, device=device)
         cache.set_decode_ctas(dctas)
+        cache.set_decode_encoder(denc)
         rend = cinr.Renderer(W, H, vol, K=32, eps_T=1e-3, lod_scale=lod_scale, ray_layout=layout,
                              step_mode=step_mode, step_lod_max=step_lod_max, use_graph=graph,
                              device=device)
@@ -72,10 +76,12 @@ def tune(inr_cached, inr_fp32, vol, frame_inputs, W, H, *, bricks=(8,), n_reqs=(
         rend.render(inr_fp32, cam, tf, cache=None, out=ref)
         psnr = _psnr(img, ref)
         results.append(dict(brick=brick, n_req=n_req, ray_layout=layout, use_graph=graph,
-                            decode_ctas=dctas, ms_per_frame=float(np.mean(ms)), psnr_db=psnr,
+                            decode_ctas=dctas, decode_encoder=denc, ms_per_frame=float(np.mean(ms)),
+                            psnr_db=psnr,
                             warmup_frames=warmup, tune_s=time.perf_counter() - t0))
         del cache, rend
         torch.cuda.synchronize()
     ok = [r for r in results if r["psnr_db"] >= min_psnr] or results
     best = min(ok, key=lambda r: r["ms_per_frame"])
-    return {k: best[k] for k in ("brick", "n_req", "ray_layout", "use_graph", "decode_ctas")}, results
+    return {k: best[k] for k in ("brick", "n_req", "ray_layout", "use_graph", "decode_ctas",
+                                 "decode_encoder")}, results

@@ -135,6 +135,7 @@ _SIGS = {
     "cinr_debug_set_entry": [_vp, C.c_int, C.c_size_t, C.c_uint32, _vp],
     "cinr_device_checks": [],
     "cinr_cache_set_decode_ctas": [_vp, C.c_int],
+    "cinr_cache_set_decode_encoder": [_vp, C.c_int],
     "cinr_debug_mma_tile": [_vp, _vp, C.c_int, C.c_int, _vp, _vp],
     "cinr_inr_status": [_vp, _vp],
     "cinr_debug_wait_timeout": [_vp, C.c_uint, _vp],
@@ -322,6 +323,10 @@ class Cache:
     def set_decode_ctas(self, ctas_per_sm):
         """Decode CTAs per SM (0: as many as fit)."""
         check(lib().cinr_cache_set_decode_ctas(self.h, int(ctas_per_sm)), "cinr_cache_set_decode_ctas")
+
+    def set_decode_encoder(self, staged):
+        """Brick decode encoder: 1 staged tile encoder, 0 per-voxel gathers."""
+        check(lib().cinr_cache_set_decode_encoder(self.h, int(staged)), "cinr_cache_set_decode_encoder")
 
     def set_entry(self, what, index, value, stream=None):
         """Writes one u32 page-table entry (tests of the device checks)."""

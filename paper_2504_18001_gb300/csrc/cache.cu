@@ -330,9 +330,9 @@ __host__ __device__ constexpr int dec_mlp_bytes() {
   return (int)(((MLPP ? sizeof(tc::TcSmem<IN, H>) : (size_t)mlp_floats<IN, H>() * 4) + 127) / 128 * 128);
 }
 template <int IN, int H, int MLPP>
-__host__ __device__ constexpr int dec_smem_bytes(int L, int S) {
+__host__ __device__ constexpr int dec_smem_bytes(int L, int S, bool staged) {
   return dec_mlp_bytes<IN, H, MLPP>() +
-         ((S <= kDecMaxS && L <= kDecMaxL) ? dec_tables_bytes(L, S) + (MLPP ? 0 : kDecStageFp32 * 8) : 0);
+         ((!MLPP && staged && S <= kDecMaxS && L <= kDecMaxL) ? dec_tables_bytes(L, S) + kDecStageFp32 * 8 : 0);
 }
 
 template <int IN, int H, int MLPP>
@@ -348,14 +348,18 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
   const uint32_t work = n * tiles_per;
   if (blockIdx.x >= work) return;  // block-uniform, before any barrier
   // the staged encoder's shared memory (bricks up to 16^3 + apron, up to
-  // 24 levels; otherwise every voxel encodes its own point)
-  const bool staged = S <= kDecMaxS && q.L <= kDecMaxL;
-  char* extra = reinterpret_cast<char*>(smem4) + dec_mlp_bytes<IN, H, MLPP>();
+  // 24 levels; otherwise every voxel encodes its own point).  The
+  // tensor-core path keeps the tables and the stage buffer in the
+  // hidden-layer operand buffer, free while a tile encodes; the FP32 path
+  // after its weights.
+  const int tb = (dec_tables_bytes(q.L, S) + 15) / 16 * 16;
+  const bool staged = c.dec_staged && S <= kDecMaxS && q.L <= kDecMaxL &&
+                      (!MLPP || tb + 64 * (int)sizeof(float2) <= (int)sizeof(tcs.a2));
+  char* extra = MLPP ? reinterpret_cast<char*>(tcs.a2) : reinterpret_cast<char*>(smem4) + dec_mlp_bytes<IN, H, MLPP>();
   AxisCell* tab = reinterpret_cast<AxisCell*>(extra);
   LevelBox* box = reinterpret_cast<LevelBox*>(extra + q.L * 3 * S * (int)sizeof(AxisCell));
-  float2* stage = MLPP ? reinterpret_cast<float2*>(tcs.a2)
-                       : reinterpret_cast<float2*>(extra + dec_tables_bytes(q.L, S));
-  const int cap = MLPP ? (int)(sizeof(tcs.a2) / sizeof(float2)) : kDecStageFp32;
+  float2* stage = reinterpret_cast<float2*>(extra + tb);
+  const int cap = MLPP ? ((int)sizeof(tcs.a2) - tb) / (int)sizeof(float2) : kDecStageFp32;
   uint32_t phase = 0;
   if (MLPP) {
     tc::load_tc_weights<IN, H, (MLPP > 0 ? MLPP - 1 : 0)>(tcs, w16, q.w);
@@ -806,7 +810,7 @@ int launch_decode(const cinr_inr_s* inr, const CacheDev& c, const uint32_t* keys
                   const uint32_t* n_dev, uint32_t n_grid, int cap_per_sm, cudaStream_t s) {
   if (n_grid == 0) return CINR_OK;
   auto k = decode_kernel<IN, H, MLPP>;
-  int smem = dec_smem_bytes<IN, H, MLPP>(inr->dev.L, c.S);
+  int smem = dec_smem_bytes<IN, H, MLPP>(inr->dev.L, c.S, c.dec_staged != 0);
   if (MLPP && smem < tc::kMinSmemPerCta) smem = tc::kMinSmemPerCta;  // <= 8 TMEM users per SM
   // residency depends on the shared memory, which depends on the INR's
   // levels and the brick size: recomputed when they change
@@ -929,6 +933,7 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
   d.page_ref = L.page_ref;
   d.page_shift = g.page_shift < 0 ? 0 : g.page_shift;
   d.n_pages = (uint32_t)g.n_pages;
+  d.dec_staged = 1;  // the staged brick encoder (cinr_cache_set_decode_encoder)
   d.n_slots = (uint32_t)ns;
   d.n_bricks = (uint32_t)g.off[g.L];
   d.err = reinterpret_cast<int*>(inr->scratch + 16);  // update kernels report to the INR's status word
@@ -1127,5 +1132,12 @@ extern "C" int cinr_cache_set_decode_ctas(cinr_cache_t c, int ctas_per_sm) {
   if (!c) return set_error(CINR_ERR_ARG, "cache is NULL");
   if (ctas_per_sm < 0 || ctas_per_sm > 8) return set_error(CINR_ERR_ARG, "ctas_per_sm must be in [0, 8]");
   c->decode_ctas = ctas_per_sm;
+  return CINR_OK;
+}
+
+extern "C" int cinr_cache_set_decode_encoder(cinr_cache_t c, int staged) {
+  if (!c) return set_error(CINR_ERR_ARG, "cache is NULL");
+  if (staged != 0 && staged != 1) return set_error(CINR_ERR_ARG, "staged must be 0 or 1");
+  c->dev.dec_staged = staged;
   return CINR_OK;
 }

@@ -149,6 +149,7 @@ struct CacheDev {
   uint32_t n_pages;
   uint32_t n_slots, n_bricks;
   int* err;  // error word of the bounds checks (checked builds)
+  int dec_staged;  // brick decode: 1 staged tile encoder, 0 per-voxel gathers
 };
 
 // Page-table entry of brick (b0, b1, b2) at LoD lev (key = its flat key):

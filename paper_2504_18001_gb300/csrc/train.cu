@@ -290,21 +290,25 @@ struct WgSmem {
   uint32_t tmem;
 };
 
-// Row r, samples base .. base+31 (zero past s1) of src (null: zeros), split
-// and stored as 8 core-matrix rows of 16 bytes (hi and lo parts).
-__device__ __forceinline__ void wg_stage_row(unsigned char* hi, unsigned char* lo, int r, int c,
-                                             const float* src, long base, long s1) {
-  float v[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const long s = base + c * 4 + u;
-    v[u] = (src && s < s1) ? src[s] : 0.0f;
-  }
+// Four consecutive samples of row src (null: zeros) starting at sample s,
+// zero past s1: one 16-byte load when the rows are 16-byte aligned (n a
+// multiple of 4; s and s1 then are too), else four scalar loads.
+__device__ __forceinline__ float4 wg_load4(const float* src, long s, long s1, bool vec) {
+  if (!src || s >= s1) return make_float4(0.f, 0.f, 0.f, 0.f);
+  if (vec) return __ldg(reinterpret_cast<const float4*>(src + s));
+  return make_float4(__ldg(src + s), s + 1 < s1 ? __ldg(src + s + 1) : 0.f,
+                     s + 2 < s1 ? __ldg(src + s + 2) : 0.f, s + 3 < s1 ? __ldg(src + s + 3) : 0.f);
+}
+
+// Splits four samples into TF32 parts and stores them as one 16-byte row of
+// a core matrix (row r, bytes 16c .. 16c+15 of the 128-byte K extent).
+__device__ __forceinline__ void wg_store4(unsigned char* hi, unsigned char* lo, int r, int c, float4 v) {
+  const float x[4] = {v.x, v.y, v.z, v.w};
   uint32_t h[4], l[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    h[u] = __float_as_uint(v[u]) & 0xFFFFE000u;
-    l[u] = __float_as_uint(v[u] - __uint_as_float(h[u]));
+    h[u] = __float_as_uint(x[u]) & 0xFFFFE000u;
+    l[u] = __float_as_uint(x[u] - __uint_as_float(h[u]));
   }
   const uint32_t off = tc::core_off_b(r, c * 16, 128);
   *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -340,16 +344,42 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(const float* __restrict__
   uint32_t phase = 0;
   bool ok = true;
   uint32_t acc = 0;
+  // each thread stages JA chunks of A and JB of B (a chunk: one row, four
+  // samples); the next tile's chunks are loaded into registers while the
+  // tensor core works on the current tile
+  constexpr int JA = 8, JB = (N * 8 + 127) / 128;
+  const bool vec = (n & 3) == 0;
+  const float* srcA[JA];
+  const float* srcB[JB];
+#pragma unroll
+  for (int i = 0; i < JA; ++i) {
+    const int r = (t + i * 128) >> 3;
+    srcA[i] = r < H ? a_dh2 + (size_t)r * n : (r < 2 * H ? a_dh1 + (size_t)(r - H) * n : nullptr);
+  }
+#pragma unroll
+  for (int i = 0; i < JB; ++i) {
+    const int e = t + i * 128, r = e >> 3;
+    srcB[i] = (e < N * 8 && r < H) ? a_h1 + (size_t)r * n
+                                  : ((e < N * 8 && r < H + IN) ? a_feat + (size_t)(r - H) * n : nullptr);
+  }
+  float4 va[JA], vb[JB];
+  auto fetch = [&](long base) {
+#pragma unroll
+    for (int i = 0; i < JA; ++i) va[i] = wg_load4(srcA[i], base + ((t + i * 128) & 7) * 4, s1, vec);
+#pragma unroll
+    for (int i = 0; i < JB; ++i) vb[i] = wg_load4(srcB[i], base + ((t + i * 128) & 7) * 4, s1, vec);
+  };
+  fetch(s0);
   for (long base = s0; base < s1; base += 32) {
-    for (int e = t; e < 128 * 8; e += 128) {
-      const int r = e >> 3, c = e & 7;
-      const float* src = r < H ? a_dh2 + (size_t)r * n : (r < 2 * H ? a_dh1 + (size_t)(r - H) * n : nullptr);
-      wg_stage_row(sm.a_hi, sm.a_lo, r, c, src, base, s1);
+#pragma unroll
+    for (int i = 0; i < JA; ++i) {
+      const int e = t + i * 128;
+      wg_store4(sm.a_hi, sm.a_lo, e >> 3, e & 7, va[i]);
     }
-    for (int e = t; e < N * 8; e += 128) {
-      const int r = e >> 3, c = e & 7;
-      const float* src = r < H ? a_h1 + (size_t)r * n : (r < H + IN ? a_feat + (size_t)(r - H) * n : nullptr);
-      wg_stage_row(sm.b_hi, sm.b_lo, r, c, src, base, s1);
+#pragma unroll
+    for (int i = 0; i < JB; ++i) {
+      const int e = t + i * 128;
+      if (e < N * 8) wg_store4(sm.b_hi, sm.b_lo, e >> 3, e & 7, vb[i]);
     }
     tc::fence_proxy_async();
     __syncthreads();
@@ -368,6 +398,7 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(const float* __restrict__
       tc::commit(&sm.bar);
     }
     acc = 1u;
+    if (base + 32 < s1) fetch(base + 32);  // in flight during the products
     ok = tc::mbar_wait(&sm.bar, phase) && ok;  // the operands may be restaged after this
     phase ^= 1u;
     tc::fence_after();

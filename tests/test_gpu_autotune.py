@@ -24,9 +24,10 @@ def test_tuner_picks_the_fastest_setting_above_the_psnr_floor():
     tf = S.tf_ramps(2)
     best, trials = autotune.tune(
         inr_c, inr32, vol, lambda f: (S.orbit_camera(f, W, H), tf), W, H, bricks=(8, 16),
-        n_reqs=(64, 512), layouts=(0,), graphs=(0, 1), decode_ctas=(0, 2), levels=3, pool_mib=64,
+        n_reqs=(64, 512), layouts=(0,), graphs=(0, 1), decode_ctas=(0, 2), decode_encoders=(1, 0),
+        levels=3, pool_mib=64,
         max_warmup=60, timed=3, min_psnr=30.0)
-    assert len(trials) == 2 * 2 * 2 * 2
+    assert len(trials) == 2 * 2 * 2 * 2 * 2
     ok = [t for t in trials if t["psnr_db"] >= 30.0]
     assert ok, trials
     fastest = min(ok, key=lambda t: t["ms_per_frame"])

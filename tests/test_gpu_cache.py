@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_req=40, ranking=1,
          preload=1, lod_scale=1.0, lod_mode=0, storage="fp32", K=32, eps=0.0, check_pixels=2e-3,
          cam_fn=None, mlp="fp32", tab="fp32", ray_layout=0, step_mode=0, step_lod_max=0,
-         use_graph=0, tf=None, macro_cell=0, lag=1, page=0, n_pages=0):
+         use_graph=0, tf=None, macro_cell=0, lag=1, page=0, n_pages=0, decode_encoder=1):
     from paper_2504_18001_gb300 import cinr
     cfg = S.INR_64
     table, w = scene(cfg)
@@ -26,6 +26,7 @@ def _run(frames, vol=(64, 64, 64), W=64, H=48, brick=8, levels=3, slots=160, n_r
                        brick=brick, levels=levels, n_req=n_req, ranking=ranking, preload=preload,
                        storage=storage, lag=lag, page=page, n_pages=n_pages)
     assert cache.n_slots == slots
+    cache.set_decode_encoder(decode_encoder)
     mo = O.march_opts(K=K, eps_T=eps, lod_mode=lod_mode, lod_scale=lod_scale, seed=11,
                       step_mode=step_mode, step_lod_max=step_lod_max)
     oc = O.Cache(p, table, w, vol, brick, levels, slots, mo, n_req=n_req, ranking=ranking,
@@ -123,13 +124,18 @@ def test_cached_fp16_storage_error():
     assert worst < 2e-2, worst
 
 
-def test_decoded_bricks_equal_oracle_bricks():
+@pytest.mark.parametrize("encoder", [1, 0], ids=["staged", "gathers"])
+@pytest.mark.parametrize("brick", [8, 16])
+def test_decoded_bricks_equal_oracle_bricks(encoder, brick):
+    # both hash-grid encoders of the brick decode (staged tile encoder,
+    # per-voxel gathers), bricks of 8^3 and 16^3 (+ apron)
     from paper_2504_18001_gb300 import cinr
-    cache, oc, hist, worst = _run(3, slots=300, n_req=80)
+    cache, oc, hist, worst = _run(3, slots=300 if brick == 8 else 120, n_req=80, brick=brick,
+                                  decode_encoder=encoder)
     pool = cache.dump(cinr.DUMP_POOL).reshape(cache.n_slots, -1)
     own = cache.dump(cinr.DUMP_OWNERS)
     used = np.nonzero(own != 0xFFFFFFFF)[0]
-    assert len(used) > 50
+    assert len(used) > (50 if brick == 8 else 20)
     for s in used[:: max(1, len(used) // 40)]:
         assert np.abs(pool[s] - oc.slot_values(int(s))).max() < 1e-4
 
