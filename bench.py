@@ -238,7 +238,7 @@ def run_gpu(args, wl):
     device = f"cuda:{local}"
     W, H = wl["W"], wl["H"]
     cfg, table, w, inr32, inr_c, vol = build_scene(args, wl, device)
-    storage = "fp16" if args.precision == "mixed" else "fp32"
+    storage = ("fp16tex" if args.tex else "fp16") if args.precision == "mixed" else "fp32"
     tuned = None
     if args.autotune:
         from paper_2504_18001_gb300 import autotune
@@ -452,7 +452,8 @@ def run_gpu(args, wl):
         "dtype": "bf16" if prec == "mixed" else "f32",
         "data": "synthetic (seeded INR, seeded camera path, seeded TF ramps)",
         "config": {"workload": wl["name"].format(prec=prec), "volume": list(vol),
-                   "cached_path": ("FP16 table + FP16 bricks + BF16 tensor-core MLP (FP32 accumulate)"
+                   "cached_path": ("FP16 table + FP16 bricks%s + BF16 tensor-core MLP (FP32 accumulate)"
+                                   % (" (texture layout, hardware bilinear)" if args.tex else "")
                                    if prec == "mixed" else "FP32"),
                    "uncached_path": "FP32 table + FP32 SIMT MLP",
                    "image": [W, H], "inr": f"L{cfg.levels} F{cfg.feats} T2^{cfg.log2_table} "
@@ -901,6 +902,8 @@ def main():
     ap.add_argument("--fill", type=int, default=None,
                     help="cache-fill frames before the warm-up frames (workload default)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
+    ap.add_argument("--tex", action="store_true",
+                    help="FP16 bricks in the texture layout, sampled by the texture units")
     ap.add_argument("--decode-encoder", type=int, default=1, choices=[0, 1],
                     help="brick decode encoder: 1 staged tile encoder, 0 per-voxel gathers")
     ap.add_argument("--no-other", action="store_true",

@@ -52,6 +52,17 @@ typedef void* cinr_stream_t;
 #define CINR_PREC_FP16 1
 #define CINR_PREC_BF16 2
 #define CINR_PREC_FP8 3 /* MLP only: E4M3 operands, FP32 accumulation (trial) */
+/* Cache storage only: FP16 bricks laid out as z-slices in a pitched 2D
+ * image (a power-of-two number of slice blocks per row, at most 16384
+ * texels wide, at most 65000 rows), sampled by the texture units: the
+ * specialised marching kernel (fixed steps, footprint LoD, flat page
+ * tables, no macro cells, preloaded coarsest LoD, bricks of 8^3 or 16^3,
+ * one ray per thread) reads a sample as two hardware-bilinear fetches and
+ * one z-lerp.  The hardware's bilinear weights carry 8 fractional bits, so
+ * values differ from the FP16 layout's FP32 trilinear by up to 2^-9 of the
+ * neighbouring voxels' difference.  Other kernels reject such a cache
+ * (CINR_ERR_UNSUPPORTED); a pool beyond the row limit is CINR_ERR_ARG. */
+#define CINR_PREC_FP16_TEX 4
 
 /* INR hyper-parameters: a multiresolution hash-grid encoder (m levels, n
  * features per level, a table of 2^log2_table entries per level) feeding a

@@ -20,7 +20,7 @@ _lib = None
 
 CINR_OK = 0
 ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_CHECK, ERR_UNSUPPORTED, ERR_NAN = range(-1, -8, -1)
-PREC = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3}
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3, "fp16tex": 4}  # fp16tex: cache storage only
 DUMP_PAGE_TABLE, DUMP_STAMPS, DUMP_OWNERS, DUMP_RANK, DUMP_REQUESTS, DUMP_VICTIMS, \
     DUMP_MISSES, DUMP_PINNED, DUMP_POOL, DUMP_PAGE_DIR, DUMP_PAGES, DUMP_PAGE_KEYS, \
     DUMP_PAGE_REFS = range(13)
@@ -334,7 +334,7 @@ class Cache:
                                          _stream(stream)), "cinr_debug_set_entry")
 
     def dump(self, what, stream=None):
-        return debug_dump(self.h, what, stream, pool_half=self.opts.storage_precision == 1)
+        return debug_dump(self.h, what, stream, pool_half=self.opts.storage_precision in (1, 4))
 
     def __del__(self):
         try:

@@ -49,8 +49,9 @@ int geometry(const int vol[3], const cinr_cache_opts* o, Geometry* g) {
   if (vol[0] < 1 || vol[1] < 1 || vol[2] < 1) return set_error(CINR_ERR_ARG, "bad volume dims");
   if (o->n_req < 1 || o->n_req > kMaxReq)
     return set_error(CINR_ERR_ARG, "n_req must be in [1, %d]", kMaxReq);
-  if (o->storage_precision != CINR_PREC_FP32 && o->storage_precision != CINR_PREC_FP16)
-    return set_error(CINR_ERR_ARG, "storage_precision must be FP32 or FP16");
+  if (o->storage_precision != CINR_PREC_FP32 && o->storage_precision != CINR_PREC_FP16 &&
+      o->storage_precision != CINR_PREC_FP16_TEX)
+    return set_error(CINR_ERR_ARG, "storage_precision must be FP32, FP16 or FP16_TEX");
   if (o->lag < 0 || o->lag > 2) return set_error(CINR_ERR_ARG, "lag must be 1 or 2 (0 means 1)");
   g->page_shift = -1;
   g->n_pages = 0;
@@ -86,6 +87,32 @@ int geometry(const int vol[3], const cinr_cache_opts* o, Geometry* g) {
   return CINR_OK;
 }
 
+// Texture layout of an FP16 pool (CINR_PREC_FP16_TEX): 2^shift slice blocks
+// of S x S texels per row (the widest power of two with 2^shift S <= 16384
+// texels: coordinates below 2^14 keep 10 fractional bits in binary32),
+// rows of `pitch` texels (a multiple of 64: 128-byte rows), at most 65000
+// texel rows (the limit of a pitched 2D texture).
+constexpr int kTexMaxWidth = 16384, kTexMaxRows = 65000;
+struct TexGeo {
+  int shift, pitch;
+};
+TexGeo tex_geo(int S) {
+  TexGeo t{0, 0};
+  while ((2 << t.shift) * S <= kTexMaxWidth) ++t.shift;
+  t.pitch = (int)align_up((size_t)((1 << t.shift) * S), 64);
+  return t;
+}
+int elem_bytes(int prec) { return prec == CINR_PREC_FP32 ? 4 : 2; }
+
+size_t pool_bytes_for(const Geometry& g, long n_slots, int prec) {
+  const size_t S3 = (size_t)g.S * g.S * g.S;
+  if (prec != CINR_PREC_FP16_TEX) return (size_t)n_slots * S3 * elem_bytes(prec);
+  const TexGeo t = tex_geo(g.S);
+  const size_t blocks = (size_t)n_slots * g.S, per_row = (size_t)1 << t.shift;
+  const size_t block_rows = (blocks + per_row - 1) / per_row;
+  return block_rows * g.S * (size_t)t.pitch * 2;
+}
+
 CacheLayout layout(const Geometry& g, long n_slots, int prec, void* base) {
   Carver c(base);
   CacheLayout L;
@@ -111,14 +138,20 @@ CacheLayout layout(const Geometry& g, long n_slots, int prec, void* base) {
   L.vic_vals = c.take<uint32_t>(kMaxReq);
   L.vic_sorted = c.take<uint32_t>(kMaxReq);
   size_t S3 = (size_t)g.S * g.S * g.S;
-  L.pool = c.take<char>((size_t)n_slots * S3 * (prec == CINR_PREC_FP16 ? 2 : 4));
+  (void)S3;
+  // 1024-byte aligned (a texture's base must be 512-byte aligned)
+  L.pool = c.take<char>(pool_bytes_for(g, n_slots, prec), 1024);
   L.bytes = align_up(c.off, 256);
   return L;
 }
 
 long slots_for(const Geometry& g, size_t pool_bytes, int prec) {
   size_t S3 = (size_t)g.S * g.S * g.S;
-  return (long)(pool_bytes / (S3 * (prec == CINR_PREC_FP16 ? 2 : 4)));
+  if (prec != CINR_PREC_FP16_TEX) return (long)(pool_bytes / (S3 * elem_bytes(prec)));
+  const TexGeo t = tex_geo(g.S);
+  size_t block_rows = pool_bytes / ((size_t)t.pitch * 2 * g.S);
+  if (block_rows > (size_t)(kTexMaxRows / g.S)) block_rows = (size_t)(kTexMaxRows / g.S);
+  return (long)(block_rows * ((size_t)1 << t.shift) / g.S);
 }
 
 // ------------------------------------------------------------ kernels
@@ -406,7 +439,8 @@ __global__ void __launch_bounds__(128) decode_kernel(InrDev q, CacheDev c, const
       y = tc::mlp_tile<IN, H, (MLPP > 0 ? MLPP - 1 : 0)>(tcs, feat, valid, phase, err);
     if (valid && in_pool) {
       const float val = fmaf(q.vscale, y, q.vmin);
-      const size_t o = (size_t)slot * S3 + v;
+      const size_t o = c.pool_tex ? tex_offset(S, c.tex_shift, c.tex_pitch, slot, lv[0], lv[1], lv[2])
+                                  : (size_t)slot * S3 + v;
       if (c.pool_prec == CINR_PREC_FP16)
         reinterpret_cast<__half*>(c.pool)[o] = __float2half_rn(val);
       else
@@ -914,7 +948,11 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
   d.owner = L.owner;
   d.pinned = L.pinned;
   d.pool = L.pool;
-  d.pool_prec = o->storage_precision;
+  d.pool_prec = o->storage_precision == CINR_PREC_FP32 ? CINR_PREC_FP32 : CINR_PREC_FP16;
+  d.pool_tex = o->storage_precision == CINR_PREC_FP16_TEX;
+  d.tex_shift = 0;
+  d.tex_pitch = 0;
+  d.tex = 0;
   d.B = g.B;
   d.invB = (g.B & (g.B - 1)) == 0 ? 1.0f / (float)g.B : 0.0f;
   d.S = g.S;
@@ -956,6 +994,33 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
 
   // device initialisation; on any failure the handle is released
   auto init = [&]() -> int {
+    if (d.pool_tex) {
+      // the pool as a pitched 2D FP16 texture, bilinear filtering,
+      // unnormalised coordinates (a descriptor over the caller's memory)
+      if (reinterpret_cast<uintptr_t>(L.pool) & 511)
+        return set_error(CINR_ERR_ARG, "the texture layout needs dev_mem 512-byte aligned");
+      const TexGeo t = tex_geo(g.S);
+      d.tex_shift = t.shift;
+      d.tex_pitch = t.pitch;
+      cudaResourceDesc rd;
+      memset(&rd, 0, sizeof(rd));
+      rd.resType = cudaResourceTypePitch2D;
+      rd.res.pitch2D.devPtr = L.pool;
+      rd.res.pitch2D.desc = cudaCreateChannelDescHalf();
+      rd.res.pitch2D.width = (size_t)t.pitch;
+      rd.res.pitch2D.height = pool_bytes_for(g, ns, CINR_PREC_FP16_TEX) / ((size_t)t.pitch * 2);
+      rd.res.pitch2D.pitchInBytes = (size_t)t.pitch * 2;
+      cudaTextureDesc td;
+      memset(&td, 0, sizeof(td));
+      td.addressMode[0] = cudaAddressModeClamp;
+      td.addressMode[1] = cudaAddressModeClamp;
+      td.filterMode = cudaFilterModeLinear;
+      td.readMode = cudaReadModeElementType;
+      td.normalizedCoords = 0;
+      cudaTextureObject_t to = 0;
+      CINR_CK(cudaCreateTextureObject(&to, &rd, &td, nullptr));
+      d.tex = (unsigned long long)to;
+    }
     size_t nb = (size_t)c->n_bricks;
     if (g.page_shift >= 0) {
       CINR_CK(cudaMemsetAsync(L.pd, 0, (size_t)g.pd_off[g.L] * 4, s));
@@ -1000,6 +1065,7 @@ extern "C" int cinr_create_cache(cinr_inr_t inr, const int dims[3], void* dev_me
 }
 
 extern "C" int cinr_destroy_cache(cinr_cache_t cache) {
+  if (cache && cache->dev.tex) cudaDestroyTextureObject((cudaTextureObject_t)cache->dev.tex);
   if (cache && cache->dstream) {
     cudaStreamSynchronize(cache->dstream);
     if (cache->e_sel) cudaEventDestroy(cache->e_sel);

@@ -78,8 +78,8 @@ struct Carver {
   size_t off = 0;
   explicit Carver(void* b) : base(static_cast<char*>(b)) {}
   template <typename T>
-  T* take(size_t count) {
-    off = align_up(off, 256);
+  T* take(size_t count, size_t align = 256) {
+    off = align_up(off, align);
     T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
     off += sizeof(T) * count;
     return p;
@@ -150,7 +150,22 @@ struct CacheDev {
   uint32_t n_slots, n_bricks;
   int* err;  // error word of the bounds checks (checked builds)
   int dec_staged;  // brick decode: 1 staged tile encoder, 0 per-voxel gathers
+  // texture layout of an FP16 pool (pool_tex != 0): slice z of slot s is
+  // block b = s S + z at texels (x + S (b & (2^tex_shift - 1)),
+  // y + S (b >> tex_shift)) of a 2D image with tex_pitch texels per row
+  int pool_tex;
+  int tex_shift;
+  int tex_pitch;
+  unsigned long long tex;  // cudaTextureObject_t over the pool
 };
+
+// Offset of voxel (x, y, z) of slot s in a pool in the texture layout.
+__host__ __device__ __forceinline__ size_t tex_offset(int S, int shift, int pitch, uint32_t s, int x, int y,
+                                                      int z) {
+  const uint32_t b = s * (uint32_t)S + (uint32_t)z;
+  const uint32_t bc = b & ((1u << shift) - 1u), br = b >> shift;
+  return ((size_t)br * S + y) * (size_t)pitch + (size_t)bc * S + x;
+}
 
 // Page-table entry of brick (b0, b1, b2) at LoD lev (key = its flat key):
 // the flat table, or the entry in its page when the page is resident.

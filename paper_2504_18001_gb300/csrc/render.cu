@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "cinr_internal.cuh"
 #include "tc_mlp.cuh"
@@ -697,7 +698,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
 // fallback walks, requests, first stamps of a slot, ray ends -- behind
 // warp-uniform votes, so that the warp issues no divergent branches on
 // its common path (all lanes of a warp march the same sample index k).
-template <bool F16POOL, int BB>
+template <bool F16POOL, int BB, bool TEX = false>
 __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __grid_constant__ FrameParams P) {
   static_assert(BB > 0 && (BB & (BB - 1)) == 0, "brick size must be a power of two");
   __shared__ float4 s_tf[256];
@@ -830,20 +831,37 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
       const float q2 = fminf(fmaxf(f_sub(s2, 0.5f), 0.0f), g.dmax2);
       const int i0 = (int)q0, i1 = (int)q1, i2 = (int)q2;
       const float f0 = f_sub(q0, (float)i0), f1 = f_sub(q1, (float)i1), f2 = f_sub(q2, (float)i2);
-      int o = ((i2 - b2 * B + 1) * S + (i1 - b1 * B + 1)) * S + (i0 - b0 * B + 1);
-      if (!in_range((uint32_t)o, S3 - SS - S - 1, c.err)) o = 0;
-      const void* bp = static_cast<const char*>(pool) + (size_t)hit_slot * S3 * (F16POOL ? 2u : 4u);
-      const float v000 = pool_ld<F16POOL>(bp, o), v100 = pool_ld<F16POOL>(bp, o + 1);
-      const float v010 = pool_ld<F16POOL>(bp, o + S), v110 = pool_ld<F16POOL>(bp, o + S + 1);
-      const float v001 = pool_ld<F16POOL>(bp, o + SS), v101 = pool_ld<F16POOL>(bp, o + SS + 1);
-      const float v011 = pool_ld<F16POOL>(bp, o + SS + S), v111 = pool_ld<F16POOL>(bp, o + SS + S + 1);
-      const float2 a0 = make_float2(v000, v001), a1 = make_float2(v100, v101);
-      const float2 c0 = make_float2(v010, v011), c1 = make_float2(v110, v111);
-      const float2 ff0 = make_float2(f0, f0);
-      const float2 X0 = f2_fma(ff0, f2_sub(a1, a0), a0);
-      const float2 X1 = f2_fma(ff0, f2_sub(c1, c0), c0);
-      const float2 Y = f2_fma(make_float2(f1, f1), f2_sub(X1, X0), X0);
-      const float v = (e & kMapped) ? fmaf(f2, Y.y - Y.x, Y.x) : 0.0f;
+      float vt;
+      if (TEX) {
+        // two bilinear fetches by the texture units (slices z and z + 1 of
+        // the slot, blocks b and b + 1 of the 2D layout) and the z-lerp; a
+        // fetch is clamped to the image, so any coordinate is safe
+        const int lx = i0 - b0 * B + 1, ly = i1 - b1 * B + 1, lz = i2 - b2 * B + 1;
+        const uint32_t blk = hit_slot * (uint32_t)S + (uint32_t)lz, m = (1u << c.tex_shift) - 1u;
+        const float x0 = (float)((int)(blk & m) * S + lx) + f0 + 0.5f;
+        const float y0 = (float)((int)(blk >> c.tex_shift) * S + ly) + f1 + 0.5f;
+        const float x1 = (float)((int)((blk + 1u) & m) * S + lx) + f0 + 0.5f;
+        const float y1 = (float)((int)((blk + 1u) >> c.tex_shift) * S + ly) + f1 + 0.5f;
+        const float t0 = tex2D<float>((cudaTextureObject_t)c.tex, x0, y0);
+        const float t1 = tex2D<float>((cudaTextureObject_t)c.tex, x1, y1);
+        vt = fmaf(f2, t1 - t0, t0);
+      } else {
+        int o = ((i2 - b2 * B + 1) * S + (i1 - b1 * B + 1)) * S + (i0 - b0 * B + 1);
+        if (!in_range((uint32_t)o, S3 - SS - S - 1, c.err)) o = 0;
+        const void* bp = static_cast<const char*>(pool) + (size_t)hit_slot * S3 * (F16POOL ? 2u : 4u);
+        const float v000 = pool_ld<F16POOL>(bp, o), v100 = pool_ld<F16POOL>(bp, o + 1);
+        const float v010 = pool_ld<F16POOL>(bp, o + S), v110 = pool_ld<F16POOL>(bp, o + S + 1);
+        const float v001 = pool_ld<F16POOL>(bp, o + SS), v101 = pool_ld<F16POOL>(bp, o + SS + 1);
+        const float v011 = pool_ld<F16POOL>(bp, o + SS + S), v111 = pool_ld<F16POOL>(bp, o + SS + S + 1);
+        const float2 a0 = make_float2(v000, v001), a1 = make_float2(v100, v101);
+        const float2 c0 = make_float2(v010, v011), c1 = make_float2(v110, v111);
+        const float2 ff0 = make_float2(f0, f0);
+        const float2 X0 = f2_fma(ff0, f2_sub(a1, a0), a0);
+        const float2 X1 = f2_fma(ff0, f2_sub(c1, c0), c0);
+        const float2 Y = f2_fma(make_float2(f1, f1), f2_sub(X1, X0), X0);
+        vt = fmaf(f2, Y.y - Y.x, Y.x);
+      }
+      const float v = (e & kMapped) ? vt : 0.0f;
       // LRU stamp: once per slot and frame (the first exchange counts it)
       const bool changed = active && (e & kMapped) && hit_slot != stamped;
       if (__any_sync(kFull, changed)) {
@@ -899,9 +917,9 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
   }
 }
 
-template <bool F16POOL, int BB>
+template <bool F16POOL, int BB, bool TEX = false>
 int launch_march_fast(const FrameParams& P, cudaStream_t s) {
-  auto k = march_fast_kernel<F16POOL, BB>;
+  auto k = march_fast_kernel<F16POOL, BB, TEX>;
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
@@ -930,6 +948,13 @@ int launch_march_cached(const FrameParams& P, cudaStream_t s) {
 template <bool F16POOL>
 int launch_march_cached_pool(const FrameParams& P, bool miss, cudaStream_t s) {
   const bool common = !miss && P.cam.step_mode == 0 && P.cam.lod_mode == 0 && !P.cache.pd && !P.mac.skip;
+  if (P.cache.pool_tex) {  // FP16 bricks in the texture layout: the specialised kernel only
+    if (F16POOL && common && P.cache.B == 8) return launch_march_fast<true, 8, true>(P, s);
+    if (F16POOL && common && P.cache.B == 16) return launch_march_fast<true, 16, true>(P, s);
+    return set_error(CINR_ERR_UNSUPPORTED,
+                     "the texture layout serves fixed steps, footprint LoD, flat tables, no macro cells, "
+                     "a preloaded coarsest LoD and bricks of 8 or 16 only");
+  }
   if (common && P.cache.B == 8) return launch_march_fast<F16POOL, 8>(P, s);
   if (common && P.cache.B == 16) return launch_march_fast<F16POOL, 16>(P, s);
   if (!miss) {
@@ -1646,6 +1671,8 @@ int render(cinr_renderer_t r, cinr_cache_t cache, cinr_inr_t inr, const cinr_cam
     if (cache->inr != inr) return set_error(CINR_ERR_ARG, "cache was built for another INR");
     if (cache->o.lag == 2 && r->o.use_graph)
       return set_error(CINR_ERR_ARG, "a lag-2 cache decodes across frames and cannot run as a per-frame graph");
+    if (cache->dev.pool_tex && (pt || r->o.ray_layout == 1))
+      return set_error(CINR_ERR_UNSUPPORTED, "the texture layout serves the thread-per-ray marching kernel only");
   }
   FrameParams P;
   memset(&P, 0, sizeof(P));
@@ -1914,6 +1941,27 @@ extern "C" int cinr_debug_dump(void* obj, int what, void* host_out, size_t cap, 
         src = c->dev.pool;
         n = (size_t)c->n_slots * c->dev.S * c->dev.S * c->dev.S;
         esz = c->dev.pool_prec == CINR_PREC_FP16 ? 2 : 4;
+        if (c->dev.pool_tex) {
+          // the texture layout, copied whole and returned in slot order
+          // (slot, z, y, x), x fastest, as the linear layout stores it
+          const int S = c->dev.S;
+          const size_t per_row = (size_t)1 << c->dev.tex_shift;
+          const size_t rows = ((size_t)c->n_slots * S + per_row - 1) / per_row * S;
+          std::vector<uint16_t> img(rows * (size_t)c->dev.tex_pitch);
+          CINR_CK(cudaMemcpyAsync(img.data(), src, img.size() * 2, cudaMemcpyDeviceToHost, s));
+          CINR_CK(cudaStreamSynchronize(s));
+          *count = n;
+          uint16_t* dst = static_cast<uint16_t*>(host_out);
+          const size_t m = n < cap ? n : cap;
+          if (dst)
+            for (size_t i = 0; i < m; ++i) {
+              const size_t S3 = (size_t)S * S * S;
+              const uint32_t slot = (uint32_t)(i / S3);
+              const int v = (int)(i % S3);
+              dst[i] = img[tex_offset(S, c->dev.tex_shift, c->dev.tex_pitch, slot, v % S, (v / S) % S, v / (S * S))];
+            }
+          return CINR_OK;
+        }
         break;
       default: return set_error(CINR_ERR_ARG, "unknown dump %d", what);
     }

@@ -160,20 +160,6 @@ __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t adesc, uint64_t bde
   }
 }
 
-// D (+)= A B^T with TF32 operands (FP32 bit patterns in shared memory, the
-// tensor core reading their top 19 bits) and an FP32 accumulator: 8 K
-// elements (32 bytes) per instruction, the same core-matrix layout as the
-// 16-bit kinds; the instruction descriptor's A/B format is 2 (TF32).
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
 __device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                         uint32_t accumulate) {
   mma<0>(dtmem, adesc, bdesc, idesc, accumulate);

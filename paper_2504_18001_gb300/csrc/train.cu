@@ -19,7 +19,6 @@
 #include <vector>
 
 #include "cinr_internal.cuh"
-#include "tc_mlp.cuh"
 
 using namespace cinr;
 
@@ -38,9 +37,8 @@ struct cinr_trainer_s {
 namespace {
 
 constexpr int kChunk = 512;      // samples per block in the weight-gradient reduction
-// bits of the trainer's status word
-constexpr int kTrainNan = 1;      // a non-finite gradient (Adam)
-constexpr int kTrainTimeout = 2;  // a bounded tensor-core wait gave up
+// bit of the trainer's status word
+constexpr int kTrainNan = 1;  // a non-finite gradient (Adam)
 constexpr int kFwdThreads = 128;
 
 __device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
@@ -267,166 +265,6 @@ __global__ void __launch_bounds__((M / 4) * (N / 4)) outer_kernel(const float* _
     for (int v = 0; v < 4; ++v) out[(ti + u) * N + tj + v] = acc[u][v];
 }
 
-// Weight gradients of the two hidden layers on the tensor cores:
-// dW2 = sum_s dh2_s h1_s^T and dW1 = sum_s dh1_s feat_s^T over the block's
-// samples, as one product D = A B^T with A = [dh2; dh1] (2H rows, padded to
-// 128) and B = [h1; feat] (H + IN rows, padded to a multiple of 16), K the
-// samples: the diagonal blocks of D are dW2 and dW1.  The activations are
-// feature-major in global memory, so each operand row is a run of
-// consecutive samples (K-major), staged 32 samples at a time into the
-// no-swizzle core-matrix layout.  FP32 operands are split into TF32 parts,
-// x = hi + lo with hi the top 19 bits of x and lo = x - hi (exact), and D
-// accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor memory (the lo*lo
-// term is below 2^-21 of the product): the accuracy of FP32 products.
-// partial1 / partial2 take the block's sums in the layout of outer_kernel.
-template <int IN, int H>
-struct WgSmem {
-  static constexpr int N = ((H + IN + 15) / 16) * 16;  // B rows (MMA N)
-  alignas(1024) unsigned char a_hi[128 * 128];         // 128 rows x 32 FP32
-  alignas(128) unsigned char a_lo[128 * 128];
-  alignas(128) unsigned char b_hi[N * 128];
-  alignas(128) unsigned char b_lo[N * 128];
-  uint64_t bar;
-  uint32_t tmem;
-};
-
-// Four consecutive samples of row src (null: zeros) starting at sample s,
-// zero past s1: one 16-byte load when the rows are 16-byte aligned (n a
-// multiple of 4; s and s1 then are too), else four scalar loads.
-__device__ __forceinline__ float4 wg_load4(const float* src, long s, long s1, bool vec) {
-  if (!src || s >= s1) return make_float4(0.f, 0.f, 0.f, 0.f);
-  if (vec) return __ldg(reinterpret_cast<const float4*>(src + s));
-  return make_float4(__ldg(src + s), s + 1 < s1 ? __ldg(src + s + 1) : 0.f,
-                     s + 2 < s1 ? __ldg(src + s + 2) : 0.f, s + 3 < s1 ? __ldg(src + s + 3) : 0.f);
-}
-
-// Splits four samples into TF32 parts and stores them as one 16-byte row of
-// a core matrix (row r, bytes 16c .. 16c+15 of the 128-byte K extent).
-__device__ __forceinline__ void wg_store4(unsigned char* hi, unsigned char* lo, int r, int c, float4 v) {
-  const float x[4] = {v.x, v.y, v.z, v.w};
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    h[u] = __float_as_uint(x[u]) & 0xFFFFE000u;
-    l[u] = __float_as_uint(x[u] - __uint_as_float(h[u]));
-  }
-  const uint32_t off = tc::core_off_b(r, c * 16, 128);
-  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-template <int IN, int H>
-__global__ void __launch_bounds__(128) wgrad_tc_kernel(const float* __restrict__ a_feat,
-                                                        const float* __restrict__ a_h1,
-                                                        const float* __restrict__ a_dh1,
-                                                        const float* __restrict__ a_dh2, long n,
-                                                        float* __restrict__ partial1,
-                                                        float* __restrict__ partial2, int* err) {
-  using SM = WgSmem<IN, H>;
-  constexpr int N = SM::N;
-  constexpr int kCols = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
-  static_assert(2 * H <= 128 && N <= 256, "shape");
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  SM& sm = *reinterpret_cast<SM*>(smraw);
-  const int t = threadIdx.x, warp = t >> 5;
-  if (t == 0) tc::mbar_init(&sm.bar, 1);
-  if (t < 32) tc::tmem_alloc(&sm.tmem, kCols);
-  tc::fence_proxy_async();
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t dt = sm.tmem;
-  const long s0 = (long)blockIdx.x * kChunk;
-  const long s1 = s0 + kChunk < n ? s0 + kChunk : n;
-  // D: M = 128, N, FP32; A and B TF32 (format 2), K-major
-  constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-                             ((uint32_t)(128 >> 4) << 24);
-  uint32_t phase = 0;
-  bool ok = true;
-  uint32_t acc = 0;
-  // each thread stages JA chunks of A and JB of B (a chunk: one row, four
-  // samples); the next tile's chunks are loaded into registers while the
-  // tensor core works on the current tile
-  constexpr int JA = 8, JB = (N * 8 + 127) / 128;
-  const bool vec = (n & 3) == 0;
-  const float* srcA[JA];
-  const float* srcB[JB];
-#pragma unroll
-  for (int i = 0; i < JA; ++i) {
-    const int r = (t + i * 128) >> 3;
-    srcA[i] = r < H ? a_dh2 + (size_t)r * n : (r < 2 * H ? a_dh1 + (size_t)(r - H) * n : nullptr);
-  }
-#pragma unroll
-  for (int i = 0; i < JB; ++i) {
-    const int e = t + i * 128, r = e >> 3;
-    srcB[i] = (e < N * 8 && r < H) ? a_h1 + (size_t)r * n
-                                  : ((e < N * 8 && r < H + IN) ? a_feat + (size_t)(r - H) * n : nullptr);
-  }
-  float4 va[JA], vb[JB];
-  auto fetch = [&](long base) {
-#pragma unroll
-    for (int i = 0; i < JA; ++i) va[i] = wg_load4(srcA[i], base + ((t + i * 128) & 7) * 4, s1, vec);
-#pragma unroll
-    for (int i = 0; i < JB; ++i) vb[i] = wg_load4(srcB[i], base + ((t + i * 128) & 7) * 4, s1, vec);
-  };
-  fetch(s0);
-  for (long base = s0; base < s1; base += 32) {
-#pragma unroll
-    for (int i = 0; i < JA; ++i) {
-      const int e = t + i * 128;
-      wg_store4(sm.a_hi, sm.a_lo, e >> 3, e & 7, va[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < JB; ++i) {
-      const int e = t + i * 128;
-      if (e < N * 8) wg_store4(sm.b_hi, sm.b_lo, e >> 3, e & 7, vb[i]);
-    }
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (t == 0) {
-      tc::fence_after();
-      const uint32_t ah = tc::smem_u32(sm.a_hi), al = tc::smem_u32(sm.a_lo);
-      const uint32_t bh = tc::smem_u32(sm.b_hi), bl = tc::smem_u32(sm.b_lo);
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {  // 8 samples (32 bytes) per instruction
-        const uint32_t o = kk * 256;
-        tc::mma_tf32(dt, tc::sdesc(ah + o, 128, 1024), tc::sdesc(bh + o, 128, 1024), idesc, acc);
-        acc = 1u;
-        tc::mma_tf32(dt, tc::sdesc(ah + o, 128, 1024), tc::sdesc(bl + o, 128, 1024), idesc, 1u);
-        tc::mma_tf32(dt, tc::sdesc(al + o, 128, 1024), tc::sdesc(bh + o, 128, 1024), idesc, 1u);
-      }
-      tc::commit(&sm.bar);
-    }
-    acc = 1u;
-    if (base + 32 < s1) fetch(base + 32);  // in flight during the products
-    ok = tc::mbar_wait(&sm.bar, phase) && ok;  // the operands may be restaged after this
-    phase ^= 1u;
-    tc::fence_after();
-    __syncthreads();
-  }
-  // thread t holds row t of D in tensor-memory lane t
-  const uint32_t lane_addr = dt + ((uint32_t)(warp * 32) << 16);
-  float* p2 = partial2 + (size_t)blockIdx.x * H * H;
-  float* p1 = partial1 + (size_t)blockIdx.x * H * IN;
-#pragma unroll 1
-  for (int c0 = 0; c0 < N; c0 += 16) {
-    float v[16];
-    tc::ld16(lane_addr + c0, v);
-    tc::wait_ld();
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int c = c0 + i;
-      if (t < H && c < H) p2[t * H + c] = v[i];
-      if (t >= H && t < 2 * H && c >= H && c < H + IN) p1[(t - H) * IN + (c - H)] = v[i];
-    }
-  }
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  if (t < 32) tc::tmem_dealloc(dt, kCols);
-  if (!ok && err && t == 0) atomicOr(err, kTrainTimeout);
-}
-
 // partial[blk][j] = sum over the block's samples of a[s] * B[j][s]: each
 // warp takes N/8 of the outputs, its lanes stride over the block's samples
 // (a[s] read once per lane for all of the warp's outputs), then a warp sum.
@@ -598,15 +436,8 @@ int grads(cinr_trainer_s* t, const float* xyz, const float* tgt, long n, const f
   float* p1 = t->partial;
   float* p2 = p1 + (size_t)blocks * H * IN;
   float* p3 = p2 + (size_t)blocks * H * H;
-  // dW1 and dW2 on the tensor cores (TF32 split to FP32 accuracy)
-  auto kw = wgrad_tc_kernel<IN, H>;
-  const int wsmem = (int)sizeof(WgSmem<IN, H>);
-  static int wg_attr = 0;
-  if (!wg_attr) {
-    CINR_CK(cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem));
-    wg_attr = 1;
-  }
-  kw<<<blocks, 128, wsmem, s>>>(a_feat, a_h1, a_dh1, a_dh2, n, p1, p2, reinterpret_cast<int*>(t->loss + 1));
+  outer_kernel<H, IN><<<blocks, (H / 4) * (IN / 4), 0, s>>>(a_dh1, a_feat, n, p1);
+  outer_kernel<H, H><<<blocks, (H / 4) * (H / 4), 0, s>>>(a_dh2, a_h1, n, p2);
   vec_kernel<H><<<blocks, 256, 0, s>>>(a_dy, a_h2, n, p3);
   reduce_kernel<<<(H * IN + 31) / 32, 256, 0, s>>>(p1, blocks, H * IN, g_w);
   reduce_kernel<<<(H * H + 31) / 32, 256, 0, s>>>(p2, blocks, H * H, g_w + H * IN);
@@ -695,7 +526,6 @@ extern "C" int cinr_trainer_status(cinr_trainer_t t, cinr_stream_t stream) {
   CINR_CK(cudaStreamSynchronize(s));
   if (!h) return CINR_OK;
   CINR_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
-  if (h & kTrainTimeout) return set_error(CINR_ERR_TIMEOUT, "a bounded tensor-core wait gave up (weight gradients)");
   return set_error(CINR_ERR_NAN, "a training step produced a non-finite gradient");
 }
 
