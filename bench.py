@@ -723,8 +723,10 @@ def run_reference(args, wl):
 def run_learned(args):
     """Learned INR from scratch: an explicit seeded field (Gaussians + value
     noise) on a dims^3 grid, the L=16 / T=2^20 INR trained by the library's
-    forward/backward/Adam kernels (batch 2^18 counter-based coordinates,
-    lr 1e-2 decayed to 1e-3 over the last fifth), then rendered through the
+    forward/backward/Adam kernels (by default the fused kernel with the MLP's
+    products on the tensor cores, FP16 operands; --train-tc 0 the FP32
+    kernels; batch 2^18 counter-based coordinates, lr 1e-2 decayed to 1e-3
+    over the last fifth), then rendered through the
     FP16 brick cache (FP16 table, BF16 tensor-core MLP) at res^2 and judged
     by PSNR against the explicit-voxel render of the same field; the
     untrained network is judged the same way."""
@@ -741,6 +743,7 @@ def run_learned(args):
     table, w = S.inr_init(cfg, seed=args.seed, table_scale=1e-4)
     inr = cinr.Inr(cinr.make_inr_params(cfg), table, w)
     tr = cinr.Trainer(inr, batch=1 << 18, lr=1e-2, seed=args.seed)
+    tr.set_tensor_cores(args.train_tc)
     for _ in range(3):  # warm-up steps (timed separately)
         tr.step(field)
     torch.cuda.synchronize()
@@ -796,12 +799,16 @@ def run_learned(args):
     return {
         "metric": "PSNR (dB) of the trained INR's cached FP16 render vs the explicit-voxel render",
         "value": psnr_trained, "unit": "dB", "higher_is_better": True, "n_gpus": 1,
-        "dtype": "f32 training; fp16/bf16 render",
+        "dtype": ({1: "fp16", 2: "bf16"}.get(args.train_tc, "") + " tensor-core MLP products, f32 accumulation, "
+                  "loss, scatter and Adam" if args.train_tc else "f32 training") + "; fp16/bf16 render",
         "data": "synthetic (seeded field: 32 Gaussians + 3-octave value noise)",
         "config": {"workload": f"learned_inr_{args.field}cube_{W}px",
                    "inr": "L16 F2 T2^20 Nmin16 b1.38 MLP32-64-64-1", "batch": 1 << 18,
                    "lr": "1e-2, exponential decay to 1e-3 over the last fifth of the steps",
-                   "steps": args.train_steps, "frames": args.learned_frames},
+                   "steps": args.train_steps, "frames": args.learned_frames,
+                   "training_kernels": ("one fused kernel per step, MLP products on the tensor cores (%s)"
+                                        % {1: "FP16, loss scale 256", 2: "BF16"}[args.train_tc]
+                                        if args.train_tc else "FP32 forward, backward and weight-gradient kernels")},
         "psnr_untrained_db": psnr_untrained,
         "train": {"ms_per_step": train_ms / steps,
                   "samples_per_s": steps * (1 << 18) / (train_ms * 1e-3),
@@ -943,6 +950,8 @@ def main():
     ap.add_argument("--field", type=int, default=1024, help="learned: explicit field edge")
     ap.add_argument("--train-steps", type=int, default=5000, help="learned: Adam steps")
     ap.add_argument("--learned-frames", type=int, default=60, help="learned: cached frames")
+    ap.add_argument("--train-tc", type=int, default=1, choices=[0, 1, 2],
+                    help="learned: fused tensor-core training kernel with 1 FP16 / 2 BF16 operands, 0 FP32 kernels")
     args = ap.parse_args()
     if args.workload == "learned":
         res = run_learned(args)

@@ -503,6 +503,22 @@ int cinr_train_step(cinr_trainer_t t, const float* field_dev,
  * caller's: the paper gives none).  Host-side only. */
 int cinr_trainer_set_lr(cinr_trainer_t t, float lr);
 
+/* Chooses the training kernels of the following steps (Sec. 4.1): 0 (the
+ * default) FP32 throughout -- forward, backward and weight-gradient
+ * kernels on the FP32 pipes, gradients within FP32 rounding of the exact
+ * ones --; 1 (FP16) or 2 (BF16) one fused kernel per step in which the
+ * MLP's five products (two forward layers, two backward products through
+ * W2 and W1, and the weight gradients of both hidden layers, accumulated
+ * over the batch) run on the tensor cores (tcgen05) with 16-bit operands
+ * and FP32 accumulation; the output layer, the loss, the table-gradient
+ * scatter and Adam stay FP32.  FP16 operands hold 11 significant bits
+ * (the back-propagated ones carry a fixed loss scale of 256, removed in
+ * FP32), BF16 operands 8, which sets the gradients' error (stated in the
+ * tests).  A bounded tensor-core wait that gives up is reported by
+ * cinr_trainer_status as CINR_ERR_TIMEOUT.  Host-side only.
+ * Errors: CINR_ERR_ARG. */
+int cinr_trainer_set_tensor_cores(cinr_trainer_t t, int mode);
+
 /* Whether any training step since the last call produced a non-finite
  * gradient (a NaN or infinite field value, or a diverged run): CINR_OK or
  * CINR_ERR_NAN (the flag is then cleared).  Synchronises `stream`. */

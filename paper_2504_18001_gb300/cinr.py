@@ -129,6 +129,7 @@ _SIGS = {
     "cinr_destroy_trainer": [_vp],
     "cinr_trainer_status": [_vp, _vp],
     "cinr_trainer_set_lr": [_vp, C.c_float],
+    "cinr_trainer_set_tensor_cores": [_vp, C.c_int],
     "cinr_train": [_vp, _vp, _P(C.c_int), _vp, C.c_long, _vp, C.c_size_t, _vp],
     "cinr_inr_export": [_vp, _vp, _vp, _vp],
     "cinr_debug_dump": [_vp, C.c_int, _vp, C.c_size_t, _P(C.c_size_t), _vp],
@@ -490,9 +491,15 @@ class Trainer:
     def set_lr(self, lr):
         check(lib().cinr_trainer_set_lr(self.h, float(lr)), "cinr_trainer_set_lr")
 
+    def set_tensor_cores(self, mode):
+        """The fused tensor-core forward / backward kernel with 1 FP16 or
+        2 BF16 operands; 0 the FP32 kernels."""
+        check(lib().cinr_trainer_set_tensor_cores(self.h, int(mode)), "cinr_trainer_set_tensor_cores")
+
     def status(self, stream=None):
         """Raises CinrError (CINR_ERR_NAN) when a step since the last check
-        produced a non-finite gradient."""
+        produced a non-finite gradient (CINR_ERR_TIMEOUT: a tensor-core wait
+        of the fused kernel gave up)."""
         check(lib().cinr_trainer_status(self.h, _stream(stream)), "cinr_trainer_status")
 
     def loss_grad(self, xyz, target, stream=None):

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "cinr_internal.cuh"
+#include "tc_mlp.cuh"
 
 using namespace cinr;
 
@@ -32,6 +33,7 @@ struct cinr_trainer_s {
   float* loss;        // device scalar
   long step;
   int n_part;         // blocks of the outer-product reduction
+  int tc;             // fused tensor-core forward / backward (train_tc_kernel): 1 FP16, 2 BF16; 0 FP32 kernels
 };
 
 namespace {
@@ -367,6 +369,323 @@ __global__ void half_copy_kernel(const float* __restrict__ w, uint16_t* __restri
   }
 }
 
+// ------------------------------------------------ fused tensor-core step
+// Forward and backward of a 128-sample tile in one kernel, the MLP's five
+// products on the tensor cores (tcgen05.mma kind::f16, FP16 or BF16
+// operands, FP32 accumulation in tensor memory):
+//   h1 = relu(feat W1^T)          A = features (K-major), B = W1 (K-major)
+//   h2 = relu(h1 W2^T)            A = h1, B = W2
+//   dh1 = (dh2 W2) on h1 > 0      A = dh2 (K-major), B = W2 read MN-major
+//   dfeat = dh1 W1                A = dh1, B = W1 read MN-major
+//   [dW2; dW1] += [dh2; dh1]^T [h1, feat]   A and B read MN-major, K = samples
+// The activations of a tile stay in shared memory, in two buffers of
+// core matrices (8 samples x 16 bytes): HF holds [h1 | feat] and DD holds
+// [dh2 | dh1] (dh2 in columns 0 .. H-1, dh1 in 64 .. 64+H-1, the rest
+// zero), each read as a K-major operand (rows = samples) by the per-sample
+// products and as an MN-major operand (K = samples) by the weight-gradient
+// product, which accumulates over all of the CTA's tiles in tensor memory
+// (its off-diagonal blocks, dh2 feat^T and dh1 h1^T, are not used).  The
+// output layer (H -> 1), the loss and dW3 stay in FP32 per thread; the
+// table gradient is scattered as in bwd_kernel.  The back-propagated
+// operands carry dL/dy as 2 r S (not 2 r / n), S = 256 for FP16 (a fixed
+// power-of-two loss scale that keeps them in FP16's normal range while the
+// residuals shrink; FP16 holds 11 significant bits against BF16's 8) and 1
+// for BF16; 1/(n S) is applied in FP32 to the scattered and the written
+// gradients.
+constexpr int kTcTrainCols = 256;  // TMEM: h / dfeat in 0 .. 63, dW from 128
+constexpr int kTrainTimeout = 2;   // a bounded tensor-core wait gave up
+
+template <int IN, int H>
+struct TrainTcSmem {
+  static constexpr int NG = (H + IN) / 8;            // core-matrix columns of HF
+  alignas(1024) unsigned char hf[128 * (H + IN) * 2];  // [h1 | feat], 128 samples
+  alignas(128) unsigned char dd[128 * 128 * 2];        // [dh2 | 0 | dh1 | 0]
+  alignas(128) unsigned char w1[H * IN * 2];           // W1 [H][IN], K-major
+  alignas(128) unsigned char w2[H * H * 2];            // W2 [H][H], K-major
+  float w3[H];
+  float g3[H];  // dW3 of the CTA
+  uint64_t bar;
+  uint32_t tmem;
+};
+
+// Byte offset of element (r, c) of a K-major BF16 operand whose rows hold
+// `groups` core-matrix columns of 8 elements.
+__device__ __forceinline__ uint32_t cm_off(int r, int c, int groups) {
+  return (uint32_t)((((r >> 3) * groups + (c >> 3)) << 7) + ((r & 7) << 4) + ((c & 7) << 1));
+}
+
+// Two values as an FP16 (FMT 0) or BF16 (FMT 1) pair, lo in the low half;
+// the _relu form clamps negative values to zero.
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
+  uint32_t w;
+  if (FMT == 1)
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+  else
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+  return w;
+}
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  if (FMT == 1) {
+    __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&b);
+  }
+  __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Eight values of row r, columns c0 .. c0+7, as one 16-byte store.
+__device__ __forceinline__ void st8(unsigned char* buf, int r, int c0, int groups, uint32_t a, uint32_t b,
+                                    uint32_t c, uint32_t d) {
+  *reinterpret_cast<uint4*>(buf + cm_off(r, c0, groups)) = make_uint4(a, b, c, d);
+}
+
+template <int IN, int H, int FMT>
+__global__ void __launch_bounds__(128, 2) train_tc_kernel(InrDev q, long n, const float* __restrict__ xyz_in,
+                                                          const float* __restrict__ tgt_in,
+                                                          const float* __restrict__ field, int3 dims, uint64_t seed,
+                                                          uint64_t first, float* __restrict__ g_table,
+                                                          float* __restrict__ p1, float* __restrict__ p2,
+                                                          float* __restrict__ p3, float* __restrict__ loss,
+                                                          int* __restrict__ status) {
+  using SM = TrainTcSmem<IN, H>;
+  constexpr int NG = SM::NG;
+  static_assert(IN % 16 == 0 && H % 16 == 0 && H <= 64 && (H + IN) % 16 == 0, "fused training shape");
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  SM& sm = *reinterpret_cast<SM*>(smraw);
+  const int t = threadIdx.x, warp = t >> 5;
+  constexpr float kScale = FMT == 0 ? 256.0f : 1.0f;  // loss scale of the back-propagated operands
+  const float inv_n = 1.0f / (float)n;
+  const float inv_ns = inv_n * (1.0f / kScale);
+  // weights as 16-bit operands, W3 in FP32; DD's unused columns zero
+  for (int e = t; e < H * IN; e += 128)
+    *reinterpret_cast<uint16_t*>(sm.w1 + cm_off(e / IN, e % IN, IN / 8)) = tc::to16<FMT == 1>(q.w[e]);
+  for (int e = t; e < H * H; e += 128)
+    *reinterpret_cast<uint16_t*>(sm.w2 + cm_off(e / H, e % H, H / 8)) = tc::to16<FMT == 1>(q.w[H * IN + e]);
+  for (int e = t; e < H; e += 128) {
+    sm.w3[e] = q.w[H * IN + H * H + e];
+    sm.g3[e] = 0.0f;
+  }
+  for (int e = t; e < 128 * 16; e += 128)  // 16-byte units of DD
+    reinterpret_cast<uint4*>(sm.dd)[e] = make_uint4(0u, 0u, 0u, 0u);
+  if (t == 0) tc::mbar_init(&sm.bar, 1);
+  if (t < 32) tc::tmem_alloc(&sm.tmem, kTcTrainCols);
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t dh = sm.tmem, dw = sm.tmem + 128u;
+  const uint32_t lane = (uint32_t)(warp * 32) << 16;
+  const uint32_t a_hf = tc::smem_u32(sm.hf), a_dd = tc::smem_u32(sm.dd);
+  const uint32_t a_w1 = tc::smem_u32(sm.w1), a_w2 = tc::smem_u32(sm.w2);
+  constexpr uint32_t fc = tc::Fmt<FMT>::code;
+  constexpr uint32_t id_h = tc::idesc_f16(128, H, fc);
+  constexpr uint32_t id_hT = id_h | (1u << 16);                           // B MN-major
+  constexpr uint32_t id_fT = tc::idesc_f16(128, IN, fc) | (1u << 16);     // B MN-major
+  constexpr uint32_t id_w = tc::idesc_f16(128, H + IN, fc) | (1u << 15) | (1u << 16);  // A, B MN-major
+  uint32_t phase = 0;
+  bool ok = true;
+  float g3[H];
+#pragma unroll
+  for (int o = 0; o < H; ++o) g3[o] = 0.0f;
+  float r2 = 0.0f;
+  auto wait_mma = [&]() {
+    ok = tc::mbar_wait(&sm.bar, phase) && ok;
+    phase ^= 1u;
+    tc::fence_after();
+  };
+  auto sync_for_mma = [&]() {
+    tc::fence_before();
+    tc::fence_proxy_async();
+    __syncthreads();
+  };
+  const long tiles = (n + 127) / 128;
+  uint32_t acc_w = 0;
+  for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const long s = tile * 128 + t;
+    const bool valid = s < n;
+    float x = 0.f, y = 0.f, z = 0.f, target = 0.f;
+    {
+      float feat[IN];
+#pragma unroll
+      for (int k = 0; k < IN; ++k) feat[k] = 0.0f;
+      if (valid) {
+        train_point(xyz_in, seed, first, s, x, y, z);
+        target = tgt_in ? tgt_in[s] : field_trilinear(field, dims, x, y, z);
+        encode_point<IN / 2>(q, x, y, z, feat);
+      }
+#pragma unroll
+      for (int k = 0; k < IN; k += 8)
+        st8(sm.hf, t, H + k, NG, pack2<FMT>(feat[k], feat[k + 1]), pack2<FMT>(feat[k + 2], feat[k + 3]),
+            pack2<FMT>(feat[k + 4], feat[k + 5]), pack2<FMT>(feat[k + 6], feat[k + 7]));
+    }
+    sync_for_mma();
+    if (t == 0) {  // h1 = feat W1^T
+      tc::fence_after();
+#pragma unroll
+      for (int kk = 0; kk < IN / 16; ++kk)
+        tc::mma<FMT>(dh, tc::sdesc(a_hf + (H / 8) * 128 + kk * 256, 128, NG * 128),
+                   tc::sdesc(a_w1 + kk * 256, 128, (IN / 8) * 128), id_h, kk > 0);
+      tc::commit(&sm.bar);
+    }
+    wait_mma();
+    uint64_t m1 = 0;  // h1 > 0
+#pragma unroll
+    for (int c0 = 0; c0 < H; c0 += 16) {
+      float v[16];
+      tc::ld16(dh + lane + c0, v);
+      tc::wait_ld();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) m1 |= (uint64_t)(v[i] > 0.0f) << (c0 + i);
+#pragma unroll
+      for (int h = 0; h < 16; h += 8)
+        st8(sm.hf, t, c0 + h, NG, pack2_relu<FMT>(v[h], v[h + 1]), pack2_relu<FMT>(v[h + 2], v[h + 3]),
+            pack2_relu<FMT>(v[h + 4], v[h + 5]), pack2_relu<FMT>(v[h + 6], v[h + 7]));
+    }
+    sync_for_mma();
+    if (t == 0) {  // h2 = h1 W2^T
+      tc::fence_after();
+#pragma unroll
+      for (int kk = 0; kk < H / 16; ++kk)
+        tc::mma<FMT>(dh, tc::sdesc(a_hf + kk * 256, 128, NG * 128), tc::sdesc(a_w2 + kk * 256, 128, (H / 8) * 128),
+                   id_h, kk > 0);
+      tc::commit(&sm.bar);
+    }
+    wait_mma();
+    {
+      // output layer, loss, dL/dy = 2 r, dW3, dh2 = dy W3 on h2 > 0
+      float h2[H];
+#pragma unroll
+      for (int c0 = 0; c0 < H; c0 += 16) {
+        tc::ld16(dh + lane + c0, h2 + c0);
+        tc::wait_ld();
+      }
+      float yv = 0.0f;
+#pragma unroll
+      for (int o = 0; o < H; ++o) yv = fmaf(sm.w3[o], fmaxf(h2[o], 0.0f), yv);
+      const float r = valid ? yv - target : 0.0f;
+      r2 += r * r;
+      const float dy = 2.0f * r, dys = dy * kScale;
+#pragma unroll
+      for (int o = 0; o < H; ++o) {
+        g3[o] = fmaf(dy, fmaxf(h2[o], 0.0f), g3[o]);
+        h2[o] = h2[o] > 0.0f ? dys * sm.w3[o] : 0.0f;
+      }
+#pragma unroll
+      for (int c0 = 0; c0 < H; c0 += 8)
+        st8(sm.dd, t, c0, 16, pack2<FMT>(h2[c0], h2[c0 + 1]), pack2<FMT>(h2[c0 + 2], h2[c0 + 3]),
+            pack2<FMT>(h2[c0 + 4], h2[c0 + 5]), pack2<FMT>(h2[c0 + 6], h2[c0 + 7]));
+    }
+    sync_for_mma();
+    if (t == 0) {  // dh1 (before the mask) = dh2 W2
+      tc::fence_after();
+#pragma unroll
+      for (int kk = 0; kk < H / 16; ++kk)
+        tc::mma<FMT>(dh, tc::sdesc(a_dd + kk * 256, 128, 16 * 128),
+                   tc::sdesc(a_w2 + kk * 2 * (H / 8) * 128, (H / 8) * 128, 128), id_hT, kk > 0);
+      tc::commit(&sm.bar);
+    }
+    wait_mma();
+#pragma unroll
+    for (int c0 = 0; c0 < H; c0 += 16) {
+      float v[16];
+      tc::ld16(dh + lane + c0, v);
+      tc::wait_ld();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = ((m1 >> (c0 + i)) & 1ull) ? v[i] : 0.0f;
+#pragma unroll
+      for (int h = 0; h < 16; h += 8)
+        st8(sm.dd, t, 64 + c0 + h, 16, pack2<FMT>(v[h], v[h + 1]), pack2<FMT>(v[h + 2], v[h + 3]),
+            pack2<FMT>(v[h + 4], v[h + 5]), pack2<FMT>(v[h + 6], v[h + 7]));
+    }
+    sync_for_mma();
+    if (t == 0) {
+      tc::fence_after();
+      // dfeat = dh1 W1
+#pragma unroll
+      for (int kk = 0; kk < H / 16; ++kk)
+        tc::mma<FMT>(dh, tc::sdesc(a_dd + 8 * 128 + kk * 256, 128, 16 * 128),
+                   tc::sdesc(a_w1 + kk * 2 * (IN / 8) * 128, (IN / 8) * 128, 128), id_fT, kk > 0);
+      // [dW2; dW1] += [dh2; dh1]^T [h1, feat] over the tile's samples
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        tc::mma<FMT>(dw, tc::sdesc(a_dd + kk * 2 * 2048, 2048, 128), tc::sdesc(a_hf + kk * 2 * NG * 128, NG * 128, 128),
+                   id_w, acc_w);
+        acc_w = 1u;
+      }
+      tc::commit(&sm.bar);
+    }
+    acc_w = 1u;
+    wait_mma();
+    // tcgen05.ld is warp-collective: every lane loads, valid or not
+    float df[IN];
+#pragma unroll
+    for (int c0 = 0; c0 < IN; c0 += 16) {
+      tc::ld16(dh + lane + c0, df + c0);
+      tc::wait_ld();
+    }
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < IN; ++k) df[k] *= inv_ns;
+      const uint32_t T = 1u << q.log2T;
+#pragma unroll
+      for (int l = 0; l < IN / 2; ++l) {
+        const int N = q.res[l];
+        int ix, iy, iz;
+        float wx, wy, wz;
+        grid_cell(x, N, ix, wx);
+        grid_cell(y, N, iy, wy);
+        grid_cell(z, N, iz, wz);
+        const bool dense = (q.dense_mask >> l) & 1u;
+        const uint32_t n1 = (uint32_t)N + 1u;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) * ((c & 4) ? wz : 1.0f - wz);
+          const uint32_t idx = (uint32_t)l * T + vertex_index(dense, n1, T, ix + (c & 1), iy + ((c >> 1) & 1),
+                                                              iz + ((c >> 2) & 1));
+          atomicAdd(reinterpret_cast<float2*>(g_table) + idx, make_float2(w * df[2 * l], w * df[2 * l + 1]));
+        }
+      }
+    }
+    tc::fence_before();
+  }
+  // the CTA's weight gradients: row t of the accumulator (dW2 rows 0 .. H-1,
+  // dW1 rows 64 .. 64+H-1), dW3 summed in shared memory
+#pragma unroll
+  for (int o = 0; o < H; ++o) atomicAdd(&sm.g3[o], g3[o]);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  {
+#pragma unroll 1
+    for (int c0 = 0; c0 < H + IN; c0 += 16) {
+      float v[16];
+      tc::ld16(dw + lane + c0, v);
+      tc::wait_ld();
+      if (!acc_w)  // no tile (not reached: the grid is at most the tile count)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int c = c0 + i;
+        if (t < H && c < H) p2[(size_t)blockIdx.x * H * H + t * H + c] = v[i] * inv_ns;
+        if (t >= 64 && t < 64 + H && c >= H) p1[(size_t)blockIdx.x * H * IN + (t - 64) * IN + (c - H)] = v[i] * inv_ns;
+      }
+    }
+  }
+  for (int e = t; e < H; e += 128) p3[(size_t)blockIdx.x * H + e] = sm.g3[e] * inv_n;
+  if (loss) {
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    if ((t & 31) == 0 && r2 != 0.0f) atomicAdd(loss, r2 * inv_n);
+  }
+  if (!ok && status && t == 0) atomicOr(status, kTrainTimeout);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (t < 32) tc::tmem_dealloc(sm.tmem, kTcTrainCols);
+}
+
 int num_sms() {
   static int n = 0;
   if (!n) {
@@ -412,11 +731,43 @@ int check(const cinr_inr_s* inr, const cinr_train_opts* o) {
   return CINR_OK;
 }
 
+// Fused tensor-core step: one persistent launch (at most 2 CTAs per SM:
+// 256 TMEM columns each; at most n_part CTAs, the partial buffers' rows),
+// then the reductions of the CTAs' weight-gradient partials.
+template <int IN, int H, int FMT>
+int grads_tc(cinr_trainer_s* t, const float* xyz, const float* tgt, long n, const float* field, int3 dims,
+             uint64_t first, float* g_table, float* g_w, cudaStream_t s) {
+  const InrDev& q = t->inr->dev;
+  auto k = train_tc_kernel<IN, H, FMT>;
+  // shared memory above a third of the SM's, so that at most 2 CTAs (512
+  // TMEM columns) share an SM
+  int smem = (int)sizeof(TrainTcSmem<IN, H>) + 1024;
+  if (smem < 80 * 1024) smem = 80 * 1024;
+  CINR_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const long tiles = (n + 127) / 128;
+  long grid = 2l * num_sms();
+  if (grid > t->n_part) grid = t->n_part;
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  float* p1 = t->partial;
+  float* p2 = p1 + (size_t)grid * H * IN;
+  float* p3 = p2 + (size_t)grid * H * H;
+  k<<<(unsigned)grid, 128, smem, s>>>(q, n, xyz, tgt, field, dims, t->o.seed, first, g_table, p1, p2, p3, t->loss,
+                                      reinterpret_cast<int*>(t->loss + 1));
+  reduce_kernel<<<(H * IN + 31) / 32, 256, 0, s>>>(p1, (int)grid, H * IN, g_w);
+  reduce_kernel<<<(H * H + 31) / 32, 256, 0, s>>>(p2, (int)grid, H * H, g_w + H * IN);
+  reduce_kernel<<<(H + 31) / 32, 256, 0, s>>>(p3, (int)grid, H, g_w + H * IN + H * H);
+  CINR_CK(cudaGetLastError());
+  return CINR_OK;
+}
+
 template <int IN, int H>
 int grads(cinr_trainer_s* t, const float* xyz, const float* tgt, long n, const float* field, int3 dims,
           uint64_t first, float* g_table, float* g_w, cudaStream_t s) {
   const InrDev& q = t->inr->dev;
   CINR_CK(cudaMemsetAsync(g_table, 0, sizeof(float) * t->n_table, s));
+  if (t->tc == 1) return grads_tc<IN, H, 0>(t, xyz, tgt, n, field, dims, first, g_table, g_w, s);
+  if (t->tc == 2) return grads_tc<IN, H, 1>(t, xyz, tgt, n, field, dims, first, g_table, g_w, s);
   const int smem = mlp_floats<IN, H>() * 4;
   auto kf = fwd_kernel<IN, H>;
   auto kb = bwd_kernel<IN, H>;
@@ -494,6 +845,7 @@ extern "C" int cinr_create_trainer(cinr_inr_t inr, const cinr_train_opts* o, voi
   t->loss = L.loss;
   t->step = 0;
   t->n_part = (int)((o->batch + kChunk - 1) / kChunk);
+  t->tc = 0;
   cudaError_t ce = cudaMemsetAsync(L.m_w, 0, sizeof(float) * t->n_w, s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(L.v_w, 0, sizeof(float) * t->n_w, s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(L.loss, 0, 64 * sizeof(float), s);
@@ -517,6 +869,13 @@ extern "C" int cinr_trainer_set_lr(cinr_trainer_t t, float lr) {
   return CINR_OK;
 }
 
+extern "C" int cinr_trainer_set_tensor_cores(cinr_trainer_t t, int mode) {
+  if (!t) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (mode < 0 || mode > 2) return set_error(CINR_ERR_ARG, "mode must be 0, 1 or 2");
+  t->tc = mode;
+  return CINR_OK;
+}
+
 extern "C" int cinr_trainer_status(cinr_trainer_t t, cinr_stream_t stream) {
   if (!t) return set_error(CINR_ERR_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -526,6 +885,8 @@ extern "C" int cinr_trainer_status(cinr_trainer_t t, cinr_stream_t stream) {
   CINR_CK(cudaStreamSynchronize(s));
   if (!h) return CINR_OK;
   CINR_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  if (h & kTrainTimeout)
+    return set_error(CINR_ERR_TIMEOUT, "a bounded tensor-core wait of the fused training kernel gave up");
   return set_error(CINR_ERR_NAN, "a training step produced a non-finite gradient");
 }
 
