@@ -243,6 +243,13 @@ __device__ __forceinline__ float f_add(float a, float b) { return __fadd_rn(a, b
 __device__ __forceinline__ float f_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float f_div(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
+// clamp01(f_mul(a, b)) in one instruction: the rounded product saturated to
+// [0, 1] (a NaN product gives 0, as clamp01 does)
+__device__ __forceinline__ float f_mul_sat(float a, float b) {
+  float r;
+  asm("mul.rn.sat.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
 
 // Pairs of binary32 operations in one instruction (FADD2 / FMUL2 / FFMA2 of
 // sm_100 and later): each component is rounded as the scalar operation, so
@@ -300,7 +307,7 @@ __device__ __forceinline__ bool sample_at(const CamDev& c, const float d[3], flo
     float p = f_add(c.o[q], f_mul(tm, d[q]));
     const float num = f_add(p, c.h[q]);
     // division by an extent of exactly 1 (the longest axis) is the identity
-    x[q] = clamp01(f_mul(num, c.inv_e[q]));
+    x[q] = f_mul_sat(num, c.inv_e[q]);
   }
   return true;
 }
@@ -341,7 +348,7 @@ __device__ __forceinline__ bool sample_in(const CamDev& c, const float d[3], flo
   for (int q = 0; q < 3; ++q) {
     const float p = f_add(c.o[q], f_mul(tm, d[q]));
     const float num = f_add(p, c.h[q]);
-    x[q] = clamp01(f_mul(num, c.inv_e[q]));
+    x[q] = f_mul_sat(num, c.inv_e[q]);
   }
   return true;
 }

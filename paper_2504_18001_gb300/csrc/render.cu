@@ -706,7 +706,12 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
   __shared__ uint32_t s_rare[2];
   const CacheDev& c = P.cache;
   if (threadIdx.x < 2) s_rare[threadIdx.x] = 0u;
-  for (int i = threadIdx.x; i < 256; i += kFrameThreads) s_tf[i] = P.tf[i];
+  // the extinction channel pre-multiplied by -log2(e): alpha = 1 - 2^(w len)
+  for (int i = threadIdx.x; i < 256; i += kFrameThreads) {
+    float4 e = P.tf[i];
+    e.w *= -1.4426950408889634f;
+    s_tf[i] = e;
+  }
   if (threadIdx.x < c.L) {
     const int l = threadIdx.x;
     LevelGeo g;
@@ -769,9 +774,9 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
       const float bnd = fminf(an, tf);
       const float tm = f_mul(f_add(a, bnd), 0.5f);
       const float len = f_sub(bnd, a);
-      const float pv0 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[0], f_mul(tm, d[0])), cam.h[0]), cam.inv_e[0])), volf0);
-      const float pv1 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[1], f_mul(tm, d[1])), cam.h[1]), cam.inv_e[1])), volf1);
-      const float pv2 = f_mul(clamp01(f_mul(f_add(f_add(cam.o[2], f_mul(tm, d[2])), cam.h[2]), cam.inv_e[2])), volf2);
+      const float pv0 = f_mul(f_mul_sat(f_add(f_add(cam.o[0], f_mul(tm, d[0])), cam.h[0]), cam.inv_e[0]), volf0);
+      const float pv1 = f_mul(f_mul_sat(f_add(f_add(cam.o[1], f_mul(tm, d[1])), cam.h[1]), cam.inv_e[1]), volf1);
+      const float pv2 = f_mul(f_mul_sat(f_add(f_add(cam.o[2], f_mul(tm, d[2])), cam.h[2]), cam.inv_e[2]), volf2);
       // stochastic LoD, footprint mode (sample_lod)
       const float xf = f_mul(tm, cam.lodc);
       int l = 0;
@@ -871,7 +876,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
       if (changed) stamped = hit_slot;
       // transfer function and front-to-back compositing
       const float4 e4 = tf_lookup_fast(s_tf, v);
-      const float alpha = 1.0f - ex2_approx(e4.w * (len * -1.4426950408889634f));
+      const float alpha = 1.0f - ex2_approx(e4.w * len);
       const float wgt = active ? T * alpha : 0.0f;
       Cr = fmaf(wgt, e4.x, Cr);
       Cg = fmaf(wgt, e4.y, Cg);
@@ -1060,7 +1065,7 @@ __device__ __forceinline__ void pt_point(const CamDev& c, const float o[3], cons
   for (int q = 0; q < 3; ++q) {
     p[q] = f_add(o[q], f_mul(t, d[q]));
     const float num = f_add(p[q], c.h[q]);
-    x[q] = clamp01(f_mul(num, c.inv_e[q]));
+    x[q] = f_mul_sat(num, c.inv_e[q]);
   }
   const float dx = f_sub(p[0], c.o[0]), dy = f_sub(p[1], c.o[1]), dz = f_sub(p[2], c.o[2]);
   dist = __fsqrt_rn(f_add(f_add(f_mul(dx, dx), f_mul(dy, dy)), f_mul(dz, dz)));
@@ -1085,7 +1090,7 @@ struct PtWalk {
 __device__ __forceinline__ void walk_axis(const MacroDev& m, const CamDev& cam, int a, float o, float d,
                                           float t, int& c, int& st, float& tm, float& td) {
   const float p = f_add(o, f_mul(t, d));
-  const float x = clamp01(f_mul(f_add(p, cam.h[a]), cam.inv_e[a]));
+  const float x = f_mul_sat(f_add(p, cam.h[a]), cam.inv_e[a]);
   const float pv = f_mul(x, (float)cam.vol[a]);
   c = min((int)pv >> m.shift, m.dims[a] - 1);
   const float dv = f_mul(f_mul(d, cam.inv_e[a]), (float)cam.vol[a]);
