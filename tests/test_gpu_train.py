@@ -167,6 +167,31 @@ def test_tensor_core_training_gains_over_untrained_network():
     assert after > 30.0, after
 
 
+@pytest.mark.parametrize("mode", [1, 2], ids=["fp16", "bf16"])
+def test_tensor_core_training_tracks_fp32_training(mode):
+    # the same 200 Adam steps from the same start with the FP32 kernels and
+    # with the fused tensor-core kernel: the loss curves agree to within
+    # the gradients' stated error (float atomics make even two FP32 runs
+    # differ in the last bits)
+    import torch
+    from paper_2504_18001_gb300 import cinr
+    cfg = S.InrConfig(levels=8, feats=2, log2_table=14, base_res=4, growth=1.5, hidden=32)
+    table, w = S.inr_init(cfg, seed=9, table_scale=1e-4)
+    field = torch.from_numpy(S.explicit_field((48, 48, 48), S.field_params(2, n_gaussians=16))).cuda()
+    curves = []
+    for tc in (0, mode):
+        inr = _inr(cfg, table, w)
+        tr = cinr.Trainer(inr, batch=1 << 15, seed=4)
+        tr.set_tensor_cores(tc)
+        curves.append(np.array([tr.step(field).item() for _ in range(200)]))
+        tr.status()
+    ref, got = curves
+    print(f"tc-track mode {mode}: final loss fp32 {ref[-1]:.3e} tc {got[-1]:.3e}")
+    assert ref[-1] < 0.05 * ref[0]
+    # the last 50 steps' mean losses within 25% of each other
+    assert abs(got[-50:].mean() - ref[-50:].mean()) <= 0.25 * ref[-50:].mean()
+
+
 def test_one_call_train_matches_oracle_adam():
     # cinr_train = a fresh trainer's steps: after 3 steps the parameters
     # follow the oracle's Adam path as the step-by-step trainer's do
