@@ -682,14 +682,16 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
 }
 
 // The marching kernel specialised on the common configuration: fixed steps
-// (step_mode 0), footprint LoD (lod_mode 0), flat page tables, no macro
+// (step_mode 0; STEP: LoD-scaled 32-sample segments, step_mode 1),
+// footprint LoD (lod_mode 0), flat page tables, no macro
 // cells, the coarsest LoD preloaded (every fallback walk ends at a mapped
 // brick) and the brick size BB a compile-time power of two.  It takes the
 // same samples, LoDs, lookups, requests, stamps and values as
 // march_cached_kernel, in the same binary32 operations; what it saves is
 // bookkeeping and control flow: no per-sample tests of the run-time modes;
 // the start of the next sample carried over from this sample's unclipped
-// end (the same tn + (k+1) dt); the dither key k * 0x9E3779B9 advanced by
+// end (the same tn + (k+1) dt, or ts + (j+1) dts in a segment, whose last
+// sample's end is the next segment's start); the dither key k * 0x9E3779B9 advanced by
 // addition; brick and voxel coordinates of non-negative values truncated
 // (the floor of a non-negative binary32); brick indices from one product
 // with 2^-l / B (products with powers of two are exact); the sample count
@@ -698,7 +700,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_cached_kernel(const __
 // fallback walks, requests, first stamps of a slot, ray ends -- behind
 // warp-uniform votes, so that the warp issues no divergent branches on
 // its common path (all lanes of a warp march the same sample index k).
-template <bool F16POOL, int BB, bool TEX = false>
+template <bool F16POOL, int BB, bool TEX = false, bool STEP = false>
 __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __grid_constant__ FrameParams P) {
   static_assert(BB > 0 && (BB & (BB - 1)) == 0, "brick size must be a power of two");
   __shared__ float4 s_tf[256];
@@ -758,6 +760,10 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
     int k = 0, seg = P.K;
     float a = tn;         // start of sample k: tn + k dt (tn + 0 dt = tn)
     float kf1 = 1.0f;     // k + 1 as binary32 (exact below 2^24)
+    // LoD-scaled steps (sched_segment): segment start ts, step dts,
+    // j + 1 for the sample's index j in the segment
+    float ts = tn, dts = 0.f, jf1 = 1.0f;
+    if (STEP) dts = f_mul(cam.dt, (float)(1 << step_level(cam, tn)));
     uint32_t kh = 0u;     // k * 0x9E3779B9
     if (active && !(a < tf)) {  // (tn < tf for a hit: not reached)
       P.out[pixel] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -770,7 +776,7 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
     // first stamps, ray ends -- sit behind warp-uniform tests.
     while (__any_sync(kFull, active)) {
       // sample k: midpoint of [a, min(tn + (k+1) dt, tf)] (sample_at)
-      const float an = f_add(tn, f_mul(kf1, cam.dt));
+      const float an = STEP ? f_add(ts, f_mul(jf1, dts)) : f_add(tn, f_mul(kf1, cam.dt));
       const float bnd = fminf(an, tf);
       const float tm = f_mul(f_add(a, bnd), 0.5f);
       const float len = f_sub(bnd, a);
@@ -887,6 +893,15 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
         kf1 = f_add(kf1, 1.0f);
         ++k;
         kh += 0x9E3779B9u;
+        if (STEP) {
+          if (jf1 == 32.0f) {  // the next 32-sample segment starts at this sample's end
+            ts = an;
+            dts = f_mul(cam.dt, (float)(1 << step_level(cam, ts)));
+            jf1 = 1.0f;
+          } else {
+            jf1 = f_add(jf1, 1.0f);
+          }
+        }
       }
       // termination after every K samples (k is the same for the warp's
       // active lanes) and the end of the ray
@@ -922,9 +937,9 @@ __global__ void __launch_bounds__(kFrameThreads, 8) march_fast_kernel(const __gr
   }
 }
 
-template <bool F16POOL, int BB, bool TEX = false>
+template <bool F16POOL, int BB, bool TEX = false, bool STEP = false>
 int launch_march_fast(const FrameParams& P, cudaStream_t s) {
-  auto k = march_fast_kernel<F16POOL, BB, TEX>;
+  auto k = march_fast_kernel<F16POOL, BB, TEX, STEP>;
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     CINR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kFrameThreads, 0));
@@ -952,16 +967,19 @@ int launch_march_cached(const FrameParams& P, cudaStream_t s) {
 // without, the shape plays no part and the brick size is specialised.
 template <bool F16POOL>
 int launch_march_cached_pool(const FrameParams& P, bool miss, cudaStream_t s) {
-  const bool common = !miss && P.cam.step_mode == 0 && P.cam.lod_mode == 0 && !P.cache.pd && !P.mac.skip;
+  const bool common = !miss && P.cam.lod_mode == 0 && !P.cache.pd && !P.mac.skip;
+  const bool step = P.cam.step_mode != 0;
   if (P.cache.pool_tex) {  // FP16 bricks in the texture layout: the specialised kernel only
-    if (F16POOL && common && P.cache.B == 8) return launch_march_fast<true, 8, true>(P, s);
-    if (F16POOL && common && P.cache.B == 16) return launch_march_fast<true, 16, true>(P, s);
+    if (F16POOL && common && !step && P.cache.B == 8) return launch_march_fast<true, 8, true>(P, s);
+    if (F16POOL && common && !step && P.cache.B == 16) return launch_march_fast<true, 16, true>(P, s);
     return set_error(CINR_ERR_UNSUPPORTED,
                      "the texture layout serves fixed steps, footprint LoD, flat tables, no macro cells, "
                      "a preloaded coarsest LoD and bricks of 8 or 16 only");
   }
-  if (common && P.cache.B == 8) return launch_march_fast<F16POOL, 8>(P, s);
-  if (common && P.cache.B == 16) return launch_march_fast<F16POOL, 16>(P, s);
+  if (common && !step && P.cache.B == 8) return launch_march_fast<F16POOL, 8>(P, s);
+  if (common && !step && P.cache.B == 16) return launch_march_fast<F16POOL, 16>(P, s);
+  if (common && step && P.cache.B == 8) return launch_march_fast<F16POOL, 8, false, true>(P, s);
+  if (common && step && P.cache.B == 16) return launch_march_fast<F16POOL, 16, false, true>(P, s);
   if (!miss) {
     switch (P.cache.B) {
       case 8: return launch_march_cached<16, 32, F16POOL, false, 8>(P, s);
