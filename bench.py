@@ -744,6 +744,7 @@ def run_learned(args):
     inr = cinr.Inr(cinr.make_inr_params(cfg), table, w)
     tr = cinr.Trainer(inr, batch=1 << 18, lr=1e-2, seed=args.seed)
     tr.set_tensor_cores(args.train_tc)
+    tr.set_stratified(args.train_strat)
     for _ in range(3):  # warm-up steps (timed separately)
         tr.step(field)
     torch.cuda.synchronize()
@@ -805,6 +806,8 @@ def run_learned(args):
         "config": {"workload": f"learned_inr_{args.field}cube_{W}px",
                    "inr": "L16 F2 T2^20 Nmin16 b1.38 MLP32-64-64-1", "batch": 1 << 18,
                    "lr": "1e-2, exponential decay to 1e-3 over the last fifth of the steps",
+                   "coordinates": ("stratified: one per cell of a 64^3 Morton-ordered grid per batch"
+                                   if args.train_strat else "uniform"),
                    "steps": args.train_steps, "frames": args.learned_frames,
                    "training_kernels": ("one fused kernel per step, MLP products on the tensor cores (%s)"
                                         % {1: "FP16, loss scale 256", 2: "BF16"}[args.train_tc]
@@ -950,6 +953,8 @@ def main():
     ap.add_argument("--field", type=int, default=1024, help="learned: explicit field edge")
     ap.add_argument("--train-steps", type=int, default=5000, help="learned: Adam steps")
     ap.add_argument("--learned-frames", type=int, default=60, help="learned: cached frames")
+    ap.add_argument("--train-strat", type=int, default=0, choices=[0, 1],
+                    help="learned: 1 stratified coordinates (one per cell of a Morton-ordered grid)")
     ap.add_argument("--train-tc", type=int, default=1, choices=[0, 1, 2],
                     help="learned: fused tensor-core training kernel with 1 FP16 / 2 BF16 operands, 0 FP32 kernels")
     args = ap.parse_args()

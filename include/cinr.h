@@ -519,6 +519,18 @@ int cinr_trainer_set_lr(cinr_trainer_t t, float lr);
  * Errors: CINR_ERR_ARG. */
 int cinr_trainer_set_tensor_cores(cinr_trainer_t t, int mode);
 
+/* Stratified training coordinates (Sec. 4.1's random coordinates, drawn
+ * per stratum) for the following steps: 1 -- sample s < 8^g of a batch of
+ * n (8^g the largest power of eight <= n) takes one point uniform in cell s
+ * of a 2^g grid over the unit cube, cells in Morton order, the rest of the
+ * batch uniform in the cube; 0 (the default) -- every sample uniform in the
+ * cube (the oracle's definition).  Both give an unbiased estimate of the
+ * field's mean squared error; stratified batches put each 128-sample tile
+ * in a compact region, so its coarse table entries are shared.  The points
+ * come from the same counter-based draws.  Host-side only.
+ * Errors: CINR_ERR_ARG. */
+int cinr_trainer_set_stratified(cinr_trainer_t t, int on);
+
 /* Whether any training step since the last call produced a non-finite
  * gradient (a NaN or infinite field value, or a diverged run): CINR_OK or
  * CINR_ERR_NAN (the flag is then cleared).  Synchronises `stream`. */

@@ -130,6 +130,7 @@ _SIGS = {
     "cinr_trainer_status": [_vp, _vp],
     "cinr_trainer_set_lr": [_vp, C.c_float],
     "cinr_trainer_set_tensor_cores": [_vp, C.c_int],
+    "cinr_trainer_set_stratified": [_vp, C.c_int],
     "cinr_train": [_vp, _vp, _P(C.c_int), _vp, C.c_long, _vp, C.c_size_t, _vp],
     "cinr_inr_export": [_vp, _vp, _vp, _vp],
     "cinr_debug_dump": [_vp, C.c_int, _vp, C.c_size_t, _P(C.c_size_t), _vp],
@@ -490,6 +491,10 @@ class Trainer:
 
     def set_lr(self, lr):
         check(lib().cinr_trainer_set_lr(self.h, float(lr)), "cinr_trainer_set_lr")
+
+    def set_stratified(self, on):
+        """1: one coordinate per cell of a Morton-ordered grid per batch; 0: uniform."""
+        check(lib().cinr_trainer_set_stratified(self.h, int(on)), "cinr_trainer_set_stratified")
 
     def set_tensor_cores(self, mode):
         """The fused tensor-core forward / backward kernel with 1 FP16 or

@@ -34,6 +34,7 @@ struct cinr_trainer_s {
   long step;
   int n_part;         // blocks of the outer-product reduction
   int tc;             // fused tensor-core forward / backward (train_tc_kernel): 1 FP16, 2 BF16; 0 FP32 kernels
+  int strat;          // 1: stratified coordinates (train_point)
 };
 
 namespace {
@@ -51,8 +52,23 @@ __device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
 }
 
 // Coordinates of sample s: given, or the counter-based uniform of the step.
+// strat = g >= 0 (stratified sampling): samples s < 8^g take one point
+// each in cell s of a 2^g grid over the unit cube, cells in Morton order
+// (consecutive samples are spatially close), the point uniform in its cell
+// from the same counter-based draws; the others (and strat < 0) are
+// uniform in the cube.  Either way every sample is uniform over its stratum
+// and the batch is an unbiased estimate of the field's mean squared error.
+__device__ __forceinline__ uint32_t morton_compact3(uint32_t v) {
+  v &= 0x09249249u;
+  v = (v ^ (v >> 2)) & 0x030C30C3u;
+  v = (v ^ (v >> 4)) & 0x0300F00Fu;
+  v = (v ^ (v >> 8)) & 0x030000FFu;
+  v = (v ^ (v >> 16)) & 0x000003FFu;
+  return v;
+}
+
 __device__ __forceinline__ void train_point(const float* xyz_in, uint64_t seed, uint64_t first, long s,
-                                            float& x, float& y, float& z) {
+                                            float& x, float& y, float& z, int strat = -1) {
   if (xyz_in) {
     x = xyz_in[3 * s];
     y = xyz_in[3 * s + 1];
@@ -62,6 +78,13 @@ __device__ __forceinline__ void train_point(const float* xyz_in, uint64_t seed, 
     x = (float)(splitmix64_dev(seed + c0) >> 40) * (1.0f / 16777216.0f);
     y = (float)(splitmix64_dev(seed + c0 + 1) >> 40) * (1.0f / 16777216.0f);
     z = (float)(splitmix64_dev(seed + c0 + 2) >> 40) * (1.0f / 16777216.0f);
+    if (strat >= 0 && s < (1l << (3 * strat))) {
+      const uint32_t m = (uint32_t)s;
+      const float inv = __int_as_float((127 - strat) << 23);  // 2^-g, exact
+      x = ((float)morton_compact3(m) + x) * inv;
+      y = ((float)morton_compact3(m >> 1) + y) * inv;
+      z = ((float)morton_compact3(m >> 2) + z) * inv;
+    }
   }
   x = clamp01(x);
   y = clamp01(y);
@@ -76,7 +99,7 @@ __global__ void __launch_bounds__(kFwdThreads, IN <= 32 ? 4 : 2) fwd_kernel(InrD
                                                           const float* __restrict__ tgt_in,
                                                           const float* __restrict__ field, int3 dims,
                                                           uint64_t seed, uint64_t first, float* __restrict__ act,
-                                                          float* __restrict__ loss) {
+                                                          float* __restrict__ loss, int strat) {
   extern __shared__ float4 smem4[];
   float* sw = reinterpret_cast<float*>(smem4);
   load_weights(sw, q.w, mlp_floats<IN, H>());
@@ -88,7 +111,7 @@ __global__ void __launch_bounds__(kFwdThreads, IN <= 32 ? 4 : 2) fwd_kernel(InrD
   float r2 = 0.0f;
   if (s < n) {
     float x, y, z;
-    train_point(xyz_in, seed, first, s, x, y, z);
+    train_point(xyz_in, seed, first, s, x, y, z, strat);
     const float t = tgt_in ? tgt_in[s] : field_trilinear(field, dims, x, y, z);
     float* a_feat = act;
     float* a_h1 = act + (size_t)IN * n;
@@ -138,7 +161,7 @@ __global__ void __launch_bounds__(kFwdThreads, IN <= 32 ? 4 : 2) fwd_kernel(InrD
 template <int IN, int H>
 __global__ void __launch_bounds__(kFwdThreads, IN <= 32 ? 4 : 2) bwd_kernel(InrDev q, long n, const float* __restrict__ xyz_in,
                                                           uint64_t seed, uint64_t first, float* __restrict__ act,
-                                                          float* __restrict__ g_table) {
+                                                          float* __restrict__ g_table, int strat) {
   extern __shared__ float4 smem4[];
   float* sw = reinterpret_cast<float*>(smem4);
   load_weights(sw, q.w, mlp_floats<IN, H>());
@@ -177,7 +200,7 @@ __global__ void __launch_bounds__(kFwdThreads, IN <= 32 ? 4 : 2) bwd_kernel(InrD
     dfeat[k] = acc;
   }
   float x, y, z;
-  train_point(xyz_in, seed, first, s, x, y, z);
+  train_point(xyz_in, seed, first, s, x, y, z, strat);
   const uint32_t T = 1u << q.log2T;
 #pragma unroll
   for (int l = 0; l < IN / 2; ++l) {
@@ -448,7 +471,7 @@ __global__ void __launch_bounds__(128, 2) train_tc_kernel(InrDev q, long n, cons
                                                           uint64_t first, float* __restrict__ g_table,
                                                           float* __restrict__ p1, float* __restrict__ p2,
                                                           float* __restrict__ p3, float* __restrict__ loss,
-                                                          int* __restrict__ status) {
+                                                          int* __restrict__ status, int strat) {
   using SM = TrainTcSmem<IN, H>;
   constexpr int NG = SM::NG;
   static_assert(IN % 16 == 0 && H % 16 == 0 && H <= 64 && (H + IN) % 16 == 0, "fused training shape");
@@ -511,7 +534,7 @@ __global__ void __launch_bounds__(128, 2) train_tc_kernel(InrDev q, long n, cons
 #pragma unroll
       for (int k = 0; k < IN; ++k) feat[k] = 0.0f;
       if (valid) {
-        train_point(xyz_in, seed, first, s, x, y, z);
+        train_point(xyz_in, seed, first, s, x, y, z, strat);
         target = tgt_in ? tgt_in[s] : field_trilinear(field, dims, x, y, z);
         encode_point<IN / 2>(q, x, y, z, feat);
       }
@@ -731,6 +754,15 @@ int check(const cinr_inr_s* inr, const cinr_train_opts* o) {
   return CINR_OK;
 }
 
+// log2 of the stratified sampling grid's edge for a batch of n (the
+// largest g with 8^g <= n), or -1 when the trainer samples uniformly.
+int strat_of(const cinr_trainer_s* t, long n) {
+  if (!t->strat) return -1;
+  int g = 0;
+  while (g < 10 && (1l << (3 * (g + 1))) <= n) ++g;
+  return g;
+}
+
 // Fused tensor-core step: one persistent launch (at most 2 CTAs per SM:
 // 256 TMEM columns each; at most n_part CTAs, the partial buffers' rows),
 // then the reductions of the CTAs' weight-gradient partials.
@@ -753,7 +785,7 @@ int grads_tc(cinr_trainer_s* t, const float* xyz, const float* tgt, long n, cons
   float* p2 = p1 + (size_t)grid * H * IN;
   float* p3 = p2 + (size_t)grid * H * H;
   k<<<(unsigned)grid, 128, smem, s>>>(q, n, xyz, tgt, field, dims, t->o.seed, first, g_table, p1, p2, p3, t->loss,
-                                      reinterpret_cast<int*>(t->loss + 1));
+                                      reinterpret_cast<int*>(t->loss + 1), strat_of(t, n));
   reduce_kernel<<<(H * IN + 31) / 32, 256, 0, s>>>(p1, (int)grid, H * IN, g_w);
   reduce_kernel<<<(H * H + 31) / 32, 256, 0, s>>>(p2, (int)grid, H * H, g_w + H * IN);
   reduce_kernel<<<(H + 31) / 32, 256, 0, s>>>(p3, (int)grid, H, g_w + H * IN + H * H);
@@ -774,8 +806,8 @@ int grads(cinr_trainer_s* t, const float* xyz, const float* tgt, long n, const f
   CINR_CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   CINR_CK(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const unsigned grid = (unsigned)((n + kFwdThreads - 1) / kFwdThreads);
-  kf<<<grid, kFwdThreads, smem, s>>>(q, n, xyz, tgt, field, dims, t->o.seed, first, t->act, t->loss);
-  kb<<<grid, kFwdThreads, smem, s>>>(q, n, xyz, t->o.seed, first, t->act, g_table);
+  kf<<<grid, kFwdThreads, smem, s>>>(q, n, xyz, tgt, field, dims, t->o.seed, first, t->act, t->loss, strat_of(t, n));
+  kb<<<grid, kFwdThreads, smem, s>>>(q, n, xyz, t->o.seed, first, t->act, g_table, strat_of(t, n));
   CINR_CK(cudaGetLastError());
   const int blocks = (int)((n + kChunk - 1) / kChunk);
   const float* a_feat = t->act;
@@ -846,6 +878,7 @@ extern "C" int cinr_create_trainer(cinr_inr_t inr, const cinr_train_opts* o, voi
   t->step = 0;
   t->n_part = (int)((o->batch + kChunk - 1) / kChunk);
   t->tc = 0;
+  t->strat = 0;
   cudaError_t ce = cudaMemsetAsync(L.m_w, 0, sizeof(float) * t->n_w, s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(L.v_w, 0, sizeof(float) * t->n_w, s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(L.loss, 0, 64 * sizeof(float), s);
@@ -873,6 +906,13 @@ extern "C" int cinr_trainer_set_tensor_cores(cinr_trainer_t t, int mode) {
   if (!t) return set_error(CINR_ERR_ARG, "NULL argument");
   if (mode < 0 || mode > 2) return set_error(CINR_ERR_ARG, "mode must be 0, 1 or 2");
   t->tc = mode;
+  return CINR_OK;
+}
+
+extern "C" int cinr_trainer_set_stratified(cinr_trainer_t t, int on) {
+  if (!t) return set_error(CINR_ERR_ARG, "NULL argument");
+  if (on != 0 && on != 1) return set_error(CINR_ERR_ARG, "on must be 0 or 1");
+  t->strat = on;
   return CINR_OK;
 }
 

@@ -105,6 +105,7 @@ def test_null_handles_are_rejected_without_device_work(L):
     # every entry point that takes a handle checks it before any CUDA call
     assert L.cinr_trainer_set_lr(None, C.c_float(1e-3)) == cinr.ERR_ARG
     assert L.cinr_trainer_set_tensor_cores(None, 1) == cinr.ERR_ARG
+    assert L.cinr_trainer_set_stratified(None, 1) == cinr.ERR_ARG
     assert L.cinr_cache_set_decode_encoder(None, 1) == cinr.ERR_ARG
     assert L.cinr_trainer_status(None, None) == cinr.ERR_ARG
     assert L.cinr_debug_wait_timeout(None, 16, None) == cinr.ERR_ARG

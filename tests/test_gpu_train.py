@@ -167,8 +167,8 @@ def test_tensor_core_training_gains_over_untrained_network():
     assert after > 30.0, after
 
 
-@pytest.mark.parametrize("mode", [1, 2], ids=["fp16", "bf16"])
-def test_tensor_core_training_tracks_fp32_training(mode):
+@pytest.mark.parametrize("mode,strat", [(1, 0), (2, 0), (1, 1)], ids=["fp16", "bf16", "fp16-stratified"])
+def test_tensor_core_training_tracks_fp32_training(mode, strat):
     # the same 200 Adam steps from the same start with the FP32 kernels and
     # with the fused tensor-core kernel: the loss curves agree to within
     # the gradients' stated error (float atomics make even two FP32 runs
@@ -183,10 +183,11 @@ def test_tensor_core_training_tracks_fp32_training(mode):
         inr = _inr(cfg, table, w)
         tr = cinr.Trainer(inr, batch=1 << 15, seed=4)
         tr.set_tensor_cores(tc)
+        tr.set_stratified(strat if tc else 0)  # the reference run samples uniformly
         curves.append(np.array([tr.step(field).item() for _ in range(200)]))
         tr.status()
     ref, got = curves
-    print(f"tc-track mode {mode}: final loss fp32 {ref[-1]:.3e} tc {got[-1]:.3e}")
+    print(f"tc-track mode {mode} strat {strat}: final loss fp32 {ref[-1]:.3e} tc {got[-1]:.3e}")
     assert ref[-1] < 0.05 * ref[0]
     # the last 50 steps' mean losses within 25% of each other
     assert abs(got[-50:].mean() - ref[-50:].mean()) <= 0.25 * ref[-50:].mean()
