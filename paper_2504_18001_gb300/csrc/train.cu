@@ -3,15 +3,23 @@
 // the MLP and the hash-grid interpolation (scatter-add of table gradients),
 // and Adam on the FP32 master parameters.
 //
-// Per step:
-//   fwd_bwd_kernel   one thread per sample: coordinates (counter-based
-//                    SplitMix64), trilinear ground truth, encode, MLP
-//                    forward, loss, MLP backward to the feature gradient,
-//                    atomic scatter-add into the table gradient; the
-//                    activations the weight gradients need are stored
-//                    structure-of-arrays (feature-major) for the next kernel;
-//   outer_kernel     weight gradients dW = sum_s a_s b_s^T over the batch,
-//                    split over blocks (partials), then reduce_kernel;
+// Per step, either
+//   train_tc_kernel  one fused kernel over 128-sample tiles: coordinates
+//                    (counter-based SplitMix64), trilinear ground truth,
+//                    encode, the MLP's forward, backward and weight-gradient
+//                    products on the tensor cores (FP16 or BF16 operands,
+//                    FP32 accumulation), loss, dW3, scatter-add into the
+//                    table gradient; the CTAs' weight-gradient partials go
+//                    to reduce_kernel;
+// or the FP32 kernels
+//   fwd_kernel       one thread per sample: coordinates, ground truth,
+//                    encode, MLP forward, loss; activations stored
+//                    feature-major for the weight gradients;
+//   bwd_kernel       MLP backward to the feature gradient, scatter-add into
+//                    the table gradient;
+//   outer_kernel /   weight gradients dW = sum_s a_s b_s^T over the batch,
+//   vec_kernel       split over blocks (partials), then reduce_kernel;
+// then
 //   adam_kernel      bias-corrected Adam over table and weights, and the
 //                    half-precision weight copy refreshed.
 #include <cmath>
