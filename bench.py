@@ -896,6 +896,7 @@ def other_configs(args):
         r = run_learned(a)
         out["learned"] = {"workload": r["config"]["workload"], "psnr_db": r["value"],
                           "psnr_untrained_db": r["psnr_untrained_db"], "train": r["train"],
+                          "training_kernels": r["config"]["training_kernels"],
                           "cached_ms_per_frame_last5": r["cached_ms_per_frame_last5"],
                           "quality_gate_ok": bool(r["value"] >= 40.0)}
     except Exception as e:
