@@ -342,15 +342,40 @@ __device__ __forceinline__ float mlp_tile(TcSmem<IN, H>& s, const float* feat, b
   fence_after();
   const uint32_t lane_addr = dt + ((uint32_t)(warp * 32) << 16);
   {
-    float h[H];
+    if (FMT == 2) {
+      float h[H];
 #pragma unroll
-    for (int c0 = 0; c0 < H; c0 += 16) {
-      ld16(lane_addr + c0, h + c0);
-      wait_ld();
+      for (int c0 = 0; c0 < H; c0 += 16) {
+        ld16(lane_addr + c0, h + c0);
+        wait_ld();
+      }
+#pragma unroll
+      for (int i = 0; i < H; ++i) h[i] = fmaxf(h[i], 0.0f);
+      store_row<FMT, H>(s.a2, t, h);
+    } else {
+      // 16-bit operands: ReLU and rounding in one paired conversion (a
+      // negative value rounds to a non-positive one, which becomes +0, as
+      // rounding the ReLU's +0 does), 16 bytes per store
+#pragma unroll
+      for (int c0 = 0; c0 < H; c0 += 16) {
+        float v[16];
+        ld16(lane_addr + c0, v);
+        wait_ld();
+#pragma unroll
+        for (int h8 = 0; h8 < 16; h8 += 8) {
+          uint32_t w[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const float lo = v[h8 + 2 * p], hi = v[h8 + 2 * p + 1];
+            if (FMT == 1)
+              asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w[p]) : "f"(hi), "f"(lo));
+            else
+              asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(w[p]) : "f"(hi), "f"(lo));
+          }
+          *reinterpret_cast<uint4*>(s.a2 + core_off(t, c0 + h8, H)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
     }
-#pragma unroll
-    for (int i = 0; i < H; ++i) h[i] = fmaxf(h[i], 0.0f);
-    store_row<FMT, H>(s.a2, t, h);
   }
   fence_before();
   fence_proxy_async();
@@ -374,7 +399,13 @@ __device__ __forceinline__ float mlp_tile(TcSmem<IN, H>& s, const float* feat, b
     ld16(lane_addr + c0, v);
     wait_ld();
 #pragma unroll
-    for (int i = 0; i < 16; ++i) y = fmaf(s.w3[c0 + i], fmaxf(v[i], 0.0f), y);
+    for (int i = 0; i < 16; i += 4) {  // the output weights four at a time, the sum in order
+      const float4 w3 = *reinterpret_cast<const float4*>(s.w3 + c0 + i);
+      y = fmaf(w3.x, fmaxf(v[i], 0.0f), y);
+      y = fmaf(w3.y, fmaxf(v[i + 1], 0.0f), y);
+      y = fmaf(w3.z, fmaxf(v[i + 2], 0.0f), y);
+      y = fmaf(w3.w, fmaxf(v[i + 3], 0.0f), y);
+    }
   }
   fence_before();
   if (!ok && err) atomicOr(err, kErrTimeout);
