@@ -61,3 +61,38 @@ def test_gpu_arm_line():
     g = d["quality_gate"]
     assert g["ok"] and g["worst_db"] >= 40.0 and g["min_db"] == 40.0
     assert e["same_cache_state_as_timed_frames"] is True
+
+
+def test_profile_counters_only_for_the_profiled_sources(tmp_path, monkeypatch):
+    # the roofline's DRAM traffic and instruction counts come from an ncu
+    # summary only while the kernel sources hash to the value it records
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    for rel in bench.KERNEL_SOURCES:
+        dst = tmp_path / rel
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        dst.write_bytes(open(os.path.join(ROOT, rel), "rb").read())
+    h = hashlib.sha256()
+    for rel in bench.KERNEL_SOURCES:
+        h.update((tmp_path / rel).read_bytes())
+    (tmp_path / "profiles").mkdir()
+    summary = tmp_path / "profiles" / "p.md"
+
+    def write(digest):
+        summary.write_text("# kernel\n\n- frame: 95\n- samples: 100\n- dram_bytes: 2000\n"
+                           f"- warp_instructions: 700\n- thread_instructions: 22000\n"
+                           f"- kernel_source_sha256_12: {digest}\n")
+
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "PROFILE_FILES", {"orbit": "p.md"})
+    write(h.hexdigest()[:12])
+    got = bench.profiled_counters("orbit")
+    assert got is not None and got["dram_bytes"] == 2000.0 and got["frame"] == 95
+    write("000000000000")
+    assert bench.profiled_counters("orbit") is None
+    # a changed source invalidates a summary that matched before
+    write(h.hexdigest()[:12])
+    src = tmp_path / bench.KERNEL_SOURCES[0]
+    src.write_bytes(src.read_bytes() + b"\n// changed\n")
+    assert bench.profiled_counters("orbit") is None
